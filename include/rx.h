@@ -1,0 +1,186 @@
+/*
+ * rx.h -- C ABI of the GB300 dual-polarisation coherent-receiver DSP chain.
+ *
+ * The chain is the coherent analogue of the real-time GPU receiver of
+ * arXiv 2104.06311 (Section "Experimental setup", paragraph on the processing
+ * chain, Fig. 1b): sample buffers are converted to floating point, filtered
+ * by an FFT/IFFT pair in overlap-save form (static frequency-domain
+ * equalisation), equalised by a sequential decision-directed LMS in the time
+ * domain, decided and demapped; Q-factors follow from BER counts (Section
+ * "Results and Discussion").  Per buffer of sample-times this library runs:
+ *
+ *   ingest (int8 or f32, times a scale)
+ *   -> CDC: overlap-save FFT_N, multiply by exp(-j beta2 L w^2/2) * sqrt(2) * RRC, IFFT_N
+ *   -> frequency-offset removal exp(-j phi_n) in front of the equaliser
+ *   -> 2x2 butterfly FIR, block CMA then DD-LMS (acquisition + segment waves)
+ *   -> blind phase search (B test angles, +-Nb window) with integer unwrap
+ *   -> hard Gray bits (packed), optional max-log LLRs and symbols
+ *   -> BER with rotation / polarisation / delay synchronisation (rx_ber).
+ *
+ * Conventions
+ *   - One sample-time = Xi, Xq, Yi, Yq (4 scalars), 2 samples per symbol.
+ *   - Device pointers are CUDA device addresses owned by the caller; the
+ *     library never frees them.  The library allocates device memory only in
+ *     rx_reserve (or implicitly on the first rx_process) and frees it in
+ *     rx_destroy.
+ *   - Every call is asynchronous on the bound CUDA stream (rx_set_cuda_stream;
+ *     default: the legacy default stream) except rx_ber, rx_get_state,
+ *     rx_set_state, rx_trace and rx_sync, which synchronise that stream.
+ *   - Errors are status codes; nothing throws across the ABI, nothing aborts,
+ *     no kernel traps.  Device-side faults (a wait that timed out) set a
+ *     sticky error word reported by the next call (RX_ETIMEOUT).
+ *   - One handle must be used by one host thread at a time.
+ */
+#ifndef RX_H_
+#define RX_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rx_stream rx_stream;
+
+typedef enum {
+  RX_OK = 0,
+  RX_EINVAL = 1,        /* bad argument or parameter combination            */
+  RX_ENOMEM = 2,        /* device allocation failed                          */
+  RX_ECUDA = 3,         /* a CUDA runtime call failed                        */
+  RX_ESTATE = 4,        /* call not valid in the current stream state        */
+  RX_ETIMEOUT = 5,      /* a bounded device-side wait gave up                */
+  RX_EUNSUPPORTED = 6   /* parameter value outside what the kernels support  */
+} rx_status;
+
+/* Input sample formats (one sample-time = Xi, Xq, Yi, Yq). */
+enum {
+  RX_I8x4 = 1,   /* int8 codes, 4 bytes per sample-time, 4-byte aligned      */
+  RX_F32x4 = 2   /* float32, 16 bytes per sample-time, 16-byte aligned       */
+};
+
+/* Keys for rx_set_param / rx_get_param.  Set before the first rx_process
+ * (or after rx_reset); later changes return RX_ESTATE. */
+enum {
+  RX_P_MOD = 1,            /* bits per symbol: 2 = QPSK (default), 4 = 16QAM         */
+  RX_P_FFT_N = 2,          /* CDC FFT size, power of two 256..8192 (0 = default:
+                              max(1024, next pow2 >= 4 V))                          */
+  RX_P_OVERLAP = 3,        /* CDC overlap V, multiple of 32 (0 = default: N_CD - 1
+                              rounded up to a multiple of 32)                        */
+  RX_P_ROLLOFF = 4,        /* RRC roll-off (default 0.1)                             */
+  RX_P_LAMBDA_NM = 5,      /* carrier wavelength in nm (default 1550)                */
+  RX_P_MU_CMA = 6,         /* CMA step (default 1e-3)                                */
+  RX_P_MU_DD = 7,          /* DD-LMS step (default 1e-3)                             */
+  RX_P_N_CMA = 8,          /* symbols adapted by CMA (default 8192)                  */
+  RX_P_UPDATE_BLOCK = 9,   /* symbols per tap update B_u, 1..32 (default 32)         */
+  RX_P_SEG_LEN = 10,       /* segment length S in symbols (default 1024)             */
+  RX_P_SEG_PRETRAIN = 11,  /* pre-training symbols W per segment (default 128)       */
+  RX_P_BPS_HALFWIN = 12,   /* BPS half window N_b (default 16, at most 64)           */
+  RX_P_BLOCK_SAMPLES = 13, /* samples per processing block; a wave holds
+                              BLOCK/2/S segments (default 65536)                     */
+  RX_P_IN_SCALE = 14,      /* ingest scale applied to every input scalar (default 1) */
+  RX_P_ACQ_MIN = 15,       /* minimum acquisition length (default 16384)             */
+  RX_P_FO_SMOOTH = 16,     /* frequency tracking divisor (default 16)                */
+  RX_P_FO_TRACK = 17,      /* 1 = estimate and remove the frequency offset (default) */
+  RX_P_LLR_OUT = 18,       /* 1 = write LLRs to rx_out.llr                          */
+  RX_P_SYM_OUT = 19,       /* 1 = write phase-recovered symbols to rx_out.sym        */
+  RX_P_EQ_OUT = 20,        /* 1 = write equaliser outputs to rx_out.eq               */
+  RX_P_CDC_OUT = 21        /* 1 = write CDC outputs to rx_out.cdc (tests)            */
+};
+
+/* One call's input: n sample-times (n even) at a device address. */
+typedef struct {
+  const void *data;   /* device pointer, layout [n][Xi, Xq, Yi, Yq]              */
+  int64_t n;          /* sample-times in this call; 0 = flush (end of stream)     */
+  int32_t dtype;      /* RX_I8x4 or RX_F32x4                                      */
+  int32_t reserved;
+} rx_in;
+
+/* One call's output.  rx_process fills n and first; all arrays are indexed by
+ * the call-relative symbol j = k - first (k = stream symbol index) and laid
+ * out [pol][...] with the given pol strides.  Hard bits: bit t of symbol j of
+ * pol p is bit (j*m + t) % 32 of word bits[p*bits_stride + (j*m + t)/32]
+ * (LSB first; QPSK bits I,Q; 16QAM bits I-sign, I-outer, Q-sign, Q-outer). */
+typedef struct {
+  uint32_t *bits;  int64_t bits_stride;   /* words per pol (required)              */
+  float *llr;      int64_t llr_stride;    /* floats per pol, j*m + t (LLR_OUT)      */
+  float *sym;      int64_t sym_stride;    /* complex (2 floats) per pol (SYM_OUT)   */
+  float *eq;       int64_t eq_stride;     /* complex per pol, equaliser out (EQ_OUT)*/
+  float *cdc;      int64_t cdc_stride;    /* complex per pol, per SAMPLE (CDC_OUT);
+                                             must hold in->n + FFT_N samples per pol */
+  int64_t capacity;                       /* symbols per pol the arrays can hold    */
+  int64_t n;                              /* out: symbols written per pol           */
+  int64_t first;                          /* out: stream index of symbol j = 0      */
+  int64_t cdc_first, cdc_n;               /* out: CDC samples written (CDC_OUT)     */
+} rx_out;
+
+/* Create a receiver for one dual-polarisation stream.
+ * baud: symbol rate [Bd] (> 0); sps: samples per symbol (must be 2);
+ * L_km: dispersion length to compensate [km] (>= 0); D_ps_nm_km: fibre
+ * dispersion [ps/(nm km)]; ntaps: butterfly taps T (odd, 3..15);
+ * bps_angles: BPS test angles B (must be 32).
+ * The dispersion inverse follows from the paper's static frequency-domain
+ * equaliser (processing-chain paragraph, arXiv 2104.06311); N_CD and V follow
+ * the textbook bound 2 floor(|D| lam^2 L / (2 c T^2)) + 1.
+ * Returns RX_EINVAL / RX_EUNSUPPORTED on bad arguments; *out is NULL then. */
+rx_status rx_create(rx_stream **out, double baud, int sps, double L_km,
+                    double D_ps_nm_km, int ntaps, int bps_angles);
+
+/* Set / read a parameter (keys above).  RX_ESTATE after the first process. */
+rx_status rx_set_param(rx_stream *rx, int key, double value);
+rx_status rx_get_param(rx_stream *rx, int key, double *value);
+
+/* Bind a CUDA stream (a cudaStream_t, e.g. torch.cuda.Stream.cuda_stream). */
+rx_status rx_set_cuda_stream(rx_stream *rx, void *cuda_stream);
+
+/* Allocate all device state for calls of up to max_call_samples sample-times.
+ * Optional: the first rx_process reserves for its own size.  Calls larger
+ * than the reservation return RX_EINVAL. */
+rx_status rx_reserve(rx_stream *rx, int64_t max_call_samples);
+
+/* Process one buffer of the stream (in->n even, > 0) or flush (in->n == 0).
+ * Enqueues the chain on the bound stream and returns; out->n symbols per pol
+ * (stream indices out->first ..) are complete once the stream reaches this
+ * point.  The chain has a fixed latency: symbols are emitted per whole
+ * acquisition / wave region once the BPS window past its end is available;
+ * the flush emits the rest.  out->capacity must be at least
+ * (in->n / 2 + 2 * BLOCK_SAMPLES) symbols. */
+rx_status rx_process(rx_stream *rx, const rx_in *in, rx_out *out);
+
+/* Bit errors of received hard bits against reference bits (both device
+ * arrays in the rx_out bit layout, n_symbols per pol, pol strides in words).
+ * Symbols [0, A + 4096) are skipped (A = acquisition length); on
+ * [A + 4096, A + 8192) each received pol p picks the reference pol q,
+ * rotation r (j^r) and delay d in [-64, 64] with the fewest errors; errors
+ * are then counted on [A + 8192, n_symbols).  sync (optional, 6 ints) gets
+ * (q, r, d) for p = 0, 1.  Synchronises the bound stream.  The paper derives
+ * Q-factors from BER counts (Section "Results and Discussion"). */
+rx_status rx_ber(rx_stream *rx, const uint32_t *rx_bits, int64_t rx_stride,
+                 const uint32_t *ref_bits, int64_t ref_stride, int64_t n_symbols,
+                 uint64_t *errors, uint64_t *bits_counted, int32_t *sync);
+
+/* Equaliser trace of wave w (w = -1: end of acquisition): the taps the wave
+ * started from, h[p][q][i] as interleaved complex floats (2*2*ntaps*2),
+ * the per-symbol frequency offset dw and the phase base Phi.  Synchronises. */
+rx_status rx_trace(rx_stream *rx, int64_t wave, float *taps, double *dw, double *Phi);
+
+/* Serialise / restore the streaming state (taps, tracking state, carried
+ * samples and symbols, counters) as an opaque host blob.  rx_get_state with
+ * blob == NULL returns the needed size in *len.  Synchronises. */
+rx_status rx_get_state(rx_stream *rx, void *blob, size_t *len);
+rx_status rx_set_state(rx_stream *rx, const void *blob, size_t len);
+
+/* Forget the stream (keeps parameters and allocations). */
+rx_status rx_reset(rx_stream *rx);
+/* Wait for all work enqueued by this handle. */
+rx_status rx_sync(rx_stream *rx);
+void rx_destroy(rx_stream *rx);
+
+const char *rx_status_str(rx_status s);
+/* Text of the last error on this handle (empty if none). */
+const char *rx_last_error(rx_stream *rx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RX_H_ */

@@ -159,41 +159,50 @@ def apply_jones(x: np.ndarray, J: np.ndarray) -> np.ndarray:
 
 def apply_pmd(x: np.ndarray, fs: float, mean_dgd_s: float, rng: np.random.Generator,
               n_sections: int = 100, block: int = 1 << 16, drift_rad: float = 1e-3,
-              margin: int = 512) -> np.ndarray:
+              margin: int = 512, n_coarse: int = 257) -> np.ndarray:
     """Random-waveplate PMD whose plate angles random-walk from block to block.
 
     Each section is a random SU(2) rotation followed by a differential group
     delay tau_s; tau_s is set so that the concatenation has the requested mean
-    DGD (Maxwellian mean = sqrt(8/(3 pi)) * rms).  Each block of `block`
-    samples is filtered in the frequency domain with its own concatenated
-    Jones matrix, using `margin` samples of context on either side.
+    DGD (Maxwellian mean = sqrt(8/(3 pi)) * rms).  The concatenated Jones
+    matrix is smooth in frequency (its scale is 1/DGD, far wider than the
+    signal band), so it is built on `n_coarse` frequencies spanning the band
+    and interpolated linearly onto each block's DFT grid.  Each block of
+    `block` samples is filtered in the frequency domain with its own matrix,
+    using `margin` samples of context on either side.
     """
     n = x.shape[-1]
     tau = mean_dgd_s / (math.sqrt(n_sections) * math.sqrt(8.0 / (3.0 * math.pi)))
     ang = rng.uniform(0, 2 * np.pi, size=(n_sections, 3))
     out = np.empty_like(x)
     nblk = (n + block - 1) // block
-    L = block + 2 * margin
-    w = 2.0 * np.pi * grid_freqs(L, fs)
+    Lb = block + 2 * margin
+    f_fine = grid_freqs(Lb, fs)
+    f_c = np.linspace(-fs / 2, fs / 2, n_coarse)
+    w_c = 2.0 * np.pi * f_c
+    d = np.stack([np.exp(1j * w_c * tau / 2), np.exp(-1j * w_c * tau / 2)], axis=-1)   # (n_coarse, 2)
     for b in range(nblk):
         if b:
             ang = ang + rng.normal(0.0, drift_rad, size=ang.shape)
-        # frequency-dependent Jones matrix of the concatenation, per bin
-        M = np.zeros((L, 2, 2), np.complex128)
+        M = np.zeros((n_coarse, 2, 2), np.complex128)
         M[:, 0, 0] = 1.0
         M[:, 1, 1] = 1.0
+        ca, sa = np.cos(ang[:, 0]), np.sin(ang[:, 0])
+        eb, ec = np.exp(1j * ang[:, 1]), np.exp(1j * ang[:, 2])
         for s in range(n_sections):
-            a, bb, c = ang[s]
-            U = np.array([[np.cos(a) * np.exp(1j * bb), -np.sin(a) * np.exp(-1j * c)],
-                          [np.sin(a) * np.exp(1j * c), np.cos(a) * np.exp(-1j * bb)]])
-            d = np.stack([np.exp(1j * w * tau / 2), np.exp(-1j * w * tau / 2)], axis=-1)
-            M = d[:, :, None] * np.einsum("pq,fqr->fpr", U, M)
+            U = np.array([[ca[s] * eb[s], -sa[s] / ec[s]], [sa[s] * ec[s], ca[s] / eb[s]]])
+            M = d[:, :, None] * (U[None] @ M)
+        Mf = np.empty((Lb, 2, 2), np.complex128)
+        for i in range(2):
+            for j in range(2):
+                Mf[:, i, j] = (np.interp(f_fine, f_c, M[:, i, j].real)
+                               + 1j * np.interp(f_fine, f_c, M[:, i, j].imag))
         lo = b * block - margin
-        seg = np.zeros((2, L), np.complex128)
-        a0, a1 = max(lo, 0), min(lo + L, n)
+        seg = np.zeros((2, Lb), np.complex128)
+        a0, a1 = max(lo, 0), min(lo + Lb, n)
         seg[:, a0 - lo:a1 - lo] = x[:, a0:a1]
         S = _fft(seg)
-        Y = np.einsum("fpq,qf->pf", M, S)
+        Y = np.einsum("fpq,qf->pf", Mf, S)
         y = _ifft(Y)
         e = min((b + 1) * block, n)
         out[:, b * block:e] = y[:, margin:margin + e - b * block]

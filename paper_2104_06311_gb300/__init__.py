@@ -1,0 +1,7 @@
+"""GB300 (sm_103a) dual-polarisation coherent-receiver DSP chain.
+
+The CUDA kernels live in ``csrc/`` and build into ``librx.so``
+(``python -m paper_2104_06311_gb300.build``); ``rx`` is the ctypes binding of
+the C ABI declared in ``include/rx.h``.
+"""
+from .rx import Receiver, load, RxError  # noqa: F401

@@ -1,0 +1,105 @@
+// Bit-error counting with rotation / polarisation / delay synchronisation.
+//
+// The paper estimates Q-factors "from BER in bins" (arXiv 2104.06311, Section
+// "Results and Discussion").  Received and reference bits use the packed
+// output layout (bit t of symbol k of a pol at bit k*m + t, LSB first).  A
+// reference symbol rotated by j maps its Gray bits as
+//   QPSK  (b0, b1)         -> (!b1, b0)
+//   16QAM (b0, b1, b2, b3) -> (!b2, b3, b0, b1)
+// (I' = -Q, Q' = I with b0/b2 the sign bits and b1/b3 the outer-level bits).
+#include "common.cuh"
+#include "rx_internal.h"
+
+namespace rx {
+
+namespace {
+__device__ __forceinline__ unsigned sym_bits(const uint32_t *row, int64_t k, int m) {
+  const int64_t bit = k * m;
+  return (row[bit >> 5] >> (bit & 31)) & ((1u << m) - 1u);
+}
+
+__device__ __forceinline__ unsigned rotate_bits(unsigned v, int r, int m) {
+  for (int i = 0; i < r; ++i) {
+    if (m == 2) {
+      const unsigned b0 = v & 1u, b1 = (v >> 1) & 1u;
+      v = (b1 ^ 1u) | (b0 << 1);
+    } else {
+      const unsigned b0 = v & 1u, b1 = (v >> 1) & 1u, b2 = (v >> 2) & 1u, b3 = (v >> 3) & 1u;
+      v = (b2 ^ 1u) | (b3 << 1) | (b0 << 2) | (b1 << 3);
+    }
+  }
+  return v;
+}
+}  // namespace
+
+// grid: 2 (rx pol) x 2 (ref pol) x 4 (rotation) x 129 (delay)
+__global__ void ber_sync_kernel(const uint32_t *rx, int64_t rxs, const uint32_t *ref, int64_t refs,
+                                int64_t K, int m, int64_t s0, int64_t s1, unsigned *counts) {
+  const int c = blockIdx.x;
+  const int d = c % 129 - 64;
+  const int r = (c / 129) % 4;
+  const int q = (c / (129 * 4)) % 2;
+  const int p = c / (129 * 4 * 2);
+  unsigned e = 0;
+  for (int64_t k = s0 + threadIdx.x; k < s1; k += blockDim.x) {
+    const int64_t kk = k + d;
+    if (kk < 0 || kk >= K) continue;
+    const unsigned a = sym_bits(rx + p * rxs, k, m);
+    const unsigned b = rotate_bits(sym_bits(ref + q * refs, kk, m), r, m);
+    e += __popc(a ^ b);
+  }
+  for (int o = 16; o > 0; o >>= 1) e += __shfl_down_sync(0xffffffffu, e, o);
+  __shared__ unsigned ws[32];
+  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = e;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned t = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += ws[w];
+    counts[c] = t;
+  }
+}
+
+// acc[0] = errors, acc[1] = bits counted; sync = (q, r, d) per rx pol
+__global__ void ber_count_kernel(const uint32_t *rx, int64_t rxs, const uint32_t *ref, int64_t refs,
+                                 int64_t K, int m, int64_t k0, const int *sync,
+                                 unsigned long long *acc) {
+  const int p = blockIdx.y;
+  const int q = sync[3 * p], r = sync[3 * p + 1], d = sync[3 * p + 2];
+  unsigned long long e = 0, n = 0;
+  for (int64_t k = k0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < K;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t kk = k + d;
+    if (kk < 0 || kk >= K) continue;
+    const unsigned a = sym_bits(rx + p * rxs, k, m);
+    const unsigned b = rotate_bits(sym_bits(ref + q * refs, kk, m), r, m);
+    e += __popc(a ^ b);
+    n += m;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    e += __shfl_down_sync(0xffffffffu, e, o);
+    n += __shfl_down_sync(0xffffffffu, n, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicAdd(&acc[0], e);
+    atomicAdd(&acc[1], n);
+  }
+}
+
+cudaError_t launch_ber_sync(const uint32_t *rx, int64_t rxs, const uint32_t *ref, int64_t refs,
+                            int64_t K, int m, int64_t s0, int64_t s1, unsigned *counts,
+                            cudaStream_t s) {
+  ber_sync_kernel<<<2 * 2 * 4 * 129, 256, 0, s>>>(rx, rxs, ref, refs, K, m, s0, s1, counts);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ber_count(const uint32_t *rx, int64_t rxs, const uint32_t *ref, int64_t refs,
+                             int64_t K, int m, int64_t k0, const int *sync,
+                             unsigned long long *acc, cudaStream_t s) {
+  const int64_t n = K - k0;
+  if (n <= 0) return cudaSuccess;
+  unsigned blocks = (unsigned)min((int64_t)1216, (n + 255) / 256);
+  ber_count_kernel<<<dim3(blocks, 2), 256, 0, s>>>(rx, rxs, ref, refs, K, m, k0, sync, acc);
+  return cudaGetLastError();
+}
+
+}  // namespace rx

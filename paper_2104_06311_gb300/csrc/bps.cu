@@ -1,0 +1,251 @@
+// Blind phase search with integer unwrap, hard decisions, LLRs and bit packing.
+//
+// The paper demaps the equaliser's decisions and sends them to host RAM
+// (arXiv 2104.06311, Section "Experimental setup", processing-chain
+// paragraph); its self-coherent KK receiver needs no carrier recovery.  The
+// intradyne chain here recovers the carrier phase by blind phase search
+// (Pfau, Hoffmann, Noe, JLT 2009):
+//   d_{k,b} = |y_k e^{-j phi_b} - dec(.)|^2, phi_b = (b/32 - 1/2) pi/2,
+//   D_{k,b} = sum_{m=-Nb..Nb} d_{k+m,b} (absent terms at the stream ends omitted),
+//   bhat_k  = argmin_b D_{k,b} (smallest b on ties),
+//   r_k = +1 / -1 / 0 when bhat_{k-1} - bhat_k > B/2 / < -B/2 / otherwise,
+//   m_k = m_{k-1} + r_k,  z_k = y_k e^{-j phi_bhat} (-j)^{m_k}.
+// Pass 1: one warp per chunk of symbols, lane = test angle; a sliding window
+//   of d values per lane in shared memory (exact re-sum every 32 symbols);
+//   argmin by a warp min-reduction on the float bits plus a ballot; writes
+//   bhat (int8), the chunk's sum of r and sum of |z - dec z|^2 = d_{k,bhat}.
+// Scan: exclusive prefix of the chunk sums per pol (+ the carried count) and
+//   the per-region noise variance sigma^2 = mean |z - dec z|^2.
+// Demap: lane = symbol; warp scan of r, derotation, hard bits packed with
+//   warp OR-reductions, optional max-log LLRs and symbols.
+#include "common.cuh"
+#include "rx_internal.h"
+
+namespace rx {
+
+namespace {
+constexpr int kBpsWarps = 4;
+
+__device__ __forceinline__ int unwrap_step(int prev, int cur) {
+  const int d = prev - cur;
+  return d > kAngles / 2 ? 1 : (d < -kAngles / 2 ? -1 : 0);
+}
+
+__device__ __forceinline__ int64_t chunk_lo(const BpsLaunch &L, int64_t j) { return L.k_lo + j * L.chunk; }
+}  // namespace
+
+template <int MB>
+__global__ void __launch_bounds__(kBpsWarps * 32) bps_pass1(BpsLaunch L) {
+  extern __shared__ float ring_all[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t j = (int64_t)blockIdx.x * kBpsWarps + warp;
+  const int p = blockIdx.y;
+  if (j >= L.n_chunks) return;
+  const int M = 2 * L.Nb + 1;
+  float *ring = ring_all + (size_t)warp * M * 32;
+  const int64_t a = chunk_lo(L, j), b = min(a + (int64_t)L.chunk, L.k_hi);
+  float sb, cb;
+  sincospif(((float)lane / 32.f - 0.5f) * 0.5f, &sb, &cb);
+  const float2 rot = make_float2(cb, -sb);
+  const float2 *y = L.y + (int64_t)p * L.y_stride - L.y_base;
+  auto dist = [&](int64_t k) -> float {
+    if (k < 0 || k >= L.K_end) return 0.f;
+    return qam_dist<MB>(cmul(y[k], rot));
+  };
+  auto slot = [&](int64_t k) -> int { return (int)((k + M) % M); };
+  const int64_t start = a > 0 ? a - 1 : a;
+  float D = 0.f;
+  for (int64_t k = start - L.Nb; k <= start + L.Nb; ++k) {
+    const float d = dist(k);
+    ring[slot(k) * 32 + lane] = d;
+  }
+  int prev = 0, R = 0;
+  float s2 = 0.f;
+  int8_t *bh = L.bhat + (int64_t)p * L.bh_stride - L.bh_base;
+  for (int64_t k = start; k < b; ++k) {
+    if (k > start) {
+      const float dn = dist(k + L.Nb);
+      const int so = slot(k - L.Nb - 1);  // leaving value occupies the entering slot
+      D += dn - ring[so * 32 + lane];
+      ring[so * 32 + lane] = dn;
+    }
+    if (((k - start) & 31) == 0) {  // exact re-sum bounds the sliding drift
+      float t = 0.f;
+      for (int m = -L.Nb; m <= L.Nb; ++m) t += ring[slot(k + m) * 32 + lane];
+      D = t;
+    }
+    const unsigned key = __float_as_uint(fmaxf(D, 0.f));
+    const unsigned mn = __reduce_min_sync(0xffffffffu, key);
+    const int bs = __ffs(__ballot_sync(0xffffffffu, key == mn)) - 1;
+    if (k >= a) {
+      if (k > 0) R += unwrap_step(prev, bs);
+      const float dk = __shfl_sync(0xffffffffu, ring[slot(k) * 32 + lane], bs);
+      s2 += dk;
+      if (lane == 0) bh[k] = (int8_t)bs;
+    }
+    prev = bs;
+  }
+  if (lane == 0) {
+    L.chunk_r[(int64_t)p * L.n_chunks + j] = R;
+    L.chunk_s2[(int64_t)p * L.n_chunks + j] = s2;
+  }
+}
+
+// One CTA per pol: exclusive prefix of chunk unwrap sums (+carry) and region sigma^2.
+__global__ void __launch_bounds__(1024) bps_scan(BpsLaunch L) {
+  __shared__ int64_t part[1024];
+  const int p = blockIdx.x, t = threadIdx.x;
+  const int64_t n = L.n_chunks;
+  const int64_t per = (n + 1023) / 1024;
+  const int64_t c0 = min((int64_t)t * per, n), c1 = min(c0 + per, n);
+  int64_t s = 0;
+  for (int64_t c = c0; c < c1; ++c) s += L.chunk_r[(int64_t)p * n + c];
+  part[t] = s;
+  __syncthreads();
+  // Hillis-Steele inclusive scan over 1024 partials
+  for (int o = 1; o < 1024; o <<= 1) {
+    int64_t v = t >= o ? part[t - o] : 0;
+    __syncthreads();
+    part[t] += v;
+    __syncthreads();
+  }
+  int64_t run = L.m_carry[p] + (t > 0 ? part[t - 1] : 0);
+  for (int64_t c = c0; c < c1; ++c) {
+    L.chunk_m[(int64_t)p * n + c] = run;
+    run += L.chunk_r[(int64_t)p * n + c];
+  }
+  __syncthreads();
+  if (t == 1023) L.m_carry[p] += part[1023];
+  // regions: [0, A), then [A + r span, ...), clipped to [k_lo, k_hi)
+  const int64_t r_lo = L.k_lo < L.A ? 0 : 1 + (L.k_lo - L.A) / L.span;
+  const int64_t r_hi = L.k_hi <= L.A ? 1 : 1 + (L.k_hi - 1 - L.A) / L.span + 1;
+  for (int64_t r = r_lo + t; r < r_hi; r += 1024) {
+    const int64_t s_r = r == 0 ? 0 : L.A + (r - 1) * L.span;
+    const int64_t e_r = min(r == 0 ? L.A : s_r + L.span, L.k_hi);
+    double acc = 0.0;
+    for (int64_t c = (s_r - L.k_lo) / L.chunk; c < n && chunk_lo(L, c) < e_r; ++c)
+      acc += (double)L.chunk_s2[(int64_t)p * n + c];
+    L.region_s2[(int64_t)p * (r_hi - r_lo) + (r - r_lo)] = acc / (double)(e_r - s_r);
+  }
+}
+
+template <int MB>
+__device__ __forceinline__ void llr_bits(float2 z, float s2inv, float *out) {
+  if (MB == 2) {
+    const float g = 2.82842712474619010f * s2inv;  // 2 sqrt2 / sigma^2
+    out[0] = g * z.x;
+    out[1] = g * z.y;
+  } else {
+    const float lv[4] = {-0.94868329805051381f, -0.31622776601683793f, 0.31622776601683793f,
+                         0.94868329805051381f};
+    // level bits: first [l < 0] -> 1,1,0,0 ; second [|l| outer] -> 1,0,0,1
+#pragma unroll
+    for (int dim = 0; dim < 2; ++dim) {
+      const float x = dim ? z.y : z.x;
+      float d[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) d[i] = (x - lv[i]) * (x - lv[i]);
+      const float f1 = fminf(d[0], d[1]), f0 = fminf(d[2], d[3]);
+      const float o1 = fminf(d[0], d[3]), o0 = fminf(d[1], d[2]);
+      out[2 * dim] = (f1 - f0) * s2inv;
+      out[2 * dim + 1] = (o1 - o0) * s2inv;
+    }
+  }
+}
+
+template <int MB>
+__global__ void __launch_bounds__(kBpsWarps * 32) bps_demap(BpsLaunch L) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t j = (int64_t)blockIdx.x * kBpsWarps + warp;
+  const int p = blockIdx.y;
+  if (j >= L.n_chunks) return;
+  const int64_t a = chunk_lo(L, j), b = min(a + (int64_t)L.chunk, L.k_hi);
+  float sb, cb;
+  sincospif(((float)lane / 32.f - 0.5f) * 0.5f, &sb, &cb);
+  const float2 rot = make_float2(cb, -sb);
+  const float2 *y = L.y + (int64_t)p * L.y_stride - L.y_base;
+  const int8_t *bh = L.bhat + (int64_t)p * L.bh_stride - L.bh_base;
+  int64_t m = L.chunk_m[(int64_t)p * L.n_chunks + j];
+  const int64_t r_lo = L.k_lo < L.A ? 0 : 1 + (L.k_lo - L.A) / L.span;
+  const int64_t r_hi = L.k_hi <= L.A ? 1 : 1 + (L.k_hi - 1 - L.A) / L.span + 1;
+  const int64_t region = a < L.A ? 0 : 1 + (a - L.A) / L.span;
+  const float s2inv = (float)(1.0 / L.region_s2[(int64_t)p * (r_hi - r_lo) + (region - r_lo)]);
+  for (int64_t base = a; base < b; base += 32) {
+    const int64_t k = base + lane;
+    const bool valid = k < b;
+    const int cur = valid ? (int)bh[k] : 0;
+    int r = 0;
+    if (valid && k > 0) r = unwrap_step((int)bh[k - 1], cur);
+    // inclusive warp scan of r
+    int sc = r;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int v = __shfl_up_sync(0xffffffffu, sc, o);
+      if (lane >= o) sc += v;
+    }
+    const int64_t mk = m + sc;
+    m += __shfl_sync(0xffffffffu, sc, 31);
+    const float rc = __shfl_sync(0xffffffffu, rot.x, cur);
+    const float rs = __shfl_sync(0xffffffffu, rot.y, cur);
+    float2 z = make_float2(0.f, 0.f);
+    unsigned v = 0;
+    const int64_t jo = k - L.out_first;
+    if (valid) {
+      z = cmul(y[k], make_float2(rc, rs));
+      switch ((int)(((mk % 4) + 4) % 4)) {  // (-j)^m
+        case 1: z = make_float2(z.y, -z.x); break;
+        case 2: z = make_float2(-z.x, -z.y); break;
+        case 3: z = make_float2(-z.y, z.x); break;
+        default: break;
+      }
+      v = qam_bits<MB>(z);
+      if (L.sym) reinterpret_cast<float2 *>(L.sym)[(int64_t)p * L.sym_stride + jo] = z;
+      if (L.llr) {
+        float o[MB];
+        llr_bits<MB>(z, s2inv, o);
+#pragma unroll
+        for (int t = 0; t < MB; ++t) L.llr[(int64_t)p * L.llr_stride + jo * MB + t] = o[t];
+      }
+    }
+    // pack: 32 / MB symbols per word
+    constexpr int SPW = 32 / MB;
+    const int64_t w0 = (base - L.out_first) * MB / 32;
+    const int nvalid = (int)min((int64_t)32, b - base);
+#pragma unroll
+    for (int w = 0; w < MB; ++w) {
+      const int g = lane / SPW;
+      const unsigned contrib = (g == w) ? (v << (MB * (lane - w * SPW))) : 0u;
+      const unsigned word = __reduce_or_sync(0xffffffffu, contrib);
+      if (lane == 0 && w * SPW < nvalid) L.bits[(int64_t)p * L.bits_stride + w0 + w] = word;
+    }
+  }
+}
+
+cudaError_t launch_bps(const BpsLaunch &L, cudaStream_t s) {
+  if (L.n_chunks <= 0) return cudaSuccess;
+  dim3 grid((unsigned)((L.n_chunks + kBpsWarps - 1) / kBpsWarps), 2);
+  const size_t sm = (size_t)kBpsWarps * (2 * L.Nb + 1) * 32 * sizeof(float);
+  cudaError_t e;
+  if (L.mod_bits == 4) {
+    e = cudaFuncSetAttribute(bps_pass1<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    bps_pass1<4><<<grid, kBpsWarps * 32, sm, s>>>(L);
+  } else {
+    e = cudaFuncSetAttribute(bps_pass1<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    bps_pass1<2><<<grid, kBpsWarps * 32, sm, s>>>(L);
+  }
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  bps_scan<<<2, 1024, 0, s>>>(L);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  if (L.mod_bits == 4) {
+    bps_demap<4><<<grid, kBpsWarps * 32, 0, s>>>(L);
+  } else {
+    bps_demap<2><<<grid, kBpsWarps * 32, 0, s>>>(L);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace rx

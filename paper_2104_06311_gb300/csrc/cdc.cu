@@ -1,0 +1,291 @@
+// Overlap-save chromatic-dispersion compensation with the RRC matched filter.
+//
+// Analogue of the paper's static frequency-domain equalisation "by
+// multiplication with an offline-optimized filter enabled by another FFT and
+// IFFT pair" (arXiv 2104.06311, Section "Experimental setup", processing-chain
+// paragraph), with the closed-form filter
+//   H_k = exp(-j beta2 L w_k^2 / 2) * sqrt(2) * H_rrc(f_k),  beta2 = -D lam^2/(2 pi c).
+// One CTA filters one overlap-save window of N samples for both polarisations:
+// ingest (int8/f32 -> f32, times the ingest scale) -> radix-16 Stockham FFT in
+// shared memory -> multiply by H/N -> inverse FFT (conjugation trick) -> the
+// central S = N - V outputs go to HBM.  Window i reads input samples
+// [iS - V/2, iS - V/2 + N) (zero outside the stream) and writes outputs
+// [iS, iS + S).
+#include <math.h>
+
+#include "common.cuh"
+#include "rx_internal.h"
+
+namespace rx {
+
+// ---------------------------------------------------------------- tables (FP64)
+__global__ void tables_kernel(float2 *H, float2 *tw, int N, double baud, double L_km, double D,
+                              double lam_nm, double rolloff) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= N) return;
+  double s, c;
+  sincospi(-2.0 * (double)k / (double)N, &s, &c);
+  tw[k] = make_float2((float)c, (float)s);
+  const double pi = 3.14159265358979323846;
+  const double fs = 2.0 * baud;
+  const double f = (double)(k < N / 2 ? k : k - N) * (fs / (double)N);
+  const double w = 2.0 * pi * f;
+  const double Dsm = D * 1e-12 / (1e-9 * 1e3);
+  const double lam = lam_nm * 1e-9;
+  const double beta2 = -Dsm * lam * lam / (2.0 * pi * 299792458.0);
+  const double ph = -beta2 * (L_km * 1e3) * w * w / 2.0;
+  const double af = fabs(f);
+  const double f1 = (1.0 - rolloff) * baud / 2.0, f2 = (1.0 + rolloff) * baud / 2.0;
+  double a = 0.0;
+  if (af <= f1) a = 1.0;
+  else if (af <= f2) a = cos(pi * (af - f1) / (2.0 * rolloff * baud));
+  a *= sqrt(2.0) / (double)N;  // matched-filter gain sqrt(sps); 1/N of the inverse DFT
+  double ps, pc;
+  sincos(ph, &ps, &pc);
+  H[k] = make_float2((float)(a * pc), (float)(a * ps));
+}
+
+cudaError_t launch_tables(float2 *H, float2 *tw, int N, double baud, double L_km, double D,
+                          double lam_nm, double rolloff, cudaStream_t s) {
+  tables_kernel<<<(N + 255) / 256, 256, 0, s>>>(H, tw, N, baud, L_km, D, lam_nm, rolloff);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- small DFTs (forward)
+__device__ __forceinline__ void dft2(float2 &a, float2 &b) {
+  float2 t = a;
+  a = cadd(t, b);
+  b = csub(t, b);
+}
+
+__device__ __forceinline__ void dft4(float2 &x0, float2 &x1, float2 &x2, float2 &x3) {
+  float2 t0 = cadd(x0, x2), t1 = csub(x0, x2);
+  float2 t2 = cadd(x1, x3), t3 = cmul_mi(csub(x1, x3));
+  x0 = cadd(t0, t2);
+  x2 = csub(t0, t2);
+  x1 = cadd(t1, t3);
+  x3 = csub(t1, t3);
+}
+
+// W_16^e = exp(-2 pi i e / 16)
+__device__ __forceinline__ float2 w16(int e) {
+  const float c1 = 0.92387953251128674f, s1 = 0.38268343236508978f, h = 0.70710678118654752f;
+  switch (e & 15) {
+    case 0: return make_float2(1.f, 0.f);
+    case 1: return make_float2(c1, -s1);
+    case 2: return make_float2(h, -h);
+    case 3: return make_float2(s1, -c1);
+    case 4: return make_float2(0.f, -1.f);
+    case 5: return make_float2(-s1, -c1);
+    case 6: return make_float2(-h, -h);
+    case 7: return make_float2(-c1, -s1);
+    case 8: return make_float2(-1.f, 0.f);
+    default: return make_float2(-c1, s1);  // e = 9 (largest used: 3*3)
+  }
+}
+
+// In-register DFT of R points, v[0..R-1] in natural order, result in natural order.
+// Sizes 8 and 16 split as N1 x 4 (n = n1 + N1 n2, k = 4 k1 + k2).
+template <int R>
+__device__ __forceinline__ void dft(float2 *v) {
+  if (R == 2) {
+    dft2(v[0], v[1]);
+  } else if (R == 4) {
+    dft4(v[0], v[1], v[2], v[3]);
+  } else if (R == 8) {
+    float2 Y[2][4];
+#pragma unroll
+    for (int n1 = 0; n1 < 2; ++n1) {
+      Y[n1][0] = v[n1]; Y[n1][1] = v[n1 + 2]; Y[n1][2] = v[n1 + 4]; Y[n1][3] = v[n1 + 6];
+      dft4(Y[n1][0], Y[n1][1], Y[n1][2], Y[n1][3]);
+    }
+#pragma unroll
+    for (int k2 = 1; k2 < 4; ++k2) Y[1][k2] = cmul(Y[1][k2], w16(2 * k2));  // W_8^{k2}
+#pragma unroll
+    for (int k2 = 0; k2 < 4; ++k2) {
+      float2 a = Y[0][k2], b = Y[1][k2];
+      dft2(a, b);
+      v[k2] = a;
+      v[4 + k2] = b;
+    }
+  } else {  // 16
+    float2 Y[4][4];
+#pragma unroll
+    for (int n1 = 0; n1 < 4; ++n1) {
+      Y[n1][0] = v[n1]; Y[n1][1] = v[n1 + 4]; Y[n1][2] = v[n1 + 8]; Y[n1][3] = v[n1 + 12];
+      dft4(Y[n1][0], Y[n1][1], Y[n1][2], Y[n1][3]);
+    }
+#pragma unroll
+    for (int n1 = 1; n1 < 4; ++n1)
+#pragma unroll
+      for (int k2 = 1; k2 < 4; ++k2) Y[n1][k2] = cmul(Y[n1][k2], w16(n1 * k2));
+#pragma unroll
+    for (int k2 = 0; k2 < 4; ++k2) {
+      dft4(Y[0][k2], Y[1][k2], Y[2][k2], Y[3][k2]);
+      v[k2] = Y[0][k2]; v[4 + k2] = Y[1][k2]; v[8 + k2] = Y[2][k2]; v[12 + k2] = Y[3][k2];
+    }
+  }
+}
+
+// shared-memory index with one float2 of padding per 32 (breaks power-of-two strides)
+__device__ __forceinline__ int pad(int i) { return i + (i >> 5); }
+
+// One radix-R Stockham pass (Govindaraju et al., SC'08 formulation): butterfly
+// j reads elements j + r N/R, applies W_{Ns R}^{r (j mod Ns)}, does an R-point
+// DFT and writes element r to (j / Ns) Ns R + (j mod Ns) + r Ns.
+template <int N, int R, int Ns>
+__device__ __forceinline__ void fft_pass(float2 *buf, int t, const float2 *__restrict__ tw) {
+  constexpr int NB = N / R, PER = 16 / R, TW = N / (Ns * R);
+  float2 v[PER][R];
+#pragma unroll
+  for (int q = 0; q < PER; ++q) {
+    const int j = t + q * (N / 16);
+    const int jm = j & (Ns - 1);
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      float2 x = buf[pad(j + r * NB)];
+      if (Ns > 1 && r > 0) x = cmul(x, __ldg(&tw[r * jm * TW]));
+      v[q][r] = x;
+    }
+    dft<R>(v[q]);
+  }
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < PER; ++q) {
+    const int j = t + q * (N / 16);
+    const int jm = j & (Ns - 1);
+    const int d = (j / Ns) * Ns * R + jm;
+#pragma unroll
+    for (int r = 0; r < R; ++r) buf[pad(d + r * Ns)] = v[q][r];
+  }
+  __syncthreads();
+}
+
+template <int N>
+__device__ __forceinline__ void fft_forward(float2 *buf, int t, const float2 *tw) {
+  fft_pass<N, 16, 1>(buf, t, tw);
+  fft_pass<N, 16, 16>(buf, t, tw);
+  if (N == 512) fft_pass<N, 2, 256>(buf, t, tw);
+  if (N == 1024) fft_pass<N, 4, 256>(buf, t, tw);
+  if (N == 2048) fft_pass<N, 8, 256>(buf, t, tw);
+  if (N >= 4096) fft_pass<N, 16, 256>(buf, t, tw);
+  if (N == 8192) fft_pass<N, 2, 4096>(buf, t, tw);
+}
+
+template <int N>
+__global__ void __launch_bounds__(N / 8) cdc_kernel(
+    int V, const uint8_t *__restrict__ tail, int64_t tail_first, int64_t tail_n,
+    const uint8_t *__restrict__ call, int64_t call_first, int64_t call_n, int dtype, float scale,
+    const float2 *__restrict__ H, const float2 *__restrict__ tw, float2 *__restrict__ u,
+    int64_t u_base, int64_t u_stride, int64_t win_first, int64_t n_total) {
+  extern __shared__ float2 smem[];
+  constexpr int PADN = N + N / 32;
+  const int S = N - V;
+  const int64_t i = win_first + blockIdx.x;
+  const int64_t lo = i * S - V / 2;
+  float2 *b0 = smem, *b1 = smem + PADN;
+  // ingest: both pols from one 4-scalar sample-time
+  for (int m = threadIdx.x; m < N; m += blockDim.x) {
+    const int64_t n = lo + m;
+    float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (n >= 0 && (n_total < 0 || n < n_total)) {
+      const uint8_t *src;
+      int64_t off;
+      if (n < call_first) { src = tail; off = n - tail_first; }
+      else { src = call; off = n - call_first; }
+      if (dtype == RX_I8x4) {
+        char4 c = reinterpret_cast<const char4 *>(src)[off];
+        x = make_float4((float)c.x, (float)c.y, (float)c.z, (float)c.w);
+      } else {
+        x = reinterpret_cast<const float4 *>(src)[off];
+      }
+    }
+    b0[pad(m)] = make_float2(x.x * scale, x.y * scale);
+    b1[pad(m)] = make_float2(x.z * scale, x.w * scale);
+  }
+  __syncthreads();
+  const int pol = threadIdx.x / (N / 16);
+  const int t = threadIdx.x % (N / 16);
+  float2 *buf = pol ? b1 : b0;
+  fft_forward<N>(buf, t, tw);
+  // multiply by H/N and conjugate (inverse via the forward transform)
+#pragma unroll
+  for (int q = 0; q < 16; ++q) {
+    const int k = t + q * (N / 16);
+    buf[pad(k)] = cconj(cmul(buf[pad(k)], __ldg(&H[k])));
+  }
+  __syncthreads();
+  fft_forward<N>(buf, t, tw);
+  float2 *out = u + (int64_t)pol * u_stride;
+  for (int tt = V / 2 + t; tt < V / 2 + S; tt += N / 16) {
+    const int64_t n = i * S + (tt - V / 2);
+    if (n_total >= 0 && n >= n_total) break;
+    out[n - u_base] = cconj(buf[pad(tt)]);
+  }
+}
+
+template <int N>
+static cudaError_t launch_cdc_n(int V, const void *tail, int64_t tail_first, int64_t tail_n,
+                                const void *call, int64_t call_first, int64_t call_n, int dtype,
+                                float scale, const float2 *H, const float2 *tw, float2 *u,
+                                int64_t u_base, int64_t u_stride, int64_t win_first,
+                                int64_t win_count, int64_t n_total, cudaStream_t s) {
+  const size_t sm = 2 * (N + N / 32) * sizeof(float2);
+  cudaError_t e = cudaFuncSetAttribute(cdc_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  cdc_kernel<N><<<(unsigned)win_count, N / 8, sm, s>>>(
+      V, (const uint8_t *)tail, tail_first, tail_n, (const uint8_t *)call, call_first, call_n,
+      dtype, scale, H, tw, u, u_base, u_stride, win_first, n_total);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cdc(int N, int V, const void *tail, int64_t tail_first, int64_t tail_n,
+                       const void *call, int64_t call_first, int64_t call_n, int dtype,
+                       float scale, const float2 *H, const float2 *tw, float2 *u,
+                       int64_t u_base, int64_t u_stride, int64_t win_first, int64_t win_count,
+                       int64_t n_total, cudaStream_t s) {
+  if (win_count <= 0) return cudaSuccess;
+#define RX_CDC_CASE(NN)                                                                     \
+  case NN:                                                                                  \
+    return launch_cdc_n<NN>(V, tail, tail_first, tail_n, call, call_first, call_n, dtype,   \
+                            scale, H, tw, u, u_base, u_stride, win_first, win_count, n_total, s);
+  switch (N) {
+    RX_CDC_CASE(256)
+    RX_CDC_CASE(512)
+    RX_CDC_CASE(1024)
+    RX_CDC_CASE(2048)
+    RX_CDC_CASE(4096)
+    RX_CDC_CASE(8192)
+    default: return cudaErrorInvalidValue;
+  }
+#undef RX_CDC_CASE
+}
+
+// ---------------------------------------------------------------- buffer moves
+__global__ void copy_cols_kernel(float2 *dst, int64_t ds, const float2 *src, int64_t ss, int64_t n) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  dst[i] = src[i];
+  dst[ds + i] = src[ss + i];
+}
+__global__ void copy_cols_i8_kernel(int8_t *dst, int64_t ds, const int8_t *src, int64_t ss, int64_t n) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  dst[i] = src[i];
+  dst[ds + i] = src[ss + i];
+}
+
+cudaError_t launch_copy_cols(float2 *dst, int64_t dst_stride, const float2 *src,
+                             int64_t src_stride, int64_t n, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  copy_cols_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(dst, dst_stride, src, src_stride, n);
+  return cudaGetLastError();
+}
+cudaError_t launch_copy_cols_i8(int8_t *dst, int64_t dst_stride, const int8_t *src,
+                                int64_t src_stride, int64_t n, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  copy_cols_i8_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(dst, dst_stride, src, src_stride, n);
+  return cudaGetLastError();
+}
+
+}  // namespace rx

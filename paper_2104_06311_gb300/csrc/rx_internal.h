@@ -1,0 +1,100 @@
+// Internal declarations shared by the host runtime and the kernel files.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/rx.h"
+
+namespace rx {
+
+constexpr int kMaxTaps = 16;      // butterfly taps T <= 15 (odd), padded to 16
+constexpr int kAngles = 32;       // BPS test angles (one per lane)
+constexpr int kEqThreads = 256;   // equaliser CTA
+constexpr int kChunkSym = 1152;   // equaliser span chunk (symbols) held in smem
+constexpr int kBpsChunk = 256;    // BPS pass-1 symbols per warp
+
+// Device-resident equaliser state (one per stream).
+struct EqState {
+  float2 taps[2][2][kMaxTaps];     // current taps h[p][q][i]
+  double dw;                       // per-symbol frequency offset (rad)
+  double Phi;                      // phase base of the next wave (rad)
+  int64_t next_wave;               // next wave to run
+  int32_t acq_done;
+  int32_t pad;
+};
+
+// Parameters of one equaliser launch (all values already validated).
+struct EqLaunch {
+  const float2 *u;          // CDC output [2][u_stride], sample n at u[n - u_base]
+  int64_t u_base, u_stride;
+  float2 *y;                // equaliser out [2][y_stride], symbol k at y[k - y_base]
+  int64_t y_base, y_stride;
+  EqState *st;
+  double2 *fo_part;         // [2][max_wave_segments] FO partial sums (double buffered)
+  float2 *tap_slot;         // [2][2*2*kMaxTaps] last-segment taps (double buffered)
+  float *trace;             // [trace_cap][2*2*kMaxTaps*2] wave start taps
+  double *trace_fo;         // [trace_cap][2] (dw, Phi)
+  int64_t trace_cap;
+  unsigned *barrier;        // grid barrier counter (zeroed before launch)
+  int *err;                 // sticky error word
+  int64_t K;                // symbols of the whole stream if known (flushed), else -1
+  int run_acq;              // 1: run the acquisition in this launch
+  int64_t A;                // acquisition length (symbols)
+  int64_t n_cma;            // CMA symbols (<= A)
+  int64_t wave_first, wave_last;  // waves [first, last) in this launch
+  int64_t n_segments;       // total segments if K known, else large
+  int P, S, W, Bu, T;
+  int mod_bits;             // 2 or 4
+  float mu_cma, mu_dd, cma_r2;
+  double fo_smooth;
+  int fo_track;
+  int nblocks;              // CTAs in the grid
+};
+
+// Per-stream BPS/demap launch description.
+struct BpsLaunch {
+  const float2 *y; int64_t y_base, y_stride;
+  int8_t *bhat; int64_t bh_base, bh_stride;
+  int *chunk_r;             // [2][n_chunks] unwrap step sums
+  float *chunk_s2;          // [2][n_chunks] sum of |z - dec z|^2
+  int64_t *chunk_m;         // [2][n_chunks] exclusive prefix (filled by the scan)
+  int64_t *m_carry;         // [2] unwrap count carried from earlier calls
+  double *region_s2;        // [2][n_regions] sigma^2 of regions in this call
+  int64_t k_lo, k_hi;       // symbols to emit [k_lo, k_hi)
+  int64_t K_end;            // symbols known to exist (stream end if flushed)
+  int64_t A, span;          // region layout
+  int chunk;                // chunk length (symbols)
+  int64_t n_chunks;
+  int Nb, mod_bits;
+  // outputs
+  uint32_t *bits; int64_t bits_stride;
+  float *llr; int64_t llr_stride;
+  float2 *sym; int64_t sym_stride;
+  int64_t out_first;        // stream index of output symbol 0
+};
+
+// Launchers (defined in the .cu files).
+cudaError_t launch_tables(float2 *H, float2 *tw, int N, double baud, double L_km, double D,
+                          double lam_nm, double rolloff, cudaStream_t s);
+cudaError_t launch_cdc(int N, int V, const void *tail, int64_t tail_first, int64_t tail_n,
+                       const void *call, int64_t call_first, int64_t call_n, int dtype,
+                       float scale, const float2 *H, const float2 *tw, float2 *u,
+                       int64_t u_base, int64_t u_stride, int64_t win_first, int64_t win_count,
+                       int64_t n_total, cudaStream_t s);
+cudaError_t launch_eq(const EqLaunch &L, cudaStream_t s);
+int eq_max_blocks();
+cudaError_t launch_bps(const BpsLaunch &L, cudaStream_t s);
+cudaError_t launch_ber_sync(const uint32_t *rx, int64_t rxs, const uint32_t *ref, int64_t refs,
+                            int64_t K, int m, int64_t s0, int64_t s1, unsigned *counts,
+                            cudaStream_t s);
+cudaError_t launch_ber_count(const uint32_t *rx, int64_t rxs, const uint32_t *ref, int64_t refs,
+                             int64_t K, int m, int64_t k0, const int *sync,
+                             unsigned long long *acc, cudaStream_t s);
+cudaError_t launch_copy_cols(float2 *dst, int64_t dst_stride, const float2 *src,
+                             int64_t src_stride, int64_t n, cudaStream_t s);
+cudaError_t launch_copy_cols_i8(int8_t *dst, int64_t dst_stride, const int8_t *src,
+                                int64_t src_stride, int64_t n, cudaStream_t s);
+
+}  // namespace rx

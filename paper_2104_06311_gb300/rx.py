@@ -1,0 +1,266 @@
+"""Thin ctypes binding of the receiver's C ABI (include/rx.h).
+
+Argument marshalling only: every step of the chain runs in the CUDA kernels of
+librx.so.  The functions carry the C names (rx_create, rx_process, rx_ber, ...);
+``Receiver`` bundles them for callers that hold torch CUDA tensors.  Loading
+fails loudly when the library has not been built: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as ct
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "librx.so")
+
+RX_OK, RX_EINVAL, RX_ENOMEM, RX_ECUDA, RX_ESTATE, RX_ETIMEOUT, RX_EUNSUPPORTED = range(7)
+RX_I8x4, RX_F32x4 = 1, 2
+
+PARAMS = {
+    "MOD": 1, "FFT_N": 2, "OVERLAP": 3, "ROLLOFF": 4, "LAMBDA_NM": 5, "MU_CMA": 6, "MU_DD": 7,
+    "N_CMA": 8, "UPDATE_BLOCK": 9, "SEG_LEN": 10, "SEG_PRETRAIN": 11, "BPS_HALFWIN": 12,
+    "BLOCK_SAMPLES": 13, "IN_SCALE": 14, "ACQ_MIN": 15, "FO_SMOOTH": 16, "FO_TRACK": 17,
+    "LLR_OUT": 18, "SYM_OUT": 19, "EQ_OUT": 20, "CDC_OUT": 21,
+}
+
+EXPORTS = ["rx_create", "rx_set_param", "rx_get_param", "rx_set_cuda_stream", "rx_reserve",
+           "rx_process", "rx_ber", "rx_trace", "rx_get_state", "rx_set_state", "rx_reset",
+           "rx_sync", "rx_destroy", "rx_status_str", "rx_last_error"]
+
+
+class rx_in(ct.Structure):
+    _fields_ = [("data", ct.c_void_p), ("n", ct.c_int64), ("dtype", ct.c_int32), ("reserved", ct.c_int32)]
+
+
+class rx_out(ct.Structure):
+    _fields_ = [("bits", ct.c_void_p), ("bits_stride", ct.c_int64),
+                ("llr", ct.c_void_p), ("llr_stride", ct.c_int64),
+                ("sym", ct.c_void_p), ("sym_stride", ct.c_int64),
+                ("eq", ct.c_void_p), ("eq_stride", ct.c_int64),
+                ("cdc", ct.c_void_p), ("cdc_stride", ct.c_int64),
+                ("capacity", ct.c_int64), ("n", ct.c_int64), ("first", ct.c_int64),
+                ("cdc_first", ct.c_int64), ("cdc_n", ct.c_int64)]
+
+
+class RxError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{msg} (status {status})")
+        self.status = status
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH) -> ct.CDLL:
+    """Load librx.so (raises if it is missing: build it with paper_2104_06311_gb300.build)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing; run `python -m paper_2104_06311_gb300.build`")
+    lib = ct.CDLL(path)
+    P = ct.c_void_p
+    lib.rx_create.argtypes = [ct.POINTER(P), ct.c_double, ct.c_int, ct.c_double, ct.c_double, ct.c_int, ct.c_int]
+    lib.rx_set_param.argtypes = [P, ct.c_int, ct.c_double]
+    lib.rx_get_param.argtypes = [P, ct.c_int, ct.POINTER(ct.c_double)]
+    lib.rx_set_cuda_stream.argtypes = [P, P]
+    lib.rx_reserve.argtypes = [P, ct.c_int64]
+    lib.rx_process.argtypes = [P, ct.POINTER(rx_in), ct.POINTER(rx_out)]
+    lib.rx_ber.argtypes = [P, P, ct.c_int64, P, ct.c_int64, ct.c_int64, ct.POINTER(ct.c_uint64),
+                           ct.POINTER(ct.c_uint64), ct.POINTER(ct.c_int32)]
+    lib.rx_trace.argtypes = [P, ct.c_int64, ct.POINTER(ct.c_float), ct.POINTER(ct.c_double), ct.POINTER(ct.c_double)]
+    lib.rx_get_state.argtypes = [P, P, ct.POINTER(ct.c_size_t)]
+    lib.rx_set_state.argtypes = [P, P, ct.c_size_t]
+    lib.rx_reset.argtypes = [P]
+    lib.rx_sync.argtypes = [P]
+    lib.rx_destroy.argtypes = [P]
+    lib.rx_destroy.restype = None
+    lib.rx_status_str.argtypes = [ct.c_int]
+    lib.rx_status_str.restype = ct.c_char_p
+    lib.rx_last_error.argtypes = [P]
+    lib.rx_last_error.restype = ct.c_char_p
+    for name in EXPORTS:
+        if name not in ("rx_destroy", "rx_status_str", "rx_last_error"):
+            getattr(lib, name).restype = ct.c_int
+    _lib = lib
+    return lib
+
+
+def _check(lib, h, status):
+    if status != RX_OK:
+        detail = lib.rx_last_error(h).decode() if h else ""
+        raise RxError(status, f"{lib.rx_status_str(status).decode()}: {detail}")
+
+
+class Receiver:
+    """One receiver stream on the current CUDA device (torch tensors in and out)."""
+
+    def __init__(self, baud, L_km, D=17.0, ntaps=15, bps_angles=32, sps=2, stream=None, **params):
+        import torch  # device memory and streams only
+        self.torch = torch
+        self.lib = load()
+        h = ct.c_void_p()
+        _check(self.lib, None, self.lib.rx_create(ct.byref(h), baud, sps, L_km, D, ntaps, bps_angles))
+        self.h = h
+        self.ntaps = ntaps
+        if stream is not None:
+            self.set_cuda_stream(stream)
+        for k, v in params.items():
+            self.set_param(k, v)
+
+    # -- C names
+    def rx_set_param(self, key, value):
+        _check(self.lib, self.h, self.lib.rx_set_param(self.h, PARAMS[key.upper()] if isinstance(key, str) else key, float(value)))
+
+    set_param = rx_set_param
+
+    def rx_get_param(self, key):
+        v = ct.c_double()
+        _check(self.lib, self.h, self.lib.rx_get_param(self.h, PARAMS[key.upper()] if isinstance(key, str) else key, ct.byref(v)))
+        return v.value
+
+    get_param = rx_get_param
+
+    def set_cuda_stream(self, stream):
+        ptr = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+        _check(self.lib, self.h, self.lib.rx_set_cuda_stream(self.h, ct.c_void_p(ptr)))
+
+    def rx_reserve(self, max_call_samples):
+        _check(self.lib, self.h, self.lib.rx_reserve(self.h, int(max_call_samples)))
+
+    reserve = rx_reserve
+
+    def rx_reset(self):
+        _check(self.lib, self.h, self.lib.rx_reset(self.h))
+
+    reset = rx_reset
+
+    def rx_sync(self):
+        _check(self.lib, self.h, self.lib.rx_sync(self.h))
+
+    sync = rx_sync
+
+    @property
+    def bits_per_symbol(self):
+        return int(self.get_param("MOD"))
+
+    def alloc_out(self, capacity, llr=False, sym=False, eq=False, cdc=False):
+        t = self.torch
+        m = self.bits_per_symbol
+        words = (capacity * m + 31) // 32
+        o = {"bits": t.zeros((2, words), dtype=t.int32, device="cuda"), "capacity": capacity}
+        if llr:
+            o["llr"] = t.zeros((2, capacity * m), dtype=t.float32, device="cuda")
+        if sym:
+            o["sym"] = t.zeros((2, capacity), dtype=t.complex64, device="cuda")
+        if eq:
+            o["eq"] = t.zeros((2, capacity), dtype=t.complex64, device="cuda")
+        if cdc:
+            o["cdc"] = t.zeros((2, 2 * capacity + 65536), dtype=t.complex64, device="cuda")
+        return o
+
+    def rx_process(self, samples, out, sym_offset=0, cdc_offset=0):
+        """Process a (n, 4) int8/float32 CUDA tensor (None = flush).
+
+        Writes into the tensors of `out` (from alloc_out) starting at symbol
+        column `sym_offset` (CDC samples at column `cdc_offset`) and returns
+        (first, n, cdc_first, cdc_n).
+        """
+        t = self.torch
+        i = rx_in()
+        if samples is None:
+            i.data, i.n, i.dtype = None, 0, RX_F32x4
+        else:
+            assert samples.is_cuda and samples.is_contiguous() and samples.shape[-1] == 4
+            i.data = samples.data_ptr()
+            i.n = samples.shape[0]
+            i.dtype = RX_I8x4 if samples.dtype == t.int8 else RX_F32x4
+        o = rx_out()
+        m = self.bits_per_symbol
+        assert (sym_offset * m) % 32 == 0
+        bits = out["bits"]
+        o.bits = bits.data_ptr() + (sym_offset * m // 32) * 4
+        o.bits_stride = bits.shape[1]
+        if "llr" in out:
+            o.llr = out["llr"].data_ptr() + sym_offset * m * 4
+            o.llr_stride = out["llr"].shape[1]
+        if "sym" in out:
+            o.sym = out["sym"].data_ptr() + sym_offset * 8
+            o.sym_stride = out["sym"].shape[1]
+        if "eq" in out:
+            o.eq = out["eq"].data_ptr() + sym_offset * 8
+            o.eq_stride = out["eq"].shape[1]
+        if "cdc" in out:
+            o.cdc = out["cdc"].data_ptr() + cdc_offset * 8
+            o.cdc_stride = out["cdc"].shape[1]
+        o.capacity = out["capacity"] - sym_offset
+        _check(self.lib, self.h, self.lib.rx_process(self.h, ct.byref(i), ct.byref(o)))
+        return o.first, o.n, o.cdc_first, o.cdc_n
+
+    process = rx_process
+
+    def rx_ber(self, rx_bits, ref_bits, n_symbols):
+        """(errors, bits_counted, sync) with rx_bits/ref_bits (2, words) int32 CUDA tensors."""
+        e, n = ct.c_uint64(), ct.c_uint64()
+        sync = (ct.c_int32 * 6)()
+        _check(self.lib, self.h, self.lib.rx_ber(self.h, rx_bits.data_ptr(), rx_bits.shape[1], ref_bits.data_ptr(),
+                                                 ref_bits.shape[1], int(n_symbols), ct.byref(e), ct.byref(n), sync))
+        return e.value, n.value, [tuple(sync[3 * p:3 * p + 3]) for p in range(2)]
+
+    ber = rx_ber
+
+    def rx_trace(self, wave):
+        import numpy as np
+        taps = (ct.c_float * (2 * 2 * self.ntaps * 2))()
+        dw, Phi = ct.c_double(), ct.c_double()
+        _check(self.lib, self.h, self.lib.rx_trace(self.h, int(wave), taps, ct.byref(dw), ct.byref(Phi)))
+        a = np.frombuffer(taps, dtype=np.float32).astype(np.float64)
+        return (a[0::2] + 1j * a[1::2]).reshape(2, 2, self.ntaps), dw.value, Phi.value
+
+    trace = rx_trace
+
+    def rx_get_state(self) -> bytes:
+        n = ct.c_size_t()
+        _check(self.lib, self.h, self.lib.rx_get_state(self.h, None, ct.byref(n)))
+        buf = ct.create_string_buffer(n.value)
+        _check(self.lib, self.h, self.lib.rx_get_state(self.h, buf, ct.byref(n)))
+        return buf.raw[:n.value]
+
+    get_state = rx_get_state
+
+    def rx_set_state(self, blob: bytes):
+        _check(self.lib, self.h, self.lib.rx_set_state(self.h, blob, len(blob)))
+
+    set_state = rx_set_state
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.rx_destroy(self.h)
+            self.h = None
+
+    rx_destroy = close
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def run_stream(self, samples, chunk=None, llr=False, sym=False, eq=False, cdc=False, out=None):
+        """Reset, process `samples` in calls of `chunk` sample-times, flush; returns outputs."""
+        n = samples.shape[0]
+        K = n // 2
+        chunk = chunk or n
+        if out is None:
+            out = self.alloc_out(K + 64, llr=llr, sym=sym, eq=eq, cdc=cdc)
+        self.reset()
+        pos = cpos = 0
+        for a in list(range(0, n, chunk)) + [None]:
+            piece = None if a is None else samples[a:a + chunk]
+            first, cnt, cfirst, cn = self.process(piece, out, sym_offset=pos, cdc_offset=cpos)
+            assert first == pos and (cn == 0 or cfirst == cpos)
+            pos += cnt
+            cpos += cn
+        out["n"] = pos
+        out["cdc_n"] = cpos
+        return out
