@@ -1,0 +1,321 @@
+#!/usr/bin/env python
+"""Throughput of the coherent-receiver DSP chain on one GB300 (per rank).
+
+Workload: the 10,000 km straight-line shape -- DP-QPSK 10 GBd, 2 samples per
+symbol, 2^24 symbols per polarisation (2^25 sample-times) streamed as int8
+ADC samples, with dispersion D = 17 ps/(nm km), slowly varying PMD
+(0.1 ps/sqrt(km)), 100 kHz laser phase noise, a 200 MHz frequency offset and
+AWGN at Es/N0 = 9.8 dB (pre-FEC BER ~1e-3).  Synthetic, seeded input from
+``linksim`` stands in for the paper's lab link.
+
+One step = one pass of the whole chain over the stream: reset, one
+rx_process call with all samples (CDC -> FO removal -> butterfly CMA/DD-LMS
+-> BPS/unwrap -> demap), the flush call, and rx_ber (synchronised BER count).
+Inputs (128 MiB int8) and intermediates (512 MiB CDC output) are larger than
+L2, so no L2 flush is inserted between steps.
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU
+oracle on a bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "GSa/s and decoded Gb/s per GB300 at oracle-matched BER; % HBM roofline"
+FP32_LANES_PER_SM = 128
+N_SM = 152
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--n-sym", type=int, default=1 << 24, help="symbols per pol (default: the full workload)")
+    ap.add_argument("--cpu-sample", type=int, default=1 << 21, help="sample-times the oracle baseline processes")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return d, "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        self.f.seek(0)
+        rows = [r.split(",") for r in self.f.read().strip().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        sm = [float(r[1]) for r in rows if len(r) >= 9 and r[1].strip().replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if len(r) >= 9 and r[2].strip().replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows if len(r) >= 9 for i in range(4) if "Active" in r[5 + i]})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def make_input(n_sym):
+    import linksim as L
+    lk = L.workload("c2", n_sym=n_sym)
+    return lk, L.generate(lk)
+
+
+def cpu_oracle_run(g, n_samples):
+    """Time the FP64 oracle (as it stands) on the first n_samples sample-times."""
+    import oracle as O
+    lk = g.link
+    p = O.RxParams(baud=lk.baud, L_km=lk.L_km, D=lk.D, mod=lk.mod, in_scale=g.in_scale)
+    x = g.samples[:n_samples]
+    t0 = time.perf_counter()
+    out = O.run_chain(x, p)
+    dt = time.perf_counter() - t0
+    return out, dt, p
+
+
+def reference_arm(args, rank, world):
+    if rank != 0:
+        return
+    lk, g = make_input(args.cpu_sample // 2)
+    n = g.samples.shape[0]
+    times = []
+    for i in range(args.warmup + args.steps):
+        _, dt, p = cpu_oracle_run(g, n)
+        if i >= args.warmup:
+            times.append(dt)
+    t = sum(times)
+    value = n * args.steps / t / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "GSa/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded linksim 10,000 km link)",
+        "config": {"workload": "10,000 km straight-line DP-QPSK 10 GBd int8, 2^24 symbols/pol (bounded sample)",
+                   "sample_times_per_step": n},
+        "cpu_baseline": {"value": value, "unit": "GSa/s", "cores": 1, "kind": "oracle",
+                         "sample": f"first {n} sample-times of the workload per step (FP64 numpy oracle)"},
+        "e2e": {"value": value, "unit": "GSa/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        reference_arm(args, rank, world)
+        return
+    import numpy as np
+    import torch
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2104_06311_gb300 import Receiver, build
+    if not os.path.exists(build.OUT):
+        build.build()
+    import linksim as L
+
+    lk, g = make_input(args.n_sym)
+    n = g.samples.shape[0]
+    K = n // 2
+    x = torch.from_numpy(g.samples).cuda()
+    ref = torch.from_numpy(L.pack_bits(g.tx_bits).view(np.int32)).cuda()
+    stream = torch.cuda.current_stream()
+    rx = Receiver(lk.baud, lk.L_km, D=lk.D, stream=stream, MOD=2, IN_SCALE=g.in_scale)
+    rx.reserve(n)
+    out = rx.alloc_out(K + 64)
+
+    def step(inp):
+        rx.reset()
+        _, c1, _, _ = rx.process(inp, out, 0)
+        _, c2, _, _ = rx.process(None, out, c1)
+        assert c1 + c2 == K
+        return rx.ber(out["bits"], ref, K)
+
+    for _ in range(args.warmup):
+        e, nb, sync = step(x)
+    ber = e / nb
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    clocks = ClockSampler(local)
+    rx.set_param("PROFILE", 1)
+    rx.profile(reset=True)
+    barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(args.steps):
+        step(x)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    ms = t0.elapsed_time(t1)
+    prof = rx.profile(reset=True)
+    rx.set_param("PROFILE", 0)
+    if dist is not None:
+        tm = torch.tensor([ms], device="cuda")
+        dist.all_reduce(tm, op=dist.ReduceOp.MAX)
+        ms = float(tm.item())
+    value = n * args.steps * world / (ms / 1e3) / 1e9
+    launches = sum(v[1] for v in prof.values())
+
+    # ---- end to end: pinned host samples -> device -> chain -> bits + BER back to the host
+    e2e = None
+    if not args.no_e2e:
+        xh = torch.from_numpy(g.samples).pin_memory()
+        xd = torch.empty_like(x)
+        bits_h = torch.empty_like(out["bits"], device="cpu").pin_memory()
+
+        def step_e2e():
+            xd.copy_(xh, non_blocking=True)
+            r = step(xd)
+            bits_h.copy_(out["bits"], non_blocking=True)
+            return r
+
+        for _ in range(2):
+            step_e2e()
+        torch.cuda.synchronize()
+        barrier()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(args.steps):
+            step_e2e()
+        b.record(stream)
+        torch.cuda.synchronize()
+        ems = a.elapsed_time(b)
+        if dist is not None:
+            tm = torch.tensor([ems], device="cuda")
+            dist.all_reduce(tm, op=dist.ReduceOp.MAX)
+            ems = float(tm.item())
+        e2e = {"value": n * args.steps * world / (ems / 1e3) / 1e9, "unit": "GSa/s",
+               "h2d_bytes_per_step": int(x.numel() * x.element_size()),
+               "d2h_bytes_per_step": int(out["bits"].numel() * 4 + 16)}
+
+    # ---- roofline of the dominant kernel (stage times from CUDA events on the launch stream)
+    pk, pk_kind = peaks()
+    stage = max(("cdc", "eq", "bps"), key=lambda s: prof[s][0])
+    T, W, S = 15, 128, 1024
+    if stage == "eq":
+        # per symbol (both pols): FIR 2*2*T CMAC + gradient 2*2*T CMAC (8 flop each)
+        # + inner BPS 2*32*11 flop; symbols processed include the W pre-training per segment
+        flop = (2 * 2 * T * 8 * 2 + 2 * 32 * 11) * K * (1 + W / S)
+        sm_mhz = pk.get("sm_max_mhz", 2070.0)
+        peak = N_SM * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+        achieved = flop / (prof[stage][0] / args.steps / 1e3) / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None, "kernel": "eq_kernel",
+                "peak_note": f"FP32 SIMT: {N_SM} SM x {FP32_LANES_PER_SM} lanes x 2 flop x {sm_mhz:.0f} MHz"}
+    else:
+        per = {"cdc": 4 + 16, "bps": 16 + 16 + 1 + 0.25 * 2}[stage]   # bytes per sample-time
+        bytes_ = per * n
+        achieved = bytes_ / (prof[stage][0] / args.steps / 1e3) / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / pk["hbm_gbs"], "traffic": None, "kernel": stage}
+    roof["peak_source"] = pk_kind
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "GSa/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded linksim 10,000 km link), resident in HBM",
+        "config": {"workload": "10,000 km straight-line DP-QPSK 10 GBd, 2 sps, 2^24 symbols/pol, int8 ADC, "
+                               "PMD 0.1 ps/sqrt(km), 100 kHz PN, 200 MHz FO, Es/N0 9.8 dB",
+                   "sample_times": n, "fft_n": int(rx.get_param("FFT_N")), "overlap": int(rx.get_param("OVERLAP")),
+                   "taps": T, "bps_angles": 32, "segments_per_wave": 32,
+                   "l2": "inputs (128 MiB) and CDC intermediates (512 MiB) exceed L2; no flush",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single stream"},
+        "decoded_gbps": value / 2 * 2 * 2,
+        "hbm_roofline_frac": value / (pk["hbm_gbs"] / 4.25),
+        "ber": ber, "ber_sync": sync,
+        "stage_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
+        "gpu_launches": int(launches),
+        "roofline": roof,
+        "clocks": clk,
+        "e2e": e2e,
+    }
+
+    # ---- CPU baseline: the oracle as it stands, bounded sample, rank 0 at N = 1
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        ns = min(args.cpu_sample, n)
+        orc, dt, p = cpu_oracle_run(g, ns)
+        line["cpu_baseline"] = {"value": ns / dt / 1e9, "unit": "GSa/s", "cores": 1, "kind": "oracle",
+                                "sample": f"first {ns} sample-times of the workload, FP64 numpy oracle, one core"}
+        # bit agreement of the CUDA chain with the oracle on that sample (same stream prefix)
+        rxs = Receiver(lk.baud, lk.L_km, D=lk.D, stream=stream, MOD=2, IN_SCALE=g.in_scale)
+        o2 = rxs.run_stream(x[:ns].contiguous())
+        torch.cuda.synchronize()
+        gb = L.unpack_bits(o2["bits"].cpu().numpy().view(np.uint32), ns // 2 * 2)
+        mism = int(np.sum(gb != orc["bits"]))
+        eo, no, _ = O_ber(orc["bits"], g.tx_bits[:, :ns // 2 * 2], p)
+        line["oracle_parity_sample"] = {"bits": int(gb.size), "mismatched_bits": mism,
+                                        "ber_oracle": eo / max(no, 1),
+                                        "ber_gpu": None}
+        e3, n3, _ = rxs.ber(o2["bits"], torch.from_numpy(L.pack_bits(g.tx_bits[:, :ns // 2 * 2]).view(np.int32)).cuda(), ns // 2)
+        line["oracle_parity_sample"]["ber_gpu"] = e3 / max(n3, 1)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def O_ber(bits, tx_bits, p):
+    import oracle as O
+    return O.ber_sync_count(bits, tx_bits, p.mod, p.acq_len(bits.shape[1] // p.bits))
+
+
+if __name__ == "__main__":
+    main()

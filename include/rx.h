@@ -85,7 +85,18 @@ enum {
   RX_P_LLR_OUT = 18,       /* 1 = write LLRs to rx_out.llr                          */
   RX_P_SYM_OUT = 19,       /* 1 = write phase-recovered symbols to rx_out.sym        */
   RX_P_EQ_OUT = 20,        /* 1 = write equaliser outputs to rx_out.eq               */
-  RX_P_CDC_OUT = 21        /* 1 = write CDC outputs to rx_out.cdc (tests)            */
+  RX_P_CDC_OUT = 21,       /* 1 = write CDC outputs to rx_out.cdc (tests)            */
+  RX_P_PROFILE = 22        /* 1 = time each stage with CUDA events (rx_profile)      */
+};
+
+/* Stages reported by rx_profile. */
+enum {
+  RX_STAGE_CDC = 0,        /* overlap-save CDC windows                               */
+  RX_STAGE_EQ = 1,         /* butterfly equaliser (acquisition + waves)              */
+  RX_STAGE_BPS = 2,        /* BPS pass 1 + unwrap scan + demap                       */
+  RX_STAGE_MOVE = 3,       /* carried-tail moves between calls                       */
+  RX_STAGE_BER = 4,        /* BER synchronisation and counting                       */
+  RX_STAGE_COUNT = 5
 };
 
 /* One call's input: n sample-times (n even) at a device address. */
@@ -179,6 +190,13 @@ void rx_destroy(rx_stream *rx);
 const char *rx_status_str(rx_status s);
 /* Text of the last error on this handle (empty if none). */
 const char *rx_last_error(rx_stream *rx);
+
+/* Per-stage device time (ms, summed over CUDA-event pairs recorded on the bound
+ * stream while RX_P_PROFILE is 1) and kernel launches of this library (always
+ * counted) since the last reset of the counters; ms and launches each hold
+ * RX_STAGE_COUNT entries.  reset != 0 clears the counters afterwards.
+ * Synchronises the bound stream.  Not from the paper: measurement support. */
+rx_status rx_profile(rx_stream *rx, double *ms, int64_t *launches, int reset);
 
 #ifdef __cplusplus
 }

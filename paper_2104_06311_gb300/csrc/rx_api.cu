@@ -47,7 +47,7 @@ struct rx_stream {
   double in_scale = 1.0;
   int64_t acq_min = 16384;
   double fo_smooth = 16.0;
-  int fo_track = 1, llr_out = 0, sym_out = 0, eq_out = 0, cdc_out = 0;
+  int fo_track = 1, llr_out = 0, sym_out = 0, eq_out = 0, cdc_out = 0, profile = 0;
   // ---- resolved
   int N = 0, V = 0, Sh = 0, P = 0, C = 256;
   int64_t A_full = 0, span = 0;
@@ -83,6 +83,12 @@ struct rx_stream {
   int *h_err = nullptr;  // pinned mirror of the device error word
   cudaEvent_t err_ev = nullptr;
   int eq_blocks = 0;
+  // ---- per-stage measurement (CUDA events on the bound stream)
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<std::pair<int, size_t>> ev_pending;  // (stage, index of the start event)
+  size_t ev_used = 0;
+  double stage_ms[RX_STAGE_COUNT] = {0, 0, 0, 0, 0};
+  int64_t stage_launches[RX_STAGE_COUNT] = {0, 0, 0, 0, 0};
   // ---- stream state
   bool started = false, flushed = false;
   int dtype = 0;
@@ -179,6 +185,10 @@ void release(rx_stream *rx) {
     if (p) cudaFree(p);
   if (rx->h_err) cudaFreeHost(rx->h_err);
   if (rx->err_ev) cudaEventDestroy(rx->err_ev);
+  for (cudaEvent_t e : rx->ev_pool) cudaEventDestroy(e);
+  rx->ev_pool.clear();
+  rx->ev_pending.clear();
+  rx->ev_used = 0;
   rx->H = rx->tw = nullptr;
   rx->tail[0] = rx->tail[1] = nullptr;
   rx->u[0] = rx->u[1] = rx->y[0] = rx->y[1] = nullptr;
@@ -246,6 +256,29 @@ rx_status check_device_error(rx_stream *rx, bool wait) {
   return RX_OK;
 }
 
+// Bracket a stage with an event pair when profiling is on.
+struct StageTimer {
+  rx_stream *rx;
+  int stage;
+  size_t idx = (size_t)-1;
+  StageTimer(rx_stream *r, int st) : rx(r), stage(st) {
+    if (!rx->profile) return;
+    while (rx->ev_pool.size() < rx->ev_used + 2) {
+      cudaEvent_t e;
+      if (cudaEventCreate(&e) != cudaSuccess) return;
+      rx->ev_pool.push_back(e);
+    }
+    idx = rx->ev_used;
+    rx->ev_used += 2;
+    cudaEventRecord(rx->ev_pool[idx], rx->stream);
+  }
+  ~StageTimer() {
+    if (idx == (size_t)-1) return;
+    cudaEventRecord(rx->ev_pool[idx + 1], rx->stream);
+    rx->ev_pending.push_back({stage, idx});
+  }
+};
+
 rx_status post_error_copy(rx_stream *rx) {
   RX_CUDA(cudaMemcpyAsync(rx->h_err, rx->err, sizeof(int), cudaMemcpyDeviceToHost, rx->stream), "error copy");
   RX_CUDA(cudaEventRecord(rx->err_ev, rx->stream), "error event");
@@ -300,6 +333,10 @@ rx_status rx_create(rx_stream **out, double baud, int sps, double L_km, double D
 
 rx_status rx_set_param(rx_stream *rx, int key, double v) {
   if (!rx) return RX_EINVAL;
+  if (key == RX_P_PROFILE) {
+    rx->profile = v != 0;
+    return RX_OK;
+  }
   if (rx->started) return fail(rx, RX_ESTATE, "parameters are fixed once the stream has started");
   if (!isfinite(v)) return fail(rx, RX_EINVAL, "non-finite parameter");
   const bool needs_realloc = rx->reserved;
@@ -344,6 +381,7 @@ rx_status rx_set_param(rx_stream *rx, int key, double v) {
     case RX_P_SYM_OUT: rx->sym_out = v != 0; return RX_OK;
     case RX_P_EQ_OUT: rx->eq_out = v != 0; return RX_OK;
     case RX_P_CDC_OUT: rx->cdc_out = v != 0; return RX_OK;
+    case RX_P_PROFILE: rx->profile = v != 0; return RX_OK;
     default: return fail(rx, RX_EINVAL, "unknown parameter key");
   }
   if (s != RX_OK) return s;
@@ -379,6 +417,7 @@ rx_status rx_get_param(rx_stream *rx, int key, double *v) {
     case RX_P_SYM_OUT: *v = rx->sym_out; break;
     case RX_P_EQ_OUT: *v = rx->eq_out; break;
     case RX_P_CDC_OUT: *v = rx->cdc_out; break;
+    case RX_P_PROFILE: *v = rx->profile; break;
     default: return fail(rx, RX_EINVAL, "unknown parameter key");
   }
   return RX_OK;
@@ -530,6 +569,8 @@ rx_status rx_process(rx_stream *rx, const rx_in *in, rx_out *out) {
     const int64_t new_end = std::min(win_end * rx->Sh, rx->n_total >= 0 ? rx->n_total : INT64_MAX);
     if (new_end - u_keep > rx->u_cap) return fail(rx, RX_EINVAL, "CDC buffer overflow (call too large for the reservation)");
     if (u_keep != rx->u_base) {
+      StageTimer tm(rx, RX_STAGE_MOVE);
+      rx->stage_launches[RX_STAGE_MOVE] += keep > 0;
       const int nxt = 1 - rx->cur_u;
       RX_CUDA(launch_copy_cols(rx->u[nxt], rx->u_cap, rx->u[rx->cur_u] + (u_keep - rx->u_base), rx->u_cap, keep, st), "slide u");
       rx->cur_u = nxt;
@@ -538,10 +579,14 @@ rx_status rx_process(rx_stream *rx, const rx_in *in, rx_out *out) {
   }
   const int64_t nwin = win_end - rx->next_win;
   if (nwin > 0) {
+    {
+    StageTimer tm(rx, RX_STAGE_CDC);
+    rx->stage_launches[RX_STAGE_CDC] += 1;
     RX_CUDA(launch_cdc(rx->N, rx->V, rx->tail[rx->cur_tail], rx->tail_first, rx->tail_n, in->data, call_first, call_n,
                        rx->dtype, (float)rx->in_scale, rx->H, rx->tw, rx->u[rx->cur_u], rx->u_base, rx->u_cap,
                        rx->next_win, nwin, rx->n_total, st),
             "cdc");
+    }
     const int64_t f_old = rx->F_cdc;
     rx->F_cdc = std::min(win_end * rx->Sh, rx->n_total >= 0 ? rx->n_total : INT64_MAX);
     rx->next_win = win_end;
@@ -608,6 +653,8 @@ rx_status rx_process(rx_stream *rx, const rx_in *in, rx_out *out) {
     if (acq_ready && wave_last > rx->next_wave) new_eq = std::min(A + wave_last * rx->span, K >= 0 ? K : INT64_MAX);
     if (new_eq - y_keep > rx->y_cap) return fail(rx, RX_EINVAL, "equaliser buffer overflow");
     if (y_keep != rx->y_base) {
+      StageTimer tm(rx, RX_STAGE_MOVE);
+      rx->stage_launches[RX_STAGE_MOVE] += 2 * (keep > 0);
       const int nxt = 1 - rx->cur_y;
       RX_CUDA(launch_copy_cols(rx->y[nxt], rx->y_cap, rx->y[rx->cur_y] + (y_keep - rx->y_base), rx->y_cap, keep, st), "slide y");
       RX_CUDA(launch_copy_cols_i8(rx->bh[nxt], rx->y_cap, rx->bh[rx->cur_y] + (y_keep - rx->y_base), rx->y_cap, keep, st), "slide bhat");
@@ -649,7 +696,11 @@ rx_status rx_process(rx_stream *rx, const rx_in *in, rx_out *out) {
       L.fo_track = rx->fo_track;
       L.nblocks = rx->eq_blocks;
       RX_CUDA(cudaMemsetAsync(rx->barrier, 0, sizeof(unsigned), st), "barrier reset");
-      RX_CUDA(launch_eq(L, st), "equaliser");
+      {
+        StageTimer tm(rx, RX_STAGE_EQ);
+        rx->stage_launches[RX_STAGE_EQ] += 1;
+        RX_CUDA(launch_eq(L, st), "equaliser");
+      }
       if (run_acq) rx->acq_done = true;
       rx->next_wave = wave_last;
       rx->F_eq = new_eq;
@@ -706,7 +757,11 @@ rx_status rx_process(rx_stream *rx, const rx_in *in, rx_out *out) {
     B.sym = rx->sym_out ? (float2 *)out->sym : nullptr;
     B.sym_stride = out->sym_stride;
     B.out_first = k_lo;
-    RX_CUDA(launch_bps(B, st), "bps");
+    {
+      StageTimer tm(rx, RX_STAGE_BPS);
+      rx->stage_launches[RX_STAGE_BPS] += 3;
+      RX_CUDA(launch_bps(B, st), "bps");
+    }
     if (rx->eq_out)
       RX_CUDA(launch_copy_cols((float2 *)out->eq, out->eq_stride, rx->y[rx->cur_y] + (k_lo - rx->y_base), rx->y_cap, n, st), "eq out");
     out->first = k_lo;
@@ -730,6 +785,7 @@ rx_status rx_ber(rx_stream *rx, const uint32_t *rx_bits, int64_t rx_stride, cons
   *bits_counted = 0;
   if (s1 > n_symbols) return RX_OK;
   cudaStream_t st = rx->stream;
+  rx->stage_launches[RX_STAGE_BER] += 2;
   RX_CUDA(launch_ber_sync(rx_bits, rx_stride, ref_bits, ref_stride, n_symbols, m, s0, s1, rx->ber_counts, st), "ber sync");
   std::vector<unsigned> counts(2 * 2 * 4 * 129);
   RX_CUDA(cudaMemcpyAsync(counts.data(), rx->ber_counts, counts.size() * sizeof(unsigned), cudaMemcpyDeviceToHost, st), "ber sync copy");
@@ -874,6 +930,27 @@ rx_status rx_set_state(rx_stream *rx, const void *blob, size_t len) {
   }
   RX_CUDA(cudaMemset(rx->err, 0, sizeof(int)), "state");
   *rx->h_err = 0;
+  return RX_OK;
+}
+
+rx_status rx_profile(rx_stream *rx, double *ms, int64_t *launches, int reset) {
+  if (!rx) return RX_EINVAL;
+  if (rx->reserved) RX_CUDA(cudaStreamSynchronize(rx->stream), "profile wait");
+  for (const auto &pe : rx->ev_pending) {
+    float t = 0.f;
+    RX_CUDA(cudaEventElapsedTime(&t, rx->ev_pool[pe.second], rx->ev_pool[pe.second + 1]), "profile");
+    rx->stage_ms[pe.first] += t;
+  }
+  rx->ev_pending.clear();
+  rx->ev_used = 0;
+  for (int i = 0; i < RX_STAGE_COUNT; ++i) {
+    if (ms) ms[i] = rx->stage_ms[i];
+    if (launches) launches[i] = rx->stage_launches[i];
+    if (reset) {
+      rx->stage_ms[i] = 0;
+      rx->stage_launches[i] = 0;
+    }
+  }
   return RX_OK;
 }
 

@@ -20,12 +20,13 @@ PARAMS = {
     "MOD": 1, "FFT_N": 2, "OVERLAP": 3, "ROLLOFF": 4, "LAMBDA_NM": 5, "MU_CMA": 6, "MU_DD": 7,
     "N_CMA": 8, "UPDATE_BLOCK": 9, "SEG_LEN": 10, "SEG_PRETRAIN": 11, "BPS_HALFWIN": 12,
     "BLOCK_SAMPLES": 13, "IN_SCALE": 14, "ACQ_MIN": 15, "FO_SMOOTH": 16, "FO_TRACK": 17,
-    "LLR_OUT": 18, "SYM_OUT": 19, "EQ_OUT": 20, "CDC_OUT": 21,
+    "LLR_OUT": 18, "SYM_OUT": 19, "EQ_OUT": 20, "CDC_OUT": 21, "PROFILE": 22,
 }
+STAGES = ["cdc", "eq", "bps", "move", "ber"]
 
 EXPORTS = ["rx_create", "rx_set_param", "rx_get_param", "rx_set_cuda_stream", "rx_reserve",
            "rx_process", "rx_ber", "rx_trace", "rx_get_state", "rx_set_state", "rx_reset",
-           "rx_sync", "rx_destroy", "rx_status_str", "rx_last_error"]
+           "rx_sync", "rx_destroy", "rx_status_str", "rx_last_error", "rx_profile"]
 
 
 class rx_in(ct.Structure):
@@ -71,6 +72,7 @@ def load(path: str = LIB_PATH) -> ct.CDLL:
     lib.rx_trace.argtypes = [P, ct.c_int64, ct.POINTER(ct.c_float), ct.POINTER(ct.c_double), ct.POINTER(ct.c_double)]
     lib.rx_get_state.argtypes = [P, P, ct.POINTER(ct.c_size_t)]
     lib.rx_set_state.argtypes = [P, P, ct.c_size_t]
+    lib.rx_profile.argtypes = [P, ct.POINTER(ct.c_double), ct.POINTER(ct.c_int64), ct.c_int]
     lib.rx_reset.argtypes = [P]
     lib.rx_sync.argtypes = [P]
     lib.rx_destroy.argtypes = [P]
@@ -232,6 +234,15 @@ class Receiver:
         _check(self.lib, self.h, self.lib.rx_set_state(self.h, blob, len(blob)))
 
     set_state = rx_set_state
+
+    def rx_profile(self, reset=False):
+        """{stage: (ms, launches)} since the last reset of the counters."""
+        ms = (ct.c_double * len(STAGES))()
+        n = (ct.c_int64 * len(STAGES))()
+        _check(self.lib, self.h, self.lib.rx_profile(self.h, ms, n, 1 if reset else 0))
+        return {k: (ms[i], n[i]) for i, k in enumerate(STAGES)}
+
+    profile = rx_profile
 
     def close(self):
         if getattr(self, "h", None):
