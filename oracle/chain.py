@@ -331,7 +331,8 @@ def lms_step(h: np.ndarray, X: np.ndarray, mode: str, p: RxParams, phis: np.ndar
     return y, h - mu * g
 
 
-def equalize(u: np.ndarray, p: RxParams, trace: dict | None = None) -> np.ndarray:
+def equalize(u: np.ndarray, p: RxParams, trace: dict | None = None,
+             follow: dict | None = None) -> np.ndarray:
     """Butterfly equaliser over the whole stream with the segment schedule.
 
     u: (2, n) CDC output at 2 samples/symbol; returns y (2, K), K = n // 2.
@@ -352,6 +353,14 @@ def equalize(u: np.ndarray, p: RxParams, trace: dict | None = None) -> np.ndarra
       * Frequency tracking per wave: dw_{w+1} = dw_w + r_w/16 with r_w a
         quarter of the argument of the 4th-power sum over adjacent pairs
         inside each segment; Phi_{w+1} = remainder(Phi_w + 2PS dw_w/sps, 2pi).
+
+    The tracked phase integrates the frequency estimate over 2PS samples per
+    wave, so a rounding-level difference in an estimate (FP32 vs FP64) grows
+    into a phase offset that no later step removes.  With `follow` (keys
+    acq_dw, wave_dw, wave_Phi: another implementation's tracker state) the
+    schedule runs on that state instead of its own estimates; its own
+    estimates are still computed and recorded in `trace` (acq_dw_own,
+    wave_r), so each estimate can be compared on identical data.
     """
     p = p.resolved()
     n = u.shape[-1]
@@ -374,6 +383,9 @@ def equalize(u: np.ndarray, p: RxParams, trace: dict | None = None) -> np.ndarra
         k1 = min(k0 + Bu, n_cma)
         y[:, k0:k1], h = lms_step(h, win.taps_input(k0, k1, T, c), "cma", p, phis)
     dw = 0.25 * np.angle(fo_estimate_sum(y[:, n_cma // 2:n_cma])) if p.fo_track else 0.0
+    dw_own = dw
+    if follow is not None:
+        dw = follow["acq_dw"]
     delta = dw / p.sps
     # -- acquisition, DD part
     if A > n_cma:
@@ -383,7 +395,8 @@ def equalize(u: np.ndarray, p: RxParams, trace: dict | None = None) -> np.ndarra
             y[:, k0:k1], h = lms_step(h, win.taps_input(k0, k1, T, c), "dd", p, phis)
     Phi = math.remainder((2 * A - 2 * n_cma) * delta, TWO_PI)
     if trace is not None:
-        trace.update(acq_dw=dw, acq_taps=h.copy(), wave_taps=[], wave_dw=[], wave_Phi=[])
+        trace.update(acq_dw=dw, acq_dw_own=dw_own, acq_taps=h.copy(), wave_taps=[], wave_dw=[],
+                     wave_Phi=[], wave_r=[])
     # -- waves
     S, W, P = p.seg_len, p.seg_pretrain, p.wave_segments()
     G = (K - A + S - 1) // S
@@ -391,6 +404,8 @@ def equalize(u: np.ndarray, p: RxParams, trace: dict | None = None) -> np.ndarra
     for w0 in range(0, G, P):
         gs = range(w0, min(w0 + P, G))
         n_w = 2 * (A + w0 * S)
+        if follow is not None and w0 // P < len(follow["wave_dw"]):
+            dw, Phi = follow["wave_dw"][w0 // P], follow["wave_Phi"][w0 // P]
         delta = dw / p.sps
         if trace is not None:
             trace["wave_taps"].append(h_start.copy())
@@ -411,6 +426,8 @@ def equalize(u: np.ndarray, p: RxParams, trace: dict | None = None) -> np.ndarra
             acc += fo_estimate_sum(y[:, ks:ke])
             h_last = hh
         r = 0.25 * np.angle(acc) if p.fo_track else 0.0
+        if trace is not None:
+            trace["wave_r"].append(r)
         Phi = math.remainder(Phi + (2 * P * S) * delta, TWO_PI)
         dw = dw + r / p.fo_smooth
         h_start = h_last
@@ -488,7 +505,8 @@ def demap(z: np.ndarray, p: RxParams):
     return bits, llr, sig
 
 
-def run_chain(samples: np.ndarray, p: RxParams, trace: dict | None = None) -> dict:
+def run_chain(samples: np.ndarray, p: RxParams, trace: dict | None = None,
+              follow: dict | None = None) -> dict:
     """Whole stream: ingest -> CDC -> equaliser -> BPS -> demap.
 
     samples: (n, 4) real [Xi, Xq, Yi, Yq] (int8 codes or floats); the ingest
@@ -500,7 +518,7 @@ def run_chain(samples: np.ndarray, p: RxParams, trace: dict | None = None) -> di
     n = a.shape[0] - (a.shape[0] % 2)
     x = np.stack([a[:n, 0] + 1j * a[:n, 1], a[:n, 2] + 1j * a[:n, 3]])
     u = cdc_overlap_save(x, cdc_filter(p), p.overlap)
-    y = equalize(u, p, trace)
+    y = equalize(u, p, trace, follow)
     bhat, m, z = bps_outer(y, p)
     bits, llr, sig = demap(z, p)
     return dict(u=u, y=y, bhat=bhat, m=m, z=z, bits=bits, llr=llr, sigma2=sig)

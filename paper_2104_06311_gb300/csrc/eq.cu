@@ -92,12 +92,26 @@ struct Rot {
 
 __device__ void load_window(const EqLaunch &L, EqSmem &sm, int64_t win_lo, int count, const Rot &rot,
                             int64_t n_limit) {
-  for (int j = threadIdx.x; j < count; j += blockDim.x) {
+  // issue every load of this thread first (HBM latency once, not per sample)
+  constexpr int kPer = (kWinMax + kEqThreads - 1) / kEqThreads;
+  float2 va[kPer], vb[kPer];
+#pragma unroll
+  for (int r = 0; r < kPer; ++r) {
+    const int j = threadIdx.x + r * kEqThreads;
     const int64_t n = win_lo + j;
-    float2 a = make_float2(0.f, 0.f), b = a;
+    va[r] = vb[r] = make_float2(0.f, 0.f);
+    if (j < count && n >= 0 && n < n_limit) {
+      va[r] = __ldg(&L.u[n - L.u_base]);
+      vb[r] = __ldg(&L.u[L.u_stride + n - L.u_base]);
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < kPer; ++r) {
+    const int j = threadIdx.x + r * kEqThreads;
+    if (j >= count) break;
+    const int64_t n = win_lo + j;
+    float2 a = va[r], b = vb[r];
     if (n >= 0 && n < n_limit) {
-      a = __ldg(&L.u[n - L.u_base]);
-      b = __ldg(&L.u[L.u_stride + n - L.u_base]);
       if (rot.on) {
         const unsigned long long ph = rot.Phi_q + (unsigned long long)(n - rot.n0) * rot.delta_q;
         const float x = (float)(int)(ph >> 32) * 4.656612873077392578125e-10f;  // turns * 2
