@@ -10,7 +10,7 @@ import numpy as np
 import linksim as L
 import oracle as O
 
-# FP32 path vs FP64 oracle: relative RMS of complex outputs (spec tolerance)
+# FP32 path vs FP64 oracle: relative RMS of complex outputs (the parity tolerance)
 REL_RMS_TOL = 1e-4
 # decisions may differ only where the oracle's soft value is this close to a boundary
 BOUNDARY_EPS = 1e-5

@@ -239,7 +239,7 @@ def test_flush_of_empty_stream_emits_nothing():
 
 
 def test_full_size_c2_sampled():
-    """BASELINE workload size (2^24 symbols/pol, int8, one call + flush): sampled checks.
+    """Full 10,000 km workload size (2^24 symbols/pol, int8, one call + flush): sampled checks.
 
     The oracle recomputes sampled CDC windows exactly and runs sampled waves of
     the equaliser from the GPU's own state at the wave start (taps, dw, Phi);
