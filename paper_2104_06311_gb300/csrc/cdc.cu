@@ -1,9 +1,9 @@
 // Overlap-save chromatic-dispersion compensation with the RRC matched filter.
 //
-// Analogue of the paper's static frequency-domain equalisation "by
-// multiplication with an offline-optimized filter enabled by another FFT and
-// IFFT pair" (arXiv 2104.06311, Section "Experimental setup", processing-chain
-// paragraph), with the closed-form filter
+// Analogue of the paper's static frequency-domain equaliser, which multiplies
+// the spectrum by a filter optimised offline between an FFT and an IFFT
+// (arXiv 2104.06311, Section "Experimental setup", processing-chain
+// paragraph); here the filter is closed-form:
 //   H_k = exp(-j beta2 L w_k^2 / 2) * sqrt(2) * H_rrc(f_k),  beta2 = -D lam^2/(2 pi c).
 // One CTA filters one overlap-save window of N samples for both polarisations:
 // ingest (int8/f32 -> f32, times the ingest scale) -> radix-16 Stockham FFT in

@@ -1,31 +1,49 @@
 // 2x2 butterfly FIR adapted by block CMA then DD-LMS, with frequency-offset
 // removal in front of it, in the acquisition + segment-wave schedule.
 //
-// The paper's receiver ends with "a four-tap adaptive time-domain DD-LMS"
-// equaliser, sequential in time, whose buffer-to-buffer dependency is carried
-// by CUDA events while other buffers proceed in parallel streams (arXiv
-// 2104.06311, Section "Experimental setup", processing-chain paragraph).  The
-// GB300 form keeps the one sequential dependency the method has (taps flowing
-// from one update block to the next) inside one persistent cooperative launch:
+// The paper's receiver finishes with a short adaptive time-domain
+// decision-directed LMS equaliser whose updates run sequentially in time;
+// its buffer-to-buffer dependency is carried by CUDA events while other
+// buffers proceed on parallel streams (arXiv 2104.06311, Section
+// "Experimental setup", processing-chain paragraph).  The GB300 form keeps the
+// method's one sequential dependency (taps flowing from one update block to
+// the next) inside one persistent cooperative launch.
 //
-//   * acquisition: CTA 0 runs symbols [0, A) as one chain of update blocks
-//     (CMA on [0, N_CMA) without rotation; the 4th-power frequency estimate
-//     over [N_CMA/2, N_CMA); DD on [N_CMA, A) with the input rotated);
+// Row split.  Output row p of the butterfly, y_p = sum_q h_pq * u_q, has an
+// error that depends on y_p alone and a gradient e_p conj(u_q); the two rows
+// therefore adapt independently given the (shared) rotated input.  One CTA of
+// four warps runs one (segment, row): 2P CTAs per wave.
+//
+//   * acquisition: CTAs 0 and 1 (rows 0 and 1) run symbols [0, A) as one chain
+//     of update blocks: CMA on [0, N_CMA) unrotated; the two rows exchange
+//     their 4th-power sums over [N_CMA/2, N_CMA) through a two-CTA barrier and
+//     both form the same frequency estimate; DD on [N_CMA, A) rotated;
 //   * waves: wave w holds P segments of S symbols; every segment starts from
 //     the taps at the end of the last segment of wave w-1, pre-trains on the W
-//     symbols before it, then equalises its own S symbols; the P segments run
-//     on P CTAs at once.  A bounded grid barrier closes each wave, after which
-//     every CTA folds the segments' 4th-power sums (fixed order, FP64) into the
-//     frequency tracker: dw += r/16, Phi = remainder(Phi + 2PS dw/2, 2pi).
+//     symbols before it, then equalises its own symbols.  A bounded grid
+//     barrier closes each wave; one warp per CTA then folds the 4th-power sums
+//     (fixed order, FP64) into the tracker: dw += r/16,
+//     Phi = Phi + 2PS dw/2 reduced to [-pi, pi].
 //
-// Per update block (B_u <= 32 symbols) a 256-thread CTA computes
-//   y_p[k] = sum_{q,i} h_pq[i] u_q[2k + c - i]                        (8 warps)
-//   DD: theta = argmin_b sum_k |y e^{-j phi_b} - dec(.)|^2 (lane = angle)
-//       e = y - dec(y e^{-j theta}) e^{j theta};  CMA: e = y (|y|^2 - R2)
-//   h_pq[i] -= mu sum_k e_p[k] conj(u_q[2k + c - i])
-// with four CTA barriers per block.  The input window of a chunk of up to
-// 1152 symbols sits in shared memory, rotated by exp(-j phi_n) computed from a
-// 64-bit fixed-point phase (exact modular arithmetic on Phi and dw/2 held in FP64).
+// One update block of B_u <= 32 symbols; warp w owns symbols 8w..8w+7 and
+// lane 4j + part works on symbol j of its warp with part = (input pol q, tap
+// half): taps i = 8 half .. 8 half + 7 of h_q.
+//   A  FIR: each lane keeps its 8 window samples u_q[2k+c-i] in registers and
+//      forms its partial sum; a 2-level xor reduction gives y to the quad.
+//   B  DD only: each lane evaluates |y e^{-j phi_b} - dec(.)|^2 for the 8
+//      angles b = 8 part + a of its symbol; a 3-level reduce-scatter over the
+//      warp's 8 symbols leaves angle 8 part + j in lane (j, part); CTA
+//      barrier; every warp sums the 4 warp partials and takes the argmin
+//      (smallest b on ties); e = y - dec(y e^{-j theta}) e^{j theta}.
+//      CMA: e = y (|y|^2 - R2).
+//   C  gradient: each lane multiplies e by its own 8 window samples
+//      (e conj(u)), a reduce-scatter leaves tap 8 half + j in lane (j, part);
+//      CTA barrier; each lane adds the 4 warp partials of its tap, updates it
+//      and the 8 taps of each FIR lane are gathered back by shuffles.
+// Frequency pairs accumulate in compensated (Kahan) FP32 per lane and are
+// summed in FP64 per segment.  The input window of a chunk of up to 1152
+// symbols sits in shared memory (rows padded against bank conflicts), rotated
+// by exp(-j phi_n) from a 64-bit fixed-point phase; Phi and dw are FP64.
 #include <math.h>
 
 #include "common.cuh"
@@ -35,16 +53,19 @@ namespace rx {
 
 namespace {
 
+constexpr int kWarps = kEqThreads / 32;  // 4
 constexpr int kWinMax = 2 * kChunkSym + 2 * 8;
+constexpr int kWinRow = kWinMax + 1;     // odd row length: pol rows land 8 bytes apart in the banks
+constexpr unsigned FULL = 0xffffffffu;
 
 struct EqSmem {
-  float2 win[2][kWinMax];
-  float2 taps[2][2][kMaxTaps];
-  float2 ybuf[2][32];
-  float2 ylast[2];
-  float bps[2][4][32];
-  float2 grad[4][2][2][kMaxTaps];
-  double2 fo_warp[8];
+  float2 win[2][kWinRow];
+  float2 ybuf[2][32];                    // double-buffered by step parity
+  float bps[kWarps][32];
+  float2 grad[2][kWarps][2][kMaxTaps];   // double-buffered by step parity
+  double2 fo_warp[kWarps];
+  double trk[2];                         // (dw, Phi) handed from warp 0 to the CTA
+  unsigned long long rotq[2];            // (Phi_q, delta_q) of the next wave
   int fail;
 };
 
@@ -57,24 +78,26 @@ __device__ __forceinline__ unsigned long long to_q64_turns(double rad) {
   return (unsigned long long)__double2ll_rn(t * 18446744073709551616.0);
 }
 
-// Bounded grid barrier: returns false (and sets the error word) on timeout or
-// when another CTA already failed.
-__device__ bool grid_barrier(const EqLaunch &L, unsigned &epoch, EqSmem &sm) {
+// Bounded barrier over `count` CTAs on counter *ctr: returns false (and sets
+// the error word) on timeout or when another CTA already failed.
+__device__ bool cta_barrier(int *err, unsigned *ctr, unsigned count, unsigned &epoch, EqSmem &sm) {
   __syncthreads();
   if (threadIdx.x == 0) {
     sm.fail = 0;
     __threadfence();
-    atomicAdd(L.barrier, 1u);
-    const unsigned target = (epoch + 1u) * (unsigned)L.nblocks;
+    atomicAdd(ctr, 1u);
+    const unsigned target = (epoch + 1u) * count;
     const unsigned long long t0 = globaltimer_ns();
-    while (ld_acquire_u32(L.barrier) < target) {
-      if (*(volatile int *)L.err != 0) { sm.fail = 1; break; }
+    unsigned ns = 32;
+    while (ld_acquire_u32(ctr) < target) {
+      if (*(volatile int *)err != 0) { sm.fail = 1; break; }
       if (globaltimer_ns() - t0 > kSpinLimitNs) {
-        atomicOr(L.err, DEV_ERR_TIMEOUT);
+        atomicOr(err, DEV_ERR_TIMEOUT);
         sm.fail = 1;
         break;
       }
-      __nanosleep(100);
+      __nanosleep(ns);
+      if (ns < 256) ns <<= 1;
     }
     __threadfence();
   }
@@ -90,8 +113,10 @@ struct Rot {
   int64_t n0;
 };
 
-__device__ void load_window(const EqLaunch &L, EqSmem &sm, int64_t win_lo, int count, const Rot &rot,
-                            int64_t n_limit) {
+// u0/u1: CDC output of pols X/Y, indexed by stream sample n.
+__device__ __forceinline__ void load_window(const float2 *__restrict__ u0, const float2 *__restrict__ u1,
+                                            EqSmem &sm, int64_t win_lo, int count, const Rot &rot,
+                                            int64_t n_limit) {
   // issue every load of this thread first (HBM latency once, not per sample)
   constexpr int kPer = (kWinMax + kEqThreads - 1) / kEqThreads;
   float2 va[kPer], vb[kPer];
@@ -101,8 +126,8 @@ __device__ void load_window(const EqLaunch &L, EqSmem &sm, int64_t win_lo, int c
     const int64_t n = win_lo + j;
     va[r] = vb[r] = make_float2(0.f, 0.f);
     if (j < count && n >= 0 && n < n_limit) {
-      va[r] = __ldg(&L.u[n - L.u_base]);
-      vb[r] = __ldg(&L.u[L.u_stride + n - L.u_base]);
+      va[r] = __ldg(&u0[n]);
+      vb[r] = __ldg(&u1[n]);
     }
   }
 #pragma unroll
@@ -111,188 +136,246 @@ __device__ void load_window(const EqLaunch &L, EqSmem &sm, int64_t win_lo, int c
     if (j >= count) break;
     const int64_t n = win_lo + j;
     float2 a = va[r], b = vb[r];
-    if (n >= 0 && n < n_limit) {
-      if (rot.on) {
-        const unsigned long long ph = rot.Phi_q + (unsigned long long)(n - rot.n0) * rot.delta_q;
-        const float x = (float)(int)(ph >> 32) * 4.656612873077392578125e-10f;  // turns * 2
-        float s, c;
-        sincospif(x, &s, &c);
-        const float2 r = make_float2(c, -s);  // exp(-j phi)
-        a = cmul(a, r);
-        b = cmul(b, r);
-      }
+    if (rot.on && n >= 0 && n < n_limit) {
+      const unsigned long long ph = rot.Phi_q + (unsigned long long)(n - rot.n0) * rot.delta_q;
+      const float x = (float)(int)(ph >> 32) * 4.656612873077392578125e-10f;  // turns * 2
+      float s, c;
+      sincospif(x, &s, &c);
+      const float2 r2 = make_float2(c, -s);  // exp(-j phi)
+      a = cmul(a, r2);
+      b = cmul(b, r2);
     }
     sm.win[0][j] = a;
     sm.win[1][j] = b;
   }
 }
 
-// Describes one run over symbols [kp, ke) with outputs from ks and FO pairs
+// One run over symbols [kp, ke) with outputs from ks and frequency pairs
 // (k-1, k) for k-1 >= fo_lo, k < fo_hi.
 struct Span {
   int64_t kp, ks, ke;
   int64_t fo_lo, fo_hi;
-  int cma;             // 1: CMA error, 0: DD error
+  int cma;
   Rot rot;
 };
 
+// Per-thread constant roles.
+struct Lane {
+  int warp, lane;
+  int j, part, q, half;   // symbol j of the warp; (q, half) = (part >> 1, part & 1)
+  int tap;                // tap this lane owns in the update: 8 half + j
+  float2 rot[8];          // exp(-j phi_b) for b = 8 part + a, a = 0..7
+  float2 rot_b;           // exp(-j phi_b) for b = lane (argmin source)
+};
+
+// Loop-invariant scalars of a launch, held in registers.
+struct Hot {
+  float2 *yrow;              // equaliser output of this row, indexed by stream symbol
+  const float2 *u0, *u1;     // CDC output of pols X / Y, indexed by stream sample
+  int T, c, Bu;
+  float mu_cma, mu_dd, cma_r2;
+};
+
+// Compensated sums of the 4th-power pairs (x and y parts).
+struct Kahan {
+  float sx, cx, sy, cy;
+};
+
+__device__ __forceinline__ void kahan_add(float &s, float &c, float v) {
+  const float y = v - c;
+  const float t = s + y;
+  c = (t - s) - y;
+  s = t;
+}
+
+// The 8 taps a FIR lane needs, gathered from the lanes owning them.
+__device__ __forceinline__ void gather_taps(float2 (&h)[8], float2 own, const Lane &ln) {
+#pragma unroll
+  for (int ii = 0; ii < 8; ++ii) {
+    h[ii].x = __shfl_sync(FULL, own.x, 4 * ii + ln.part);
+    h[ii].y = __shfl_sync(FULL, own.y, 4 * ii + ln.part);
+  }
+}
+
 template <int MB>
-__device__ void run_span(const EqLaunch &L, EqSmem &sm, const Span &sp, double2 &fo_acc,
-                         float2 rot_b, int64_t n_limit) {
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int T = L.T, c = (T - 1) / 2, Bu = L.Bu;
+__device__ __forceinline__ void run_span(const Hot hot, EqSmem &sm, const Span sp, const Lane &ln,
+                                         float2 &own, float2 (&h)[8], Kahan &fo, int64_t n_limit) {
+  const int T = hot.T, c = hot.c, Bu = hot.Bu;
   const int chunk = (kChunkSym / Bu) * Bu;
-  const float mu = sp.cma ? L.mu_cma : L.mu_dd;
-  const int p = warp >> 2, kq = warp & 3;
+  const float mu = sp.cma ? hot.mu_cma : hot.mu_dd;
+  const int kl = ln.warp * 8 + ln.j;     // this lane's symbol within a block
+  const bool hi4 = ln.j & 4, hi2 = ln.j & 2, hi1 = ln.j & 1;
+  int step = 0;
   for (int64_t cs = sp.kp; cs < sp.ke; cs += chunk) {
     const int64_t ce = min(cs + (int64_t)chunk, sp.ke);
     const int64_t win_lo = 2 * cs - c;
     const int count = (int)(2 * (ce - cs) + 2 * c - 1);
-    __syncthreads();  // previous chunk's readers are done with win
-    load_window(L, sm, win_lo, count, sp.rot, n_limit);
+    const int nsteps = (int)((ce - cs + Bu - 1) / Bu);
+    __syncthreads();  // every warp is done with the previous chunk's window
+    load_window(hot.u0, hot.u1, sm, win_lo, count, sp.rot, n_limit);
     __syncthreads();
-    for (int64_t k0 = cs; k0 < ce; k0 += Bu) {
+    for (int t = 0; t < nsteps; ++t, ++step) {
+      const int64_t k0 = cs + (int64_t)t * Bu;
       const int nk = (int)min((int64_t)Bu, ce - k0);
       const bool out = k0 >= sp.ks;
-      // ---- phase A: FIR, 4 lanes per (pol, symbol)
+      const int par = step & 1;
+      const bool act = kl < nk;
+      // last symbol of the previous block (read before anyone can overwrite it)
+      const float2 yprev_last = sm.ybuf[par ^ 1][Bu - 1];
+      // ---- A: FIR
+      float2 x[8];
+      float ax0 = 0.f, ay0 = 0.f, ax1 = 0.f, ay1 = 0.f;
       {
-        const int ksub = lane >> 2, part = lane & 3, q = part >> 1, half = part & 1;
-        const int kl = kq * 8 + ksub;
-        float2 acc = make_float2(0.f, 0.f);
-        if (kl < nk) {
-          const int base = (int)(2 * (k0 + kl) + c - win_lo);
-          const int i0 = half ? 8 : 0;
+        const float2 *xw = sm.win[ln.q] + (2 * t * Bu + 2 * c) + 2 * kl - ln.half * 8;
 #pragma unroll
-          for (int ii = 0; ii < 8; ++ii) {
-            const int i = i0 + ii;
-            if (i < T && (half || i < 8)) {
-              const float2 h = sm.taps[p][q][i], x = sm.win[q][base - i];
-              acc.x = fmaf(h.x, x.x, fmaf(-h.y, x.y, acc.x));
-              acc.y = fmaf(h.x, x.y, fmaf(h.y, x.x, acc.y));
-            }
-          }
-        }
-        acc.x += __shfl_xor_sync(0xffffffffu, acc.x, 1);
-        acc.y += __shfl_xor_sync(0xffffffffu, acc.y, 1);
-        acc.x += __shfl_xor_sync(0xffffffffu, acc.x, 2);
-        acc.y += __shfl_xor_sync(0xffffffffu, acc.y, 2);
-        if (part == 0) {
-          sm.ybuf[p][kl] = kl < nk ? acc : make_float2(0.f, 0.f);
-          if (out && kl < nk) L.y[(int64_t)p * L.y_stride + (k0 + kl - L.y_base)] = acc;
+        for (int ii = 0; ii < 8; ++ii)
+          x[ii] = (act && ln.half * 8 + ii < T) ? xw[-ii] : make_float2(0.f, 0.f);
+#pragma unroll
+        for (int ii = 0; ii < 8; ii += 2) {
+          ax0 = fmaf(h[ii].x, x[ii].x, fmaf(-h[ii].y, x[ii].y, ax0));
+          ay0 = fmaf(h[ii].x, x[ii].y, fmaf(h[ii].y, x[ii].x, ay0));
+          ax1 = fmaf(h[ii + 1].x, x[ii + 1].x, fmaf(-h[ii + 1].y, x[ii + 1].y, ax1));
+          ay1 = fmaf(h[ii + 1].x, x[ii + 1].y, fmaf(h[ii + 1].y, x[ii + 1].x, ay1));
         }
       }
-      __syncthreads();  // (1) ybuf ready
-      // ---- phase B: error per symbol
-      float2 er = make_float2(0.f, 0.f);
+      float2 yv = make_float2(ax0 + ax1, ay0 + ay1);
+      yv.x += __shfl_xor_sync(FULL, yv.x, 1);
+      yv.y += __shfl_xor_sync(FULL, yv.y, 1);
+      yv.x += __shfl_xor_sync(FULL, yv.x, 2);
+      yv.y += __shfl_xor_sync(FULL, yv.y, 2);
+      if (ln.part == 0) {
+        sm.ybuf[par][kl] = act ? yv : make_float2(0.f, 0.f);
+        if (out && act) hot.yrow[k0 + kl] = yv;
+      }
+      // ---- B: error
       float2 eth = make_float2(1.f, 0.f);  // exp(j theta)
       if (!sp.cma) {
-        float ds = 0.f;
+        float d[8];
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          const int kl = kq * 8 + j;
-          if (kl < nk) ds += qam_dist<MB>(cmul(sm.ybuf[p][kl], rot_b));
+        for (int a = 0; a < 8; ++a) d[a] = act ? qam_dist<MB>(cmul(yv, ln.rot[a])) : 0.f;
+        float e1[4], e2[2];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+          const float send = hi4 ? d[a] : d[a + 4];
+          e1[a] = (hi4 ? d[a + 4] : d[a]) + __shfl_xor_sync(FULL, send, 16);
         }
-        sm.bps[p][kq][lane] = ds;
-        __syncthreads();  // (2)
-        const float D = (sm.bps[p][0][lane] + sm.bps[p][1][lane]) + (sm.bps[p][2][lane] + sm.bps[p][3][lane]);
+#pragma unroll
+        for (int a = 0; a < 2; ++a) {
+          const float send = hi2 ? e1[a] : e1[a + 2];
+          e2[a] = (hi2 ? e1[a + 2] : e1[a]) + __shfl_xor_sync(FULL, send, 8);
+        }
+        const float send = hi1 ? e2[0] : e2[1];
+        const float dsum = (hi1 ? e2[1] : e2[0]) + __shfl_xor_sync(FULL, send, 4);
+        sm.bps[ln.warp][ln.part * 8 + ln.j] = dsum;
+        __syncthreads();  // (1)
+        const float D = (sm.bps[0][ln.lane] + sm.bps[1][ln.lane]) + (sm.bps[2][ln.lane] + sm.bps[3][ln.lane]);
         const unsigned key = __float_as_uint(D);
-        const unsigned mn = __reduce_min_sync(0xffffffffu, key);
-        const int bstar = __ffs(__ballot_sync(0xffffffffu, key == mn)) - 1;
-        const float rc = __shfl_sync(0xffffffffu, rot_b.x, bstar);
-        const float rs = __shfl_sync(0xffffffffu, rot_b.y, bstar);
-        eth = make_float2(rc, -rs);
+        const unsigned mn = __reduce_min_sync(FULL, key);
+        const int bstar = __ffs(__ballot_sync(FULL, key == mn)) - 1;
+        eth = make_float2(__shfl_sync(FULL, ln.rot_b.x, bstar), -__shfl_sync(FULL, ln.rot_b.y, bstar));
       }
-      if (lane < 8) {
-        const int kl = kq * 8 + lane;
-        if (kl < nk) {
-          const float2 yv = sm.ybuf[p][kl];
-          if (sp.cma) {
-            const float m2 = yv.x * yv.x + yv.y * yv.y - L.cma_r2;
-            er = cscale(yv, m2);
-          } else {
-            const float2 d = qam_decide<MB>(cmulc(yv, eth));
-            er = csub(yv, cmul(d, eth));
-          }
-          // frequency-offset pairs
-          const int64_t k = k0 + kl;
-          if (out && k - 1 >= sp.fo_lo && k < sp.fo_hi) {
-            const float2 yp = kl > 0 ? sm.ybuf[p][kl - 1] : sm.ylast[p];
-            const float2 v = cmulc(yv, yp);
-            const float2 v2 = cmul(v, v);
-            const float2 v4 = cmul(v2, v2);
-            fo_acc.x += (double)v4.x;
-            fo_acc.y += (double)v4.y;
-          }
+      float2 er = make_float2(0.f, 0.f);
+      if (act) {
+        if (sp.cma) {
+          er = cscale(yv, yv.x * yv.x + yv.y * yv.y - hot.cma_r2);
+        } else {
+          const float2 dd = qam_decide<MB>(cmulc(yv, eth));
+          er = csub(yv, cmul(dd, eth));
         }
       }
-      // ---- phase C: gradient partial over this warp's 8 symbols
+      // ---- C: gradient e conj(u) of this lane's 8 taps, reduce-scatter over the warp's symbols
       {
-        const int q = lane / T, i = lane - q * T;
-        float2 g = make_float2(0.f, 0.f);
+        float2 g[8];
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          const float ex = __shfl_sync(0xffffffffu, er.x, j);
-          const float ey = __shfl_sync(0xffffffffu, er.y, j);
-          const int kl = kq * 8 + j;
-          if (lane < 2 * T && kl < nk) {
-            const float2 x = sm.win[q][(int)(2 * (k0 + kl) + c - i - win_lo)];
-            // e * conj(x)
-            g.x = fmaf(ex, x.x, fmaf(ey, x.y, g.x));
-            g.y = fmaf(ey, x.x, fmaf(-ex, x.y, g.y));
-          }
+        for (int ii = 0; ii < 8; ++ii) g[ii] = cmulc(er, x[ii]);
+        float2 g1[4], g2[2];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+          const float2 s2 = hi4 ? g[a] : g[a + 4];
+          const float2 k2 = hi4 ? g[a + 4] : g[a];
+          g1[a] = make_float2(k2.x + __shfl_xor_sync(FULL, s2.x, 16), k2.y + __shfl_xor_sync(FULL, s2.y, 16));
         }
-        if (lane < 2 * T) sm.grad[kq][p][q][i] = g;
+#pragma unroll
+        for (int a = 0; a < 2; ++a) {
+          const float2 s2 = hi2 ? g1[a] : g1[a + 2];
+          const float2 k2 = hi2 ? g1[a + 2] : g1[a];
+          g2[a] = make_float2(k2.x + __shfl_xor_sync(FULL, s2.x, 8), k2.y + __shfl_xor_sync(FULL, s2.y, 8));
+        }
+        const float2 s2 = hi1 ? g2[0] : g2[1];
+        const float2 k2 = hi1 ? g2[1] : g2[0];
+        sm.grad[par][ln.warp][ln.q][ln.tap] =
+            make_float2(k2.x + __shfl_xor_sync(FULL, s2.x, 4), k2.y + __shfl_xor_sync(FULL, s2.y, 4));
       }
-      __syncthreads();  // (3)
-      if (tid < 4 * T) {
-        const int pp = tid / (2 * T), r = tid - pp * 2 * T, q = r / T, i = r - q * T;
-        const float2 g0 = sm.grad[0][pp][q][i], g1 = sm.grad[1][pp][q][i];
-        const float2 g2 = sm.grad[2][pp][q][i], g3 = sm.grad[3][pp][q][i];
-        const float gx = (g0.x + g1.x) + (g2.x + g3.x), gy = (g0.y + g1.y) + (g2.y + g3.y);
-        float2 h = sm.taps[pp][q][i];
-        h.x -= mu * gx;
-        h.y -= mu * gy;
-        sm.taps[pp][q][i] = h;
+      // previous symbol for the frequency pairs: in-warp neighbour, else shared memory
+      const float yupx = __shfl_up_sync(FULL, yv.x, 4), yupy = __shfl_up_sync(FULL, yv.y, 4);
+      __syncthreads();  // (2)
+      // ---- frequency pairs (k-1, k) inside [fo_lo, fo_hi)
+      if (out && act && ln.part == 0) {
+        const int64_t k = k0 + kl;
+        if (k - 1 >= sp.fo_lo && k < sp.fo_hi) {
+          float2 yp;
+          if (ln.j > 0) yp = make_float2(yupx, yupy);
+          else if (ln.warp > 0) yp = sm.ybuf[par][kl - 1];
+          else yp = yprev_last;
+          const float2 v = cmulc(yv, yp);
+          const float2 v2 = cmul(v, v);
+          const float2 v4 = cmul(v2, v2);
+          kahan_add(fo.sx, fo.cx, v4.x);
+          kahan_add(fo.sy, fo.cy, v4.y);
+        }
       }
-      if (tid == 0) {
-        sm.ylast[0] = sm.ybuf[0][nk - 1];
-        sm.ylast[1] = sm.ybuf[1][nk - 1];
+      // ---- tap update: this lane's own tap, then every FIR lane gathers its 8
+      if (ln.tap < T) {
+        const float2 g0 = sm.grad[par][0][ln.q][ln.tap], g1 = sm.grad[par][1][ln.q][ln.tap];
+        const float2 g2 = sm.grad[par][2][ln.q][ln.tap], g3 = sm.grad[par][3][ln.q][ln.tap];
+        own.x -= mu * ((g0.x + g1.x) + (g2.x + g3.x));
+        own.y -= mu * ((g0.y + g1.y) + (g2.y + g3.y));
       }
-      __syncthreads();  // (4) taps updated
+      gather_taps(h, own, ln);
     }
   }
 }
 
-// Reduce the per-lane FO accumulators (lanes 0..7 of every warp) in a fixed order.
-__device__ double2 reduce_fo(EqSmem &sm, double2 acc) {
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int o = 4; o >= 1; o >>= 1) {
-    acc.x += __shfl_down_sync(0xffffffffu, acc.x, o);
-    acc.y += __shfl_down_sync(0xffffffffu, acc.y, o);
+// Segment total of the per-lane compensated pair sums, in FP64 and a fixed order.
+__device__ __forceinline__ double2 reduce_fo(EqSmem &sm, const Kahan &fo, const Lane &ln) {
+  double2 acc = make_double2((double)fo.sx - (double)fo.cx, (double)fo.sy - (double)fo.cy);
+  for (int o = 16; o >= 4; o >>= 1) {
+    acc.x += __shfl_xor_sync(FULL, acc.x, o);
+    acc.y += __shfl_xor_sync(FULL, acc.y, o);
   }
   __syncthreads();
-  if (lane == 0) sm.fo_warp[warp] = acc;
+  if (ln.lane == 0) sm.fo_warp[ln.warp] = acc;
   __syncthreads();
-  double2 s = make_double2(0.0, 0.0);
-  for (int w = 0; w < 8; ++w) {
-    s.x += sm.fo_warp[w].x;
-    s.y += sm.fo_warp[w].y;
-  }
+  double2 s;
+  s.x = (sm.fo_warp[0].x + sm.fo_warp[1].x) + (sm.fo_warp[2].x + sm.fo_warp[3].x);
+  s.y = (sm.fo_warp[0].y + sm.fo_warp[1].y) + (sm.fo_warp[2].y + sm.fo_warp[3].y);
   return s;
 }
 
-__device__ void taps_from_global(EqSmem &sm, const float2 *src) {
-  for (int j = threadIdx.x; j < 2 * 2 * kMaxTaps; j += blockDim.x)
-    (&sm.taps[0][0][0])[j] = __ldcg(&src[j]);
+// This lane's own tap of row p from a [2][2][kMaxTaps] array, then the FIR gather.
+__device__ __forceinline__ void load_row(float2 &own, float2 (&h)[8], const float2 *src, int p, const Lane &ln) {
+  own = __ldcg(&src[(p * 2 + ln.q) * kMaxTaps + ln.tap]);
+  gather_taps(h, own, ln);
 }
 
-__device__ void write_trace(const EqLaunch &L, int64_t idx, const float2 *taps, double dw, double Phi) {
-  if (idx < 0 || idx >= L.trace_cap) return;
-  for (int j = threadIdx.x; j < 2 * 2 * kMaxTaps; j += blockDim.x) {
-    L.trace[idx * 4 * kMaxTaps * 2 + 2 * j] = taps[j].x;
-    L.trace[idx * 4 * kMaxTaps * 2 + 2 * j + 1] = taps[j].y;
+// Row p's taps (warp 0's 32 lanes own all of them) to dst and, optionally, a trace entry.
+__device__ __forceinline__ void store_row(float2 own, float2 *dst, float *trace, int p, const Lane &ln) {
+  if (ln.warp == 0) {
+    const int idx = (p * 2 + ln.q) * kMaxTaps + ln.tap;
+    __stcg(&dst[idx], own);
+    if (trace) {
+      trace[2 * idx] = own.x;
+      trace[2 * idx + 1] = own.y;
+    }
   }
-  if (threadIdx.x == 0) {
+}
+
+__device__ __forceinline__ float *trace_slot(const EqLaunch &L, int64_t idx) {
+  return (idx >= 0 && idx < L.trace_cap) ? L.trace + idx * 4 * kMaxTaps * 2 : nullptr;
+}
+
+__device__ __forceinline__ void trace_fo(const EqLaunch &L, int64_t idx, double dw, double Phi) {
+  if (idx >= 0 && idx < L.trace_cap) {
     L.trace_fo[idx * 2] = dw;
     L.trace_fo[idx * 2 + 1] = Phi;
   }
@@ -303,30 +386,67 @@ __device__ void write_trace(const EqLaunch &L, int64_t idx, const float2 *taps, 
 template <int MB>
 __global__ void __launch_bounds__(kEqThreads, 1) eq_kernel(EqLaunch L) {
   __shared__ EqSmem sm;
-  const int lane = threadIdx.x & 31;
-  // lane's BPS test angle: exp(-j phi_b), phi_b = (b/32 - 1/2) pi/2
-  float sb, cb;
-  sincospif(((float)lane / 32.f - 0.5f) * 0.5f, &sb, &cb);
-  const float2 rot_b = make_float2(cb, -sb);
+  Lane ln;
+  ln.warp = threadIdx.x >> 5;
+  ln.lane = threadIdx.x & 31;
+  ln.j = ln.lane >> 2;
+  ln.part = ln.lane & 3;
+  ln.q = ln.part >> 1;
+  ln.half = ln.part & 1;
+  ln.tap = ln.half * 8 + ln.j;
+#pragma unroll
+  for (int a = 0; a < 8; ++a) {
+    // phi_b = (b/32 - 1/2) pi/2 for b = 8 part + a
+    float sb, cb;
+    sincospif(((float)(ln.part * 8 + a) / 32.f - 0.5f) * 0.5f, &sb, &cb);
+    ln.rot[a] = make_float2(cb, -sb);
+  }
+  {
+    float sb, cb;
+    sincospif(((float)ln.lane / 32.f - 0.5f) * 0.5f, &sb, &cb);
+    ln.rot_b = make_float2(cb, -sb);
+  }
+  const int p = blockIdx.x & 1;              // butterfly row of this CTA
+  const int slot = blockIdx.x >> 1;          // segment slot
+  const int nslots = L.nblocks >> 1;
   const int64_t n_limit = L.K >= 0 ? 2 * L.K : (int64_t)1 << 62;
-  unsigned epoch = 0;
-  double2 fo_acc;
+  Hot hot;
+  hot.yrow = L.y + (int64_t)p * L.y_stride - L.y_base;
+  hot.u0 = L.u - L.u_base;
+  hot.u1 = L.u + L.u_stride - L.u_base;
+  hot.T = L.T;
+  hot.c = (L.T - 1) / 2;
+  hot.Bu = L.Bu;
+  hot.mu_cma = L.mu_cma;
+  hot.mu_dd = L.mu_dd;
+  hot.cma_r2 = L.cma_r2;
+  unsigned epoch = 0, epoch2 = 0;
+  float2 own, h[8];
+  Kahan fo;
+  const double two_pi = 6.283185307179586477, inv_two_pi = 0.15915494309189533577;
+  if (threadIdx.x == 0) {
+    sm.ybuf[0][31] = sm.ybuf[1][31] = make_float2(0.f, 0.f);
+  }
 
   if (L.run_acq) {
-    if (blockIdx.x == 0) {
-      taps_from_global(sm, &L.st->taps[0][0][0]);
-      if (threadIdx.x == 0) sm.ylast[0] = sm.ylast[1] = make_float2(0.f, 0.f);
-      __syncthreads();
-      // CMA part, no rotation
+    if (blockIdx.x < 2) {
+      load_row(own, h, &L.st->taps[0][0][0], p, ln);
       Span sp;
       sp.kp = 0; sp.ks = 0; sp.ke = L.n_cma;
       sp.fo_lo = L.n_cma / 2; sp.fo_hi = L.n_cma;
       sp.cma = 1;
       sp.rot.on = 0; sp.rot.Phi_q = 0; sp.rot.delta_q = 0; sp.rot.n0 = 0;
-      fo_acc = make_double2(0.0, 0.0);
-      run_span<MB>(L, sm, sp, fo_acc, rot_b, n_limit);
-      const double2 s = reduce_fo(sm, fo_acc);
-      const double dw = L.fo_track ? 0.25 * atan2(s.y, s.x) : 0.0;
+      fo = Kahan{0.f, 0.f, 0.f, 0.f};
+      run_span<MB>(hot, sm, sp, ln, own, h, fo, n_limit);
+      const double2 s = reduce_fo(sm, fo, ln);
+      if (threadIdx.x == 0) {
+        __stcg(&L.fo_part[p].x, s.x);
+        __stcg(&L.fo_part[p].y, s.y);
+      }
+      if (!cta_barrier(L.err, L.barrier + 1, 2u, epoch2, sm)) return;
+      const double ax = __ldcg(&L.fo_part[0].x) + __ldcg(&L.fo_part[1].x);
+      const double ay = __ldcg(&L.fo_part[0].y) + __ldcg(&L.fo_part[1].y);
+      const double dw = L.fo_track ? 0.25 * atan2(ay, ax) : 0.0;
       const double delta = dw / 2.0;
       if (L.A > L.n_cma) {
         Span sd;
@@ -335,40 +455,49 @@ __global__ void __launch_bounds__(kEqThreads, 1) eq_kernel(EqLaunch L) {
         sd.cma = 0;
         sd.rot.on = L.fo_track;
         sd.rot.Phi_q = 0; sd.rot.delta_q = to_q64_turns(delta); sd.rot.n0 = 2 * L.n_cma;
-        run_span<MB>(L, sm, sd, fo_acc, rot_b, n_limit);
+        run_span<MB>(hot, sm, sd, ln, own, h, fo, n_limit);
       }
-      const double Phi = remainder(__dmul_rn((double)(2 * L.A - 2 * L.n_cma), delta), 6.283185307179586477);
-      __syncthreads();
-      for (int j = threadIdx.x; j < 2 * 2 * kMaxTaps; j += blockDim.x)
-        __stcg(&(&L.st->taps[0][0][0])[j], (&sm.taps[0][0][0])[j]);
-      if (threadIdx.x == 0) {
+      // end of acquisition = trace entries 0 (acquisition) and 1 (start of wave 0)
+      store_row(own, &L.st->taps[0][0][0], trace_slot(L, 0), p, ln);
+      float *t1 = trace_slot(L, 1);
+      if (t1 && ln.warp == 0) {
+        const int idx = (p * 2 + ln.q) * kMaxTaps + ln.tap;
+        t1[2 * idx] = own.x;
+        t1[2 * idx + 1] = own.y;
+      }
+      if (blockIdx.x == 0 && threadIdx.x == 0) {
+        const double Phi = remainder(__dmul_rn((double)(2 * L.A - 2 * L.n_cma), delta), two_pi);
         L.st->dw = dw;
         L.st->Phi = Phi;
         L.st->acq_done = 1;
         L.st->next_wave = 0;
+        trace_fo(L, 0, dw, Phi);
+        trace_fo(L, 1, dw, Phi);
       }
-      write_trace(L, 0, &sm.taps[0][0][0], dw, Phi);
     }
-    if (!grid_barrier(L, epoch, sm)) return;
+    if (!cta_barrier(L.err, L.barrier, (unsigned)L.nblocks, epoch, sm)) return;
   }
 
   if (L.wave_last <= L.wave_first) return;
-  double dw = __ldcg(&L.st->dw), Phi = __ldcg(&L.st->Phi);
+  if (ln.warp == 0 && ln.lane == 0) {
+    const double dw0 = __ldcg(&L.st->dw), Phi0 = __ldcg(&L.st->Phi);
+    sm.trk[0] = dw0;
+    sm.trk[1] = Phi0;
+    sm.rotq[0] = to_q64_turns(Phi0);
+    sm.rotq[1] = to_q64_turns(dw0 / 2.0);
+  }
+  __syncthreads();
   for (int64_t w = L.wave_first; w < L.wave_last; ++w) {
     const float2 *start = (w == L.wave_first) ? &L.st->taps[0][0][0] : L.tap_slot + ((w - 1) & 1) * 4 * kMaxTaps;
-    const double delta = dw / 2.0;
     const int64_t g0 = w * L.P;
     const int64_t g_end = min(g0 + (int64_t)L.P, L.n_segments);
-    const int64_t n_w = 2 * (L.A + g0 * L.S);
     Rot rot;
     rot.on = L.fo_track;
-    rot.Phi_q = to_q64_turns(Phi);
-    rot.delta_q = to_q64_turns(delta);
-    rot.n0 = n_w;
-    for (int64_t g = g0 + blockIdx.x; g < g_end; g += L.nblocks) {
-      __syncthreads();
-      taps_from_global(sm, start);
-      if (threadIdx.x == 0) sm.ylast[0] = sm.ylast[1] = make_float2(0.f, 0.f);
+    rot.Phi_q = sm.rotq[0];
+    rot.delta_q = sm.rotq[1];
+    rot.n0 = 2 * (L.A + g0 * L.S);
+    for (int64_t g = g0 + slot; g < g_end; g += nslots) {
+      load_row(own, h, start, p, ln);
       Span sp;
       sp.ks = L.A + g * L.S;
       sp.ke = L.K >= 0 ? min(sp.ks + (int64_t)L.S, L.K) : sp.ks + L.S;
@@ -376,55 +505,63 @@ __global__ void __launch_bounds__(kEqThreads, 1) eq_kernel(EqLaunch L) {
       sp.fo_lo = sp.ks; sp.fo_hi = sp.ke;
       sp.cma = 0;
       sp.rot = rot;
-      fo_acc = make_double2(0.0, 0.0);
-      run_span<MB>(L, sm, sp, fo_acc, rot_b, n_limit);
-      const double2 s = reduce_fo(sm, fo_acc);
+      fo = Kahan{0.f, 0.f, 0.f, 0.f};
+      run_span<MB>(hot, sm, sp, ln, own, h, fo, n_limit);
+      const double2 s = reduce_fo(sm, fo, ln);
       if (threadIdx.x == 0) {
-        double2 *slot = L.fo_part + (w & 1) * L.P + (g - g0);
-        __stcg(&slot->x, s.x);
-        __stcg(&slot->y, s.y);
+        double2 *dst = L.fo_part + (w & 1) * 2 * L.P + (g - g0) * 2 + p;
+        __stcg(&dst->x, s.x);
+        __stcg(&dst->y, s.y);
       }
-      if (g == g_end - 1) {
-        float2 *dst = L.tap_slot + (w & 1) * 4 * kMaxTaps;
-        for (int j = threadIdx.x; j < 4 * kMaxTaps; j += blockDim.x) __stcg(&dst[j], (&sm.taps[0][0][0])[j]);
+      // the last segment's end taps start wave w + 1 (trace entry w + 2)
+      if (g == g_end - 1) store_row(own, L.tap_slot + (w & 1) * 4 * kMaxTaps, trace_slot(L, w + 2), p, ln);
+    }
+    if (!cta_barrier(L.err, L.barrier, (unsigned)L.nblocks, epoch, sm)) return;
+    // one warp folds the wave's partials (fixed tree, identical in every CTA)
+    if (ln.warp == 0) {
+      const double2 *src = L.fo_part + (w & 1) * 2 * L.P;
+      const int n = (int)(2 * (g_end - g0));
+      double2 v = make_double2(0.0, 0.0);
+      for (int jj = ln.lane; jj < n; jj += 32) {
+        v.x += __ldcg(&src[jj].x);
+        v.y += __ldcg(&src[jj].y);
+      }
+      for (int o = 16; o >= 1; o >>= 1) {
+        v.x += __shfl_xor_sync(FULL, v.x, o);
+        v.y += __shfl_xor_sync(FULL, v.y, o);
+      }
+      if (ln.lane == 0) {
+        const double dw = sm.trk[0], Phi = sm.trk[1];
+        const double r = L.fo_track ? 0.25 * atan2(v.y, v.x) : 0.0;
+        double Pn = __dadd_rn(Phi, __dmul_rn((double)(2 * (int64_t)L.P * L.S), dw / 2.0));
+        Pn = fma(-two_pi, rint(Pn * inv_two_pi), Pn);
+        const double dn = __dadd_rn(dw, r / L.fo_smooth);
+        sm.trk[0] = dn;
+        sm.trk[1] = Pn;
+        sm.rotq[0] = to_q64_turns(Pn);
+        sm.rotq[1] = to_q64_turns(dn / 2.0);
+        if (blockIdx.x == 0) trace_fo(L, w + 2, dn, Pn);
       }
     }
-    if (!grid_barrier(L, epoch, sm)) return;
-    // every CTA folds the wave's partials identically
-    double ax = 0.0, ay = 0.0;
-    for (int64_t j = 0; j < g_end - g0; ++j) {
-      const double2 *slot = L.fo_part + (w & 1) * L.P + j;
-      ax += __ldcg(&slot->x);
-      ay += __ldcg(&slot->y);
-    }
-    const double r = L.fo_track ? 0.25 * atan2(ay, ax) : 0.0;
-    if (blockIdx.x == 0) {
-      __syncthreads();
-      taps_from_global(sm, start);
-      __syncthreads();
-      write_trace(L, w + 1, &sm.taps[0][0][0], dw, Phi);
-    }
-    Phi = remainder(__dadd_rn(Phi, __dmul_rn((double)(2 * (int64_t)L.P * L.S), delta)), 6.283185307179586477);
-    dw = __dadd_rn(dw, r / L.fo_smooth);
+    __syncthreads();
   }
   if (blockIdx.x == 0) {
     const float2 *last = L.tap_slot + ((L.wave_last - 1) & 1) * 4 * kMaxTaps;
-    for (int j = threadIdx.x; j < 4 * kMaxTaps; j += blockDim.x)
-      __stcg(&(&L.st->taps[0][0][0])[j], __ldcg(&last[j]));
+    for (int jj = threadIdx.x; jj < 4 * kMaxTaps; jj += blockDim.x)
+      __stcg(&(&L.st->taps[0][0][0])[jj], __ldcg(&last[jj]));
     if (threadIdx.x == 0) {
-      L.st->dw = dw;
-      L.st->Phi = Phi;
+      L.st->dw = sm.trk[0];
+      L.st->Phi = sm.trk[1];
       L.st->next_wave = L.wave_last;
     }
   }
 }
 
 int eq_max_blocks() {
-  int dev = 0, sms = 0, per = 0;
+  int dev = 0, sms = 0, per = 0, per4 = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, eq_kernel<2>, kEqThreads, 0);
-  int per4 = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per4, eq_kernel<4>, kEqThreads, 0);
   return sms * min(per, per4);
 }

@@ -457,11 +457,11 @@ rx_status rx_reserve(rx_stream *rx, int64_t max_call) {
     RX_ALLOC(rx->bh[i], (size_t)2 * rx->y_cap);
   }
   RX_ALLOC(rx->st, 1);
-  RX_ALLOC(rx->fo_part, (size_t)2 * rx->P);
+  RX_ALLOC(rx->fo_part, (size_t)4 * rx->P);
   RX_ALLOC(rx->tap_slot, (size_t)2 * 4 * kMaxTaps);
   RX_ALLOC(rx->trace, (size_t)rx->trace_cap * 4 * kMaxTaps * 2);
   RX_ALLOC(rx->trace_fo, (size_t)rx->trace_cap * 2);
-  RX_ALLOC(rx->barrier, 1);
+  RX_ALLOC(rx->barrier, 2);
   RX_ALLOC(rx->err, 1);
   RX_ALLOC(rx->chunk_r, (size_t)2 * rx->chunk_cap);
   RX_ALLOC(rx->chunk_s2, (size_t)2 * rx->chunk_cap);
@@ -479,8 +479,8 @@ rx_status rx_reserve(rx_stream *rx, int64_t max_call) {
   if (e != cudaSuccess) { release(rx); return cuda_fail(rx, e, "event"); }
   e = launch_tables(rx->H, rx->tw, rx->N, rx->baud, rx->L_km, rx->D, rx->lam_nm, rx->rolloff, rx->stream);
   if (e != cudaSuccess) { release(rx); return cuda_fail(rx, e, "filter tables"); }
-  rx->eq_blocks = std::min(rx->P, eq_max_blocks());
-  if (rx->eq_blocks < 1) { release(rx); return fail(rx, RX_ECUDA, "equaliser kernel cannot be resident"); }
+  rx->eq_blocks = 2 * std::min(rx->P, eq_max_blocks() / 2);
+  if (rx->eq_blocks < 2) { release(rx); return fail(rx, RX_ECUDA, "equaliser kernel cannot be resident"); }
   rx->reserved = true;
   reset_host_state(rx);
   s = init_device_state(rx);
@@ -695,7 +695,7 @@ rx_status rx_process(rx_stream *rx, const rx_in *in, rx_out *out) {
       L.fo_smooth = rx->fo_smooth;
       L.fo_track = rx->fo_track;
       L.nblocks = rx->eq_blocks;
-      RX_CUDA(cudaMemsetAsync(rx->barrier, 0, sizeof(unsigned), st), "barrier reset");
+      RX_CUDA(cudaMemsetAsync(rx->barrier, 0, 2 * sizeof(unsigned), st), "barrier reset");
       {
         StageTimer tm(rx, RX_STAGE_EQ);
         rx->stage_launches[RX_STAGE_EQ] += 1;

@@ -11,7 +11,7 @@ namespace rx {
 
 constexpr int kMaxTaps = 16;      // butterfly taps T <= 15 (odd), padded to 16
 constexpr int kAngles = 32;       // BPS test angles (one per lane)
-constexpr int kEqThreads = 256;   // equaliser CTA
+constexpr int kEqThreads = 128;   // equaliser CTA: 4 warps, one butterfly row
 constexpr int kChunkSym = 1152;   // equaliser span chunk (symbols) held in smem
 constexpr int kBpsChunk = 256;    // BPS pass-1 symbols per warp
 
@@ -32,12 +32,12 @@ struct EqLaunch {
   float2 *y;                // equaliser out [2][y_stride], symbol k at y[k - y_base]
   int64_t y_base, y_stride;
   EqState *st;
-  double2 *fo_part;         // [2][max_wave_segments] FO partial sums (double buffered)
+  double2 *fo_part;         // [2][2 * P] FO partial sums per (segment, row), double buffered
   float2 *tap_slot;         // [2][2*2*kMaxTaps] last-segment taps (double buffered)
   float *trace;             // [trace_cap][2*2*kMaxTaps*2] wave start taps
   double *trace_fo;         // [trace_cap][2] (dw, Phi)
   int64_t trace_cap;
-  unsigned *barrier;        // grid barrier counter (zeroed before launch)
+  unsigned *barrier;        // [0] grid barrier, [1] acquisition row pair (zeroed before launch)
   int *err;                 // sticky error word
   int64_t K;                // symbols of the whole stream if known (flushed), else -1
   int run_acq;              // 1: run the acquisition in this launch
@@ -50,7 +50,7 @@ struct EqLaunch {
   float mu_cma, mu_dd, cma_r2;
   double fo_smooth;
   int fo_track;
-  int nblocks;              // CTAs in the grid
+  int nblocks;              // CTAs in the grid (even: 2 rows per segment slot)
 };
 
 // Per-stream BPS/demap launch description.
