@@ -34,57 +34,77 @@ __device__ __forceinline__ int unwrap_step(int prev, int cur) {
 __device__ __forceinline__ int64_t chunk_lo(const BpsLaunch &L, int64_t j) { return L.k_lo + j * L.chunk; }
 }  // namespace
 
+// Per-warp shared memory of pass 1: the d ring (M x 32 floats), the staged
+// equaliser outputs of the chunk with its +-Nb halo, and the chunk's angle bytes.
+__host__ __device__ inline int pass1_ys_cap(int chunk, int Nb) { return chunk + 2 * Nb + 2; }
+__host__ __device__ inline size_t pass1_warp_bytes(int chunk, int Nb) {
+  return (size_t)(2 * Nb + 1) * 32 * sizeof(float) + (size_t)pass1_ys_cap(chunk, Nb) * sizeof(float2) +
+         (size_t)((chunk + 15) / 16) * 16;
+}
+
 template <int MB>
 __global__ void __launch_bounds__(kBpsWarps * 32) bps_pass1(BpsLaunch L) {
-  extern __shared__ float ring_all[];
+  extern __shared__ float4 smem_raw[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t j = (int64_t)blockIdx.x * kBpsWarps + warp;
   const int p = blockIdx.y;
   if (j >= L.n_chunks) return;
-  const int M = 2 * L.Nb + 1;
-  float *ring = ring_all + (size_t)warp * M * 32;
+  const int Nb = L.Nb, M = 2 * Nb + 1;
+  char *base = reinterpret_cast<char *>(smem_raw) + (size_t)warp * pass1_warp_bytes(L.chunk, Nb);
+  float *ring = reinterpret_cast<float *>(base);
+  float2 *ys = reinterpret_cast<float2 *>(base + (size_t)M * 32 * sizeof(float));
+  int8_t *bq = reinterpret_cast<int8_t *>(ys + pass1_ys_cap(L.chunk, Nb));
   const int64_t a = chunk_lo(L, j), b = min(a + (int64_t)L.chunk, L.k_hi);
+  const int64_t start = a > 0 ? a - 1 : a;
+  const int64_t lo = start - Nb;                 // ys[i] holds symbol lo + i
+  const int n_ys = (int)(b - 1 + Nb - lo + 1);
   float sb, cb;
   sincospif(((float)lane / 32.f - 0.5f) * 0.5f, &sb, &cb);
-  const float2 rot = make_float2(cb, -sb);
+  const float2 rot = make_float2(cb, -sb);      // this lane's test angle exp(-j phi_b)
   const float2 *y = L.y + (int64_t)p * L.y_stride - L.y_base;
-  auto dist = [&](int64_t k) -> float {
-    if (k < 0 || k >= L.K_end) return 0.f;
-    return qam_dist<MB>(cmul(y[k], rot));
-  };
-  auto slot = [&](int64_t k) -> int { return (int)((k + M) % M); };
-  const int64_t start = a > 0 ? a - 1 : a;
-  float D = 0.f;
-  for (int64_t k = start - L.Nb; k <= start + L.Nb; ++k) {
-    const float d = dist(k);
-    ring[slot(k) * 32 + lane] = d;
+  for (int i = lane; i < n_ys; i += 32) {       // coalesced staging
+    const int64_t k = lo + i;
+    ys[i] = (k >= 0 && k < L.K_end) ? y[k] : make_float2(0.f, 0.f);
   }
+  __syncwarp();
+  const int64_t v_lo = -lo, v_hi = L.K_end - lo;  // valid staged indices [v_lo, v_hi)
+  auto dist = [&](int i) -> float {
+    return (i >= v_lo && i < v_hi) ? qam_dist<MB>(cmul(ys[i], rot)) : 0.f;
+  };
+  for (int i = 0; i < M; ++i) ring[i * 32 + lane] = dist(i);   // window of symbol `start`
+  int s_out = 0;                                 // slot of the oldest symbol in the window
+  float D = 0.f;
   int prev = 0, R = 0;
   float s2 = 0.f;
-  int8_t *bh = L.bhat + (int64_t)p * L.bh_stride - L.bh_base;
-  for (int64_t k = start; k < b; ++k) {
-    if (k > start) {
-      const float dn = dist(k + L.Nb);
-      const int so = slot(k - L.Nb - 1);  // leaving value occupies the entering slot
-      D += dn - ring[so * 32 + lane];
-      ring[so * 32 + lane] = dn;
+  const int nt = (int)(b - start);
+  for (int t = 0; t < nt; ++t) {                 // symbol k = start + t
+    if (t > 0) {
+      const float dn = dist(t + 2 * Nb);         // entering symbol k + Nb
+      D += dn - ring[s_out * 32 + lane];         // leaving symbol k - Nb - 1
+      ring[s_out * 32 + lane] = dn;
+      s_out = (s_out + 1 == M) ? 0 : s_out + 1;
     }
-    if (((k - start) & 31) == 0) {  // exact re-sum bounds the sliding drift
-      float t = 0.f;
-      for (int m = -L.Nb; m <= L.Nb; ++m) t += ring[slot(k + m) * 32 + lane];
-      D = t;
+    if ((t & 31) == 0) {                         // exact re-sum bounds the sliding drift
+      float e = 0.f;
+      for (int s = 0; s < M; ++s) e += ring[s * 32 + lane];
+      D = e;
     }
     const unsigned key = __float_as_uint(fmaxf(D, 0.f));
     const unsigned mn = __reduce_min_sync(0xffffffffu, key);
     const int bs = __ffs(__ballot_sync(0xffffffffu, key == mn)) - 1;
+    const int64_t k = start + t;
     if (k >= a) {
       if (k > 0) R += unwrap_step(prev, bs);
-      const float dk = __shfl_sync(0xffffffffu, ring[slot(k) * 32 + lane], bs);
-      s2 += dk;
-      if (lane == 0) bh[k] = (int8_t)bs;
+      int sk = s_out + Nb;                       // slot of symbol k
+      if (sk >= M) sk -= M;
+      s2 += __shfl_sync(0xffffffffu, ring[sk * 32 + lane], bs);
+      if (lane == 0) bq[k - a] = (int8_t)bs;
     }
     prev = bs;
   }
+  __syncwarp();
+  int8_t *bh = L.bhat + (int64_t)p * L.bh_stride - L.bh_base;
+  for (int i = lane; i < (int)(b - a); i += 32) bh[a + i] = bq[i];
   if (lane == 0) {
     L.chunk_r[(int64_t)p * L.n_chunks + j] = R;
     L.chunk_s2[(int64_t)p * L.n_chunks + j] = s2;
@@ -224,7 +244,7 @@ __global__ void __launch_bounds__(kBpsWarps * 32) bps_demap(BpsLaunch L) {
 cudaError_t launch_bps(const BpsLaunch &L, cudaStream_t s) {
   if (L.n_chunks <= 0) return cudaSuccess;
   dim3 grid((unsigned)((L.n_chunks + kBpsWarps - 1) / kBpsWarps), 2);
-  const size_t sm = (size_t)kBpsWarps * (2 * L.Nb + 1) * 32 * sizeof(float);
+  const size_t sm = (size_t)kBpsWarps * pass1_warp_bytes(L.chunk, L.Nb);
   cudaError_t e;
   if (L.mod_bits == 4) {
     e = cudaFuncSetAttribute(bps_pass1<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
