@@ -63,11 +63,40 @@ struct EqSmem {
   float2 ybuf[2][32];                    // double-buffered by step parity
   float bps[kWarps][32];
   float2 grad[2][kWarps][2][kMaxTaps];   // double-buffered by step parity
-  double2 fo_warp[kWarps];
-  double trk[2];                         // (dw, Phi) handed from warp 0 to the CTA
-  unsigned long long rotq[2];            // (Phi_q, delta_q) of the next wave
+  float4 fo_warp[kWarps];                // per-warp double-float pair sums
+  float2 rtab[256];                      // exp(-j 2 pi m / 256)
+  unsigned long long phq;                // tracker: phase base, Q0.64 turns
+  long long dq;                          // tracker: per-sample increment, Q0.64 turns
   int fail;
 };
+
+// Double-float (hi + lo) arithmetic for the frequency sums: Knuth's two-sum
+// keeps ~44 bits in FP32 operations (FP64 issues slowly on this part).
+struct df {
+  float hi, lo;
+};
+__device__ __forceinline__ df df_add(df a, df b) {
+  const float s = a.hi + b.hi;
+  const float bb = s - a.hi;
+  float e = (a.hi - (s - bb)) + (b.hi - bb);
+  e += a.lo + b.lo;
+  const float hi = s + e;
+  return df{hi, e - (hi - s)};
+}
+__device__ __forceinline__ float4 df4_add(float4 a, float4 b) {
+  const df x = df_add(df{a.x, a.y}, df{b.x, b.y});
+  const df y = df_add(df{a.z, a.w}, df{b.z, b.w});
+  return make_float4(x.hi, x.lo, y.hi, y.lo);
+}
+__device__ __forceinline__ float4 shfl_xor_f4(float4 v, int o) {
+  return make_float4(__shfl_xor_sync(FULL, v.x, o), __shfl_xor_sync(FULL, v.y, o),
+                     __shfl_xor_sync(FULL, v.z, o), __shfl_xor_sync(FULL, v.w, o));
+}
+
+// Q0.64 turns -> radians in [-pi, pi)
+__device__ __forceinline__ double q64_to_rad(unsigned long long q) {
+  return (double)(long long)q * 3.4061215800865545e-19;  // 2 pi / 2^64
+}
 
 __device__ __forceinline__ unsigned long long to_q64_turns(double rad) {
   // radians -> fraction of a turn in [-1/2, 1/2) as a two's-complement Q0.64
@@ -137,11 +166,14 @@ __device__ __forceinline__ void load_window(const float2 *__restrict__ u0, const
     const int64_t n = win_lo + j;
     float2 a = va[r], b = vb[r];
     if (rot.on && n >= 0 && n < n_limit) {
-      const unsigned long long ph = rot.Phi_q + (unsigned long long)(n - rot.n0) * rot.delta_q;
-      const float x = (float)(int)(ph >> 32) * 4.656612873077392578125e-10f;  // turns * 2
-      float s, c;
-      sincospif(x, &s, &c);
-      const float2 r2 = make_float2(c, -s);  // exp(-j phi)
+      // exp(-j phi): top 8 bits of the turn from the table, the rest
+      // (theta < 2 pi / 256) by its Taylor series (error < 1e-12)
+      const unsigned ph = (unsigned)((rot.Phi_q + (unsigned long long)(n - rot.n0) * rot.delta_q) >> 32);
+      const float th = (float)(ph & 0xFFFFFFu) * 1.4629180792671596e-09f;  // 2 pi / 2^32
+      const float t2 = th * th;
+      const float cs = fmaf(t2, fmaf(t2, 1.f / 24.f, -0.5f), 1.f);
+      const float sn = th * fmaf(t2, fmaf(t2, 1.f / 120.f, -1.f / 6.f), 1.f);
+      const float2 r2 = cmul(sm.rtab[ph >> 24], make_float2(cs, -sn));
       a = cmul(a, r2);
       b = cmul(b, r2);
     }
@@ -336,20 +368,17 @@ __device__ __forceinline__ void run_span(const Hot hot, EqSmem &sm, const Span s
   }
 }
 
-// Segment total of the per-lane compensated pair sums, in FP64 and a fixed order.
-__device__ __forceinline__ double2 reduce_fo(EqSmem &sm, const Kahan &fo, const Lane &ln) {
-  double2 acc = make_double2((double)fo.sx - (double)fo.cx, (double)fo.sy - (double)fo.cy);
-  for (int o = 16; o >= 4; o >>= 1) {
-    acc.x += __shfl_xor_sync(FULL, acc.x, o);
-    acc.y += __shfl_xor_sync(FULL, acc.y, o);
-  }
+// Segment total of the per-lane compensated pair sums as double-float
+// (x_hi, x_lo, y_hi, y_lo), in a fixed order.
+__device__ __forceinline__ float4 reduce_fo(EqSmem &sm, const Kahan &fo, const Lane &ln) {
+  // Kahan (s, c) holds s - c; renormalise into (hi, lo)
+  const float hx = fo.sx - fo.cx, hy = fo.sy - fo.cy;
+  float4 acc = make_float4(hx, (fo.sx - hx) - fo.cx, hy, (fo.sy - hy) - fo.cy);
+  for (int o = 16; o >= 4; o >>= 1) acc = df4_add(acc, shfl_xor_f4(acc, o));
   __syncthreads();
   if (ln.lane == 0) sm.fo_warp[ln.warp] = acc;
   __syncthreads();
-  double2 s;
-  s.x = (sm.fo_warp[0].x + sm.fo_warp[1].x) + (sm.fo_warp[2].x + sm.fo_warp[3].x);
-  s.y = (sm.fo_warp[0].y + sm.fo_warp[1].y) + (sm.fo_warp[2].y + sm.fo_warp[3].y);
-  return s;
+  return df4_add(df4_add(sm.fo_warp[0], sm.fo_warp[1]), df4_add(sm.fo_warp[2], sm.fo_warp[3]));
 }
 
 // This lane's own tap of row p from a [2][2][kMaxTaps] array, then the FIR gather.
@@ -423,10 +452,15 @@ __global__ void __launch_bounds__(kEqThreads, 1) eq_kernel(EqLaunch L) {
   unsigned epoch = 0, epoch2 = 0;
   float2 own, h[8];
   Kahan fo;
-  const double two_pi = 6.283185307179586477, inv_two_pi = 0.15915494309189533577;
   if (threadIdx.x == 0) {
     sm.ybuf[0][31] = sm.ybuf[1][31] = make_float2(0.f, 0.f);
   }
+  for (int m = threadIdx.x; m < 256; m += kEqThreads) {
+    float s, c;
+    sincospif((float)m / 128.f, &s, &c);
+    sm.rtab[m] = make_float2(c, -s);
+  }
+  __syncthreads();
 
   if (L.run_acq) {
     if (blockIdx.x < 2) {
@@ -438,15 +472,12 @@ __global__ void __launch_bounds__(kEqThreads, 1) eq_kernel(EqLaunch L) {
       sp.rot.on = 0; sp.rot.Phi_q = 0; sp.rot.delta_q = 0; sp.rot.n0 = 0;
       fo = Kahan{0.f, 0.f, 0.f, 0.f};
       run_span<MB>(hot, sm, sp, ln, own, h, fo, n_limit);
-      const double2 s = reduce_fo(sm, fo, ln);
-      if (threadIdx.x == 0) {
-        __stcg(&L.fo_part[p].x, s.x);
-        __stcg(&L.fo_part[p].y, s.y);
-      }
+      const float4 s = reduce_fo(sm, fo, ln);
+      if (threadIdx.x == 0) __stcg(&L.fo_part[p], s);
       if (!cta_barrier(L.err, L.barrier + 1, 2u, epoch2, sm)) return;
-      const double ax = __ldcg(&L.fo_part[0].x) + __ldcg(&L.fo_part[1].x);
-      const double ay = __ldcg(&L.fo_part[0].y) + __ldcg(&L.fo_part[1].y);
-      const double dw = L.fo_track ? 0.25 * atan2(ay, ax) : 0.0;
+      const float4 s01 = df4_add(__ldcg(&L.fo_part[0]), __ldcg(&L.fo_part[1]));
+      const double ax = (double)s01.x + (double)s01.y, ay = (double)s01.z + (double)s01.w;
+      const double dw = L.fo_track ? 0.25 * atan2(ay, ax) : 0.0;   // once per stream
       const double delta = dw / 2.0;
       if (L.A > L.n_cma) {
         Span sd;
@@ -466,9 +497,14 @@ __global__ void __launch_bounds__(kEqThreads, 1) eq_kernel(EqLaunch L) {
         t1[2 * idx + 1] = own.y;
       }
       if (blockIdx.x == 0 && threadIdx.x == 0) {
-        const double Phi = remainder(__dmul_rn((double)(2 * L.A - 2 * L.n_cma), delta), two_pi);
+        // tracker as a 64-bit fixed-point NCO: exact modular phase arithmetic
+        const long long dq = (long long)to_q64_turns(delta);
+        const unsigned long long phq = (unsigned long long)(2 * L.A - 2 * L.n_cma) * (unsigned long long)dq;
+        const double Phi = q64_to_rad(phq);
         L.st->dw = dw;
         L.st->Phi = Phi;
+        L.st->delta_q = dq;
+        L.st->Phi_q = phq;
         L.st->acq_done = 1;
         L.st->next_wave = 0;
         trace_fo(L, 0, dw, Phi);
@@ -479,12 +515,9 @@ __global__ void __launch_bounds__(kEqThreads, 1) eq_kernel(EqLaunch L) {
   }
 
   if (L.wave_last <= L.wave_first) return;
-  if (ln.warp == 0 && ln.lane == 0) {
-    const double dw0 = __ldcg(&L.st->dw), Phi0 = __ldcg(&L.st->Phi);
-    sm.trk[0] = dw0;
-    sm.trk[1] = Phi0;
-    sm.rotq[0] = to_q64_turns(Phi0);
-    sm.rotq[1] = to_q64_turns(dw0 / 2.0);
+  if (threadIdx.x == 0) {
+    sm.phq = __ldcg(&L.st->Phi_q);
+    sm.dq = __ldcg(&L.st->delta_q);
   }
   __syncthreads();
   for (int64_t w = L.wave_first; w < L.wave_last; ++w) {
@@ -493,8 +526,8 @@ __global__ void __launch_bounds__(kEqThreads, 1) eq_kernel(EqLaunch L) {
     const int64_t g_end = min(g0 + (int64_t)L.P, L.n_segments);
     Rot rot;
     rot.on = L.fo_track;
-    rot.Phi_q = sm.rotq[0];
-    rot.delta_q = sm.rotq[1];
+    rot.Phi_q = sm.phq;
+    rot.delta_q = (unsigned long long)sm.dq;
     rot.n0 = 2 * (L.A + g0 * L.S);
     for (int64_t g = g0 + slot; g < g_end; g += nslots) {
       load_row(own, h, start, p, ln);
@@ -507,40 +540,26 @@ __global__ void __launch_bounds__(kEqThreads, 1) eq_kernel(EqLaunch L) {
       sp.rot = rot;
       fo = Kahan{0.f, 0.f, 0.f, 0.f};
       run_span<MB>(hot, sm, sp, ln, own, h, fo, n_limit);
-      const double2 s = reduce_fo(sm, fo, ln);
-      if (threadIdx.x == 0) {
-        double2 *dst = L.fo_part + (w & 1) * 2 * L.P + (g - g0) * 2 + p;
-        __stcg(&dst->x, s.x);
-        __stcg(&dst->y, s.y);
-      }
+      const float4 s = reduce_fo(sm, fo, ln);
+      if (threadIdx.x == 0) __stcg(L.fo_part + (w & 1) * 2 * L.P + (g - g0) * 2 + p, s);
       // the last segment's end taps start wave w + 1 (trace entry w + 2)
       if (g == g_end - 1) store_row(own, L.tap_slot + (w & 1) * 4 * kMaxTaps, trace_slot(L, w + 2), p, ln);
     }
     if (!cta_barrier(L.err, L.barrier, (unsigned)L.nblocks, epoch, sm)) return;
     // one warp folds the wave's partials (fixed tree, identical in every CTA)
     if (ln.warp == 0) {
-      const double2 *src = L.fo_part + (w & 1) * 2 * L.P;
+      const float4 *src = L.fo_part + (w & 1) * 2 * L.P;
       const int n = (int)(2 * (g_end - g0));
-      double2 v = make_double2(0.0, 0.0);
-      for (int jj = ln.lane; jj < n; jj += 32) {
-        v.x += __ldcg(&src[jj].x);
-        v.y += __ldcg(&src[jj].y);
-      }
-      for (int o = 16; o >= 1; o >>= 1) {
-        v.x += __shfl_xor_sync(FULL, v.x, o);
-        v.y += __shfl_xor_sync(FULL, v.y, o);
-      }
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      for (int jj = ln.lane; jj < n; jj += 32) v = df4_add(v, __ldcg(&src[jj]));
+      for (int o = 16; o >= 1; o >>= 1) v = df4_add(v, shfl_xor_f4(v, o));
       if (ln.lane == 0) {
-        const double dw = sm.trk[0], Phi = sm.trk[1];
-        const double r = L.fo_track ? 0.25 * atan2(v.y, v.x) : 0.0;
-        double Pn = __dadd_rn(Phi, __dmul_rn((double)(2 * (int64_t)L.P * L.S), dw / 2.0));
-        Pn = fma(-two_pi, rint(Pn * inv_two_pi), Pn);
-        const double dn = __dadd_rn(dw, r / L.fo_smooth);
-        sm.trk[0] = dn;
-        sm.trk[1] = Pn;
-        sm.rotq[0] = to_q64_turns(Pn);
-        sm.rotq[1] = to_q64_turns(dn / 2.0);
-        if (blockIdx.x == 0) trace_fo(L, w + 2, dn, Pn);
+        // r = 1/4 arg(sum); Phi += 2PS (dw/2); dw += r/16 -- in Q0.64 turns
+        const float r = L.fo_track ? 0.25f * atan2f(v.z + v.w, v.x + v.y) : 0.f;
+        const long long dq = sm.dq;
+        sm.phq += (unsigned long long)(2 * (long long)L.P * L.S) * (unsigned long long)dq;
+        sm.dq = dq + __float2ll_rn(r * L.inc_scale);
+        if (blockIdx.x == 0) trace_fo(L, w + 2, (double)sm.dq * 6.8122431601731090e-19, q64_to_rad(sm.phq));
       }
     }
     __syncthreads();
@@ -550,19 +569,27 @@ __global__ void __launch_bounds__(kEqThreads, 1) eq_kernel(EqLaunch L) {
     for (int jj = threadIdx.x; jj < 4 * kMaxTaps; jj += blockDim.x)
       __stcg(&(&L.st->taps[0][0][0])[jj], __ldcg(&last[jj]));
     if (threadIdx.x == 0) {
-      L.st->dw = sm.trk[0];
-      L.st->Phi = sm.trk[1];
+      L.st->Phi_q = sm.phq;
+      L.st->delta_q = sm.dq;
+      L.st->dw = (double)sm.dq * 6.8122431601731090e-19;   // 4 pi / 2^64 rad per symbol
+      L.st->Phi = q64_to_rad(sm.phq);
       L.st->next_wave = L.wave_last;
     }
   }
 }
 
+// Unused dynamic shared memory that keeps one equaliser CTA per SM: the update
+// step is a latency chain, so a second CTA on the same SM only slows both.
+constexpr int kEqPadSmem = 96 * 1024;
+
 int eq_max_blocks() {
   int dev = 0, sms = 0, per = 0, per4 = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, eq_kernel<2>, kEqThreads, 0);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per4, eq_kernel<4>, kEqThreads, 0);
+  cudaFuncSetAttribute(eq_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kEqPadSmem);
+  cudaFuncSetAttribute(eq_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, kEqPadSmem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, eq_kernel<2>, kEqThreads, kEqPadSmem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per4, eq_kernel<4>, kEqThreads, kEqPadSmem);
   return sms * min(per, per4);
 }
 
@@ -570,7 +597,7 @@ cudaError_t launch_eq(const EqLaunch &L, cudaStream_t s) {
   EqLaunch a = L;
   void *args[] = {&a};
   const void *fn = L.mod_bits == 4 ? (const void *)eq_kernel<4> : (const void *)eq_kernel<2>;
-  return cudaLaunchCooperativeKernel(fn, dim3(L.nblocks), dim3(kEqThreads), args, 0, s);
+  return cudaLaunchCooperativeKernel(fn, dim3(L.nblocks), dim3(kEqThreads), args, kEqPadSmem, s);
 }
 
 }  // namespace rx

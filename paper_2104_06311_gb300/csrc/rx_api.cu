@@ -64,7 +64,7 @@ struct rx_stream {
   int8_t *bh[2] = {nullptr, nullptr};
   int64_t y_cap = 0;
   EqState *st = nullptr;
-  double2 *fo_part = nullptr;
+  float4 *fo_part = nullptr;
   float2 *tap_slot = nullptr;
   float *trace = nullptr;
   double *trace_fo = nullptr;
@@ -693,6 +693,7 @@ rx_status rx_process(rx_stream *rx, const rx_in *in, rx_out *out) {
       L.mu_dd = (float)rx->mu_dd;
       L.cma_r2 = rx->mod_bits == 4 ? 1.32f : 1.0f;
       L.fo_smooth = rx->fo_smooth;
+      L.inc_scale = (float)(18446744073709551616.0 / (4.0 * 3.14159265358979323846 * rx->fo_smooth));
       L.fo_track = rx->fo_track;
       L.nblocks = rx->eq_blocks;
       RX_CUDA(cudaMemsetAsync(rx->barrier, 0, 2 * sizeof(unsigned), st), "barrier reset");

@@ -18,8 +18,10 @@ constexpr int kBpsChunk = 256;    // BPS pass-1 symbols per warp
 // Device-resident equaliser state (one per stream).
 struct EqState {
   float2 taps[2][2][kMaxTaps];     // current taps h[p][q][i]
-  double dw;                       // per-symbol frequency offset (rad)
-  double Phi;                      // phase base of the next wave (rad)
+  double dw;                       // per-symbol frequency offset (rad), reported
+  double Phi;                      // phase base of the next wave (rad), reported
+  unsigned long long Phi_q;        // phase base as Q0.64 turns (the tracked value)
+  long long delta_q;               // per-sample phase increment dw/2 as Q0.64 turns
   int64_t next_wave;               // next wave to run
   int32_t acq_done;
   int32_t pad;
@@ -32,7 +34,8 @@ struct EqLaunch {
   float2 *y;                // equaliser out [2][y_stride], symbol k at y[k - y_base]
   int64_t y_base, y_stride;
   EqState *st;
-  double2 *fo_part;         // [2][2 * P] FO partial sums per (segment, row), double buffered
+  float4 *fo_part;          // [2][2 * P] FO partial sums per (segment, row) as double-float
+                            // (x_hi, x_lo, y_hi, y_lo), double buffered
   float2 *tap_slot;         // [2][2*2*kMaxTaps] last-segment taps (double buffered)
   float *trace;             // [trace_cap][2*2*kMaxTaps*2] wave start taps
   double *trace_fo;         // [trace_cap][2] (dw, Phi)
@@ -49,6 +52,7 @@ struct EqLaunch {
   int mod_bits;             // 2 or 4
   float mu_cma, mu_dd, cma_r2;
   double fo_smooth;
+  float inc_scale;          // 2^64 / (4 pi fo_smooth): tracker step r -> Q0.64 per sample
   int fo_track;
   int nblocks;              // CTAs in the grid (even: 2 rows per segment slot)
 };
