@@ -42,7 +42,7 @@ __host__ __device__ inline size_t pass1_warp_bytes(int chunk, int Nb) {
          (size_t)((chunk + 15) / 16) * 16;
 }
 
-template <int MB>
+template <int MB, bool NEED_S2>
 __global__ void __launch_bounds__(kBpsWarps * 32) bps_pass1(BpsLaunch L) {
   extern __shared__ float4 smem_raw[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -68,8 +68,10 @@ __global__ void __launch_bounds__(kBpsWarps * 32) bps_pass1(BpsLaunch L) {
   }
   __syncwarp();
   const int64_t v_lo = -lo, v_hi = L.K_end - lo;  // valid staged indices [v_lo, v_hi)
+  const bool edge = v_lo > 0 || v_hi < n_ys;      // chunk window touches a stream end
   auto dist = [&](int i) -> float {
-    return (i >= v_lo && i < v_hi) ? qam_dist<MB>(cmul(ys[i], rot)) : 0.f;
+    if (edge && (i < v_lo || i >= v_hi)) return 0.f;
+    return qam_dist<MB>(cmul(ys[i], rot));
   };
   for (int i = 0; i < M; ++i) ring[i * 32 + lane] = dist(i);   // window of symbol `start`
   int s_out = 0;                                 // slot of the oldest symbol in the window
@@ -95,9 +97,11 @@ __global__ void __launch_bounds__(kBpsWarps * 32) bps_pass1(BpsLaunch L) {
     const int64_t k = start + t;
     if (k >= a) {
       if (k > 0) R += unwrap_step(prev, bs);
-      int sk = s_out + Nb;                       // slot of symbol k
-      if (sk >= M) sk -= M;
-      s2 += __shfl_sync(0xffffffffu, ring[sk * 32 + lane], bs);
+      if (NEED_S2) {
+        int sk = s_out + Nb;                     // slot of symbol k
+        if (sk >= M) sk -= M;
+        s2 += __shfl_sync(0xffffffffu, ring[sk * 32 + lane], bs);
+      }
       if (lane == 0) bq[k - a] = (int8_t)bs;
     }
     prev = bs;
@@ -246,15 +250,16 @@ cudaError_t launch_bps(const BpsLaunch &L, cudaStream_t s) {
   dim3 grid((unsigned)((L.n_chunks + kBpsWarps - 1) / kBpsWarps), 2);
   const size_t sm = (size_t)kBpsWarps * pass1_warp_bytes(L.chunk, L.Nb);
   cudaError_t e;
+#define RX_PASS1(MB, NS)                                                                      \
+  e = cudaFuncSetAttribute(bps_pass1<MB, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm); \
+  if (e != cudaSuccess) return e;                                                             \
+  bps_pass1<MB, NS><<<grid, kBpsWarps * 32, sm, s>>>(L);
   if (L.mod_bits == 4) {
-    e = cudaFuncSetAttribute(bps_pass1<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e != cudaSuccess) return e;
-    bps_pass1<4><<<grid, kBpsWarps * 32, sm, s>>>(L);
+    if (L.need_s2) { RX_PASS1(4, true) } else { RX_PASS1(4, false) }
   } else {
-    e = cudaFuncSetAttribute(bps_pass1<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e != cudaSuccess) return e;
-    bps_pass1<2><<<grid, kBpsWarps * 32, sm, s>>>(L);
+    if (L.need_s2) { RX_PASS1(2, true) } else { RX_PASS1(2, false) }
   }
+#undef RX_PASS1
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   bps_scan<<<2, 1024, 0, s>>>(L);

@@ -279,6 +279,21 @@ __device__ __forceinline__ void run_span(const Hot hot, EqSmem &sm, const Span s
         sm.ybuf[par][kl] = act ? yv : make_float2(0.f, 0.f);
         if (out && act) hot.yrow[k0 + kl] = yv;
       }
+      // frequency pairs (k-1, k) inside [fo_lo, fo_hi); the previous symbol is the
+      // in-warp neighbour, else (after a CTA barrier) the previous warp's last one
+      const float yupx = __shfl_up_sync(FULL, yv.x, 4), yupy = __shfl_up_sync(FULL, yv.y, 4);
+      const int64_t kk = k0 + kl;
+      const bool fo_on = out && act && ln.part == 0 && kk - 1 >= sp.fo_lo && kk < sp.fo_hi;
+      // branch-free so the compiler can interleave it with the argmin chain
+      auto fo_pair = [&]() {
+        const float2 yw = sm.ybuf[par][kl > 0 ? kl - 1 : 0];
+        float2 yp = ln.j > 0 ? make_float2(yupx, yupy) : (ln.warp > 0 ? yw : yprev_last);
+        const float2 v = cmulc(yv, yp);
+        const float2 v2 = cmul(v, v);
+        const float2 v4 = cmul(v2, v2);
+        kahan_add(fo.sx, fo.cx, fo_on ? v4.x : 0.f);   // a select: stale inputs cannot leak
+        kahan_add(fo.sy, fo.cy, fo_on ? v4.y : 0.f);
+      };
       // ---- B: error
       float2 eth = make_float2(1.f, 0.f);  // exp(j theta)
       if (!sp.cma) {
@@ -300,6 +315,7 @@ __device__ __forceinline__ void run_span(const Hot hot, EqSmem &sm, const Span s
         const float dsum = (hi1 ? e2[1] : e2[0]) + __shfl_xor_sync(FULL, send, 4);
         sm.bps[ln.warp][ln.part * 8 + ln.j] = dsum;
         __syncthreads();  // (1)
+        fo_pair();
         const float D = (sm.bps[0][ln.lane] + sm.bps[1][ln.lane]) + (sm.bps[2][ln.lane] + sm.bps[3][ln.lane]);
         const unsigned key = __float_as_uint(D);
         const unsigned mn = __reduce_min_sync(FULL, key);
@@ -338,24 +354,8 @@ __device__ __forceinline__ void run_span(const Hot hot, EqSmem &sm, const Span s
         sm.grad[par][ln.warp][ln.q][ln.tap] =
             make_float2(k2.x + __shfl_xor_sync(FULL, s2.x, 4), k2.y + __shfl_xor_sync(FULL, s2.y, 4));
       }
-      // previous symbol for the frequency pairs: in-warp neighbour, else shared memory
-      const float yupx = __shfl_up_sync(FULL, yv.x, 4), yupy = __shfl_up_sync(FULL, yv.y, 4);
       __syncthreads();  // (2)
-      // ---- frequency pairs (k-1, k) inside [fo_lo, fo_hi)
-      if (out && act && ln.part == 0) {
-        const int64_t k = k0 + kl;
-        if (k - 1 >= sp.fo_lo && k < sp.fo_hi) {
-          float2 yp;
-          if (ln.j > 0) yp = make_float2(yupx, yupy);
-          else if (ln.warp > 0) yp = sm.ybuf[par][kl - 1];
-          else yp = yprev_last;
-          const float2 v = cmulc(yv, yp);
-          const float2 v2 = cmul(v, v);
-          const float2 v4 = cmul(v2, v2);
-          kahan_add(fo.sx, fo.cx, v4.x);
-          kahan_add(fo.sy, fo.cy, v4.y);
-        }
-      }
+      if (sp.cma) fo_pair();  // DD blocks did this in the shadow of the argmin
       // ---- tap update: this lane's own tap, then every FIR lane gathers its 8
       if (ln.tap < T) {
         const float2 g0 = sm.grad[par][0][ln.q][ln.tap], g1 = sm.grad[par][1][ln.q][ln.tap];

@@ -748,6 +748,7 @@ rx_status rx_process(rx_stream *rx, const rx_in *in, rx_out *out) {
     B.span = rx->span;
     B.Nb = rx->Nb;
     B.mod_bits = rx->mod_bits;
+    B.need_s2 = rx->llr_out;
     const int64_t r_lo = k_lo < rx->A ? 0 : 1 + (k_lo - rx->A) / rx->span;
     const int64_t r_hi = k_hi <= rx->A ? 1 : 1 + (k_hi - 1 - rx->A) / rx->span + 1;
     if (r_hi - r_lo > rx->region_cap) return fail(rx, RX_EINVAL, "region table overflow");

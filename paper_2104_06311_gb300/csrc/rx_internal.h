@@ -72,6 +72,7 @@ struct BpsLaunch {
   int chunk;                // chunk length (symbols)
   int64_t n_chunks;
   int Nb, mod_bits;
+  int need_s2;              // 1: sum |z - dec z|^2 per chunk (only the LLRs use sigma^2)
   // outputs
   uint32_t *bits; int64_t bits_stride;
   float *llr; int64_t llr_stride;
