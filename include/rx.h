@@ -86,7 +86,10 @@ enum {
   RX_P_SYM_OUT = 19,       /* 1 = write phase-recovered symbols to rx_out.sym        */
   RX_P_EQ_OUT = 20,        /* 1 = write equaliser outputs to rx_out.eq               */
   RX_P_CDC_OUT = 21,       /* 1 = write CDC outputs to rx_out.cdc (tests)            */
-  RX_P_PROFILE = 22        /* 1 = time each stage with CUDA events (rx_profile)      */
+  RX_P_PROFILE = 22,       /* 1 = time each stage with CUDA events (rx_profile)      */
+  RX_P_PIPELINE = 23       /* pieces per call overlapped on three internal streams
+                              (CDC ahead of, BPS behind the equaliser); 1..64,
+                              default 12; 1 = the stages run back to back          */
 };
 
 /* Stages reported by rx_profile. */

@@ -578,9 +578,11 @@ __global__ void __launch_bounds__(kEqThreads, 1) eq_kernel(EqLaunch L) {
   }
 }
 
-// Unused dynamic shared memory that keeps one equaliser CTA per SM: the update
-// step is a latency chain, so a second CTA on the same SM only slows both.
-constexpr int kEqPadSmem = 96 * 1024;
+// Unused dynamic shared memory that keeps the equaliser's SMs to itself: the
+// update step is a latency chain, so any other CTA on the same SM (a second
+// equaliser CTA, or the CDC / BPS kernels the host pipelines beside it on
+// other streams) would only slow it.
+constexpr int kEqPadSmem = 180 * 1024;
 
 int eq_max_blocks() {
   int dev = 0, sms = 0, per = 0, per4 = 0;

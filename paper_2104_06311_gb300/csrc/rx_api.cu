@@ -30,6 +30,7 @@ using namespace rx;
 
 namespace {
 constexpr double kC = 299792458.0;
+constexpr int kMaxPieces = 64;
 constexpr uint32_t kStateMagic = 0x52584231u;  // "RXB1"
 }  // namespace
 
@@ -83,6 +84,10 @@ struct rx_stream {
   int *h_err = nullptr;  // pinned mirror of the device error word
   cudaEvent_t err_ev = nullptr;
   int eq_blocks = 0;
+  int pieces = 12;                  // pipeline pieces per call (RX_P_PIPELINE)
+  cudaStream_t sub[3] = {nullptr, nullptr, nullptr};   // CDC, equaliser, BPS streams
+  cudaEvent_t ev_fork = nullptr;
+  cudaEvent_t ev_piece[3][kMaxPieces] = {};
   // ---- per-stage measurement (CUDA events on the bound stream)
   std::vector<cudaEvent_t> ev_pool;
   std::vector<std::pair<int, size_t>> ev_pending;  // (stage, index of the start event)
@@ -186,6 +191,12 @@ void release(rx_stream *rx) {
   if (rx->h_err) cudaFreeHost(rx->h_err);
   if (rx->err_ev) cudaEventDestroy(rx->err_ev);
   for (cudaEvent_t e : rx->ev_pool) cudaEventDestroy(e);
+  for (int i = 0; i < 3; ++i) {
+    for (int j = 0; j < kMaxPieces; ++j)
+      if (rx->ev_piece[i][j]) cudaEventDestroy(rx->ev_piece[i][j]), rx->ev_piece[i][j] = nullptr;
+    if (rx->sub[i]) cudaStreamDestroy(rx->sub[i]), rx->sub[i] = nullptr;
+  }
+  if (rx->ev_fork) cudaEventDestroy(rx->ev_fork), rx->ev_fork = nullptr;
   rx->ev_pool.clear();
   rx->ev_pending.clear();
   rx->ev_used = 0;
@@ -261,7 +272,8 @@ struct StageTimer {
   rx_stream *rx;
   int stage;
   size_t idx = (size_t)-1;
-  StageTimer(rx_stream *r, int st) : rx(r), stage(st) {
+  cudaStream_t strm;
+  StageTimer(rx_stream *r, int st, cudaStream_t sm) : rx(r), stage(st), strm(sm) {
     if (!rx->profile) return;
     while (rx->ev_pool.size() < rx->ev_used + 2) {
       cudaEvent_t e;
@@ -270,11 +282,11 @@ struct StageTimer {
     }
     idx = rx->ev_used;
     rx->ev_used += 2;
-    cudaEventRecord(rx->ev_pool[idx], rx->stream);
+    cudaEventRecord(rx->ev_pool[idx], strm);
   }
   ~StageTimer() {
     if (idx == (size_t)-1) return;
-    cudaEventRecord(rx->ev_pool[idx + 1], rx->stream);
+    cudaEventRecord(rx->ev_pool[idx + 1], strm);
     rx->ev_pending.push_back({stage, idx});
   }
 };
@@ -382,6 +394,7 @@ rx_status rx_set_param(rx_stream *rx, int key, double v) {
     case RX_P_EQ_OUT: rx->eq_out = v != 0; return RX_OK;
     case RX_P_CDC_OUT: rx->cdc_out = v != 0; return RX_OK;
     case RX_P_PROFILE: rx->profile = v != 0; return RX_OK;
+    case RX_P_PIPELINE: s = as_int(1, kMaxPieces, &t); rx->pieces = (int)t; return s;
     default: return fail(rx, RX_EINVAL, "unknown parameter key");
   }
   if (s != RX_OK) return s;
@@ -418,6 +431,7 @@ rx_status rx_get_param(rx_stream *rx, int key, double *v) {
     case RX_P_EQ_OUT: *v = rx->eq_out; break;
     case RX_P_CDC_OUT: *v = rx->cdc_out; break;
     case RX_P_PROFILE: *v = rx->profile; break;
+    case RX_P_PIPELINE: *v = rx->pieces; break;
     default: return fail(rx, RX_EINVAL, "unknown parameter key");
   }
   return RX_OK;
@@ -477,6 +491,13 @@ rx_status rx_reserve(rx_stream *rx, int64_t max_call) {
   *rx->h_err = 0;
   e = cudaEventCreateWithFlags(&rx->err_ev, cudaEventDisableTiming);
   if (e != cudaSuccess) { release(rx); return cuda_fail(rx, e, "event"); }
+  for (int i = 0; i < 3 && e == cudaSuccess; ++i) {
+    e = cudaStreamCreateWithFlags(&rx->sub[i], cudaStreamNonBlocking);
+    for (int j = 0; j < kMaxPieces && e == cudaSuccess; ++j)
+      e = cudaEventCreateWithFlags(&rx->ev_piece[i][j], cudaEventDisableTiming);
+  }
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&rx->ev_fork, cudaEventDisableTiming);
+  if (e != cudaSuccess) { release(rx); return cuda_fail(rx, e, "pipeline streams"); }
   e = launch_tables(rx->H, rx->tw, rx->N, rx->baud, rx->L_km, rx->D, rx->lam_nm, rx->rolloff, rx->stream);
   if (e != cudaSuccess) { release(rx); return cuda_fail(rx, e, "filter tables"); }
   rx->eq_blocks = 2 * std::min(rx->P, eq_max_blocks() / 2);
@@ -541,7 +562,7 @@ rx_status rx_process(rx_stream *rx, const rx_in *in, rx_out *out) {
   out->cdc_first = rx->F_cdc;
   out->cdc_n = 0;
 
-  // ---------------------------------------------------------------- CDC
+  // ---------------------------------------------------------------- plan
   const int64_t call_first = rx->M_in;
   const int64_t call_n = flush ? 0 : in->n;
   rx->M_in += call_n;
@@ -549,6 +570,8 @@ rx_status rx_process(rx_stream *rx, const rx_in *in, rx_out *out) {
     rx->flushed = true;
     rx->n_total = rx->M_in;
   }
+  const int64_t INF = INT64_MAX / 4;
+  const int64_t n_total = rx->n_total >= 0 ? rx->n_total : INF;
   int64_t win_end;
   if (flush) {
     win_end = (rx->n_total + rx->Sh - 1) / rx->Sh;
@@ -556,112 +579,114 @@ rx_status rx_process(rx_stream *rx, const rx_in *in, rx_out *out) {
     win_end = rx->M_in >= rx->V / 2 ? (rx->M_in - rx->V / 2) / rx->Sh : 0;
   }
   win_end = std::max(win_end, rx->next_win);
-  // equaliser needs u from here on
-  int64_t u_keep = 0;
-  if (rx->acq_done) {
-    const int64_t ks = rx->A + rx->next_wave * rx->span;
-    u_keep = std::max<int64_t>(0, 2 * (ks - rx->W) - c);
-  }
-  u_keep = std::min(u_keep, rx->F_cdc);
-  {
-    // slide u: keep [u_keep, F_cdc) at the start of the other buffer
-    const int64_t keep = rx->F_cdc - u_keep;
-    const int64_t new_end = std::min(win_end * rx->Sh, rx->n_total >= 0 ? rx->n_total : INT64_MAX);
-    if (new_end - u_keep > rx->u_cap) return fail(rx, RX_EINVAL, "CDC buffer overflow (call too large for the reservation)");
-    if (u_keep != rx->u_base) {
-      StageTimer tm(rx, RX_STAGE_MOVE);
-      rx->stage_launches[RX_STAGE_MOVE] += keep > 0;
-      const int nxt = 1 - rx->cur_u;
-      RX_CUDA(launch_copy_cols(rx->u[nxt], rx->u_cap, rx->u[rx->cur_u] + (u_keep - rx->u_base), rx->u_cap, keep, st), "slide u");
-      rx->cur_u = nxt;
-      rx->u_base = u_keep;
-    }
-  }
-  const int64_t nwin = win_end - rx->next_win;
-  if (nwin > 0) {
-    {
-    StageTimer tm(rx, RX_STAGE_CDC);
-    rx->stage_launches[RX_STAGE_CDC] += 1;
-    RX_CUDA(launch_cdc(rx->N, rx->V, rx->tail[rx->cur_tail], rx->tail_first, rx->tail_n, in->data, call_first, call_n,
-                       rx->dtype, (float)rx->in_scale, rx->H, rx->tw, rx->u[rx->cur_u], rx->u_base, rx->u_cap,
-                       rx->next_win, nwin, rx->n_total, st),
-            "cdc");
-    }
-    const int64_t f_old = rx->F_cdc;
-    rx->F_cdc = std::min(win_end * rx->Sh, rx->n_total >= 0 ? rx->n_total : INT64_MAX);
-    rx->next_win = win_end;
-    if (rx->cdc_out) {
-      const int64_t n = rx->F_cdc - f_old;  // the cdc array holds in->n + N samples per pol
-      RX_CUDA(launch_copy_cols((float2 *)out->cdc, out->cdc_stride, rx->u[rx->cur_u] + (f_old - rx->u_base), rx->u_cap, n, st), "cdc out");
-      out->cdc_first = f_old;
-      out->cdc_n = n;
-    }
-  }
-  // carry the raw input still needed by later windows: [next_win*Sh - V/2, M_in)
-  if (!flush) {
-    const int64_t need_lo = std::max<int64_t>(0, rx->next_win * rx->Sh - rx->V / 2);
-    const int64_t n_keep = rx->M_in - need_lo;
-    if (n_keep > rx->tail_cap) return fail(rx, RX_EINVAL, "input tail overflow");
-    const int nxt = 1 - rx->cur_tail;
-    const size_t elem = rx->dtype == RX_I8x4 ? 4 : 16;
-    // part from the old tail: [need_lo, call_first)
-    if (need_lo < call_first) {
-      const int64_t n_old = call_first - need_lo;
-      RX_CUDA(cudaMemcpyAsync(rx->tail[nxt], rx->tail[rx->cur_tail] + (need_lo - rx->tail_first) * elem, n_old * elem,
-                              cudaMemcpyDeviceToDevice, st),
-              "tail");
-      RX_CUDA(cudaMemcpyAsync(rx->tail[nxt] + n_old * elem, in->data, call_n * elem, cudaMemcpyDeviceToDevice, st), "tail");
-    } else {
-      RX_CUDA(cudaMemcpyAsync(rx->tail[nxt], (const uint8_t *)in->data + (need_lo - call_first) * elem, n_keep * elem,
-                              cudaMemcpyDeviceToDevice, st),
-              "tail");
-    }
-    rx->cur_tail = nxt;
-    rx->tail_first = need_lo;
-    rx->tail_n = n_keep;
-  }
-
-  // ---------------------------------------------------------------- equaliser
+  const int64_t win_first = rx->next_win;
+  const int64_t F_cdc_old = rx->F_cdc;
+  const int64_t F_cdc_new = win_end > win_first ? std::min(win_end * rx->Sh, n_total) : F_cdc_old;
+  // equaliser: acquisition and the waves whose inputs (with FIR support) exist
   const int64_t K = rx->flushed ? rx->n_total / 2 : -1;
   if (!rx->acq_done) rx->A = rx->flushed ? std::min(rx->A_full, K) : rx->A_full;
   const int64_t A = rx->A;
-  EqLaunch L;
-  memset(&L, 0, sizeof(L));
   bool run_acq = false;
-  if (!rx->acq_done) {
-    if (rx->flushed ? (A > 0) : (rx->F_cdc >= 2 * A + c)) run_acq = true;
-  }
+  if (!rx->acq_done) run_acq = rx->flushed ? (A > 0) : (F_cdc_new >= 2 * A + c);
   const bool acq_ready = rx->acq_done || run_acq;
-  int64_t n_seg = INT64_MAX / 4, wave_last = rx->next_wave;
+  int64_t n_seg = INF, wave_last = rx->next_wave;
   if (acq_ready) {
     if (rx->flushed) {
       n_seg = K > A ? (K - A + rx->S - 1) / rx->S : 0;
       wave_last = (n_seg + rx->P - 1) / rx->P;
     } else {
-      // complete waves whose inputs (with the FIR support) are computed
-      const int64_t avail = rx->F_cdc - c;  // samples < avail usable
-      const int64_t ke_max = avail / 2;     // symbols with 2k + c < F_cdc
+      const int64_t ke_max = (F_cdc_new - c) / 2;  // symbols with 2k + c < F_cdc
       wave_last = ke_max > A ? (ke_max - A) / rx->span : 0;
     }
     wave_last = std::max(wave_last, rx->next_wave);
   }
-  const int64_t y_keep = std::max<int64_t>(0, rx->F_out - rx->Nb - 1);
-  {
-    const int64_t keep = std::max<int64_t>(0, rx->F_eq - y_keep);
-    int64_t new_eq = rx->F_eq;
-    if (run_acq) new_eq = A;
-    if (acq_ready && wave_last > rx->next_wave) new_eq = std::min(A + wave_last * rx->span, K >= 0 ? K : INT64_MAX);
-    if (new_eq - y_keep > rx->y_cap) return fail(rx, RX_EINVAL, "equaliser buffer overflow");
-    if (y_keep != rx->y_base) {
-      StageTimer tm(rx, RX_STAGE_MOVE);
-      rx->stage_launches[RX_STAGE_MOVE] += 2 * (keep > 0);
-      const int nxt = 1 - rx->cur_y;
-      RX_CUDA(launch_copy_cols(rx->y[nxt], rx->y_cap, rx->y[rx->cur_y] + (y_keep - rx->y_base), rx->y_cap, keep, st), "slide y");
-      RX_CUDA(launch_copy_cols_i8(rx->bh[nxt], rx->y_cap, rx->bh[rx->cur_y] + (y_keep - rx->y_base), rx->y_cap, keep, st), "slide bhat");
-      rx->cur_y = nxt;
-      rx->y_base = y_keep;
+  const int64_t wave_first = rx->next_wave;
+  const bool eq_work = run_acq || (acq_ready && wave_last > wave_first);
+  auto eq_frontier = [&](int64_t wb) -> int64_t {  // symbols equalised once waves < wb ran
+    if (!acq_ready) return rx->F_eq;
+    if (wb <= wave_first && !run_acq) return rx->F_eq;
+    return wb > 0 ? std::min(A + wb * rx->span, K >= 0 ? K : INF) : A;
+  };
+  const int64_t new_eq = eq_work ? eq_frontier(wave_last) : rx->F_eq;
+  // BPS/demap: whole regions whose +-Nb window is complete (everything at flush)
+  auto emit_frontier = [&](int64_t f_eq, bool last) -> int64_t {
+    if (!(rx->acq_done || run_acq)) return rx->F_out;
+    if (rx->flushed && last) return f_eq;
+    int64_t k_hi = rx->F_out, e = region_end_after(rx, rx->F_out);
+    while (e + rx->Nb < f_eq) {
+      k_hi = e;
+      e = region_end_after(rx, e);
     }
-    if (run_acq || (acq_ready && wave_last > rx->next_wave)) {
+    return k_hi;
+  };
+  const int64_t k_lo = rx->F_out;
+  const int64_t k_hi = emit_frontier(new_eq, true);
+  if (k_hi - k_lo > out->capacity) return fail(rx, RX_EINVAL, "output capacity too small");
+
+  // ---------------------------------------------------------------- carried buffers (bound stream)
+  int64_t u_keep = 0;
+  if (rx->acq_done) u_keep = std::max<int64_t>(0, 2 * (A + wave_first * rx->span - rx->W) - c);
+  u_keep = std::min(u_keep, F_cdc_old);
+  if (F_cdc_new - u_keep > rx->u_cap) return fail(rx, RX_EINVAL, "CDC buffer overflow (call too large for the reservation)");
+  const int64_t y_keep = std::max<int64_t>(0, rx->F_out - rx->Nb - 1);
+  if (new_eq - y_keep > rx->y_cap) return fail(rx, RX_EINVAL, "equaliser buffer overflow");
+  if (u_keep != rx->u_base) {
+    const int64_t keep = F_cdc_old - u_keep;
+    StageTimer tm(rx, RX_STAGE_MOVE, st);
+    rx->stage_launches[RX_STAGE_MOVE] += keep > 0;
+    const int nxt = 1 - rx->cur_u;
+    RX_CUDA(launch_copy_cols(rx->u[nxt], rx->u_cap, rx->u[rx->cur_u] + (u_keep - rx->u_base), rx->u_cap, keep, st), "slide u");
+    rx->cur_u = nxt;
+    rx->u_base = u_keep;
+  }
+  if (y_keep != rx->y_base) {
+    const int64_t keep = std::max<int64_t>(0, rx->F_eq - y_keep);
+    StageTimer tm(rx, RX_STAGE_MOVE, st);
+    rx->stage_launches[RX_STAGE_MOVE] += 2 * (keep > 0);
+    const int nxt = 1 - rx->cur_y;
+    RX_CUDA(launch_copy_cols(rx->y[nxt], rx->y_cap, rx->y[rx->cur_y] + (y_keep - rx->y_base), rx->y_cap, keep, st), "slide y");
+    RX_CUDA(launch_copy_cols_i8(rx->bh[nxt], rx->y_cap, rx->bh[rx->cur_y] + (y_keep - rx->y_base), rx->y_cap, keep, st), "slide bhat");
+    rx->cur_y = nxt;
+    rx->y_base = y_keep;
+  }
+
+  // ---------------------------------------------------------------- pieces on three streams
+  // Piece j: CDC windows it needs (CDC stream) -> its equaliser waves (EQ
+  // stream, after the CDC piece) -> the regions its output completes (BPS
+  // stream, after the EQ piece).  Pieces overlap: CDC runs ahead, BPS runs
+  // behind the equaliser on the SMs the equaliser leaves free.
+  const int64_t n_waves = eq_work ? wave_last - wave_first : 0;
+  int np = 1;
+  if (n_waves > 0) np = (int)std::min<int64_t>(std::max(1, rx->pieces), n_waves);
+  np = std::min(np, kMaxPieces);
+  RX_CUDA(cudaEventRecord(rx->ev_fork, st), "fork");
+  for (int i = 0; i < 3; ++i) RX_CUDA(cudaStreamWaitEvent(rx->sub[i], rx->ev_fork, 0), "fork");
+  int64_t w_done = win_first, wa = wave_first, kdone = k_lo;
+  for (int j = 0; j < np; ++j) {
+    const bool last = j == np - 1;
+    const int64_t wb = last ? wave_last : wave_first + (n_waves * (j + 1)) / np;
+    const int64_t f_eq_j = eq_work ? eq_frontier(wb) : rx->F_eq;
+    // CDC windows for this piece
+    int64_t w_need = win_end;
+    if (!last) {
+      const int64_t need = std::min(2 * f_eq_j + c + 1, F_cdc_new);
+      w_need = std::min(win_end, std::max(w_done, (need + rx->Sh - 1) / rx->Sh));
+    }
+    if (w_need > w_done) {
+      StageTimer tm(rx, RX_STAGE_CDC, rx->sub[0]);
+      rx->stage_launches[RX_STAGE_CDC] += 1;
+      RX_CUDA(launch_cdc(rx->N, rx->V, rx->tail[rx->cur_tail], rx->tail_first, rx->tail_n, in->data, call_first,
+                         call_n, rx->dtype, (float)rx->in_scale, rx->H, rx->tw, rx->u[rx->cur_u], rx->u_base,
+                         rx->u_cap, w_done, w_need - w_done, rx->n_total, rx->sub[0]),
+              "cdc");
+      w_done = w_need;
+    }
+    RX_CUDA(cudaEventRecord(rx->ev_piece[0][j], rx->sub[0]), "event");
+    // equaliser waves [wa, wb) (and the acquisition in piece 0)
+    if (eq_work && (wb > wa || (j == 0 && run_acq))) {
+      RX_CUDA(cudaStreamWaitEvent(rx->sub[1], rx->ev_piece[0][j], 0), "event");
+      EqLaunch L;
+      memset(&L, 0, sizeof(L));
       L.u = rx->u[rx->cur_u];
       L.u_base = rx->u_base;
       L.u_stride = rx->u_cap;
@@ -677,11 +702,11 @@ rx_status rx_process(rx_stream *rx, const rx_in *in, rx_out *out) {
       L.barrier = rx->barrier;
       L.err = rx->err;
       L.K = K;
-      L.run_acq = run_acq;
+      L.run_acq = j == 0 && run_acq;
       L.A = A;
       L.n_cma = std::min(rx->n_cma, A);
-      L.wave_first = rx->next_wave;
-      L.wave_last = wave_last;
+      L.wave_first = wa;
+      L.wave_last = wb;
       L.n_segments = n_seg;
       L.P = rx->P;
       L.S = rx->S;
@@ -696,80 +721,101 @@ rx_status rx_process(rx_stream *rx, const rx_in *in, rx_out *out) {
       L.inc_scale = (float)(18446744073709551616.0 / (4.0 * 3.14159265358979323846 * rx->fo_smooth));
       L.fo_track = rx->fo_track;
       L.nblocks = rx->eq_blocks;
-      RX_CUDA(cudaMemsetAsync(rx->barrier, 0, 2 * sizeof(unsigned), st), "barrier reset");
-      {
-        StageTimer tm(rx, RX_STAGE_EQ);
-        rx->stage_launches[RX_STAGE_EQ] += 1;
-        RX_CUDA(launch_eq(L, st), "equaliser");
-      }
-      if (run_acq) rx->acq_done = true;
-      rx->next_wave = wave_last;
-      rx->F_eq = new_eq;
+      RX_CUDA(cudaMemsetAsync(rx->barrier, 0, 2 * sizeof(unsigned), rx->sub[1]), "barrier reset");
+      StageTimer tm(rx, RX_STAGE_EQ, rx->sub[1]);
+      rx->stage_launches[RX_STAGE_EQ] += 1;
+      RX_CUDA(launch_eq(L, rx->sub[1]), "equaliser");
+      wa = wb;
     }
-  }
-
-  // ---------------------------------------------------------------- BPS + demap
-  int64_t k_hi = rx->F_out;
-  if (rx->acq_done) {
-    if (rx->flushed) {
-      k_hi = rx->F_eq;  // == K once everything ran
-    } else {
-      int64_t e = region_end_after(rx, rx->F_out);
-      while (e + rx->Nb < rx->F_eq) {
-        k_hi = e;
-        e = region_end_after(rx, e);
-      }
-    }
-  }
-  const int64_t k_lo = rx->F_out;
-  if (k_hi > k_lo) {
-    const int64_t n = k_hi - k_lo;
-    if (n > out->capacity) return fail(rx, RX_EINVAL, "output capacity too small");
-    BpsLaunch B;
-    memset(&B, 0, sizeof(B));
-    B.y = rx->y[rx->cur_y];
-    B.y_base = rx->y_base;
-    B.y_stride = rx->y_cap;
-    B.bhat = rx->bh[rx->cur_y];
-    B.bh_base = rx->y_base;
-    B.bh_stride = rx->y_cap;
-    B.chunk = rx->C;
-    B.n_chunks = (n + rx->C - 1) / rx->C;
-    if (B.n_chunks > rx->chunk_cap) return fail(rx, RX_EINVAL, "chunk table overflow");
-    B.chunk_r = rx->chunk_r;
-    B.chunk_s2 = rx->chunk_s2;
-    B.chunk_m = rx->chunk_m;
-    B.m_carry = rx->m_carry;
-    B.region_s2 = rx->region_s2;
-    B.k_lo = k_lo;
-    B.k_hi = k_hi;
-    B.K_end = rx->flushed ? K : rx->F_eq;
-    B.A = rx->A;
-    B.span = rx->span;
-    B.Nb = rx->Nb;
-    B.mod_bits = rx->mod_bits;
-    B.need_s2 = rx->llr_out;
-    const int64_t r_lo = k_lo < rx->A ? 0 : 1 + (k_lo - rx->A) / rx->span;
-    const int64_t r_hi = k_hi <= rx->A ? 1 : 1 + (k_hi - 1 - rx->A) / rx->span + 1;
-    if (r_hi - r_lo > rx->region_cap) return fail(rx, RX_EINVAL, "region table overflow");
-    B.bits = out->bits;
-    B.bits_stride = out->bits_stride;
-    B.llr = rx->llr_out ? out->llr : nullptr;
-    B.llr_stride = out->llr_stride;
-    B.sym = rx->sym_out ? (float2 *)out->sym : nullptr;
-    B.sym_stride = out->sym_stride;
-    B.out_first = k_lo;
-    {
-      StageTimer tm(rx, RX_STAGE_BPS);
+    RX_CUDA(cudaEventRecord(rx->ev_piece[1][j], rx->sub[1]), "event");
+    // BPS + demap of the regions this piece completes
+    const int64_t kj = last ? k_hi : std::max(kdone, emit_frontier(f_eq_j, false));
+    if (kj > kdone) {
+      RX_CUDA(cudaStreamWaitEvent(rx->sub[2], rx->ev_piece[1][j], 0), "event");
+      BpsLaunch B;
+      memset(&B, 0, sizeof(B));
+      B.y = rx->y[rx->cur_y];
+      B.y_base = rx->y_base;
+      B.y_stride = rx->y_cap;
+      B.bhat = rx->bh[rx->cur_y];
+      B.bh_base = rx->y_base;
+      B.bh_stride = rx->y_cap;
+      B.chunk = rx->C;
+      B.n_chunks = (kj - kdone + rx->C - 1) / rx->C;
+      if (B.n_chunks > rx->chunk_cap) return fail(rx, RX_EINVAL, "chunk table overflow");
+      B.chunk_r = rx->chunk_r;
+      B.chunk_s2 = rx->chunk_s2;
+      B.chunk_m = rx->chunk_m;
+      B.m_carry = rx->m_carry;
+      B.region_s2 = rx->region_s2;
+      B.k_lo = kdone;
+      B.k_hi = kj;
+      B.K_end = (rx->flushed && last) ? K : f_eq_j;
+      B.A = A;
+      B.span = rx->span;
+      B.Nb = rx->Nb;
+      B.mod_bits = rx->mod_bits;
+      B.need_s2 = rx->llr_out;
+      const int64_t r_lo = kdone < A ? 0 : 1 + (kdone - A) / rx->span;
+      const int64_t r_hi = kj <= A ? 1 : 1 + (kj - 1 - A) / rx->span + 1;
+      if (r_hi - r_lo > rx->region_cap) return fail(rx, RX_EINVAL, "region table overflow");
+      B.bits = out->bits;
+      B.bits_stride = out->bits_stride;
+      B.llr = rx->llr_out ? out->llr : nullptr;
+      B.llr_stride = out->llr_stride;
+      B.sym = rx->sym_out ? (float2 *)out->sym : nullptr;
+      B.sym_stride = out->sym_stride;
+      B.out_first = k_lo;
+      StageTimer tm(rx, RX_STAGE_BPS, rx->sub[2]);
       rx->stage_launches[RX_STAGE_BPS] += 3;
-      RX_CUDA(launch_bps(B, st), "bps");
+      RX_CUDA(launch_bps(B, rx->sub[2]), "bps");
+      kdone = kj;
     }
-    if (rx->eq_out)
-      RX_CUDA(launch_copy_cols((float2 *)out->eq, out->eq_stride, rx->y[rx->cur_y] + (k_lo - rx->y_base), rx->y_cap, n, st), "eq out");
-    out->first = k_lo;
-    out->n = n;
-    rx->F_out = k_hi;
+    RX_CUDA(cudaEventRecord(rx->ev_piece[2][j], rx->sub[2]), "event");
   }
+  for (int i = 0; i < 3; ++i) RX_CUDA(cudaStreamWaitEvent(st, rx->ev_piece[i][np - 1], 0), "join");
+
+  // ---------------------------------------------------------------- after the join (bound stream)
+  if (rx->cdc_out && F_cdc_new > F_cdc_old) {
+    const int64_t n = F_cdc_new - F_cdc_old;  // the cdc array holds in->n + N samples per pol
+    RX_CUDA(launch_copy_cols((float2 *)out->cdc, out->cdc_stride, rx->u[rx->cur_u] + (F_cdc_old - rx->u_base), rx->u_cap, n, st), "cdc out");
+    out->cdc_first = F_cdc_old;
+    out->cdc_n = n;
+  }
+  if (rx->eq_out && k_hi > k_lo)
+    RX_CUDA(launch_copy_cols((float2 *)out->eq, out->eq_stride, rx->y[rx->cur_y] + (k_lo - rx->y_base), rx->y_cap, k_hi - k_lo, st), "eq out");
+  rx->next_win = win_end;
+  rx->F_cdc = F_cdc_new;
+  // carry the raw input still needed by later windows: [next_win*Sh - V/2, M_in)
+  if (!flush) {
+    const int64_t need_lo = std::max<int64_t>(0, rx->next_win * rx->Sh - rx->V / 2);
+    const int64_t n_keep = rx->M_in - need_lo;
+    if (n_keep > rx->tail_cap) return fail(rx, RX_EINVAL, "input tail overflow");
+    const int nxt = 1 - rx->cur_tail;
+    const size_t elem = rx->dtype == RX_I8x4 ? 4 : 16;
+    if (need_lo < call_first) {
+      const int64_t n_old = call_first - need_lo;
+      RX_CUDA(cudaMemcpyAsync(rx->tail[nxt], rx->tail[rx->cur_tail] + (need_lo - rx->tail_first) * elem, n_old * elem,
+                              cudaMemcpyDeviceToDevice, st),
+              "tail");
+      RX_CUDA(cudaMemcpyAsync(rx->tail[nxt] + n_old * elem, in->data, call_n * elem, cudaMemcpyDeviceToDevice, st), "tail");
+    } else {
+      RX_CUDA(cudaMemcpyAsync(rx->tail[nxt], (const uint8_t *)in->data + (need_lo - call_first) * elem, n_keep * elem,
+                              cudaMemcpyDeviceToDevice, st),
+              "tail");
+    }
+    rx->cur_tail = nxt;
+    rx->tail_first = need_lo;
+    rx->tail_n = n_keep;
+  }
+  if (eq_work) {
+    if (run_acq) rx->acq_done = true;
+    rx->next_wave = wave_last;
+    rx->F_eq = new_eq;
+  }
+  out->first = k_lo;
+  out->n = k_hi - k_lo;
+  rx->F_out = k_hi;
   return post_error_copy(rx);
 }
 

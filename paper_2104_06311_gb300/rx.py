@@ -20,7 +20,7 @@ PARAMS = {
     "MOD": 1, "FFT_N": 2, "OVERLAP": 3, "ROLLOFF": 4, "LAMBDA_NM": 5, "MU_CMA": 6, "MU_DD": 7,
     "N_CMA": 8, "UPDATE_BLOCK": 9, "SEG_LEN": 10, "SEG_PRETRAIN": 11, "BPS_HALFWIN": 12,
     "BLOCK_SAMPLES": 13, "IN_SCALE": 14, "ACQ_MIN": 15, "FO_SMOOTH": 16, "FO_TRACK": 17,
-    "LLR_OUT": 18, "SYM_OUT": 19, "EQ_OUT": 20, "CDC_OUT": 21, "PROFILE": 22,
+    "LLR_OUT": 18, "SYM_OUT": 19, "EQ_OUT": 20, "CDC_OUT": 21, "PROFILE": 22, "PIPELINE": 23,
 }
 STAGES = ["cdc", "eq", "bps", "move", "ber"]
 
