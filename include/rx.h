@@ -201,6 +201,28 @@ const char *rx_last_error(rx_stream *rx);
  * Synchronises the bound stream.  Not from the paper: measurement support. */
 rx_status rx_profile(rx_stream *rx, double *ms, int64_t *launches, int reset);
 
+/* Blind phase search, unwrap and hard Gray bits of one equalised block,
+ * without allocating any device memory.  The paper has no counterpart: this
+ * exists for callers that cannot call cudaMalloc when they need carrier
+ * recovery (code being recorded into a CUDA graph, real-time loops that must
+ * not hit the allocator's implicit device synchronisation, hosts with a
+ * fixed device-memory budget).  It runs the same kernels as rx_process's BPS
+ * stage (32 test angles, +-bps_halfwin window, unwrap count starting at 0)
+ * and treats y[0, n_symbols) of each polarisation as a whole stream.
+ *   y: device, [pol][y_stride] complex floats (re, im), 8-byte aligned;
+ *   bits: device, [pol][bits_stride] words in the rx_out bit layout;
+ *   bits_per_symbol: 2 (QPSK) or 4 (16QAM); bps_halfwin: 0..64;
+ *   cuda_stream: the stream to run on (NULL = legacy default stream).
+ * Scratch lives in one file-scope device array sized for at most 1048576
+ * symbols per polarisation (~2.1 MiB, held by every GPU that loads the
+ * library until the process exits); larger n_symbols returns RX_EINVAL.
+ * All calls share that array: calls that overlap on the GPU race.  The first
+ * call on a device looks up the array's device address and caches it; make
+ * it before any stream capture.  Asynchronous on cuda_stream. */
+rx_status rx_bps_demap_noalloc(const float *y, int64_t y_stride, int64_t n_symbols,
+                               int bits_per_symbol, int bps_halfwin, uint32_t *bits,
+                               int64_t bits_stride, void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

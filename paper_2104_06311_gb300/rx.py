@@ -26,7 +26,8 @@ STAGES = ["cdc", "eq", "bps", "move", "ber"]
 
 EXPORTS = ["rx_create", "rx_set_param", "rx_get_param", "rx_set_cuda_stream", "rx_reserve",
            "rx_process", "rx_ber", "rx_trace", "rx_get_state", "rx_set_state", "rx_reset",
-           "rx_sync", "rx_destroy", "rx_status_str", "rx_last_error", "rx_profile"]
+           "rx_sync", "rx_destroy", "rx_status_str", "rx_last_error", "rx_profile",
+           "rx_bps_demap_noalloc"]
 
 
 class rx_in(ct.Structure):
@@ -73,6 +74,7 @@ def load(path: str = LIB_PATH) -> ct.CDLL:
     lib.rx_get_state.argtypes = [P, P, ct.POINTER(ct.c_size_t)]
     lib.rx_set_state.argtypes = [P, P, ct.c_size_t]
     lib.rx_profile.argtypes = [P, ct.POINTER(ct.c_double), ct.POINTER(ct.c_int64), ct.c_int]
+    lib.rx_bps_demap_noalloc.argtypes = [P, ct.c_int64, ct.c_int64, ct.c_int, ct.c_int, P, ct.c_int64, P]
     lib.rx_reset.argtypes = [P]
     lib.rx_sync.argtypes = [P]
     lib.rx_destroy.argtypes = [P]
