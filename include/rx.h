@@ -63,8 +63,8 @@ enum {
  * (or after rx_reset); later changes return RX_ESTATE. */
 enum {
   RX_P_MOD = 1,            /* bits per symbol: 2 = QPSK (default), 4 = 16QAM         */
-  RX_P_FFT_N = 2,          /* CDC FFT size, power of two 256..8192 (0 = default:
-                              max(1024, next pow2 >= 4 V))                          */
+  RX_P_FFT_N = 2,          /* CDC FFT size, power of two 256..16384 (0 = default:
+                              max(1024, next pow2 >= 4 V), at most 16384)           */
   RX_P_OVERLAP = 3,        /* CDC overlap V, multiple of 32 (0 = default: N_CD - 1
                               rounded up to a multiple of 32)                        */
   RX_P_ROLLOFF = 4,        /* RRC roll-off (default 0.1)                             */

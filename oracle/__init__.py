@@ -20,6 +20,6 @@ invariants, brute force, BER theory).  None is marked "parity unpinned".
 from .chain import (  # noqa: F401
     RxParams, n_cd_taps, default_overlap, default_fft_n, cd_response, rrc_response,
     cdc_filter, cdc_overlap_save, bps_outer_angles, region_bounds, lms_step,
-    decide, hard_bits, llr_maxlog, fo_estimate_sum, equalize, bps_outer, demap,
+    decide, hard_bits, llr_maxlog, fo_estimate_sum, ring_weight, equalize, bps_outer, demap,
     run_chain, ber_sync_count, q_from_ber, ber_theory,
 )

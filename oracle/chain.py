@@ -38,8 +38,8 @@ def n_cd_taps(baud: float, sps: int, L_km: float, D_ps_nm_km: float, lam_nm: flo
 
     Textbook bound (Savory, "Digital filters for coherent optical receivers",
     2008) for the length of a time-domain CD compensating filter.  The paper
-    is silent; its static equaliser "automatically handles dispersion
-    compensation" (Section "Introduction").
+    is silent on it; its introduction says only that the receiver's
+    equalisation takes care of dispersion compensation digitally.
     """
     T = 1.0 / (sps * baud)
     D = abs(D_ps_nm_km) * 1e-12 / (1e-9 * 1e3)
@@ -53,9 +53,12 @@ def default_overlap(ncd: int) -> int:
 
 
 def default_fft_n(V: int) -> int:
-    """Smallest power of two >= 4V, and at least 1024 (the paper's FFT size)."""
+    """Smallest power of two >= 4V, at least 1024 (the paper's FFT size) and at
+    most 16384 (a configuration choice the paper does not make: beyond 4V the
+    overlap-save overhead V/N only shrinks slowly, and 16384 is the largest
+    transform the receiver library offers)."""
     n = 1024
-    while n < 4 * V:
+    while n < 4 * V and n < 16384:
         n *= 2
     return n
 
@@ -122,9 +125,9 @@ def _grid(p: RxParams, N: int) -> np.ndarray:
 def cd_response(p: RxParams, N: int) -> np.ndarray:
     """Dispersion compensation exp(-j beta2 L w_k^2 / 2), beta2 = -D lam^2/(2 pi c).
 
-    The inverse of the fibre's exp(+j beta2 L w^2/2) (paper-silent; the paper's
-    static equaliser "automatically handles dispersion compensation", Section
-    "Introduction").  Bin k sits at f_k = k fs/N for k < N/2, (k-N) fs/N else.
+    The inverse of the fibre's exp(+j beta2 L w^2/2) (paper-silent: the paper's
+    introduction only says its equalisation compensates dispersion digitally).
+    Bin k sits at f_k = k fs/N for k < N/2, (k-N) fs/N else.
     """
     w = TWO_PI * _grid(p, N)
     D = p.D * 1e-12 / (1e-9 * 1e3)
@@ -247,19 +250,37 @@ def llr_maxlog(z: np.ndarray, sigma2: np.ndarray, mod: str) -> np.ndarray:
 # ---------------------------------------------------------------------------
 # Frequency offset: differential 4th-power estimator (paper-silent)
 # ---------------------------------------------------------------------------
-def fo_estimate_sum(y: np.ndarray) -> complex:
-    """sum over pols and adjacent pairs of (y_k conj(y_{k-1}))^4.
+def ring_weight(a: np.ndarray) -> np.ndarray:
+    """Weight of a 16QAM symbol with power a = |y|^2 in the frequency estimate.
 
-    A quarter of its argument estimates the per-symbol frequency offset of
-    QPSK-like signals (the 4th power removes the pi/2-symmetric data).  The
-    paper's KK receiver instead downshifts a known carrier tone to DC
+    Unit-energy 16QAM has rings at |s|^2 = 0.2, 1.0 and 1.8.  The inner and
+    outer rings sit at odd multiples of pi/4 (their 4th power is -|s|^4, as for
+    QPSK); the middle ring's 4th power is not aligned with them and only adds
+    self-noise (QPSK partitioning: Fatadin, Ives, Savory, IEEE PTL 2010).  The
+    weight is 0 for |a - 1| <= 0.2, 1 for |a - 1| >= 0.4 and linear between:
+    a soft edge, so that the estimate is continuous in the samples.
+    """
+    return np.clip((np.abs(a - 1.0) - 0.2) / 0.2, 0.0, 1.0)
+
+
+def fo_estimate_sum(y: np.ndarray, mod: str = "qpsk") -> complex:
+    """sum over pols and adjacent pairs of w_k w_{k-1} (y_k conj(y_{k-1}))^4.
+
+    A quarter of its argument estimates the per-symbol frequency offset (the
+    4th power removes the pi/2-symmetric data).  QPSK: w = 1.  16QAM: w =
+    ring_weight(|y|^2), which keeps the pi/4-aligned inner and outer rings.
+    The paper's KK receiver instead downshifts a known carrier tone to DC
     (processing-chain paragraph); the estimator is the textbook one for
     coherent detection with a free-running local oscillator.
     """
     if y.shape[-1] < 2:
         return 0j
     v = y[..., 1:] * np.conj(y[..., :-1])
-    return complex(np.sum(v ** 4))
+    v4 = v ** 4
+    if mod == "16qam":
+        w = ring_weight(y.real ** 2 + y.imag ** 2)
+        v4 = v4 * (w[..., 1:] * w[..., :-1])
+    return complex(np.sum(v4))
 
 
 # ---------------------------------------------------------------------------
@@ -351,7 +372,7 @@ def equalize(u: np.ndarray, p: RxParams, trace: dict | None = None,
         symbols.  Its input is rotated by exp(-j (Phi_w + (n - n_w) dw_w/sps)),
         n_w = 2 (A + w P S).
       * Frequency tracking per wave: dw_{w+1} = dw_w + r_w/16 with r_w a
-        quarter of the argument of the 4th-power sum over adjacent pairs
+        quarter of the argument of fo_estimate_sum over adjacent pairs
         inside each segment; Phi_{w+1} = remainder(Phi_w + 2PS dw_w/sps, 2pi).
 
     The tracked phase integrates the frequency estimate over 2PS samples per
@@ -382,7 +403,7 @@ def equalize(u: np.ndarray, p: RxParams, trace: dict | None = None,
     for k0 in range(0, n_cma, Bu):
         k1 = min(k0 + Bu, n_cma)
         y[:, k0:k1], h = lms_step(h, win.taps_input(k0, k1, T, c), "cma", p, phis)
-    dw = 0.25 * np.angle(fo_estimate_sum(y[:, n_cma // 2:n_cma])) if p.fo_track else 0.0
+    dw = 0.25 * np.angle(fo_estimate_sum(y[:, n_cma // 2:n_cma], p.mod)) if p.fo_track else 0.0
     dw_own = dw
     if follow is not None:
         dw = follow["acq_dw"]
@@ -423,7 +444,7 @@ def equalize(u: np.ndarray, p: RxParams, trace: dict | None = None,
             for k0 in range(ks, ke, Bu):
                 k1 = min(k0 + Bu, ke)
                 y[:, k0:k1], hh = lms_step(hh, win.taps_input(k0, k1, T, c), "dd", p, phis)
-            acc += fo_estimate_sum(y[:, ks:ke])
+            acc += fo_estimate_sum(y[:, ks:ke], p.mod)
             h_last = hh
         r = 0.25 * np.angle(acc) if p.fo_track else 0.0
         if trace is not None:

@@ -84,15 +84,25 @@ __device__ __forceinline__ float2 w16(int e) {
   }
 }
 
+// W_32^k = exp(-2 pi i k / 32), k = 0..15
+__device__ __forceinline__ float2 w32(int k) {
+  const float c[16] = {1.f, 0.98078528040323043f, 0.92387953251128674f, 0.83146961230254524f,
+                       0.70710678118654752f, 0.55557023301960218f, 0.38268343236508978f, 0.19509032201612827f,
+                       0.f, -0.19509032201612827f, -0.38268343236508978f, -0.55557023301960218f,
+                       -0.70710678118654752f, -0.83146961230254524f, -0.92387953251128674f, -0.98078528040323043f};
+  return make_float2(c[k], -c[(k + 8) & 15] * (k < 8 ? 1.f : -1.f));
+}
+
 // In-register DFT of R points, v[0..R-1] in natural order, result in natural order.
-// Sizes 8 and 16 split as N1 x 4 (n = n1 + N1 n2, k = 4 k1 + k2).
+// Sizes 8, 16, 32 split as N1 x N2 (n = n1 + N1 n2, k = N2 k1 + k2): inner DFTs
+// of size N2 over n2, twiddles W_R^{n1 k2}, outer DFTs of size N1 over n1.
 template <int R>
 __device__ __forceinline__ void dft(float2 *v) {
-  if (R == 2) {
+  if constexpr (R == 2) {
     dft2(v[0], v[1]);
-  } else if (R == 4) {
+  } else if constexpr (R == 4) {
     dft4(v[0], v[1], v[2], v[3]);
-  } else if (R == 8) {
+  } else if constexpr (R == 8) {
     float2 Y[2][4];
 #pragma unroll
     for (int n1 = 0; n1 < 2; ++n1) {
@@ -108,7 +118,7 @@ __device__ __forceinline__ void dft(float2 *v) {
       v[k2] = a;
       v[4 + k2] = b;
     }
-  } else {  // 16
+  } else if constexpr (R == 16) {
     float2 Y[4][4];
 #pragma unroll
     for (int n1 = 0; n1 < 4; ++n1) {
@@ -124,6 +134,22 @@ __device__ __forceinline__ void dft(float2 *v) {
       dft4(Y[0][k2], Y[1][k2], Y[2][k2], Y[3][k2]);
       v[k2] = Y[0][k2]; v[4 + k2] = Y[1][k2]; v[8 + k2] = Y[2][k2]; v[12 + k2] = Y[3][k2];
     }
+  } else {  // 32 = 2 x 16
+    float2 A[16], Bv[16];
+#pragma unroll
+    for (int n2 = 0; n2 < 16; ++n2) {
+      A[n2] = v[2 * n2];
+      Bv[n2] = v[2 * n2 + 1];
+    }
+    dft<16>(A);
+    dft<16>(Bv);
+#pragma unroll
+    for (int k2 = 1; k2 < 16; ++k2) Bv[k2] = cmul(Bv[k2], w32(k2));
+#pragma unroll
+    for (int k2 = 0; k2 < 16; ++k2) {
+      v[k2] = cadd(A[k2], Bv[k2]);
+      v[16 + k2] = csub(A[k2], Bv[k2]);
+    }
   }
 }
 
@@ -132,14 +158,16 @@ __device__ __forceinline__ int pad(int i) { return i + (i >> 5); }
 
 // One radix-R Stockham pass (Govindaraju et al., SC'08 formulation): butterfly
 // j reads elements j + r N/R, applies W_{Ns R}^{r (j mod Ns)}, does an R-point
-// DFT and writes element r to (j / Ns) Ns R + (j mod Ns) + r Ns.
-template <int N, int R, int Ns>
+// DFT and writes element r to (j / Ns) Ns R + (j mod Ns) + r Ns.  Each of the
+// N / VPT threads of a transform owns VPT / R butterflies and keeps their
+// values in registers across the barrier (in-place pass).
+template <int N, int VPT, int R, int Ns>
 __device__ __forceinline__ void fft_pass(float2 *buf, int t, const float2 *__restrict__ tw) {
-  constexpr int NB = N / R, PER = 16 / R, TW = N / (Ns * R);
+  constexpr int NB = N / R, PER = VPT / R, TW = N / (Ns * R), TPP = N / VPT;
   float2 v[PER][R];
 #pragma unroll
   for (int q = 0; q < PER; ++q) {
-    const int j = t + q * (N / 16);
+    const int j = t + q * TPP;
     const int jm = j & (Ns - 1);
 #pragma unroll
     for (int r = 0; r < R; ++r) {
@@ -152,7 +180,7 @@ __device__ __forceinline__ void fft_pass(float2 *buf, int t, const float2 *__res
   __syncthreads();
 #pragma unroll
   for (int q = 0; q < PER; ++q) {
-    const int j = t + q * (N / 16);
+    const int j = t + q * TPP;
     const int jm = j & (Ns - 1);
     const int d = (j / Ns) * Ns * R + jm;
 #pragma unroll
@@ -161,30 +189,41 @@ __device__ __forceinline__ void fft_pass(float2 *buf, int t, const float2 *__res
   __syncthreads();
 }
 
-template <int N>
+template <int N, int VPT>
 __device__ __forceinline__ void fft_forward(float2 *buf, int t, const float2 *tw) {
-  fft_pass<N, 16, 1>(buf, t, tw);
-  fft_pass<N, 16, 16>(buf, t, tw);
-  if (N == 512) fft_pass<N, 2, 256>(buf, t, tw);
-  if (N == 1024) fft_pass<N, 4, 256>(buf, t, tw);
-  if (N == 2048) fft_pass<N, 8, 256>(buf, t, tw);
-  if (N >= 4096) fft_pass<N, 16, 256>(buf, t, tw);
-  if (N == 8192) fft_pass<N, 2, 4096>(buf, t, tw);
+  if constexpr (N == 16384) {  // 16 x 16 x 16 x 4
+    fft_pass<N, VPT, 16, 1>(buf, t, tw);
+    fft_pass<N, VPT, 16, 16>(buf, t, tw);
+    fft_pass<N, VPT, 16, 256>(buf, t, tw);
+    fft_pass<N, VPT, 4, 4096>(buf, t, tw);
+  } else {
+    fft_pass<N, VPT, 16, 1>(buf, t, tw);
+    fft_pass<N, VPT, 16, 16>(buf, t, tw);
+    if constexpr (N == 512) fft_pass<N, VPT, 2, 256>(buf, t, tw);
+    if constexpr (N == 1024) fft_pass<N, VPT, 4, 256>(buf, t, tw);
+    if constexpr (N == 2048) fft_pass<N, VPT, 8, 256>(buf, t, tw);
+    if constexpr (N >= 4096) fft_pass<N, VPT, 16, 256>(buf, t, tw);
+    if constexpr (N == 8192) fft_pass<N, VPT, 2, 4096>(buf, t, tw);
+  }
 }
 
-template <int N>
-__global__ void __launch_bounds__(N / 8) cdc_kernel(
+// One CTA per window (both polarisations, SPLIT = false) or per (window, pol)
+// (SPLIT = true, blockIdx.y = pol) for the large transforms.
+template <int N, int VPT, bool SPLIT>
+__global__ void __launch_bounds__((SPLIT ? 1 : 2) * N / VPT) cdc_kernel(
     int V, const uint8_t *__restrict__ tail, int64_t tail_first, int64_t tail_n,
     const uint8_t *__restrict__ call, int64_t call_first, int64_t call_n, int dtype, float scale,
     const float2 *__restrict__ H, const float2 *__restrict__ tw, float2 *__restrict__ u,
     int64_t u_base, int64_t u_stride, int64_t win_first, int64_t n_total) {
   extern __shared__ float2 smem[];
   constexpr int PADN = N + N / 32;
+  constexpr int TPP = N / VPT;  // threads per transform
   const int S = N - V;
   const int64_t i = win_first + blockIdx.x;
   const int64_t lo = i * S - V / 2;
+  const int psplit = SPLIT ? (int)blockIdx.y : 0;
   float2 *b0 = smem, *b1 = smem + PADN;
-  // ingest: both pols from one 4-scalar sample-time
+  // ingest: one 4-scalar sample-time gives both pols
   for (int m = threadIdx.x; m < N; m += blockDim.x) {
     const int64_t n = lo + m;
     float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -200,40 +239,46 @@ __global__ void __launch_bounds__(N / 8) cdc_kernel(
         x = reinterpret_cast<const float4 *>(src)[off];
       }
     }
-    b0[pad(m)] = make_float2(x.x * scale, x.y * scale);
-    b1[pad(m)] = make_float2(x.z * scale, x.w * scale);
+    if (SPLIT) {
+      b0[pad(m)] = psplit ? make_float2(x.z * scale, x.w * scale) : make_float2(x.x * scale, x.y * scale);
+    } else {
+      b0[pad(m)] = make_float2(x.x * scale, x.y * scale);
+      b1[pad(m)] = make_float2(x.z * scale, x.w * scale);
+    }
   }
   __syncthreads();
-  const int pol = threadIdx.x / (N / 16);
-  const int t = threadIdx.x % (N / 16);
-  float2 *buf = pol ? b1 : b0;
-  fft_forward<N>(buf, t, tw);
+  const int pol = SPLIT ? psplit : threadIdx.x / TPP;
+  const int t = threadIdx.x % TPP;
+  float2 *buf = (!SPLIT && pol) ? b1 : b0;
+  fft_forward<N, VPT>(buf, t, tw);
   // multiply by H/N and conjugate (inverse via the forward transform)
-#pragma unroll
-  for (int q = 0; q < 16; ++q) {
-    const int k = t + q * (N / 16);
+  // a full unroll at VPT = 32 makes the register allocator spill heavily
+#pragma unroll(VPT > 16 ? 2 : VPT)
+  for (int q = 0; q < VPT; ++q) {
+    const int k = t + q * TPP;
     buf[pad(k)] = cconj(cmul(buf[pad(k)], __ldg(&H[k])));
   }
   __syncthreads();
-  fft_forward<N>(buf, t, tw);
+  fft_forward<N, VPT>(buf, t, tw);
   float2 *out = u + (int64_t)pol * u_stride;
-  for (int tt = V / 2 + t; tt < V / 2 + S; tt += N / 16) {
+  for (int tt = V / 2 + t; tt < V / 2 + S; tt += TPP) {
     const int64_t n = i * S + (tt - V / 2);
     if (n_total >= 0 && n >= n_total) break;
     out[n - u_base] = cconj(buf[pad(tt)]);
   }
 }
 
-template <int N>
+template <int N, int VPT, bool SPLIT>
 static cudaError_t launch_cdc_n(int V, const void *tail, int64_t tail_first, int64_t tail_n,
                                 const void *call, int64_t call_first, int64_t call_n, int dtype,
                                 float scale, const float2 *H, const float2 *tw, float2 *u,
                                 int64_t u_base, int64_t u_stride, int64_t win_first,
                                 int64_t win_count, int64_t n_total, cudaStream_t s) {
-  const size_t sm = 2 * (N + N / 32) * sizeof(float2);
-  cudaError_t e = cudaFuncSetAttribute(cdc_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  const size_t sm = (SPLIT ? 1 : 2) * (N + N / 32) * sizeof(float2);
+  cudaError_t e = cudaFuncSetAttribute(cdc_kernel<N, VPT, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
-  cdc_kernel<N><<<(unsigned)win_count, N / 8, sm, s>>>(
+  dim3 grid((unsigned)win_count, SPLIT ? 2 : 1);
+  cdc_kernel<N, VPT, SPLIT><<<grid, (SPLIT ? 1 : 2) * N / VPT, sm, s>>>(
       V, (const uint8_t *)tail, tail_first, tail_n, (const uint8_t *)call, call_first, call_n,
       dtype, scale, H, tw, u, u_base, u_stride, win_first, n_total);
   return cudaGetLastError();
@@ -245,17 +290,19 @@ cudaError_t launch_cdc(int N, int V, const void *tail, int64_t tail_first, int64
                        int64_t u_base, int64_t u_stride, int64_t win_first, int64_t win_count,
                        int64_t n_total, cudaStream_t s) {
   if (win_count <= 0) return cudaSuccess;
-#define RX_CDC_CASE(NN)                                                                     \
-  case NN:                                                                                  \
-    return launch_cdc_n<NN>(V, tail, tail_first, tail_n, call, call_first, call_n, dtype,   \
-                            scale, H, tw, u, u_base, u_stride, win_first, win_count, n_total, s);
+#define RX_CDC_CASE(NN, VPT, SPLIT)                                                                \
+  case NN:                                                                                         \
+    return launch_cdc_n<NN, VPT, SPLIT>(V, tail, tail_first, tail_n, call, call_first, call_n,     \
+                                        dtype, scale, H, tw, u, u_base, u_stride, win_first,       \
+                                        win_count, n_total, s);
   switch (N) {
-    RX_CDC_CASE(256)
-    RX_CDC_CASE(512)
-    RX_CDC_CASE(1024)
-    RX_CDC_CASE(2048)
-    RX_CDC_CASE(4096)
-    RX_CDC_CASE(8192)
+    RX_CDC_CASE(256, 16, false)
+    RX_CDC_CASE(512, 16, false)
+    RX_CDC_CASE(1024, 16, false)
+    RX_CDC_CASE(2048, 16, false)
+    RX_CDC_CASE(4096, 16, false)
+    RX_CDC_CASE(8192, 16, true)
+    RX_CDC_CASE(16384, 32, true)
     default: return cudaErrorInvalidValue;
   }
 #undef RX_CDC_CASE

@@ -22,8 +22,9 @@
 //     the taps at the end of the last segment of wave w-1, pre-trains on the W
 //     symbols before it, then equalises its own symbols.  A bounded grid
 //     barrier closes each wave; one warp per CTA then folds the 4th-power sums
-//     (fixed order, FP64) into the tracker: dw += r/16,
-//     Phi = Phi + 2PS dw/2 reduced to [-pi, pi].
+//     (fixed order, double-float) into the tracker: dw += r/16,
+//     Phi = Phi + 2PS dw/2, both held as 64-bit fixed-point turns so that
+//     the modular phase sum is exact.
 //
 // One update block of B_u <= 32 symbols; warp w owns symbols 8w..8w+7 and
 // lane 4j + part works on symbol j of its warp with part = (input pol q, tap
@@ -40,10 +41,12 @@
 //      (e conj(u)), a reduce-scatter leaves tap 8 half + j in lane (j, part);
 //      CTA barrier; each lane adds the 4 warp partials of its tap, updates it
 //      and the 8 taps of each FIR lane are gathered back by shuffles.
-// Frequency pairs accumulate in compensated (Kahan) FP32 per lane and are
-// summed in FP64 per segment.  The input window of a chunk of up to 1152
-// symbols sits in shared memory (rows padded against bank conflicts), rotated
-// by exp(-j phi_n) from a 64-bit fixed-point phase; Phi and dw are FP64.
+// Frequency pairs (y_k conj(y_{k-1}))^4, for 16QAM weighted by the ring
+// weights of both symbols, accumulate in compensated (Kahan) FP32 per lane and
+// are summed as double-float per segment.  The input window of a chunk of up
+// to 1152 symbols sits in shared memory (rows padded against bank conflicts),
+// rotated by exp(-j phi_n) from the 64-bit fixed-point phase through a
+// 256-entry phasor table and a short Taylor polynomial.
 #include <math.h>
 
 #include "common.cuh"
@@ -229,6 +232,13 @@ __device__ __forceinline__ void gather_taps(float2 (&h)[8], float2 own, const La
   }
 }
 
+// Weight of a 16QAM symbol of power a = |y|^2 in the frequency estimate: 0 on the
+// middle ring (|s|^2 = 1, not pi/4-aligned), 1 from |a - 1| >= 0.4 (the inner
+// and outer rings), linear in between so that the estimate is continuous.
+__device__ __forceinline__ float ring_weight(float a) {
+  return fminf(fmaxf((fabsf(a - 1.f) - 0.2f) * 5.f, 0.f), 1.f);
+}
+
 template <int MB>
 __device__ __forceinline__ void run_span(const Hot hot, EqSmem &sm, const Span sp, const Lane &ln,
                                          float2 &own, float2 (&h)[8], Kahan &fo, int64_t n_limit) {
@@ -290,7 +300,12 @@ __device__ __forceinline__ void run_span(const Hot hot, EqSmem &sm, const Span s
         float2 yp = ln.j > 0 ? make_float2(yupx, yupy) : (ln.warp > 0 ? yw : yprev_last);
         const float2 v = cmulc(yv, yp);
         const float2 v2 = cmul(v, v);
-        const float2 v4 = cmul(v2, v2);
+        float2 v4 = cmul(v2, v2);
+        if (MB == 4) {  // 16QAM: keep the pi/4-aligned inner and outer rings (soft edge)
+          const float wk = ring_weight(yv.x * yv.x + yv.y * yv.y);
+          const float wp = ring_weight(yp.x * yp.x + yp.y * yp.y);
+          v4 = cscale(v4, wk * wp);
+        }
         kahan_add(fo.sx, fo.cx, fo_on ? v4.x : 0.f);   // a select: stale inputs cannot leak
         kahan_add(fo.sy, fo.cy, fo_on ? v4.y : 0.f);
       };

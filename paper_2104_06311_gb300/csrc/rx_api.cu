@@ -145,10 +145,12 @@ rx_status resolve(rx_stream *rx) {
   int N = rx->fft_n_req;
   if (N == 0) {
     N = 1024;
-    while (N < 4 * V) N *= 2;
+    while (N < 4 * V && N < 16384) N *= 2;
   }
-  if (!is_pow2(N) || N < 256 || N > 8192)
-    return fail(rx, RX_EUNSUPPORTED, "FFT size must be a power of two in [256, 8192] (dispersion too large for the single-CTA FFT)");
+  if (!is_pow2(N) || N < 256 || N > 16384)
+    return fail(rx, RX_EUNSUPPORTED, "FFT size must be a power of two in [256, 16384] (dispersion too large for the single-CTA FFT)");
+  if (rx->overlap_req == 0 && rx->fft_n_req == 0 && V >= N / 2)
+    return fail(rx, RX_EUNSUPPORTED, "dispersion too large: the overlap it needs does not fit below half of the largest FFT size (16384)");
   if (V % 32 != 0 || V < 0 || V >= N / 2)
     return fail(rx, RX_EINVAL, "overlap must be a multiple of 32 below N/2");
   if (rx->Bu < 1 || rx->Bu > 32) return fail(rx, RX_EUNSUPPORTED, "update block must be 1..32");
@@ -399,6 +401,7 @@ rx_status rx_set_param(rx_stream *rx, int key, double v) {
   }
   if (s != RX_OK) return s;
   if (needs_realloc) release(rx);  // layout-changing parameter: re-reserve on next use
+  rx->N = 0;                       // and re-resolve the layout on the next query
   return RX_OK;
 }
 

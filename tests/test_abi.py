@@ -58,7 +58,8 @@ def test_create_rejects_bad_arguments(lib):
 
 
 @pytest.mark.parametrize("L_km,baud,N,V", [(1000, 10e9, 1024, 64), (10000, 10e9, 4096, 544),
-                                           (2000, 32e9, 8192, 1120), (0, 10e9, 1024, 32)])
+                                           (2000, 32e9, 8192, 1120), (0, 10e9, 1024, 32),
+                                           (6000, 32e9, 16384, 3360), (10000, 32e9, 16384, 5600)])
 def test_parameter_resolution_on_host(lib, L_km, baud, N, V):
     from paper_2104_06311_gb300 import rx
     st, h = _create(lib, baud, 2, float(L_km), 17.0, 15, 32)
@@ -71,9 +72,12 @@ def test_parameter_resolution_on_host(lib, L_km, baud, N, V):
 
 def test_dispersion_beyond_single_cta_fft_is_reported(lib):
     from paper_2104_06311_gb300 import rx
-    st, h = _create(lib, 32e9, 2, 6000.0, 17.0, 15, 32)   # N_CD 3349 -> N 16384
+    st, h = _create(lib, 32e9, 2, 20000.0, 17.0, 15, 32)   # N_CD 11161 -> V 11168 > 16384 / 2
     assert st == rx.RX_OK
     v = ct.c_double()
+    assert lib.rx_get_param(h, rx.PARAMS["FFT_N"], ct.byref(v)) == rx.RX_EUNSUPPORTED
+    assert b"dispersion too large" in lib.rx_last_error(h)
+    assert lib.rx_set_param(h, rx.PARAMS["FFT_N"], 32768.0) == rx.RX_OK
     assert lib.rx_get_param(h, rx.PARAMS["FFT_N"], ct.byref(v)) == rx.RX_EUNSUPPORTED
     assert b"FFT size" in lib.rx_last_error(h)
     lib.rx_destroy(h)

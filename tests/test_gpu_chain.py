@@ -152,7 +152,18 @@ def test_16qam_parity():
     print("16qam parity", rep)
 
 
-@pytest.mark.parametrize("N", [256, 512, 2048, 4096])
+def test_c3_16qam_6000km_parity():
+    """DP-16QAM 32 GBd over 6000 km (N_CD 3349 -> V 3360, N 16384: one CTA per window and pol)."""
+    lk = L.workload("c3", n_sym=1 << 16)
+    g = L.generate(lk)
+    p = rx_params(lk, g.in_scale)
+    assert p.fft_n == 16384 and p.overlap == 3360
+    gpu = run_gpu(p, g.samples)
+    rep, _ = check_chain(p, g, gpu, {})
+    print("c3 parity", rep)
+
+
+@pytest.mark.parametrize("N", [256, 512, 2048, 4096, 8192, 16384])
 def test_cdc_fft_sizes(N):
     lk = L.Link(n_sym=20000 + 123, L_km=300.0, snr_db=15.0, seed=77 + N)
     g = L.generate(lk)

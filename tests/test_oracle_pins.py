@@ -219,6 +219,44 @@ def test_fo_estimator_unbiased_at_c2_snr():
     assert np.all(np.abs(ests - dw) < 0.06 * dw)
 
 
+def test_ring_weight_keeps_inner_and_outer_16qam_rings():
+    a = np.array([0.2, 1.8, 1.0, 0.8, 1.2, 1.3, 0.7, 0.6, 1.4, 0.0, 3.0])
+    assert np.allclose(O.ring_weight(a), [1, 1, 0, 0, 0, 0.5, 0.5, 1, 1, 1, 1], atol=1e-12)
+
+
+def test_fo_estimator_16qam_exact_noise_free():
+    # the inner and outer rings are pi/4-aligned and the middle ring weighs 0, so a
+    # noise-free 16QAM stream gives the offset exactly; with the middle ring included
+    # the estimate is biased
+    rng = np.random.default_rng(5)
+    K = 1 << 12
+    s = L.map_symbols(L.random_bits(19, 2 * 4 * K).reshape(2, -1), "16qam")
+    dw = -0.0418
+    y = s * np.exp(1j * (dw * np.arange(K) + rng.uniform(0, 6, (2, 1))))
+    assert abs(0.25 * np.angle(O.fo_estimate_sum(y, "16qam")) - dw) < 1e-12
+    assert abs(0.25 * np.angle(O.fo_estimate_sum(y, "qpsk")) - dw) > 3e-4
+
+
+def test_fo_estimator_16qam_spread_at_18db():
+    # 2^14 symbols per pol at Es/N0 = 18 dB, 32 independent draws: the ring-weighted
+    # estimate is unbiased (mean within 1e-3 rad of the offset, about 3 standard
+    # errors) and spreads about a third as much as the unweighted 4th-power sum,
+    # whose middle-ring self-noise dominates
+    K = 1 << 14
+    dw = 0.02
+    sig = math.sqrt(10 ** (-1.8) / 2)
+    ests, raw = [], []
+    for seed in range(32):
+        rng = np.random.default_rng(700 + seed)
+        s = L.map_symbols(L.random_bits(3000 + seed, 2 * 4 * K).reshape(2, -1), "16qam")
+        y = s * np.exp(1j * dw * np.arange(K)) + sig * (rng.standard_normal((2, K)) + 1j * rng.standard_normal((2, K)))
+        ests.append(0.25 * np.angle(O.fo_estimate_sum(y, "16qam")))
+        raw.append(0.25 * np.angle(O.fo_estimate_sum(y, "qpsk")))
+    ests, raw = np.array(ests) - dw, np.array(raw) - dw
+    assert abs(ests.mean()) < 1e-3 and np.all(np.abs(ests) < 8e-3)
+    assert raw.std() > 2 * ests.std()
+
+
 # --------------------------------------------------------------- BPS + unwrap
 def _qpsk(K, seed):
     return L.map_symbols(L.random_bits(seed, 2 * 2 * K).reshape(2, -1), "qpsk")
