@@ -330,3 +330,25 @@ def workload(name: str, n_sym: int | None = None) -> Link:
     if n_sym is not None:
         lk = dataclasses.replace(lk, n_sym=n_sym)
     return lk
+
+
+def workload_batch(n_ch: int = 64, seed: int = 2104063114, log2_len=(18.0, 22.0), L_km=(2000.0, 10000.0),
+                   baud=(10e9, 32e9), snr_db=(10.0, 18.0), len_quantum: int = 1 << 15) -> list:
+    """Independent WDM channels of uneven length, symbol rate, dispersion and format.
+
+    Per channel (drawn from a PCG64 stream seeded with `seed`): length 2^u
+    symbols per pol with u ~ U[log2_len] rounded to a multiple of len_quantum,
+    L ~ U[L_km], baud ~ U[baud], QPSK or 16QAM with probability 1/2 each,
+    SNR ~ U[snr_db], a random fixed Jones rotation, int8 ADC, and its own bit
+    seed seed + ch.  No inter-channel crosstalk, phase noise or frequency offset.
+    """
+    rng = np.random.default_rng(np.random.PCG64(seed))
+    links = []
+    for ch in range(n_ch):
+        u = rng.uniform(*log2_len)
+        n_sym = max(len_quantum, int(round(2.0 ** u / len_quantum)) * len_quantum)
+        links.append(Link(mod="16qam" if rng.uniform() < 0.5 else "qpsk", baud=float(rng.uniform(*baud)),
+                          n_sym=n_sym, L_km=float(rng.uniform(*L_km)),
+                          jones=(float(rng.uniform(0, math.pi)), float(rng.uniform(0, 2 * math.pi))),
+                          snr_db=float(rng.uniform(*snr_db)), adc="int8", seed=seed + ch))
+    return links

@@ -1,0 +1,682 @@
+// Batched form: many independent channels through the receiver chain in one
+// enqueue (declared in rx_batch.h).
+//
+// The paper fills its GPU by running many sample buffers on parallel CUDA
+// streams, ordered by events where the sequential LMS state crosses buffers
+// (arXiv 2104.06311, Section "Experimental setup", processing-chain
+// paragraph).  Across independent channels there is no such dependency, so
+// the GB300 form runs them side by side inside single launches:
+//
+//   CDC      one overlap-save launch per channel (each thousands of windows),
+//            FFT size per channel from the autotuner below;
+//   EQ       ONE persistent cooperative launch for all channels: channel c
+//            owns a team of CTAs (an even count, two butterfly rows per
+//            segment slot) that runs its acquisition and its segment waves
+//            and synchronises on the channel's own barrier words;
+//   BPS      pass 1 / unwrap scan / demap launches per channel;
+// all enqueued on the bound stream and, from the second call with the same
+// pointers and sizes, replayed from a captured CUDA graph.
+//
+// Autotuner.  The CDC kernel's cost per window depends on the FFT size N
+// only; a channel with overlap V keeps N - V output samples per window.  The
+// first batch on a device times the CDC kernel for every N in 256..16384 on
+// synthetic windows (CUDA events, best of three) and caches ns per window;
+// each channel then takes the admissible N (V < N/2) with the least time per
+// output sample.  Team sizes come from a cost model of the equaliser
+// schedule: a channel's time is its acquisition (A / B_u update steps, one
+// CTA pair) plus, per wave, ceil(P / pairs) passes of (S + W) / B_u steps and
+// a fixed wave overhead; pairs go one at a time to the channel whose time is
+// currently largest, within the co-resident CTA budget of the launch.
+#include <string.h>
+
+#include <algorithm>
+#include <map>
+#include <mutex>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "../../include/rx_batch.h"
+#include "rx_internal.h"
+
+using namespace rx;
+
+namespace {
+
+// chain defaults (the rx.h defaults)
+constexpr int kS = 1024, kW = 128, kBu = 32, kNb = 16;
+constexpr int64_t kNcma = 8192, kAcqMin = 16384, kBlockSamples = 65536;
+constexpr double kMu = 1e-3, kRolloff = 0.1, kLamNm = 1550.0, kFoSmooth = 16.0;
+constexpr int kMaxChannels = 4096;
+constexpr int kWaveOverheadSteps = 8;   // cost model: grid barrier + FO fold per wave
+
+struct Chan {
+  rx_chan_cfg cfg;
+  int N = 0, V = 0, P = 0, C = 256, team = 2;
+  int64_t A_full = 0, span = 0, n_cap = 0, K_cap = 0;
+  int64_t u_stride = 0, y_stride = 0, chunk_cap = 0, region_cap = 0, trace_cap = 0;
+  double ns_per_sample = 0;
+  float2 *H = nullptr, *tw = nullptr, *u = nullptr, *y = nullptr, *tap_slot = nullptr;
+  int8_t *bh = nullptr;
+  int *chunk_r = nullptr;
+  float *chunk_s2 = nullptr;
+  int64_t *chunk_m = nullptr;
+  double *region_s2 = nullptr;
+  EqState *st = nullptr;
+  float4 *fo_part = nullptr;
+  float *trace = nullptr;
+  double *trace_fo = nullptr;
+};
+
+std::mutex g_tune_mu;
+std::map<std::pair<int, int>, double> g_tune;   // (device, N) -> ns per window
+
+__global__ void batch_init_kernel(const EqLaunch *__restrict__ Ls) {
+  const EqLaunch &L = Ls[blockIdx.x];
+  const int c = (L.T - 1) / 2;
+  float2 *taps = &L.st->taps[0][0][0];
+  for (int i = threadIdx.x; i < 4 * kMaxTaps; i += blockDim.x) {
+    const int pq = i / kMaxTaps, tap = i % kMaxTaps;
+    taps[i] = make_float2((tap == c && (pq == 0 || pq == 3)) ? 1.f : 0.f, 0.f);
+  }
+  for (int64_t i = threadIdx.x; i < 2 * L.trace_cap; i += blockDim.x) L.trace_fo[i] = 0.0;
+  if (threadIdx.x == 0) {
+    L.st->dw = 0.0;
+    L.st->Phi = 0.0;
+    L.st->Phi_q = 0ull;
+    L.st->delta_q = 0ll;
+    L.st->next_wave = 0;
+    L.st->acq_done = 0;
+    L.barrier[0] = 0u;
+    L.barrier[1] = 0u;
+  }
+}
+
+}  // namespace
+
+struct rx_batch {
+  int n_ch = 0;
+  std::vector<Chan> ch;
+  cudaStream_t stream = nullptr;
+  cudaStream_t cap_stream = nullptr;         // graph capture only
+  bool use_graph = true;
+  int eq_ctas = 0, pad_smem = 0;
+  EqLaunch *d_L = nullptr, *h_L = nullptr;   // h_L: pinned host copy source
+  int2 *d_team = nullptr;
+  unsigned *barriers = nullptr;              // [n_ch][2]
+  int64_t *m_carry = nullptr;                // [n_ch][2]
+  int *err = nullptr, *h_err = nullptr;
+  cudaEvent_t err_ev = nullptr;
+  unsigned *ber_counts = nullptr;
+  unsigned long long *ber_acc = nullptr;
+  int *ber_sync = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  std::vector<int64_t> sig, gsig, hsig;      // last eager call / captured graph / launch table
+  bool processed = false;
+  std::string msg;
+  std::vector<void *> allocs;
+};
+
+namespace {
+
+rx_status bfail(rx_batch *b, rx_status s, const std::string &m) {
+  if (b) b->msg = m;
+  return s;
+}
+
+rx_status bcuda(rx_batch *b, cudaError_t e, const char *where) {
+  return bfail(b, RX_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define BX_CUDA(call, where)                                  \
+  do {                                                        \
+    cudaError_t e_ = (call);                                  \
+    if (e_ != cudaSuccess) return bcuda(b, e_, where);        \
+  } while (0)
+
+template <class Tp>
+rx_status balloc(rx_batch *b, Tp **p, size_t count) {
+  void *q = nullptr;
+  const cudaError_t e = cudaMalloc(&q, std::max<size_t>(count, 1) * sizeof(Tp));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return bfail(b, RX_ENOMEM, "device allocation failed");
+  }
+  b->allocs.push_back(q);
+  *p = static_cast<Tp *>(q);
+  return RX_OK;
+}
+
+void release(rx_batch *b) {
+  if (b->gexec) cudaGraphExecDestroy(b->gexec);
+  b->gexec = nullptr;
+  for (void *p : b->allocs) cudaFree(p);
+  b->allocs.clear();
+  if (b->h_L) cudaFreeHost(b->h_L);
+  if (b->h_err) cudaFreeHost(b->h_err);
+  if (b->err_ev) cudaEventDestroy(b->err_ev);
+  if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+  b->cap_stream = nullptr;
+  b->h_L = nullptr;
+  b->h_err = nullptr;
+  b->err_ev = nullptr;
+}
+
+rx_status check_cfg(rx_batch *b, int i, const rx_chan_cfg &c) {
+  const std::string who = "channel " + std::to_string(i) + ": ";
+  if (!(c.baud > 0) || !(c.L_km >= 0) || c.D_ps_nm_km != c.D_ps_nm_km || !(c.in_scale > 0))
+    return bfail(b, RX_EINVAL, who + "baud, L_km, D or in_scale out of range");
+  if (c.max_samples <= 0 || c.max_samples % 2) return bfail(b, RX_EINVAL, who + "max_samples must be even and positive");
+  if (c.mod_bits != 2 && c.mod_bits != 4) return bfail(b, RX_EUNSUPPORTED, who + "mod_bits must be 2 or 4");
+  if (c.ntaps < 3 || c.ntaps > 15 || c.ntaps % 2 == 0) return bfail(b, RX_EUNSUPPORTED, who + "ntaps must be odd, 3..15");
+  if (c.fft_n != 0 && (!is_pow2(c.fft_n) || c.fft_n < 256 || c.fft_n > 16384))
+    return bfail(b, RX_EUNSUPPORTED, who + "FFT size must be a power of two in [256, 16384]");
+  if (c.overlap < 0 || c.overlap % 32) return bfail(b, RX_EINVAL, who + "overlap must be a multiple of 32");
+  return RX_OK;
+}
+
+// ns per CDC window for every FFT size, measured once per device.
+rx_status tune_table(rx_batch *b, std::map<int, double> &out) {
+  int dev = 0, sms = 0;
+  BX_CUDA(cudaGetDevice(&dev), "device");
+  BX_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "device");
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  for (int N = 256; N <= 16384; N *= 2) {
+    auto it = g_tune.find({dev, N});
+    if (it != g_tune.end()) {
+      out[N] = it->second;
+      continue;
+    }
+    const int V = 32;
+    const int64_t nw = 8LL * sms;                  // windows per timed launch
+    const int64_t n = nw * (N - V);                // sample-times those windows cover
+    void *in = nullptr, *uu = nullptr, *H = nullptr, *tw = nullptr;
+    cudaError_t e = cudaMalloc(&in, (size_t)(n + N) * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&uu, (size_t)2 * n * sizeof(float2));
+    if (e == cudaSuccess) e = cudaMalloc(&H, (size_t)N * sizeof(float2));
+    if (e == cudaSuccess) e = cudaMalloc(&tw, (size_t)N * sizeof(float2));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    if (e == cudaSuccess) e = cudaMemsetAsync(in, 0, (size_t)(n + N) * 4, b->stream);
+    if (e == cudaSuccess) e = launch_tables((float2 *)H, (float2 *)tw, N, 10e9, 0.0, 17.0, kLamNm, kRolloff, b->stream);
+    float best = 1e30f;
+    for (int r = 0; r < 4 && e == cudaSuccess; ++r) {
+      e = cudaEventRecord(e0, b->stream);
+      if (e == cudaSuccess)
+        e = launch_cdc(N, V, nullptr, 0, 0, in, 0, n, RX_I8x4, 1.f, (const float2 *)H, (const float2 *)tw,
+                       (float2 *)uu, 0, n, 0, nw, n, b->stream);
+      if (e == cudaSuccess) e = cudaEventRecord(e1, b->stream);
+      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      float ms = 0.f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+      if (e == cudaSuccess && r > 0) best = std::min(best, ms);   // r = 0 warms up
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(in);
+    cudaFree(uu);
+    cudaFree(H);
+    cudaFree(tw);
+    if (e != cudaSuccess) return bcuda(b, e, "autotuner");
+    const double ns = (double)best * 1e6 / (double)nw;
+    g_tune[{dev, N}] = ns;
+    out[N] = ns;
+  }
+  return RX_OK;
+}
+
+double eq_cost(const Chan &c, int pairs) {
+  const int64_t A = std::min(c.A_full, c.K_cap);
+  const int64_t n_seg = c.K_cap > A ? (c.K_cap - A + kS - 1) / kS : 0;
+  const int64_t waves = (n_seg + c.P - 1) / c.P;
+  const int64_t passes = (c.P + pairs - 1) / pairs;
+  return (double)(A / kBu) + (double)waves * (double)(passes * ((kS + kW) / kBu) + kWaveOverheadSteps);
+}
+
+rx_status check_device_error(rx_batch *b, bool wait) {
+  if (!b->processed) return RX_OK;
+  if (wait) {
+    BX_CUDA(cudaEventSynchronize(b->err_ev), "error check");
+  } else if (cudaEventQuery(b->err_ev) != cudaSuccess) {
+    cudaGetLastError();   // not ready yet: checked by a later call
+    return RX_OK;
+  }
+  if (*b->h_err != 0) return bfail(b, RX_ETIMEOUT, "a bounded device wait gave up (equaliser team barrier)");
+  return RX_OK;
+}
+
+// Everything one call enqueues (eagerly or under capture).
+rx_status enqueue(rx_batch *b, const rx_in *ins, rx_out *outs, cudaStream_t s) {
+  BX_CUDA(cudaMemcpyAsync(b->d_L, b->h_L, (size_t)b->n_ch * sizeof(EqLaunch), cudaMemcpyHostToDevice, s), "launch table");
+  BX_CUDA(cudaMemsetAsync(b->m_carry, 0, (size_t)2 * b->n_ch * sizeof(int64_t), s), "unwrap carry");
+  batch_init_kernel<<<b->n_ch, 128, 0, s>>>(b->d_L);
+  BX_CUDA(cudaGetLastError(), "state init");
+  for (int i = 0; i < b->n_ch; ++i) {
+    const Chan &c = b->ch[i];
+    const int64_t n = ins[i].n;
+    if (n == 0) continue;
+    const int Sh = c.N - c.V;
+    BX_CUDA(launch_cdc(c.N, c.V, nullptr, 0, 0, ins[i].data, 0, n, ins[i].dtype, (float)c.cfg.in_scale, c.H, c.tw,
+                       c.u, 0, c.u_stride, 0, (n + Sh - 1) / Sh, n, s),
+            "cdc");
+  }
+  BX_CUDA(launch_eq_batch(b->d_L, b->d_team, b->eq_ctas, b->pad_smem, s), "equaliser");
+  for (int i = 0; i < b->n_ch; ++i) {
+    const Chan &c = b->ch[i];
+    const EqLaunch &L = b->h_L[i];
+    const int64_t K = L.K;
+    if (K == 0) continue;
+    BpsLaunch B;
+    memset(&B, 0, sizeof(B));
+    B.y = c.y;
+    B.y_base = 0;
+    B.y_stride = c.y_stride;
+    B.bhat = c.bh;
+    B.bh_base = 0;
+    B.bh_stride = c.y_stride;
+    B.chunk = c.C;
+    B.n_chunks = (K + c.C - 1) / c.C;
+    B.chunk_r = c.chunk_r;
+    B.chunk_s2 = c.chunk_s2;
+    B.chunk_m = c.chunk_m;
+    B.m_carry = b->m_carry + 2 * i;
+    B.region_s2 = c.region_s2;
+    B.k_lo = 0;
+    B.k_hi = K;
+    B.K_end = K;
+    B.A = L.A;
+    B.span = c.span;
+    B.Nb = kNb;
+    B.mod_bits = c.cfg.mod_bits;
+    B.need_s2 = outs[i].llr != nullptr;
+    B.bits = outs[i].bits;
+    B.bits_stride = outs[i].bits_stride;
+    B.llr = outs[i].llr;
+    B.llr_stride = outs[i].llr_stride;
+    B.sym = reinterpret_cast<float2 *>(outs[i].sym);
+    B.sym_stride = outs[i].sym_stride;
+    B.out_first = 0;
+    BX_CUDA(launch_bps(B, s), "bps");
+    if (outs[i].eq)
+      BX_CUDA(launch_copy_cols(reinterpret_cast<float2 *>(outs[i].eq), outs[i].eq_stride, c.y, c.y_stride, K, s), "eq out");
+    if (outs[i].cdc)
+      BX_CUDA(launch_copy_cols(reinterpret_cast<float2 *>(outs[i].cdc), outs[i].cdc_stride, c.u, c.u_stride, ins[i].n, s),
+              "cdc out");
+  }
+  return RX_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+rx_status rx_batch_create(rx_batch **out, int n_ch, const rx_chan_cfg *cfgs) {
+  if (!out) return RX_EINVAL;
+  *out = nullptr;
+  if (n_ch < 1 || n_ch > kMaxChannels || !cfgs) return RX_EINVAL;
+  rx_batch *b = new (std::nothrow) rx_batch();
+  if (!b) return RX_ENOMEM;
+  *out = b;
+  b->n_ch = n_ch;
+  b->ch.resize(n_ch);
+  // ---- per-channel layout (host only)
+  for (int i = 0; i < n_ch; ++i) {
+    Chan &c = b->ch[i];
+    c.cfg = cfgs[i];
+    rx_status s = check_cfg(b, i, c.cfg);
+    if (s != RX_OK) return s;
+    const int64_t ncd = n_cd_taps(c.cfg.baud, 2, c.cfg.L_km, c.cfg.D_ps_nm_km, kLamNm);
+    c.V = c.cfg.overlap ? c.cfg.overlap : (int)std::max<int64_t>(32, ((ncd - 1 + 31) / 32) * 32);
+    if (c.V >= 16384 / 2)
+      return bfail(b, RX_EUNSUPPORTED, "channel " + std::to_string(i) + ": dispersion too large for the largest FFT size (16384)");
+    if (c.cfg.fft_n && c.V >= c.cfg.fft_n / 2)
+      return bfail(b, RX_EINVAL, "channel " + std::to_string(i) + ": overlap must be below N/2");
+    c.P = (int)std::max<int64_t>(1, (kBlockSamples / 2) / kS);
+    c.span = (int64_t)c.P * kS;
+    c.A_full = std::max(kNcma, kAcqMin);
+    c.C = 256;
+    while (c.C > 32 && (c.A_full % c.C != 0 || c.span % c.C != 0)) c.C /= 2;
+    c.n_cap = c.cfg.max_samples;
+    c.K_cap = c.n_cap / 2;
+  }
+  // ---- device side
+  BX_CUDA(cudaStreamSynchronize(b->stream), "create");
+  std::map<int, double> tab;
+  rx_status s = tune_table(b, tab);
+  if (s != RX_OK) return s;
+  for (int i = 0; i < n_ch; ++i) {
+    Chan &c = b->ch[i];
+    if (c.cfg.fft_n) {
+      c.N = c.cfg.fft_n;
+    } else {
+      double best = 1e300;
+      for (const auto &kv : tab) {
+        if (c.V >= kv.first / 2) continue;
+        const double per = kv.second / (double)(kv.first - c.V);
+        if (per < best) {
+          best = per;
+          c.N = kv.first;
+        }
+      }
+    }
+    c.ns_per_sample = tab[c.N] / (double)(c.N - c.V);
+  }
+  // equaliser launch: co-resident CTA budget and teams
+  b->pad_smem = 0;
+  const int budget = eq_batch_max_blocks(b->pad_smem) & ~1;
+  if (budget < 2 * n_ch) {
+    release(b);
+    return bfail(b, RX_EUNSUPPORTED, "more channels than CTA pairs the equaliser launch can keep resident (" +
+                                         std::to_string(budget / 2) + ")");
+  }
+  std::vector<int> pairs(n_ch, 1);
+  int left = budget / 2 - n_ch;
+  while (left > 0) {
+    int pick = -1;
+    double worst = -1;
+    for (int i = 0; i < n_ch; ++i) {
+      if (pairs[i] >= b->ch[i].P) continue;
+      const double t = eq_cost(b->ch[i], pairs[i]);
+      if (t > worst && eq_cost(b->ch[i], pairs[i] + 1) < t) {
+        worst = t;
+        pick = i;
+      }
+    }
+    if (pick < 0) break;
+    ++pairs[pick];
+    --left;
+  }
+  std::vector<int2> team;
+  for (int i = 0; i < n_ch; ++i) {
+    b->ch[i].team = 2 * pairs[i];
+    for (int j = 0; j < 2 * pairs[i]; ++j) team.push_back(make_int2(i, j));
+  }
+  b->eq_ctas = (int)team.size();
+#define BX_ALLOC(ptr, count)                   \
+  do {                                         \
+    rx_status s_ = balloc(b, &(ptr), (count)); \
+    if (s_ != RX_OK) { release(b); return s_; } \
+  } while (0)
+  BX_ALLOC(b->d_L, (size_t)n_ch);
+  BX_ALLOC(b->d_team, team.size());
+  BX_ALLOC(b->barriers, (size_t)2 * n_ch);
+  BX_ALLOC(b->m_carry, (size_t)2 * n_ch);
+  BX_ALLOC(b->err, 1);
+  BX_ALLOC(b->ber_counts, 2 * 2 * 4 * 129);
+  BX_ALLOC(b->ber_acc, 2);
+  BX_ALLOC(b->ber_sync, 6);
+  for (int i = 0; i < n_ch; ++i) {
+    Chan &c = b->ch[i];
+    const int64_t A = std::min(c.A_full, c.K_cap);
+    const int64_t n_seg = c.K_cap > A ? (c.K_cap - A + kS - 1) / kS : 0;
+    const int64_t waves = (n_seg + c.P - 1) / c.P;
+    c.u_stride = c.n_cap + 64;
+    c.y_stride = c.K_cap + 64;
+    c.chunk_cap = (c.K_cap + c.C - 1) / c.C + 16;
+    c.region_cap = (c.K_cap > A ? (c.K_cap - A + c.span - 1) / c.span : 0) + 1 + 16;
+    c.trace_cap = waves + 2;
+    BX_ALLOC(c.H, (size_t)c.N);
+    BX_ALLOC(c.tw, (size_t)c.N);
+    BX_ALLOC(c.u, (size_t)2 * c.u_stride);
+    BX_ALLOC(c.y, (size_t)2 * c.y_stride);
+    BX_ALLOC(c.bh, (size_t)2 * c.y_stride);
+    BX_ALLOC(c.chunk_r, (size_t)2 * c.chunk_cap);
+    BX_ALLOC(c.chunk_s2, (size_t)2 * c.chunk_cap);
+    BX_ALLOC(c.chunk_m, (size_t)2 * c.chunk_cap);
+    BX_ALLOC(c.region_s2, (size_t)2 * c.region_cap);
+    BX_ALLOC(c.st, 1);
+    BX_ALLOC(c.fo_part, (size_t)4 * c.P);
+    BX_ALLOC(c.tap_slot, (size_t)2 * 4 * kMaxTaps);
+    BX_ALLOC(c.trace, (size_t)c.trace_cap * 4 * kMaxTaps * 2);
+    BX_ALLOC(c.trace_fo, (size_t)c.trace_cap * 2);
+    BX_CUDA(launch_tables(c.H, c.tw, c.N, c.cfg.baud, c.cfg.L_km, c.cfg.D_ps_nm_km, kLamNm, kRolloff, b->stream),
+            "filter tables");
+  }
+#undef BX_ALLOC
+  cudaError_t e = cudaMallocHost((void **)&b->h_L, (size_t)n_ch * sizeof(EqLaunch));
+  if (e == cudaSuccess) e = cudaMallocHost((void **)&b->h_err, sizeof(int));
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->err_ev, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking);
+  if (e != cudaSuccess) {
+    release(b);
+    return bcuda(b, e, "pinned launch table");
+  }
+  memset(b->h_L, 0, (size_t)n_ch * sizeof(EqLaunch));
+  *b->h_err = 0;
+  BX_CUDA(cudaMemcpyAsync(b->d_team, team.data(), team.size() * sizeof(int2), cudaMemcpyHostToDevice, b->stream), "team map");
+  BX_CUDA(cudaMemsetAsync(b->err, 0, sizeof(int), b->stream), "error word");
+  BX_CUDA(cudaStreamSynchronize(b->stream), "create");
+  return RX_OK;
+}
+
+rx_status rx_batch_set_param(rx_batch *b, int key, double v) {
+  if (!b) return RX_EINVAL;
+  if (key == RX_BP_GRAPH) {
+    b->use_graph = v != 0;
+    return RX_OK;
+  }
+  return bfail(b, RX_EINVAL, "unknown or read-only batch parameter");
+}
+
+rx_status rx_batch_get_param(rx_batch *b, int ch, int key, double *v) {
+  if (!b || !v) return RX_EINVAL;
+  if (ch == -1) {
+    switch (key) {
+      case RX_BP_GRAPH: *v = b->use_graph; return RX_OK;
+      case RX_BP_EQ_CTAS: *v = b->eq_ctas; return RX_OK;
+      default: return bfail(b, RX_EINVAL, "unknown batch parameter");
+    }
+  }
+  if (ch < 0 || ch >= b->n_ch) return bfail(b, RX_EINVAL, "channel out of range");
+  const Chan &c = b->ch[ch];
+  switch (key) {
+    case RX_P_MOD: *v = c.cfg.mod_bits; break;
+    case RX_P_FFT_N: *v = c.N; break;
+    case RX_P_OVERLAP: *v = c.V; break;
+    case RX_P_ROLLOFF: *v = kRolloff; break;
+    case RX_P_LAMBDA_NM: *v = kLamNm; break;
+    case RX_P_MU_CMA: *v = kMu; break;
+    case RX_P_MU_DD: *v = kMu; break;
+    case RX_P_N_CMA: *v = (double)kNcma; break;
+    case RX_P_UPDATE_BLOCK: *v = kBu; break;
+    case RX_P_SEG_LEN: *v = kS; break;
+    case RX_P_SEG_PRETRAIN: *v = kW; break;
+    case RX_P_BPS_HALFWIN: *v = kNb; break;
+    case RX_P_BLOCK_SAMPLES: *v = (double)kBlockSamples; break;
+    case RX_P_IN_SCALE: *v = c.cfg.in_scale; break;
+    case RX_P_ACQ_MIN: *v = (double)kAcqMin; break;
+    case RX_P_FO_SMOOTH: *v = kFoSmooth; break;
+    case RX_P_FO_TRACK: *v = 1; break;
+    case RX_BP_EQ_TEAM: *v = c.team; break;
+    case RX_BP_CDC_NS_PER_SAMPLE: *v = c.ns_per_sample; break;
+    default: return bfail(b, RX_EINVAL, "unknown channel parameter");
+  }
+  return RX_OK;
+}
+
+rx_status rx_batch_set_cuda_stream(rx_batch *b, void *s) {
+  if (!b) return RX_EINVAL;
+  if ((cudaStream_t)s != b->stream) {
+    if (b->gexec) cudaGraphExecDestroy(b->gexec);
+    b->gexec = nullptr;
+    b->gsig.clear();
+    b->sig.clear();
+  }
+  b->stream = (cudaStream_t)s;
+  return RX_OK;
+}
+
+rx_status rx_batch_process(rx_batch *b, const rx_in *ins, rx_out *outs) {
+  if (!b || !ins || !outs) return RX_EINVAL;
+  rx_status s = check_device_error(b, false);
+  if (s != RX_OK) return s;
+  std::vector<int64_t> sig;
+  sig.reserve((size_t)b->n_ch * 16);
+  for (int i = 0; i < b->n_ch; ++i) {
+    const Chan &c = b->ch[i];
+    const rx_in &in = ins[i];
+    const rx_out &o = outs[i];
+    const std::string who = "channel " + std::to_string(i) + ": ";
+    if (in.n < 0 || in.n % 2 || in.n > c.n_cap) return bfail(b, RX_EINVAL, who + "sample count must be even, within max_samples");
+    if (in.n > 0) {
+      if (!in.data) return bfail(b, RX_EINVAL, who + "null input");
+      if (in.dtype != RX_I8x4 && in.dtype != RX_F32x4) return bfail(b, RX_EINVAL, who + "unknown input dtype");
+      if ((uintptr_t)in.data % (in.dtype == RX_I8x4 ? 4 : 16)) return bfail(b, RX_EINVAL, who + "input misaligned");
+    }
+    const int64_t K = in.n / 2;
+    if (!o.bits) return bfail(b, RX_EINVAL, who + "null bit output");
+    if (o.capacity < K) return bfail(b, RX_EINVAL, who + "output capacity too small");
+    if (o.bits_stride * 32 < K * c.cfg.mod_bits) return bfail(b, RX_EINVAL, who + "bit stride too small");
+    if ((o.llr && o.llr_stride < K * c.cfg.mod_bits) || (o.sym && o.sym_stride < K) || (o.eq && o.eq_stride < K) ||
+        (o.cdc && o.cdc_stride < in.n))
+      return bfail(b, RX_EINVAL, who + "an optional output's stride is too small");
+    const int64_t vals[] = {(int64_t)(uintptr_t)in.data, in.n, in.dtype, (int64_t)(uintptr_t)o.bits, o.bits_stride,
+                            (int64_t)(uintptr_t)o.llr, o.llr_stride, (int64_t)(uintptr_t)o.sym, o.sym_stride,
+                            (int64_t)(uintptr_t)o.eq, o.eq_stride, (int64_t)(uintptr_t)o.cdc, o.cdc_stride};
+    sig.insert(sig.end(), std::begin(vals), std::end(vals));
+  }
+  const bool replay = b->use_graph && b->gexec && sig == b->gsig;
+  if (sig != b->hsig) {
+    // the launch table is about to change: earlier work that reads it must be done
+    BX_CUDA(cudaStreamSynchronize(b->stream), "launch table");
+    b->hsig = sig;
+    for (int i = 0; i < b->n_ch; ++i) {
+      const Chan &c = b->ch[i];
+      const int64_t K = ins[i].n / 2;
+      const int64_t A = std::min(c.A_full, K);
+      const int64_t n_seg = K > A ? (K - A + kS - 1) / kS : 0;
+      EqLaunch &L = b->h_L[i];
+      memset(&L, 0, sizeof(L));
+      L.u = c.u;
+      L.u_base = 0;
+      L.u_stride = c.u_stride;
+      L.y = c.y;
+      L.y_base = 0;
+      L.y_stride = c.y_stride;
+      L.st = c.st;
+      L.fo_part = c.fo_part;
+      L.tap_slot = c.tap_slot;
+      L.trace = c.trace;
+      L.trace_fo = c.trace_fo;
+      L.trace_cap = c.trace_cap;
+      L.barrier = b->barriers + 2 * i;
+      L.err = b->err;
+      L.K = K;
+      L.run_acq = A > 0;
+      L.A = A;
+      L.n_cma = std::min(kNcma, A);
+      L.wave_first = 0;
+      L.wave_last = (n_seg + c.P - 1) / c.P;
+      L.n_segments = n_seg;
+      L.P = c.P;
+      L.S = kS;
+      L.W = kW;
+      L.Bu = kBu;
+      L.T = c.cfg.ntaps;
+      L.mod_bits = c.cfg.mod_bits;
+      L.mu_cma = (float)kMu;
+      L.mu_dd = (float)kMu;
+      L.cma_r2 = c.cfg.mod_bits == 4 ? 1.32f : 1.0f;
+      L.fo_smooth = kFoSmooth;
+      L.inc_scale = (float)(18446744073709551616.0 / (4.0 * 3.14159265358979323846 * kFoSmooth));
+      L.fo_track = 1;
+      L.nblocks = c.team;
+    }
+  }
+  if (replay) {
+    BX_CUDA(cudaGraphLaunch(b->gexec, b->stream), "graph replay");
+  } else if (b->use_graph && sig == b->sig) {
+    // second call with these pointers and sizes: capture, then replay from now on
+    if (b->gexec) cudaGraphExecDestroy(b->gexec);
+    b->gexec = nullptr;
+    // captured on the library's own stream (the bound one may be the legacy
+    // default stream, which cannot be captured); replayed on the bound one
+    BX_CUDA(cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal), "capture");
+    rx_status st = enqueue(b, ins, outs, b->cap_stream);
+    cudaGraph_t g = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(b->cap_stream, &g);
+    if (st != RX_OK) {
+      if (g) cudaGraphDestroy(g);
+      return st;
+    }
+    if (e != cudaSuccess) return bcuda(b, e, "capture");
+    const cudaError_t e2 = cudaGraphInstantiate(&b->gexec, g, 0);
+    cudaGraphDestroy(g);
+    if (e2 != cudaSuccess) {
+      b->gexec = nullptr;
+      return bcuda(b, e2, "graph instantiate");
+    }
+    b->gsig = sig;
+    BX_CUDA(cudaGraphLaunch(b->gexec, b->stream), "graph launch");
+  } else {
+    s = enqueue(b, ins, outs, b->stream);
+    if (s != RX_OK) return s;
+    b->sig = sig;
+  }
+  for (int i = 0; i < b->n_ch; ++i) {
+    outs[i].n = ins[i].n / 2;
+    outs[i].first = 0;
+    outs[i].cdc_first = 0;
+    outs[i].cdc_n = outs[i].cdc ? ins[i].n : 0;
+  }
+  BX_CUDA(cudaMemcpyAsync(b->h_err, b->err, sizeof(int), cudaMemcpyDeviceToHost, b->stream), "error copy");
+  BX_CUDA(cudaEventRecord(b->err_ev, b->stream), "error event");
+  b->processed = true;
+  return RX_OK;
+}
+
+rx_status rx_batch_ber(rx_batch *b, int ch, const uint32_t *rx_bits, int64_t rx_stride, const uint32_t *ref_bits,
+                       int64_t ref_stride, int64_t n_symbols, uint64_t *errors, uint64_t *bits_counted,
+                       int32_t *sync) {
+  if (!b || !rx_bits || !ref_bits || !errors || !bits_counted || n_symbols < 0) return RX_EINVAL;
+  if (ch < 0 || ch >= b->n_ch) return bfail(b, RX_EINVAL, "channel out of range");
+  const Chan &c = b->ch[ch];
+  BX_CUDA(ber_run(rx_bits, rx_stride, ref_bits, ref_stride, n_symbols, c.cfg.mod_bits,
+                  std::min(c.A_full, n_symbols), b->ber_counts, b->ber_sync, b->ber_acc, b->stream, errors,
+                  bits_counted, sync),
+          "ber");
+  return RX_OK;
+}
+
+rx_status rx_batch_trace(rx_batch *b, int ch, int64_t wave, float *taps, double *dw, double *Phi) {
+  if (!b || !taps || !dw || !Phi) return RX_EINVAL;
+  if (ch < 0 || ch >= b->n_ch) return bfail(b, RX_EINVAL, "channel out of range");
+  const Chan &c = b->ch[ch];
+  const int64_t idx = wave + 1;
+  if (idx < 0 || idx >= c.trace_cap) return bfail(b, RX_EINVAL, "wave outside the trace");
+  BX_CUDA(cudaStreamSynchronize(b->stream), "trace wait");
+  std::vector<float> t(4 * kMaxTaps * 2);
+  BX_CUDA(cudaMemcpy(t.data(), c.trace + idx * 4 * kMaxTaps * 2, t.size() * sizeof(float), cudaMemcpyDeviceToHost), "trace");
+  double fo[2];
+  BX_CUDA(cudaMemcpy(fo, c.trace_fo + idx * 2, sizeof(fo), cudaMemcpyDeviceToHost), "trace");
+  const int T = c.cfg.ntaps;
+  for (int p = 0; p < 2; ++p)
+    for (int q = 0; q < 2; ++q)
+      for (int i = 0; i < T; ++i) {
+        const int src = ((p * 2 + q) * kMaxTaps + i) * 2;
+        const int dst = ((p * 2 + q) * T + i) * 2;
+        taps[dst] = t[src];
+        taps[dst + 1] = t[src + 1];
+      }
+  *dw = fo[0];
+  *Phi = fo[1];
+  return RX_OK;
+}
+
+rx_status rx_batch_sync(rx_batch *b) {
+  if (!b) return RX_EINVAL;
+  BX_CUDA(cudaStreamSynchronize(b->stream), "synchronize");
+  return check_device_error(b, true);
+}
+
+void rx_batch_destroy(rx_batch *b) {
+  if (!b) return;
+  if (b->processed) cudaStreamSynchronize(b->stream);
+  release(b);
+  delete b;
+}
+
+const char *rx_batch_last_error(rx_batch *b) { return b ? b->msg.c_str() : "null handle"; }
+
+}  // extern "C"

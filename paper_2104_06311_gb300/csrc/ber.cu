@@ -7,6 +7,11 @@
 //   QPSK  (b0, b1)         -> (!b1, b0)
 //   16QAM (b0, b1, b2, b3) -> (!b2, b3, b0, b1)
 // (I' = -Q, Q' = I with b0/b2 the sign bits and b1/b3 the outer-level bits).
+#include <stdint.h>
+#include <string.h>
+
+#include <vector>
+
 #include "common.cuh"
 #include "rx_internal.h"
 
@@ -100,6 +105,49 @@ cudaError_t launch_ber_count(const uint32_t *rx, int64_t rxs, const uint32_t *re
   unsigned blocks = (unsigned)min((int64_t)1216, (n + 255) / 256);
   ber_count_kernel<<<dim3(blocks, 2), 256, 0, s>>>(rx, rxs, ref, refs, K, m, k0, sync, acc);
   return cudaGetLastError();
+}
+
+cudaError_t ber_run(const uint32_t *rx_bits, int64_t rx_stride, const uint32_t *ref_bits, int64_t ref_stride,
+                    int64_t n_symbols, int m, int64_t A, unsigned *counts_dev, int32_t *sync_dev,
+                    unsigned long long *acc_dev, cudaStream_t st, uint64_t *errors, uint64_t *bits_counted,
+                    int32_t *sync) {
+  const int64_t s0 = A + 4096, s1 = A + 8192;
+  *errors = 0;
+  *bits_counted = 0;
+  if (s1 > n_symbols) return cudaSuccess;
+  cudaError_t e = launch_ber_sync(rx_bits, rx_stride, ref_bits, ref_stride, n_symbols, m, s0, s1, counts_dev, st);
+  if (e != cudaSuccess) return e;
+  std::vector<unsigned> counts(2 * 2 * 4 * 129);
+  e = cudaMemcpyAsync(counts.data(), counts_dev, counts.size() * sizeof(unsigned), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return e;
+  int32_t h_sync[6] = {0, 0, 0, 0, 0, 0};
+  for (int p = 0; p < 2; ++p) {  // fewest errors; ties keep the first (q, r, d) in scan order
+    unsigned best = UINT32_MAX;
+    for (int q = 0; q < 2; ++q)
+      for (int r = 0; r < 4; ++r)
+        for (int d = -64; d <= 64; ++d) {
+          const unsigned ec = counts[((p * 2 + q) * 4 + r) * 129 + (d + 64)];
+          if (ec < best) {
+            best = ec;
+            h_sync[3 * p] = q;
+            h_sync[3 * p + 1] = r;
+            h_sync[3 * p + 2] = d;
+          }
+        }
+  }
+  e = cudaMemcpyAsync(sync_dev, h_sync, sizeof(h_sync), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(acc_dev, 0, 2 * sizeof(unsigned long long), st);
+  if (e == cudaSuccess)
+    e = launch_ber_count(rx_bits, rx_stride, ref_bits, ref_stride, n_symbols, m, s1, sync_dev, acc_dev, st);
+  unsigned long long acc[2] = {0, 0};
+  if (e == cudaSuccess) e = cudaMemcpyAsync(acc, acc_dev, sizeof(acc), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return e;
+  *errors = acc[0];
+  *bits_counted = acc[1];
+  if (sync) memcpy(sync, h_sync, sizeof(h_sync));
+  return cudaSuccess;
 }
 
 }  // namespace rx

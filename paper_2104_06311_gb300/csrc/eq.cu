@@ -232,11 +232,21 @@ __device__ __forceinline__ void gather_taps(float2 (&h)[8], float2 own, const La
   }
 }
 
+// Complex products rounded term by term (never contracted into FMAs).
+__device__ __forceinline__ float2 cmul_rn(float2 a, float2 b) {
+  return make_float2(__fsub_rn(__fmul_rn(a.x, b.x), __fmul_rn(a.y, b.y)),
+                     __fadd_rn(__fmul_rn(a.x, b.y), __fmul_rn(a.y, b.x)));
+}
+__device__ __forceinline__ float2 cmulc_rn(float2 a, float2 b) {  // a conj(b)
+  return make_float2(__fadd_rn(__fmul_rn(a.x, b.x), __fmul_rn(a.y, b.y)),
+                     __fsub_rn(__fmul_rn(a.y, b.x), __fmul_rn(a.x, b.y)));
+}
+
 // Weight of a 16QAM symbol of power a = |y|^2 in the frequency estimate: 0 on the
 // middle ring (|s|^2 = 1, not pi/4-aligned), 1 from |a - 1| >= 0.4 (the inner
 // and outer rings), linear in between so that the estimate is continuous.
 __device__ __forceinline__ float ring_weight(float a) {
-  return fminf(fmaxf((fabsf(a - 1.f) - 0.2f) * 5.f, 0.f), 1.f);
+  return fminf(fmaxf(__fmul_rn(__fsub_rn(fabsf(__fsub_rn(a, 1.f)), 0.2f), 5.f), 0.f), 1.f);
 }
 
 template <int MB>
@@ -298,13 +308,16 @@ __device__ __forceinline__ void run_span(const Hot hot, EqSmem &sm, const Span s
       auto fo_pair = [&]() {
         const float2 yw = sm.ybuf[par][kl > 0 ? kl - 1 : 0];
         float2 yp = ln.j > 0 ? make_float2(yupx, yupy) : (ln.warp > 0 ? yw : yprev_last);
-        const float2 v = cmulc(yv, yp);
-        const float2 v2 = cmul(v, v);
-        float2 v4 = cmul(v2, v2);
+        // explicitly rounded products: no FMA contraction, so that every
+        // kernel this body is compiled into forms the same estimate
+        const float2 v = cmulc_rn(yv, yp);
+        const float2 v2 = cmul_rn(v, v);
+        float2 v4 = cmul_rn(v2, v2);
         if (MB == 4) {  // 16QAM: keep the pi/4-aligned inner and outer rings (soft edge)
-          const float wk = ring_weight(yv.x * yv.x + yv.y * yv.y);
-          const float wp = ring_weight(yp.x * yp.x + yp.y * yp.y);
-          v4 = cscale(v4, wk * wp);
+          const float wk = ring_weight(__fadd_rn(__fmul_rn(yv.x, yv.x), __fmul_rn(yv.y, yv.y)));
+          const float wp = ring_weight(__fadd_rn(__fmul_rn(yp.x, yp.x), __fmul_rn(yp.y, yp.y)));
+          const float w = __fmul_rn(wk, wp);
+          v4 = make_float2(__fmul_rn(v4.x, w), __fmul_rn(v4.y, w));
         }
         kahan_add(fo.sx, fo.cx, fo_on ? v4.x : 0.f);   // a select: stale inputs cannot leak
         kahan_add(fo.sy, fo.cy, fo_on ? v4.y : 0.f);
@@ -427,9 +440,10 @@ __device__ __forceinline__ void trace_fo(const EqLaunch &L, int64_t idx, double 
 
 }  // namespace
 
+// One CTA's part of an equaliser launch: CTA `cta` of the L.nblocks CTAs that
+// serve this stream (a whole grid, or a team inside a batched grid).
 template <int MB>
-__global__ void __launch_bounds__(kEqThreads, 1) eq_kernel(EqLaunch L) {
-  __shared__ EqSmem sm;
+__device__ __forceinline__ void eq_body(const EqLaunch &L, const int cta, EqSmem &sm) {
   Lane ln;
   ln.warp = threadIdx.x >> 5;
   ln.lane = threadIdx.x & 31;
@@ -450,8 +464,8 @@ __global__ void __launch_bounds__(kEqThreads, 1) eq_kernel(EqLaunch L) {
     sincospif(((float)ln.lane / 32.f - 0.5f) * 0.5f, &sb, &cb);
     ln.rot_b = make_float2(cb, -sb);
   }
-  const int p = blockIdx.x & 1;              // butterfly row of this CTA
-  const int slot = blockIdx.x >> 1;          // segment slot
+  const int p = cta & 1;              // butterfly row of this CTA
+  const int slot = cta >> 1;          // segment slot
   const int nslots = L.nblocks >> 1;
   const int64_t n_limit = L.K >= 0 ? 2 * L.K : (int64_t)1 << 62;
   Hot hot;
@@ -478,7 +492,7 @@ __global__ void __launch_bounds__(kEqThreads, 1) eq_kernel(EqLaunch L) {
   __syncthreads();
 
   if (L.run_acq) {
-    if (blockIdx.x < 2) {
+    if (cta < 2) {
       load_row(own, h, &L.st->taps[0][0][0], p, ln);
       Span sp;
       sp.kp = 0; sp.ks = 0; sp.ke = L.n_cma;
@@ -511,7 +525,7 @@ __global__ void __launch_bounds__(kEqThreads, 1) eq_kernel(EqLaunch L) {
         t1[2 * idx] = own.x;
         t1[2 * idx + 1] = own.y;
       }
-      if (blockIdx.x == 0 && threadIdx.x == 0) {
+      if (cta == 0 && threadIdx.x == 0) {
         // tracker as a 64-bit fixed-point NCO: exact modular phase arithmetic
         const long long dq = (long long)to_q64_turns(delta);
         const unsigned long long phq = (unsigned long long)(2 * L.A - 2 * L.n_cma) * (unsigned long long)dq;
@@ -574,12 +588,12 @@ __global__ void __launch_bounds__(kEqThreads, 1) eq_kernel(EqLaunch L) {
         const long long dq = sm.dq;
         sm.phq += (unsigned long long)(2 * (long long)L.P * L.S) * (unsigned long long)dq;
         sm.dq = dq + __float2ll_rn(r * L.inc_scale);
-        if (blockIdx.x == 0) trace_fo(L, w + 2, (double)sm.dq * 6.8122431601731090e-19, q64_to_rad(sm.phq));
+        if (cta == 0) trace_fo(L, w + 2, (double)sm.dq * 6.8122431601731090e-19, q64_to_rad(sm.phq));
       }
     }
     __syncthreads();
   }
-  if (blockIdx.x == 0) {
+  if (cta == 0) {
     const float2 *last = L.tap_slot + ((L.wave_last - 1) & 1) * 4 * kMaxTaps;
     for (int jj = threadIdx.x; jj < 4 * kMaxTaps; jj += blockDim.x)
       __stcg(&(&L.st->taps[0][0][0])[jj], __ldcg(&last[jj]));
@@ -591,6 +605,12 @@ __global__ void __launch_bounds__(kEqThreads, 1) eq_kernel(EqLaunch L) {
       L.st->next_wave = L.wave_last;
     }
   }
+}
+
+template <int MB>
+__global__ void __launch_bounds__(kEqThreads, 1) eq_kernel(EqLaunch L) {
+  __shared__ EqSmem sm;
+  eq_body<MB>(L, (int)blockIdx.x, sm);
 }
 
 // Unused dynamic shared memory that keeps the equaliser's SMs to itself: the
@@ -608,6 +628,37 @@ int eq_max_blocks() {
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, eq_kernel<2>, kEqThreads, kEqPadSmem);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per4, eq_kernel<4>, kEqThreads, kEqPadSmem);
   return sms * min(per, per4);
+}
+
+// Batched form: one cooperative launch serves many independent streams.  CTA
+// b works for stream team[b].x as its CTA team[b].y; each stream's team
+// synchronises on its own barrier words (EqLaunch::nblocks = team size).
+__global__ void __launch_bounds__(kEqThreads, 1) eq_batch_kernel(const EqLaunch *__restrict__ Ls,
+                                                                 const int2 *__restrict__ team) {
+  __shared__ EqSmem sm;
+  const int2 t = team[blockIdx.x];
+  const EqLaunch &L = Ls[t.x];
+  if (L.mod_bits == 4) eq_body<4>(L, t.y, sm);
+  else eq_body<2>(L, t.y, sm);
+}
+
+int eq_batch_max_blocks(int pad_smem) {
+  int dev = 0, sms = 0, per = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (cudaFuncSetAttribute(eq_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, pad_smem) != cudaSuccess)
+    return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, eq_batch_kernel, kEqThreads, pad_smem) != cudaSuccess)
+    return 0;
+  return sms * per;
+}
+
+cudaError_t launch_eq_batch(const EqLaunch *d_L, const int2 *d_team, int nblocks, int pad_smem, cudaStream_t s) {
+  const EqLaunch *a0 = d_L;
+  const int2 *a1 = d_team;
+  void *args[] = {&a0, &a1};
+  return cudaLaunchCooperativeKernel((const void *)eq_batch_kernel, dim3(nblocks), dim3(kEqThreads), args,
+                                     (size_t)pad_smem, s);
 }
 
 cudaError_t launch_eq(const EqLaunch &L, cudaStream_t s) {

@@ -29,7 +29,6 @@
 using namespace rx;
 
 namespace {
-constexpr double kC = 299792458.0;
 constexpr int kMaxPieces = 64;
 constexpr uint32_t kStateMagic = 0x52584231u;  // "RXB1"
 }  // namespace
@@ -129,14 +128,6 @@ rx_status cuda_fail(rx_stream *rx, cudaError_t e, const char *where) {
     if (e_ != cudaSuccess) return cuda_fail(rx, e_, where); \
   } while (0)
 
-int64_t n_cd_taps(double baud, int sps, double L_km, double D, double lam_nm) {
-  const double Tsym = 1.0 / (sps * baud);
-  const double Dsm = fabs(D) * 1e-12 / (1e-9 * 1e3);
-  const double lam = lam_nm * 1e-9;
-  return 2 * (int64_t)floor(Dsm * lam * lam * L_km * 1e3 / (2.0 * kC * Tsym * Tsym)) + 1;
-}
-
-bool is_pow2(int64_t v) { return v > 0 && (v & (v - 1)) == 0; }
 
 rx_status resolve(rx_stream *rx) {
   const int64_t ncd = n_cd_taps(rx->baud, rx->sps, rx->L_km, rx->D, rx->lam_nm);
@@ -829,42 +820,11 @@ rx_status rx_ber(rx_stream *rx, const uint32_t *rx_bits, int64_t rx_stride, cons
     rx_status s = rx_reserve(rx, 2 * 65536);
     if (s != RX_OK) return s;
   }
-  const int m = rx->mod_bits;
   const int64_t A = std::min(rx->A_full, n_symbols);
-  const int64_t s0 = A + 4096, s1 = A + 8192;
-  *errors = 0;
-  *bits_counted = 0;
-  if (s1 > n_symbols) return RX_OK;
-  cudaStream_t st = rx->stream;
   rx->stage_launches[RX_STAGE_BER] += 2;
-  RX_CUDA(launch_ber_sync(rx_bits, rx_stride, ref_bits, ref_stride, n_symbols, m, s0, s1, rx->ber_counts, st), "ber sync");
-  std::vector<unsigned> counts(2 * 2 * 4 * 129);
-  RX_CUDA(cudaMemcpyAsync(counts.data(), rx->ber_counts, counts.size() * sizeof(unsigned), cudaMemcpyDeviceToHost, st), "ber sync copy");
-  RX_CUDA(cudaStreamSynchronize(st), "ber sync wait");
-  int h_sync[6];
-  for (int p = 0; p < 2; ++p) {
-    unsigned best = UINT32_MAX;
-    for (int q = 0; q < 2; ++q)
-      for (int r = 0; r < 4; ++r)
-        for (int d = -64; d <= 64; ++d) {
-          const unsigned e = counts[((p * 2 + q) * 4 + r) * 129 + (d + 64)];
-          if (e < best) {
-            best = e;
-            h_sync[3 * p] = q;
-            h_sync[3 * p + 1] = r;
-            h_sync[3 * p + 2] = d;
-          }
-        }
-  }
-  RX_CUDA(cudaMemcpyAsync(rx->ber_sync, h_sync, sizeof(h_sync), cudaMemcpyHostToDevice, st), "ber sync set");
-  RX_CUDA(cudaMemsetAsync(rx->ber_acc, 0, 2 * sizeof(unsigned long long), st), "ber acc");
-  RX_CUDA(launch_ber_count(rx_bits, rx_stride, ref_bits, ref_stride, n_symbols, m, s1, rx->ber_sync, rx->ber_acc, st), "ber count");
-  unsigned long long acc[2];
-  RX_CUDA(cudaMemcpyAsync(acc, rx->ber_acc, sizeof(acc), cudaMemcpyDeviceToHost, st), "ber copy");
-  RX_CUDA(cudaStreamSynchronize(st), "ber wait");
-  *errors = acc[0];
-  *bits_counted = acc[1];
-  if (sync) memcpy(sync, h_sync, sizeof(h_sync));
+  RX_CUDA(ber_run(rx_bits, rx_stride, ref_bits, ref_stride, n_symbols, rx->mod_bits, A, rx->ber_counts,
+                  rx->ber_sync, rx->ber_acc, rx->stream, errors, bits_counted, sync),
+          "ber");
   return RX_OK;
 }
 

@@ -15,6 +15,19 @@ constexpr int kEqThreads = 128;   // equaliser CTA: 4 warps, one butterfly row
 constexpr int kChunkSym = 1152;   // equaliser span chunk (symbols) held in smem
 constexpr int kBpsChunk = 256;    // BPS pass-1 symbols per warp
 
+// Length of a time-domain CD compensating filter, 2 floor(|D| lam^2 L /
+// (2 c T^2)) + 1 with T the sample period (the textbook bound; the paper's
+// static equaliser leaves it open).
+inline int64_t n_cd_taps(double baud, int sps, double L_km, double D, double lam_nm) {
+  const double Tsym = 1.0 / (sps * baud);
+  const double Dsm = (D < 0 ? -D : D) * 1e-12 / (1e-9 * 1e3);
+  const double lam = lam_nm * 1e-9;
+  const double v = Dsm * lam * lam * L_km * 1e3 / (2.0 * 299792458.0 * Tsym * Tsym);
+  return 2 * (int64_t)v + 1;   // v >= 0: truncation is the floor
+}
+
+inline bool is_pow2(int64_t v) { return v > 0 && (v & (v - 1)) == 0; }
+
 // Device-resident equaliser state (one per stream).
 struct EqState {
   float2 taps[2][2][kMaxTaps];     // current taps h[p][q][i]
@@ -89,6 +102,11 @@ cudaError_t launch_cdc(int N, int V, const void *tail, int64_t tail_first, int64
                        int64_t u_base, int64_t u_stride, int64_t win_first, int64_t win_count,
                        int64_t n_total, cudaStream_t s);
 cudaError_t launch_eq(const EqLaunch &L, cudaStream_t s);
+// Batched equaliser: one cooperative launch of nblocks CTAs; d_team[b] =
+// (stream, CTA within that stream's team).  pad_smem: unused dynamic shared
+// memory per CTA (limits CTAs per SM).
+int eq_batch_max_blocks(int pad_smem);
+cudaError_t launch_eq_batch(const EqLaunch *d_L, const int2 *d_team, int nblocks, int pad_smem, cudaStream_t s);
 int eq_max_blocks();
 cudaError_t launch_bps(const BpsLaunch &L, cudaStream_t s);
 cudaError_t launch_ber_sync(const uint32_t *rx, int64_t rxs, const uint32_t *ref, int64_t refs,
@@ -97,6 +115,12 @@ cudaError_t launch_ber_sync(const uint32_t *rx, int64_t rxs, const uint32_t *ref
 cudaError_t launch_ber_count(const uint32_t *rx, int64_t rxs, const uint32_t *ref, int64_t refs,
                              int64_t K, int m, int64_t k0, const int *sync,
                              unsigned long long *acc, cudaStream_t s);
+// Whole BER measurement (sync window, host-side choice of (q, r, d) per pol,
+// count); synchronises st.  Layout and skip rule as rx_ber.
+cudaError_t ber_run(const uint32_t *rx_bits, int64_t rx_stride, const uint32_t *ref_bits, int64_t ref_stride,
+                    int64_t n_symbols, int m, int64_t A, unsigned *counts_dev, int32_t *sync_dev,
+                    unsigned long long *acc_dev, cudaStream_t st, uint64_t *errors, uint64_t *bits_counted,
+                    int32_t *sync);
 cudaError_t launch_copy_cols(float2 *dst, int64_t dst_stride, const float2 *src,
                              int64_t src_stride, int64_t n, cudaStream_t s);
 cudaError_t launch_copy_cols_i8(int8_t *dst, int64_t dst_stride, const int8_t *src,

@@ -27,7 +27,11 @@ STAGES = ["cdc", "eq", "bps", "move", "ber"]
 EXPORTS = ["rx_create", "rx_set_param", "rx_get_param", "rx_set_cuda_stream", "rx_reserve",
            "rx_process", "rx_ber", "rx_trace", "rx_get_state", "rx_set_state", "rx_reset",
            "rx_sync", "rx_destroy", "rx_status_str", "rx_last_error", "rx_profile",
-           "rx_bps_demap_noalloc"]
+           "rx_bps_demap_noalloc",
+           "rx_batch_create", "rx_batch_set_param", "rx_batch_get_param", "rx_batch_set_cuda_stream",
+           "rx_batch_process", "rx_batch_ber", "rx_batch_trace", "rx_batch_sync", "rx_batch_destroy",
+           "rx_batch_last_error"]
+BATCH_PARAMS = {"GRAPH": 100, "EQ_CTAS": 101, "EQ_TEAM": 102, "CDC_NS_PER_SAMPLE": 103}
 
 
 class rx_in(ct.Structure):
@@ -42,6 +46,12 @@ class rx_out(ct.Structure):
                 ("cdc", ct.c_void_p), ("cdc_stride", ct.c_int64),
                 ("capacity", ct.c_int64), ("n", ct.c_int64), ("first", ct.c_int64),
                 ("cdc_first", ct.c_int64), ("cdc_n", ct.c_int64)]
+
+
+class rx_chan_cfg(ct.Structure):
+    _fields_ = [("baud", ct.c_double), ("L_km", ct.c_double), ("D_ps_nm_km", ct.c_double),
+                ("in_scale", ct.c_double), ("max_samples", ct.c_int64), ("mod_bits", ct.c_int32),
+                ("ntaps", ct.c_int32), ("fft_n", ct.c_int32), ("overlap", ct.c_int32)]
 
 
 class RxError(RuntimeError):
@@ -83,8 +93,22 @@ def load(path: str = LIB_PATH) -> ct.CDLL:
     lib.rx_status_str.restype = ct.c_char_p
     lib.rx_last_error.argtypes = [P]
     lib.rx_last_error.restype = ct.c_char_p
+    lib.rx_batch_create.argtypes = [ct.POINTER(P), ct.c_int, ct.POINTER(rx_chan_cfg)]
+    lib.rx_batch_set_param.argtypes = [P, ct.c_int, ct.c_double]
+    lib.rx_batch_get_param.argtypes = [P, ct.c_int, ct.c_int, ct.POINTER(ct.c_double)]
+    lib.rx_batch_set_cuda_stream.argtypes = [P, P]
+    lib.rx_batch_process.argtypes = [P, ct.POINTER(rx_in), ct.POINTER(rx_out)]
+    lib.rx_batch_ber.argtypes = [P, ct.c_int, P, ct.c_int64, P, ct.c_int64, ct.c_int64, ct.POINTER(ct.c_uint64),
+                                 ct.POINTER(ct.c_uint64), ct.POINTER(ct.c_int32)]
+    lib.rx_batch_trace.argtypes = [P, ct.c_int, ct.c_int64, ct.POINTER(ct.c_float), ct.POINTER(ct.c_double),
+                                   ct.POINTER(ct.c_double)]
+    lib.rx_batch_sync.argtypes = [P]
+    lib.rx_batch_destroy.argtypes = [P]
+    lib.rx_batch_destroy.restype = None
+    lib.rx_batch_last_error.argtypes = [P]
+    lib.rx_batch_last_error.restype = ct.c_char_p
     for name in EXPORTS:
-        if name not in ("rx_destroy", "rx_status_str", "rx_last_error"):
+        if name not in ("rx_destroy", "rx_status_str", "rx_last_error", "rx_batch_destroy", "rx_batch_last_error"):
             getattr(lib, name).restype = ct.c_int
     _lib = lib
     return lib
@@ -277,3 +301,151 @@ class Receiver:
         out["n"] = pos
         out["cdc_n"] = cpos
         return out
+
+
+def _bcheck(lib, h, status):
+    if status != RX_OK:
+        detail = lib.rx_batch_last_error(h).decode() if h else ""
+        raise RxError(status, f"{lib.rx_status_str(status).decode()}: {detail}")
+
+
+class Batch:
+    """Batched form (include/rx_batch.h): many channels, whole streams, one enqueue.
+
+    cfgs: list of dicts with keys baud, L_km, D (17), in_scale (1), max_samples,
+    mod_bits (2), ntaps (15), fft_n (0 = autotuned), overlap (0 = default).
+    """
+
+    def __init__(self, cfgs, stream=None):
+        import torch
+        self.torch = torch
+        self.lib = load()
+        n = len(cfgs)
+        arr = (rx_chan_cfg * n)()
+        for i, c in enumerate(cfgs):
+            arr[i] = rx_chan_cfg(float(c["baud"]), float(c["L_km"]), float(c.get("D", 17.0)),
+                                 float(c.get("in_scale", 1.0)), int(c["max_samples"]), int(c.get("mod_bits", 2)),
+                                 int(c.get("ntaps", 15)), int(c.get("fft_n", 0)), int(c.get("overlap", 0)))
+        h = ct.c_void_p()
+        st = self.lib.rx_batch_create(ct.byref(h), n, arr)
+        if st != RX_OK:
+            msg = self.lib.rx_batch_last_error(h).decode() if h else ""
+            if h:
+                self.lib.rx_batch_destroy(h)
+            raise RxError(st, f"{self.lib.rx_status_str(st).decode()}: {msg}")
+        self.h = h
+        self.n_ch = n
+        self.cfgs = [dict(c) for c in cfgs]
+        if stream is not None:
+            self.set_cuda_stream(stream)
+
+    def set_cuda_stream(self, stream):
+        ptr = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+        _bcheck(self.lib, self.h, self.lib.rx_batch_set_cuda_stream(self.h, ct.c_void_p(ptr)))
+
+    def rx_batch_set_param(self, key, value):
+        k = BATCH_PARAMS[key.upper()] if isinstance(key, str) else key
+        _bcheck(self.lib, self.h, self.lib.rx_batch_set_param(self.h, k, float(value)))
+
+    set_param = rx_batch_set_param
+
+    def rx_batch_get_param(self, ch, key):
+        if isinstance(key, str):
+            key = BATCH_PARAMS.get(key.upper()) or PARAMS[key.upper()]
+        v = ct.c_double()
+        _bcheck(self.lib, self.h, self.lib.rx_batch_get_param(self.h, int(ch), key, ct.byref(v)))
+        return v.value
+
+    get_param = rx_batch_get_param
+
+    def bits_per_symbol(self, ch):
+        return int(self.cfgs[ch].get("mod_bits", 2))
+
+    def alloc_outs(self, samples, llr=False, sym=False, eq=False, cdc=False):
+        t = self.torch
+        outs = []
+        for ch, x in enumerate(samples):
+            K = x.shape[0] // 2
+            m = self.bits_per_symbol(ch)
+            cap = K + 32
+            o = {"bits": t.zeros((2, (cap * m + 31) // 32), dtype=t.int32, device="cuda"), "capacity": cap}
+            if llr:
+                o["llr"] = t.zeros((2, cap * m), dtype=t.float32, device="cuda")
+            if sym:
+                o["sym"] = t.zeros((2, cap), dtype=t.complex64, device="cuda")
+            if eq:
+                o["eq"] = t.zeros((2, cap), dtype=t.complex64, device="cuda")
+            if cdc:
+                o["cdc"] = t.zeros((2, x.shape[0] + 64), dtype=t.complex64, device="cuda")
+            outs.append(o)
+        return outs
+
+    def rx_batch_process(self, samples, outs):
+        """samples: list of (n_c, 4) int8/float32 CUDA tensors; outs from alloc_outs."""
+        t = self.torch
+        n = self.n_ch
+        ins = (rx_in * n)()
+        os_ = (rx_out * n)()
+        for c in range(n):
+            x = samples[c]
+            if x is None or x.shape[0] == 0:
+                ins[c].data, ins[c].n, ins[c].dtype = None, 0, RX_F32x4
+            else:
+                assert x.is_cuda and x.is_contiguous() and x.shape[-1] == 4
+                ins[c].data = x.data_ptr()
+                ins[c].n = x.shape[0]
+                ins[c].dtype = RX_I8x4 if x.dtype == t.int8 else RX_F32x4
+            o = outs[c]
+            os_[c].bits = o["bits"].data_ptr()
+            os_[c].bits_stride = o["bits"].shape[1]
+            for k in ("llr", "sym", "eq", "cdc"):
+                if k in o:
+                    setattr(os_[c], k, o[k].data_ptr())
+                    setattr(os_[c], k + "_stride", o[k].shape[1])
+            os_[c].capacity = o["capacity"]
+        _bcheck(self.lib, self.h, self.lib.rx_batch_process(self.h, ins, os_))
+        for c in range(n):
+            outs[c]["n"] = os_[c].n
+            outs[c]["cdc_n"] = os_[c].cdc_n
+        return outs
+
+    process = rx_batch_process
+
+    def rx_batch_ber(self, ch, rx_bits, ref_bits, n_symbols):
+        e, n = ct.c_uint64(), ct.c_uint64()
+        sync = (ct.c_int32 * 6)()
+        _bcheck(self.lib, self.h, self.lib.rx_batch_ber(self.h, int(ch), rx_bits.data_ptr(), rx_bits.shape[1],
+                                                        ref_bits.data_ptr(), ref_bits.shape[1], int(n_symbols),
+                                                        ct.byref(e), ct.byref(n), sync))
+        return e.value, n.value, [tuple(sync[3 * p:3 * p + 3]) for p in range(2)]
+
+    ber = rx_batch_ber
+
+    def rx_batch_trace(self, ch, wave):
+        import numpy as np
+        T = int(self.cfgs[ch].get("ntaps", 15))
+        taps = (ct.c_float * (2 * 2 * T * 2))()
+        dw, Phi = ct.c_double(), ct.c_double()
+        _bcheck(self.lib, self.h, self.lib.rx_batch_trace(self.h, int(ch), int(wave), taps, ct.byref(dw), ct.byref(Phi)))
+        a = np.frombuffer(taps, dtype=np.float32).astype(np.float64)
+        return (a[0::2] + 1j * a[1::2]).reshape(2, 2, T), dw.value, Phi.value
+
+    trace = rx_batch_trace
+
+    def rx_batch_sync(self):
+        _bcheck(self.lib, self.h, self.lib.rx_batch_sync(self.h))
+
+    sync = rx_batch_sync
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.rx_batch_destroy(self.h)
+            self.h = None
+
+    rx_batch_destroy = close
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

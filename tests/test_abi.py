@@ -1,6 +1,6 @@
 """Host-side checks of the C ABI (no GPU compute): the library builds and loads,
-exports every function include/rx.h declares, resolves parameters on the host
-and reports argument errors as status codes."""
+exports every function the headers in include/ declare, resolves parameters on
+the host and reports argument errors as status codes."""
 import ctypes as ct
 import os
 import re
@@ -23,16 +23,57 @@ def lib():
 
 
 def declared_functions():
-    text = open(os.path.join(ROOT, "include", "rx.h")).read()
-    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"\b(rx_[a-z_]+)\s*\(", text)))
+    names = set()
+    inc = os.path.join(ROOT, "include")
+    for f in sorted(os.listdir(inc)):
+        if f.endswith(".h"):
+            text = re.sub(r"/\*.*?\*/", "", open(os.path.join(inc, f)).read(), flags=re.S)
+            names |= set(re.findall(r"\b(rx_[a-z_0-9]+)\s*\(", text))
+    return sorted(names)
 
 
 def test_every_declared_function_is_exported(lib):
+    from paper_2104_06311_gb300 import rx
     names = declared_functions()
-    assert len(names) >= 15
+    assert len(names) >= 25
     for n in names:
         assert hasattr(lib, n), n
+    assert sorted(rx.EXPORTS) == names   # the binding covers exactly the declared ABI
+
+
+def _chan(**kw):
+    from paper_2104_06311_gb300 import rx
+    d = dict(baud=10e9, L_km=1000.0, D_ps_nm_km=17.0, in_scale=1.0, max_samples=1 << 17, mod_bits=2,
+             ntaps=15, fft_n=0, overlap=0)
+    d.update(kw)
+    return rx.rx_chan_cfg(**d)
+
+
+@pytest.mark.parametrize("bad,status,text", [
+    (dict(mod_bits=3), "RX_EUNSUPPORTED", b"channel 1: mod_bits"),
+    (dict(ntaps=16), "RX_EUNSUPPORTED", b"channel 1: ntaps"),
+    (dict(max_samples=1001), "RX_EINVAL", b"channel 1: max_samples"),
+    (dict(fft_n=3000), "RX_EUNSUPPORTED", b"channel 1: FFT size"),
+    (dict(baud=0.0), "RX_EINVAL", b"channel 1: baud"),
+    (dict(L_km=20000.0, baud=32e9), "RX_EUNSUPPORTED", b"channel 1: dispersion too large"),
+])
+def test_batch_create_reports_the_bad_channel(lib, bad, status, text):
+    from paper_2104_06311_gb300 import rx
+    cfgs = (rx.rx_chan_cfg * 3)(_chan(), _chan(**bad), _chan())
+    h = ct.c_void_p()
+    st = lib.rx_batch_create(ct.byref(h), 3, cfgs)
+    assert st == getattr(rx, status)
+    assert text in lib.rx_batch_last_error(h)
+    lib.rx_batch_destroy(h)
+
+
+def test_batch_create_argument_errors(lib):
+    from paper_2104_06311_gb300 import rx
+    h = ct.c_void_p()
+    cfgs = (rx.rx_chan_cfg * 1)(_chan())
+    assert lib.rx_batch_create(ct.byref(h), 0, cfgs) == rx.RX_EINVAL and not h.value
+    assert lib.rx_batch_create(ct.byref(h), 1, None) == rx.RX_EINVAL and not h.value
+    assert lib.rx_batch_process(None, None, None) == rx.RX_EINVAL
 
 
 def test_status_strings(lib):

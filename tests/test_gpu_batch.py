@@ -1,0 +1,117 @@
+"""GPU parity of the batched form (include/rx_batch.h): every channel of one
+batch against the FP64 oracle on its own seeded input, with the same
+tolerances as the single-stream chain, plus exact agreement with the
+single-stream receiver and with graph replays."""
+import numpy as np
+import pytest
+
+import linksim as L
+from chain_helpers import ensure_built, rx_params, run_gpu
+from test_gpu_chain import check_chain
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    ensure_built()
+
+
+# uneven channels: formats, rates, dispersion (one N per autotuned choice),
+# a ragged length, an acquisition-only stream and an empty one
+LINKS = [
+    L.Link(mod="qpsk", baud=10e9, n_sym=1 << 15, L_km=1000.0, snr_db=12.0, adc="int8", seed=31),
+    L.Link(mod="16qam", baud=32e9, n_sym=1 << 16, L_km=2000.0, jones=(1.1, 0.4), snr_db=18.0, adc="int8", seed=32),
+    L.Link(mod="qpsk", baud=10e9, n_sym=45_000, L_km=8000.0, jones=(0.3, 2.0), snr_db=11.0, adc="int8",
+           seed=33),
+    L.Link(mod="16qam", baud=20e9, n_sym=40_000, L_km=500.0, jones=(2.0, 1.0), snr_db=17.0, adc="f32", seed=34),
+    L.Link(mod="qpsk", baud=25e9, n_sym=6000, L_km=3000.0, snr_db=13.0, adc="int8", seed=35),
+]
+
+
+def _samples(gens):
+    import torch
+    return [torch.from_numpy(np.ascontiguousarray(g.samples)).cuda() for g in gens]
+
+
+def _cfg(lk, g):
+    return dict(baud=lk.baud, L_km=lk.L_km, in_scale=g.in_scale, max_samples=g.samples.shape[0] + 64,
+                mod_bits=4 if lk.mod == "16qam" else 2)
+
+
+class _ChanTrace:
+    def __init__(self, batch, ch):
+        self.batch, self.ch = batch, ch
+
+    def trace(self, w):
+        return self.batch.trace(self.ch, w)
+
+
+def _gpu_dict(batch, ch, out, p):
+    K = out["n"]
+    m = p.bits
+    res = dict(n=K, cdc_n=out["cdc_n"],
+               u=out["cdc"][:, :out["cdc_n"]].cpu().numpy().astype(np.complex128),
+               y=out["eq"][:, :K].cpu().numpy().astype(np.complex128),
+               z=out["sym"][:, :K].cpu().numpy().astype(np.complex128),
+               llr=out["llr"][:, :K * m].cpu().numpy().astype(np.float64),
+               words=out["bits"].cpu().numpy().view(np.uint32), bits_t=out["bits"])
+    res["bits"] = L.unpack_bits(res["words"], K * m)
+    res["rx"] = _ChanTrace(batch, ch)
+    return res
+
+
+def test_batch_channels_match_oracle_and_single_stream():
+    from paper_2104_06311_gb300 import Batch
+    import torch
+    gens = [L.generate(lk) for lk in LINKS]
+    xs = _samples(gens)
+    cfgs = [_cfg(lk, g) for lk, g in zip(LINKS, gens)] + [dict(baud=12e9, L_km=100.0, max_samples=1024)]
+    xs.append(None)   # an empty channel in the same launch
+    b = Batch(cfgs)
+    assert b.get_param(-1, "EQ_CTAS") >= 2 * len(cfgs)
+    outs = b.alloc_outs([x if x is not None else torch.zeros((0, 4), device="cuda") for x in xs],
+                        llr=True, sym=True, eq=True, cdc=True)
+    b.process(xs, outs)
+    b.sync()
+    assert outs[-1]["n"] == 0
+    for ch, (lk, g) in enumerate(zip(LINKS, gens)):
+        N, V = int(b.get_param(ch, "FFT_N")), int(b.get_param(ch, "OVERLAP"))
+        assert V < N // 2 and b.get_param(ch, "EQ_TEAM") >= 2
+        p = rx_params(lk, g.in_scale, fft_n=N, overlap=V)
+        rep, _ = check_chain(p, g, _gpu_dict(b, ch, outs[ch], p), {})
+        print("batch ch", ch, lk.mod, lk.baud, lk.L_km, "N", N, "V", V, "team", b.get_param(ch, "EQ_TEAM"), rep)
+        # the single-stream receiver with the same parameters gives the same bits and symbols
+        if ch in (1, 2):
+            single = run_gpu(p, g.samples)
+            nw = (lk.n_sym * p.bits + 31) // 32
+            assert np.array_equal(single["words"][:, :nw], outs[ch]["bits"].cpu().numpy().view(np.uint32)[:, :nw])
+            yb = outs[ch]["eq"][:, :single["n"]].cpu().numpy().astype(np.complex128)
+            assert np.array_equal(single["y"], yb)
+        # BER through the batch counter
+        ref = torch.from_numpy(L.pack_bits(g.tx_bits).view(np.int32)).cuda()
+        e, n, _ = b.ber(ch, outs[ch]["bits"], ref, lk.n_sym)
+        assert n == 0 or e / n < 0.05
+
+
+def test_batch_graph_replay_is_exact():
+    """Eager call, captured call, replayed call: identical outputs; graphs off: identical too."""
+    from paper_2104_06311_gb300 import Batch
+    links = LINKS[:3]
+    gens = [L.generate(lk) for lk in links]
+    xs = _samples(gens)
+    b = Batch([_cfg(lk, g) for lk, g in zip(links, gens)])
+    runs = []
+    outs = b.alloc_outs(xs, eq=True)    # same pointers every call: call 2 captures, call 3 replays
+    for it in range(4):
+        if it == 3:
+            b.set_param("GRAPH", 0)
+        for o in outs:
+            o["bits"].zero_()
+            o["eq"].zero_()
+        b.process(xs, outs)
+        b.sync()
+        runs.append([(o["bits"].cpu().numpy(), o["eq"].cpu().numpy()) for o in outs])
+    for r in runs[1:]:
+        for (b0, y0), (b1, y1) in zip(runs[0], r):
+            assert np.array_equal(b0, b1) and np.array_equal(y0, y1)
