@@ -18,8 +18,9 @@
  *     and device) and takes the N with the least time per output sample
  *     (N - V samples per window); team sizes come from a cost model of the
  *     equaliser schedule;
- *   - the whole enqueue is captured in a CUDA graph on the first call and
- *     replayed while the call's pointers and sizes stay the same.
+ *   - the whole enqueue is captured in a CUDA graph on the second call with
+ *     the same pointers and sizes (the first runs eagerly) and replayed on
+ *     later calls while they stay the same.
  * Each channel's results equal those of an rx_stream with the same
  * parameters fed the whole stream and flushed.
  *
@@ -60,8 +61,10 @@ enum {
   RX_BP_GRAPH = 100,        /* 1 = capture the enqueue in a CUDA graph (default)   */
   RX_BP_EQ_CTAS = 101,      /* read-only: CTAs of the shared equaliser launch      */
   RX_BP_EQ_TEAM = 102,      /* read-only, per channel: CTAs of its equaliser team  */
-  RX_BP_CDC_NS_PER_SAMPLE = 103  /* read-only, per channel: autotuned CDC kernel
+  RX_BP_CDC_NS_PER_SAMPLE = 103, /* read-only, per channel: autotuned CDC kernel
                                     time per output sample-time [ns]               */
+  RX_BP_PROFILE = 104       /* 1 = time the stages of each call with CUDA events
+                               (such calls run eagerly, not from the graph)        */
 };
 
 /* Create a batch of n_ch channels (1..4096) and allocate all device state,
@@ -91,6 +94,12 @@ rx_status rx_batch_ber(rx_batch *b, int ch, const uint32_t *rx_bits, int64_t rx_
 
 /* Equaliser trace of channel ch as rx_trace (synchronises). */
 rx_status rx_batch_trace(rx_batch *b, int ch, int64_t wave, float *taps, double *dw, double *Phi);
+
+/* Per-stage device time (ms) of profiled calls and kernel launches of all
+ * calls since the last reset, as rx_profile (RX_STAGE_* indices; MOVE counts
+ * state initialisation and output copies).  Synchronises.  Not from the
+ * paper: measurement support. */
+rx_status rx_batch_profile(rx_batch *b, double *ms, int64_t *launches, int reset);
 
 /* Wait for the enqueued work; reports a device-side timeout. */
 rx_status rx_batch_sync(rx_batch *b);

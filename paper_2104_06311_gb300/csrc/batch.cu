@@ -115,6 +115,14 @@ struct rx_batch {
   bool processed = false;
   std::string msg;
   std::vector<void *> allocs;
+  // profiling (RX_BP_PROFILE): stage event pairs of eager calls, launch counts
+  bool profile = false;
+  std::vector<cudaEvent_t> ev_pool;
+  size_t ev_used = 0;
+  std::vector<std::pair<int, size_t>> ev_pending;
+  double stage_ms[RX_STAGE_COUNT] = {0, 0, 0, 0, 0};
+  int64_t stage_launches[RX_STAGE_COUNT] = {0, 0, 0, 0, 0};
+  int64_t graph_launches[RX_STAGE_COUNT] = {0, 0, 0, 0, 0};   // per replay of the captured graph
 };
 
 namespace {
@@ -156,6 +164,8 @@ void release(rx_batch *b) {
   if (b->h_err) cudaFreeHost(b->h_err);
   if (b->err_ev) cudaEventDestroy(b->err_ev);
   if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+  for (cudaEvent_t e : b->ev_pool) cudaEventDestroy(e);
+  b->ev_pool.clear();
   b->cap_stream = nullptr;
   b->h_L = nullptr;
   b->h_err = nullptr;
@@ -246,22 +256,57 @@ rx_status check_device_error(rx_batch *b, bool wait) {
   return RX_OK;
 }
 
-// Everything one call enqueues (eagerly or under capture).
-rx_status enqueue(rx_batch *b, const rx_in *ins, rx_out *outs, cudaStream_t s) {
+// Event pair around a stage of an eager, profiled call.
+struct BStage {
+  rx_batch *b;
+  int stage;
+  cudaStream_t s;
+  size_t idx = (size_t)-1;
+  BStage(rx_batch *bb, int st, cudaStream_t ss, bool on) : b(bb), stage(st), s(ss) {
+    if (!on) return;
+    while (b->ev_pool.size() < b->ev_used + 2) {
+      cudaEvent_t e;
+      if (cudaEventCreate(&e) != cudaSuccess) return;
+      b->ev_pool.push_back(e);
+    }
+    idx = b->ev_used;
+    b->ev_used += 2;
+    cudaEventRecord(b->ev_pool[idx], s);
+  }
+  ~BStage() {
+    if (idx == (size_t)-1) return;
+    cudaEventRecord(b->ev_pool[idx + 1], s);
+    b->ev_pending.push_back({stage, idx});
+  }
+};
+
+// Everything one call enqueues (eagerly or under capture); launches[] gets
+// the kernel launches per stage.
+rx_status enqueue(rx_batch *b, const rx_in *ins, rx_out *outs, cudaStream_t s, bool timed, int64_t *launches) {
   BX_CUDA(cudaMemcpyAsync(b->d_L, b->h_L, (size_t)b->n_ch * sizeof(EqLaunch), cudaMemcpyHostToDevice, s), "launch table");
   BX_CUDA(cudaMemsetAsync(b->m_carry, 0, (size_t)2 * b->n_ch * sizeof(int64_t), s), "unwrap carry");
   batch_init_kernel<<<b->n_ch, 128, 0, s>>>(b->d_L);
   BX_CUDA(cudaGetLastError(), "state init");
-  for (int i = 0; i < b->n_ch; ++i) {
-    const Chan &c = b->ch[i];
-    const int64_t n = ins[i].n;
-    if (n == 0) continue;
-    const int Sh = c.N - c.V;
-    BX_CUDA(launch_cdc(c.N, c.V, nullptr, 0, 0, ins[i].data, 0, n, ins[i].dtype, (float)c.cfg.in_scale, c.H, c.tw,
-                       c.u, 0, c.u_stride, 0, (n + Sh - 1) / Sh, n, s),
-            "cdc");
+  launches[RX_STAGE_MOVE] += 1;
+  {
+    BStage tm(b, RX_STAGE_CDC, s, timed);
+    for (int i = 0; i < b->n_ch; ++i) {
+      const Chan &c = b->ch[i];
+      const int64_t n = ins[i].n;
+      if (n == 0) continue;
+      const int Sh = c.N - c.V;
+      BX_CUDA(launch_cdc(c.N, c.V, nullptr, 0, 0, ins[i].data, 0, n, ins[i].dtype, (float)c.cfg.in_scale, c.H, c.tw,
+                         c.u, 0, c.u_stride, 0, (n + Sh - 1) / Sh, n, s),
+              "cdc");
+      launches[RX_STAGE_CDC] += 1;
+    }
   }
-  BX_CUDA(launch_eq_batch(b->d_L, b->d_team, b->eq_ctas, b->pad_smem, s), "equaliser");
+  {
+    BStage tm(b, RX_STAGE_EQ, s, timed);
+    BX_CUDA(launch_eq_batch(b->d_L, b->d_team, b->eq_ctas, b->pad_smem, s), "equaliser");
+    launches[RX_STAGE_EQ] += 1;
+  }
+  BStage tm(b, RX_STAGE_BPS, s, timed);
   for (int i = 0; i < b->n_ch; ++i) {
     const Chan &c = b->ch[i];
     const EqLaunch &L = b->h_L[i];
@@ -298,11 +343,16 @@ rx_status enqueue(rx_batch *b, const rx_in *ins, rx_out *outs, cudaStream_t s) {
     B.sym_stride = outs[i].sym_stride;
     B.out_first = 0;
     BX_CUDA(launch_bps(B, s), "bps");
-    if (outs[i].eq)
+    launches[RX_STAGE_BPS] += 3;
+    if (outs[i].eq) {
       BX_CUDA(launch_copy_cols(reinterpret_cast<float2 *>(outs[i].eq), outs[i].eq_stride, c.y, c.y_stride, K, s), "eq out");
-    if (outs[i].cdc)
+      launches[RX_STAGE_MOVE] += 1;
+    }
+    if (outs[i].cdc) {
       BX_CUDA(launch_copy_cols(reinterpret_cast<float2 *>(outs[i].cdc), outs[i].cdc_stride, c.u, c.u_stride, ins[i].n, s),
               "cdc out");
+      launches[RX_STAGE_MOVE] += 1;
+    }
   }
   return RX_OK;
 }
@@ -456,6 +506,10 @@ rx_status rx_batch_set_param(rx_batch *b, int key, double v) {
     b->use_graph = v != 0;
     return RX_OK;
   }
+  if (key == RX_BP_PROFILE) {
+    b->profile = v != 0;
+    return RX_OK;
+  }
   return bfail(b, RX_EINVAL, "unknown or read-only batch parameter");
 }
 
@@ -464,6 +518,7 @@ rx_status rx_batch_get_param(rx_batch *b, int ch, int key, double *v) {
   if (ch == -1) {
     switch (key) {
       case RX_BP_GRAPH: *v = b->use_graph; return RX_OK;
+      case RX_BP_PROFILE: *v = b->profile; return RX_OK;
       case RX_BP_EQ_CTAS: *v = b->eq_ctas; return RX_OK;
       default: return bfail(b, RX_EINVAL, "unknown batch parameter");
     }
@@ -536,7 +591,9 @@ rx_status rx_batch_process(rx_batch *b, const rx_in *ins, rx_out *outs) {
                             (int64_t)(uintptr_t)o.eq, o.eq_stride, (int64_t)(uintptr_t)o.cdc, o.cdc_stride};
     sig.insert(sig.end(), std::begin(vals), std::end(vals));
   }
-  const bool replay = b->use_graph && b->gexec && sig == b->gsig;
+  // profiled calls run eagerly: events cannot time the inside of a graph
+  const bool graphs = b->use_graph && !b->profile;
+  const bool replay = graphs && b->gexec && sig == b->gsig;
   if (sig != b->hsig) {
     // the launch table is about to change: earlier work that reads it must be done
     BX_CUDA(cudaStreamSynchronize(b->stream), "launch table");
@@ -586,14 +643,16 @@ rx_status rx_batch_process(rx_batch *b, const rx_in *ins, rx_out *outs) {
   }
   if (replay) {
     BX_CUDA(cudaGraphLaunch(b->gexec, b->stream), "graph replay");
-  } else if (b->use_graph && sig == b->sig) {
+    for (int k = 0; k < RX_STAGE_COUNT; ++k) b->stage_launches[k] += b->graph_launches[k];
+  } else if (graphs && sig == b->sig) {
     // second call with these pointers and sizes: capture, then replay from now on
     if (b->gexec) cudaGraphExecDestroy(b->gexec);
     b->gexec = nullptr;
     // captured on the library's own stream (the bound one may be the legacy
     // default stream, which cannot be captured); replayed on the bound one
     BX_CUDA(cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal), "capture");
-    rx_status st = enqueue(b, ins, outs, b->cap_stream);
+    int64_t gl[RX_STAGE_COUNT] = {0, 0, 0, 0, 0};
+    rx_status st = enqueue(b, ins, outs, b->cap_stream, false, gl);
     cudaGraph_t g = nullptr;
     const cudaError_t e = cudaStreamEndCapture(b->cap_stream, &g);
     if (st != RX_OK) {
@@ -608,9 +667,13 @@ rx_status rx_batch_process(rx_batch *b, const rx_in *ins, rx_out *outs) {
       return bcuda(b, e2, "graph instantiate");
     }
     b->gsig = sig;
+    for (int k = 0; k < RX_STAGE_COUNT; ++k) {
+      b->graph_launches[k] = gl[k];
+      b->stage_launches[k] += gl[k];
+    }
     BX_CUDA(cudaGraphLaunch(b->gexec, b->stream), "graph launch");
   } else {
-    s = enqueue(b, ins, outs, b->stream);
+    s = enqueue(b, ins, outs, b->stream, b->profile, b->stage_launches);
     if (s != RX_OK) return s;
     b->sig = sig;
   }
@@ -661,6 +724,27 @@ rx_status rx_batch_trace(rx_batch *b, int ch, int64_t wave, float *taps, double 
       }
   *dw = fo[0];
   *Phi = fo[1];
+  return RX_OK;
+}
+
+rx_status rx_batch_profile(rx_batch *b, double *ms, int64_t *launches, int reset) {
+  if (!b) return RX_EINVAL;
+  BX_CUDA(cudaStreamSynchronize(b->stream), "profile wait");
+  for (const auto &pe : b->ev_pending) {
+    float t = 0.f;
+    BX_CUDA(cudaEventElapsedTime(&t, b->ev_pool[pe.second], b->ev_pool[pe.second + 1]), "profile");
+    b->stage_ms[pe.first] += t;
+  }
+  b->ev_pending.clear();
+  b->ev_used = 0;
+  for (int i = 0; i < RX_STAGE_COUNT; ++i) {
+    if (ms) ms[i] = b->stage_ms[i];
+    if (launches) launches[i] = b->stage_launches[i];
+    if (reset) {
+      b->stage_ms[i] = 0;
+      b->stage_launches[i] = 0;
+    }
+  }
   return RX_OK;
 }
 

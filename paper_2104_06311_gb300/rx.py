@@ -30,8 +30,8 @@ EXPORTS = ["rx_create", "rx_set_param", "rx_get_param", "rx_set_cuda_stream", "r
            "rx_bps_demap_noalloc",
            "rx_batch_create", "rx_batch_set_param", "rx_batch_get_param", "rx_batch_set_cuda_stream",
            "rx_batch_process", "rx_batch_ber", "rx_batch_trace", "rx_batch_sync", "rx_batch_destroy",
-           "rx_batch_last_error"]
-BATCH_PARAMS = {"GRAPH": 100, "EQ_CTAS": 101, "EQ_TEAM": 102, "CDC_NS_PER_SAMPLE": 103}
+           "rx_batch_last_error", "rx_batch_profile"]
+BATCH_PARAMS = {"GRAPH": 100, "EQ_CTAS": 101, "EQ_TEAM": 102, "CDC_NS_PER_SAMPLE": 103, "PROFILE": 104}
 
 
 class rx_in(ct.Structure):
@@ -102,6 +102,7 @@ def load(path: str = LIB_PATH) -> ct.CDLL:
                                  ct.POINTER(ct.c_uint64), ct.POINTER(ct.c_int32)]
     lib.rx_batch_trace.argtypes = [P, ct.c_int, ct.c_int64, ct.POINTER(ct.c_float), ct.POINTER(ct.c_double),
                                    ct.POINTER(ct.c_double)]
+    lib.rx_batch_profile.argtypes = [P, ct.POINTER(ct.c_double), ct.POINTER(ct.c_int64), ct.c_int]
     lib.rx_batch_sync.argtypes = [P]
     lib.rx_batch_destroy.argtypes = [P]
     lib.rx_batch_destroy.restype = None
@@ -431,6 +432,15 @@ class Batch:
         return (a[0::2] + 1j * a[1::2]).reshape(2, 2, T), dw.value, Phi.value
 
     trace = rx_batch_trace
+
+    def rx_batch_profile(self, reset=False):
+        """{stage: (ms, launches)} since the last reset of the counters."""
+        ms = (ct.c_double * len(STAGES))()
+        n = (ct.c_int64 * len(STAGES))()
+        _bcheck(self.lib, self.h, self.lib.rx_batch_profile(self.h, ms, n, 1 if reset else 0))
+        return {k: (ms[i], n[i]) for i, k in enumerate(STAGES)}
+
+    profile = rx_batch_profile
 
     def rx_batch_sync(self):
         _bcheck(self.lib, self.h, self.lib.rx_batch_sync(self.h))
