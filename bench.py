@@ -276,7 +276,12 @@ def bench_batch(args, rank, world, local):
                    "l2": f"inputs ({n_total * 4 >> 20} MiB) and CDC intermediates exceed L2; no flush",
                    "parallelism": f"replicas x{world}" if world > 1 else "one batch"},
         "decoded_gbps": bits_total * args.steps * world / (ms / 1e3) / 1e9,
-        "ber_per_channel": {"min": min(x for x in ber if x is not None), "max": max(x for x in ber if x is not None)},
+        "ber_per_channel": {"min": min(x for x in ber if x is not None),
+                            "median": statistics.median(x for x in ber if x is not None),
+                            "max": max(x for x in ber if x is not None),
+                            "channels_above_0.1": sum(1 for x in ber if x is not None and x > 0.1),
+                            "note": "16QAM channels below ~15 dB Es/N0 lose lock under the blind defaults "
+                                    "(the oracle shows the same)"},
         "stage_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
         "gpu_launches": int(launches),
         "roofline": roof,
