@@ -69,10 +69,15 @@ def conv1d_backward(h: np.ndarray, W: np.ndarray, da: np.ndarray):
     return dh, dW, db
 
 
-def forward(params, x: np.ndarray):
-    """Returns (y, cache) with cache = [h_0, a_1, h_1, ..., a_L]."""
-    h = x
-    cache = [x]
+def forward(params, x: np.ndarray, x_conv: np.ndarray | None = None):
+    """Returns (y, cache) with cache = [h_0, a_1, h_1, ..., a_L].
+
+    x_conv (default x) feeds the first convolution; the residual always adds
+    x.  A caller whose network stores its input features at lower precision
+    passes them rounded here (a statement about the input, not the method).
+    """
+    h = x if x_conv is None else x_conv
+    cache = [h]
     L = len(params)
     for l, (W, b) in enumerate(params):
         a = conv1d(h, W, b)
@@ -83,9 +88,9 @@ def forward(params, x: np.ndarray):
     return x + h, cache
 
 
-def loss_and_grads(params, x: np.ndarray, t: np.ndarray):
-    """J and its gradients [(dW, db)] per layer."""
-    y, cache = forward(params, x)
+def loss_and_grads(params, x: np.ndarray, t: np.ndarray, x_conv: np.ndarray | None = None):
+    """J and its gradients [(dW, db)] per layer (x_conv as in forward)."""
+    y, cache = forward(params, x, x_conv)
     K = x.shape[0]
     diff = y - t
     J = float(np.sum(diff * diff) / (4.0 * K))

@@ -2,7 +2,7 @@
 
 The CUDA kernels live in ``csrc/`` and build into ``librx.so``
 (``python -m paper_2104_06311_gb300.build``); ``rx`` is the ctypes binding of
-the C ABI declared in ``include/rx.h`` (``Receiver``) and
-``include/rx_batch.h`` (``Batch``).
+the C ABI declared in ``include/rx.h`` (``Receiver``), ``include/rx_batch.h``
+(``Batch``) and ``include/rx_cnn.h`` (``CNN``).
 """
-from .rx import Batch, Receiver, load, RxError  # noqa: F401
+from .rx import CNN, Batch, Receiver, load, RxError  # noqa: F401

@@ -1,0 +1,657 @@
+// Learned post-equaliser (declared in rx_cnn.h): BF16 tensor-core
+// convolutions with FP32 accumulation for the forward pass, the input
+// gradient and the weight gradient, and an FP32 Adam update.
+//
+// Layout.  Activations are channels-last BF16 rows [n][c] (c = 16 for the
+// 4 input features and for dJ/dy, zero padded; 64 for hidden layers).  A
+// convolution out[n][co] = sum_k sum_ci in[n + k - 7][ci] W[k][ci][co] is 15
+// accumulated GEMMs over shifted views of the same input rows, so one CTA
+// stages a tile of 128 + 14 input rows and all 15 weight matrices in shared
+// memory and its 8 warps each produce 16 rows x all output channels with
+// mma.m16n8k16 (BF16 in, FP32 accumulate); ldmatrix feeds the fragments
+// from rows padded by 16 bytes (conflict-free).  The input gradient is the
+// same convolution with the taps reversed and W transposed (packed once per
+// update), fused with the ReLU mask of the layer below.  The weight
+// gradient dW[k][ci][co] = sum_n in[n + k - 7][ci] dz[n][co] is a GEMM with
+// the symbols as the reduction dimension: CTAs own (symbol chunk, 3 taps),
+// read both operands transposed by ldmatrix.trans, and add their partial
+// sums into the FP32 gradient with atomics.
+#include <cuda_bf16.h>
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/rx_cnn.h"
+
+namespace {
+
+typedef __nv_bfloat16 bf16;
+
+constexpr int KS = 15, HALF = 7, CH = 64, FEAT = 4, FEATP = 16;
+constexpr int TM = 128;          // symbols per tile
+constexpr int kThreads = 256;    // 8 warps x 16 rows
+constexpr int TG = 3;            // taps per weight-gradient CTA (5 groups)
+
+__device__ __forceinline__ unsigned smem_u32(const void *p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void ldsm_x4(unsigned addr, unsigned &r0, unsigned &r1, unsigned &r2, unsigned &r3) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+               : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3) : "r"(addr));
+}
+__device__ __forceinline__ void ldsm_x4_t(unsigned addr, unsigned &r0, unsigned &r1, unsigned &r2, unsigned &r3) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+               : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3) : "r"(addr));
+}
+__device__ __forceinline__ void ldsm_x2(unsigned addr, unsigned &r0, unsigned &r1) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0,%1}, [%2];\n" : "=r"(r0), "=r"(r1) : "r"(addr));
+}
+__device__ __forceinline__ void ldsm_x2_t(unsigned addr, unsigned &r0, unsigned &r1) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x2.trans.shared.b16 {%0,%1}, [%2];\n" : "=r"(r0), "=r"(r1) : "r"(addr));
+}
+// D = A (16x16, row) * B (16x8, col) + D, BF16 inputs, FP32 accumulate
+__device__ __forceinline__ void mma(float (&c)[4], unsigned a0, unsigned a1, unsigned a2, unsigned a3, unsigned b0,
+                                    unsigned b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+enum { EPI_RELU = 0, EPI_LAST = 1, EPI_MASK = 2 };
+
+struct ConvArgs {
+  const bf16 *in;             // [K][CIN]
+  int64_t K;
+  const bf16 *w;              // [15][COUT][CIN]
+  const float *bias;          // [n_bias] (EPI_RELU, EPI_LAST)
+  int n_bias;
+  bf16 *out;                  // [K][COUT] (EPI_RELU, EPI_MASK)
+  const bf16 *mask;           // [K][COUT] (EPI_MASK): keep where mask > 0
+  // EPI_LAST: y = z + conv (4 channels = 2 complex pols); training also
+  // forms dJ/dy = 2 (y - t) / (4K) into dout [K][16] and the loss
+  const float2 *z; int64_t z_stride;
+  float2 *y; int64_t y_stride;
+  const float2 *t; int64_t t_stride;
+  bf16 *dout;
+  double *loss;
+  float inv4k;
+};
+
+template <int CIN, int COUT, int EPI>
+__global__ void __launch_bounds__(kThreads, 1) conv_kernel(const ConvArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr int CP = CIN + 8;                       // padded shared row (elements)
+  bf16 *Ws = reinterpret_cast<bf16 *>(smem_raw);    // [15][COUT][CP]
+  bf16 *Xs = Ws + KS * COUT * CP;                   // [TM + 14][CP]
+  constexpr int CH8 = CIN / 8;                      // 16-byte pieces per row
+  for (int i = threadIdx.x; i < KS * COUT * CH8; i += kThreads) {
+    const int row = i / CH8, p = i % CH8;
+    *reinterpret_cast<uint4 *>(Ws + row * CP + p * 8) = *reinterpret_cast<const uint4 *>(a.w + (size_t)row * CIN + p * 8);
+  }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int group = lane >> 2, tig = lane & 3;
+  const int m0 = warp * 16;
+  // ldmatrix row / column of this lane: A (rows 0-7 | 8-15) x (cols 0-7 | 8-15) in
+  // fragment order; B (out channels 0-7 | 8-15) x (in channels 0-7 | 8-15)
+  const int a_row = (lane & 7) + ((lane >> 3) & 1) * 8, a_col = (lane >> 4) * 8;
+  const int b_row = (lane & 7) + (lane >> 4) * 8, b_col = ((lane >> 3) & 1) * 8;
+  const int64_t n_tiles = (a.K + TM - 1) / TM;
+  double loss_part = 0.0;
+  for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+    const int64_t n0 = tile * TM;
+    __syncthreads();   // weights staged, previous tile's rows consumed
+    for (int i = threadIdx.x; i < (TM + 2 * HALF) * CH8; i += kThreads) {
+      const int r = i / CH8, p = i % CH8;
+      const int64_t n = n0 - HALF + r;
+      uint4 v = make_uint4(0u, 0u, 0u, 0u);
+      if (n >= 0 && n < a.K) v = *reinterpret_cast<const uint4 *>(a.in + n * CIN + p * 8);
+      *reinterpret_cast<uint4 *>(Xs + r * CP + p * 8) = v;
+    }
+    __syncthreads();
+    float acc[COUT / 8][4];
+#pragma unroll
+    for (int j = 0; j < COUT / 8; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.f;
+#pragma unroll 1
+    for (int k = 0; k < KS; ++k) {
+#pragma unroll
+      for (int cc = 0; cc < CIN / 16; ++cc) {
+        unsigned a0, a1, a2, a3;
+        ldsm_x4(smem_u32(Xs + (m0 + k + a_row) * CP + cc * 16 + a_col), a0, a1, a2, a3);
+        if constexpr (COUT >= 16) {
+#pragma unroll
+          for (int jp = 0; jp < COUT / 16; ++jp) {
+            unsigned b0, b1, b2, b3;
+            ldsm_x4(smem_u32(Ws + (k * COUT + jp * 16 + b_row) * CP + cc * 16 + b_col), b0, b1, b2, b3);
+            mma(acc[2 * jp], a0, a1, a2, a3, b0, b1);
+            mma(acc[2 * jp + 1], a0, a1, a2, a3, b2, b3);
+          }
+        } else {
+          unsigned b0, b1;
+          ldsm_x2(smem_u32(Ws + (k * COUT + (lane & 7)) * CP + cc * 16 + b_col), b0, b1);
+          mma(acc[0], a0, a1, a2, a3, b0, b1);
+        }
+      }
+    }
+    // epilogue: rows n0 + m0 + group (+8), channels j*8 + 2 tig (+1)
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int64_t n = n0 + m0 + group + 8 * h;
+      if (n >= a.K) continue;
+      if constexpr (EPI == EPI_LAST) {
+        if (tig < 2) {   // channels 2 tig, 2 tig + 1 = (re, im) of pol tig
+          const int pol = tig;
+          const float2 x = a.z[pol * a.z_stride + n];
+          const float b0 = 2 * pol < a.n_bias ? a.bias[2 * pol] : 0.f;
+          const float b1 = 2 * pol + 1 < a.n_bias ? a.bias[2 * pol + 1] : 0.f;
+          const float2 yv = make_float2(x.x + (acc[0][2 * h] + b0), x.y + (acc[0][2 * h + 1] + b1));
+          if (a.y) a.y[pol * a.y_stride + n] = yv;
+          if (a.t) {
+            const float2 tv = a.t[pol * a.t_stride + n];
+            const float dx = yv.x - tv.x, dy = yv.y - tv.y;
+            loss_part += (double)dx * dx + (double)dy * dy;
+            *reinterpret_cast<__nv_bfloat162 *>(a.dout + n * FEATP + 2 * pol) =
+                __floats2bfloat162_rn(2.f * dx * a.inv4k, 2.f * dy * a.inv4k);
+          }
+        }
+      } else {
+#pragma unroll
+        for (int j = 0; j < COUT / 8; ++j) {
+          const int co = j * 8 + 2 * tig;
+          float v0 = acc[j][2 * h], v1 = acc[j][2 * h + 1];
+          if constexpr (EPI == EPI_RELU) {
+            v0 = fmaxf(v0 + (co < a.n_bias ? a.bias[co] : 0.f), 0.f);
+            v1 = fmaxf(v1 + (co + 1 < a.n_bias ? a.bias[co + 1] : 0.f), 0.f);
+          } else {
+            const __nv_bfloat162 mk = *reinterpret_cast<const __nv_bfloat162 *>(a.mask + n * COUT + co);
+            v0 = __bfloat162float(mk.x) > 0.f ? v0 : 0.f;
+            v1 = __bfloat162float(mk.y) > 0.f ? v1 : 0.f;
+          }
+          *reinterpret_cast<__nv_bfloat162 *>(a.out + n * COUT + co) = __floats2bfloat162_rn(v0, v1);
+        }
+      }
+    }
+  }
+  if constexpr (EPI == EPI_LAST) {
+    if (a.t) {
+      for (int o = 16; o >= 1; o >>= 1) loss_part += __shfl_xor_sync(0xffffffffu, loss_part, o);
+      if (lane == 0 && loss_part != 0.0) atomicAdd(a.loss, loss_part * (double)a.inv4k);
+    }
+  }
+}
+
+struct DwArgs {
+  const bf16 *in;     // layer input [K][CIN]
+  const bf16 *dz;     // dJ/d(pre-activation) [K][COUT]
+  int64_t K, chunk;
+  float *dw;          // master layout [15][ci_true][co_true] (accumulated)
+  float *db;          // [co_true] (accumulated)
+  int ci_true, co_true;
+};
+
+// dW[k][ci][co] += sum_n in[n + k - 7][ci] dz[n][co] over this CTA's symbols,
+// taps 3 blockIdx.y .. + 2; CTAs with blockIdx.y == 0 also add db.
+template <int CIN, int COUT>
+__global__ void __launch_bounds__(kThreads) dw_kernel(const DwArgs a) {
+  constexpr int CPX = CIN + 8, CPZ = COUT + 8;
+  __shared__ __align__(16) bf16 Xs[(TM + 2 * HALF) * CPX];
+  __shared__ __align__(16) bf16 Zs[TM * CPZ];
+  constexpr int CB = CIN / 16, CT = COUT / 8, WPB = 8 / CB, TPW = CT / WPB;
+  static_assert(TPW >= 1 && CB * WPB == 8, "warp layout");
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int group = lane >> 2, tig = lane & 3;
+  const int cb = warp % CB, tile0 = (warp / CB) * TPW;
+  const int tap0 = blockIdx.y * TG;
+  const int64_t s0 = (int64_t)blockIdx.x * a.chunk, s1 = min(a.K, s0 + a.chunk);
+  float acc[TG][TPW][4];
+#pragma unroll
+  for (int t = 0; t < TG; ++t)
+#pragma unroll
+    for (int j = 0; j < TPW; ++j) acc[t][j][0] = acc[t][j][1] = acc[t][j][2] = acc[t][j][3] = 0.f;
+  float dbp = 0.f;
+  // ldmatrix.trans lanes: matrix j = lane / 8
+  const int ax_row = (lane & 7) + ((lane >> 4) & 1) * 8, ax_col = cb * 16 + ((lane >> 3) & 1) * 8;
+  const int bz_row = (lane & 7) + ((lane >> 3) & 1) * 8;
+  for (int64_t n0 = s0; n0 < s1; n0 += TM) {
+    __syncthreads();
+    for (int i = threadIdx.x; i < (TM + 2 * HALF) * (CIN / 8); i += kThreads) {
+      const int r = i / (CIN / 8), p = i % (CIN / 8);
+      const int64_t n = n0 - HALF + r;
+      uint4 v = make_uint4(0u, 0u, 0u, 0u);
+      if (n >= 0 && n < a.K) v = *reinterpret_cast<const uint4 *>(a.in + n * CIN + p * 8);
+      *reinterpret_cast<uint4 *>(Xs + r * CPX + p * 8) = v;
+    }
+    for (int i = threadIdx.x; i < TM * (COUT / 8); i += kThreads) {
+      const int r = i / (COUT / 8), p = i % (COUT / 8);
+      const int64_t n = n0 + r;
+      uint4 v = make_uint4(0u, 0u, 0u, 0u);
+      if (n < s1) v = *reinterpret_cast<const uint4 *>(a.dz + n * COUT + p * 8);
+      *reinterpret_cast<uint4 *>(Zs + r * CPZ + p * 8) = v;
+    }
+    __syncthreads();
+#pragma unroll 1
+    for (int s = 0; s < TM / 16; ++s) {
+      unsigned b[TPW][2];
+#pragma unroll
+      for (int j = 0; j < TPW; ++j)
+        ldsm_x2_t(smem_u32(Zs + (16 * s + bz_row) * CPZ + (tile0 + j) * 8), b[j][0], b[j][1]);
+#pragma unroll
+      for (int t = 0; t < TG; ++t) {
+        unsigned a0, a1, a2, a3;
+        ldsm_x4_t(smem_u32(Xs + (16 * s + tap0 + t + ax_row) * CPX + ax_col), a0, a1, a2, a3);
+#pragma unroll
+        for (int j = 0; j < TPW; ++j) mma(acc[t][j], a0, a1, a2, a3, b[j][0], b[j][1]);
+      }
+    }
+    if (blockIdx.y == 0 && threadIdx.x < COUT) {
+      for (int r = 0; r < TM; ++r) dbp += __bfloat162float(Zs[r * CPZ + threadIdx.x]);
+    }
+  }
+#pragma unroll
+  for (int t = 0; t < TG; ++t) {
+    const int k = tap0 + t;
+#pragma unroll
+    for (int j = 0; j < TPW; ++j) {
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int ci = cb * 16 + group + 8 * h;
+        const int co = (tile0 + j) * 8 + 2 * tig;
+        if (ci < a.ci_true) {
+          if (co < a.co_true) atomicAdd(&a.dw[((size_t)k * a.ci_true + ci) * a.co_true + co], acc[t][j][2 * h]);
+          if (co + 1 < a.co_true) atomicAdd(&a.dw[((size_t)k * a.ci_true + ci) * a.co_true + co + 1], acc[t][j][2 * h + 1]);
+        }
+      }
+    }
+  }
+  if (blockIdx.y == 0 && threadIdx.x < a.co_true && dbp != 0.f) atomicAdd(&a.db[threadIdx.x], dbp);
+}
+
+__global__ void features_kernel(const float2 *__restrict__ z, int64_t z_stride, int64_t K, bf16 *__restrict__ x) {
+  for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < K; n += (int64_t)gridDim.x * blockDim.x) {
+    const float2 p0 = z[n], p1 = z[z_stride + n];
+    __nv_bfloat162 v[8];
+    v[0] = __floats2bfloat162_rn(p0.x, p0.y);
+    v[1] = __floats2bfloat162_rn(p1.x, p1.y);
+    for (int i = 2; i < 8; ++i) v[i] = __floats2bfloat162_rn(0.f, 0.f);
+    uint4 *dst = reinterpret_cast<uint4 *>(x + n * FEATP);
+    dst[0] = *reinterpret_cast<uint4 *>(&v[0]);
+    dst[1] = *reinterpret_cast<uint4 *>(&v[4]);
+  }
+}
+
+// Adam on the flat FP32 parameters (c1 = 1 - b1^s, c2 = 1 - b2^s).
+__global__ void adam_kernel(float *__restrict__ P, const float *__restrict__ G, float *__restrict__ M,
+                            float *__restrict__ V, int64_t n, float lr, float c1, float c2) {
+  const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const float g = G[i];
+    const float m = b1 * M[i] + (1.f - b1) * g;
+    const float v = b2 * V[i] + (1.f - b2) * g * g;
+    M[i] = m;
+    V[i] = v;
+    P[i] -= lr * (m / c1) / (sqrtf(v / c2) + eps);
+  }
+}
+
+// Packed BF16 weights of one layer from the master W[k][ci][co]:
+//   wf[k][co][ci]  (forward, COUTP x CINP, zero padded)
+//   wb[j][ci][co]  = W[14 - j][ci][co] (input gradient, ci x COPB, zero padded)
+__global__ void pack_kernel(const float *__restrict__ W, int ci_true, int co_true, bf16 *__restrict__ wf, int cinp,
+                            int coutp, bf16 *__restrict__ wb, int copb) {
+  const int nf = KS * coutp * cinp;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nf; i += gridDim.x * blockDim.x) {
+    const int k = i / (coutp * cinp), co = (i / cinp) % coutp, ci = i % cinp;
+    const float v = (ci < ci_true && co < co_true) ? W[((size_t)k * ci_true + ci) * co_true + co] : 0.f;
+    wf[i] = __float2bfloat16_rn(v);
+  }
+  if (!wb) return;
+  const int nb = KS * ci_true * copb;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nb; i += gridDim.x * blockDim.x) {
+    const int j = i / (ci_true * copb), ci = (i / copb) % ci_true, co = i % copb;
+    const float v = co < co_true ? W[((size_t)(KS - 1 - j) * ci_true + ci) * co_true + co] : 0.f;
+    wb[i] = __float2bfloat16_rn(v);
+  }
+}
+
+__global__ void add_kernel(double *acc, const double *v) { *acc += *v; }
+
+template <int CIN, int COUT, int EPI>
+size_t conv_smem() {
+  return (size_t)(KS * COUT + TM + 2 * HALF) * (CIN + 8) * sizeof(bf16);
+}
+
+template <int CIN, int COUT, int EPI>
+cudaError_t conv_prepare() {
+  return cudaFuncSetAttribute(conv_kernel<CIN, COUT, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)conv_smem<CIN, COUT, EPI>());
+}
+
+}  // namespace
+
+struct rx_cnn {
+  int L = 0;
+  int64_t Kmax = 0, n_params = 0;
+  std::vector<int> ci, co;             // true dims per layer
+  std::vector<int64_t> off_w, off_b;   // offsets into the flat parameters
+  cudaStream_t stream = nullptr;
+  int sms = 0;
+  float *P = nullptr, *G = nullptr, *M = nullptr, *V = nullptr;
+  std::vector<bf16 *> wf, wb;
+  bf16 *x0 = nullptr, *dout = nullptr, *dza = nullptr, *dzb = nullptr;
+  std::vector<bf16 *> h;               // hidden outputs h_1 .. h_{L-1}
+  double *loss = nullptr;
+  int64_t step = 0;
+  std::vector<void *> allocs;
+  std::string msg;
+};
+
+namespace {
+
+rx_status cfail(rx_cnn *c, rx_status s, const std::string &m) {
+  if (c) c->msg = m;
+  return s;
+}
+
+#define CX_CUDA(call, where)                                                                   \
+  do {                                                                                         \
+    cudaError_t e_ = (call);                                                                   \
+    if (e_ != cudaSuccess) return cfail(c, RX_ECUDA, std::string(where) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+template <class Tp>
+rx_status calloc_dev(rx_cnn *c, Tp **p, size_t count) {
+  void *q = nullptr;
+  if (cudaMalloc(&q, std::max<size_t>(count, 1) * sizeof(Tp)) != cudaSuccess) {
+    cudaGetLastError();
+    return cfail(c, RX_ENOMEM, "device allocation failed");
+  }
+  c->allocs.push_back(q);
+  *p = static_cast<Tp *>(q);
+  return RX_OK;
+}
+
+void release(rx_cnn *c) {
+  for (void *p : c->allocs) cudaFree(p);
+  c->allocs.clear();
+}
+
+int conv_grid(const rx_cnn *c, int64_t K) {
+  return (int)std::max<int64_t>(1, std::min<int64_t>((K + TM - 1) / TM, c->sms));
+}
+
+template <int CIN, int COUT, int EPI>
+cudaError_t launch_conv(const rx_cnn *c, const ConvArgs &a) {
+  conv_kernel<CIN, COUT, EPI><<<conv_grid(c, a.K), kThreads, conv_smem<CIN, COUT, EPI>(), c->stream>>>(a);
+  return cudaGetLastError();
+}
+
+template <int CIN, int COUT>
+cudaError_t launch_dw(const rx_cnn *c, const bf16 *in, const bf16 *dz, int64_t K, int l) {
+  DwArgs a;
+  a.in = in;
+  a.dz = dz;
+  a.K = K;
+  const int64_t want = std::max<int64_t>(1, (int64_t)2 * c->sms / (KS / TG));
+  a.chunk = ((K + want - 1) / want + TM - 1) / TM * TM;
+  a.dw = c->G + c->off_w[l];
+  a.db = c->G + c->off_b[l];
+  a.ci_true = c->ci[l];
+  a.co_true = c->co[l];
+  dim3 grid((unsigned)((K + a.chunk - 1) / a.chunk), KS / TG);
+  dw_kernel<CIN, COUT><<<grid, kThreads, 0, c->stream>>>(a);
+  return cudaGetLastError();
+}
+
+rx_status check_sym(rx_cnn *c, const float *p, int64_t stride, int64_t K, const char *what) {
+  if (!p) return cfail(c, RX_EINVAL, std::string("null ") + what);
+  if ((uintptr_t)p % 8) return cfail(c, RX_EINVAL, std::string(what) + " misaligned");
+  if (stride < K) return cfail(c, RX_EINVAL, std::string(what) + " stride too small");
+  return RX_OK;
+}
+
+// Forward pass; with t, also the loss and dJ/dy.  y may be NULL.
+rx_status forward(rx_cnn *c, const float *z, int64_t zs, float *y, int64_t ys, const float *t, int64_t ts, int64_t K) {
+  const int g = (int)std::min<int64_t>((K + 255) / 256, 4 * c->sms);
+  features_kernel<<<std::max(1, g), 256, 0, c->stream>>>(reinterpret_cast<const float2 *>(z), zs, K, c->x0);
+  CX_CUDA(cudaGetLastError(), "features");
+  const int L = c->L;
+  for (int l = 0; l < L; ++l) {
+    ConvArgs a;
+    memset(&a, 0, sizeof(a));
+    a.K = K;
+    a.w = c->wf[l];
+    a.bias = c->P + c->off_b[l];
+    a.n_bias = c->co[l];
+    if (l < L - 1) {
+      a.in = l == 0 ? c->x0 : c->h[l - 1];
+      a.out = c->h[l];
+      CX_CUDA((l == 0 ? launch_conv<FEATP, CH, EPI_RELU>(c, a) : launch_conv<CH, CH, EPI_RELU>(c, a)), "conv");
+    } else {
+      a.in = L == 1 ? c->x0 : c->h[L - 2];
+      a.z = reinterpret_cast<const float2 *>(z);
+      a.z_stride = zs;
+      a.y = reinterpret_cast<float2 *>(y);
+      a.y_stride = ys;
+      a.t = reinterpret_cast<const float2 *>(t);
+      a.t_stride = ts;
+      a.dout = c->dout;
+      a.loss = c->loss;
+      a.inv4k = (float)(1.0 / (4.0 * (double)K));
+      CX_CUDA((launch_conv<CH, 8, EPI_LAST>(c, a)), "conv (last)");
+    }
+  }
+  return RX_OK;
+}
+
+// Backward pass into c->G (zeroed here) from c->dout and the stored activations.
+rx_status backward(rx_cnn *c, int64_t K) {
+  CX_CUDA(cudaMemsetAsync(c->G, 0, (size_t)c->n_params * sizeof(float), c->stream), "zero grads");
+  const int L = c->L;
+  const bf16 *dz = c->dout;      // [K][16] for the last layer
+  bf16 *bufs[2] = {c->dza, c->dzb};
+  for (int l = L - 1; l >= 0; --l) {
+    const bf16 *in = l == 0 ? c->x0 : c->h[l - 1];
+    const bool last = l == L - 1;
+    if (l == 0) {
+      CX_CUDA((launch_dw<FEATP, CH>(c, in, dz, K, l)), "weight gradient");
+    } else if (last) {
+      CX_CUDA((launch_dw<CH, FEATP>(c, in, dz, K, l)), "weight gradient");
+    } else {
+      CX_CUDA((launch_dw<CH, CH>(c, in, dz, K, l)), "weight gradient");
+    }
+    if (l == 0) break;
+    // dJ/d(pre-activation of layer l - 1) = (dz conv W_l^T reversed) * [h_{l-1} > 0]
+    ConvArgs a;
+    memset(&a, 0, sizeof(a));
+    a.in = dz;
+    a.K = K;
+    a.w = c->wb[l];
+    a.mask = c->h[l - 1];
+    bf16 *out = bufs[l & 1];
+    a.out = out;
+    if (last) {
+      CX_CUDA((launch_conv<FEATP, CH, EPI_MASK>(c, a)), "input gradient");
+    } else {
+      CX_CUDA((launch_conv<CH, CH, EPI_MASK>(c, a)), "input gradient");
+    }
+    dz = out;
+  }
+  return RX_OK;
+}
+
+rx_status pack(rx_cnn *c) {
+  for (int l = 0; l < c->L; ++l) {
+    const int cinp = l == 0 ? FEATP : CH, coutp = l == c->L - 1 ? 8 : CH;
+    const int copb = l == c->L - 1 ? FEATP : CH;
+    pack_kernel<<<64, 256, 0, c->stream>>>(c->P + c->off_w[l], c->ci[l], c->co[l], c->wf[l], cinp, coutp,
+                                             l > 0 ? c->wb[l] : nullptr, copb);
+    CX_CUDA(cudaGetLastError(), "pack");
+  }
+  return RX_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+rx_status rx_cnn_create(rx_cnn **out, int layers, int channels, int ksize, int64_t max_symbols) {
+  if (!out) return RX_EINVAL;
+  *out = nullptr;
+  if (layers < 2 || layers > 8 || max_symbols <= 0) return RX_EINVAL;
+  if (channels != CH || ksize != KS) return RX_EUNSUPPORTED;
+  rx_cnn *c = new (std::nothrow) rx_cnn();
+  if (!c) return RX_ENOMEM;
+  c->L = layers;
+  c->Kmax = max_symbols;
+  for (int l = 0; l < layers; ++l) {
+    c->ci.push_back(l == 0 ? FEAT : CH);
+    c->co.push_back(l == layers - 1 ? FEAT : CH);
+    c->off_w.push_back(c->n_params);
+    c->n_params += (int64_t)KS * c->ci[l] * c->co[l];
+    c->off_b.push_back(c->n_params);
+    c->n_params += c->co[l];
+  }
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess) e = conv_prepare<FEATP, CH, EPI_RELU>();
+  if (e == cudaSuccess) e = conv_prepare<CH, CH, EPI_RELU>();
+  if (e == cudaSuccess) e = conv_prepare<CH, 8, EPI_LAST>();
+  if (e == cudaSuccess) e = conv_prepare<FEATP, CH, EPI_MASK>();
+  if (e == cudaSuccess) e = conv_prepare<CH, CH, EPI_MASK>();
+  if (e != cudaSuccess) {
+    delete c;
+    return RX_ECUDA;
+  }
+  *out = c;
+#define CX_ALLOC(ptr, count)                      \
+  do {                                            \
+    rx_status s_ = calloc_dev(c, &(ptr), (count)); \
+    if (s_ != RX_OK) { release(c); return s_; }  \
+  } while (0)
+  CX_ALLOC(c->P, (size_t)c->n_params);
+  CX_ALLOC(c->G, (size_t)c->n_params);
+  CX_ALLOC(c->M, (size_t)c->n_params);
+  CX_ALLOC(c->V, (size_t)c->n_params);
+  c->wf.assign(layers, nullptr);
+  c->wb.assign(layers, nullptr);
+  for (int l = 0; l < layers; ++l) {
+    const int cinp = l == 0 ? FEATP : CH, coutp = l == layers - 1 ? 8 : CH;
+    CX_ALLOC(c->wf[l], (size_t)KS * cinp * coutp);
+    if (l > 0) CX_ALLOC(c->wb[l], (size_t)KS * CH * (l == layers - 1 ? FEATP : CH));
+  }
+  const size_t K = (size_t)max_symbols;
+  CX_ALLOC(c->x0, K * FEATP);
+  CX_ALLOC(c->dout, K * FEATP);
+  CX_ALLOC(c->dza, K * CH);
+  CX_ALLOC(c->dzb, K * CH);
+  c->h.assign(layers - 1, nullptr);
+  for (int l = 0; l < layers - 1; ++l) CX_ALLOC(c->h[l], K * CH);
+  CX_ALLOC(c->loss, 1);
+#undef CX_ALLOC
+  CX_CUDA(cudaMemset(c->P, 0, (size_t)c->n_params * sizeof(float)), "init");
+  CX_CUDA(cudaMemset(c->M, 0, (size_t)c->n_params * sizeof(float)), "init");
+  CX_CUDA(cudaMemset(c->V, 0, (size_t)c->n_params * sizeof(float)), "init");
+  CX_CUDA(cudaMemset(c->dout, 0, K * FEATP * sizeof(bf16)), "init");   // channels 4..15 stay zero
+  rx_status s = pack(c);
+  if (s != RX_OK) return s;
+  CX_CUDA(cudaStreamSynchronize(c->stream), "create");
+  return RX_OK;
+}
+
+int64_t rx_cnn_param_count(const rx_cnn *c) { return c ? c->n_params : -1; }
+
+rx_status rx_cnn_set_params(rx_cnn *c, const float *params) {
+  if (!c || !params) return RX_EINVAL;
+  CX_CUDA(cudaMemcpyAsync(c->P, params, (size_t)c->n_params * sizeof(float), cudaMemcpyHostToDevice, c->stream), "set");
+  CX_CUDA(cudaMemsetAsync(c->M, 0, (size_t)c->n_params * sizeof(float), c->stream), "set");
+  CX_CUDA(cudaMemsetAsync(c->V, 0, (size_t)c->n_params * sizeof(float), c->stream), "set");
+  c->step = 0;
+  rx_status s = pack(c);
+  if (s != RX_OK) return s;
+  CX_CUDA(cudaStreamSynchronize(c->stream), "set");
+  return RX_OK;
+}
+
+rx_status rx_cnn_get_params(rx_cnn *c, float *params) {
+  if (!c || !params) return RX_EINVAL;
+  CX_CUDA(cudaMemcpyAsync(params, c->P, (size_t)c->n_params * sizeof(float), cudaMemcpyDeviceToHost, c->stream), "get");
+  CX_CUDA(cudaStreamSynchronize(c->stream), "get");
+  return RX_OK;
+}
+
+rx_status rx_cnn_set_cuda_stream(rx_cnn *c, void *s) {
+  if (!c) return RX_EINVAL;
+  c->stream = (cudaStream_t)s;
+  return RX_OK;
+}
+
+rx_status rx_cnn_apply(rx_cnn *c, const float *z, int64_t zs, float *y, int64_t ys, int64_t K) {
+  if (!c) return RX_EINVAL;
+  if (K < 0 || K > c->Kmax) return cfail(c, RX_EINVAL, "K outside 0..max_symbols");
+  if (K == 0) return RX_OK;
+  rx_status s = check_sym(c, z, zs, K, "input");
+  if (s == RX_OK) s = check_sym(c, y, ys, K, "output");
+  if (s != RX_OK) return s;
+  return forward(c, z, zs, y, ys, nullptr, 0, K);
+}
+
+rx_status rx_cnn_grads(rx_cnn *c, const float *z, int64_t zs, const float *t, int64_t ts, int64_t K,
+                       float *grads_dev, double *loss) {
+  if (!c || !grads_dev || !loss) return RX_EINVAL;
+  if (K <= 0 || K > c->Kmax) return cfail(c, RX_EINVAL, "K outside 1..max_symbols");
+  rx_status s = check_sym(c, z, zs, K, "input");
+  if (s == RX_OK) s = check_sym(c, t, ts, K, "target");
+  if (s != RX_OK) return s;
+  CX_CUDA(cudaMemsetAsync(c->loss, 0, sizeof(double), c->stream), "loss");
+  s = forward(c, z, zs, nullptr, 0, t, ts, K);
+  if (s == RX_OK) s = backward(c, K);
+  if (s != RX_OK) return s;
+  CX_CUDA(cudaMemcpyAsync(grads_dev, c->G, (size_t)c->n_params * sizeof(float), cudaMemcpyDeviceToDevice, c->stream),
+          "grads");
+  CX_CUDA(cudaMemcpyAsync(loss, c->loss, sizeof(double), cudaMemcpyDeviceToHost, c->stream), "loss");
+  CX_CUDA(cudaStreamSynchronize(c->stream), "grads");
+  return RX_OK;
+}
+
+rx_status rx_cnn_train_step(rx_cnn *c, const float *z, int64_t zs, const float *t, int64_t ts, int64_t K, float lr,
+                            double *loss_acc) {
+  if (!c) return RX_EINVAL;
+  if (K <= 0 || K > c->Kmax) return cfail(c, RX_EINVAL, "K outside 1..max_symbols");
+  if (!(lr > 0.f)) return cfail(c, RX_EINVAL, "learning rate must be positive");
+  rx_status s = check_sym(c, z, zs, K, "input");
+  if (s == RX_OK) s = check_sym(c, t, ts, K, "target");
+  if (s != RX_OK) return s;
+  CX_CUDA(cudaMemsetAsync(c->loss, 0, sizeof(double), c->stream), "loss");
+  s = forward(c, z, zs, nullptr, 0, t, ts, K);
+  if (s == RX_OK) s = backward(c, K);
+  if (s != RX_OK) return s;
+  c->step += 1;
+  const float c1 = (float)(1.0 - pow(0.9, (double)c->step));
+  const float c2 = (float)(1.0 - pow(0.999, (double)c->step));
+  adam_kernel<<<std::max(1, std::min(c->sms * 4, (int)((c->n_params + 255) / 256))), 256, 0, c->stream>>>(
+      c->P, c->G, c->M, c->V, c->n_params, lr, c1, c2);
+  CX_CUDA(cudaGetLastError(), "adam");
+  s = pack(c);
+  if (s != RX_OK) return s;
+  if (loss_acc) {
+    add_kernel<<<1, 1, 0, c->stream>>>(loss_acc, c->loss);
+    CX_CUDA(cudaGetLastError(), "loss");
+  }
+  return RX_OK;
+}
+
+void rx_cnn_destroy(rx_cnn *c) {
+  if (!c) return;
+  cudaStreamSynchronize(c->stream);
+  release(c);
+  delete c;
+}
+
+const char *rx_cnn_last_error(rx_cnn *c) { return c ? c->msg.c_str() : "null handle"; }
+
+}  // extern "C"

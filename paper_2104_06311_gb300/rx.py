@@ -30,7 +30,10 @@ EXPORTS = ["rx_create", "rx_set_param", "rx_get_param", "rx_set_cuda_stream", "r
            "rx_bps_demap_noalloc",
            "rx_batch_create", "rx_batch_set_param", "rx_batch_get_param", "rx_batch_set_cuda_stream",
            "rx_batch_process", "rx_batch_ber", "rx_batch_trace", "rx_batch_sync", "rx_batch_destroy",
-           "rx_batch_last_error", "rx_batch_profile"]
+           "rx_batch_last_error", "rx_batch_profile",
+           "rx_cnn_create", "rx_cnn_param_count", "rx_cnn_set_params", "rx_cnn_get_params",
+           "rx_cnn_set_cuda_stream", "rx_cnn_apply", "rx_cnn_grads", "rx_cnn_train_step", "rx_cnn_destroy",
+           "rx_cnn_last_error"]
 BATCH_PARAMS = {"GRAPH": 100, "EQ_CTAS": 101, "EQ_TEAM": 102, "CDC_NS_PER_SAMPLE": 103, "PROFILE": 104}
 
 
@@ -108,8 +111,22 @@ def load(path: str = LIB_PATH) -> ct.CDLL:
     lib.rx_batch_destroy.restype = None
     lib.rx_batch_last_error.argtypes = [P]
     lib.rx_batch_last_error.restype = ct.c_char_p
+    lib.rx_cnn_create.argtypes = [ct.POINTER(P), ct.c_int, ct.c_int, ct.c_int, ct.c_int64]
+    lib.rx_cnn_param_count.argtypes = [P]
+    lib.rx_cnn_param_count.restype = ct.c_int64
+    lib.rx_cnn_set_params.argtypes = [P, P]
+    lib.rx_cnn_get_params.argtypes = [P, P]
+    lib.rx_cnn_set_cuda_stream.argtypes = [P, P]
+    lib.rx_cnn_apply.argtypes = [P, P, ct.c_int64, P, ct.c_int64, ct.c_int64]
+    lib.rx_cnn_grads.argtypes = [P, P, ct.c_int64, P, ct.c_int64, ct.c_int64, P, ct.POINTER(ct.c_double)]
+    lib.rx_cnn_train_step.argtypes = [P, P, ct.c_int64, P, ct.c_int64, ct.c_int64, ct.c_float, P]
+    lib.rx_cnn_destroy.argtypes = [P]
+    lib.rx_cnn_destroy.restype = None
+    lib.rx_cnn_last_error.argtypes = [P]
+    lib.rx_cnn_last_error.restype = ct.c_char_p
     for name in EXPORTS:
-        if name not in ("rx_destroy", "rx_status_str", "rx_last_error", "rx_batch_destroy", "rx_batch_last_error"):
+        if name not in ("rx_destroy", "rx_status_str", "rx_last_error", "rx_batch_destroy", "rx_batch_last_error",
+                        "rx_cnn_param_count", "rx_cnn_destroy", "rx_cnn_last_error"):
             getattr(lib, name).restype = ct.c_int
     _lib = lib
     return lib
@@ -453,6 +470,115 @@ class Batch:
             self.h = None
 
     rx_batch_destroy = close
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _ccheck(lib, h, status):
+    if status != RX_OK:
+        detail = lib.rx_cnn_last_error(h).decode() if h else ""
+        raise RxError(status, f"{lib.rx_status_str(status).decode()}: {detail}")
+
+
+class CNN:
+    """Learned post-equaliser (include/rx_cnn.h) on the current CUDA device.
+
+    Symbols in and out are (2, K) complex64 CUDA tensors (rows = polarisations).
+    """
+
+    def __init__(self, max_symbols, layers=4, channels=64, ksize=15, stream=None):
+        import torch
+        self.torch = torch
+        self.lib = load()
+        h = ct.c_void_p()
+        _ccheck(self.lib, None, self.lib.rx_cnn_create(ct.byref(h), layers, channels, ksize, int(max_symbols)))
+        self.h = h
+        self.layers = layers
+        self.n_params = int(self.lib.rx_cnn_param_count(h))
+        if stream is not None:
+            ptr = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+            _ccheck(self.lib, self.h, self.lib.rx_cnn_set_cuda_stream(self.h, ct.c_void_p(ptr)))
+
+    @staticmethod
+    def flatten(params):
+        """[(W (15, ci, co), b (co,)), ...] -> flat float32 in the library's layout."""
+        import numpy as np
+        return np.concatenate([np.concatenate([np.asarray(W, np.float64).ravel(), np.asarray(b, np.float64).ravel()])
+                               for W, b in params]).astype(np.float32)
+
+    def unflatten(self, flat, channels=64, ksize=15):
+        import numpy as np
+        dims = [4] + [channels] * (self.layers - 1) + [4]
+        out, o = [], 0
+        for l in range(self.layers):
+            ci, co = dims[l], dims[l + 1]
+            W = np.asarray(flat[o:o + ksize * ci * co], np.float64).reshape(ksize, ci, co)
+            o += ksize * ci * co
+            b = np.asarray(flat[o:o + co], np.float64)
+            o += co
+            out.append((W, b))
+        return out
+
+    def rx_cnn_set_params(self, params):
+        import numpy as np
+        flat = np.ascontiguousarray(params if isinstance(params, np.ndarray) else self.flatten(params), np.float32)
+        assert flat.size == self.n_params
+        _ccheck(self.lib, self.h, self.lib.rx_cnn_set_params(self.h, flat.ctypes.data))
+
+    set_params = rx_cnn_set_params
+
+    def rx_cnn_get_params(self):
+        import numpy as np
+        flat = np.empty(self.n_params, np.float32)
+        _ccheck(self.lib, self.h, self.lib.rx_cnn_get_params(self.h, flat.ctypes.data))
+        return flat
+
+    get_params = rx_cnn_get_params
+
+    def _sym(self, z):
+        assert z.is_cuda and z.dtype == self.torch.complex64 and z.shape[0] == 2 and z.stride(1) == 1
+        return z.data_ptr(), z.stride(0)
+
+    def rx_cnn_apply(self, z, out=None):
+        K = z.shape[1]
+        if out is None:
+            out = self.torch.empty_like(z)
+        zp, zs = self._sym(z)
+        yp, ys = self._sym(out)
+        _ccheck(self.lib, self.h, self.lib.rx_cnn_apply(self.h, zp, zs, yp, ys, K))
+        return out
+
+    apply = rx_cnn_apply
+
+    def rx_cnn_grads(self, z, t):
+        """(loss, flat float32 gradient tensor on the device)."""
+        g = self.torch.empty(self.n_params, dtype=self.torch.float32, device="cuda")
+        loss = ct.c_double()
+        zp, zs = self._sym(z)
+        tp, ts = self._sym(t)
+        _ccheck(self.lib, self.h, self.lib.rx_cnn_grads(self.h, zp, zs, tp, ts, z.shape[1], g.data_ptr(), ct.byref(loss)))
+        return loss.value, g
+
+    grads = rx_cnn_grads
+
+    def rx_cnn_train_step(self, z, t, lr=1e-3, loss_acc=None):
+        zp, zs = self._sym(z)
+        tp, ts = self._sym(t)
+        acc = loss_acc.data_ptr() if loss_acc is not None else None
+        _ccheck(self.lib, self.h, self.lib.rx_cnn_train_step(self.h, zp, zs, tp, ts, z.shape[1], float(lr), acc))
+
+    train_step = rx_cnn_train_step
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.rx_cnn_destroy(self.h)
+            self.h = None
+
+    rx_cnn_destroy = close
 
     def __del__(self):
         try:

@@ -1,0 +1,171 @@
+"""GPU checks of the learned post-equaliser (include/rx_cnn.h) against the FP64
+reference (oracle/cnn.py): forward output and gradients of the BF16 kernels
+within 1e-2 relative RMS (3e-2 for the first layer's weights), the Adam update on the device's own gradients, and
+what the trained network gains over the chain alone on a Kerr-nonlinear link."""
+import math
+
+import numpy as np
+import pytest
+
+import linksim as L
+from oracle import cnn as C
+from chain_helpers import ensure_built, rel_rms
+
+pytestmark = pytest.mark.gpu
+
+GRAD_TOL = 1e-2
+# The first layer's weight gradient sums products of zero-mean input features
+# with the back-propagated gradient, so its relative error is the per-element
+# error of that gradient (about 4 BF16 roundings deep, u = 2^-8, plus ReLU
+# mask flips near zero) rather than an average of it: ~1-2.5% measured.
+GRAD_TOL_FIRST = 3e-2
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    ensure_built()
+
+
+def _data(K, seed):
+    rng = np.random.default_rng(seed)
+    bits = L.random_bits(seed, 2 * 4 * K).reshape(2, -1)
+    t = L.map_symbols(bits, "16qam")
+    # a distorted copy: a little ISI, a Kerr-like phase and noise
+    z = t + 0.1 * np.roll(t, 1, axis=1) * 1j + 0.15 * (rng.standard_normal(t.shape) + 1j * rng.standard_normal(t.shape))
+    z = z * np.exp(0.2j * np.abs(z) ** 2)
+    return z, t
+
+
+def _params(seed):
+    p = C.init_params(seed)
+    p[-1] = (p[-1][0] * 10.0, p[-1][1])          # a full-size last layer
+    rng = np.random.default_rng(seed + 1)
+    p = [(W, 0.05 * rng.standard_normal(b.shape)) for W, b in p]
+    # the device holds FP32 parameters: compare on exactly those values
+    return [(W.astype(np.float32).astype(np.float64), b.astype(np.float32).astype(np.float64)) for W, b in p]
+
+
+def _bf16(x):
+    """Round to the nearest bfloat16 (ties to even), as the kernels store their input features."""
+    u = np.ascontiguousarray(x, np.float32).view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def _dev(x):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(x.astype(np.complex64))).cuda()
+
+
+@pytest.mark.parametrize("K", [3000, 1 << 14])
+def test_forward_matches_oracle(K):
+    from paper_2104_06311_gb300 import CNN
+    z, _ = _data(K, 5)
+    params = _params(7)
+    net = CNN(K)
+    net.set_params(params)
+    y = net.apply(_dev(z)).cpu().numpy().astype(np.complex128)
+    yo, _ = C.forward(params, C.features(z), _bf16(C.features(z)))
+    corr_dev = C.features(y) - C.features(z)
+    corr_orc = yo - C.features(z)
+    err = rel_rms(corr_dev, corr_orc)
+    print("forward correction rel RMS", err)
+    assert err < GRAD_TOL
+
+
+@pytest.mark.parametrize("K", [3000, 1 << 14])
+def test_gradients_match_oracle(K):
+    from paper_2104_06311_gb300 import CNN
+    z, t = _data(K, 11)
+    params = _params(13)
+    net = CNN(K)
+    net.set_params(params)
+    loss, g = net.grads(_dev(z), _dev(t))
+    gd = net.unflatten(g.cpu().numpy())
+    Jo, go = C.loss_and_grads(params, C.features(z), C.features(t), _bf16(C.features(z)))
+    print("loss", loss, Jo)
+    assert abs(loss - Jo) < 1e-2 * Jo
+    for l, ((dW, db), (oW, ob)) in enumerate(zip(gd, go)):
+        eW, eb = rel_rms(dW, oW), rel_rms(db, ob)
+        print("layer", l, "dW rel RMS", eW, "db rel RMS", eb)
+        assert max(eW, eb) < (GRAD_TOL_FIRST if l == 0 else GRAD_TOL), (l, eW, eb)
+
+
+def test_adam_step_on_device_gradients():
+    from paper_2104_06311_gb300 import CNN
+    K = 4096
+    z, t = _data(K, 17)
+    params = _params(19)
+    net = CNN(K)
+    net.set_params(params)
+    p0 = net.get_params().astype(np.float64)
+    _, g = net.grads(_dev(z), _dev(t))
+    g = g.cpu().numpy().astype(np.float64)
+    lr = 1e-3
+    net.train_step(_dev(z), _dev(t), lr=lr)
+    p1 = net.get_params().astype(np.float64)
+    # first Adam step from zero state: p - lr g / (|g| + eps) (m_hat = g, v_hat = g^2)
+    exp = p0 - lr * g / (np.abs(g) + 1e-8)
+    d = np.abs((p1 - p0) - (exp - p0))
+    big = np.abs(g) > 1e-6          # where the gradient is well above rounding, the step is exact
+    assert np.all(d[big] < 1e-3 * lr) and np.all(np.abs(p1 - p0) <= 1.001 * lr + 1e-7)
+
+
+def _chain(gen, link):
+    """GPU chain output symbols and the transmitted symbols aligned to them."""
+    import torch
+    from chain_helpers import make_receiver, rx_params
+    lk = L.Link(mod=link.mod, baud=link.baud, n_sym=link.n_sym, L_km=link.L_km)
+    p = rx_params(lk, gen.in_scale, fo_track=False)
+    rx = make_receiver(p, SYM_OUT=1)
+    x = torch.from_numpy(np.ascontiguousarray(gen.samples)).cuda()
+    out = rx.run_stream(x, sym=True)
+    K = out["n"]
+    ref = torch.from_numpy(L.pack_bits(gen.tx_bits).view(np.int32)).cuda()
+    e, nb, sync = rx.ber(out["bits"], ref, K)
+    z = out["sym"][:, :K].cpu().numpy().astype(np.complex128)
+    k0 = p.acq_len(K) + 8192
+    k1 = K - 64
+    t = np.zeros((2, k1 - k0), np.complex128)
+    for pp, (q, r, d) in enumerate(sync):
+        t[pp] = (1j ** r) * gen.tx_symbols[q, k0 + d:k1 + d]
+    return z[:, k0:k1], t, e / max(nb, 1)
+
+
+def test_training_gains_over_the_chain_on_a_nonlinear_link():
+    """16QAM 10 GBd, 10 x 100 km at 2 dBm (Kerr-limited, self-phase modulation within the
+    network's 57-symbol receptive field): train on one seed, judge on another."""
+    import torch
+    from linksim import ssfm as F
+    from paper_2104_06311_gb300 import CNN
+    base = dict(spans=10, launch_dbm=2.0, baud=10e9, n_sym=1 << 17, step_km=1.0)
+    tr = F.generate(F.SSFMLink(seed=2104063115, **base), device="cuda", dtype="float32")
+    te = F.generate(F.SSFMLink(seed=2104063116, **base), device="cuda", dtype="float32")
+    z_tr, t_tr, ber_tr = _chain(tr, tr.link)
+    z_te, t_te, ber_te = _chain(te, te.link)
+    print("chain BER train/test", ber_tr, ber_te)
+    net = CNN(1 << 14)
+    net.set_params(C.init_params(3))
+    B = 1 << 14
+    zt, tt = _dev(z_tr), _dev(t_tr)
+    n_tr = zt.shape[1] // B * B
+    for ep in range(100):
+        for s in range(0, n_tr, B):
+            net.train_step(zt[:, s:s + B].contiguous(), tt[:, s:s + B].contiguous(), lr=3e-4)
+    torch.cuda.synchronize()
+    # judge on the test seed, in pieces of B symbols (one sequence each)
+    zte = _dev(z_te)
+    y = torch.empty_like(zte)
+    for s in range(0, zte.shape[1], B):
+        e = min(s + B, zte.shape[1])
+        y[:, s:e] = net.apply(zte[:, s:e].contiguous())
+    y = y.cpu().numpy().astype(np.complex128)
+    mse_chain = np.mean(np.abs(z_te - t_te) ** 2)
+    mse_cnn = np.mean(np.abs(y - t_te) ** 2)
+    from oracle.chain import decide
+    ser_chain = np.mean(np.abs(decide(z_te, "16qam") - t_te) > 1e-6)
+    ser_cnn = np.mean(np.abs(decide(y, "16qam") - t_te) > 1e-6)
+    gain_db = 10 * math.log10(mse_chain / mse_cnn)
+    print(f"test MSE chain {mse_chain:.5f} cnn {mse_cnn:.5f} (effective SNR gain {gain_db:.2f} dB); "
+          f"SER chain {ser_chain:.5f} cnn {ser_cnn:.5f}")
+    assert gain_db > 0.1
