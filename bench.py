@@ -47,8 +47,11 @@ def parse():
     ap.add_argument("--cpu-sample", type=int, default=1 << 21, help="sample-times the oracle baseline processes")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", choices=["c2", "c4"], default="c2",
-                    help="c2: the 10,000 km single stream (default); c4: the 64-channel batched form")
+    ap.add_argument("--precision", choices=["fp32", "fp16", "bf16"], default="fp32",
+                    help="storage of the CDC transform and its output (single-stream workloads)")
+    ap.add_argument("--workload", choices=["c2", "c3", "c4", "c5"], default="c2",
+                    help="c2: the 10,000 km single stream (default); c4: the 64-channel batched form; "
+                         "c5: the chain plus the learned post-equaliser on a Kerr-nonlinear link")
     ap.add_argument("--channels", type=int, default=64, help="c4: number of channels")
     return ap.parse_args()
 
@@ -101,9 +104,16 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def make_input(n_sym):
+WORKLOADS = {
+    "c2": "10,000 km straight-line DP-QPSK 10 GBd, 2 sps, 2^24 symbols/pol, int8 ADC, "
+          "PMD 0.1 ps/sqrt(km), 100 kHz PN, 200 MHz FO, Es/N0 9.8 dB",
+    "c3": "DP-16QAM 32 GBd, 2 sps, 2^22 symbols/pol, 6000 km, 100 kHz PN, Es/N0 18 dB, int8 ADC",
+}
+
+
+def make_input(n_sym, name="c2"):
     import linksim as L
-    lk = L.workload("c2", n_sym=n_sym)
+    lk = L.workload(name, n_sym=n_sym)
     return lk, L.generate(lk)
 
 
@@ -304,6 +314,145 @@ def bench_batch(args, rank, world, local):
         dist.destroy_process_group()
 
 
+def bench_learned(args, rank, world, local):
+    """Chain + CNN post-equaliser on a split-step (Kerr) link: training and inference."""
+    import numpy as np
+    import torch
+    torch.cuda.set_device(local)
+    from paper_2104_06311_gb300 import CNN, Receiver, build
+    if not os.path.exists(build.OUT):
+        build.build()
+    import linksim as L
+    from linksim import ssfm as F
+    n_sym = min(args.n_sym, 1 << 22)
+    spec = dict(mod="16qam", baud=10e9, spans=10, span_km=100.0, launch_dbm=2.0, n_sym=n_sym, step_km=1.0)
+    stream = torch.cuda.current_stream()
+    sets = {}
+    for name, seed in (("train", 2104063115), ("test", 2104063116)):
+        g = F.generate(F.SSFMLink(seed=seed, **spec), device="cuda", dtype="float32")
+        x = torch.from_numpy(np.ascontiguousarray(g.samples)).cuda()
+        rx = Receiver(spec["baud"], g.link.L_km, stream=stream, MOD=4, IN_SCALE=g.in_scale, FO_TRACK=0, SYM_OUT=1)
+        out = rx.run_stream(x, sym=True)
+        K = out["n"]
+        ref = torch.from_numpy(L.pack_bits(g.tx_bits).view(np.int32)).cuda()
+        e, nb, sync = rx.ber(out["bits"], ref, K)
+        k0, k1 = 16384 + 8192, K - 64
+        t = np.zeros((2, k1 - k0), np.complex64)
+        for pp, (q, r, d) in enumerate(sync):
+            t[pp] = (1j ** r) * g.tx_symbols[q, k0 + d:k1 + d]
+        zc = out["sym"][:, k0:k1].contiguous()
+        t = L.align_rotation(zc.cpu().numpy(), t).astype(np.complex64)
+        sets[name] = dict(x=x, rx=rx, z=zc, t=torch.from_numpy(t).cuda(), ber=e / max(nb, 1), K=K)
+    B, BI = 1 << 14, 1 << 20          # training sequences / inference sequences (symbols)
+    tr, te = sets["train"], sets["test"]
+    n_tr = tr["z"].shape[1] // B * B
+    net = CNN(BI, stream=stream)
+    net.set_params(L.cnn_init_params(3))     # seeded He-normal initial weights
+
+    def epoch(lr):
+        for s in range(0, n_tr, B):
+            net.train_step(tr["z"][:, s:s + B], tr["t"][:, s:s + B], lr=lr)
+
+    for _ in range(args.warmup):
+        epoch(3e-4)
+    net.set_profile(True)
+    net.profile(reset=True)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(args.steps):
+        epoch(3e-4)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    train_ms = t0.elapsed_time(t1) / args.steps
+    prof_train = net.profile(reset=True)
+    # inference over the test stream, in sequences of B symbols
+    zt = te["z"]
+    y = torch.empty_like(zt)
+
+    def infer():
+        for s in range(0, zt.shape[1], BI):
+            e = min(s + BI, zt.shape[1])
+            net.apply(zt[:, s:e], out=y[:, s:e])
+
+    infer()
+    net.profile(reset=True)
+    a_ = torch.cuda.Event(enable_timing=True)
+    b_ = torch.cuda.Event(enable_timing=True)
+    a_.record(stream)
+    for _ in range(args.steps):
+        infer()
+    b_.record(stream)
+    torch.cuda.synchronize()
+    infer_ms = a_.elapsed_time(b_) / args.steps
+    prof_inf = net.profile(reset=True)
+    net.set_profile(False)
+    # end to end: chain + CNN over the test stream (whole-stream steps)
+    xt = te["x"]
+    n = xt.shape[0]
+    c0 = torch.cuda.Event(enable_timing=True)
+    c1 = torch.cuda.Event(enable_timing=True)
+    outc = te["rx"].alloc_out(n // 2 + 64, sym=True)
+    c0.record(stream)
+    for _ in range(args.steps):
+        te["rx"].run_stream(xt, sym=True, out=outc)
+        infer()
+    c1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = c0.elapsed_time(c1) / args.steps
+    yh = y.cpu().numpy().astype(np.complex128)
+    zh, th = zt.cpu().numpy().astype(np.complex128), te["t"].cpu().numpy().astype(np.complex128)
+    mse_c, mse_n = float(np.mean(np.abs(zh - th) ** 2)), float(np.mean(np.abs(yh - th) ** 2))
+    flop_sym = 2 * 15 * (4 * 64 + 64 * 64 * 2 + 64 * 4)          # forward, per symbol
+    n_inf = zt.shape[1]
+    pk, pk_kind = peaks()
+    # the 64 -> 64 forward convolutions: (layers - 2) per pass, 2*15*64*64 flop per symbol each
+    hid_ms, hid_n = prof_inf["fwd_hidden"]
+    per_launch_flop = args.steps * 2 * (2 * 15 * 64 * 64 * n_inf) / max(1, hid_n)
+    per_launch_ms = hid_ms / max(1, hid_n)
+    achieved = per_launch_flop / (per_launch_ms / 1e3) / 1e12
+    roof = {"bound": "tensor", "achieved": achieved, "peak": pk["bf16_tflops"], "unit": "TFLOP/s",
+            "frac": achieved / pk["bf16_tflops"], "traffic": None, "kernel": "conv_kernel<64,64> (forward)",
+            "peak_source": pk_kind, "note": "mma.sync m16n8k16 BF16; peak = measured cuBLAS bf16 burst"}
+    line = {
+        "metric": METRIC, "value": n / (e2e_ms / 1e3) / 1e9, "unit": "GSa/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": e2e_ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "bf16",
+        "data": "synthetic split-step (Manakov) link, seeded; train and test seeds differ",
+        "config": {"workload": "DP-16QAM 10 GBd, 10 x 100 km SSMF (0.2 dB/km, gamma 1.3 /W/km, NF 5 dB), 2 dBm, "
+                               f"{n_sym} symbols/pol; chain + 4-layer CNN (64 ch, k 15) post-equaliser",
+                   "sample_times": n, "batch_symbols": B, "l2": "CNN activations (512 MiB per layer) exceed L2"},
+        "step": "e2e: whole-stream chain + CNN inference; training epochs timed separately",
+        "train": {"ms_per_epoch": train_ms, "symbols_per_epoch": n_tr,
+                  "tflops": 3 * flop_sym * n_tr / (train_ms / 1e3) / 1e12,
+                  "kernel_ms_per_epoch": {k: v[0] / args.steps for k, v in prof_train.items()}},
+        "inference": {"ms": infer_ms, "symbols": n_inf, "gsym_per_s": n_inf / (infer_ms / 1e3) / 1e9,
+                      "tflops": flop_sym * n_inf / (infer_ms / 1e3) / 1e12},
+        "gain": {"mse_chain": mse_c, "mse_cnn": mse_n, "effective_snr_gain_db": 10 * math.log10(mse_c / mse_n),
+                 "chain_ber_test": te["ber"]},
+        "roofline": roof, "clocks": clk,
+        "gpu_launches": int(sum(v[1] for v in prof_train.values())),
+        "e2e": {"value": n / (e2e_ms / 1e3) / 1e9, "unit": "GSa/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0,
+                "note": "inputs resident on the device"},
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        import oracle.cnn as OC
+        ns = 1 << 12
+        params = net.unflatten(net.get_params())
+        zs = zh[:, :ns]
+        t0_ = time.perf_counter()
+        OC.forward(params, OC.features(zs))
+        dt = time.perf_counter() - t0_
+        line["cpu_baseline"] = {"value": 2 * ns / dt / 1e9, "unit": "GSa/s", "cores": 1, "kind": "oracle",
+                                "sample": f"FP64 CNN forward (oracle) on the first {ns} test symbols, one core; "
+                                          "GSa/s = 2 samples per symbol"}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", "0"))
@@ -314,6 +463,9 @@ def main():
         return
     if args.workload == "c4":
         bench_batch(args, rank, world, local)
+        return
+    if args.workload == "c5":
+        bench_learned(args, rank, world, local)
         return
     import numpy as np
     import torch
@@ -327,13 +479,16 @@ def main():
         build.build()
     import linksim as L
 
-    lk, g = make_input(args.n_sym)
+    n_sym = args.n_sym if args.workload == "c2" else min(args.n_sym, 1 << 22)
+    lk, g = make_input(n_sym, args.workload)
     n = g.samples.shape[0]
     K = n // 2
     x = torch.from_numpy(g.samples).cuda()
     ref = torch.from_numpy(L.pack_bits(g.tx_bits).view(np.int32)).cuda()
     stream = torch.cuda.current_stream()
-    rx = Receiver(lk.baud, lk.L_km, D=lk.D, stream=stream, MOD=2, IN_SCALE=g.in_scale)
+    mbits = L.bits_per_symbol(lk.mod)
+    prec = {"fp32": 0, "fp16": 1, "bf16": 2}[args.precision]
+    rx = Receiver(lk.baud, lk.L_km, D=lk.D, stream=stream, MOD=mbits, IN_SCALE=g.in_scale, PRECISION=prec)
     rx.reserve(n)
     out = rx.alloc_out(K + 64)
 
@@ -435,15 +590,14 @@ def main():
     line = {
         "metric": METRIC, "value": value, "unit": "GSa/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-        "data": "synthetic (seeded linksim 10,000 km link), resident in HBM",
-        "config": {"workload": "10,000 km straight-line DP-QPSK 10 GBd, 2 sps, 2^24 symbols/pol, int8 ADC, "
-                               "PMD 0.1 ps/sqrt(km), 100 kHz PN, 200 MHz FO, Es/N0 9.8 dB",
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32" if prec == 0 else f"f32 ({args.precision} CDC storage)",
+        "data": f"synthetic (seeded linksim {lk.L_km:.0f} km link), resident in HBM",
+        "config": {"workload": WORKLOADS[args.workload], "precision": args.precision,
                    "sample_times": n, "fft_n": int(rx.get_param("FFT_N")), "overlap": int(rx.get_param("OVERLAP")),
                    "taps": T, "bps_angles": 32, "segments_per_wave": 32,
-                   "l2": "inputs (128 MiB) and CDC intermediates (512 MiB) exceed L2; no flush",
+                   "l2": f"inputs ({n * 4 >> 20} MiB) and CDC intermediates ({n * 16 >> 20} MiB) exceed L2; no flush",
                    "parallelism": f"replicas x{world}" if world > 1 else "single stream"},
-        "decoded_gbps": value / 2 * 2 * 2,
+        "decoded_gbps": value / 2 * 2 * mbits,
         "hbm_roofline_frac": value / (pk["hbm_gbs"] / 4.25),
         "ber": ber, "ber_sync": sync,
         "stage_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
@@ -460,16 +614,16 @@ def main():
         line["cpu_baseline"] = {"value": ns / dt / 1e9, "unit": "GSa/s", "cores": 1, "kind": "oracle",
                                 "sample": f"first {ns} sample-times of the workload, FP64 numpy oracle, one core"}
         # bit agreement of the CUDA chain with the oracle on that sample (same stream prefix)
-        rxs = Receiver(lk.baud, lk.L_km, D=lk.D, stream=stream, MOD=2, IN_SCALE=g.in_scale)
+        rxs = Receiver(lk.baud, lk.L_km, D=lk.D, stream=stream, MOD=mbits, IN_SCALE=g.in_scale, PRECISION=prec)
         o2 = rxs.run_stream(x[:ns].contiguous())
         torch.cuda.synchronize()
-        gb = L.unpack_bits(o2["bits"].cpu().numpy().view(np.uint32), ns // 2 * 2)
+        gb = L.unpack_bits(o2["bits"].cpu().numpy().view(np.uint32), ns // 2 * mbits)
         mism = int(np.sum(gb != orc["bits"]))
-        eo, no, _ = O_ber(orc["bits"], g.tx_bits[:, :ns // 2 * 2], p)
+        eo, no, _ = O_ber(orc["bits"], g.tx_bits[:, :ns // 2 * mbits], p)
         line["oracle_parity_sample"] = {"bits": int(gb.size), "mismatched_bits": mism,
                                         "ber_oracle": eo / max(no, 1),
                                         "ber_gpu": None}
-        e3, n3, _ = rxs.ber(o2["bits"], torch.from_numpy(L.pack_bits(g.tx_bits[:, :ns // 2 * 2]).view(np.int32)).cuda(), ns // 2)
+        e3, n3, _ = rxs.ber(o2["bits"], torch.from_numpy(L.pack_bits(g.tx_bits[:, :ns // 2 * mbits]).view(np.int32)).cuda(), ns // 2)
         line["oracle_parity_sample"]["ber_gpu"] = e3 / max(n3, 1)
     if rank == 0:
         print(json.dumps(line), flush=True)

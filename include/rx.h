@@ -87,9 +87,13 @@ enum {
   RX_P_EQ_OUT = 20,        /* 1 = write equaliser outputs to rx_out.eq               */
   RX_P_CDC_OUT = 21,       /* 1 = write CDC outputs to rx_out.cdc (tests)            */
   RX_P_PROFILE = 22,       /* 1 = time each stage with CUDA events (rx_profile)      */
-  RX_P_PIPELINE = 23       /* pieces per call overlapped on three internal streams
+  RX_P_PIPELINE = 23,      /* pieces per call overlapped on three internal streams
                               (CDC ahead of, BPS behind the equaliser); 1..64,
                               default 12; 1 = the stages run back to back          */
+  RX_P_PRECISION = 24      /* precision form: storage of the CDC transform and of
+                              its output: 0 = FP32 (default), 1 = FP16, 2 = BF16;
+                              butterflies and the equaliser compute in FP32, the
+                              phase trackers stay 64-bit                           */
 };
 
 /* Stages reported by rx_profile. */

@@ -67,6 +67,23 @@ rx_status rx_cnn_grads(rx_cnn *c, const float *z, int64_t z_stride, const float 
 rx_status rx_cnn_train_step(rx_cnn *c, const float *z, int64_t z_stride, const float *t, int64_t t_stride,
                             int64_t K, float lr, double *loss_acc);
 
+/* Launch kinds reported by rx_cnn_profile. */
+enum {
+  RX_CNN_K_FWD_HIDDEN = 0,  /* forward convolutions 64 -> 64                     */
+  RX_CNN_K_FWD_EDGE = 1,    /* forward convolutions 4 -> 64 and 64 -> 4 (+ loss)  */
+  RX_CNN_K_DX = 2,          /* input-gradient convolutions (ReLU mask fused)       */
+  RX_CNN_K_DW = 3,          /* weight-gradient reductions                          */
+  RX_CNN_K_UPDATE = 4,      /* Adam                                               */
+  RX_CNN_KINDS = 5
+};
+
+/* 1 = bracket every launch with CUDA events (rx_cnn_profile reads them). */
+rx_status rx_cnn_set_profile(rx_cnn *c, int on);
+/* Device time (ms, summed over profiled launches) and launch counts (all
+ * launches) per kind since the last reset; ms and launches hold RX_CNN_KINDS
+ * entries.  Synchronises.  Not from the paper: measurement support. */
+rx_status rx_cnn_profile(rx_cnn *c, double *ms, int64_t *launches, int reset);
+
 void rx_cnn_destroy(rx_cnn *c);
 const char *rx_cnn_last_error(rx_cnn *c);
 

@@ -352,3 +352,33 @@ def workload_batch(n_ch: int = 64, seed: int = 2104063114, log2_len=(18.0, 22.0)
                           jones=(float(rng.uniform(0, math.pi)), float(rng.uniform(0, 2 * math.pi))),
                           snr_db=float(rng.uniform(*snr_db)), adc="int8", seed=seed + ch))
     return links
+
+
+def cnn_init_params(seed: int, channels: int = 64, ksize: int = 15, layers: int = 4, feat: int = 4):
+    """Seeded initial weights of the post-equaliser CNN: He-normal W (std
+    sqrt(2 / fan_in), shape (ksize, ci, co)) and zero biases; the last layer
+    is scaled by 0.1 so the untrained network starts near y = x."""
+    rng = np.random.default_rng(np.random.PCG64(seed))
+    dims = [feat] + [channels] * (layers - 1) + [feat]
+    params = []
+    for l in range(layers):
+        ci, co = dims[l], dims[l + 1]
+        W = rng.standard_normal((ksize, ci, co)) * np.sqrt(2.0 / (ksize * ci))
+        if l == layers - 1:
+            W *= 0.1
+        params.append((W, np.zeros(co)))
+    return params
+
+
+def align_rotation(z: np.ndarray, t: np.ndarray, block: int = 4096) -> np.ndarray:
+    """Reference symbols t (2, K) rotated per block by the j^r (r = 0..3) that
+    best matches the received z: genie-aided labels that stay aligned across
+    a pi/2 cycle slip of the receiver's phase recovery (for training and
+    judging a post-equaliser, not for counting errors)."""
+    out = np.empty_like(t)
+    for p in range(t.shape[0]):
+        for b0 in range(0, t.shape[1], block):
+            zz, tt = z[p, b0:b0 + block], t[p, b0:b0 + block]
+            r = int(np.argmin([np.sum(np.abs(zz - (1j ** q) * tt) ** 2) for q in range(4)]))
+            out[p, b0:b0 + block] = (1j ** r) * tt
+    return out

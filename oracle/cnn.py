@@ -132,16 +132,6 @@ class Adam:
         return out
 
 
-def init_params(seed: int, channels: int = 64, ksize: int = 15, layers: int = 4, feat: int = 4):
-    """He-normal weights (std sqrt(2 / fan_in)) and zero biases, seeded; the
-    last layer is scaled by 0.1 so the untrained network starts near y = x."""
-    rng = np.random.default_rng(np.random.PCG64(seed))
-    dims = [feat] + [channels] * (layers - 1) + [feat]
-    params = []
-    for l in range(layers):
-        ci, co = dims[l], dims[l + 1]
-        W = rng.standard_normal((ksize, ci, co)) * np.sqrt(2.0 / (ksize * ci))
-        if l == layers - 1:
-            W *= 0.1
-        params.append((W, np.zeros(co)))
-    return params
+# Seeded initial weights are inputs of the method: they come from the shared
+# generator module (linksim), like every other random draw.
+from linksim import cnn_init_params as init_params  # noqa: E402,F401

@@ -11,12 +11,29 @@
 // central S = N - V outputs go to HBM.  Window i reads input samples
 // [iS - V/2, iS - V/2 + N) (zero outside the stream) and writes outputs
 // [iS, iS + S).
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <math.h>
 
 #include "common.cuh"
 #include "rx_internal.h"
 
 namespace rx {
+
+// ---------------------------------------------------------------- storage formats
+// The precision form keeps the shared-memory transform and the CDC output in
+// FP16 or BF16 pairs; every butterfly still computes in FP32 registers
+// (reduced-precision operands, FP32 accumulation).
+__device__ __forceinline__ float2 ld2(const float2 &v) { return v; }
+__device__ __forceinline__ float2 ld2(const __half2 &v) { return __half22float2(v); }
+__device__ __forceinline__ float2 ld2(const __nv_bfloat162 &v) { return __bfloat1622float2(v); }
+template <class S> __device__ __forceinline__ S st2(float2 v);
+template <> __device__ __forceinline__ float2 st2<float2>(float2 v) { return v; }
+template <> __device__ __forceinline__ __half2 st2<__half2>(float2 v) { return __float22half2_rn(v); }
+template <> __device__ __forceinline__ __nv_bfloat162 st2<__nv_bfloat162>(float2 v) { return __float22bfloat162_rn(v); }
+template <int FMT> struct Fmt { typedef float2 T; };
+template <> struct Fmt<RX_FMT_F16> { typedef __half2 T; };
+template <> struct Fmt<RX_FMT_BF16> { typedef __nv_bfloat162 T; };
 
 // ---------------------------------------------------------------- tables (FP64)
 __global__ void tables_kernel(float2 *H, float2 *tw, int N, double baud, double L_km, double D,
@@ -161,8 +178,8 @@ __device__ __forceinline__ int pad(int i) { return i + (i >> 5); }
 // DFT and writes element r to (j / Ns) Ns R + (j mod Ns) + r Ns.  Each of the
 // N / VPT threads of a transform owns VPT / R butterflies and keeps their
 // values in registers across the barrier (in-place pass).
-template <int N, int VPT, int R, int Ns>
-__device__ __forceinline__ void fft_pass(float2 *buf, int t, const float2 *__restrict__ tw) {
+template <int N, int VPT, int R, int Ns, class S>
+__device__ __forceinline__ void fft_pass(S *buf, int t, const float2 *__restrict__ tw) {
   constexpr int NB = N / R, PER = VPT / R, TW = N / (Ns * R), TPP = N / VPT;
   float2 v[PER][R];
 #pragma unroll
@@ -171,7 +188,7 @@ __device__ __forceinline__ void fft_pass(float2 *buf, int t, const float2 *__res
     const int jm = j & (Ns - 1);
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-      float2 x = buf[pad(j + r * NB)];
+      float2 x = ld2(buf[pad(j + r * NB)]);
       if (Ns > 1 && r > 0) x = cmul(x, __ldg(&tw[r * jm * TW]));
       v[q][r] = x;
     }
@@ -184,13 +201,13 @@ __device__ __forceinline__ void fft_pass(float2 *buf, int t, const float2 *__res
     const int jm = j & (Ns - 1);
     const int d = (j / Ns) * Ns * R + jm;
 #pragma unroll
-    for (int r = 0; r < R; ++r) buf[pad(d + r * Ns)] = v[q][r];
+    for (int r = 0; r < R; ++r) buf[pad(d + r * Ns)] = st2<S>(v[q][r]);
   }
   __syncthreads();
 }
 
-template <int N, int VPT>
-__device__ __forceinline__ void fft_forward(float2 *buf, int t, const float2 *tw) {
+template <int N, int VPT, class S>
+__device__ __forceinline__ void fft_forward(S *buf, int t, const float2 *tw) {
   if constexpr (N == 16384) {  // 16 x 16 x 16 x 4
     fft_pass<N, VPT, 16, 1>(buf, t, tw);
     fft_pass<N, VPT, 16, 16>(buf, t, tw);
@@ -208,21 +225,27 @@ __device__ __forceinline__ void fft_forward(float2 *buf, int t, const float2 *tw
 }
 
 // One CTA per window (both polarisations, SPLIT = false) or per (window, pol)
-// (SPLIT = true, blockIdx.y = pol) for the large transforms.
-template <int N, int VPT, bool SPLIT>
+// (SPLIT = true, blockIdx.y = pol) for the large transforms.  FMT selects the
+// storage of the shared-memory transform and of u (RX_FMT_*); reduced formats
+// scale the window by 1/sqrt(N) on ingest and H by sqrt(N) (kept in `hscale`)
+// so that every intermediate stays near unit magnitude (FP16 range).
+template <int N, int VPT, bool SPLIT, int FMT>
 __global__ void __launch_bounds__((SPLIT ? 1 : 2) * N / VPT) cdc_kernel(
     int V, const uint8_t *__restrict__ tail, int64_t tail_first, int64_t tail_n,
     const uint8_t *__restrict__ call, int64_t call_first, int64_t call_n, int dtype, float scale,
-    const float2 *__restrict__ H, const float2 *__restrict__ tw, float2 *__restrict__ u,
+    float hscale, const float2 *__restrict__ H, const float2 *__restrict__ tw, void *__restrict__ u_out,
     int64_t u_base, int64_t u_stride, int64_t win_first, int64_t n_total) {
-  extern __shared__ float2 smem[];
+  typedef typename Fmt<FMT>::T S;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  S *smem = reinterpret_cast<S *>(smem_raw);
+  S *u = reinterpret_cast<S *>(u_out);
   constexpr int PADN = N + N / 32;
   constexpr int TPP = N / VPT;  // threads per transform
-  const int S = N - V;
+  const int S_hop = N - V;
   const int64_t i = win_first + blockIdx.x;
-  const int64_t lo = i * S - V / 2;
+  const int64_t lo = i * S_hop - V / 2;
   const int psplit = SPLIT ? (int)blockIdx.y : 0;
-  float2 *b0 = smem, *b1 = smem + PADN;
+  S *b0 = smem, *b1 = smem + PADN;
   // ingest: one 4-scalar sample-time gives both pols
   for (int m = threadIdx.x; m < N; m += blockDim.x) {
     const int64_t n = lo + m;
@@ -240,61 +263,66 @@ __global__ void __launch_bounds__((SPLIT ? 1 : 2) * N / VPT) cdc_kernel(
       }
     }
     if (SPLIT) {
-      b0[pad(m)] = psplit ? make_float2(x.z * scale, x.w * scale) : make_float2(x.x * scale, x.y * scale);
+      b0[pad(m)] = st2<S>(psplit ? make_float2(x.z * scale, x.w * scale) : make_float2(x.x * scale, x.y * scale));
     } else {
-      b0[pad(m)] = make_float2(x.x * scale, x.y * scale);
-      b1[pad(m)] = make_float2(x.z * scale, x.w * scale);
+      b0[pad(m)] = st2<S>(make_float2(x.x * scale, x.y * scale));
+      b1[pad(m)] = st2<S>(make_float2(x.z * scale, x.w * scale));
     }
   }
   __syncthreads();
   const int pol = SPLIT ? psplit : threadIdx.x / TPP;
   const int t = threadIdx.x % TPP;
-  float2 *buf = (!SPLIT && pol) ? b1 : b0;
+  S *buf = (!SPLIT && pol) ? b1 : b0;
   fft_forward<N, VPT>(buf, t, tw);
   // multiply by H/N and conjugate (inverse via the forward transform)
-  // a full unroll at VPT = 32 makes the register allocator spill heavily
+  // (a full unroll at VPT = 32 makes the register allocator spill heavily)
 #pragma unroll(VPT > 16 ? 2 : VPT)
   for (int q = 0; q < VPT; ++q) {
     const int k = t + q * TPP;
-    buf[pad(k)] = cconj(cmul(buf[pad(k)], __ldg(&H[k])));
+    float2 hk = __ldg(&H[k]);
+    if (FMT != RX_FMT_F32) hk = make_float2(hk.x * hscale, hk.y * hscale);
+    buf[pad(k)] = st2<S>(cconj(cmul(ld2(buf[pad(k)]), hk)));
   }
   __syncthreads();
   fft_forward<N, VPT>(buf, t, tw);
-  float2 *out = u + (int64_t)pol * u_stride;
-  for (int tt = V / 2 + t; tt < V / 2 + S; tt += TPP) {
-    const int64_t n = i * S + (tt - V / 2);
+  S *out = u + (int64_t)pol * u_stride;
+  for (int tt = V / 2 + t; tt < V / 2 + S_hop; tt += TPP) {
+    const int64_t n = i * S_hop + (tt - V / 2);
     if (n_total >= 0 && n >= n_total) break;
-    out[n - u_base] = cconj(buf[pad(tt)]);
+    out[n - u_base] = st2<S>(cconj(ld2(buf[pad(tt)])));
   }
 }
 
-template <int N, int VPT, bool SPLIT>
+template <int N, int VPT, bool SPLIT, int FMT>
 static cudaError_t launch_cdc_n(int V, const void *tail, int64_t tail_first, int64_t tail_n,
                                 const void *call, int64_t call_first, int64_t call_n, int dtype,
-                                float scale, const float2 *H, const float2 *tw, float2 *u,
+                                float scale, const float2 *H, const float2 *tw, void *u,
                                 int64_t u_base, int64_t u_stride, int64_t win_first,
                                 int64_t win_count, int64_t n_total, cudaStream_t s) {
-  const size_t sm = (SPLIT ? 1 : 2) * (N + N / 32) * sizeof(float2);
-  cudaError_t e = cudaFuncSetAttribute(cdc_kernel<N, VPT, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  typedef typename Fmt<FMT>::T S;
+  const size_t sm = (SPLIT ? 1 : 2) * (N + N / 32) * sizeof(S);
+  cudaError_t e = cudaFuncSetAttribute(cdc_kernel<N, VPT, SPLIT, FMT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
   dim3 grid((unsigned)win_count, SPLIT ? 2 : 1);
-  cdc_kernel<N, VPT, SPLIT><<<grid, (SPLIT ? 1 : 2) * N / VPT, sm, s>>>(
+  const float rs = sqrtf((float)N);
+  const float in_scale = FMT == RX_FMT_F32 ? scale : scale / rs;
+  cdc_kernel<N, VPT, SPLIT, FMT><<<grid, (SPLIT ? 1 : 2) * N / VPT, sm, s>>>(
       V, (const uint8_t *)tail, tail_first, tail_n, (const uint8_t *)call, call_first, call_n,
-      dtype, scale, H, tw, u, u_base, u_stride, win_first, n_total);
+      dtype, in_scale, rs, H, tw, u, u_base, u_stride, win_first, n_total);
   return cudaGetLastError();
 }
 
-cudaError_t launch_cdc(int N, int V, const void *tail, int64_t tail_first, int64_t tail_n,
-                       const void *call, int64_t call_first, int64_t call_n, int dtype,
-                       float scale, const float2 *H, const float2 *tw, float2 *u,
-                       int64_t u_base, int64_t u_stride, int64_t win_first, int64_t win_count,
-                       int64_t n_total, cudaStream_t s) {
-  if (win_count <= 0) return cudaSuccess;
+template <int FMT>
+static cudaError_t launch_cdc_fmt(int N, int V, const void *tail, int64_t tail_first, int64_t tail_n,
+                                  const void *call, int64_t call_first, int64_t call_n, int dtype,
+                                  float scale, const float2 *H, const float2 *tw, void *u,
+                                  int64_t u_base, int64_t u_stride, int64_t win_first, int64_t win_count,
+                                  int64_t n_total, cudaStream_t s) {
 #define RX_CDC_CASE(NN, VPT, SPLIT)                                                                \
   case NN:                                                                                         \
-    return launch_cdc_n<NN, VPT, SPLIT>(V, tail, tail_first, tail_n, call, call_first, call_n,     \
-                                        dtype, scale, H, tw, u, u_base, u_stride, win_first,       \
-                                        win_count, n_total, s);
+    return launch_cdc_n<NN, VPT, SPLIT, FMT>(V, tail, tail_first, tail_n, call, call_first, call_n, \
+                                             dtype, scale, H, tw, u, u_base, u_stride, win_first,  \
+                                             win_count, n_total, s);
   switch (N) {
     RX_CDC_CASE(256, 16, false)
     RX_CDC_CASE(512, 16, false)
@@ -306,6 +334,26 @@ cudaError_t launch_cdc(int N, int V, const void *tail, int64_t tail_first, int64
     default: return cudaErrorInvalidValue;
   }
 #undef RX_CDC_CASE
+}
+
+cudaError_t launch_cdc(int N, int V, const void *tail, int64_t tail_first, int64_t tail_n,
+                       const void *call, int64_t call_first, int64_t call_n, int dtype,
+                       float scale, const float2 *H, const float2 *tw, void *u,
+                       int64_t u_base, int64_t u_stride, int64_t win_first, int64_t win_count,
+                       int64_t n_total, cudaStream_t s, int fmt) {
+  if (win_count <= 0) return cudaSuccess;
+  switch (fmt) {
+    case RX_FMT_F32:
+      return launch_cdc_fmt<RX_FMT_F32>(N, V, tail, tail_first, tail_n, call, call_first, call_n, dtype, scale, H, tw,
+                                        u, u_base, u_stride, win_first, win_count, n_total, s);
+    case RX_FMT_F16:
+      return launch_cdc_fmt<RX_FMT_F16>(N, V, tail, tail_first, tail_n, call, call_first, call_n, dtype, scale, H, tw,
+                                        u, u_base, u_stride, win_first, win_count, n_total, s);
+    case RX_FMT_BF16:
+      return launch_cdc_fmt<RX_FMT_BF16>(N, V, tail, tail_first, tail_n, call, call_first, call_n, dtype, scale, H,
+                                         tw, u, u_base, u_stride, win_first, win_count, n_total, s);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 // ---------------------------------------------------------------- buffer moves
@@ -328,6 +376,45 @@ cudaError_t launch_copy_cols(float2 *dst, int64_t dst_stride, const float2 *src,
   copy_cols_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(dst, dst_stride, src, src_stride, n);
   return cudaGetLastError();
 }
+__global__ void copy_cols_u32_kernel(uint32_t *dst, int64_t ds, const uint32_t *src, int64_t ss, int64_t n) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  dst[i] = src[i];
+  dst[ds + i] = src[ss + i];
+}
+template <int FMT>
+__global__ void cols_to_f32_kernel(float2 *dst, int64_t ds, const void *src_v, int64_t ss, int64_t n) {
+  typedef typename Fmt<FMT>::T S;
+  const S *src = reinterpret_cast<const S *>(src_v);
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  dst[i] = ld2(src[i]);
+  dst[ds + i] = ld2(src[ss + i]);
+}
+
+cudaError_t launch_copy_cols_fmt(void *dst, int64_t dst_stride, const void *src, int64_t src_stride, int64_t n,
+                                 int fmt, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  if (fmt == RX_FMT_F32)
+    return launch_copy_cols((float2 *)dst, dst_stride, (const float2 *)src, src_stride, n, s);
+  copy_cols_u32_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>((uint32_t *)dst, dst_stride, (const uint32_t *)src,
+                                                                  src_stride, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cols_to_f32(float2 *dst, int64_t dst_stride, const void *src, int64_t src_stride, int64_t n,
+                               int fmt, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  const unsigned g = (unsigned)((n + 255) / 256);
+  switch (fmt) {
+    case RX_FMT_F32: cols_to_f32_kernel<RX_FMT_F32><<<g, 256, 0, s>>>(dst, dst_stride, src, src_stride, n); break;
+    case RX_FMT_F16: cols_to_f32_kernel<RX_FMT_F16><<<g, 256, 0, s>>>(dst, dst_stride, src, src_stride, n); break;
+    case RX_FMT_BF16: cols_to_f32_kernel<RX_FMT_BF16><<<g, 256, 0, s>>>(dst, dst_stride, src, src_stride, n); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
 cudaError_t launch_copy_cols_i8(int8_t *dst, int64_t dst_stride, const int8_t *src,
                                 int64_t src_stride, int64_t n, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;

@@ -347,6 +347,13 @@ struct rx_cnn {
   int64_t step = 0;
   std::vector<void *> allocs;
   std::string msg;
+  // profiling: event pairs around launches of each kind (RX_CNN_K_*)
+  bool profile = false;
+  std::vector<cudaEvent_t> ev_pool;
+  size_t ev_used = 0;
+  std::vector<std::pair<int, size_t>> ev_pending;
+  double kind_ms[RX_CNN_KINDS] = {0, 0, 0, 0, 0};
+  int64_t kind_launches[RX_CNN_KINDS] = {0, 0, 0, 0, 0};
 };
 
 namespace {
@@ -379,18 +386,44 @@ void release(rx_cnn *c) {
   c->allocs.clear();
 }
 
+// Event pair around one launch of a kind, when profiling.
+struct KTimer {
+  rx_cnn *c;
+  int kind;
+  size_t idx = (size_t)-1;
+  KTimer(rx_cnn *cc, int k) : c(cc), kind(k) {
+    c->kind_launches[kind] += 1;
+    if (!c->profile) return;
+    while (c->ev_pool.size() < c->ev_used + 2) {
+      cudaEvent_t e;
+      if (cudaEventCreate(&e) != cudaSuccess) return;
+      c->ev_pool.push_back(e);
+    }
+    idx = c->ev_used;
+    c->ev_used += 2;
+    cudaEventRecord(c->ev_pool[idx], c->stream);
+  }
+  ~KTimer() {
+    if (idx == (size_t)-1) return;
+    cudaEventRecord(c->ev_pool[idx + 1], c->stream);
+    c->ev_pending.push_back({kind, idx});
+  }
+};
+
 int conv_grid(const rx_cnn *c, int64_t K) {
   return (int)std::max<int64_t>(1, std::min<int64_t>((K + TM - 1) / TM, c->sms));
 }
 
 template <int CIN, int COUT, int EPI>
-cudaError_t launch_conv(const rx_cnn *c, const ConvArgs &a) {
+cudaError_t launch_conv(rx_cnn *c, const ConvArgs &a) {
+  KTimer tm(c, EPI == EPI_MASK ? RX_CNN_K_DX : (CIN == CH && COUT == CH ? RX_CNN_K_FWD_HIDDEN : RX_CNN_K_FWD_EDGE));
   conv_kernel<CIN, COUT, EPI><<<conv_grid(c, a.K), kThreads, conv_smem<CIN, COUT, EPI>(), c->stream>>>(a);
   return cudaGetLastError();
 }
 
 template <int CIN, int COUT>
-cudaError_t launch_dw(const rx_cnn *c, const bf16 *in, const bf16 *dz, int64_t K, int l) {
+cudaError_t launch_dw(rx_cnn *c, const bf16 *in, const bf16 *dz, int64_t K, int l) {
+  KTimer tm(c, RX_CNN_K_DW);
   DwArgs a;
   a.in = in;
   a.dz = dz;
@@ -633,6 +666,7 @@ rx_status rx_cnn_train_step(rx_cnn *c, const float *z, int64_t zs, const float *
   c->step += 1;
   const float c1 = (float)(1.0 - pow(0.9, (double)c->step));
   const float c2 = (float)(1.0 - pow(0.999, (double)c->step));
+  KTimer tm(c, RX_CNN_K_UPDATE);
   adam_kernel<<<std::max(1, std::min(c->sms * 4, (int)((c->n_params + 255) / 256))), 256, 0, c->stream>>>(
       c->P, c->G, c->M, c->V, c->n_params, lr, c1, c2);
   CX_CUDA(cudaGetLastError(), "adam");
@@ -645,9 +679,37 @@ rx_status rx_cnn_train_step(rx_cnn *c, const float *z, int64_t zs, const float *
   return RX_OK;
 }
 
+rx_status rx_cnn_set_profile(rx_cnn *c, int on) {
+  if (!c) return RX_EINVAL;
+  c->profile = on != 0;
+  return RX_OK;
+}
+
+rx_status rx_cnn_profile(rx_cnn *c, double *ms, int64_t *launches, int reset) {
+  if (!c) return RX_EINVAL;
+  CX_CUDA(cudaStreamSynchronize(c->stream), "profile wait");
+  for (const auto &pe : c->ev_pending) {
+    float t = 0.f;
+    CX_CUDA(cudaEventElapsedTime(&t, c->ev_pool[pe.second], c->ev_pool[pe.second + 1]), "profile");
+    c->kind_ms[pe.first] += t;
+  }
+  c->ev_pending.clear();
+  c->ev_used = 0;
+  for (int i = 0; i < RX_CNN_KINDS; ++i) {
+    if (ms) ms[i] = c->kind_ms[i];
+    if (launches) launches[i] = c->kind_launches[i];
+    if (reset) {
+      c->kind_ms[i] = 0;
+      c->kind_launches[i] = 0;
+    }
+  }
+  return RX_OK;
+}
+
 void rx_cnn_destroy(rx_cnn *c) {
   if (!c) return;
   cudaStreamSynchronize(c->stream);
+  for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
   release(c);
   delete c;
 }

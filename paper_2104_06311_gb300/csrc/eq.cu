@@ -47,6 +47,8 @@
 // to 1152 symbols sits in shared memory (rows padded against bank conflicts),
 // rotated by exp(-j phi_n) from the 64-bit fixed-point phase through a
 // 256-entry phasor table and a short Taylor polynomial.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <math.h>
 
 #include "common.cuh"
@@ -146,22 +148,39 @@ struct Rot {
 };
 
 // u0/u1: CDC output of pols X/Y, indexed by stream sample n.
-__device__ __forceinline__ void load_window(const float2 *__restrict__ u0, const float2 *__restrict__ u1,
-                                            EqSmem &sm, int64_t win_lo, int count, const Rot &rot,
+// Sample n of a CDC output row stored in format fmt (RX_FMT_*), as complex float.
+__device__ __forceinline__ float2 ld_u(const unsigned char *__restrict__ row, int64_t n, int fmt) {
+  if (fmt == RX_FMT_F32) return __ldg(reinterpret_cast<const float2 *>(row) + n);
+  const unsigned w = __ldg(reinterpret_cast<const unsigned *>(row) + n);
+  if (fmt == RX_FMT_F16) return __half22float2(*reinterpret_cast<const __half2 *>(&w));
+  return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&w));
+}
+
+__device__ __forceinline__ void load_window(const unsigned char *__restrict__ u0, const unsigned char *__restrict__ u1,
+                                            int fmt, EqSmem &sm, int64_t win_lo, int count, const Rot &rot,
                                             int64_t n_limit) {
   // issue every load of this thread first (HBM latency once, not per sample)
   constexpr int kPer = (kWinMax + kEqThreads - 1) / kEqThreads;
   float2 va[kPer], vb[kPer];
-#pragma unroll
-  for (int r = 0; r < kPer; ++r) {
-    const int j = threadIdx.x + r * kEqThreads;
-    const int64_t n = win_lo + j;
-    va[r] = vb[r] = make_float2(0.f, 0.f);
-    if (j < count && n >= 0 && n < n_limit) {
-      va[r] = __ldg(&u0[n]);
-      vb[r] = __ldg(&u1[n]);
-    }
+  // one loop per format (the format is uniform: no per-sample branch)
+#define RX_LOAD_LOOP(FMT_)                                   \
+  _Pragma("unroll") for (int r = 0; r < kPer; ++r) {         \
+    const int j = threadIdx.x + r * kEqThreads;              \
+    const int64_t n = win_lo + j;                            \
+    va[r] = vb[r] = make_float2(0.f, 0.f);                   \
+    if (j < count && n >= 0 && n < n_limit) {                \
+      va[r] = ld_u(u0, n, FMT_);                             \
+      vb[r] = ld_u(u1, n, FMT_);                             \
+    }                                                        \
   }
+  if (fmt == RX_FMT_F32) {
+    RX_LOAD_LOOP(RX_FMT_F32)
+  } else if (fmt == RX_FMT_F16) {
+    RX_LOAD_LOOP(RX_FMT_F16)
+  } else {
+    RX_LOAD_LOOP(RX_FMT_BF16)
+  }
+#undef RX_LOAD_LOOP
 #pragma unroll
   for (int r = 0; r < kPer; ++r) {
     const int j = threadIdx.x + r * kEqThreads;
@@ -205,8 +224,9 @@ struct Lane {
 
 // Loop-invariant scalars of a launch, held in registers.
 struct Hot {
-  float2 *yrow;              // equaliser output of this row, indexed by stream symbol
-  const float2 *u0, *u1;     // CDC output of pols X / Y, indexed by stream sample
+  float2 *yrow;                    // equaliser output of this row, indexed by stream symbol
+  const unsigned char *u0, *u1;    // CDC output of pols X / Y (format u_fmt), indexed by stream sample
+  int u_fmt;
   int T, c, Bu;
   float mu_cma, mu_dd, cma_r2;
 };
@@ -264,7 +284,7 @@ __device__ __forceinline__ void run_span(const Hot hot, EqSmem &sm, const Span s
     const int count = (int)(2 * (ce - cs) + 2 * c - 1);
     const int nsteps = (int)((ce - cs + Bu - 1) / Bu);
     __syncthreads();  // every warp is done with the previous chunk's window
-    load_window(hot.u0, hot.u1, sm, win_lo, count, sp.rot, n_limit);
+    load_window(hot.u0, hot.u1, hot.u_fmt, sm, win_lo, count, sp.rot, n_limit);
     __syncthreads();
     for (int t = 0; t < nsteps; ++t, ++step) {
       const int64_t k0 = cs + (int64_t)t * Bu;
@@ -470,8 +490,13 @@ __device__ __forceinline__ void eq_body(const EqLaunch &L, const int cta, EqSmem
   const int64_t n_limit = L.K >= 0 ? 2 * L.K : (int64_t)1 << 62;
   Hot hot;
   hot.yrow = L.y + (int64_t)p * L.y_stride - L.y_base;
-  hot.u0 = L.u - L.u_base;
-  hot.u1 = L.u + L.u_stride - L.u_base;
+  {
+    const int64_t esz = fmt_bytes(L.u_fmt);
+    const unsigned char *ub = static_cast<const unsigned char *>(L.u);
+    hot.u0 = ub - L.u_base * esz;
+    hot.u1 = ub + (L.u_stride - L.u_base) * esz;
+    hot.u_fmt = L.u_fmt;
+  }
   hot.T = L.T;
   hot.c = (L.T - 1) / 2;
   hot.Bu = L.Bu;

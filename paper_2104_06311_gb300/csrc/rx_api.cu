@@ -58,7 +58,8 @@ struct rx_stream {
   float2 *H = nullptr, *tw = nullptr;
   uint8_t *tail[2] = {nullptr, nullptr};
   int64_t tail_cap = 0;  // sample-times
-  float2 *u[2] = {nullptr, nullptr};
+  float2 *u[2] = {nullptr, nullptr};   // CDC output, [2][u_cap] samples of fmt_bytes(fmt) bytes each
+  int fmt = RX_FMT_F32;                // storage format of the CDC output (RX_P_PRECISION)
   int64_t u_cap = 0;
   float2 *y[2] = {nullptr, nullptr};
   int8_t *bh[2] = {nullptr, nullptr};
@@ -290,6 +291,11 @@ rx_status post_error_copy(rx_stream *rx) {
   return RX_OK;
 }
 
+// Sample n (buffer-relative) of pol p of CDC buffer b, in the buffer's format.
+unsigned char *u_at(rx_stream *rx, int b, int p, int64_t n) {
+  return reinterpret_cast<unsigned char *>(rx->u[b]) + (p * rx->u_cap + n) * fmt_bytes(rx->fmt);
+}
+
 // Region layout: region 0 = [0, A), region r >= 1 = [A + (r-1) span, A + r span).
 int64_t region_end_after(const rx_stream *rx, int64_t k) {
   // end of the region that starts at or contains symbol k
@@ -388,6 +394,7 @@ rx_status rx_set_param(rx_stream *rx, int key, double v) {
     case RX_P_CDC_OUT: rx->cdc_out = v != 0; return RX_OK;
     case RX_P_PROFILE: rx->profile = v != 0; return RX_OK;
     case RX_P_PIPELINE: s = as_int(1, kMaxPieces, &t); rx->pieces = (int)t; return s;
+    case RX_P_PRECISION: s = as_int(0, 2, &t); rx->fmt = (int)t; break;
     default: return fail(rx, RX_EINVAL, "unknown parameter key");
   }
   if (s != RX_OK) return s;
@@ -425,6 +432,7 @@ rx_status rx_get_param(rx_stream *rx, int key, double *v) {
     case RX_P_EQ_OUT: *v = rx->eq_out; break;
     case RX_P_CDC_OUT: *v = rx->cdc_out; break;
     case RX_P_PROFILE: *v = rx->profile; break;
+    case RX_P_PRECISION: *v = rx->fmt; break;
     case RX_P_PIPELINE: *v = rx->pieces; break;
     default: return fail(rx, RX_EINVAL, "unknown parameter key");
   }
@@ -629,7 +637,9 @@ rx_status rx_process(rx_stream *rx, const rx_in *in, rx_out *out) {
     StageTimer tm(rx, RX_STAGE_MOVE, st);
     rx->stage_launches[RX_STAGE_MOVE] += keep > 0;
     const int nxt = 1 - rx->cur_u;
-    RX_CUDA(launch_copy_cols(rx->u[nxt], rx->u_cap, rx->u[rx->cur_u] + (u_keep - rx->u_base), rx->u_cap, keep, st), "slide u");
+    RX_CUDA(launch_copy_cols_fmt(u_at(rx, nxt, 0, 0), rx->u_cap, u_at(rx, rx->cur_u, 0, u_keep - rx->u_base), rx->u_cap,
+                                 keep, rx->fmt, st),
+            "slide u");
     rx->cur_u = nxt;
     rx->u_base = u_keep;
   }
@@ -671,7 +681,7 @@ rx_status rx_process(rx_stream *rx, const rx_in *in, rx_out *out) {
       rx->stage_launches[RX_STAGE_CDC] += 1;
       RX_CUDA(launch_cdc(rx->N, rx->V, rx->tail[rx->cur_tail], rx->tail_first, rx->tail_n, in->data, call_first,
                          call_n, rx->dtype, (float)rx->in_scale, rx->H, rx->tw, rx->u[rx->cur_u], rx->u_base,
-                         rx->u_cap, w_done, w_need - w_done, rx->n_total, rx->sub[0]),
+                         rx->u_cap, w_done, w_need - w_done, rx->n_total, rx->sub[0], rx->fmt),
               "cdc");
       w_done = w_need;
     }
@@ -715,6 +725,7 @@ rx_status rx_process(rx_stream *rx, const rx_in *in, rx_out *out) {
       L.inc_scale = (float)(18446744073709551616.0 / (4.0 * 3.14159265358979323846 * rx->fo_smooth));
       L.fo_track = rx->fo_track;
       L.nblocks = rx->eq_blocks;
+      L.u_fmt = rx->fmt;
       RX_CUDA(cudaMemsetAsync(rx->barrier, 0, 2 * sizeof(unsigned), rx->sub[1]), "barrier reset");
       StageTimer tm(rx, RX_STAGE_EQ, rx->sub[1]);
       rx->stage_launches[RX_STAGE_EQ] += 1;
@@ -772,7 +783,9 @@ rx_status rx_process(rx_stream *rx, const rx_in *in, rx_out *out) {
   // ---------------------------------------------------------------- after the join (bound stream)
   if (rx->cdc_out && F_cdc_new > F_cdc_old) {
     const int64_t n = F_cdc_new - F_cdc_old;  // the cdc array holds in->n + N samples per pol
-    RX_CUDA(launch_copy_cols((float2 *)out->cdc, out->cdc_stride, rx->u[rx->cur_u] + (F_cdc_old - rx->u_base), rx->u_cap, n, st), "cdc out");
+    RX_CUDA(launch_cols_to_f32((float2 *)out->cdc, out->cdc_stride, u_at(rx, rx->cur_u, 0, F_cdc_old - rx->u_base),
+                               rx->u_cap, n, rx->fmt, st),
+            "cdc out");
     out->cdc_first = F_cdc_old;
     out->cdc_n = n;
   }
@@ -865,7 +878,7 @@ rx_status rx_get_state(rx_stream *rx, void *blob, size_t *len) {
   const size_t elem = rx->dtype == RX_I8x4 ? 4 : 16;
   const int64_t nu = rx->F_cdc - rx->u_base, ny = rx->F_eq - rx->y_base;
   const size_t need = sizeof(BlobHeader) + sizeof(EqState) + 2 * sizeof(int64_t) + rx->tail_n * elem +
-                      2 * nu * sizeof(float2) + 2 * ny * (sizeof(float2) + 1);
+                      2 * nu * fmt_bytes(rx->fmt) + 2 * ny * (sizeof(float2) + 1);
   if (!blob) {
     *len = need;
     return RX_OK;
@@ -882,15 +895,15 @@ rx_status rx_get_state(rx_stream *rx, void *blob, size_t *len) {
   v[0] = rx->started; v[1] = rx->flushed; v[2] = rx->dtype; v[3] = rx->M_in; v[4] = rx->n_total;
   v[5] = rx->tail_first; v[6] = rx->tail_n; v[7] = rx->next_win; v[8] = rx->F_cdc; v[9] = rx->u_base;
   v[10] = rx->acq_done; v[11] = rx->next_wave; v[12] = rx->F_eq; v[13] = rx->A; v[14] = rx->y_base;
-  v[15] = rx->F_out; v[16] = rx->N; v[17] = rx->T; v[18] = rx->P; v[19] = rx->max_call;
+  v[15] = rx->F_out; v[16] = rx->N; v[17] = rx->T; v[18] = rx->P; v[19] = rx->max_call; v[20] = rx->fmt;
   uint8_t *o = (uint8_t *)blob;
   memcpy(o, &h, sizeof(h)); o += sizeof(h);
   RX_CUDA(cudaMemcpy(o, rx->st, sizeof(EqState), cudaMemcpyDeviceToHost), "state"); o += sizeof(EqState);
   RX_CUDA(cudaMemcpy(o, rx->m_carry, 2 * sizeof(int64_t), cudaMemcpyDeviceToHost), "state"); o += 2 * sizeof(int64_t);
   RX_CUDA(cudaMemcpy(o, rx->tail[rx->cur_tail], rx->tail_n * elem, cudaMemcpyDeviceToHost), "state"); o += rx->tail_n * elem;
   for (int p = 0; p < 2; ++p) {
-    RX_CUDA(cudaMemcpy(o, rx->u[rx->cur_u] + p * rx->u_cap, nu * sizeof(float2), cudaMemcpyDeviceToHost), "state");
-    o += nu * sizeof(float2);
+    RX_CUDA(cudaMemcpy(o, u_at(rx, rx->cur_u, p, 0), nu * fmt_bytes(rx->fmt), cudaMemcpyDeviceToHost), "state");
+    o += nu * fmt_bytes(rx->fmt);
   }
   for (int p = 0; p < 2; ++p) {
     RX_CUDA(cudaMemcpy(o, rx->y[rx->cur_y] + p * rx->y_cap, ny * sizeof(float2), cudaMemcpyDeviceToHost), "state");
@@ -912,11 +925,12 @@ rx_status rx_set_state(rx_stream *rx, const void *blob, size_t len) {
     rx_status s = rx_reserve(rx, v[19]);
     if (s != RX_OK) return s;
   }
-  if (v[16] != rx->N || v[17] != rx->T || v[18] != rx->P) return fail(rx, RX_EINVAL, "state from a receiver with other parameters");
+  if (v[16] != rx->N || v[17] != rx->T || v[18] != rx->P || v[20] != rx->fmt)
+    return fail(rx, RX_EINVAL, "state from a receiver with other parameters");
   const size_t elem = v[2] == RX_I8x4 ? 4 : 16;
   const int64_t tail_n = v[6], nu = v[8] - v[9], ny = v[12] - v[14];
   const size_t need = sizeof(BlobHeader) + sizeof(EqState) + 2 * sizeof(int64_t) + tail_n * elem +
-                      2 * nu * sizeof(float2) + 2 * ny * (sizeof(float2) + 1);
+                      2 * nu * fmt_bytes(rx->fmt) + 2 * ny * (sizeof(float2) + 1);
   if (len < need) return fail(rx, RX_EINVAL, "state blob truncated");
   if (tail_n > rx->tail_cap || nu > rx->u_cap || ny > rx->y_cap) return fail(rx, RX_EINVAL, "state does not fit the reservation");
   RX_CUDA(cudaStreamSynchronize(rx->stream), "state wait");
@@ -930,8 +944,8 @@ rx_status rx_set_state(rx_stream *rx, const void *blob, size_t len) {
   RX_CUDA(cudaMemcpy(rx->m_carry, o, 2 * sizeof(int64_t), cudaMemcpyHostToDevice), "state"); o += 2 * sizeof(int64_t);
   RX_CUDA(cudaMemcpy(rx->tail[0], o, tail_n * elem, cudaMemcpyHostToDevice), "state"); o += tail_n * elem;
   for (int p = 0; p < 2; ++p) {
-    RX_CUDA(cudaMemcpy(rx->u[0] + p * rx->u_cap, o, nu * sizeof(float2), cudaMemcpyHostToDevice), "state");
-    o += nu * sizeof(float2);
+    RX_CUDA(cudaMemcpy(u_at(rx, 0, p, 0), o, nu * fmt_bytes(rx->fmt), cudaMemcpyHostToDevice), "state");
+    o += nu * fmt_bytes(rx->fmt);
   }
   for (int p = 0; p < 2; ++p) {
     RX_CUDA(cudaMemcpy(rx->y[0] + p * rx->y_cap, o, ny * sizeof(float2), cudaMemcpyHostToDevice), "state");

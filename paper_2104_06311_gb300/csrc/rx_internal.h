@@ -15,6 +15,10 @@ constexpr int kEqThreads = 128;   // equaliser CTA: 4 warps, one butterfly row
 constexpr int kChunkSym = 1152;   // equaliser span chunk (symbols) held in smem
 constexpr int kBpsChunk = 256;    // BPS pass-1 symbols per warp
 
+// Storage formats of the CDC output (precision form).
+enum { RX_FMT_F32 = 0, RX_FMT_F16 = 1, RX_FMT_BF16 = 2 };
+__host__ __device__ inline int fmt_bytes(int fmt) { return fmt == RX_FMT_F32 ? 8 : 4; }
+
 // Length of a time-domain CD compensating filter, 2 floor(|D| lam^2 L /
 // (2 c T^2)) + 1 with T the sample period (the textbook bound; the paper's
 // static equaliser leaves it open).
@@ -42,7 +46,7 @@ struct EqState {
 
 // Parameters of one equaliser launch (all values already validated).
 struct EqLaunch {
-  const float2 *u;          // CDC output [2][u_stride], sample n at u[n - u_base]
+  const void *u;            // CDC output [2][u_stride], sample n at u[n - u_base] (format u_fmt)
   int64_t u_base, u_stride;
   float2 *y;                // equaliser out [2][y_stride], symbol k at y[k - y_base]
   int64_t y_base, y_stride;
@@ -68,6 +72,7 @@ struct EqLaunch {
   float inc_scale;          // 2^64 / (4 pi fo_smooth): tracker step r -> Q0.64 per sample
   int fo_track;
   int nblocks;              // CTAs in the grid (even: 2 rows per segment slot)
+  int u_fmt;                // storage format of u (RX_FMT_*)
 };
 
 // Per-stream BPS/demap launch description.
@@ -98,9 +103,9 @@ cudaError_t launch_tables(float2 *H, float2 *tw, int N, double baud, double L_km
                           double lam_nm, double rolloff, cudaStream_t s);
 cudaError_t launch_cdc(int N, int V, const void *tail, int64_t tail_first, int64_t tail_n,
                        const void *call, int64_t call_first, int64_t call_n, int dtype,
-                       float scale, const float2 *H, const float2 *tw, float2 *u,
+                       float scale, const float2 *H, const float2 *tw, void *u,
                        int64_t u_base, int64_t u_stride, int64_t win_first, int64_t win_count,
-                       int64_t n_total, cudaStream_t s);
+                       int64_t n_total, cudaStream_t s, int fmt = RX_FMT_F32);
 cudaError_t launch_eq(const EqLaunch &L, cudaStream_t s);
 // Batched equaliser: one cooperative launch of nblocks CTAs; d_team[b] =
 // (stream, CTA within that stream's team).  pad_smem: unused dynamic shared
@@ -123,6 +128,11 @@ cudaError_t ber_run(const uint32_t *rx_bits, int64_t rx_stride, const uint32_t *
                     int32_t *sync);
 cudaError_t launch_copy_cols(float2 *dst, int64_t dst_stride, const float2 *src,
                              int64_t src_stride, int64_t n, cudaStream_t s);
+// Column copies in a storage format (fmt) and conversion to complex float.
+cudaError_t launch_copy_cols_fmt(void *dst, int64_t dst_stride, const void *src, int64_t src_stride, int64_t n,
+                                 int fmt, cudaStream_t s);
+cudaError_t launch_cols_to_f32(float2 *dst, int64_t dst_stride, const void *src, int64_t src_stride, int64_t n,
+                               int fmt, cudaStream_t s);
 cudaError_t launch_copy_cols_i8(int8_t *dst, int64_t dst_stride, const int8_t *src,
                                 int64_t src_stride, int64_t n, cudaStream_t s);
 

@@ -21,6 +21,7 @@ PARAMS = {
     "N_CMA": 8, "UPDATE_BLOCK": 9, "SEG_LEN": 10, "SEG_PRETRAIN": 11, "BPS_HALFWIN": 12,
     "BLOCK_SAMPLES": 13, "IN_SCALE": 14, "ACQ_MIN": 15, "FO_SMOOTH": 16, "FO_TRACK": 17,
     "LLR_OUT": 18, "SYM_OUT": 19, "EQ_OUT": 20, "CDC_OUT": 21, "PROFILE": 22, "PIPELINE": 23,
+    "PRECISION": 24,
 }
 STAGES = ["cdc", "eq", "bps", "move", "ber"]
 
@@ -33,7 +34,8 @@ EXPORTS = ["rx_create", "rx_set_param", "rx_get_param", "rx_set_cuda_stream", "r
            "rx_batch_last_error", "rx_batch_profile",
            "rx_cnn_create", "rx_cnn_param_count", "rx_cnn_set_params", "rx_cnn_get_params",
            "rx_cnn_set_cuda_stream", "rx_cnn_apply", "rx_cnn_grads", "rx_cnn_train_step", "rx_cnn_destroy",
-           "rx_cnn_last_error"]
+           "rx_cnn_last_error", "rx_cnn_set_profile", "rx_cnn_profile"]
+CNN_KINDS = ["fwd_hidden", "fwd_edge", "dx", "dw", "update"]
 BATCH_PARAMS = {"GRAPH": 100, "EQ_CTAS": 101, "EQ_TEAM": 102, "CDC_NS_PER_SAMPLE": 103, "PROFILE": 104}
 
 
@@ -120,6 +122,8 @@ def load(path: str = LIB_PATH) -> ct.CDLL:
     lib.rx_cnn_apply.argtypes = [P, P, ct.c_int64, P, ct.c_int64, ct.c_int64]
     lib.rx_cnn_grads.argtypes = [P, P, ct.c_int64, P, ct.c_int64, ct.c_int64, P, ct.POINTER(ct.c_double)]
     lib.rx_cnn_train_step.argtypes = [P, P, ct.c_int64, P, ct.c_int64, ct.c_int64, ct.c_float, P]
+    lib.rx_cnn_set_profile.argtypes = [P, ct.c_int]
+    lib.rx_cnn_profile.argtypes = [P, ct.POINTER(ct.c_double), ct.POINTER(ct.c_int64), ct.c_int]
     lib.rx_cnn_destroy.argtypes = [P]
     lib.rx_cnn_destroy.restype = None
     lib.rx_cnn_last_error.argtypes = [P]
@@ -572,6 +576,20 @@ class CNN:
         _ccheck(self.lib, self.h, self.lib.rx_cnn_train_step(self.h, zp, zs, tp, ts, z.shape[1], float(lr), acc))
 
     train_step = rx_cnn_train_step
+
+    def rx_cnn_set_profile(self, on=True):
+        _ccheck(self.lib, self.h, self.lib.rx_cnn_set_profile(self.h, 1 if on else 0))
+
+    set_profile = rx_cnn_set_profile
+
+    def rx_cnn_profile(self, reset=False):
+        """{kind: (ms, launches)} since the last reset."""
+        ms = (ct.c_double * len(CNN_KINDS))()
+        n = (ct.c_int64 * len(CNN_KINDS))()
+        _ccheck(self.lib, self.h, self.lib.rx_cnn_profile(self.h, ms, n, 1 if reset else 0))
+        return {k: (ms[i], n[i]) for i, k in enumerate(CNN_KINDS)}
+
+    profile = rx_cnn_profile
 
     def close(self):
         if getattr(self, "h", None):

@@ -129,7 +129,7 @@ def _chain(gen, link):
     t = np.zeros((2, k1 - k0), np.complex128)
     for pp, (q, r, d) in enumerate(sync):
         t[pp] = (1j ** r) * gen.tx_symbols[q, k0 + d:k1 + d]
-    return z[:, k0:k1], t, e / max(nb, 1)
+    return z[:, k0:k1], L.align_rotation(z[:, k0:k1], t), e / max(nb, 1)
 
 
 def test_training_gains_over_the_chain_on_a_nonlinear_link():

@@ -1,0 +1,99 @@
+"""Precision form on the 16QAM 32 GBd 6000 km shape (N = 16384): the CDC
+transform and its output stored in FP16 or BF16 (FP32 arithmetic, 64-bit
+phase trackers) against the FP64 oracle, stage by stage, with the penalty
+relative to the FP32 chain stated per result.
+
+Bounds from the arithmetic: each FP16 (BF16) rounding has relative RMS error
+u / sqrt(3) with u = 2^-11 (2^-8); the transform stores ~2 x 4 passes plus
+ingest, filter and output (~11 roundings), so the CDC output sits near
+sqrt(11) u / sqrt(3) ~ 1e-3 (8e-3) of the oracle; that noise is ~60 dB
+(42 dB) below the signal, so the effective-SNR penalty at 18 dB must stay
+below 0.1 dB (the stated budget) for both."""
+import math
+
+import numpy as np
+import pytest
+
+import linksim as L
+import oracle as O
+from chain_helpers import ensure_built, make_receiver, rel_rms, rx_params
+from test_gpu_chain import gpu_tracker
+
+pytestmark = pytest.mark.gpu
+
+U_TOL = {0: 1e-4, 1: 3e-3, 2: 2e-2}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    ensure_built()
+
+
+def _run(p, g, fmt):
+    import torch
+    rx = make_receiver(p, LLR_OUT=1, SYM_OUT=1, EQ_OUT=1, CDC_OUT=1, PRECISION=fmt)
+    assert rx.get_param("PRECISION") == fmt
+    x = torch.from_numpy(np.ascontiguousarray(g.samples)).cuda()
+    out = rx.run_stream(x, llr=True, sym=True, eq=True, cdc=True)
+    torch.cuda.synchronize()
+    K = out["n"]
+    res = dict(rx=rx, K=K, u=out["cdc"][:, :out["cdc_n"]].cpu().numpy().astype(np.complex128),
+               y=out["eq"][:, :K].cpu().numpy().astype(np.complex128),
+               z=out["sym"][:, :K].cpu().numpy().astype(np.complex128),
+               bits=L.unpack_bits(out["bits"].cpu().numpy().view(np.uint32), K * p.bits))
+    ref = torch.from_numpy(L.pack_bits(g.tx_bits).view(np.int32)).cuda()
+    e, n, _ = rx.ber(out["bits"], ref, K)
+    res["ber"] = (e, n)
+    return res
+
+
+def _evm_db(z, mod, k0):
+    d = O.decide(z[:, k0:], mod)
+    return 10 * math.log10(np.mean(np.abs(z[:, k0:] - d) ** 2) / np.mean(np.abs(d) ** 2))
+
+
+def test_precision_forms_against_oracle_and_fp32():
+    lk = L.workload("c3", n_sym=1 << 16)
+    g = L.generate(lk)
+    p = rx_params(lk, g.in_scale)
+    assert p.fft_n == 16384
+    K = lk.n_sym
+    k0 = p.acq_len(K) + 8192
+    runs = {fmt: _run(p, g, fmt) for fmt in (0, 1, 2)}
+    rows = []
+    for fmt, r in runs.items():
+        dev = gpu_tracker(r["rx"], p, K)
+        orc = O.run_chain(g.samples, p, {}, follow=dev)
+        e_u = rel_rms(r["u"][:, :2 * K], orc["u"])
+        e_y = rel_rms(r["y"], orc["y"])
+        evm = _evm_db(r["z"], p.mod, k0)
+        evm_o = _evm_db(orc["z"], p.mod, k0)
+        e, n = r["ber"]
+        rows.append((fmt, e_u, e_y, evm, evm_o, e / max(n, 1)))
+        assert e_u < U_TOL[fmt], (fmt, e_u)
+    evm32 = rows[0][3]
+    for fmt, e_u, e_y, evm, evm_o, ber in rows:
+        name = {0: "FP32", 1: "FP16", 2: "BF16"}[fmt]
+        print(f"{name}: CDC rel RMS {e_u:.2e}, equaliser rel RMS {e_y:.2e}, EVM {evm:.3f} dB "
+              f"(oracle {evm_o:.3f} dB), penalty vs FP32 {evm - evm32:+.4f} dB, BER {ber:.3e}")
+        assert evm - evm32 < 0.1
+    # BER of every form within 3 sigma (Poisson) of the FP32 count
+    e32 = runs[0]["ber"][0]
+    for fmt in (1, 2):
+        assert abs(runs[fmt]["ber"][0] - e32) < 3 * math.sqrt(max(e32, 25)) + 5, (fmt, runs[fmt]["ber"], e32)
+
+
+def test_precision_streaming_and_state_roundtrip():
+    """FP16 storage through the carried-tail path: streamed calls equal one call bit for bit."""
+    import torch
+    lk = L.Link(mod="qpsk", baud=10e9, n_sym=60_000, L_km=2000.0, snr_db=12.0, adc="int8", seed=91)
+    g = L.generate(lk)
+    p = rx_params(lk, g.in_scale)
+    x = torch.from_numpy(np.ascontiguousarray(g.samples)).cuda()
+    outs = []
+    for chunk in (None, 20_000 * 2 + 64):
+        rx = make_receiver(p, EQ_OUT=1, PRECISION=1)
+        o = rx.run_stream(x, chunk=chunk, eq=True)
+        torch.cuda.synchronize()
+        outs.append((o["bits"].cpu().numpy(), o["eq"][:, :o["n"]].cpu().numpy()))
+    assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
