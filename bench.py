@@ -56,6 +56,21 @@ def parse():
     return ap.parse_args()
 
 
+def max_over_ranks(ms, dist=None, device="cpu"):
+    """The slowest rank's time (every rank gets it); ms itself on one rank."""
+    if dist is None:
+        return ms
+    import torch
+    t = torch.tensor([float(ms)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank, steps, world, ms):
+    """Units all ranks processed (replicas: each rank its own full workload) per second, in 1e9/s."""
+    return units_per_rank * steps * world / (ms / 1e3) / 1e9
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -213,11 +228,8 @@ def bench_batch(args, rank, world, local):
     clk = clocks.stop()
     ms = t0.elapsed_time(t1)
     launches = sum(v[1] for v in b.profile(reset=True).values())
-    if dist is not None:
-        tm = torch.tensor([ms], device="cuda")
-        dist.all_reduce(tm, op=dist.ReduceOp.MAX)
-        ms = float(tm.item())
-    value = n_total * args.steps * world / (ms / 1e3) / 1e9
+    ms = max_over_ranks(ms, dist, "cuda")
+    value = whole_job_rate(n_total, args.steps, world, ms)
     # stage split from profiled (eager) calls
     b.set_param("PROFILE", 1)
     for _ in range(args.steps):
@@ -525,11 +537,8 @@ def main():
     ms = t0.elapsed_time(t1)
     prof = rx.profile(reset=True)
     rx.set_param("PROFILE", 0)
-    if dist is not None:
-        tm = torch.tensor([ms], device="cuda")
-        dist.all_reduce(tm, op=dist.ReduceOp.MAX)
-        ms = float(tm.item())
-    value = n * args.steps * world / (ms / 1e3) / 1e9
+    ms = max_over_ranks(ms, dist, "cuda")
+    value = whole_job_rate(n, args.steps, world, ms)
     launches = sum(v[1] for v in prof.values())
 
     # ---- end to end: pinned host samples -> device -> chain -> bits + BER back to the host
@@ -557,11 +566,8 @@ def main():
         b.record(stream)
         torch.cuda.synchronize()
         ems = a.elapsed_time(b)
-        if dist is not None:
-            tm = torch.tensor([ems], device="cuda")
-            dist.all_reduce(tm, op=dist.ReduceOp.MAX)
-            ems = float(tm.item())
-        e2e = {"value": n * args.steps * world / (ems / 1e3) / 1e9, "unit": "GSa/s",
+        ems = max_over_ranks(ems, dist, "cuda")
+        e2e = {"value": whole_job_rate(n, args.steps, world, ems), "unit": "GSa/s",
                "h2d_bytes_per_step": int(x.numel() * x.element_size()),
                "d2h_bytes_per_step": int(out["bits"].numel() * 4 + 16)}
 
