@@ -428,8 +428,10 @@ def bench_learned(args, rank, world, local):
     per_launch_ms = hid_ms / max(1, hid_n)
     achieved = per_launch_flop / (per_launch_ms / 1e3) / 1e12
     roof = {"bound": "tensor", "achieved": achieved, "peak": pk["bf16_tflops"], "unit": "TFLOP/s",
-            "frac": achieved / pk["bf16_tflops"], "traffic": None, "kernel": "conv_kernel<64,64> (forward)",
-            "peak_source": pk_kind, "note": "mma.sync m16n8k16 BF16; peak = measured cuBLAS bf16 burst"}
+            "frac": achieved / pk["bf16_tflops"], "traffic": None, "kernel": "conv_tc_kernel (64 -> 64 forward)",
+            "peak_source": pk_kind,
+            "note": "tcgen05.mma kind::f16 M128 N64 K16, BF16 in, FP32 in tensor memory; "
+                    "peak = measured cuBLAS bf16 burst"}
     line = {
         "metric": METRIC, "value": n / (e2e_ms / 1e3) / 1e9, "unit": "GSa/s", "n_gpus": 1, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": e2e_ms, "higher_is_better": True, "scaling": "weak",

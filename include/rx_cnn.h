@@ -24,8 +24,8 @@
  * (pol X, pol Y) with the given row strides in complex elements, 8-byte
  * aligned.  All calls are asynchronous on the bound stream except those
  * that return host values (rx_cnn_grads' loss, rx_cnn_get_params), which
- * synchronise it.  Status codes as rx.h; device memory is allocated in
- * rx_cnn_create only.
+ * synchronise it and report a device-side wait that gave up (RX_ETIMEOUT).
+ * Status codes as rx.h; device memory is allocated in rx_cnn_create only.
  */
 #ifndef RX_CNN_H_
 #define RX_CNN_H_
@@ -76,6 +76,15 @@ enum {
   RX_CNN_K_UPDATE = 4,      /* Adam                                               */
   RX_CNN_KINDS = 5
 };
+
+/* Options for rx_cnn_set_option. */
+enum {
+  RX_CNN_OPT_TCGEN05 = 1    /* 1 (default): the 64 -> 64 convolutions (forward and
+                               input gradient) run on tcgen05 / tensor memory;
+                               0: on warp-level mma.sync (BF16, FP32 accumulate),
+                               the kernel the first and last layers always use   */
+};
+rx_status rx_cnn_set_option(rx_cnn *c, int key, int value);
 
 /* 1 = bracket every launch with CUDA events (rx_cnn_profile reads them). */
 rx_status rx_cnn_set_profile(rx_cnn *c, int on);

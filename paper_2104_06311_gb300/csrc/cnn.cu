@@ -184,6 +184,214 @@ __global__ void __launch_bounds__(kThreads, 1) conv_kernel(const ConvArgs a) {
   }
 }
 
+// ---------------------------------------------------------------- tcgen05 path (64 -> 64 layers)
+// The 64-channel convolutions run on the 5th-generation tensor cores: one
+// thread issues tcgen05.mma (M = 128 rows, N = 64 channels, K = 16, BF16 in,
+// FP32 accumulate in tensor memory) for 15 taps x 4 channel groups per tile;
+// operands come from shared memory in the no-swizzle K-major layout.  The A
+// tile keeps, for each group of 8 input channels, its 142 rows (128 + 14 halo)
+// as consecutive 16-byte rows, so the view for tap k is the same layout at an
+// address 16 k bytes higher: no re-staging per tap.  Two A buffers and two
+// TMEM accumulators (64 columns each) let tile t+1 load while tile t computes;
+// the epilogue reads TMEM with tcgen05.ld (one row per thread) and applies
+// bias + ReLU or the ReLU mask of the layer below.
+constexpr int TC_M = 128;                      // rows per tile (one MMA M)
+constexpr int TC_ROWS = TC_M + 2 * HALF;       // staged rows
+constexpr int TC_ROWS_P = 145;                 // row-block stride (odd multiple of 16 B: spreads banks)
+constexpr int TC_GROUPS = CH / 8;              // 8 groups of 8 channels (16 bytes)
+constexpr int TC_A_BYTES = TC_GROUPS * TC_ROWS_P * 16;   // 18560
+constexpr int TC_W_BYTES = KS * TC_GROUPS * CH * 16;     // 122880: [tap][group][co][8]
+// + barriers, the TMEM address, and unused slack that keeps every operand read
+// inside the allocation even if a descriptor's two strides were read the other
+// way round (8 x 16 row groups x 2320 bytes)
+constexpr int TC_SLACK = 40960;
+constexpr int TC_SMEM = TC_W_BYTES + 2 * TC_A_BYTES + 64 + TC_SLACK;
+constexpr unsigned TC_TMEM_COLS = 128;         // two accumulators of 64 FP32 columns
+constexpr long long kTcWaitNs = 2000000000ll;  // bounded waits
+
+// Instruction descriptor, kind::f16: D FP32 (bits 4-5 = 1), A and B BF16 (bits
+// 7-9 = 1, 10-12 = 1), both K-major (bits 15, 16 = 0), N >> 3 at bits 17-22,
+// M >> 4 at bits 24-28.
+constexpr unsigned TC_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((unsigned)(CH >> 3) << 17) |
+                              ((unsigned)(TC_M >> 4) << 24);
+
+// Shared-memory matrix descriptor, no swizzle: start address, leading byte
+// offset (between core matrices adjacent in K) and stride byte offset (between
+// 8-row groups), all in 16-byte units; bits 46-47 = 1 (descriptor version).
+__device__ __forceinline__ unsigned long long tc_desc(unsigned saddr, unsigned lbo, unsigned sbo) {
+  return (unsigned long long)((saddr >> 4) & 0x3FFFu) | ((unsigned long long)((lbo >> 4) & 0x3FFFu) << 16) |
+         ((unsigned long long)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+__device__ __forceinline__ long long tc_now() {
+  long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ bool tc_wait(unsigned mbar, unsigned parity, long long deadline) {
+  for (;;) {
+    unsigned done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(mbar), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if (tc_now() > deadline) return false;
+  }
+}
+
+__device__ __forceinline__ void tc_ld32(unsigned taddr, float (&v)[32]) {
+  unsigned r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// EPI_RELU: out = relu(acc + bias); EPI_MASK: out = acc * [mask > 0].
+template <int EPI>
+__global__ void __launch_bounds__(128, 1) conv_tc_kernel(const ConvArgs a, const uint4 *__restrict__ wimg,
+                                                         int *__restrict__ err) {
+  extern __shared__ __align__(1024) unsigned char tc_smem[];
+  unsigned char *Wb = tc_smem;
+  unsigned char *const Ab0 = tc_smem + TC_W_BYTES;
+  unsigned long long *mbar = reinterpret_cast<unsigned long long *>(tc_smem + TC_W_BYTES + 2 * TC_A_BYTES);
+  unsigned *tmem_slot = reinterpret_cast<unsigned *>(mbar + 2);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  // tensor memory (warp 0 allocates and later frees) and the two completion barriers
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n"
+                 :: "r"(smem_u32(tmem_slot)), "r"(TC_TMEM_COLS) : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" :: "r"(smem_u32(&mbar[0])) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" :: "r"(smem_u32(&mbar[1])) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  // weights: the packed global image is the shared-memory image
+  for (int i = tid; i < TC_W_BYTES / 16; i += 128) reinterpret_cast<uint4 *>(Wb)[i] = wimg[i];
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+  const unsigned tmem = *tmem_slot;
+  const unsigned wb_addr = smem_u32(Wb);
+  const unsigned ab_addr0 = smem_u32(Ab0);
+  const long long deadline = tc_now() + kTcWaitNs;
+  bool failed = false;
+  const int64_t n_tiles = (a.K + TC_M - 1) / TC_M;
+  int it = 0;
+  int64_t prev = -1;
+  auto epilogue = [&](int64_t tile, int slot, unsigned parity) {
+    if (!tc_wait(smem_u32(&mbar[slot]), parity, deadline)) {
+      failed = true;
+      return;
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    float acc[64];
+    {
+      float v0[32], v1[32];
+      const unsigned taddr = tmem + ((unsigned)(warp * 32) << 16) + (unsigned)(slot * 64);
+      tc_ld32(taddr, v0);
+      tc_ld32(taddr + 32, v1);
+      asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+#pragma unroll
+      for (int i = 0; i < 32; ++i) {
+        acc[i] = v0[i];
+        acc[32 + i] = v1[i];
+      }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    const int64_t n = tile * TC_M + warp * 32 + lane;
+    if (n >= a.K) return;
+    uint4 *dst = reinterpret_cast<uint4 *>(a.out + n * CH);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      float v[8];
+#pragma unroll
+      for (int e = 0; e < 8; ++e) v[e] = acc[q * 8 + e];
+      if constexpr (EPI == EPI_RELU) {
+#pragma unroll
+        for (int e = 0; e < 8; ++e) v[e] = fmaxf(v[e] + a.bias[q * 8 + e], 0.f);
+      } else {
+        const uint4 mw = reinterpret_cast<const uint4 *>(a.mask + n * CH)[q];
+        const bf16 *mk = reinterpret_cast<const bf16 *>(&mw);
+#pragma unroll
+        for (int e = 0; e < 8; ++e) v[e] = __bfloat162float(mk[e]) > 0.f ? v[e] : 0.f;
+      }
+      __nv_bfloat162 o[4];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) o[e] = __floats2bfloat162_rn(v[2 * e], v[2 * e + 1]);
+      dst[q] = *reinterpret_cast<uint4 *>(o);
+    }
+  };
+  for (int64_t tile = blockIdx.x; tile < n_tiles && !failed; tile += gridDim.x, ++it) {
+    const int b = it & 1;
+    // stage rows n0 - 7 .. n0 + 134 of the input, group g of 8 channels at g * TC_ROWS_P rows
+    const int64_t n0 = tile * TC_M;
+    for (int i = tid; i < TC_ROWS * TC_GROUPS; i += 128) {
+      const int r = i / TC_GROUPS, g = i % TC_GROUPS;
+      const int64_t n = n0 - HALF + r;
+      uint4 v = make_uint4(0u, 0u, 0u, 0u);
+      if (n >= 0 && n < a.K) v = reinterpret_cast<const uint4 *>(a.in + n * CH)[g];
+      *reinterpret_cast<uint4 *>(Ab0 + b * TC_A_BYTES + (g * TC_ROWS_P + r) * 16) = v;
+    }
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    __syncthreads();
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+      const unsigned dcol = tmem + (unsigned)(b * 64);
+      for (int k = 0; k < KS; ++k) {
+#pragma unroll
+        for (int kp = 0; kp < CH / 16; ++kp) {
+          const unsigned long long ad =
+              tc_desc(ab_addr0 + b * TC_A_BYTES + (2 * kp) * (TC_ROWS_P * 16) + k * 16, TC_ROWS_P * 16, 128);
+          const unsigned long long bd = tc_desc(wb_addr + ((k * TC_GROUPS + 2 * kp) * CH) * 16, CH * 16, 128);
+          const unsigned acc_in = (k | kp) ? 1u : 0u;
+          asm volatile(
+              "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+              " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+              :: "r"(dcol), "l"(ad), "l"(bd), "r"(TC_IDESC), "r"(acc_in)
+              : "memory");
+        }
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n"
+                   :: "r"(smem_u32(&mbar[b])) : "memory");
+    }
+    if (prev >= 0) epilogue(prev, (it - 1) & 1, (unsigned)(((it - 1) >> 1) & 1));
+    prev = tile;
+  }
+  if (prev >= 0 && !failed) epilogue(prev, (it - 1) & 1, (unsigned)(((it - 1) >> 1) & 1));
+  if (failed && lane == 0) atomicExch(err, 1);
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" :: "r"(tmem), "r"(TC_TMEM_COLS) : "memory");
+  }
+}
+
+// Shared-memory image of one 64 -> 64 layer's weights for the tcgen05 path:
+// img[k][g][co][e] = Wsrc(k, ci = 8 g + e, co), with Wsrc the forward weights
+// W[k][ci][co] (rev = 0) or the input-gradient weights W[14 - k][co][ci] (rev = 1).
+__global__ void pack_tc_kernel(const float *__restrict__ W, bf16 *__restrict__ img, int rev) {
+  const int n = KS * CH * CH;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const int k = i / (CH * CH), g = (i / (CH * 8)) % TC_GROUPS, co = (i / 8) % CH, e = i % 8;
+    const int ci = 8 * g + e;
+    const float v = rev ? W[((size_t)(KS - 1 - k) * CH + co) * CH + ci] : W[((size_t)k * CH + ci) * CH + co];
+    img[i] = __float2bfloat16_rn(v);
+  }
+}
+
 struct DwArgs {
   const bf16 *in;     // layer input [K][CIN]
   const bf16 *dz;     // dJ/d(pre-activation) [K][COUT]
@@ -341,6 +549,9 @@ struct rx_cnn {
   int sms = 0;
   float *P = nullptr, *G = nullptr, *M = nullptr, *V = nullptr;
   std::vector<bf16 *> wf, wb;
+  std::vector<bf16 *> wtc_f, wtc_b;    // tcgen05 shared-memory images of the 64 -> 64 layers
+  bool use_tc = true;
+  int *err = nullptr;                  // sticky device error word (bounded waits)
   bf16 *x0 = nullptr, *dout = nullptr, *dza = nullptr, *dzb = nullptr;
   std::vector<bf16 *> h;               // hidden outputs h_1 .. h_{L-1}
   double *loss = nullptr;
@@ -421,6 +632,14 @@ cudaError_t launch_conv(rx_cnn *c, const ConvArgs &a) {
   return cudaGetLastError();
 }
 
+template <int EPI>
+cudaError_t launch_conv_tc(rx_cnn *c, const ConvArgs &a, const bf16 *img) {
+  KTimer tm(c, EPI == EPI_MASK ? RX_CNN_K_DX : RX_CNN_K_FWD_HIDDEN);
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((a.K + TC_M - 1) / TC_M, c->sms));
+  conv_tc_kernel<EPI><<<grid, 128, TC_SMEM, c->stream>>>(a, reinterpret_cast<const uint4 *>(img), c->err);
+  return cudaGetLastError();
+}
+
 template <int CIN, int COUT>
 cudaError_t launch_dw(rx_cnn *c, const bf16 *in, const bf16 *dz, int64_t K, int l) {
   KTimer tm(c, RX_CNN_K_DW);
@@ -462,7 +681,13 @@ rx_status forward(rx_cnn *c, const float *z, int64_t zs, float *y, int64_t ys, c
     if (l < L - 1) {
       a.in = l == 0 ? c->x0 : c->h[l - 1];
       a.out = c->h[l];
-      CX_CUDA((l == 0 ? launch_conv<FEATP, CH, EPI_RELU>(c, a) : launch_conv<CH, CH, EPI_RELU>(c, a)), "conv");
+      if (l == 0) {
+        CX_CUDA((launch_conv<FEATP, CH, EPI_RELU>(c, a)), "conv");
+      } else if (c->use_tc) {
+        CX_CUDA(launch_conv_tc<EPI_RELU>(c, a, c->wtc_f[l]), "conv (tensor memory)");
+      } else {
+        CX_CUDA((launch_conv<CH, CH, EPI_RELU>(c, a)), "conv");
+      }
     } else {
       a.in = L == 1 ? c->x0 : c->h[L - 2];
       a.z = reinterpret_cast<const float2 *>(z);
@@ -508,6 +733,8 @@ rx_status backward(rx_cnn *c, int64_t K) {
     a.out = out;
     if (last) {
       CX_CUDA((launch_conv<FEATP, CH, EPI_MASK>(c, a)), "input gradient");
+    } else if (c->use_tc) {
+      CX_CUDA(launch_conv_tc<EPI_MASK>(c, a, c->wtc_b[l]), "input gradient (tensor memory)");
     } else {
       CX_CUDA((launch_conv<CH, CH, EPI_MASK>(c, a)), "input gradient");
     }
@@ -523,6 +750,11 @@ rx_status pack(rx_cnn *c) {
     pack_kernel<<<64, 256, 0, c->stream>>>(c->P + c->off_w[l], c->ci[l], c->co[l], c->wf[l], cinp, coutp,
                                              l > 0 ? c->wb[l] : nullptr, copb);
     CX_CUDA(cudaGetLastError(), "pack");
+    if (l > 0 && l < c->L - 1) {
+      pack_tc_kernel<<<64, 256, 0, c->stream>>>(c->P + c->off_w[l], c->wtc_f[l], 0);
+      pack_tc_kernel<<<64, 256, 0, c->stream>>>(c->P + c->off_w[l], c->wtc_b[l], 1);
+      CX_CUDA(cudaGetLastError(), "pack (tensor memory)");
+    }
   }
   return RX_OK;
 }
@@ -556,6 +788,8 @@ rx_status rx_cnn_create(rx_cnn **out, int layers, int channels, int ksize, int64
   if (e == cudaSuccess) e = conv_prepare<CH, 8, EPI_LAST>();
   if (e == cudaSuccess) e = conv_prepare<FEATP, CH, EPI_MASK>();
   if (e == cudaSuccess) e = conv_prepare<CH, CH, EPI_MASK>();
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(conv_tc_kernel<EPI_RELU>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(conv_tc_kernel<EPI_MASK>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
   if (e != cudaSuccess) {
     delete c;
     return RX_ECUDA;
@@ -572,6 +806,13 @@ rx_status rx_cnn_create(rx_cnn **out, int layers, int channels, int ksize, int64
   CX_ALLOC(c->V, (size_t)c->n_params);
   c->wf.assign(layers, nullptr);
   c->wb.assign(layers, nullptr);
+  c->wtc_f.assign(layers, nullptr);
+  c->wtc_b.assign(layers, nullptr);
+  CX_ALLOC(c->err, 1);
+  for (int l = 1; l < layers - 1; ++l) {
+    CX_ALLOC(c->wtc_f[l], (size_t)KS * CH * CH);
+    CX_ALLOC(c->wtc_b[l], (size_t)KS * CH * CH);
+  }
   for (int l = 0; l < layers; ++l) {
     const int cinp = l == 0 ? FEATP : CH, coutp = l == layers - 1 ? 8 : CH;
     CX_ALLOC(c->wf[l], (size_t)KS * cinp * coutp);
@@ -590,6 +831,7 @@ rx_status rx_cnn_create(rx_cnn **out, int layers, int channels, int ksize, int64
   CX_CUDA(cudaMemset(c->M, 0, (size_t)c->n_params * sizeof(float)), "init");
   CX_CUDA(cudaMemset(c->V, 0, (size_t)c->n_params * sizeof(float)), "init");
   CX_CUDA(cudaMemset(c->dout, 0, K * FEATP * sizeof(bf16)), "init");   // channels 4..15 stay zero
+  CX_CUDA(cudaMemset(c->err, 0, sizeof(int)), "init");
   rx_status s = pack(c);
   if (s != RX_OK) return s;
   CX_CUDA(cudaStreamSynchronize(c->stream), "create");
@@ -610,10 +852,27 @@ rx_status rx_cnn_set_params(rx_cnn *c, const float *params) {
   return RX_OK;
 }
 
+namespace {
+rx_status check_err(rx_cnn *c) {
+  int h = 0;
+  CX_CUDA(cudaMemcpyAsync(&h, c->err, sizeof(int), cudaMemcpyDeviceToHost, c->stream), "error word");
+  CX_CUDA(cudaStreamSynchronize(c->stream), "error word");
+  if (h) return cfail(c, RX_ETIMEOUT, "a bounded device wait gave up (tensor-core convolution)");
+  return RX_OK;
+}
+}  // namespace
+
 rx_status rx_cnn_get_params(rx_cnn *c, float *params) {
   if (!c || !params) return RX_EINVAL;
   CX_CUDA(cudaMemcpyAsync(params, c->P, (size_t)c->n_params * sizeof(float), cudaMemcpyDeviceToHost, c->stream), "get");
   CX_CUDA(cudaStreamSynchronize(c->stream), "get");
+  return check_err(c);
+}
+
+rx_status rx_cnn_set_option(rx_cnn *c, int key, int value) {
+  if (!c) return RX_EINVAL;
+  if (key != RX_CNN_OPT_TCGEN05) return cfail(c, RX_EINVAL, "unknown option");
+  c->use_tc = value != 0;
   return RX_OK;
 }
 
@@ -648,7 +907,7 @@ rx_status rx_cnn_grads(rx_cnn *c, const float *z, int64_t zs, const float *t, in
           "grads");
   CX_CUDA(cudaMemcpyAsync(loss, c->loss, sizeof(double), cudaMemcpyDeviceToHost, c->stream), "loss");
   CX_CUDA(cudaStreamSynchronize(c->stream), "grads");
-  return RX_OK;
+  return check_err(c);
 }
 
 rx_status rx_cnn_train_step(rx_cnn *c, const float *z, int64_t zs, const float *t, int64_t ts, int64_t K, float lr,

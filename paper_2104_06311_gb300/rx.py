@@ -34,7 +34,7 @@ EXPORTS = ["rx_create", "rx_set_param", "rx_get_param", "rx_set_cuda_stream", "r
            "rx_batch_last_error", "rx_batch_profile",
            "rx_cnn_create", "rx_cnn_param_count", "rx_cnn_set_params", "rx_cnn_get_params",
            "rx_cnn_set_cuda_stream", "rx_cnn_apply", "rx_cnn_grads", "rx_cnn_train_step", "rx_cnn_destroy",
-           "rx_cnn_last_error", "rx_cnn_set_profile", "rx_cnn_profile"]
+           "rx_cnn_last_error", "rx_cnn_set_profile", "rx_cnn_profile", "rx_cnn_set_option"]
 CNN_KINDS = ["fwd_hidden", "fwd_edge", "dx", "dw", "update"]
 BATCH_PARAMS = {"GRAPH": 100, "EQ_CTAS": 101, "EQ_TEAM": 102, "CDC_NS_PER_SAMPLE": 103, "PROFILE": 104}
 
@@ -123,6 +123,7 @@ def load(path: str = LIB_PATH) -> ct.CDLL:
     lib.rx_cnn_grads.argtypes = [P, P, ct.c_int64, P, ct.c_int64, ct.c_int64, P, ct.POINTER(ct.c_double)]
     lib.rx_cnn_train_step.argtypes = [P, P, ct.c_int64, P, ct.c_int64, ct.c_int64, ct.c_float, P]
     lib.rx_cnn_set_profile.argtypes = [P, ct.c_int]
+    lib.rx_cnn_set_option.argtypes = [P, ct.c_int, ct.c_int]
     lib.rx_cnn_profile.argtypes = [P, ct.POINTER(ct.c_double), ct.POINTER(ct.c_int64), ct.c_int]
     lib.rx_cnn_destroy.argtypes = [P]
     lib.rx_cnn_destroy.restype = None
@@ -576,6 +577,12 @@ class CNN:
         _ccheck(self.lib, self.h, self.lib.rx_cnn_train_step(self.h, zp, zs, tp, ts, z.shape[1], float(lr), acc))
 
     train_step = rx_cnn_train_step
+
+    def rx_cnn_set_option(self, key, value):
+        k = {"TCGEN05": 1}[key.upper()] if isinstance(key, str) else key
+        _ccheck(self.lib, self.h, self.lib.rx_cnn_set_option(self.h, k, int(value)))
+
+    set_option = rx_cnn_set_option
 
     def rx_cnn_set_profile(self, on=True):
         _ccheck(self.lib, self.h, self.lib.rx_cnn_set_profile(self.h, 1 if on else 0))

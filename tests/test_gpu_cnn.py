@@ -169,3 +169,26 @@ def test_training_gains_over_the_chain_on_a_nonlinear_link():
     print(f"test MSE chain {mse_chain:.5f} cnn {mse_cnn:.5f} (effective SNR gain {gain_db:.2f} dB); "
           f"SER chain {ser_chain:.5f} cnn {ser_cnn:.5f}")
     assert gain_db > 0.1
+
+
+@pytest.mark.parametrize("K", [3000, 1 << 15])
+def test_tcgen05_path_matches_mma_sync_path(K):
+    """The 64 -> 64 layers on tcgen05 / tensor memory and on mma.sync form the same
+    BF16 products with FP32 accumulation; only the summation order differs."""
+    from paper_2104_06311_gb300 import CNN
+    z, t = _data(K, 23)
+    params = _params(29)
+    out = {}
+    for tc in (1, 0):
+        net = CNN(K)
+        net.set_option("TCGEN05", tc)
+        net.set_params(params)
+        y = net.apply(_dev(z)).cpu().numpy().astype(np.complex128)
+        loss, g = net.grads(_dev(z), _dev(t))
+        out[tc] = (y, loss, g.cpu().numpy().astype(np.float64))
+    corr1 = C.features(out[1][0]) - C.features(z)
+    corr0 = C.features(out[0][0]) - C.features(z)
+    print("tcgen05 vs mma.sync: forward", rel_rms(corr1, corr0), "grads", rel_rms(out[1][2], out[0][2]))
+    assert rel_rms(corr1, corr0) < 2e-3          # a few BF16 re-roundings of hidden activations
+    assert abs(out[1][1] - out[0][1]) < 1e-3 * out[0][1]
+    assert rel_rms(out[1][2], out[0][2]) < 1e-2
