@@ -53,6 +53,7 @@ def parse():
                     help="c2: the 10,000 km single stream (default); c4: the 64-channel batched form; "
                          "c5: the chain plus the learned post-equaliser on a Kerr-nonlinear link")
     ap.add_argument("--channels", type=int, default=64, help="c4: number of channels")
+    ap.add_argument("--train-symbols", type=int, default=1 << 14, help="c5: symbols per training sequence")
     return ap.parse_args()
 
 
@@ -355,7 +356,7 @@ def bench_learned(args, rank, world, local):
         zc = out["sym"][:, k0:k1].contiguous()
         t = L.align_rotation(zc.cpu().numpy(), t).astype(np.complex64)
         sets[name] = dict(x=x, rx=rx, z=zc, t=torch.from_numpy(t).cuda(), ber=e / max(nb, 1), K=K)
-    B, BI = 1 << 14, 1 << 20          # training sequences / inference sequences (symbols)
+    B, BI = args.train_symbols, 1 << 20   # training sequences / inference sequences (symbols)
     tr, te = sets["train"], sets["test"]
     n_tr = tr["z"].shape[1] // B * B
     net = CNN(BI, stream=stream)
