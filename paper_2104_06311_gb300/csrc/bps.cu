@@ -79,32 +79,53 @@ __global__ void __launch_bounds__(kBpsWarps * 32) bps_pass1(BpsLaunch L) {
   int prev = 0, R = 0;
   float s2 = 0.f;
   const int nt = (int)(b - start);
-  for (int t = 0; t < nt; ++t) {                 // symbol k = start + t
-    if (t > 0) {
-      const float dn = dist(t + 2 * Nb);         // entering symbol k + Nb
-      D += dn - ring[s_out * 32 + lane];         // leaving symbol k - Nb - 1
-      ring[s_out * 32 + lane] = dn;
-      s_out = (s_out + 1 == M) ? 0 : s_out + 1;
-    }
-    if ((t & 31) == 0) {                         // exact re-sum bounds the sliding drift
-      float e = 0.f;
-      for (int s = 0; s < M; ++s) e += ring[s * 32 + lane];
-      D = e;
-    }
-    const unsigned key = __float_as_uint(fmaxf(D, 0.f));
-    const unsigned mn = __reduce_min_sync(0xffffffffu, key);
-    const int bs = __ffs(__ballot_sync(0xffffffffu, key == mn)) - 1;
-    const int64_t k = start + t;
-    if (k >= a) {
-      if (k > 0) R += unwrap_step(prev, bs);
-      if (NEED_S2) {
-        int sk = s_out + Nb;                     // slot of symbol k
-        if (sk >= M) sk -= M;
-        s2 += __shfl_sync(0xffffffffu, ring[sk * 32 + lane], bs);
+  // kGroup symbols at a time: first their window sums (a sliding chain per lane),
+  // then their independent warp argmins back to back, then the unwrap in order
+  constexpr int kGroup = 8;
+  for (int t0 = 0; t0 < nt; t0 += kGroup) {
+    const int cnt = min(kGroup, nt - t0);
+    float Dv[kGroup];
+#pragma unroll
+    for (int u = 0; u < kGroup; ++u) {
+      if (u < cnt) {
+        const int t = t0 + u;                    // symbol k = start + t
+        if (t > 0) {
+          const float dn = dist(t + 2 * Nb);     // entering symbol k + Nb
+          D += dn - ring[s_out * 32 + lane];     // leaving symbol k - Nb - 1
+          ring[s_out * 32 + lane] = dn;
+          s_out = (s_out + 1 == M) ? 0 : s_out + 1;
+        }
+        if ((t & 31) == 0) {                     // exact re-sum every 32 bounds the sliding drift
+          float e = 0.f;
+          for (int q = 0; q < M; ++q) e += ring[q * 32 + lane];
+          D = e;
+        }
+        Dv[u] = D;
       }
-      if (lane == 0) bq[k - a] = (int8_t)bs;
     }
-    prev = bs;
+    int bsv[kGroup];
+#pragma unroll
+    for (int u = 0; u < kGroup; ++u) {
+      if (u < cnt) {
+        const unsigned key = __float_as_uint(fmaxf(Dv[u], 0.f));
+        const unsigned mn = __reduce_min_sync(0xffffffffu, key);
+        bsv[u] = __ffs(__ballot_sync(0xffffffffu, key == mn)) - 1;
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kGroup; ++u) {
+      if (u < cnt) {
+        const int t = t0 + u;
+        const int bs = bsv[u];
+        const int64_t k = start + t;
+        if (k >= a) {
+          if (k > 0) R += unwrap_step(prev, bs);
+          if (NEED_S2) s2 += __shfl_sync(0xffffffffu, dist(t + Nb), bs);   // d of symbol k at angle bs
+          if (lane == 0) bq[k - a] = (int8_t)bs;
+        }
+        prev = bs;
+      }
+    }
   }
   __syncwarp();
   int8_t *bh = L.bhat + (int64_t)p * L.bh_stride - L.bh_base;
