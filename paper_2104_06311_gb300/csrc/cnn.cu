@@ -16,6 +16,7 @@
 // the symbols as the reduction dimension: CTAs own (symbol chunk, 3 taps),
 // read both operands transposed by ldmatrix.trans, and add their partial
 // sums into the FP32 gradient with atomics.
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <math.h>
 #include <string.h>
@@ -185,27 +186,32 @@ __global__ void __launch_bounds__(kThreads, 1) conv_kernel(const ConvArgs a) {
 }
 
 // ---------------------------------------------------------------- tcgen05 path (64 -> 64 layers)
-// The 64-channel convolutions run on the 5th-generation tensor cores: one
-// thread issues tcgen05.mma (M = 128 rows, N = 64 channels, K = 16, BF16 in,
-// FP32 accumulate in tensor memory) for 15 taps x 4 channel groups per tile;
-// operands come from shared memory in the no-swizzle K-major layout.  The A
-// tile keeps, for each group of 8 input channels, its 142 rows (128 + 14 halo)
-// as consecutive 16-byte rows, so the view for tap k is the same layout at an
-// address 16 k bytes higher: no re-staging per tap.  Two A buffers and two
-// TMEM accumulators (64 columns each) let tile t+1 load while tile t computes;
-// the epilogue reads TMEM with tcgen05.ld (one row per thread) and applies
-// bias + ReLU or the ReLU mask of the layer below.
+// The 64-channel convolutions run on the 5th-generation tensor cores.  One
+// thread is the producer and the MMA issuer: TMA (cp.async.bulk.tensor, 2-D
+// tensor map over the [K][64] BF16 activations) brings each tile's 142 input
+// rows (128 outputs + 14 halo rows, zero-filled beyond the sequence) into one
+// of three shared-memory stages, one group of 8 channels per box; a 1-D bulk
+// copy brings the packed weights once per CTA.  tcgen05.mma (M = 128 rows,
+// N = 64 channels, K = 16, BF16 in, FP32 accumulate in tensor memory) runs
+// 15 taps x 4 channel groups per tile from shared-memory descriptors in the
+// no-swizzle K-major layout: the box of a channel group is 142 rows of 16
+// bytes, so the operand for tap k is the same layout 16 k bytes further on
+// (no re-staging per tap).  Two TMEM accumulators let all four warps read
+// tile t back (tcgen05.ld, one row per thread) and apply bias + ReLU or the
+// ReLU mask of the layer below while tile t+1 computes and t+2 loads.
 constexpr int TC_M = 128;                      // rows per tile (one MMA M)
-constexpr int TC_ROWS = TC_M + 2 * HALF;       // staged rows
-constexpr int TC_ROWS_P = 145;                 // row-block stride (odd multiple of 16 B: spreads banks)
+constexpr int TC_ROWS = TC_M + 2 * HALF;       // 142 rows per TMA box
+constexpr int TC_ROWS_P = 144;                 // group stride in rows (2304 B: 128-byte aligned)
 constexpr int TC_GROUPS = CH / 8;              // 8 groups of 8 channels (16 bytes)
-constexpr int TC_A_BYTES = TC_GROUPS * TC_ROWS_P * 16;   // 18560
+constexpr int TC_STAGES = 3;
+constexpr int TC_A_BYTES = TC_GROUPS * TC_ROWS_P * 16;   // 18432 per stage
+constexpr int TC_A_TX = TC_GROUPS * TC_ROWS * 16;        // 18176 bytes landed per stage
 constexpr int TC_W_BYTES = KS * TC_GROUPS * CH * 16;     // 122880: [tap][group][co][8]
 // + barriers, the TMEM address, and unused slack that keeps every operand read
 // inside the allocation even if a descriptor's two strides were read the other
-// way round (8 x 16 row groups x 2320 bytes)
-constexpr int TC_SLACK = 40960;
-constexpr int TC_SMEM = TC_W_BYTES + 2 * TC_A_BYTES + 64 + TC_SLACK;
+// way round (16 row groups x 2304 bytes past the last stage)
+constexpr int TC_SLACK = 38912;
+constexpr int TC_SMEM = TC_W_BYTES + TC_STAGES * TC_A_BYTES + 128 + TC_SLACK;
 constexpr unsigned TC_TMEM_COLS = 128;         // two accumulators of 64 FP32 columns
 constexpr long long kTcWaitNs = 2000000000ll;  // bounded waits
 
@@ -242,6 +248,25 @@ __device__ __forceinline__ bool tc_wait(unsigned mbar, unsigned parity, long lon
   }
 }
 
+__device__ __forceinline__ void tc_expect(unsigned mbar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" :: "r"(mbar), "r"(bytes) : "memory");
+}
+
+// A tile: 8 boxes of (8 channels x 142 rows) at x = 8 g, y = n0 - 7 (negative or
+// past-the-end rows read as zero); x * 2 bytes is a multiple of 16.
+__device__ __forceinline__ void tc_load_tile(const CUtensorMap *tmap, unsigned stage_addr, int64_t n0, unsigned mbar) {
+  tc_expect(mbar, (unsigned)TC_A_TX);
+  const int y = (int)(n0 - HALF);
+#pragma unroll
+  for (int g = 0; g < TC_GROUPS; ++g) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];\n"
+        :: "r"(stage_addr + (unsigned)(g * TC_ROWS_P * 16)), "l"(reinterpret_cast<unsigned long long>(tmap)),
+           "r"(g * 8), "r"(y), "r"(mbar)
+        : "memory");
+  }
+}
+
 __device__ __forceinline__ void tc_ld32(unsigned taddr, float (&v)[32]) {
   unsigned r[32];
   asm volatile(
@@ -258,41 +283,53 @@ __device__ __forceinline__ void tc_ld32(unsigned taddr, float (&v)[32]) {
 
 // EPI_RELU: out = relu(acc + bias); EPI_MASK: out = acc * [mask > 0].
 template <int EPI>
-__global__ void __launch_bounds__(128, 1) conv_tc_kernel(const ConvArgs a, const uint4 *__restrict__ wimg,
-                                                         int *__restrict__ err) {
+__global__ void __launch_bounds__(128, 1) conv_tc_kernel(const __grid_constant__ CUtensorMap tmap, const ConvArgs a,
+                                                         const void *__restrict__ wimg, int *__restrict__ err) {
   extern __shared__ __align__(1024) unsigned char tc_smem[];
-  unsigned char *Wb = tc_smem;
+  unsigned char *const Wb = tc_smem;
   unsigned char *const Ab0 = tc_smem + TC_W_BYTES;
-  unsigned long long *mbar = reinterpret_cast<unsigned long long *>(tc_smem + TC_W_BYTES + 2 * TC_A_BYTES);
-  unsigned *tmem_slot = reinterpret_cast<unsigned *>(mbar + 2);
+  // barriers: [0] weights, [1..3] stage full, [4..5] accumulator ready
+  unsigned long long *bars = reinterpret_cast<unsigned long long *>(tc_smem + TC_W_BYTES + TC_STAGES * TC_A_BYTES);
+  unsigned *tmem_slot = reinterpret_cast<unsigned *>(bars + 8);
+  volatile int *fail_flag = reinterpret_cast<volatile int *>(bars + 9);   // CTA-uniform failure
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  // tensor memory (warp 0 allocates and later frees) and the two completion barriers
+  const unsigned bar_w = smem_u32(&bars[0]);
+  auto bar_full = [&](int s) { return smem_u32(&bars[1 + s]); };
+  auto bar_mma = [&](int s) { return smem_u32(&bars[4 + s]); };
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n"
                  :: "r"(smem_u32(tmem_slot)), "r"(TC_TMEM_COLS) : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
   }
   if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" :: "r"(smem_u32(&mbar[0])) : "memory");
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" :: "r"(smem_u32(&mbar[1])) : "memory");
+    for (int i = 0; i < 6; ++i) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" :: "r"(smem_u32(&bars[i])) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    *fail_flag = 0;
   }
-  // weights: the packed global image is the shared-memory image
-  for (int i = tid; i < TC_W_BYTES / 16; i += 128) reinterpret_cast<uint4 *>(Wb)[i] = wimg[i];
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
   const unsigned tmem = *tmem_slot;
-  const unsigned wb_addr = smem_u32(Wb);
-  const unsigned ab_addr0 = smem_u32(Ab0);
+  const unsigned wb_addr = smem_u32(Wb), ab_addr0 = smem_u32(Ab0);
   const long long deadline = tc_now() + kTcWaitNs;
-  bool failed = false;
   const int64_t n_tiles = (a.K + TC_M - 1) / TC_M;
-  int it = 0;
-  int64_t prev = -1;
-  auto epilogue = [&](int64_t tile, int slot, unsigned parity) {
-    if (!tc_wait(smem_u32(&mbar[slot]), parity, deadline)) {
-      failed = true;
+  const int64_t step = gridDim.x;
+  if (tid == 0) {
+    asm volatile("prefetch.tensormap [%0];\n" :: "l"(reinterpret_cast<unsigned long long>(&tmap)) : "memory");
+    tc_expect(bar_w, (unsigned)TC_W_BYTES);
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n"
+                 :: "r"(wb_addr), "l"(reinterpret_cast<unsigned long long>(wimg)), "r"((unsigned)TC_W_BYTES),
+                    "r"(bar_w)
+                 : "memory");
+    for (int s = 0; s < 2; ++s) {
+      const int64_t tile = blockIdx.x + s * step;
+      if (tile < n_tiles) tc_load_tile(&tmap, ab_addr0 + s * TC_A_BYTES, tile * TC_M, bar_full(s));
+    }
+  }
+  auto epilogue = [&](int64_t tile, int it) {
+    const int slot = it & 1;
+    if (!tc_wait(bar_mma(slot), (unsigned)((it >> 1) & 1), deadline)) {
+      *fail_flag = 1;
       return;
     }
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
@@ -309,7 +346,6 @@ __global__ void __launch_bounds__(128, 1) conv_tc_kernel(const ConvArgs a, const
         acc[32 + i] = v1[i];
       }
     }
-    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
     const int64_t n = tile * TC_M + warp * 32 + lane;
     if (n >= a.K) return;
     uint4 *dst = reinterpret_cast<uint4 *>(a.out + n * CH);
@@ -333,44 +369,53 @@ __global__ void __launch_bounds__(128, 1) conv_tc_kernel(const ConvArgs a, const
       dst[q] = *reinterpret_cast<uint4 *>(o);
     }
   };
-  for (int64_t tile = blockIdx.x; tile < n_tiles && !failed; tile += gridDim.x, ++it) {
-    const int b = it & 1;
-    // stage rows n0 - 7 .. n0 + 134 of the input, group g of 8 channels at g * TC_ROWS_P rows
-    const int64_t n0 = tile * TC_M;
-    for (int i = tid; i < TC_ROWS * TC_GROUPS; i += 128) {
-      const int r = i / TC_GROUPS, g = i % TC_GROUPS;
-      const int64_t n = n0 - HALF + r;
-      uint4 v = make_uint4(0u, 0u, 0u, 0u);
-      if (n >= 0 && n < a.K) v = reinterpret_cast<const uint4 *>(a.in + n * CH)[g];
-      *reinterpret_cast<uint4 *>(Ab0 + b * TC_A_BYTES + (g * TC_ROWS_P + r) * 16) = v;
-    }
-    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+  int it = 0;
+  for (int64_t tile = blockIdx.x; tile < n_tiles; tile += step, ++it) {
+    // every read of the accumulator this tile overwrites (tile it - 2) is done
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
     __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    if (*fail_flag) break;                       // uniform: read after the barrier
     if (tid == 0) {
-      asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-      const unsigned dcol = tmem + (unsigned)(b * 64);
-      for (int k = 0; k < KS; ++k) {
+      const int s = it % TC_STAGES;
+      bool ok = true;
+      if (it == 0) ok = tc_wait(bar_w, 0u, deadline);
+      ok = ok && tc_wait(bar_full(s), (unsigned)((it / TC_STAGES) & 1), deadline);
+      if (ok) {
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+        const unsigned dcol = tmem + (unsigned)((it & 1) * 64);
+        const unsigned abase = ab_addr0 + s * TC_A_BYTES;
+        for (int k = 0; k < KS; ++k) {
 #pragma unroll
-        for (int kp = 0; kp < CH / 16; ++kp) {
-          const unsigned long long ad =
-              tc_desc(ab_addr0 + b * TC_A_BYTES + (2 * kp) * (TC_ROWS_P * 16) + k * 16, TC_ROWS_P * 16, 128);
-          const unsigned long long bd = tc_desc(wb_addr + ((k * TC_GROUPS + 2 * kp) * CH) * 16, CH * 16, 128);
-          const unsigned acc_in = (k | kp) ? 1u : 0u;
-          asm volatile(
-              "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-              " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
-              :: "r"(dcol), "l"(ad), "l"(bd), "r"(TC_IDESC), "r"(acc_in)
-              : "memory");
+          for (int kp = 0; kp < CH / 16; ++kp) {
+            const unsigned long long ad = tc_desc(abase + (2 * kp) * (TC_ROWS_P * 16) + k * 16, TC_ROWS_P * 16, 128);
+            const unsigned long long bd = tc_desc(wb_addr + ((k * TC_GROUPS + 2 * kp) * CH) * 16, CH * 16, 128);
+            const unsigned acc_in = (k | kp) ? 1u : 0u;
+            asm volatile(
+                "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+                :: "r"(dcol), "l"(ad), "l"(bd), "r"(TC_IDESC), "r"(acc_in)
+                : "memory");
+          }
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n"
+                     :: "r"(bar_mma(it & 1)) : "memory");
+        // the stage of tile it + 2 last held tile it - 1: free once its MMAs are done
+        const int64_t t2 = tile + 2 * step;
+        if (t2 < n_tiles) {
+          if (it >= 1) ok = tc_wait(bar_mma((it - 1) & 1), (unsigned)(((it - 1) >> 1) & 1), deadline);
+          if (ok) tc_load_tile(&tmap, ab_addr0 + ((it + 2) % TC_STAGES) * TC_A_BYTES, t2 * TC_M, bar_full((it + 2) % TC_STAGES));
         }
       }
-      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n"
-                   :: "r"(smem_u32(&mbar[b])) : "memory");
+      if (!ok) *fail_flag = 1;
     }
-    if (prev >= 0) epilogue(prev, (it - 1) & 1, (unsigned)(((it - 1) >> 1) & 1));
-    prev = tile;
+    __syncwarp();
+    if (it >= 1) epilogue(tile - step, it - 1);
   }
-  if (prev >= 0 && !failed) epilogue(prev, (it - 1) & 1, (unsigned)(((it - 1) >> 1) & 1));
-  if (failed && lane == 0) atomicExch(err, 1);
+  __syncthreads();
+  if (!*fail_flag && it >= 1) epilogue(blockIdx.x + (int64_t)(it - 1) * step, it - 1);
+  __syncthreads();
+  if (*fail_flag && tid == 0) atomicExch(err, 1);
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
   __syncthreads();
   if (warp == 0) {
@@ -632,11 +677,44 @@ cudaError_t launch_conv(rx_cnn *c, const ConvArgs &a) {
   return cudaGetLastError();
 }
 
+// cuTensorMapEncodeTiled from the driver, looked up once through the runtime.
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_tiled() {
+  static EncodeTiledFn fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+    else
+      cudaGetLastError();
+  }
+  return fn;
+}
+
 template <int EPI>
 cudaError_t launch_conv_tc(rx_cnn *c, const ConvArgs &a, const bf16 *img) {
   KTimer tm(c, EPI == EPI_MASK ? RX_CNN_K_DX : RX_CNN_K_FWD_HIDDEN);
+  EncodeTiledFn enc = encode_tiled();
+  if (!enc) return cudaErrorNotSupported;
+  // [K][64] BF16 rows: dim 0 = channels (contiguous), dim 1 = symbols (128-byte stride)
+  CUtensorMap tmap;
+  const cuuint64_t dims[2] = {(cuuint64_t)CH, (cuuint64_t)a.K};
+  const cuuint64_t strides[1] = {(cuuint64_t)CH * sizeof(bf16)};
+  const cuuint32_t box[2] = {8u, (cuuint32_t)TC_ROWS};
+  const cuuint32_t estr[2] = {1u, 1u};
+  if (enc(&tmap, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<bf16 *>(a.in), dims, strides, box, estr,
+          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    return cudaErrorInvalidValue;
   const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((a.K + TC_M - 1) / TC_M, c->sms));
-  conv_tc_kernel<EPI><<<grid, 128, TC_SMEM, c->stream>>>(a, reinterpret_cast<const uint4 *>(img), c->err);
+  conv_tc_kernel<EPI><<<grid, 128, TC_SMEM, c->stream>>>(tmap, a, img, c->err);
   return cudaGetLastError();
 }
 
