@@ -536,9 +536,21 @@ __global__ void features_kernel(const float2 *__restrict__ z, int64_t z_stride, 
   }
 }
 
-// Adam on the flat FP32 parameters (c1 = 1 - b1^s, c2 = 1 - b2^s).
-__global__ void adam_kernel(float *__restrict__ P, const float *__restrict__ G, float *__restrict__ M,
-                            float *__restrict__ V, int64_t n, float lr, float c1, float c2) {
+
+// Adam on every parameter with the packed BF16 copies of each updated weight
+// written in the same pass (one launch per training step).
+struct PackLayer {
+  long long off_w, off_b;
+  int ci, co, cinp, coutp, copb, tc;
+  bf16 *wf, *wb, *wtc_f, *wtc_b;
+};
+struct PackTable {
+  PackLayer l[8];
+  int L;
+};
+
+__global__ void adam_pack_kernel(const PackTable tab, float *__restrict__ P, const float *__restrict__ G,
+                                 float *__restrict__ M, float *__restrict__ V, int64_t n, float lr, float c1, float c2) {
   const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const float g = G[i];
@@ -546,7 +558,21 @@ __global__ void adam_kernel(float *__restrict__ P, const float *__restrict__ G, 
     const float v = b2 * V[i] + (1.f - b2) * g * g;
     M[i] = m;
     V[i] = v;
-    P[i] -= lr * (m / c1) / (sqrtf(v / c2) + eps);
+    const float w = P[i] - lr * (m / c1) / (sqrtf(v / c2) + eps);
+    P[i] = w;
+    int l = 0;
+    while (l + 1 < tab.L && i >= tab.l[l + 1].off_w) ++l;
+    const PackLayer &y = tab.l[l];
+    if (i >= y.off_b) continue;                  // a bias: read from P directly
+    const int r = (int)(i - y.off_w);
+    const int co = r % y.co, ci = (r / y.co) % y.ci, k = r / (y.co * y.ci);
+    const bf16 wv = __float2bfloat16_rn(w);
+    y.wf[((size_t)k * y.coutp + co) * y.cinp + ci] = wv;
+    if (y.wb) y.wb[((size_t)(KS - 1 - k) * y.ci + ci) * y.copb + co] = wv;
+    if (y.tc) {
+      y.wtc_f[(((size_t)k * TC_GROUPS + ci / 8) * CH + co) * 8 + ci % 8] = wv;
+      y.wtc_b[(((size_t)(KS - 1 - k) * TC_GROUPS + co / 8) * CH + ci) * 8 + co % 8] = wv;
+    }
   }
 }
 
@@ -1003,12 +1029,30 @@ rx_status rx_cnn_train_step(rx_cnn *c, const float *z, int64_t zs, const float *
   c->step += 1;
   const float c1 = (float)(1.0 - pow(0.9, (double)c->step));
   const float c2 = (float)(1.0 - pow(0.999, (double)c->step));
-  KTimer tm(c, RX_CNN_K_UPDATE);
-  adam_kernel<<<std::max(1, std::min(c->sms * 4, (int)((c->n_params + 255) / 256))), 256, 0, c->stream>>>(
-      c->P, c->G, c->M, c->V, c->n_params, lr, c1, c2);
-  CX_CUDA(cudaGetLastError(), "adam");
-  s = pack(c);
-  if (s != RX_OK) return s;
+  {
+    KTimer tm(c, RX_CNN_K_UPDATE);
+    PackTable tab;
+    memset(&tab, 0, sizeof(tab));
+    tab.L = c->L;
+    for (int l = 0; l < c->L; ++l) {
+      PackLayer &y = tab.l[l];
+      y.off_w = c->off_w[l];
+      y.off_b = c->off_b[l];
+      y.ci = c->ci[l];
+      y.co = c->co[l];
+      y.cinp = l == 0 ? FEATP : CH;
+      y.coutp = l == c->L - 1 ? 8 : CH;
+      y.copb = l == c->L - 1 ? FEATP : CH;
+      y.wf = c->wf[l];
+      y.wb = l > 0 ? c->wb[l] : nullptr;
+      y.tc = (l > 0 && l < c->L - 1) ? 1 : 0;
+      y.wtc_f = c->wtc_f[l];
+      y.wtc_b = c->wtc_b[l];
+    }
+    adam_pack_kernel<<<std::max(1, std::min(c->sms * 4, (int)((c->n_params + 255) / 256))), 256, 0, c->stream>>>(
+        tab, c->P, c->G, c->M, c->V, c->n_params, lr, c1, c2);
+    CX_CUDA(cudaGetLastError(), "adam");
+  }
   if (loss_acc) {
     add_kernel<<<1, 1, 0, c->stream>>>(loss_acc, c->loss);
     CX_CUDA(cudaGetLastError(), "loss");
