@@ -148,7 +148,9 @@ def cpu_oracle_run(g, n_samples):
 def reference_arm(args, rank, world):
     if rank != 0:
         return
-    lk, g = make_input(args.cpu_sample // 2)
+    # each step a bounded sample (2^19 sample-times, ~2 s of FP64 numpy) so that a
+    # default --steps 40 --warmup 3 run ends within a few minutes
+    lk, g = make_input(min(args.cpu_sample, 1 << 19) // 2)
     n = g.samples.shape[0]
     times = []
     for i in range(args.warmup + args.steps):
