@@ -1,0 +1,71 @@
+/*
+ * rx_kk.h -- Kramers-Kronig (self-coherent) receiver front end: the paper's own
+ * processing chain ahead of its adaptive equaliser (arXiv 2104.06311, Section
+ * "Experimental setup", processing-chain paragraph): real ADC samples of the
+ * detected intensity -> floating point -> square root and logarithm -> the
+ * optical phase from a Hilbert transform done by a pair of 1024-point 100 %
+ * overlap-save FFTs -> the field rebuilt from amplitude and phase and shifted
+ * to DC -> a static frequency-domain filter (another FFT/IFFT pair) that also
+ * downsamples from 4 to 2 samples per symbol.
+ *
+ * Readings (the paper gives the steps, not their constants): the Hilbert image
+ * has the response j sign(f) (signal side band below the carrier, minimum-phase
+ * field); amplitude sqrt(max(I, 1e-30)); the 100 % overlap-save is N = 1024
+ * with overlap N/2, samples outside the buffer count as zero log-amplitude;
+ * the static filter is the dispersion inverse exp(-j beta2 L w^2/2) times the
+ * RRC matched filter (the paper optimised its filter offline from lab data),
+ * in N = 1024 windows with overlap max(N/2, the textbook CD length); the
+ * decimation keeps the bins of |f| < fs/4 and applies a factor 1/2.  A buffer is
+ * processed as a whole (zero outside it), like the paper's 2^22-sample buffers.
+ *
+ * Conventions as rx.h: device pointers owned by the caller, status codes, no
+ * traps, allocation only in rx_kk_create.
+ */
+#ifndef RX_KK_H_
+#define RX_KK_H_
+
+#include "rx.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rx_kk rx_kk;
+
+/* Input sample formats: one real intensity sample each. */
+enum {
+  RX_KK_I8 = 1,    /* int8 ADC codes c: I = (c + in_offset) * in_scale          */
+  RX_KK_F32 = 2    /* float32 x:        I = (x + in_offset) * in_scale          */
+};
+
+/* baud: symbol rate; sps: input samples per symbol (must be 4); carrier_hz:
+ * frequency of the carrier tone relative to the signal (the paper: 0.516 GHz
+ * for 1 GBd); L_km, D_ps_nm_km: dispersion to compensate; rolloff: RRC roll-off
+ * (the paper: 0.01); max_samples: the largest buffer (even, > 0). */
+rx_status rx_kk_create(rx_kk **out, double baud, int sps, double carrier_hz, double L_km,
+                       double D_ps_nm_km, double rolloff, int64_t max_samples);
+
+rx_status rx_kk_set_cuda_stream(rx_kk *k, void *cuda_stream);
+
+/* Overlap of the static filter's windows (samples at the input rate). */
+rx_status rx_kk_get_overlap(rx_kk *k, int *overlap);
+
+/* One buffer of n input samples (n even, <= max_samples) -> y: n/2 complex
+ * floats (re, im) at 2 samples per symbol; field (optional, may be NULL): the
+ * rebuilt field shifted to DC at the input rate, n complex floats.  Device
+ * pointers; y and field 8-byte aligned.  Asynchronous on the bound stream. */
+rx_status rx_kk_process(rx_kk *k, const void *in, int dtype, int64_t n, float in_scale, float in_offset,
+                        float *y, float *field);
+
+/* Per-stage device time (ms; [0] Hilbert + field rebuild, [1] static filter)
+ * of the calls since the last reset, with profiling on (on != 0).  The first
+ * call with on = 1 switches profiling on; synchronises. */
+rx_status rx_kk_profile(rx_kk *k, int on, double *ms, int reset);
+
+void rx_kk_destroy(rx_kk *k);
+const char *rx_kk_last_error(rx_kk *k);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RX_KK_H_ */

@@ -3,6 +3,6 @@
 The CUDA kernels live in ``csrc/`` and build into ``librx.so``
 (``python -m paper_2104_06311_gb300.build``); ``rx`` is the ctypes binding of
 the C ABI declared in ``include/rx.h`` (``Receiver``), ``include/rx_batch.h``
-(``Batch``) and ``include/rx_cnn.h`` (``CNN``).
+(``Batch``), ``include/rx_cnn.h`` (``CNN``) and ``include/rx_kk.h`` (``KKFrontEnd``).
 """
-from .rx import CNN, Batch, Receiver, load, RxError  # noqa: F401
+from .rx import CNN, Batch, KKFrontEnd, Receiver, load, RxError  # noqa: F401

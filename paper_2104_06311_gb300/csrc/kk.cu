@@ -1,0 +1,296 @@
+// Kramers-Kronig receiver front end (declared in rx_kk.h).
+//
+// Stage 1 (kk_hilbert_kernel, one 64-thread CTA per window of 1024 samples,
+// hop 512): intensity I -> a = sqrt(max(I, 1e-30)), ln a; radix-16 Stockham FFT
+// in shared memory; multiply by j sign(f) / N and conjugate; the same forward
+// FFT again gives the Hilbert image phi (inverse by conjugation); the kept
+// half of the window becomes E = a exp(j phi) exp(j 2 pi f_c n / fs), the
+// shift to DC taken from a 64-bit fixed-point phase accumulator.
+// Stage 2 (kk_filter_kernel, one 32-thread CTA per window): FFT 1024 of the
+// field, multiply by the static filter (dispersion inverse x RRC, with the 1/2
+// of the decimated DFT and 1/512 of the inverse folded in), keep the 512 bins
+// of |f| < fs/4, inverse 512-point FFT, keep the window's centre at 2 samples
+// per symbol.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/rx_kk.h"
+#include "fft.cuh"
+#include "rx_internal.h"
+
+namespace rx {
+namespace {
+
+constexpr int KN = 1024;          // transform length of both stages
+constexpr int KH = KN / 2;        // Hilbert overlap and hop (100 % overlap-save)
+constexpr int KN2 = KN / 2;       // decimated transform length
+
+__global__ void __launch_bounds__(KN / 16) kk_hilbert_kernel(const void *__restrict__ in, int dtype, int64_t n,
+                                                             float scale, float offset, const float2 *__restrict__ tw,
+                                                             unsigned long long inc_q, float2 *__restrict__ E) {
+  __shared__ float2 buf[KN + KN / 32];
+  const int t = threadIdx.x;
+  const int64_t lo = (int64_t)blockIdx.x * KH - KH / 2;
+  auto intensity = [&](int64_t m) -> float {
+    const float x = dtype == RX_KK_I8 ? (float)reinterpret_cast<const int8_t *>(in)[m]
+                                      : reinterpret_cast<const float *>(in)[m];
+    return (x + offset) * scale;
+  };
+  for (int m = t; m < KN; m += blockDim.x) {
+    const int64_t nn = lo + m;
+    float la = 0.f;                              // outside the buffer: zero log-amplitude
+    if (nn >= 0 && nn < n) la = logf(sqrtf(fmaxf(intensity(nn), 1e-30f)));
+    buf[pad(m)] = make_float2(la, 0.f);
+  }
+  __syncthreads();
+  fft_forward<KN, 16>(buf, t, tw);
+  const float inv = 1.f / (float)KN;
+#pragma unroll
+  for (int q = 0; q < 16; ++q) {
+    const int k = t + q * (KN / 16);
+    const float2 v = buf[pad(k)];
+    float2 h;
+    if (k == 0 || k == KN / 2) h = make_float2(0.f, 0.f);
+    else if (k < KN / 2) h = make_float2(-v.y * inv, v.x * inv);     // x j
+    else h = make_float2(v.y * inv, -v.x * inv);                      // x (-j)
+    buf[pad(k)] = cconj(h);
+  }
+  __syncthreads();
+  fft_forward<KN, 16>(buf, t, tw);
+  for (int m = KH / 2 + t; m < KH / 2 + KH; m += blockDim.x) {
+    const int64_t nn = (int64_t)blockIdx.x * KH + (m - KH / 2);
+    if (nn >= n) break;
+    const float phi = buf[pad(m)].x;             // real part of the inverse
+    const float a = sqrtf(fmaxf(intensity(nn), 1e-30f));
+    float sp, cp;
+    sincosf(phi, &sp, &cp);
+    // exp(j 2 pi f_c n / fs): the top 24 bits of the Q0.64 turn n * inc_q
+    const unsigned long long ph = (unsigned long long)nn * inc_q;
+    const float turns = (float)(ph >> 40) * 5.9604644775390625e-08f;   // 2^-24
+    float ss, cs;
+    sincospif(2.f * turns, &ss, &cs);
+    const float ex = a * cp, ey = a * sp;
+    E[nn] = make_float2(ex * cs - ey * ss, ex * ss + ey * cs);
+  }
+}
+
+__global__ void __launch_bounds__(32) kk_filter_kernel(const float2 *__restrict__ E, int64_t n, int V,
+                                                       const float2 *__restrict__ H, const float2 *__restrict__ tw,
+                                                       const float2 *__restrict__ tw2, float2 *__restrict__ y) {
+  __shared__ float2 buf[KN + KN / 32];
+  __shared__ float2 buf2[KN2 + KN2 / 32];
+  const int t = threadIdx.x;
+  const int S = KN - V;
+  const int64_t lo = (int64_t)blockIdx.x * S - V / 2;
+  for (int m = t; m < KN; m += 32) {
+    const int64_t nn = lo + m;
+    buf[pad(m)] = (nn >= 0 && nn < n) ? E[nn] : make_float2(0.f, 0.f);
+  }
+  __syncthreads();
+  fft_forward<KN, 32>(buf, t, tw);
+  // keep |f| < fs/4: bins k < 256 -> k, k >= 768 -> k - 512; conjugate for the inverse
+  for (int k = t; k < KN; k += 32) {
+    if (k >= KN / 4 && k < KN - KN / 4) continue;
+    const int d = k < KN / 4 ? k : k - KN2;
+    buf2[pad(d)] = cconj(cmul(buf[pad(k)], __ldg(&H[k])));
+  }
+  __syncthreads();
+  fft_forward<KN2, 16>(buf2, t, tw2);
+  const int64_t out0 = (int64_t)blockIdx.x * (S / 2);
+  for (int m = V / 4 + t; m < V / 4 + S / 2; m += 32) {
+    const int64_t o = out0 + (m - V / 4);
+    if (o >= n / 2) break;
+    y[o] = cconj(buf2[pad(m)]);
+  }
+}
+
+}  // namespace
+}  // namespace rx
+
+using namespace rx;
+
+struct rx_kk {
+  double baud = 0, carrier = 0, L_km = 0, D = 0, rolloff = 0;
+  int sps = 4, V = KH;
+  int64_t max_n = 0;
+  unsigned long long inc_q = 0;
+  cudaStream_t stream = nullptr;
+  float2 *tw = nullptr, *tw2 = nullptr, *H = nullptr, *Hs = nullptr, *E = nullptr;
+  bool profile = false;
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> pending;
+  double ms[2] = {0, 0};
+  std::string msg;
+};
+
+namespace {
+
+rx_status kfail(rx_kk *k, rx_status s, const std::string &m) {
+  if (k) k->msg = m;
+  return s;
+}
+
+void kk_release(rx_kk *k) {
+  cudaFree(k->tw);
+  cudaFree(k->tw2);
+  cudaFree(k->H);
+  cudaFree(k->Hs);
+  cudaFree(k->E);
+  k->tw = k->tw2 = k->H = k->Hs = k->E = nullptr;
+  std::vector<cudaEvent_t> seen;     // consecutive stages share an event
+  for (auto &p : k->pending)
+    for (cudaEvent_t ev : {p.second.first, p.second.second})
+      if (std::find(seen.begin(), seen.end(), ev) == seen.end()) seen.push_back(ev);
+  for (cudaEvent_t ev : seen) cudaEventDestroy(ev);
+  k->pending.clear();
+}
+
+}  // namespace
+
+extern "C" {
+
+rx_status rx_kk_create(rx_kk **out, double baud, int sps, double carrier_hz, double L_km, double D_ps_nm_km,
+                       double rolloff, int64_t max_samples) {
+  if (!out) return RX_EINVAL;
+  *out = nullptr;
+  if (!(baud > 0) || !(L_km >= 0) || !(rolloff > 0 && rolloff <= 1) || max_samples <= 0 || max_samples % 2 ||
+      carrier_hz != carrier_hz || D_ps_nm_km != D_ps_nm_km)
+    return RX_EINVAL;
+  if (sps != 4) return RX_EUNSUPPORTED;
+  rx_kk *k = new (std::nothrow) rx_kk();
+  if (!k) return RX_ENOMEM;
+  *out = k;
+  k->baud = baud;
+  k->sps = sps;
+  k->carrier = carrier_hz;
+  k->L_km = L_km;
+  k->D = D_ps_nm_km;
+  k->rolloff = rolloff;
+  k->max_n = max_samples;
+  const int64_t ncd = n_cd_taps(baud, sps, L_km, D_ps_nm_km, 1550.0);
+  k->V = (int)std::max<int64_t>(KH, ((ncd - 1 + 31) / 32) * 32);
+  if (k->V >= KN) return kfail(k, RX_EUNSUPPORTED, "dispersion too large for the 1024-point static filter");
+  // f_c / fs as a Q0.64 turn increment
+  double frac = carrier_hz / (sps * baud);
+  frac -= floor(frac);
+  k->inc_q = (unsigned long long)(frac * 18446744073709551616.0);
+  cudaError_t e = cudaMalloc(&k->tw, KN * sizeof(float2));
+  if (e == cudaSuccess) e = cudaMalloc(&k->tw2, KN2 * sizeof(float2));
+  if (e == cudaSuccess) e = cudaMalloc(&k->Hs, KN * sizeof(float2));
+  if (e == cudaSuccess) e = cudaMalloc(&k->H, KN * sizeof(float2));
+  if (e == cudaSuccess) e = cudaMalloc(&k->E, (size_t)max_samples * sizeof(float2));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    kk_release(k);
+    return kfail(k, RX_ENOMEM, "device allocation failed");
+  }
+  // twiddles of both transform sizes (the scratch filter table is unused)
+  e = launch_tables(k->Hs, k->tw, KN, baud, 0.0, 0.0, 1550.0, rolloff, k->stream);
+  if (e == cudaSuccess) e = launch_tables(k->Hs, k->tw2, KN2, baud, 0.0, 0.0, 1550.0, rolloff, k->stream);
+  // static filter on the input grid, with the 1/2 of the decimated DFT and 1/512 of its inverse
+  std::vector<float2> h(KN);
+  const double pi = 3.14159265358979323846, fs = sps * baud;
+  const double Dsm = D_ps_nm_km * 1e-12 / (1e-9 * 1e3), lam = 1550e-9;
+  const double beta2 = -Dsm * lam * lam / (2.0 * pi * 299792458.0);
+  const double f1 = (1.0 - rolloff) * baud / 2.0, f2 = (1.0 + rolloff) * baud / 2.0;
+  for (int i = 0; i < KN; ++i) {
+    const double f = (double)(i < KN / 2 ? i : i - KN) * fs / KN, af = fabs(f);
+    double r = 0.0;
+    if (af <= f1) r = 1.0;
+    else if (af <= f2) r = cos(pi * (af - f1) / (2.0 * rolloff * baud));
+    const double w = 2.0 * pi * f, ph = -beta2 * (L_km * 1e3) * w * w / 2.0;
+    const double g = r * 0.5 / KN2;
+    h[i] = make_float2((float)(g * cos(ph)), (float)(g * sin(ph)));
+  }
+  if (e == cudaSuccess) e = cudaMemcpy(k->H, h.data(), KN * sizeof(float2), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(k->stream);
+  if (e != cudaSuccess) {
+    kk_release(k);
+    return kfail(k, RX_ECUDA, std::string("create: ") + cudaGetErrorString(e));
+  }
+  return RX_OK;
+}
+
+rx_status rx_kk_set_cuda_stream(rx_kk *k, void *s) {
+  if (!k) return RX_EINVAL;
+  k->stream = (cudaStream_t)s;
+  return RX_OK;
+}
+
+rx_status rx_kk_get_overlap(rx_kk *k, int *v) {
+  if (!k || !v) return RX_EINVAL;
+  *v = k->V;
+  return RX_OK;
+}
+
+rx_status rx_kk_process(rx_kk *k, const void *in, int dtype, int64_t n, float in_scale, float in_offset, float *y,
+                        float *field) {
+  if (!k) return RX_EINVAL;
+  if (n < 0 || n % 2 || n > k->max_n) return kfail(k, RX_EINVAL, "sample count must be even and within max_samples");
+  if (dtype != RX_KK_I8 && dtype != RX_KK_F32) return kfail(k, RX_EINVAL, "unknown input dtype");
+  if (n == 0) return RX_OK;
+  if (!in || !y) return kfail(k, RX_EINVAL, "null input or output");
+  if ((uintptr_t)y % 8 || (field && (uintptr_t)field % 8) || (dtype == RX_KK_F32 && (uintptr_t)in % 4))
+    return kfail(k, RX_EINVAL, "misaligned buffer");
+  float2 *E = field ? reinterpret_cast<float2 *>(field) : k->E;
+  cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+  if (k->profile)
+    for (auto &e : ev)
+      if (cudaEventCreate(&e) != cudaSuccess) return kfail(k, RX_ECUDA, "event");
+  if (ev[0]) cudaEventRecord(ev[0], k->stream);
+  const unsigned g1 = (unsigned)((n + KH - 1) / KH);
+  kk_hilbert_kernel<<<g1, KN / 16, 0, k->stream>>>(in, dtype, n, in_scale, in_offset, k->tw, k->inc_q, E);
+  cudaError_t e = cudaGetLastError();
+  if (ev[1]) cudaEventRecord(ev[1], k->stream);
+  const int S = KN - k->V;
+  const unsigned g2 = (unsigned)((n + S - 1) / S);
+  if (e == cudaSuccess) {
+    kk_filter_kernel<<<g2, 32, 0, k->stream>>>(E, n, k->V, k->H, k->tw, k->tw2, reinterpret_cast<float2 *>(y));
+    e = cudaGetLastError();
+  }
+  if (ev[2]) {
+    cudaEventRecord(ev[2], k->stream);
+    k->pending.push_back({0, {ev[0], ev[1]}});
+    k->pending.push_back({1, {ev[1], ev[2]}});
+  }
+  if (e != cudaSuccess) return kfail(k, RX_ECUDA, std::string("launch: ") + cudaGetErrorString(e));
+  return RX_OK;
+}
+
+rx_status rx_kk_profile(rx_kk *k, int on, double *ms, int reset) {
+  if (!k) return RX_EINVAL;
+  k->profile = on != 0;
+  if (cudaStreamSynchronize(k->stream) != cudaSuccess) return kfail(k, RX_ECUDA, "profile wait");
+  // events are shared between consecutive stages: destroy each once
+  std::vector<cudaEvent_t> seen;
+  for (auto &p : k->pending) {
+    float t = 0.f;
+    cudaEventElapsedTime(&t, p.second.first, p.second.second);
+    k->ms[p.first] += t;
+    for (cudaEvent_t ev : {p.second.first, p.second.second})
+      if (std::find(seen.begin(), seen.end(), ev) == seen.end()) seen.push_back(ev);
+  }
+  for (cudaEvent_t ev : seen) cudaEventDestroy(ev);
+  k->pending.clear();
+  if (ms) {
+    ms[0] = k->ms[0];
+    ms[1] = k->ms[1];
+  }
+  if (reset) k->ms[0] = k->ms[1] = 0;
+  return RX_OK;
+}
+
+void rx_kk_destroy(rx_kk *k) {
+  if (!k) return;
+  cudaStreamSynchronize(k->stream);
+  kk_release(k);
+  delete k;
+}
+
+const char *rx_kk_last_error(rx_kk *k) { return k ? k->msg.c_str() : "null handle"; }
+
+}  // extern "C"

@@ -34,7 +34,9 @@ EXPORTS = ["rx_create", "rx_set_param", "rx_get_param", "rx_set_cuda_stream", "r
            "rx_batch_last_error", "rx_batch_profile",
            "rx_cnn_create", "rx_cnn_param_count", "rx_cnn_set_params", "rx_cnn_get_params",
            "rx_cnn_set_cuda_stream", "rx_cnn_apply", "rx_cnn_grads", "rx_cnn_train_step", "rx_cnn_destroy",
-           "rx_cnn_last_error", "rx_cnn_set_profile", "rx_cnn_profile", "rx_cnn_set_option"]
+           "rx_cnn_last_error", "rx_cnn_set_profile", "rx_cnn_profile", "rx_cnn_set_option",
+           "rx_kk_create", "rx_kk_set_cuda_stream", "rx_kk_get_overlap", "rx_kk_process", "rx_kk_profile",
+           "rx_kk_destroy", "rx_kk_last_error"]
 CNN_KINDS = ["fwd_hidden", "fwd_edge", "dx", "dw", "update"]
 BATCH_PARAMS = {"GRAPH": 100, "EQ_CTAS": 101, "EQ_TEAM": 102, "CDC_NS_PER_SAMPLE": 103, "PROFILE": 104}
 
@@ -125,13 +127,24 @@ def load(path: str = LIB_PATH) -> ct.CDLL:
     lib.rx_cnn_set_profile.argtypes = [P, ct.c_int]
     lib.rx_cnn_set_option.argtypes = [P, ct.c_int, ct.c_int]
     lib.rx_cnn_profile.argtypes = [P, ct.POINTER(ct.c_double), ct.POINTER(ct.c_int64), ct.c_int]
+    lib.rx_kk_create.argtypes = [ct.POINTER(P), ct.c_double, ct.c_int, ct.c_double, ct.c_double, ct.c_double,
+                                 ct.c_double, ct.c_int64]
+    lib.rx_kk_set_cuda_stream.argtypes = [P, P]
+    lib.rx_kk_get_overlap.argtypes = [P, ct.POINTER(ct.c_int)]
+    lib.rx_kk_process.argtypes = [P, P, ct.c_int, ct.c_int64, ct.c_float, ct.c_float, P, P]
+    lib.rx_kk_profile.argtypes = [P, ct.c_int, ct.POINTER(ct.c_double), ct.c_int]
+    lib.rx_kk_destroy.argtypes = [P]
+    lib.rx_kk_destroy.restype = None
+    lib.rx_kk_last_error.argtypes = [P]
+    lib.rx_kk_last_error.restype = ct.c_char_p
     lib.rx_cnn_destroy.argtypes = [P]
     lib.rx_cnn_destroy.restype = None
     lib.rx_cnn_last_error.argtypes = [P]
     lib.rx_cnn_last_error.restype = ct.c_char_p
     for name in EXPORTS:
         if name not in ("rx_destroy", "rx_status_str", "rx_last_error", "rx_batch_destroy", "rx_batch_last_error",
-                        "rx_cnn_param_count", "rx_cnn_destroy", "rx_cnn_last_error"):
+                        "rx_cnn_param_count", "rx_cnn_destroy", "rx_cnn_last_error", "rx_kk_destroy",
+                        "rx_kk_last_error"):
             getattr(lib, name).restype = ct.c_int
     _lib = lib
     return lib
@@ -604,6 +617,75 @@ class CNN:
             self.h = None
 
     rx_cnn_destroy = close
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _kcheck(lib, h, status):
+    if status != RX_OK:
+        detail = lib.rx_kk_last_error(h).decode() if h else ""
+        raise RxError(status, f"{lib.rx_status_str(status).decode()}: {detail}")
+
+
+class KKFrontEnd:
+    """Kramers-Kronig receiver front end (include/rx_kk.h): real intensity samples
+    at 4 samples/symbol -> rebuilt field at 2 samples/symbol (complex64 tensors)."""
+
+    def __init__(self, baud, carrier_hz, L_km, max_samples, D=17.0, rolloff=0.01, sps=4, stream=None):
+        import torch
+        self.torch = torch
+        self.lib = load()
+        h = ct.c_void_p()
+        st = self.lib.rx_kk_create(ct.byref(h), float(baud), int(sps), float(carrier_hz), float(L_km), float(D),
+                                   float(rolloff), int(max_samples))
+        if st != RX_OK:
+            msg = self.lib.rx_kk_last_error(h).decode() if h else ""
+            if h:
+                self.lib.rx_kk_destroy(h)
+            raise RxError(st, f"{self.lib.rx_status_str(st).decode()}: {msg}")
+        self.h = h
+        if stream is not None:
+            ptr = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+            _kcheck(self.lib, self.h, self.lib.rx_kk_set_cuda_stream(self.h, ct.c_void_p(ptr)))
+
+    @property
+    def overlap(self):
+        v = ct.c_int()
+        _kcheck(self.lib, self.h, self.lib.rx_kk_get_overlap(self.h, ct.byref(v)))
+        return v.value
+
+    def rx_kk_process(self, samples, in_scale=1.0, in_offset=0.0, field=False, out=None):
+        """samples: 1-D int8 or float32 CUDA tensor -> (y at 2 sps, field at the input rate or None)."""
+        t = self.torch
+        assert samples.is_cuda and samples.is_contiguous() and samples.dim() == 1
+        n = samples.shape[0]
+        dt = 1 if samples.dtype == t.int8 else 2
+        y = out if out is not None else t.empty(n // 2, dtype=t.complex64, device="cuda")
+        f = t.empty(n, dtype=t.complex64, device="cuda") if field else None
+        _kcheck(self.lib, self.h, self.lib.rx_kk_process(self.h, samples.data_ptr(), dt, n, float(in_scale),
+                                                         float(in_offset), y.data_ptr(),
+                                                         f.data_ptr() if f is not None else None))
+        return y, f
+
+    process = rx_kk_process
+
+    def rx_kk_profile(self, on=True, reset=False):
+        ms = (ct.c_double * 2)()
+        _kcheck(self.lib, self.h, self.lib.rx_kk_profile(self.h, 1 if on else 0, ms, 1 if reset else 0))
+        return {"hilbert": ms[0], "filter": ms[1]}
+
+    profile = rx_kk_profile
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.rx_kk_destroy(self.h)
+            self.h = None
+
+    rx_kk_destroy = close
 
     def __del__(self):
         try:
