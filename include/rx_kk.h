@@ -12,9 +12,12 @@
  * has the response j sign(f) (signal side band below the carrier, minimum-phase
  * field); amplitude sqrt(max(I, 1e-30)); the 100 % overlap-save is N = 1024
  * with overlap N/2, samples outside the buffer count as zero log-amplitude;
- * the static filter is the dispersion inverse exp(-j beta2 L w^2/2) times the
- * RRC matched filter (the paper optimised its filter offline from lab data),
- * in N = 1024 windows with overlap max(N/2, the textbook CD length); the
+ * the static filter is sqrt(sps) times the dispersion inverse
+ * exp(-j beta2 L w^2/2) times the RRC matched filter, times the constant
+ * exp(+j beta2 L w_c^2/2) that takes back the dispersion phase of the carrier
+ * tone the field is referenced to (unit symbol gain, no constant phase: what
+ * the paper's offline optimisation from lab data converges to), in N = 1024
+ * windows with overlap max(N/2, the textbook CD length); the
  * decimation keeps the bins of |f| < fs/4 and applies a factor 1/2.  A buffer is
  * processed as a whole (zero outside it), like the paper's 2^22-sample buffers.
  *

@@ -5,6 +5,9 @@ Transmitter: Gray QAM symbols at `baud`, RRC (roll-off 0.01) at `sps` samples
 per symbol (the 4 GS/s ADC at 1 GBd gives 4), plus a carrier tone at
 `carrier_hz` on the edge of the signal band, scaled so that carrier power /
 signal power = CSPR.  Fibre: chromatic dispersion over L km (whole stream).
+Optional transmitter IQ imbalance on the signal (Q arm gain 10^(g/20) and phase
+skew theta): x = mu s + nu s*, mu = (1 + rho e^{j theta})/2,
+nu = (1 - rho e^{j theta})/2 -- what a widely-linear equaliser undoes.
 Receiver: AWGN on the optical field at Es/N0 = `snr_db` (signal power over
 noise), square-law photodetection I = |E|^2, and either float32 samples or an
 8-bit ADC (codes 0..255 stored as int8 c - 128; I = (c + 128) * step).
@@ -34,6 +37,8 @@ class KKLink:
     snr_db: float | None = 25.0
     adc: str = "int8"
     seed: int = 2104063117
+    iq_gain_db: float = 0.0
+    iq_phase_deg: float = 0.0
 
     @property
     def fs(self) -> float:
@@ -52,12 +57,22 @@ class KKGenerated:
     in_offset: float
 
 
+def iq_imbalance(link: KKLink) -> tuple[complex, complex]:
+    """(mu, nu) of the transmitter's widely-linear distortion x = mu s + nu s*."""
+    r = 10.0 ** (link.iq_gain_db / 20.0) * complex(math.cos(math.radians(link.iq_phase_deg)),
+                                                   math.sin(math.radians(link.iq_phase_deg)))
+    return (1.0 + r) / 2.0, (1.0 - r) / 2.0
+
+
 def generate(link: KKLink) -> KKGenerated:
     m = bits_per_symbol(link.mod)
     K = link.n_sym
     bits = random_bits(link.seed, K * m)
     sym = map_symbols(bits.reshape(1, -1), link.mod)[0]
     s = tx_shape(sym[None, :], link.baud, link.rolloff, link.sps)[0]
+    mu, nu = iq_imbalance(link)
+    if nu != 0.0:
+        s = mu * s + nu * np.conj(s)
     n = s.shape[0]
     p_s = float(np.mean(np.abs(s) ** 2))
     amp = math.sqrt(p_s * 10.0 ** (link.cspr_db / 10.0))

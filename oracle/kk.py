@@ -18,7 +18,12 @@ that also downsamples from 4 to 2 samples per symbol.  Readings:
   * Shift to DC: multiply by exp(+j 2 pi f_c n / fs) (the carrier moves to
     +f_c, outside the RRC band, and the next filter removes it).
   * Static filter (the paper's offline-optimised filter has no closed form):
-    exp(-j beta2 L w^2 / 2) times the RRC matched filter on the fs grid, in
+    sqrt(sps) exp(-j beta2 L w^2 / 2) times the RRC matched filter on the fs
+    grid, times the constant exp(+j beta2 L w_c^2 / 2) that takes back the
+    phase the carrier tone at w_c = 2 pi f_c picked up in the fibre (the
+    rebuilt field is referenced to the received tone), so that symbols come
+    out with unit gain and no constant phase -- what an offline fit against
+    known symbols converges to; in
     overlap-save windows of N = 1024 with V = max(N/2, the textbook CD length
     rounded up to 32) (100 % overlap like the Hilbert pair, which also covers
     most of the 1 %-roll-off RRC response); downsampling keeps the N/2 bins of
@@ -73,7 +78,8 @@ def n_cd_taps(baud: float, sps: int, L_km: float, D: float, lam_nm: float) -> in
     return 2 * int(math.floor(Dsm * lam * lam * L_km * 1e3 / (2.0 * 299792458.0 * T * T))) + 1
 
 
-def static_filter(baud: float, fs: float, L_km: float, D: float, lam_nm: float, rolloff: float, N: int) -> np.ndarray:
+def static_filter(baud: float, fs: float, L_km: float, D: float, lam_nm: float, rolloff: float, N: int,
+                  f_c: float = 0.0) -> np.ndarray:
     f = grid(N, fs)
     Dsm = D * 1e-12 / (1e-9 * 1e3)
     lam = lam_nm * 1e-9
@@ -81,7 +87,8 @@ def static_filter(baud: float, fs: float, L_km: float, D: float, lam_nm: float, 
     af = np.abs(f)
     f1, f2 = (1.0 - rolloff) * baud / 2.0, (1.0 + rolloff) * baud / 2.0
     rrc = np.where(af <= f1, 1.0, np.where(af <= f2, np.cos(np.pi * (af - f1) / (2.0 * rolloff * baud)), 0.0))
-    return np.exp(-1j * beta2 * (L_km * 1e3) * (TWO_PI * f) ** 2 / 2.0) * rrc
+    gain = math.sqrt(fs / baud) * np.exp(1j * beta2 * (L_km * 1e3) * (TWO_PI * f_c) ** 2 / 2.0)
+    return gain * np.exp(-1j * beta2 * (L_km * 1e3) * (TWO_PI * f) ** 2 / 2.0) * rrc
 
 
 def hilbert_field(I: np.ndarray, fs: float, f_c: float, N: int = 1024) -> np.ndarray:
@@ -121,5 +128,5 @@ def kk_frontend(samples: np.ndarray, in_scale: float, in_offset: float, baud: fl
     I = (np.asarray(samples, np.float64) + in_offset) * in_scale
     E = hilbert_field(I, fs, f_c, N)
     V = max(N // 2, ((n_cd_taps(baud, sps, L_km, D, lam_nm) - 1 + 31) // 32) * 32)
-    H = static_filter(baud, fs, L_km, D, lam_nm, rolloff, N)
+    H = static_filter(baud, fs, L_km, D, lam_nm, rolloff, N, f_c)
     return decimating_filter(E, H, V), E, V

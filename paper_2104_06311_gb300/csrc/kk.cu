@@ -191,7 +191,9 @@ rx_status rx_kk_create(rx_kk **out, double baud, int sps, double carrier_hz, dou
   // twiddles of both transform sizes (the scratch filter table is unused)
   e = launch_tables(k->Hs, k->tw, KN, baud, 0.0, 0.0, 1550.0, rolloff, k->stream);
   if (e == cudaSuccess) e = launch_tables(k->Hs, k->tw2, KN2, baud, 0.0, 0.0, 1550.0, rolloff, k->stream);
-  // static filter on the input grid, with the 1/2 of the decimated DFT and 1/512 of its inverse
+  // static filter on the input grid: sqrt(sps) RRC x dispersion inverse x the constant that takes back
+  // the carrier tone's own dispersion phase (unit symbol gain, no constant phase), with the 1/2 of the
+  // decimated DFT and the 1/512 of its inverse
   std::vector<float2> h(KN);
   const double pi = 3.14159265358979323846, fs = sps * baud;
   const double Dsm = D_ps_nm_km * 1e-12 / (1e-9 * 1e3), lam = 1550e-9;
@@ -202,8 +204,9 @@ rx_status rx_kk_create(rx_kk **out, double baud, int sps, double carrier_hz, dou
     double r = 0.0;
     if (af <= f1) r = 1.0;
     else if (af <= f2) r = cos(pi * (af - f1) / (2.0 * rolloff * baud));
-    const double w = 2.0 * pi * f, ph = -beta2 * (L_km * 1e3) * w * w / 2.0;
-    const double g = r * 0.5 / KN2;
+    const double w = 2.0 * pi * f, wc = 2.0 * pi * carrier_hz;
+    const double ph = -beta2 * (L_km * 1e3) * (w * w - wc * wc) / 2.0;
+    const double g = r * sqrt((double)sps) * 0.5 / KN2;
     h[i] = make_float2((float)(g * cos(ph)), (float)(g * sin(ph)));
   }
   if (e == cudaSuccess) e = cudaMemcpy(k->H, h.data(), KN * sizeof(float2), cudaMemcpyHostToDevice);

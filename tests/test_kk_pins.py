@@ -78,10 +78,28 @@ def test_end_to_end_noise_free_symbols():
     assert V == 512
     z = y[0::2][256:-256]
     t = g.tx_symbols[256:-256]
-    c = np.vdot(t, z) / np.vdot(t, t)            # one complex gain (scale and carrier phase)
+    c = np.vdot(t, z) / np.vdot(t, t)            # the complex gain left over
     evm = np.linalg.norm(z - c * t) / np.linalg.norm(c * t)
     assert evm < 0.03, evm
-    # the 16QAM decisions are error-free
+    # sqrt(sps) and the carrier's dispersion phase are in the static filter: unit gain,
+    # no constant phase (without the phase term the angle would be beta2 L w_c^2/2 = 0.114)
+    assert abs(c - 1.0) < 2e-3, c
+    # the 16QAM decisions are error-free without any correction
     d = L.map_symbols(L.random_bits(lk.seed, lk.n_sym * 4).reshape(1, -1), "16qam")[0][256:-256]
     from oracle.chain import decide
-    assert np.array_equal(decide(z / c, "16qam"), d)
+    assert np.array_equal(decide(z, "16qam"), d)
+
+
+def test_static_filter_phase_term_cancels_the_carrier_dispersion_phase():
+    # through CD alone, a tone at f_c picks up exp(+j beta2 L w_c^2/2); the KK field is
+    # referenced to that tone, so it carries the conjugate, and the static filter's
+    # constant must be the tone's own phase, whatever L and f_c
+    for L_km, k in ((1000.0, 528), (7600.0, 307)):
+        fc = k * 4e9 / 4096                          # on the DFT grid: a pure tone
+        tone = np.exp(2j * np.pi * fc / 4e9 * np.arange(4096))
+        rx = L.apply_dispersion(tone[None, :], 4e9, L_km, 17.0, 1550.0)[0]
+        ph = np.angle(np.vdot(tone, rx))
+        H = K.static_filter(1e9, 4e9, L_km, 17.0, 1550.0, 0.01, 1024, fc)
+        assert abs(abs(H[0]) - 2.0) < 1e-12                 # sqrt(sps) at DC
+        assert abs(ph) > 0.05
+        assert abs(np.angle(H[0] * np.exp(-1j * ph))) < 1e-9
