@@ -53,12 +53,19 @@ rx_status rx_kk_set_cuda_stream(rx_kk *k, void *cuda_stream);
 /* Overlap of the static filter's windows (samples at the input rate). */
 rx_status rx_kk_get_overlap(rx_kk *k, int *overlap);
 
-/* One buffer of n input samples (n even, <= max_samples) -> y: n/2 complex
- * floats (re, im) at 2 samples per symbol; field (optional, may be NULL): the
- * rebuilt field shifted to DC at the input rate, n complex floats.  Device
+/* The next buffer of the stream: n input samples (n even, <= max_samples) ->
+ * y: n/2 complex floats (re, im) at 2 samples per symbol; field (optional, may
+ * be NULL): the rebuilt field shifted to DC at the input rate, n complex floats.
+ * The shift to DC runs on the stream's sample count (sample m of the buffer is
+ * stream sample pos + m, pos = the samples of all earlier calls since create, or
+ * as set by rx_kk_set_position), so consecutive buffers share one carrier phase.  Device
  * pointers; y and field 8-byte aligned.  Asynchronous on the bound stream. */
 rx_status rx_kk_process(rx_kk *k, const void *in, int dtype, int64_t n, float in_scale, float in_offset,
                         float *y, float *field);
+
+/* Stream index of the next buffer's first sample (>= 0; 0 restarts the
+ * stream, another value replays a buffer recorded at that position). */
+rx_status rx_kk_set_position(rx_kk *k, int64_t pos);
 
 /* Per-stage device time (ms; [0] Hilbert + field rebuild, [1] static filter)
  * of the calls since the last reset, with profiling on (on != 0).  The first

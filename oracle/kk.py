@@ -15,7 +15,9 @@ that also downsamples from 4 to 2 samples per symbol.  Readings:
     ln a with the response j sign(f) (the signal sits below the carrier, so the
     reconstructed field is minimum phase with negative-frequency side band;
     Mecozzi, Antonelli, Shtaif, Optica 2016); eps = 1e-30.
-  * Shift to DC: multiply by exp(+j 2 pi f_c n / fs) (the carrier moves to
+  * Shift to DC: multiply by exp(+j 2 pi f_c n / fs) with n the sample's
+    index in the whole stream (buffer i starts at n0 = the samples before it),
+    so that consecutive buffers share one carrier phase (the carrier moves to
     +f_c, outside the RRC band, and the next filter removes it).
   * Static filter (the paper's offline-optimised filter has no closed form):
     sqrt(sps) exp(-j beta2 L w^2 / 2) times the RRC matched filter on the fs
@@ -91,14 +93,16 @@ def static_filter(baud: float, fs: float, L_km: float, D: float, lam_nm: float, 
     return gain * np.exp(-1j * beta2 * (L_km * 1e3) * (TWO_PI * f) ** 2 / 2.0) * rrc
 
 
-def hilbert_field(I: np.ndarray, fs: float, f_c: float, N: int = 1024) -> np.ndarray:
-    """Rebuilt field shifted to DC at the input rate (complex, same length as I)."""
+def hilbert_field(I: np.ndarray, fs: float, f_c: float, N: int = 1024, n0: int = 0) -> np.ndarray:
+    """Rebuilt field shifted to DC at the input rate (complex, same length as I);
+    n0 is the stream index of I[0]."""
     n = I.shape[0]
     a = np.sqrt(np.maximum(I, EPS))
     lna = np.log(a)
     phi = overlap_save(lna.astype(np.complex128), hilbert_response(N), N // 2).real
     E = a * np.exp(1j * phi)
-    return E * np.exp(1j * TWO_PI * (f_c / fs) * np.arange(n))
+    turns = np.mod((f_c / fs) * (n0 + np.arange(n, dtype=np.float64)), 1.0)
+    return E * np.exp(1j * TWO_PI * turns)
 
 
 def decimating_filter(E: np.ndarray, H: np.ndarray, V: int) -> np.ndarray:
@@ -122,11 +126,13 @@ def decimating_filter(E: np.ndarray, H: np.ndarray, V: int) -> np.ndarray:
 
 
 def kk_frontend(samples: np.ndarray, in_scale: float, in_offset: float, baud: float, sps: int, f_c: float,
-                L_km: float, D: float = 17.0, lam_nm: float = 1550.0, rolloff: float = 0.01, N: int = 1024):
-    """Receiver samples -> (field at 2 samples/symbol, field at the input rate, V of the filter)."""
+                L_km: float, D: float = 17.0, lam_nm: float = 1550.0, rolloff: float = 0.01, N: int = 1024,
+                n0: int = 0):
+    """One buffer of receiver samples, the first at stream index n0 -> (field at 2
+    samples/symbol, field at the input rate, V of the filter)."""
     fs = sps * baud
     I = (np.asarray(samples, np.float64) + in_offset) * in_scale
-    E = hilbert_field(I, fs, f_c, N)
+    E = hilbert_field(I, fs, f_c, N, n0)
     V = max(N // 2, ((n_cd_taps(baud, sps, L_km, D, lam_nm) - 1 + 31) // 32) * 32)
     H = static_filter(baud, fs, L_km, D, lam_nm, rolloff, N, f_c)
     return decimating_filter(E, H, V), E, V

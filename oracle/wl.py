@@ -66,7 +66,7 @@ def _regressor(x: np.ndarray, k: int, T: int) -> np.ndarray:
 
 def _run(x: np.ndarray, w: np.ndarray, k0: int, k1: int, p: WLParams, z: np.ndarray | None) -> np.ndarray:
     """Symbols k0..k1-1 in order from taps w (copied); z[k] written when z is given."""
-    h, g = w[0].copy(), w[1].copy()
+    h, g = w[0].copy(), (np.zeros_like(w[1]) if p.linear else w[1].copy())
     for k in range(k0, k1):
         u = _regressor(x, k, p.ntaps)
         zk = np.dot(h, u) + np.dot(g, np.conj(u))

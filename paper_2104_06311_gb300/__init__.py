@@ -3,6 +3,7 @@
 The CUDA kernels live in ``csrc/`` and build into ``librx.so``
 (``python -m paper_2104_06311_gb300.build``); ``rx`` is the ctypes binding of
 the C ABI declared in ``include/rx.h`` (``Receiver``), ``include/rx_batch.h``
-(``Batch``), ``include/rx_cnn.h`` (``CNN``) and ``include/rx_kk.h`` (``KKFrontEnd``).
+(``Batch``), ``include/rx_cnn.h`` (``CNN``), ``include/rx_kk.h`` (``KKFrontEnd``) and
+``include/rx_wl.h`` (``WLEqualiser``).
 """
-from .rx import CNN, Batch, KKFrontEnd, Receiver, load, RxError  # noqa: F401
+from .rx import CNN, Batch, KKFrontEnd, Receiver, WLEqualiser, load, RxError  # noqa: F401

@@ -32,7 +32,8 @@ constexpr int KN2 = KN / 2;       // decimated transform length
 
 __global__ void __launch_bounds__(KN / 16) kk_hilbert_kernel(const void *__restrict__ in, int dtype, int64_t n,
                                                              float scale, float offset, const float2 *__restrict__ tw,
-                                                             unsigned long long inc_q, float2 *__restrict__ E) {
+                                                             unsigned long long inc_q, unsigned long long ph0,
+                                                             float2 *__restrict__ E) {
   __shared__ float2 buf[KN + KN / 32];
   const int t = threadIdx.x;
   const int64_t lo = (int64_t)blockIdx.x * KH - KH / 2;
@@ -69,8 +70,9 @@ __global__ void __launch_bounds__(KN / 16) kk_hilbert_kernel(const void *__restr
     const float a = sqrtf(fmaxf(intensity(nn), 1e-30f));
     float sp, cp;
     sincosf(phi, &sp, &cp);
-    // exp(j 2 pi f_c n / fs): the top 24 bits of the Q0.64 turn n * inc_q
-    const unsigned long long ph = (unsigned long long)nn * inc_q;
+    // exp(j 2 pi f_c (pos + n) / fs), pos = the buffer's first sample in the stream: the top
+    // 24 bits of the Q0.64 turn ph0 + n inc_q (ph0 = pos inc_q mod 2^64)
+    const unsigned long long ph = ph0 + (unsigned long long)nn * inc_q;
     const float turns = (float)(ph >> 40) * 5.9604644775390625e-08f;   // 2^-24
     float ss, cs;
     sincospif(2.f * turns, &ss, &cs);
@@ -119,6 +121,7 @@ struct rx_kk {
   int sps = 4, V = KH;
   int64_t max_n = 0;
   unsigned long long inc_q = 0;
+  int64_t pos = 0;                  // stream position of the next buffer's first sample
   cudaStream_t stream = nullptr;
   float2 *tw = nullptr, *tw2 = nullptr, *H = nullptr, *Hs = nullptr, *E = nullptr;
   bool profile = false;
@@ -246,7 +249,8 @@ rx_status rx_kk_process(rx_kk *k, const void *in, int dtype, int64_t n, float in
       if (cudaEventCreate(&e) != cudaSuccess) return kfail(k, RX_ECUDA, "event");
   if (ev[0]) cudaEventRecord(ev[0], k->stream);
   const unsigned g1 = (unsigned)((n + KH - 1) / KH);
-  kk_hilbert_kernel<<<g1, KN / 16, 0, k->stream>>>(in, dtype, n, in_scale, in_offset, k->tw, k->inc_q, E);
+  kk_hilbert_kernel<<<g1, KN / 16, 0, k->stream>>>(in, dtype, n, in_scale, in_offset, k->tw, k->inc_q,
+                                                   (unsigned long long)k->pos * k->inc_q, E);
   cudaError_t e = cudaGetLastError();
   if (ev[1]) cudaEventRecord(ev[1], k->stream);
   const int S = KN - k->V;
@@ -261,6 +265,14 @@ rx_status rx_kk_process(rx_kk *k, const void *in, int dtype, int64_t n, float in
     k->pending.push_back({1, {ev[1], ev[2]}});
   }
   if (e != cudaSuccess) return kfail(k, RX_ECUDA, std::string("launch: ") + cudaGetErrorString(e));
+  k->pos += n;
+  return RX_OK;
+}
+
+rx_status rx_kk_set_position(rx_kk *k, int64_t pos) {
+  if (!k) return RX_EINVAL;
+  if (pos < 0) return kfail(k, RX_EINVAL, "stream position must be >= 0");
+  k->pos = pos;
   return RX_OK;
 }
 

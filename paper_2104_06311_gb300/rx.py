@@ -36,7 +36,10 @@ EXPORTS = ["rx_create", "rx_set_param", "rx_get_param", "rx_set_cuda_stream", "r
            "rx_cnn_set_cuda_stream", "rx_cnn_apply", "rx_cnn_grads", "rx_cnn_train_step", "rx_cnn_destroy",
            "rx_cnn_last_error", "rx_cnn_set_profile", "rx_cnn_profile", "rx_cnn_set_option",
            "rx_kk_create", "rx_kk_set_cuda_stream", "rx_kk_get_overlap", "rx_kk_process", "rx_kk_profile",
-           "rx_kk_destroy", "rx_kk_last_error"]
+           "rx_kk_set_position", "rx_kk_destroy", "rx_kk_last_error",
+           "rx_wl_create", "rx_wl_set_param", "rx_wl_get_param", "rx_wl_set_cuda_stream", "rx_wl_set_taps",
+           "rx_wl_get_taps", "rx_wl_process", "rx_wl_reset", "rx_wl_profile", "rx_wl_destroy", "rx_wl_last_error"]
+WL_PARAMS = {"MU": 1, "SEG_LEN": 2, "PRETRAIN": 3, "ACQ": 4, "LINEAR": 5}
 CNN_KINDS = ["fwd_hidden", "fwd_edge", "dx", "dw", "update"]
 BATCH_PARAMS = {"GRAPH": 100, "EQ_CTAS": 101, "EQ_TEAM": 102, "CDC_NS_PER_SAMPLE": 103, "PROFILE": 104}
 
@@ -133,10 +136,24 @@ def load(path: str = LIB_PATH) -> ct.CDLL:
     lib.rx_kk_get_overlap.argtypes = [P, ct.POINTER(ct.c_int)]
     lib.rx_kk_process.argtypes = [P, P, ct.c_int, ct.c_int64, ct.c_float, ct.c_float, P, P]
     lib.rx_kk_profile.argtypes = [P, ct.c_int, ct.POINTER(ct.c_double), ct.c_int]
+    lib.rx_kk_set_position.argtypes = [P, ct.c_int64]
     lib.rx_kk_destroy.argtypes = [P]
     lib.rx_kk_destroy.restype = None
     lib.rx_kk_last_error.argtypes = [P]
     lib.rx_kk_last_error.restype = ct.c_char_p
+    lib.rx_wl_create.argtypes = [ct.POINTER(P), ct.c_int, ct.c_int, ct.c_int64]
+    lib.rx_wl_set_param.argtypes = [P, ct.c_int, ct.c_double]
+    lib.rx_wl_get_param.argtypes = [P, ct.c_int, ct.POINTER(ct.c_double)]
+    lib.rx_wl_set_cuda_stream.argtypes = [P, P]
+    lib.rx_wl_set_taps.argtypes = [P, ct.POINTER(ct.c_float)]
+    lib.rx_wl_get_taps.argtypes = [P, ct.POINTER(ct.c_double)]
+    lib.rx_wl_process.argtypes = [P, P, ct.c_int64, P, P]
+    lib.rx_wl_reset.argtypes = [P]
+    lib.rx_wl_profile.argtypes = [P, ct.c_int, ct.POINTER(ct.c_double), ct.c_int]
+    lib.rx_wl_destroy.argtypes = [P]
+    lib.rx_wl_destroy.restype = None
+    lib.rx_wl_last_error.argtypes = [P]
+    lib.rx_wl_last_error.restype = ct.c_char_p
     lib.rx_cnn_destroy.argtypes = [P]
     lib.rx_cnn_destroy.restype = None
     lib.rx_cnn_last_error.argtypes = [P]
@@ -144,7 +161,7 @@ def load(path: str = LIB_PATH) -> ct.CDLL:
     for name in EXPORTS:
         if name not in ("rx_destroy", "rx_status_str", "rx_last_error", "rx_batch_destroy", "rx_batch_last_error",
                         "rx_cnn_param_count", "rx_cnn_destroy", "rx_cnn_last_error", "rx_kk_destroy",
-                        "rx_kk_last_error"):
+                        "rx_kk_last_error", "rx_wl_destroy", "rx_wl_last_error"):
             getattr(lib, name).restype = ct.c_int
     _lib = lib
     return lib
@@ -673,6 +690,11 @@ class KKFrontEnd:
 
     process = rx_kk_process
 
+    def rx_kk_set_position(self, pos=0):
+        _kcheck(self.lib, self.h, self.lib.rx_kk_set_position(self.h, int(pos)))
+
+    set_position = rx_kk_set_position
+
     def rx_kk_profile(self, on=True, reset=False):
         ms = (ct.c_double * 2)()
         _kcheck(self.lib, self.h, self.lib.rx_kk_profile(self.h, 1 if on else 0, ms, 1 if reset else 0))
@@ -686,6 +708,104 @@ class KKFrontEnd:
             self.h = None
 
     rx_kk_destroy = close
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _wcheck(lib, h, status):
+    if status != RX_OK:
+        detail = lib.rx_wl_last_error(h).decode() if h else ""
+        raise RxError(status, f"{lib.rx_status_str(status).decode()}: {detail}")
+
+
+class WLEqualiser:
+    """Four-tap widely-linear DD-LMS equaliser (include/rx_wl.h): complex64 field
+    at 2 samples/symbol -> packed Gray bits (int32 words) and optional outputs."""
+
+    def __init__(self, mod_bits, max_symbols, ntaps=4, stream=None, **params):
+        import torch
+        self.torch = torch
+        self.lib = load()
+        self.mod_bits = int(mod_bits)
+        h = ct.c_void_p()
+        st = self.lib.rx_wl_create(ct.byref(h), self.mod_bits, int(ntaps), int(max_symbols))
+        if st != RX_OK:
+            raise RxError(st, self.lib.rx_status_str(st).decode())
+        self.h = h
+        self.ntaps = int(ntaps)
+        if stream is not None:
+            ptr = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+            _wcheck(self.lib, self.h, self.lib.rx_wl_set_cuda_stream(self.h, ct.c_void_p(ptr)))
+        for k, v in params.items():
+            self.rx_wl_set_param(k, v)
+
+    def rx_wl_set_param(self, key, value):
+        _wcheck(self.lib, self.h, self.lib.rx_wl_set_param(self.h, WL_PARAMS[key.upper()], float(value)))
+
+    set_param = rx_wl_set_param
+
+    def rx_wl_get_param(self, key):
+        v = ct.c_double()
+        _wcheck(self.lib, self.h, self.lib.rx_wl_get_param(self.h, WL_PARAMS[key.upper()], ct.byref(v)))
+        return v.value
+
+    get_param = rx_wl_get_param
+
+    def rx_wl_set_taps(self, taps):
+        """taps: (2, T) complex array-like, row 0 = h on x, row 1 = g on conj(x)."""
+        import numpy as np
+        t = np.asarray(taps, np.complex128).reshape(2, self.ntaps)
+        flat = np.stack([t.real, t.imag], -1).reshape(-1).astype(np.float32)
+        _wcheck(self.lib, self.h, self.lib.rx_wl_set_taps(self.h, flat.ctypes.data_as(ct.POINTER(ct.c_float))))
+
+    set_taps = rx_wl_set_taps
+
+    def rx_wl_get_taps(self):
+        import numpy as np
+        buf = (ct.c_double * (4 * self.ntaps))()
+        _wcheck(self.lib, self.h, self.lib.rx_wl_get_taps(self.h, buf))
+        a = np.frombuffer(buf, np.float64).reshape(2, self.ntaps, 2)
+        return a[..., 0] + 1j * a[..., 1]
+
+    get_taps = rx_wl_get_taps
+
+    def rx_wl_process(self, x, want_z=False, bits=None):
+        """x: 1-D complex64 CUDA tensor (2 samples/symbol) -> (bits int32 words, z complex64 or None)."""
+        t = self.torch
+        assert x.is_cuda and x.is_contiguous() and x.dim() == 1 and x.dtype == t.complex64
+        n = x.shape[0]
+        K = n // 2
+        words = (K * self.mod_bits + 31) // 32
+        b = bits if bits is not None else t.empty(max(words, 1), dtype=t.int32, device="cuda")
+        z = t.empty(K, dtype=t.complex64, device="cuda") if want_z else None
+        _wcheck(self.lib, self.h, self.lib.rx_wl_process(self.h, x.data_ptr(), n, b.data_ptr(),
+                                                         z.data_ptr() if z is not None else None))
+        return b[:words], z
+
+    process = rx_wl_process
+
+    def rx_wl_reset(self):
+        _wcheck(self.lib, self.h, self.lib.rx_wl_reset(self.h))
+
+    reset = rx_wl_reset
+
+    def rx_wl_profile(self, on=True, reset=False):
+        ms = (ct.c_double * 2)()
+        _wcheck(self.lib, self.h, self.lib.rx_wl_profile(self.h, 1 if on else 0, ms, 1 if reset else 0))
+        return {"acquisition": ms[0], "segments": ms[1]}
+
+    profile = rx_wl_profile
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.rx_wl_destroy(self.h)
+            self.h = None
+
+    rx_wl_destroy = close
 
     def __del__(self):
         try:

@@ -103,3 +103,23 @@ def test_static_filter_phase_term_cancels_the_carrier_dispersion_phase():
         assert abs(abs(H[0]) - 2.0) < 1e-12                 # sqrt(sps) at DC
         assert abs(ph) > 0.05
         assert abs(np.angle(H[0] * np.exp(-1j * ph))) < 1e-9
+
+
+def test_consecutive_buffers_share_the_carrier_phase():
+    # a buffer processed on its own, with its stream index n0, equals the whole-stream
+    # result away from its edges (windows aligned: n0 a multiple of both hops);
+    # with n0 = 0 it would carry the constant rotation exp(-j 2 pi f_c n0 / fs)
+    lk = LK.KKLink(n_sym=1 << 13, adc="f32", snr_db=30.0, L_km=2000.0)
+    g = LK.generate(lk)
+    n = g.samples.shape[0]
+    n0 = n // 2
+    whole, _, V = K.kk_frontend(g.samples, g.in_scale, g.in_offset, lk.baud, lk.sps, lk.carrier_hz, lk.L_km)
+    assert n0 % 512 == 0 and n0 % (1024 - V) == 0
+    second, _, _ = K.kk_frontend(g.samples[n0:], g.in_scale, g.in_offset, lk.baud, lk.sps, lk.carrier_hz,
+                                 lk.L_km, n0=n0)
+    inner = slice(2048, n // 4 - 2048)
+    ref = whole[n0 // 2:][inner]
+    assert np.abs(second[inner] - ref).max() < 1e-9 * np.abs(ref).max()
+    wrong, _, _ = K.kk_frontend(g.samples[n0:], g.in_scale, g.in_offset, lk.baud, lk.sps, lk.carrier_hz, lk.L_km)
+    rot = np.vdot(ref, wrong[inner]) / np.vdot(ref, ref)
+    assert abs(np.angle(rot) - math.remainder(-2 * math.pi * lk.carrier_hz / lk.fs * n0, 2 * math.pi)) < 1e-9
