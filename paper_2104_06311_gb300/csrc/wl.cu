@@ -51,11 +51,10 @@ __device__ __forceinline__ float wl_decide(float v, unsigned &b) {
     b = v < 0.f ? 1u : 0u;                                   // x >= 0 decides +
     return v >= 0.f ? 0.70710678118654752f : -0.70710678118654752f;
   } else {
-    const float t = v * 3.16227766016837933f;
-    const bool outer = fabsf(t) > 2.f;
-    b = (t < 0.f ? 1u : 0u) | (outer ? 2u : 0u);
+    const bool outer = fabsf(v) > 0.63245553203367587f;      // |x sqrt 10| > 2
+    b = (v < 0.f ? 1u : 0u) | (outer ? 2u : 0u);
     const float l = outer ? 0.94868329805051381f : 0.31622776601683793f;   // 3 / sqrt 10, 1 / sqrt 10
-    return t >= 0.f ? l : -l;
+    return v >= 0.f ? l : -l;
   }
 }
 
@@ -150,8 +149,8 @@ struct WlRec {
     }
     unsigned br, bi;
     const float dr = wl_decide<MB>(zr, br), di = wl_decide<MB>(zi, bi);
-    er = mu_s * (dr - zr);
-    ei = mu_s * (di - zi);
+    er = fmaf(mu_s, dr, -mu_s * zr);     // mu_s z beside the decision, one FMA after it
+    ei = fmaf(mu_s, di, -mu_s * zi);
     b = MB == 2 ? (br | (bi << 1)) : (br | (bi << 2));
   }
 
@@ -185,7 +184,7 @@ constexpr int WSUB = 16;                 // symbols per sub-chunk: whole bit wor
 // ring, one chunk ahead of the recursion.  Chunks split into 16-symbol halves,
 // each entirely pretraining or entirely output (p0, s0 and S are multiples of
 // 16), so a full half runs unrolled with its bits gathered in registers.
-template <int MB, bool LINEAR>
+template <int MB, bool LINEAR, bool HAS_Z>
 __global__ void __launch_bounds__(WBLOCK) wl_kernel(const float4 *__restrict__ x4, int64_t K, int64_t s_begin,
                                                     int S, int nseg, int Wp, const WlTaps *__restrict__ taps_in,
                                                     WlTaps *__restrict__ taps_out, uint32_t *__restrict__ bits,
@@ -264,7 +263,7 @@ __global__ void __launch_bounds__(WBLOCK) wl_kernel(const float4 *__restrict__ x
 #pragma unroll
         for (int q = 0; q < WSUB; ++q) {
           st.step(r[q], mu_s, zr, zi, b);
-          if (z) z[start + q] = make_float2(zr, zi);
+          if (HAS_Z) z[start + q] = make_float2(zr, zi);
           w[(q * MB) >> 5] |= b << ((q * MB) & 31);
         }
         uint32_t *bw = bits + ((start * MB) >> 5);
@@ -276,7 +275,7 @@ __global__ void __launch_bounds__(WBLOCK) wl_kernel(const float4 *__restrict__ x
         for (int t = 0; t < WPS; ++t) w[t] = 0u;
         for (int q = 0; q < (int)nv; ++q) {
           st.step(r[q], mu_s, zr, zi, b);
-          if (z) z[start + q] = make_float2(zr, zi);
+          if (HAS_Z) z[start + q] = make_float2(zr, zi);
           if (MB == 2) w[0] |= b << (2 * q);
           else if (q < 8) w[0] |= b << (4 * q);
           else w[WPS - 1] |= b << (4 * (q - 8));
@@ -306,18 +305,23 @@ __global__ void __launch_bounds__(WBLOCK) wl_kernel(const float4 *__restrict__ x
   }
 }
 
-// one launch, modulation and form as template arguments
+// one launch, modulation, form and the optional output as template arguments
+template <int MB, bool LINEAR>
+void launch_wl_mf(unsigned grid, cudaStream_t s, const float4 *x4, int64_t K, int64_t s_begin, int S, int nseg,
+                  int Wp, const WlTaps *tin, WlTaps *tout, uint32_t *bits, float2 *z, float mu) {
+  if (z)
+    wl_kernel<MB, LINEAR, true><<<grid, WBLOCK, 0, s>>>(x4, K, s_begin, S, nseg, Wp, tin, tout, bits, z, mu);
+  else
+    wl_kernel<MB, LINEAR, false><<<grid, WBLOCK, 0, s>>>(x4, K, s_begin, S, nseg, Wp, tin, tout, bits, z, mu);
+}
+
 cudaError_t launch_wl(int mb, bool linear, unsigned grid, cudaStream_t s, const float4 *x4, int64_t K,
                       int64_t s_begin, int S, int nseg, int Wp, const WlTaps *tin, WlTaps *tout, uint32_t *bits,
                       float2 *z, float mu) {
-  if (mb == 2 && !linear)
-    wl_kernel<2, false><<<grid, WBLOCK, 0, s>>>(x4, K, s_begin, S, nseg, Wp, tin, tout, bits, z, mu);
-  else if (mb == 2)
-    wl_kernel<2, true><<<grid, WBLOCK, 0, s>>>(x4, K, s_begin, S, nseg, Wp, tin, tout, bits, z, mu);
-  else if (!linear)
-    wl_kernel<4, false><<<grid, WBLOCK, 0, s>>>(x4, K, s_begin, S, nseg, Wp, tin, tout, bits, z, mu);
-  else
-    wl_kernel<4, true><<<grid, WBLOCK, 0, s>>>(x4, K, s_begin, S, nseg, Wp, tin, tout, bits, z, mu);
+  if (mb == 2 && !linear) launch_wl_mf<2, false>(grid, s, x4, K, s_begin, S, nseg, Wp, tin, tout, bits, z, mu);
+  else if (mb == 2) launch_wl_mf<2, true>(grid, s, x4, K, s_begin, S, nseg, Wp, tin, tout, bits, z, mu);
+  else if (!linear) launch_wl_mf<4, false>(grid, s, x4, K, s_begin, S, nseg, Wp, tin, tout, bits, z, mu);
+  else launch_wl_mf<4, true>(grid, s, x4, K, s_begin, S, nseg, Wp, tin, tout, bits, z, mu);
   return cudaGetLastError();
 }
 
