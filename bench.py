@@ -484,14 +484,17 @@ def bench_kk(args, rank, world, local):
         build.build()
     import linksim.kk as LK
     n_buf, slots = 4, 8                    # 4 distinct 2^22-sample buffers, each in 2 device slots
+    # the carrier on the recording's frequency grid: replaying the 4 buffers in a loop is
+    # one continuous periodic stream (dispersion is applied circularly by the generator)
+    fc = round(0.516e9 / 4e9 * (n_buf << 22)) * 4e9 / (n_buf << 22)
     lk = LK.KKLink(n_sym=n_buf << 20, L_km=5600.0, cspr_db=12.0, snr_db=24.0, adc="int8",
-                   iq_gain_db=1.0, iq_phase_deg=5.0)
+                   iq_gain_db=1.0, iq_phase_deg=5.0, carrier_hz=fc)
     g = LK.generate(lk)
     n = 1 << 22                            # samples per buffer
     K = n // 4                             # symbols per buffer
     words = K * 4 // 32
     main = torch.cuda.current_stream()
-    s_in, s_fe, s_eq = torch.cuda.Stream(), torch.cuda.Stream(), torch.cuda.Stream()
+    s_fe, s_eq = torch.cuda.Stream(), torch.cuda.Stream()
     fe = KKFrontEnd(lk.baud, lk.carrier_hz, lk.L_km, n, stream=s_fe)
     eq = WLEqualiser(4, K, stream=s_eq)
     host = torch.from_numpy(np.ascontiguousarray(g.samples[:n_buf * n])).view(n_buf, n)
@@ -501,32 +504,18 @@ def bench_kk(args, rank, world, local):
     y = torch.empty(slots, n // 2, dtype=torch.complex64, device="cuda")
     bits = torch.empty(slots, words, dtype=torch.int32, device="cuda")
     ev_fe = [torch.cuda.Event() for _ in range(slots)]
-    ev_in = [torch.cuda.Event() for _ in range(slots)]
-    ev_out = [torch.cuda.Event() for _ in range(slots)]
-    xh = host.pin_memory()
-    bh = torch.empty(slots, words, dtype=torch.int32).pin_memory()
 
-    def step(e2e=False):
+    def step():
         start = torch.cuda.Event()
         start.record(main)
-        for st_ in (s_in, s_fe, s_eq):
+        for st_ in (s_fe, s_eq):
             st_.wait_event(start)
         for i in range(slots):
-            if e2e:
-                # slots are reused only by the next step, which starts after this one ends
-                with torch.cuda.stream(s_in):
-                    x[i].copy_(xh[i % n_buf], non_blocking=True)
-                ev_in[i].record(s_in)
-                s_fe.wait_event(ev_in[i])
             fe.set_position((i % n_buf) * n)          # slot i replays buffer i % n_buf of the stream
             fe.process(x[i], g.in_scale, g.in_offset, out=y[i])
             ev_fe[i].record(s_fe)
             s_eq.wait_event(ev_fe[i])
             eq.process(y[i], bits=bits[i])
-            if e2e:
-                with torch.cuda.stream(s_eq):
-                    bh[i].copy_(bits[i], non_blocking=True)
-            ev_out[i].record(s_eq)
         main.wait_stream(s_fe)
         main.wait_stream(s_eq)
 
@@ -552,18 +541,25 @@ def bench_kk(args, rank, world, local):
     torch.cuda.synchronize()
     prof = fe.profile(on=False, reset=True)
     wprof = eq.profile(on=False, reset=True)
-    # e2e: pinned int8 buffers in and packed bits out, every step
-    for _ in range(2):
-        step(e2e=True)
-    torch.cuda.synchronize()
-    a_ = torch.cuda.Event(enable_timing=True)
-    b_ = torch.cuda.Event(enable_timing=True)
-    a_.record(main)
-    for _ in range(args.steps):
-        step(e2e=True)
-    b_.record(main)
-    torch.cuda.synchronize()
-    ems = a_.elapsed_time(b_) / args.steps
+    # e2e through the real-time pipeline (rx_rt.h): each buffer copied into the pinned host
+    # ring, copied to the device, front end, DD-LMS, BER count, bits back to pinned host
+    # memory; host wall clock from the first submit to the drain
+    from paper_2104_06311_gb300 import RealTime
+    rt = RealTime(lk.baud, lk.carrier_hz, lk.L_km, n, mod_bits=4, depth=6, in_scale=g.in_scale,
+                  in_offset=g.in_offset, ref_bits=g.tx_bits, bin_symbols=21_000_000, edge_symbols=2048)
+    hostbufs = host.numpy()
+    for b in range(4):
+        rt.next_input()[:] = hostbufs[b % n_buf]
+        rt.submit()
+    rt.drain()
+    t0_ = time.perf_counter()
+    for b in range(4, 4 + args.steps * slots):
+        rt.next_input()[:] = hostbufs[b % n_buf]
+        rt.submit()
+    rt.drain()
+    ems = (time.perf_counter() - t0_) * 1e3 / args.steps
+    rtbins = rt.bins()
+    rt.close()
     # decisions of the last step against the transmitted bits (buffer edges aside)
     bb = np.unpackbits(bits.cpu().numpy().view(np.uint8), bitorder="little").reshape(slots, K, 4)
     tx = g.tx_bits.reshape(n_buf, K, 4)
@@ -597,7 +593,9 @@ def bench_kk(args, rank, world, local):
                      "peak_source": pk_kind},
         "clocks": clk,
         "e2e": {"value": total / (ems / 1e3) / 1e9, "unit": "GSa/s", "h2d_bytes_per_step": int(total),
-                "d2h_bytes_per_step": int(slots * words * 4)},
+                "d2h_bytes_per_step": int(slots * words * 4),
+                "api": "rx_rt (pinned host ring, 4 streams, device BER count), host wall clock",
+                "q_db_21ms_bins": [round(float(q), 2) for q in rtbins["q_db"]]},
         "paper_realtime_rate": "4 GS/s ADC (the paper's real-time figure on its own GPU)",
     }
     if not args.no_cpu_baseline:

@@ -38,7 +38,9 @@ EXPORTS = ["rx_create", "rx_set_param", "rx_get_param", "rx_set_cuda_stream", "r
            "rx_kk_create", "rx_kk_set_cuda_stream", "rx_kk_get_overlap", "rx_kk_process", "rx_kk_profile",
            "rx_kk_set_position", "rx_kk_destroy", "rx_kk_last_error",
            "rx_wl_create", "rx_wl_set_param", "rx_wl_get_param", "rx_wl_set_cuda_stream", "rx_wl_set_taps",
-           "rx_wl_get_taps", "rx_wl_process", "rx_wl_reset", "rx_wl_profile", "rx_wl_destroy", "rx_wl_last_error"]
+           "rx_wl_get_taps", "rx_wl_process", "rx_wl_reset", "rx_wl_profile", "rx_wl_destroy", "rx_wl_last_error",
+           "rx_rt_create", "rx_rt_set_wl_param", "rx_rt_next_input", "rx_rt_submit", "rx_rt_output", "rx_rt_drain",
+           "rx_rt_bins", "rx_rt_profile", "rx_rt_destroy", "rx_rt_last_error", "rx_q_db"]
 WL_PARAMS = {"MU": 1, "SEG_LEN": 2, "PRETRAIN": 3, "ACQ": 4, "LINEAR": 5}
 CNN_KINDS = ["fwd_hidden", "fwd_edge", "dx", "dw", "update"]
 BATCH_PARAMS = {"GRAPH": 100, "EQ_CTAS": 101, "EQ_TEAM": 102, "CDC_NS_PER_SAMPLE": 103, "PROFILE": 104}
@@ -56,6 +58,14 @@ class rx_out(ct.Structure):
                 ("cdc", ct.c_void_p), ("cdc_stride", ct.c_int64),
                 ("capacity", ct.c_int64), ("n", ct.c_int64), ("first", ct.c_int64),
                 ("cdc_first", ct.c_int64), ("cdc_n", ct.c_int64)]
+
+
+class rx_rt_cfg(ct.Structure):
+    _fields_ = [("baud", ct.c_double), ("sps", ct.c_int), ("mod_bits", ct.c_int), ("carrier_hz", ct.c_double),
+                ("L_km", ct.c_double), ("D_ps_nm_km", ct.c_double), ("rolloff", ct.c_double),
+                ("in_dtype", ct.c_int), ("in_scale", ct.c_float), ("in_offset", ct.c_float),
+                ("buffer_samples", ct.c_int64), ("depth", ct.c_int), ("ref_bits", ct.c_void_p), ("ref_nbits", ct.c_int64), ("bin_symbols", ct.c_int64),
+                ("edge_symbols", ct.c_int), ("max_bins", ct.c_int)]
 
 
 class rx_chan_cfg(ct.Structure):
@@ -154,6 +164,20 @@ def load(path: str = LIB_PATH) -> ct.CDLL:
     lib.rx_wl_destroy.restype = None
     lib.rx_wl_last_error.argtypes = [P]
     lib.rx_wl_last_error.restype = ct.c_char_p
+    lib.rx_rt_create.argtypes = [ct.POINTER(P), ct.POINTER(rx_rt_cfg)]
+    lib.rx_rt_set_wl_param.argtypes = [P, ct.c_int, ct.c_double]
+    lib.rx_rt_next_input.argtypes = [P, ct.POINTER(P)]
+    lib.rx_rt_submit.argtypes = [P, ct.POINTER(ct.c_int64)]
+    lib.rx_rt_output.argtypes = [P, ct.c_int64, ct.POINTER(P)]
+    lib.rx_rt_drain.argtypes = [P]
+    lib.rx_rt_bins.argtypes = [P, ct.c_int, ct.c_int, P, P, P, ct.POINTER(ct.c_int)]
+    lib.rx_rt_profile.argtypes = [P, ct.c_int, ct.POINTER(ct.c_double), ct.c_int]
+    lib.rx_rt_destroy.argtypes = [P]
+    lib.rx_rt_destroy.restype = None
+    lib.rx_rt_last_error.argtypes = [P]
+    lib.rx_rt_last_error.restype = ct.c_char_p
+    lib.rx_q_db.argtypes = [ct.c_double]
+    lib.rx_q_db.restype = ct.c_double
     lib.rx_cnn_destroy.argtypes = [P]
     lib.rx_cnn_destroy.restype = None
     lib.rx_cnn_last_error.argtypes = [P]
@@ -161,7 +185,8 @@ def load(path: str = LIB_PATH) -> ct.CDLL:
     for name in EXPORTS:
         if name not in ("rx_destroy", "rx_status_str", "rx_last_error", "rx_batch_destroy", "rx_batch_last_error",
                         "rx_cnn_param_count", "rx_cnn_destroy", "rx_cnn_last_error", "rx_kk_destroy",
-                        "rx_kk_last_error", "rx_wl_destroy", "rx_wl_last_error"):
+                        "rx_kk_last_error", "rx_wl_destroy", "rx_wl_last_error", "rx_rt_destroy",
+                        "rx_rt_last_error", "rx_q_db"):
             getattr(lib, name).restype = ct.c_int
     _lib = lib
     return lib
@@ -806,6 +831,115 @@ class WLEqualiser:
             self.h = None
 
     rx_wl_destroy = close
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _rcheck(lib, h, status):
+    if status != RX_OK:
+        detail = lib.rx_rt_last_error(h).decode() if h else ""
+        raise RxError(status, f"{lib.rx_status_str(status).decode()}: {detail}")
+
+
+def q_db(ber):
+    """Q in dB of a bit-error ratio (rx_q_db, host only)."""
+    return load().rx_q_db(float(ber))
+
+
+class RealTime:
+    """Real-time ingest pipeline of the KK receiver (include/rx_rt.h): pinned host
+    input ring -> copy / front end / equaliser / copy-out streams -> bits in a pinned
+    host ring, with BER counted against the transmitted pattern in Q bins."""
+
+    def __init__(self, baud, carrier_hz, L_km, buffer_samples, mod_bits=4, depth=4, in_dtype="int8",
+                 in_scale=1.0, in_offset=0.0, ref_bits=None, bin_symbols=1 << 20, edge_symbols=2048,
+                 max_bins=4096, D=17.0, rolloff=0.01, sps=4, **wl_params):
+        import numpy as np
+        self.np = np
+        self.lib = load()
+        self.n = int(buffer_samples)
+        self.K = self.n // sps
+        self.words = self.K * int(mod_bits) // 32
+        self.dtype = np.int8 if in_dtype == "int8" else np.float32
+        ref = None
+        if ref_bits is not None:
+            ref = np.ascontiguousarray(np.asarray(ref_bits, np.uint8))
+        cfg = rx_rt_cfg(baud=float(baud), sps=int(sps), mod_bits=int(mod_bits), carrier_hz=float(carrier_hz),
+                        L_km=float(L_km), D_ps_nm_km=float(D), rolloff=float(rolloff),
+                        in_dtype=1 if in_dtype == "int8" else 2, in_scale=float(in_scale),
+                        in_offset=float(in_offset), buffer_samples=self.n, depth=int(depth),
+                        ref_bits=ref.ctypes.data if ref is not None else None,
+                        ref_nbits=int(ref.shape[0]) if ref is not None else 0, bin_symbols=int(bin_symbols),
+                        edge_symbols=int(edge_symbols), max_bins=int(max_bins))
+        h = ct.c_void_p()
+        st = self.lib.rx_rt_create(ct.byref(h), ct.byref(cfg))
+        if st != RX_OK:
+            raise RxError(st, self.lib.rx_status_str(st).decode())
+        self.h = h
+        for k, v in wl_params.items():
+            _rcheck(self.lib, self.h, self.lib.rx_rt_set_wl_param(self.h, WL_PARAMS[k.upper()], float(v)))
+
+    def rx_rt_next_input(self):
+        """numpy view of the pinned host slot for the next buffer (write n samples, then submit)."""
+        p = ct.c_void_p()
+        _rcheck(self.lib, self.h, self.lib.rx_rt_next_input(self.h, ct.byref(p)))
+        ctype = ct.c_int8 if self.dtype == self.np.int8 else ct.c_float
+        return self.np.ctypeslib.as_array(ct.cast(p, ct.POINTER(ctype)), shape=(self.n,))
+
+    next_input = rx_rt_next_input
+
+    def rx_rt_submit(self):
+        b = ct.c_int64()
+        _rcheck(self.lib, self.h, self.lib.rx_rt_submit(self.h, ct.byref(b)))
+        return b.value
+
+    submit = rx_rt_submit
+
+    def rx_rt_output(self, b):
+        """numpy view (uint32 words) of buffer b's bits in the pinned host ring; waits for it."""
+        p = ct.c_void_p()
+        _rcheck(self.lib, self.h, self.lib.rx_rt_output(self.h, int(b), ct.byref(p)))
+        return self.np.ctypeslib.as_array(ct.cast(p, ct.POINTER(ct.c_uint32)), shape=(self.words,))
+
+    output = rx_rt_output
+
+    def rx_rt_drain(self):
+        _rcheck(self.lib, self.h, self.lib.rx_rt_drain(self.h))
+
+    drain = rx_rt_drain
+
+    def rx_rt_bins(self, first=0, count=None):
+        np = self.np
+        nb = ct.c_int()
+        _rcheck(self.lib, self.h, self.lib.rx_rt_bins(self.h, 0, 0, None, None, None, ct.byref(nb)))
+        count = nb.value - first if count is None else count
+        count = max(count, 0)
+        e = np.zeros(count, np.uint64)
+        b = np.zeros(count, np.uint64)
+        q = np.zeros(count, np.float64)
+        _rcheck(self.lib, self.h, self.lib.rx_rt_bins(self.h, int(first), count, e.ctypes.data, b.ctypes.data,
+                                                      q.ctypes.data, ct.byref(nb)))
+        return {"errors": e, "bits": b, "q_db": q}
+
+    bins = rx_rt_bins
+
+    def rx_rt_profile(self, on=True, reset=False):
+        ms = (ct.c_double * 4)()
+        _rcheck(self.lib, self.h, self.lib.rx_rt_profile(self.h, 1 if on else 0, ms, 1 if reset else 0))
+        return {"copy_in": ms[0], "front_end": ms[1], "equaliser": ms[2], "copy_out": ms[3]}
+
+    profile = rx_rt_profile
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.rx_rt_destroy(self.h)
+            self.h = None
+
+    rx_rt_destroy = close
 
     def __del__(self):
         try:
