@@ -11,15 +11,24 @@
  * Readings (the paper gives the steps, not their constants): the Hilbert image
  * has the response j sign(f) (signal side band below the carrier, minimum-phase
  * field); amplitude sqrt(max(I, 1e-30)); the 100 % overlap-save is N = 1024
- * with overlap N/2, samples outside the buffer count as zero log-amplitude;
+ * with overlap N/2, samples outside the stream count as zero log-amplitude;
  * the static filter is sqrt(sps) times the dispersion inverse
  * exp(-j beta2 L w^2/2) times the RRC matched filter, times the constant
  * exp(+j beta2 L w_c^2/2) that takes back the dispersion phase of the carrier
  * tone the field is referenced to (unit symbol gain, no constant phase: what
  * the paper's offline optimisation from lab data converges to), in N = 1024
  * windows with overlap max(N/2, the textbook CD length); the
- * decimation keeps the bins of |f| < fs/4 and applies a factor 1/2.  A buffer is
- * processed as a whole (zero outside it), like the paper's 2^22-sample buffers.
+ * decimation keeps the bins of |f| < fs/4 and applies a factor 1/2.
+ *
+ * Streaming.  Buffers are consecutive pieces of one stream (the paper's 2^22-
+ * sample ADC buffers): the windows of both stages sit on the stream's sample
+ * grid and reach into the previous buffer (kept as history) and ahead into the
+ * current one, so the output equals the whole stream filtered at once.  The
+ * look-ahead makes the output lag the input by a fixed delay D = 1536 samples
+ * (rx_kk_get_delay): a call with input samples [pos, pos + n) returns output
+ * samples [pos - D, pos - D + n); outputs before the stream start are zero, and
+ * rx_kk_flush returns the last D samples once the stream has ended (the field
+ * outside the stream is zero, as if the stream were filtered whole).
  *
  * Conventions as rx.h: device pointers owned by the caller, status codes, no
  * traps, allocation only in rx_kk_create.
@@ -53,18 +62,27 @@ rx_status rx_kk_set_cuda_stream(rx_kk *k, void *cuda_stream);
 /* Overlap of the static filter's windows (samples at the input rate). */
 rx_status rx_kk_get_overlap(rx_kk *k, int *overlap);
 
-/* The next buffer of the stream: n input samples (n even, <= max_samples) ->
- * y: n/2 complex floats (re, im) at 2 samples per symbol; field (optional, may
- * be NULL): the rebuilt field shifted to DC at the input rate, n complex floats.
- * The shift to DC runs on the stream's sample count (sample m of the buffer is
- * stream sample pos + m, pos = the samples of all earlier calls since create, or
- * as set by rx_kk_set_position), so consecutive buffers share one carrier phase.  Device
+/* The next buffer of the stream: n input samples (a multiple of 512, <= max_samples)
+ * -> y: output samples [pos - D, pos - D + n) at 2 samples per symbol, n/2 complex
+ * floats (re, im); field (optional, may be NULL): the rebuilt field shifted to DC,
+ * at the input rate, over the same samples, n complex floats.  Sample m of the
+ * buffer is stream sample pos + m, pos = the samples of all earlier calls since
+ * the stream started (create, rx_kk_flush, or rx_kk_set_position); the shift to
+ * DC runs on that index, so consecutive buffers share one carrier phase.  Device
  * pointers; y and field 8-byte aligned.  Asynchronous on the bound stream. */
 rx_status rx_kk_process(rx_kk *k, const void *in, int dtype, int64_t n, float in_scale, float in_offset,
                         float *y, float *field);
 
-/* Stream index of the next buffer's first sample (>= 0; 0 restarts the
- * stream, another value replays a buffer recorded at that position). */
+/* End of the stream: y (D/2 complex floats) and field (optional, D complex
+ * floats) get the last D output samples [pos - D, pos); the next call starts a
+ * new stream at sample 0. */
+rx_status rx_kk_flush(rx_kk *k, float *y, float *field);
+
+/* The output delay D in samples at the input rate (1536). */
+rx_status rx_kk_get_delay(rx_kk *k, int *delay);
+
+/* Start a new stream whose first sample has index pos (>= 0): nothing before it
+ * is used, outputs before it are zero. */
 rx_status rx_kk_set_position(rx_kk *k, int64_t pos);
 
 /* Per-stage device time (ms; [0] Hilbert + field rebuild, [1] static filter)

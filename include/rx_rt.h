@@ -19,11 +19,15 @@
  * so that the copies, the front end of buffer b + 1 and the equaliser of buffer b
  * overlap.
  *
- * BER: symbol k of buffer b is stream symbol b K + k (K = n / sps); its bits are
- * compared with the reference pattern, repeated from stream symbol 0, bit for bit;
- * edge_symbols symbols at each end of every buffer are not counted (each buffer is
- * filtered as a whole).  Bin i holds stream symbols [i B, (i + 1) B), B =
- * bin_symbols; Q_dB = 20 log10(sqrt(2) erfcinv(2 BER)).
+ * The front end streams with a fixed delay of D samples (rx_kk.h), so output
+ * symbol k of buffer b is stream symbol b K - D / sps + k (K = n / sps); symbols
+ * before the stream start are not counted, and rx_rt_flush delivers the last
+ * D / sps symbols once the input has ended.
+ *
+ * BER: every counted symbol's bits are compared with the reference pattern,
+ * repeated from stream symbol 0, bit for bit; edge_symbols symbols at each end of
+ * every block may be left out.  Bin i holds stream symbols [i B, (i + 1) B),
+ * B = bin_symbols; Q_dB = 20 log10(sqrt(2) erfcinv(2 BER)).
  *
  * Conventions as rx.h: status codes, no traps; allocation only in rx_rt_create;
  * one host thread per handle.
@@ -48,13 +52,13 @@ typedef struct {
   double rolloff;           /* RRC roll-off                                            */
   int in_dtype;             /* RX_KK_I8 or RX_KK_F32 (rx_kk.h)                         */
   float in_scale, in_offset;/* intensity = (sample + in_offset) * in_scale             */
-  int64_t buffer_samples;   /* n: samples per buffer, a multiple of 16 sps             */
+  int64_t buffer_samples;   /* n: samples per buffer, a multiple of 512                */
   int depth;                /* buffers in flight (ring slots), 2..16                   */
   const uint8_t *ref_bits;  /* host, one bit per byte: the transmitted pattern (copied
                                at create); NULL: no BER counting                       */
   int64_t ref_nbits;        /* pattern length, a multiple of 32                        */
   int64_t bin_symbols;      /* symbols per Q bin, a multiple of 16                     */
-  int edge_symbols;         /* symbols not counted at each buffer end, multiple of 16  */
+  int edge_symbols;         /* symbols not counted at each block end, multiple of 16   */
   int max_bins;             /* bins kept (later symbols are not counted)               */
 } rx_rt_cfg;
 
@@ -71,6 +75,11 @@ rx_status rx_rt_next_input(rx_rt *rt, void **host_slot);
 /* Enqueue the buffer written into the slot from rx_rt_next_input; returns its
  * index b (0, 1, ...).  Does not wait for the GPU. */
 rx_status rx_rt_submit(rx_rt *rt, int64_t *index);
+
+/* End of the input: the front end's last D samples go through the equaliser and
+ * the count as one more (short) block, D / sps symbols, with index *index; no
+ * buffer can follow. */
+rx_status rx_rt_flush(rx_rt *rt, int64_t *index);
 
 /* Decided bits of buffer b (K m bits packed LSB-first in uint32 words, as rx_wl.h)
  * in the pinned host ring; waits for that buffer.  Valid until buffer b + depth is

@@ -6,8 +6,9 @@
  * DD-LMS equaliser in widely-linear form, and its decisions are demapped).
  *
  * Definition (the paper names the method; the constants are readings):
- *   z_k = sum_{i<T} h[i] x[2k+c-i] + g[i] conj(x[2k+c-i]),  T = 4, c = 1,
- *   x = 0 outside the buffer;  start h[c] = 1, the rest 0;
+ *   z_k = sum_{i<T} h[i] x[2k+c-i] + g[i] conj(x[2k+c-i]),  T = 4, c = 1;
+ *   before the buffer x continues with the previous buffer's last two samples
+ *   (zero for the first buffer), after it x = 0;  start h[c] = 1, the rest 0;
  *   e_k = dec(z_k) - z_k on the unit-energy square QPSK / 16QAM grid;
  *   after every symbol h[i] += mu e_k conj(x[2k+c-i]), g[i] += mu e_k x[2k+c-i]
  *   (the strictly linear variant keeps g = 0).
@@ -68,7 +69,7 @@ rx_status rx_wl_get_taps(rx_wl *w, double *taps);
  * n = 0 is a no-op. */
 rx_status rx_wl_process(rx_wl *w, const float *x, int64_t n, uint32_t *bits, float *z);
 
-/* Back to the start taps and a new acquisition. */
+/* Back to the start taps and a new acquisition (no previous samples). */
 rx_status rx_wl_reset(rx_wl *w);
 
 /* Device time (ms; [0] acquisition, [1] segment waves) of the calls since the

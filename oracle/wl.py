@@ -10,7 +10,8 @@ constants):
 
   * Four taps per branch at T/2 spacing on the regressor x and on its
     conjugate: z_k = sum_i h[i] x[2k+c-i] + g[i] conj(x[2k+c-i]), i = 0..T-1,
-    c = (T-1)//2, x = 0 outside the buffer.  Start: h[c] = 1, all else 0 (the
+    c = (T-1)//2; before the buffer x continues with the previous buffer's last
+    samples (zero for the first buffer), after it x = 0.  Start: h[c] = 1, all else 0 (the
     static filter delivers unit gain and no constant phase).
   * Decision-directed error e_k = dec(z_k) - z_k on the unit-energy square
     constellation; the LMS step after every symbol (the textbook, sequential
@@ -53,22 +54,26 @@ def initial_taps(T: int) -> np.ndarray:
     return w
 
 
-def _regressor(x: np.ndarray, k: int, T: int) -> np.ndarray:
-    """x[2k+c-i] for i = 0..T-1, zero outside the buffer."""
+def _regressor(x: np.ndarray, k: int, T: int, tail: np.ndarray) -> np.ndarray:
+    """x[2k+c-i] for i = 0..T-1: tail[len(tail) + n] for n < 0 (the previous buffer's
+    last samples), zero past the buffer."""
     c = (T - 1) // 2
     u = np.zeros(T, np.complex128)
     for i in range(T):
         n = 2 * k + c - i
         if 0 <= n < x.shape[0]:
             u[i] = x[n]
+        elif -tail.shape[0] <= n < 0:
+            u[i] = tail[tail.shape[0] + n]
     return u
 
 
-def _run(x: np.ndarray, w: np.ndarray, k0: int, k1: int, p: WLParams, z: np.ndarray | None) -> np.ndarray:
+def _run(x: np.ndarray, w: np.ndarray, k0: int, k1: int, p: WLParams, z: np.ndarray | None,
+         tail: np.ndarray) -> np.ndarray:
     """Symbols k0..k1-1 in order from taps w (copied); z[k] written when z is given."""
     h, g = w[0].copy(), (np.zeros_like(w[1]) if p.linear else w[1].copy())
     for k in range(k0, k1):
-        u = _regressor(x, k, p.ntaps)
+        u = _regressor(x, k, p.ntaps, tail)
         zk = np.dot(h, u) + np.dot(g, np.conj(u))
         e = decide(np.array([zk]), p.mod)[0] - zk
         h += p.mu * e * np.conj(u)
@@ -83,6 +88,7 @@ def _run(x: np.ndarray, w: np.ndarray, k0: int, k1: int, p: WLParams, z: np.ndar
 class WLState:
     taps: np.ndarray
     acquired: bool = False
+    tail: np.ndarray = dataclasses.field(default_factory=lambda: np.zeros(2, np.complex128))
 
 
 def wl_equalise(x: np.ndarray, p: WLParams, state: WLState | None = None):
@@ -97,14 +103,16 @@ def wl_equalise(x: np.ndarray, p: WLParams, state: WLState | None = None):
     K = x.shape[0] // 2
     z = np.zeros(K, np.complex128)
     w = state.taps
+    tail = state.tail
     a0 = 0
     if not state.acquired:
         a0 = min(p.acq, K)
-        w = _run(x, w, 0, a0, p, z)
+        w = _run(x, w, 0, a0, p, z, tail)
     end = w
     for s0 in range(a0, K, p.seg_len):
         s1 = min(s0 + p.seg_len, K)
-        pre = _run(x, w, max(0, s0 - p.pretrain), s0, p, None)
-        end = _run(x, pre, s0, s1, p, z)
+        pre = _run(x, w, max(0, s0 - p.pretrain), s0, p, None, tail)
+        end = _run(x, pre, s0, s1, p, z, tail)
     bits = hard_bits(z, p.mod)
-    return z, bits, WLState(end, True)
+    new_tail = x[-2:].copy() if x.shape[0] >= 2 else tail.copy()
+    return z, bits, WLState(end, True, new_tail)

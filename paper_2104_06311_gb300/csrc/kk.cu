@@ -29,23 +29,46 @@ namespace {
 constexpr int KN = 1024;          // transform length of both stages
 constexpr int KH = KN / 2;        // Hilbert overlap and hop (100 % overlap-save)
 constexpr int KN2 = KN / 2;       // decimated transform length
+constexpr int KDELAY = 1536;      // output delay (samples): the look-ahead of both stages (1280), rounded to 512
+constexpr int KHIST = 3072;       // input history kept from earlier buffers (samples)
+constexpr int KEDGE = 1024;       // field computed beyond the output range on each side
 
-__global__ void __launch_bounds__(KN / 16) kk_hilbert_kernel(const void *__restrict__ in, int dtype, int64_t n,
-                                                             float scale, float offset, const float2 *__restrict__ tw,
-                                                             unsigned long long inc_q, unsigned long long ph0,
-                                                             float2 *__restrict__ E) {
+// Where stream sample s comes from: the current buffer [pos, pos + n), the history
+// of earlier buffers [pos - KHIST, pos) (float intensities), or nothing (before the
+// stream start or at / after its end: outside, zero log-amplitude and zero field).
+struct KkSrc {
+  const void *in;
+  int dtype;
+  int64_t pos, n;
+  float scale, offset;
+  const float *hist;
+  int64_t start, end;
+};
+
+__device__ __forceinline__ bool kk_inside(const KkSrc &src, int64_t s) { return s >= src.start && s < src.end; }
+
+__device__ __forceinline__ float kk_intensity(const KkSrc &src, int64_t s) {
+  if (s >= src.pos) {
+    const int64_t m = s - src.pos;
+    const float x = src.dtype == RX_KK_I8 ? (float)reinterpret_cast<const int8_t *>(src.in)[m]
+                                          : reinterpret_cast<const float *>(src.in)[m];
+    return (x + src.offset) * src.scale;
+  }
+  return src.hist[s - (src.pos - KHIST)];
+}
+
+// Window b: the field of stream samples [e0 + 512 b, e0 + 512 b + 512) from the
+// input over [e0 + 512 b - 256, e0 + 512 b + 768), written to E[s - e0].
+__global__ void __launch_bounds__(KN / 16) kk_hilbert_kernel(KkSrc src, int64_t e0, const float2 *__restrict__ tw,
+                                                             unsigned long long inc_q, float2 *__restrict__ E) {
   __shared__ float2 buf[KN + KN / 32];
   const int t = threadIdx.x;
-  const int64_t lo = (int64_t)blockIdx.x * KH - KH / 2;
-  auto intensity = [&](int64_t m) -> float {
-    const float x = dtype == RX_KK_I8 ? (float)reinterpret_cast<const int8_t *>(in)[m]
-                                      : reinterpret_cast<const float *>(in)[m];
-    return (x + offset) * scale;
-  };
+  const int64_t s0 = e0 + (int64_t)blockIdx.x * KH;   // first kept sample
+  const int64_t lo = s0 - KH / 2;
   for (int m = t; m < KN; m += blockDim.x) {
-    const int64_t nn = lo + m;
-    float la = 0.f;                              // outside the buffer: zero log-amplitude
-    if (nn >= 0 && nn < n) la = logf(sqrtf(fmaxf(intensity(nn), 1e-30f)));
+    const int64_t s = lo + m;
+    float la = 0.f;                              // outside the stream: zero log-amplitude
+    if (kk_inside(src, s)) la = logf(sqrtf(fmaxf(kk_intensity(src, s), 1e-30f)));
     buf[pad(m)] = make_float2(la, 0.f);
   }
   __syncthreads();
@@ -64,36 +87,48 @@ __global__ void __launch_bounds__(KN / 16) kk_hilbert_kernel(const void *__restr
   __syncthreads();
   fft_forward<KN, 16>(buf, t, tw);
   for (int m = KH / 2 + t; m < KH / 2 + KH; m += blockDim.x) {
-    const int64_t nn = (int64_t)blockIdx.x * KH + (m - KH / 2);
-    if (nn >= n) break;
-    const float phi = buf[pad(m)].x;             // real part of the inverse
-    const float a = sqrtf(fmaxf(intensity(nn), 1e-30f));
-    float sp, cp;
-    sincosf(phi, &sp, &cp);
-    // exp(j 2 pi f_c (pos + n) / fs), pos = the buffer's first sample in the stream: the top
-    // 24 bits of the Q0.64 turn ph0 + n inc_q (ph0 = pos inc_q mod 2^64)
-    const unsigned long long ph = ph0 + (unsigned long long)nn * inc_q;
-    const float turns = (float)(ph >> 40) * 5.9604644775390625e-08f;   // 2^-24
-    float ss, cs;
-    sincospif(2.f * turns, &ss, &cs);
-    const float ex = a * cp, ey = a * sp;
-    E[nn] = make_float2(ex * cs - ey * ss, ex * ss + ey * cs);
+    const int64_t s = s0 + (m - KH / 2);
+    float2 e = make_float2(0.f, 0.f);            // outside the stream: zero field
+    if (kk_inside(src, s)) {
+      const float phi = buf[pad(m)].x;           // real part of the inverse
+      const float a = sqrtf(fmaxf(kk_intensity(src, s), 1e-30f));
+      float sp, cp;
+      sincosf(phi, &sp, &cp);
+      // exp(j 2 pi f_c s / fs) at stream sample s: the top 24 bits of the Q0.64 turn s inc_q
+      const unsigned long long ph = (unsigned long long)s * inc_q;
+      const float turns = (float)(ph >> 40) * 5.9604644775390625e-08f;   // 2^-24
+      float ss, cs;
+      sincospif(2.f * turns, &ss, &cs);
+      const float ex = a * cp, ey = a * sp;
+      e = make_float2(ex * cs - ey * ss, ex * ss + ey * cs);
+    }
+    E[s - e0] = e;
   }
 }
 
-__global__ void __launch_bounds__(32) kk_filter_kernel(const float2 *__restrict__ E, int64_t n, int V,
+// Window i0 + b of the static filter: E over [i S - V/2, i S - V/2 + 1024) (E[s - e0]),
+// output samples t in [i S, i S + S) inside [o0, o0 + no) at 2 samples/symbol to
+// y[(t - o0)/2] (zero before the stream start); optionally the field itself to
+// field[t - o0] for every t of the range.
+__global__ void __launch_bounds__(32) kk_filter_kernel(const float2 *__restrict__ E, int64_t e0, int64_t i0, int64_t o0,
+                                                       int64_t no, int64_t start, int V,
                                                        const float2 *__restrict__ H, const float2 *__restrict__ tw,
-                                                       const float2 *__restrict__ tw2, float2 *__restrict__ y) {
+                                                       const float2 *__restrict__ tw2, float2 *__restrict__ y,
+                                                       float2 *__restrict__ field) {
   __shared__ float2 buf[KN + KN / 32];
   __shared__ float2 buf2[KN2 + KN2 / 32];
   const int t = threadIdx.x;
   const int S = KN - V;
-  const int64_t lo = (int64_t)blockIdx.x * S - V / 2;
-  for (int m = t; m < KN; m += 32) {
-    const int64_t nn = lo + m;
-    buf[pad(m)] = (nn >= 0 && nn < n) ? E[nn] : make_float2(0.f, 0.f);
-  }
+  const int64_t i = i0 + blockIdx.x;
+  const int64_t lo = i * S - V / 2;
+  for (int m = t; m < KN; m += 32) buf[pad(m)] = E[lo + m - e0];
   __syncthreads();
+  if (field) {
+    for (int m = V / 2 + t; m < V / 2 + S; m += 32) {
+      const int64_t tt = lo + m;
+      if (tt >= o0 && tt < o0 + no) field[tt - o0] = buf[pad(m)];
+    }
+  }
   fft_forward<KN, 32>(buf, t, tw);
   // keep |f| < fs/4: bins k < 256 -> k, k >= 768 -> k - 512; conjugate for the inverse
   for (int k = t; k < KN; k += 32) {
@@ -103,12 +138,19 @@ __global__ void __launch_bounds__(32) kk_filter_kernel(const float2 *__restrict_
   }
   __syncthreads();
   fft_forward<KN2, 16>(buf2, t, tw2);
-  const int64_t out0 = (int64_t)blockIdx.x * (S / 2);
   for (int m = V / 4 + t; m < V / 4 + S / 2; m += 32) {
-    const int64_t o = out0 + (m - V / 4);
-    if (o >= n / 2) break;
-    y[o] = cconj(buf2[pad(m)]);
+    const int64_t tt = i * S + 2 * (m - V / 4);      // input-rate sample of this output
+    if (tt < o0 || tt >= o0 + no) continue;
+    y[(tt - o0) / 2] = tt >= start ? cconj(buf2[pad(m)]) : make_float2(0.f, 0.f);
   }
+}
+
+// History for the next buffer: intensities of stream samples [pos + n - KHIST, pos + n).
+__global__ void kk_hist_kernel(KkSrc src, float *__restrict__ next) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= KHIST) return;
+  const int64_t s = src.pos + src.n - KHIST + j;
+  next[j] = kk_intensity(src, s);   // entries before the stream start are never read
 }
 
 }  // namespace
@@ -122,8 +164,11 @@ struct rx_kk {
   int64_t max_n = 0;
   unsigned long long inc_q = 0;
   int64_t pos = 0;                  // stream position of the next buffer's first sample
+  int64_t start = 0;                // first sample of the current stream
   cudaStream_t stream = nullptr;
   float2 *tw = nullptr, *tw2 = nullptr, *H = nullptr, *Hs = nullptr, *E = nullptr;
+  float *hist[2] = {nullptr, nullptr};   // input history ping-pong (KHIST intensities each)
+  int cur = 0;
   bool profile = false;
   std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> pending;
   double ms[2] = {0, 0};
@@ -143,7 +188,10 @@ void kk_release(rx_kk *k) {
   cudaFree(k->H);
   cudaFree(k->Hs);
   cudaFree(k->E);
+  cudaFree(k->hist[0]);
+  cudaFree(k->hist[1]);
   k->tw = k->tw2 = k->H = k->Hs = k->E = nullptr;
+  k->hist[0] = k->hist[1] = nullptr;
   std::vector<cudaEvent_t> seen;     // consecutive stages share an event
   for (auto &p : k->pending)
     for (cudaEvent_t ev : {p.second.first, p.second.second})
@@ -185,7 +233,11 @@ rx_status rx_kk_create(rx_kk **out, double baud, int sps, double carrier_hz, dou
   if (e == cudaSuccess) e = cudaMalloc(&k->tw2, KN2 * sizeof(float2));
   if (e == cudaSuccess) e = cudaMalloc(&k->Hs, KN * sizeof(float2));
   if (e == cudaSuccess) e = cudaMalloc(&k->H, KN * sizeof(float2));
-  if (e == cudaSuccess) e = cudaMalloc(&k->E, (size_t)max_samples * sizeof(float2));
+  // field scratch: the output range plus KEDGE on each side (a flush covers KDELAY)
+  if (e == cudaSuccess)
+    e = cudaMalloc(&k->E, (size_t)(std::max<int64_t>(max_samples, KDELAY) + 2 * KEDGE) * sizeof(float2));
+  if (e == cudaSuccess) e = cudaMalloc(&k->hist[0], KHIST * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc(&k->hist[1], KHIST * sizeof(float));
   if (e != cudaSuccess) {
     cudaGetLastError();
     kk_release(k);
@@ -233,30 +285,36 @@ rx_status rx_kk_get_overlap(rx_kk *k, int *v) {
   return RX_OK;
 }
 
-rx_status rx_kk_process(rx_kk *k, const void *in, int dtype, int64_t n, float in_scale, float in_offset, float *y,
-                        float *field) {
-  if (!k) return RX_EINVAL;
-  if (n < 0 || n % 2 || n > k->max_n) return kfail(k, RX_EINVAL, "sample count must be even and within max_samples");
-  if (dtype != RX_KK_I8 && dtype != RX_KK_F32) return kfail(k, RX_EINVAL, "unknown input dtype");
-  if (n == 0) return RX_OK;
-  if (!in || !y) return kfail(k, RX_EINVAL, "null input or output");
-  if ((uintptr_t)y % 8 || (field && (uintptr_t)field % 8) || (dtype == RX_KK_F32 && (uintptr_t)in % 4))
-    return kfail(k, RX_EINVAL, "misaligned buffer");
-  float2 *E = field ? reinterpret_cast<float2 *>(field) : k->E;
+}  // extern "C"
+
+namespace {
+
+int64_t floor_div(int64_t a, int64_t b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
+
+// Output samples [pos - KDELAY, pos - KDELAY + no) of the stream whose input is
+// known on [start, end): Hilbert windows over the field range with KEDGE on each
+// side, then the static filter's windows over the output range.
+rx_status kk_run(rx_kk *k, const KkSrc &src, int64_t no, float *y, float *field) {
   cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
   if (k->profile)
     for (auto &e : ev)
       if (cudaEventCreate(&e) != cudaSuccess) return kfail(k, RX_ECUDA, "event");
+  const int64_t o0 = k->pos - KDELAY, e0 = o0 - KEDGE;
   if (ev[0]) cudaEventRecord(ev[0], k->stream);
-  const unsigned g1 = (unsigned)((n + KH - 1) / KH);
-  kk_hilbert_kernel<<<g1, KN / 16, 0, k->stream>>>(in, dtype, n, in_scale, in_offset, k->tw, k->inc_q,
-                                                   (unsigned long long)k->pos * k->inc_q, E);
+  const unsigned g1 = (unsigned)((no + 2 * KEDGE) / KH);
+  kk_hilbert_kernel<<<g1, KN / 16, 0, k->stream>>>(src, e0, k->tw, k->inc_q, k->E);
   cudaError_t e = cudaGetLastError();
   if (ev[1]) cudaEventRecord(ev[1], k->stream);
   const int S = KN - k->V;
-  const unsigned g2 = (unsigned)((n + S - 1) / S);
+  const int64_t i0 = floor_div(o0, S), i1 = floor_div(o0 + no - 1, S);
   if (e == cudaSuccess) {
-    kk_filter_kernel<<<g2, 32, 0, k->stream>>>(E, n, k->V, k->H, k->tw, k->tw2, reinterpret_cast<float2 *>(y));
+    kk_filter_kernel<<<(unsigned)(i1 - i0 + 1), 32, 0, k->stream>>>(
+        k->E, e0, i0, o0, no, k->start, k->V, k->H, k->tw, k->tw2, reinterpret_cast<float2 *>(y),
+        reinterpret_cast<float2 *>(field));
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess && src.n > 0) {
+    kk_hist_kernel<<<(KHIST + 255) / 256, 256, 0, k->stream>>>(src, k->hist[1 - k->cur]);
     e = cudaGetLastError();
   }
   if (ev[2]) {
@@ -265,14 +323,52 @@ rx_status rx_kk_process(rx_kk *k, const void *in, int dtype, int64_t n, float in
     k->pending.push_back({1, {ev[1], ev[2]}});
   }
   if (e != cudaSuccess) return kfail(k, RX_ECUDA, std::string("launch: ") + cudaGetErrorString(e));
+  return RX_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+rx_status rx_kk_process(rx_kk *k, const void *in, int dtype, int64_t n, float in_scale, float in_offset, float *y,
+                        float *field) {
+  if (!k) return RX_EINVAL;
+  if (n < 0 || n % KH || n > k->max_n)
+    return kfail(k, RX_EINVAL, "sample count must be a multiple of 512 and within max_samples");
+  if (dtype != RX_KK_I8 && dtype != RX_KK_F32) return kfail(k, RX_EINVAL, "unknown input dtype");
+  if (n == 0) return RX_OK;
+  if (!in || !y) return kfail(k, RX_EINVAL, "null input or output");
+  if ((uintptr_t)y % 8 || (field && (uintptr_t)field % 8) || (dtype == RX_KK_F32 && (uintptr_t)in % 4))
+    return kfail(k, RX_EINVAL, "misaligned buffer");
+  KkSrc src{in, dtype, k->pos, n, in_scale, in_offset, k->hist[k->cur], k->start, k->pos + n};
+  const rx_status s = kk_run(k, src, n, y, field);
+  if (s != RX_OK) return s;
+  k->cur = 1 - k->cur;
   k->pos += n;
+  return RX_OK;
+}
+
+rx_status rx_kk_flush(rx_kk *k, float *y, float *field) {
+  if (!k) return RX_EINVAL;
+  if (!y) return kfail(k, RX_EINVAL, "null output");
+  if ((uintptr_t)y % 8 || (field && (uintptr_t)field % 8)) return kfail(k, RX_EINVAL, "misaligned buffer");
+  KkSrc src{nullptr, RX_KK_F32, k->pos, 0, 1.f, 0.f, k->hist[k->cur], k->start, k->pos};
+  const rx_status s = kk_run(k, src, KDELAY, y, field);
+  if (s != RX_OK) return s;
+  k->pos = k->start = 0;     // the stream has ended: the next call starts a new one at 0
+  return RX_OK;
+}
+
+rx_status rx_kk_get_delay(rx_kk *k, int *delay) {
+  if (!k || !delay) return RX_EINVAL;
+  *delay = KDELAY;
   return RX_OK;
 }
 
 rx_status rx_kk_set_position(rx_kk *k, int64_t pos) {
   if (!k) return RX_EINVAL;
   if (pos < 0) return kfail(k, RX_EINVAL, "stream position must be >= 0");
-  k->pos = pos;
+  k->pos = k->start = pos;
   return RX_OK;
 }
 

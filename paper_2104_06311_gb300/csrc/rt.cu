@@ -62,6 +62,8 @@ struct rx_rt {
   unsigned long long *err = nullptr;    // device error counters per bin
   std::vector<unsigned long long> counted;   // counted bits per bin (host bookkeeping)
   int64_t next = 0;                     // index of the next buffer
+  int64_t delay_sym = 0;                // front-end delay in symbols
+  bool ended = false;                   // rx_rt_flush ran
   bool have_slot = false;
   bool profile = false;
   std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> pending;
@@ -117,12 +119,12 @@ void rt_release(rx_rt *r) {
   for (int i = 0; i < 4; ++i) r->st[i] = nullptr;
 }
 
-// counted bits per bin of buffer b: symbols [b K + edge, (b + 1) K - edge)
-void count_bits(rx_rt *r, int64_t b) {
+// counted bits per bin of output symbols [sym0 + edge, sym0 + nsym - edge), stream symbols >= 0
+void count_bits(rx_rt *r, int64_t sym0, int64_t nsym) {
   if (!r->ref) return;
   const int64_t B = r->cfg.bin_symbols, m = r->cfg.mod_bits;
-  int64_t s = b * r->K + r->cfg.edge_symbols;
-  const int64_t e = (b + 1) * r->K - r->cfg.edge_symbols;
+  int64_t s = std::max<int64_t>(sym0 + r->cfg.edge_symbols, 0);
+  const int64_t e = sym0 + nsym - r->cfg.edge_symbols;
   while (s < e) {
     const int64_t bin = s / B;
     const int64_t hi = std::min(e, (bin + 1) * B);
@@ -131,6 +133,26 @@ void count_bits(rx_rt *r, int64_t b) {
     r->counted[bin] += (unsigned long long)((hi - s) * m);
     s = hi;
   }
+}
+
+// Errors of one output block (nsym symbols from stream symbol sym0, bits in `bits`)
+// into the bins, on the equaliser stream; counted bits on the host.
+cudaError_t count_block(rx_rt *r, const uint32_t *bits, int64_t sym0, int64_t nsym) {
+  if (!r->ref) return cudaSuccess;
+  const int m = r->cfg.mod_bits;
+  const int s_per_w = 32 / m;
+  const int64_t words = nsym / s_per_w;
+  int64_t w0 = (int64_t)r->cfg.edge_symbols / s_per_w;
+  const int64_t w1 = words - w0;
+  if (sym0 < 0) w0 = std::max<int64_t>(w0, (-sym0 + s_per_w - 1) / s_per_w);   // not before the stream start
+  if (w0 >= w1) return cudaSuccess;
+  // pattern word of this block's word 0 (sym0 m is a multiple of 32), reduced to [0, ref_words)
+  int64_t ref_w0 = (int64_t)(((__int128)sym0 * m / 32) % r->ref_words);
+  if (ref_w0 < 0) ref_w0 += r->ref_words;
+  rt_count_kernel<<<64, 256, 0, r->st[2]>>>(bits, r->ref, r->ref_words, ref_w0, w0, w1, s_per_w, sym0,
+                                            r->cfg.bin_symbols, r->cfg.max_bins, r->err);
+  count_bits(r, sym0, nsym);
+  return cudaGetLastError();
 }
 
 }  // namespace
@@ -157,7 +179,7 @@ rx_status rx_rt_create(rx_rt **out, const rx_rt_cfg *cfg) {
   const rx_rt_cfg &c = *cfg;
   if (!(c.baud > 0) || c.sps != 4 || (c.mod_bits != 2 && c.mod_bits != 4) ||
       (c.in_dtype != RX_KK_I8 && c.in_dtype != RX_KK_F32) || c.buffer_samples <= 0 ||
-      c.buffer_samples % (16 * c.sps) || c.depth < 2 || c.depth > 16 || c.edge_symbols < 0 ||
+      c.buffer_samples % 512 || c.depth < 2 || c.depth > 16 || c.edge_symbols < 0 ||
       c.edge_symbols % 16 || c.max_bins < 0)
     return RX_EINVAL;
   if (c.ref_bits && (c.ref_nbits <= 0 || c.ref_nbits % 32 || c.bin_symbols <= 0 || c.bin_symbols % 16))
@@ -186,6 +208,11 @@ rx_status rx_rt_create(rx_rt **out, const rx_rt_cfg *cfg) {
   if (s != RX_OK) return bail(s, "equaliser");
   rx_kk_set_cuda_stream(r->kk, r->st[1]);
   rx_wl_set_cuda_stream(r->wl, r->st[2]);
+  {
+    int d = 0;
+    rx_kk_get_delay(r->kk, &d);
+    r->delay_sym = d / c.sps;     // 1536 / 4 = 384: a multiple of 16 symbols, whole bit words
+  }
   const int D = c.depth;
   r->host_in.assign(D, nullptr);
   r->host_bits.assign(D, nullptr);
@@ -249,6 +276,7 @@ rx_status rx_rt_next_input(rx_rt *r, void **slot) {
 rx_status rx_rt_submit(rx_rt *r, int64_t *index) {
   if (!r) return RX_EINVAL;
   if (!r->have_slot) return rfail(r, RX_ESTATE, "rx_rt_next_input first");
+  if (r->ended) return rfail(r, RX_ESTATE, "the stream has ended (rx_rt_flush)");
   const int D = r->cfg.depth;
   const int64_t b = r->next;
   const int k = (int)(b % D);
@@ -277,7 +305,6 @@ rx_status rx_rt_submit(rx_rt *r, int64_t *index) {
   r->have_slot = false;
   r->next = b + 1;
   mark(2, 1);
-  rx_kk_set_position(r->kk, b * r->n);
   rx_status s = rx_kk_process(r->kk, r->dev_in[k], r->cfg.in_dtype, r->n, r->cfg.in_scale, r->cfg.in_offset,
                               r->dev_y[k], nullptr);
   if (s != RX_OK) return rfail(r, s, std::string("front end: ") + rx_kk_last_error(r->kk));
@@ -290,18 +317,10 @@ rx_status rx_rt_submit(rx_rt *r, int64_t *index) {
   mark(4, 2);
   s = rx_wl_process(r->wl, r->dev_y[k], r->n / 2, r->dev_bits[k], nullptr);
   if (s != RX_OK) return rfail(r, s, std::string("equaliser: ") + rx_wl_last_error(r->wl));
-  if (r->ref) {
-    const int m = r->cfg.mod_bits;
-    const int s_per_w = 32 / m;
-    const int64_t w0 = (int64_t)r->cfg.edge_symbols / s_per_w, w1 = r->words - w0;
-    // stream bit offset of this buffer, in words, modulo the pattern
-    const int64_t ref_w0 = (int64_t)(((__int128)b * r->words) % r->ref_words);
-    rt_count_kernel<<<64, 256, 0, r->st[2]>>>(r->dev_bits[k], r->ref, r->ref_words, ref_w0, w0, w1, s_per_w,
-                                              b * r->K, r->cfg.bin_symbols, r->cfg.max_bins, r->err);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return rcuda(r, e, "count");
-    count_bits(r, b);
-  }
+  // the front end's output lags its input by delay samples: output symbol k of buffer b
+  // is stream symbol b K - delay / sps + k
+  e = count_block(r, r->dev_bits[k], b * r->K - r->delay_sym, r->K);
+  if (e != cudaSuccess) return rcuda(r, e, "count");
   mark(5, 2);
   e = cudaEventRecord(r->ev[2][k], r->st[2]);
   // copy out
@@ -314,6 +333,44 @@ rx_status rx_rt_submit(rx_rt *r, int64_t *index) {
   if (e != cudaSuccess) return rcuda(r, e, "enqueue equaliser");
   if (r->profile)
     for (int i = 0; i < 4; ++i) r->pending.push_back({i, {pe[2 * i], pe[2 * i + 1]}});
+  if (index) *index = b;
+  return RX_OK;
+}
+
+rx_status rx_rt_flush(rx_rt *r, int64_t *index) {
+  if (!r) return RX_EINVAL;
+  if (r->ended) return rfail(r, RX_ESTATE, "the stream has ended already");
+  if (r->next == 0) return rfail(r, RX_ESTATE, "no buffer was submitted");
+  const int D = r->cfg.depth;
+  const int64_t b = r->next;
+  const int k = (int)(b % D);
+  // the slot's earlier buffer must be through every stage
+  if (r->slot_buffer[k] >= 0) {
+    rx_status s = rcuda(r, cudaEventSynchronize(r->ev[3][k]), "wait for the slot");
+    if (s != RX_OK) return s;
+  }
+  cudaError_t e = cudaStreamWaitEvent(r->st[1], r->ev[1][(b - 1) % D], 0);
+  if (e != cudaSuccess) return rcuda(r, e, "enqueue flush");
+  rx_status s = rx_kk_flush(r->kk, r->dev_y[k], nullptr);
+  if (s != RX_OK) return rfail(r, s, std::string("front end: ") + rx_kk_last_error(r->kk));
+  e = cudaEventRecord(r->ev[1][k], r->st[1]);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(r->st[2], r->ev[1][k], 0);
+  if (e != cudaSuccess) return rcuda(r, e, "enqueue flush");
+  const int64_t nsym = r->delay_sym;     // the last delay samples: delay / 2 at 2 sps
+  s = rx_wl_process(r->wl, r->dev_y[k], 2 * nsym, r->dev_bits[k], nullptr);
+  if (s != RX_OK) return rfail(r, s, std::string("equaliser: ") + rx_wl_last_error(r->wl));
+  e = count_block(r, r->dev_bits[k], b * r->K - r->delay_sym, nsym);
+  if (e == cudaSuccess) e = cudaEventRecord(r->ev[2][k], r->st[2]);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(r->st[3], r->ev[2][k], 0);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(r->host_bits[k], r->dev_bits[k], (size_t)nsym * r->cfg.mod_bits / 8, cudaMemcpyDeviceToHost,
+                        r->st[3]);
+  if (e == cudaSuccess) e = cudaEventRecord(r->ev[3][k], r->st[3]);
+  if (e == cudaSuccess) e = cudaEventRecord(r->ev[0][k], r->st[3]);
+  if (e != cudaSuccess) return rcuda(r, e, "enqueue flush");
+  r->slot_buffer[k] = b;
+  r->next = b + 1;
+  r->ended = true;
   if (index) *index = b;
   return RX_OK;
 }

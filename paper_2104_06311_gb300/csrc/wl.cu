@@ -188,7 +188,7 @@ template <int MB, bool LINEAR, bool HAS_Z>
 __global__ void __launch_bounds__(WBLOCK) wl_kernel(const float4 *__restrict__ x4, int64_t K, int64_t s_begin,
                                                     int S, int nseg, int Wp, const WlTaps *__restrict__ taps_in,
                                                     WlTaps *__restrict__ taps_out, uint32_t *__restrict__ bits,
-                                                    float2 *__restrict__ z, float mu) {
+                                                    float2 *__restrict__ z, float mu, const float4 *__restrict__ tail) {
   __shared__ __align__(16) float4 ring[2][WBLOCK][WROW];
   constexpr int WPS = WSUB * MB / 32;    // bit words per sub-chunk: 1 (QPSK) or 2 (16QAM)
   const int lane = threadIdx.x;
@@ -226,11 +226,12 @@ __global__ void __launch_bounds__(WBLOCK) wl_kernel(const float4 *__restrict__ x
       st.m[i][2] = hi;
     }
   }
-  // regressor history x[2 p0 - 1], x[2 p0 - 2] (zero before the buffer); no pending update
+  // regressor history x[2 p0 - 1], x[2 p0 - 2]: before the buffer, the previous
+  // buffer's last two samples; no pending update
 #pragma unroll
   for (int i = 0; i < WT; ++i) st.u[i][0] = st.u[i][1] = 0.f;
-  if (live && p0 > 0) {
-    const float4 h = __ldg(&x4[p0 - 1]);
+  if (live) {
+    const float4 h = p0 > 0 ? __ldg(&x4[p0 - 1]) : *tail;
     st.u[1][0] = h.x; st.u[1][1] = h.y;   // x[2 p0 - 2]
     st.u[0][0] = h.z; st.u[0][1] = h.w;   // x[2 p0 - 1]
   }
@@ -308,20 +309,20 @@ __global__ void __launch_bounds__(WBLOCK) wl_kernel(const float4 *__restrict__ x
 // one launch, modulation, form and the optional output as template arguments
 template <int MB, bool LINEAR>
 void launch_wl_mf(unsigned grid, cudaStream_t s, const float4 *x4, int64_t K, int64_t s_begin, int S, int nseg,
-                  int Wp, const WlTaps *tin, WlTaps *tout, uint32_t *bits, float2 *z, float mu) {
+                  int Wp, const WlTaps *tin, WlTaps *tout, uint32_t *bits, float2 *z, float mu, const float4 *tail) {
   if (z)
-    wl_kernel<MB, LINEAR, true><<<grid, WBLOCK, 0, s>>>(x4, K, s_begin, S, nseg, Wp, tin, tout, bits, z, mu);
+    wl_kernel<MB, LINEAR, true><<<grid, WBLOCK, 0, s>>>(x4, K, s_begin, S, nseg, Wp, tin, tout, bits, z, mu, tail);
   else
-    wl_kernel<MB, LINEAR, false><<<grid, WBLOCK, 0, s>>>(x4, K, s_begin, S, nseg, Wp, tin, tout, bits, z, mu);
+    wl_kernel<MB, LINEAR, false><<<grid, WBLOCK, 0, s>>>(x4, K, s_begin, S, nseg, Wp, tin, tout, bits, z, mu, tail);
 }
 
 cudaError_t launch_wl(int mb, bool linear, unsigned grid, cudaStream_t s, const float4 *x4, int64_t K,
                       int64_t s_begin, int S, int nseg, int Wp, const WlTaps *tin, WlTaps *tout, uint32_t *bits,
-                      float2 *z, float mu) {
-  if (mb == 2 && !linear) launch_wl_mf<2, false>(grid, s, x4, K, s_begin, S, nseg, Wp, tin, tout, bits, z, mu);
-  else if (mb == 2) launch_wl_mf<2, true>(grid, s, x4, K, s_begin, S, nseg, Wp, tin, tout, bits, z, mu);
-  else if (!linear) launch_wl_mf<4, false>(grid, s, x4, K, s_begin, S, nseg, Wp, tin, tout, bits, z, mu);
-  else launch_wl_mf<4, true>(grid, s, x4, K, s_begin, S, nseg, Wp, tin, tout, bits, z, mu);
+                      float2 *z, float mu, const float4 *tail) {
+  if (mb == 2 && !linear) launch_wl_mf<2, false>(grid, s, x4, K, s_begin, S, nseg, Wp, tin, tout, bits, z, mu, tail);
+  else if (mb == 2) launch_wl_mf<2, true>(grid, s, x4, K, s_begin, S, nseg, Wp, tin, tout, bits, z, mu, tail);
+  else if (!linear) launch_wl_mf<4, false>(grid, s, x4, K, s_begin, S, nseg, Wp, tin, tout, bits, z, mu, tail);
+  else launch_wl_mf<4, true>(grid, s, x4, K, s_begin, S, nseg, Wp, tin, tout, bits, z, mu, tail);
   return cudaGetLastError();
 }
 
@@ -340,6 +341,7 @@ struct rx_wl {
   bool acquired = false;
   WlTaps start{};            // host copy of the start taps (matrix form)
   WlTaps *dev = nullptr;     // [0], [1]: wave-start taps ping-pong; [2]: acquisition end
+  float4 *tail = nullptr;    // the previous buffer's last two samples (zero for the first)
   int cur = 0;               // which of dev[0..1] holds the taps for the next call
   cudaStream_t stream = nullptr;
   bool profile = false;
@@ -380,6 +382,7 @@ void from_matrix(const WlTaps &o, double *t) {
 
 rx_status upload_start(rx_wl *w) {
   cudaError_t e = cudaMemcpyAsync(&w->dev[0], &w->start, sizeof(WlTaps), cudaMemcpyHostToDevice, w->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(w->tail, 0, sizeof(float4), w->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(w->stream);
   if (e != cudaSuccess) return wfail(w, RX_ECUDA, std::string("taps upload: ") + cudaGetErrorString(e));
   w->cur = 0;
@@ -411,13 +414,15 @@ rx_status rx_wl_create(rx_wl **out, int mod_bits, int ntaps, int64_t max_symbols
   double t[4 * WT] = {0};
   t[2 * WC] = 1.0;
   w->start = to_matrix(t);
-  if (cudaMalloc(&w->dev, 3 * sizeof(WlTaps)) != cudaSuccess) {
+  if (cudaMalloc(&w->dev, 3 * sizeof(WlTaps)) != cudaSuccess || cudaMalloc(&w->tail, sizeof(float4)) != cudaSuccess) {
     cudaGetLastError();
+    cudaFree(w->dev);
     delete w;
     return RX_ENOMEM;
   }
   if (upload_start(w) != RX_OK) {
     cudaFree(w->dev);
+    cudaFree(w->tail);
     delete w;
     return RX_ECUDA;
   }
@@ -517,7 +522,7 @@ rx_status rx_wl_process(rx_wl *w, const float *x, int64_t n, uint32_t *bits, flo
     a0 = std::min<int64_t>(w->A, K);
     if (a0 > 0) {
       e = launch_wl(w->mb, w->linear, 1, w->stream, x4, K, 0, (int)a0, 1, 0, from, &w->dev[2], bits, z2,
-                    (float)w->mu);
+                    (float)w->mu, w->tail);
       from = &w->dev[2];
     }
     w->acquired = true;
@@ -529,13 +534,15 @@ rx_status rx_wl_process(rx_wl *w, const float *x, int64_t n, uint32_t *bits, flo
     const int64_t nseg = (rest + w->S - 1) / w->S;
     const unsigned grid = (unsigned)((nseg + WBLOCK - 1) / WBLOCK);
     e = launch_wl(w->mb, w->linear, grid, w->stream, x4, K, a0, w->S, (int)nseg, w->W, from, &w->dev[nxt], bits,
-                  z2, (float)w->mu);
+                  z2, (float)w->mu, w->tail);
     w->cur = nxt;
   } else if (e == cudaSuccess && a0 > 0) {
     // the whole call was acquisition: its end taps start the next call
     e = cudaMemcpyAsync(&w->dev[nxt], &w->dev[2], sizeof(WlTaps), cudaMemcpyDeviceToDevice, w->stream);
     w->cur = nxt;
   }
+  // this buffer's last two samples continue the next buffer's first regressor
+  if (e == cudaSuccess) e = cudaMemcpyAsync(w->tail, x4 + (K - 1), sizeof(float4), cudaMemcpyDeviceToDevice, w->stream);
   if (ev[2]) {
     cudaEventRecord(ev[2], w->stream);
     w->pending.push_back({0, {ev[0], ev[1]}});
@@ -575,6 +582,7 @@ void rx_wl_destroy(rx_wl *w) {
   cudaStreamSynchronize(w->stream);
   drop_events(w);
   cudaFree(w->dev);
+  cudaFree(w->tail);
   delete w;
 }
 

@@ -36,10 +36,10 @@ EXPORTS = ["rx_create", "rx_set_param", "rx_get_param", "rx_set_cuda_stream", "r
            "rx_cnn_set_cuda_stream", "rx_cnn_apply", "rx_cnn_grads", "rx_cnn_train_step", "rx_cnn_destroy",
            "rx_cnn_last_error", "rx_cnn_set_profile", "rx_cnn_profile", "rx_cnn_set_option",
            "rx_kk_create", "rx_kk_set_cuda_stream", "rx_kk_get_overlap", "rx_kk_process", "rx_kk_profile",
-           "rx_kk_set_position", "rx_kk_destroy", "rx_kk_last_error",
+           "rx_kk_set_position", "rx_kk_flush", "rx_kk_get_delay", "rx_kk_destroy", "rx_kk_last_error",
            "rx_wl_create", "rx_wl_set_param", "rx_wl_get_param", "rx_wl_set_cuda_stream", "rx_wl_set_taps",
            "rx_wl_get_taps", "rx_wl_process", "rx_wl_reset", "rx_wl_profile", "rx_wl_destroy", "rx_wl_last_error",
-           "rx_rt_create", "rx_rt_set_wl_param", "rx_rt_next_input", "rx_rt_submit", "rx_rt_output", "rx_rt_drain",
+           "rx_rt_create", "rx_rt_set_wl_param", "rx_rt_next_input", "rx_rt_submit", "rx_rt_flush", "rx_rt_output", "rx_rt_drain",
            "rx_rt_bins", "rx_rt_profile", "rx_rt_destroy", "rx_rt_last_error", "rx_q_db"]
 WL_PARAMS = {"MU": 1, "SEG_LEN": 2, "PRETRAIN": 3, "ACQ": 4, "LINEAR": 5}
 CNN_KINDS = ["fwd_hidden", "fwd_edge", "dx", "dw", "update"]
@@ -147,6 +147,8 @@ def load(path: str = LIB_PATH) -> ct.CDLL:
     lib.rx_kk_process.argtypes = [P, P, ct.c_int, ct.c_int64, ct.c_float, ct.c_float, P, P]
     lib.rx_kk_profile.argtypes = [P, ct.c_int, ct.POINTER(ct.c_double), ct.c_int]
     lib.rx_kk_set_position.argtypes = [P, ct.c_int64]
+    lib.rx_kk_flush.argtypes = [P, P, P]
+    lib.rx_kk_get_delay.argtypes = [P, ct.POINTER(ct.c_int)]
     lib.rx_kk_destroy.argtypes = [P]
     lib.rx_kk_destroy.restype = None
     lib.rx_kk_last_error.argtypes = [P]
@@ -169,6 +171,7 @@ def load(path: str = LIB_PATH) -> ct.CDLL:
     lib.rx_rt_next_input.argtypes = [P, ct.POINTER(P)]
     lib.rx_rt_submit.argtypes = [P, ct.POINTER(ct.c_int64)]
     lib.rx_rt_output.argtypes = [P, ct.c_int64, ct.POINTER(P)]
+    lib.rx_rt_flush.argtypes = [P, ct.POINTER(ct.c_int64)]
     lib.rx_rt_drain.argtypes = [P]
     lib.rx_rt_bins.argtypes = [P, ct.c_int, ct.c_int, P, P, P, ct.POINTER(ct.c_int)]
     lib.rx_rt_profile.argtypes = [P, ct.c_int, ct.POINTER(ct.c_double), ct.c_int]
@@ -700,8 +703,26 @@ class KKFrontEnd:
         _kcheck(self.lib, self.h, self.lib.rx_kk_get_overlap(self.h, ct.byref(v)))
         return v.value
 
+    @property
+    def delay(self):
+        v = ct.c_int()
+        _kcheck(self.lib, self.h, self.lib.rx_kk_get_delay(self.h, ct.byref(v)))
+        return v.value
+
+    def rx_kk_flush(self, field=False, out=None):
+        """The last `delay` output samples of the stream -> (y at 2 sps, field or None)."""
+        t = self.torch
+        d = self.delay
+        y = out if out is not None else t.empty(d // 2, dtype=t.complex64, device="cuda")
+        f = t.empty(d, dtype=t.complex64, device="cuda") if field else None
+        _kcheck(self.lib, self.h, self.lib.rx_kk_flush(self.h, y.data_ptr(), f.data_ptr() if f is not None else None))
+        return y, f
+
+    flush = rx_kk_flush
+
     def rx_kk_process(self, samples, in_scale=1.0, in_offset=0.0, field=False, out=None):
-        """samples: 1-D int8 or float32 CUDA tensor -> (y at 2 sps, field at the input rate or None)."""
+        """samples: 1-D int8 or float32 CUDA tensor (a multiple of 512 long) -> (y at 2 sps,
+        field at the input rate or None), both `delay` samples behind the input."""
         t = self.torch
         assert samples.is_cuda and samples.is_contiguous() and samples.dim() == 1
         n = samples.shape[0]
@@ -856,7 +877,7 @@ class RealTime:
     host ring, with BER counted against the transmitted pattern in Q bins."""
 
     def __init__(self, baud, carrier_hz, L_km, buffer_samples, mod_bits=4, depth=4, in_dtype="int8",
-                 in_scale=1.0, in_offset=0.0, ref_bits=None, bin_symbols=1 << 20, edge_symbols=2048,
+                 in_scale=1.0, in_offset=0.0, ref_bits=None, bin_symbols=1 << 20, edge_symbols=0,
                  max_bins=4096, D=17.0, rolloff=0.01, sps=4, **wl_params):
         import numpy as np
         self.np = np
@@ -898,6 +919,14 @@ class RealTime:
         return b.value
 
     submit = rx_rt_submit
+
+    def rx_rt_flush(self):
+        """End of the input: the last delayed symbols as one more block; returns its index."""
+        b = ct.c_int64()
+        _rcheck(self.lib, self.h, self.lib.rx_rt_flush(self.h, ct.byref(b)))
+        return b.value
+
+    flush = rx_rt_flush
 
     def rx_rt_output(self, b):
         """numpy view (uint32 words) of buffer b's bits in the pinned host ring; waits for it."""

@@ -4,7 +4,9 @@ recording's frequency grid, so that replaying them in a loop is one continuous
 stream) fed buffer after buffer through the pinned host ring.  Checked: every
 bin's device error count and counted bits against an independent count from the
 bits delivered to host memory, Q per bin from the BER, and that the pipeline keeps
-up with the paper's 4 GS/s ADC from host memory to decided bits in host memory."""
+up with the paper's 4 GS/s ADC from host memory to decided bits in host memory.
+The front end streams (no symbol is lost at buffer boundaries): with the flush,
+every stream symbol is counted exactly once."""
 import math
 import time
 
@@ -39,7 +41,7 @@ def link():
 def _pipeline(lk, g, bin_symbols, depth=4):
     from paper_2104_06311_gb300 import RealTime
     return RealTime(lk.baud, lk.carrier_hz, lk.L_km, N, mod_bits=4, depth=depth, in_scale=g.in_scale,
-                    in_offset=g.in_offset, ref_bits=g.tx_bits, bin_symbols=bin_symbols, edge_symbols=2048)
+                    in_offset=g.in_offset, ref_bits=g.tx_bits, bin_symbols=bin_symbols)
 
 
 def test_bins_match_an_independent_count(link):
@@ -59,10 +61,16 @@ def test_bins_match_an_independent_count(link):
         if b >= 1:
             got.append((b - 1, rt.output(b - 1).copy()))
     got.append((n_buf - 1, rt.output(n_buf - 1).copy()))
+    bf = rt.flush()                          # the front end's last delayed symbols
+    assert bf == n_buf
+    D = 384                                  # front-end delay in symbols (1536 samples / 4)
+    got.append((bf, rt.output(bf)[:D * 4 // 32].copy()))
     for b, words in got:
-        bits = np.unpackbits(words.view(np.uint8), bitorder="little").reshape(K, 4)
-        k = np.arange(2048, K - 2048)
-        s = b * K + k
+        nk = words.shape[0] * 32 // 4
+        bits = np.unpackbits(words.view(np.uint8), bitorder="little").reshape(nk, 4)
+        k = np.arange(nk)
+        s = b * K - D + k                    # stream symbol of output symbol k
+        k, s = k[s >= 0], s[s >= 0]
         e = np.count_nonzero(bits[k] != tx[s % (N_REC * K)], axis=1)
         for bin_ in np.unique(s // B):
             sel = (s // B) == bin_
@@ -71,6 +79,7 @@ def test_bins_match_an_independent_count(link):
     res = rt.bins()
     nb = len(res["errors"])
     assert nb == max(cnt) + 1
+    assert sum(cnt.values()) == 4 * n_buf * K    # every symbol of the stream, once
     for i in range(nb):
         assert int(res["errors"][i]) == err.get(i, 0), i
         assert int(res["bits"][i]) == cnt.get(i, 0), i

@@ -112,7 +112,7 @@ def test_segment_schedule_is_local():
     assert np.array_equal(sty.taps, st.taps)
     # the next call starts from the end state: with mu = 0 it is a fixed filter
     p0 = W.WLParams(mod="16qam", mu=0.0, seg_len=S, pretrain=Wp, acq=1024)
-    z2, _, _ = W.wl_equalise(x, p0, st)
+    z2, _, _ = W.wl_equalise(x, p0, W.WLState(st.taps, True))     # no previous samples
     full = np.convolve(x, st.taps[0]) + np.convolve(np.conj(x), st.taps[1])
     assert np.abs(z2 - full[2 * np.arange(K) + 1]).max() < 1e-12
 
@@ -140,3 +140,23 @@ def test_awgn_ber_16qam_matches_theory():
     half = 2.576 * math.sqrt(pb * (1 - pb) / n)
     assert err >= 200
     assert abs(err / n - pb) < half, (err / n, pb, half)
+
+
+def test_previous_buffer_samples_continue_the_regressor():
+    # two calls on the halves of x equal one call on x when the second call sees
+    # the first's last samples and starts from its taps: check at mu = 0 against
+    # the plain convolution of the whole x
+    rng = np.random.default_rng(21)
+    K = 600
+    x = rng.standard_normal(2 * K) + 1j * rng.standard_normal(2 * K)
+    taps = rng.standard_normal((2, 4)) + 1j * rng.standard_normal((2, 4))
+    p = W.WLParams(mod="qpsk", mu=0.0, seg_len=64, pretrain=16, acq=0)
+    z1, _, st = W.wl_equalise(x[:K], p, W.WLState(taps.copy()))
+    z2, _, _ = W.wl_equalise(x[K:], p, st)
+    full = np.convolve(x, taps[0]) + np.convolve(np.conj(x), taps[1])
+    z = np.concatenate([z1, z2])
+    # symbol k reads x[2k-2 .. 2k+1]: within its own buffer except the 2 samples before it
+    assert np.abs(z - full[2 * np.arange(K) + 1]).max() < 1e-12
+    # without the previous samples the first symbol of the second half would differ
+    z2b, _, _ = W.wl_equalise(x[K:], p, W.WLState(st.taps, True))
+    assert abs(z2b[0] - z2[0]) > 1e-3 and np.array_equal(z2b[1:], z2[1:])
