@@ -32,7 +32,8 @@
 //   A  FIR: each lane keeps its 8 window samples u_q[2k+c-i] in registers and
 //      forms its partial sum; a 2-level xor reduction gives y to the quad.
 //   B  DD only: each lane evaluates |y e^{-j phi_b} - dec(.)|^2 for the 8
-//      angles b = 8 part + a of its symbol; a 3-level reduce-scatter over the
+//      angles b = 8 part + a of its symbol (QPSK: the equivalent -(|Re| + |Im|)
+//      of the rotated symbol); a 3-level reduce-scatter over the
 //      warp's 8 symbols leaves angle 8 part + j in lane (j, part); CTA
 //      barrier; every warp sums the 4 warp partials and takes the argmin
 //      (smallest b on ties); e = y - dec(y e^{-j theta}) e^{j theta}.
@@ -347,7 +348,12 @@ __device__ __forceinline__ void run_span(const Hot hot, EqSmem &sm, const Span s
       if (!sp.cma) {
         float d[8];
 #pragma unroll
-        for (int a = 0; a < 8; ++a) d[a] = act ? qam_dist<MB>(cmul(yv, ln.rot[a])) : 0.f;
+        for (int a = 0; a < 8; ++a) {
+          const float2 w = cmul(yv, ln.rot[a]);
+          // QPSK: |w - dec w|^2 = |y|^2 + 1 - sqrt2 (|Re w| + |Im w|), and |y|^2 is the same
+          // for every angle, so -(|Re w| + |Im w|) orders the angles alike
+          d[a] = act ? (MB == 2 ? -(fabsf(w.x) + fabsf(w.y)) : qam_dist<MB>(w)) : 0.f;
+        }
         float e1[4], e2[2];
 #pragma unroll
         for (int a = 0; a < 4; ++a) {
@@ -365,7 +371,9 @@ __device__ __forceinline__ void run_span(const Hot hot, EqSmem &sm, const Span s
         __syncthreads();  // (1)
         fo_pair();
         const float D = (sm.bps[0][ln.lane] + sm.bps[1][ln.lane]) + (sm.bps[2][ln.lane] + sm.bps[3][ln.lane]);
-        const unsigned key = __float_as_uint(D);
+        // order-preserving key of a float (the QPSK cost is negative)
+        const unsigned u = __float_as_uint(D);
+        const unsigned key = (u & 0x80000000u) ? ~u : (u | 0x80000000u);
         const unsigned mn = __reduce_min_sync(FULL, key);
         const int bstar = __ffs(__ballot_sync(FULL, key == mn)) - 1;
         eth = make_float2(__shfl_sync(FULL, ln.rot_b.x, bstar), -__shfl_sync(FULL, ln.rot_b.y, bstar));
