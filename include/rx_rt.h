@@ -76,6 +76,12 @@ rx_status rx_rt_next_input(rx_rt *rt, void **host_slot);
  * index b (0, 1, ...).  Does not wait for the GPU. */
 rx_status rx_rt_submit(rx_rt *rt, int64_t *index);
 
+/* Enqueue a buffer straight from the caller's host memory (n samples of
+ * in_dtype; pinned, e.g. the ADC driver's DMA buffer, for an asynchronous copy):
+ * no staging copy.  The caller keeps the samples unchanged until rx_rt_output of
+ * this buffer (or rx_rt_drain) returns.  Returns the buffer index. */
+rx_status rx_rt_submit_from(rx_rt *rt, const void *host_samples, int64_t *index);
+
 /* End of the input: the front end's last D samples go through the equaliser and
  * the count as one more (short) block, D / sps symbols, with index *index; no
  * buffer can follow. */

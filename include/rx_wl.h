@@ -38,7 +38,7 @@ typedef struct rx_wl rx_wl;
  * (or after rx_wl_reset), else RX_ESTATE. */
 enum {
   RX_WL_MU = 1,        /* LMS step mu (default 1e-3)                                  */
-  RX_WL_SEG_LEN = 2,   /* segment length S, symbols, multiple of 16 (default 1024)    */
+  RX_WL_SEG_LEN = 2,   /* segment length S, symbols, multiple of 16 (default 256)     */
   RX_WL_PRETRAIN = 3,  /* pretraining W, symbols, multiple of 16 (default 128)        */
   RX_WL_ACQ = 4,       /* acquisition span A, symbols, multiple of 16 (default 8192)  */
   RX_WL_LINEAR = 5     /* 1: strictly linear equaliser, g held at 0 (default 0)       */

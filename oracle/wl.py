@@ -41,7 +41,7 @@ class WLParams:
     mod: str = "16qam"
     ntaps: int = 4
     mu: float = 1e-3
-    seg_len: int = 1024
+    seg_len: int = 256
     pretrain: int = 128
     acq: int = 8192
     linear: bool = False

@@ -59,7 +59,7 @@ __device__ __forceinline__ float kk_intensity(const KkSrc &src, int64_t s) {
 
 // Window b: the field of stream samples [e0 + 512 b, e0 + 512 b + 512) from the
 // input over [e0 + 512 b - 256, e0 + 512 b + 768), written to E[s - e0].
-__global__ void __launch_bounds__(KN / 16) kk_hilbert_kernel(KkSrc src, int64_t e0, const float2 *__restrict__ tw,
+__global__ void __launch_bounds__(KN / 16, 10) kk_hilbert_kernel(KkSrc src, int64_t e0, const float2 *__restrict__ tw,
                                                              unsigned long long inc_q, float2 *__restrict__ E) {
   __shared__ float2 buf[KN + KN / 32];
   const int t = threadIdx.x;
@@ -110,7 +110,7 @@ __global__ void __launch_bounds__(KN / 16) kk_hilbert_kernel(KkSrc src, int64_t 
 // output samples t in [i S, i S + S) inside [o0, o0 + no) at 2 samples/symbol to
 // y[(t - o0)/2] (zero before the stream start); optionally the field itself to
 // field[t - o0] for every t of the range.
-__global__ void __launch_bounds__(32) kk_filter_kernel(const float2 *__restrict__ E, int64_t e0, int64_t i0, int64_t o0,
+__global__ void __launch_bounds__(32, 20) kk_filter_kernel(const float2 *__restrict__ E, int64_t e0, int64_t i0, int64_t o0,
                                                        int64_t no, int64_t start, int V,
                                                        const float2 *__restrict__ H, const float2 *__restrict__ tw,
                                                        const float2 *__restrict__ tw2, float2 *__restrict__ y,

@@ -273,10 +273,12 @@ rx_status rx_rt_next_input(rx_rt *r, void **slot) {
   return RX_OK;
 }
 
-rx_status rx_rt_submit(rx_rt *r, int64_t *index) {
-  if (!r) return RX_EINVAL;
-  if (!r->have_slot) return rfail(r, RX_ESTATE, "rx_rt_next_input first");
-  if (r->ended) return rfail(r, RX_ESTATE, "the stream has ended (rx_rt_flush)");
+}  // extern "C"
+
+namespace {
+
+// One buffer through the four stages; src = the host samples to copy in.
+rx_status rt_enqueue(rx_rt *r, const void *src, int64_t *index) {
   const int D = r->cfg.depth;
   const int64_t b = r->next;
   const int k = (int)(b % D);
@@ -294,7 +296,7 @@ rx_status rx_rt_submit(rx_rt *r, int64_t *index) {
   if (reused) e = cudaStreamWaitEvent(r->st[0], r->ev[1][k], 0);
   mark(0, 0);
   if (e == cudaSuccess)
-    e = cudaMemcpyAsync(r->dev_in[k], r->host_in[k], r->in_bytes, cudaMemcpyHostToDevice, r->st[0]);
+    e = cudaMemcpyAsync(r->dev_in[k], src, r->in_bytes, cudaMemcpyHostToDevice, r->st[0]);
   mark(1, 0);
   if (e == cudaSuccess) e = cudaEventRecord(r->ev[0][k], r->st[0]);
   // front end: after the copy; the field slot is free once the equaliser of b - D is done
@@ -335,6 +337,25 @@ rx_status rx_rt_submit(rx_rt *r, int64_t *index) {
     for (int i = 0; i < 4; ++i) r->pending.push_back({i, {pe[2 * i], pe[2 * i + 1]}});
   if (index) *index = b;
   return RX_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+rx_status rx_rt_submit(rx_rt *r, int64_t *index) {
+  if (!r) return RX_EINVAL;
+  if (!r->have_slot) return rfail(r, RX_ESTATE, "rx_rt_next_input first");
+  if (r->ended) return rfail(r, RX_ESTATE, "the stream has ended (rx_rt_flush)");
+  return rt_enqueue(r, r->host_in[r->next % r->cfg.depth], index);
+}
+
+rx_status rx_rt_submit_from(rx_rt *r, const void *host_samples, int64_t *index) {
+  if (!r || !host_samples) return RX_EINVAL;
+  if (r->ended) return rfail(r, RX_ESTATE, "the stream has ended (rx_rt_flush)");
+  if (r->cfg.in_dtype == RX_KK_F32 && (uintptr_t)host_samples % 4) return rfail(r, RX_EINVAL, "misaligned buffer");
+  // device slots are reused in order; the GPU-side event waits in rt_enqueue order them
+  return rt_enqueue(r, host_samples, index);
 }
 
 rx_status rx_rt_flush(rx_rt *r, int64_t *index) {

@@ -335,7 +335,7 @@ struct rx_wl {
   int mb = 2;
   int64_t max_k = 0;
   double mu = 1e-3;
-  int S = 1024, W = 128, A = 8192;
+  int S = 256, W = 128, A = 8192;
   bool linear = false;
   bool started = false;      // a call since create / reset
   bool acquired = false;

@@ -39,7 +39,7 @@ EXPORTS = ["rx_create", "rx_set_param", "rx_get_param", "rx_set_cuda_stream", "r
            "rx_kk_set_position", "rx_kk_flush", "rx_kk_get_delay", "rx_kk_destroy", "rx_kk_last_error",
            "rx_wl_create", "rx_wl_set_param", "rx_wl_get_param", "rx_wl_set_cuda_stream", "rx_wl_set_taps",
            "rx_wl_get_taps", "rx_wl_process", "rx_wl_reset", "rx_wl_profile", "rx_wl_destroy", "rx_wl_last_error",
-           "rx_rt_create", "rx_rt_set_wl_param", "rx_rt_next_input", "rx_rt_submit", "rx_rt_flush", "rx_rt_output", "rx_rt_drain",
+           "rx_rt_create", "rx_rt_set_wl_param", "rx_rt_next_input", "rx_rt_submit", "rx_rt_submit_from", "rx_rt_flush", "rx_rt_output", "rx_rt_drain",
            "rx_rt_bins", "rx_rt_profile", "rx_rt_destroy", "rx_rt_last_error", "rx_q_db"]
 WL_PARAMS = {"MU": 1, "SEG_LEN": 2, "PRETRAIN": 3, "ACQ": 4, "LINEAR": 5}
 CNN_KINDS = ["fwd_hidden", "fwd_edge", "dx", "dw", "update"]
@@ -172,6 +172,7 @@ def load(path: str = LIB_PATH) -> ct.CDLL:
     lib.rx_rt_submit.argtypes = [P, ct.POINTER(ct.c_int64)]
     lib.rx_rt_output.argtypes = [P, ct.c_int64, ct.POINTER(P)]
     lib.rx_rt_flush.argtypes = [P, ct.POINTER(ct.c_int64)]
+    lib.rx_rt_submit_from.argtypes = [P, P, ct.POINTER(ct.c_int64)]
     lib.rx_rt_drain.argtypes = [P]
     lib.rx_rt_bins.argtypes = [P, ct.c_int, ct.c_int, P, P, P, ct.POINTER(ct.c_int)]
     lib.rx_rt_profile.argtypes = [P, ct.c_int, ct.POINTER(ct.c_double), ct.c_int]
@@ -919,6 +920,16 @@ class RealTime:
         return b.value
 
     submit = rx_rt_submit
+
+    def rx_rt_submit_from(self, samples):
+        """Enqueue a buffer from the caller's host memory (a contiguous numpy array or
+        pinned CPU tensor of n samples), kept unchanged until its output is read."""
+        ptr = samples.data_ptr() if hasattr(samples, "data_ptr") else samples.ctypes.data
+        b = ct.c_int64()
+        _rcheck(self.lib, self.h, self.lib.rx_rt_submit_from(self.h, ct.c_void_p(ptr), ct.byref(b)))
+        return b.value
+
+    submit_from = rx_rt_submit_from
 
     def rx_rt_flush(self):
         """End of the input: the last delayed symbols as one more block; returns its index."""

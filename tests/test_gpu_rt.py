@@ -119,3 +119,28 @@ def test_sustained_real_time_rate(link):
     full = res["bits"] == max(res["bits"])
     assert np.all(np.isfinite(q[full])) and np.ptp(q[full]) < 0.5   # stable over the run
     rt.close()
+
+
+def test_submit_from_caller_buffers_matches_the_staged_ring(link):
+    # the same stream through the caller-buffer entry point gives the same bits and bins
+    import torch
+    lk, g, rec = link
+    pinned = torch.from_numpy(np.ascontiguousarray(rec)).pin_memory()
+    outs = []
+    for mode in ("ring", "from"):
+        rt = _pipeline(lk, g, 1 << 20)
+        got = []
+        for b in range(6):
+            if mode == "ring":
+                rt.next_input()[:] = rec[b % N_REC]
+                rt.submit()
+            else:
+                rt.submit_from(pinned[b % N_REC])
+            if b >= 2:
+                got.append(rt.output(b - 2).copy())
+        rt.drain()
+        outs.append((got, rt.bins()))
+        rt.close()
+    for a, b in zip(outs[0][0], outs[1][0]):
+        assert np.array_equal(a, b)
+    assert np.array_equal(outs[0][1]["errors"], outs[1][1]["errors"])
