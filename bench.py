@@ -308,6 +308,7 @@ def bench_batch(args, rank, world, local):
                             "note": "16QAM channels below ~15 dB Es/N0 lose lock under the blind defaults "
                                     "(the oracle shows the same)"},
         "stage_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
+        "stage_rooflines": stage_roofs,
         "gpu_launches": int(launches),
         "roofline": roof,
         "clocks": clk,
@@ -742,6 +743,20 @@ def main():
         roof = {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
                 "frac": achieved / pk["hbm_gbs"], "traffic": None, "kernel": stage}
     roof["peak_source"] = pk_kind
+    # every stage against both ceilings (algorithmic bytes and flops per sample-time)
+    alu_peak = N_SM * FP32_LANES_PER_SM * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6
+    work = {"cdc": (4 + 16, 290.0),                                   # int8 in, 2 pols complex64 out
+            "eq": (16 + 8, (2 * 2 * T * 8 * 2 + 2 * 32 * 11) * 0.5 * (1 + W / S)),
+            "bps": (8 + 1 + 0.25, 32 * 11.0 + 8)}                        # per symbol-pol = per sample-time
+    stage_roofs = {}
+    for st_, (bpu, fpu) in work.items():
+        t_s = prof[st_][0] / args.steps / 1e3
+        if t_s <= 0:
+            continue
+        stage_roofs[st_] = {"ms": t_s * 1e3, "gsa_s": n / t_s / 1e9,
+                            "hbm_frac": bpu * n / t_s / (pk["hbm_gbs"] * 1e9),
+                            "alu_frac": fpu * n / t_s / alu_peak,
+                            "bytes_per_sample_time": bpu, "flop_per_sample_time": fpu}
 
     line = {
         "metric": METRIC, "value": value, "unit": "GSa/s", "n_gpus": world, "steps": args.steps,
@@ -757,6 +772,7 @@ def main():
         "hbm_roofline_frac": value / (pk["hbm_gbs"] / 4.25),
         "ber": ber, "ber_sync": sync,
         "stage_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
+        "stage_rooflines": stage_roofs,
         "gpu_launches": int(launches),
         "roofline": roof,
         "clocks": clk,
