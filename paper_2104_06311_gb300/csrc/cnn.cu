@@ -35,7 +35,7 @@ typedef __nv_bfloat16 bf16;
 constexpr int KS = 15, HALF = 7, CH = 64, FEAT = 4, FEATP = 16;
 constexpr int TM = 128;          // symbols per tile
 constexpr int kThreads = 256;    // 8 warps x 16 rows
-constexpr int TG = 3;            // taps per weight-gradient CTA (5 groups)
+constexpr int TG = 5;            // taps per weight-gradient CTA (3 groups)
 
 __device__ __forceinline__ unsigned smem_u32(const void *p) {
   return (unsigned)__cvta_generic_to_shared(p);
@@ -446,13 +446,28 @@ struct DwArgs {
   int ci_true, co_true;
 };
 
+// 16-byte asynchronous global -> shared copy; src_bytes 0 zero-fills (nothing is read).
+__device__ __forceinline__ void dw_cp16(void *dst, const void *src, int src_bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(smem_u32(dst)), "l"(src), "r"(src_bytes)
+               : "memory");
+}
+
+template <int CIN, int COUT>
+constexpr int dw_smem_bytes() {
+  return 2 * ((TM + 2 * HALF) * (CIN + 8) + TM * (COUT + 8)) * (int)sizeof(bf16);
+}
+
 // dW[k][ci][co] += sum_n in[n + k - 7][ci] dz[n][co] over this CTA's symbols,
-// taps 3 blockIdx.y .. + 2; CTAs with blockIdx.y == 0 also add db.
+// taps TG blockIdx.y .. + TG - 1; CTAs with blockIdx.y == 0 also add db.  The
+// input and gradient tiles of TM symbols are double-buffered in dynamic shared
+// memory: the copies of tile i + 1 fly while the MMAs of tile i run.
 template <int CIN, int COUT>
 __global__ void __launch_bounds__(kThreads) dw_kernel(const DwArgs a) {
   constexpr int CPX = CIN + 8, CPZ = COUT + 8;
-  __shared__ __align__(16) bf16 Xs[(TM + 2 * HALF) * CPX];
-  __shared__ __align__(16) bf16 Zs[TM * CPZ];
+  constexpr int XT = (TM + 2 * HALF) * CPX, ZT = TM * CPZ;
+  extern __shared__ __align__(16) unsigned char dw_smem[];
+  bf16 *const Xb = reinterpret_cast<bf16 *>(dw_smem);     // [2][XT]
+  bf16 *const Zb = Xb + 2 * XT;                            // [2][ZT]
   constexpr int CB = CIN / 16, CT = COUT / 8, WPB = 8 / CB, TPW = CT / WPB;
   static_assert(TPW >= 1 && CB * WPB == 8, "warp layout");
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -466,26 +481,37 @@ __global__ void __launch_bounds__(kThreads) dw_kernel(const DwArgs a) {
 #pragma unroll
     for (int j = 0; j < TPW; ++j) acc[t][j][0] = acc[t][j][1] = acc[t][j][2] = acc[t][j][3] = 0.f;
   float dbp = 0.f;
-  // ldmatrix.trans lanes: matrix j = lane / 8
-  const int ax_row = (lane & 7) + ((lane >> 4) & 1) * 8, ax_col = cb * 16 + ((lane >> 3) & 1) * 8;
-  const int bz_row = (lane & 7) + ((lane >> 3) & 1) * 8;
-  for (int64_t n0 = s0; n0 < s1; n0 += TM) {
-    __syncthreads();
+  // tile at symbol n0 into buffer `buf`: input rows n0 - 7 .. n0 + TM + 6, gradient rows n0 .. n0 + TM - 1
+  auto issue = [&](int buf, int64_t n0) {
+    bf16 *Xs = Xb + buf * XT, *Zs = Zb + buf * ZT;
     for (int i = threadIdx.x; i < (TM + 2 * HALF) * (CIN / 8); i += kThreads) {
       const int r = i / (CIN / 8), p = i % (CIN / 8);
       const int64_t n = n0 - HALF + r;
-      uint4 v = make_uint4(0u, 0u, 0u, 0u);
-      if (n >= 0 && n < a.K) v = *reinterpret_cast<const uint4 *>(a.in + n * CIN + p * 8);
-      *reinterpret_cast<uint4 *>(Xs + r * CPX + p * 8) = v;
+      const bool ok = n >= 0 && n < a.K;
+      dw_cp16(Xs + r * CPX + p * 8, ok ? (const void *)(a.in + n * CIN + p * 8) : (const void *)a.in, ok ? 16 : 0);
     }
     for (int i = threadIdx.x; i < TM * (COUT / 8); i += kThreads) {
       const int r = i / (COUT / 8), p = i % (COUT / 8);
       const int64_t n = n0 + r;
-      uint4 v = make_uint4(0u, 0u, 0u, 0u);
-      if (n < s1) v = *reinterpret_cast<const uint4 *>(a.dz + n * COUT + p * 8);
-      *reinterpret_cast<uint4 *>(Zs + r * CPZ + p * 8) = v;
+      const bool ok = n < s1;
+      dw_cp16(Zs + r * CPZ + p * 8, ok ? (const void *)(a.dz + n * COUT + p * 8) : (const void *)a.dz, ok ? 16 : 0);
+    }
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+  };
+  // ldmatrix.trans lanes: matrix j = lane / 8
+  const int ax_row = (lane & 7) + ((lane >> 4) & 1) * 8, ax_col = cb * 16 + ((lane >> 3) & 1) * 8;
+  const int bz_row = (lane & 7) + ((lane >> 3) & 1) * 8;
+  if (s0 < s1) issue(0, s0);
+  int it = 0;
+  for (int64_t n0 = s0; n0 < s1; n0 += TM, ++it) {
+    if (n0 + TM < s1) {
+      issue((it + 1) & 1, n0 + TM);
+      asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+    } else {
+      asm volatile("cp.async.wait_group 0;\n" ::: "memory");
     }
     __syncthreads();
+    const bf16 *Xs = Xb + (it & 1) * XT, *Zs = Zb + (it & 1) * ZT;
 #pragma unroll 1
     for (int s = 0; s < TM / 16; ++s) {
       unsigned b[TPW][2];
@@ -503,6 +529,7 @@ __global__ void __launch_bounds__(kThreads) dw_kernel(const DwArgs a) {
     if (blockIdx.y == 0 && threadIdx.x < COUT) {
       for (int r = 0; r < TM; ++r) dbp += __bfloat162float(Zs[r * CPZ + threadIdx.x]);
     }
+    __syncthreads();  // this buffer is refilled by the copies issued in the next iteration
   }
 #pragma unroll
   for (int t = 0; t < TG; ++t) {
@@ -514,8 +541,14 @@ __global__ void __launch_bounds__(kThreads) dw_kernel(const DwArgs a) {
         const int ci = cb * 16 + group + 8 * h;
         const int co = (tile0 + j) * 8 + 2 * tig;
         if (ci < a.ci_true) {
-          if (co < a.co_true) atomicAdd(&a.dw[((size_t)k * a.ci_true + ci) * a.co_true + co], acc[t][j][2 * h]);
-          if (co + 1 < a.co_true) atomicAdd(&a.dw[((size_t)k * a.ci_true + ci) * a.co_true + co + 1], acc[t][j][2 * h + 1]);
+          float *d = &a.dw[((size_t)k * a.ci_true + ci) * a.co_true + co];
+          if (co + 1 < a.co_true && ((uintptr_t)d & 7) == 0) {
+            // both columns in one 8-byte vector atomic
+            atomicAdd(reinterpret_cast<float2 *>(d), make_float2(acc[t][j][2 * h], acc[t][j][2 * h + 1]));
+          } else {
+            if (co < a.co_true) atomicAdd(d, acc[t][j][2 * h]);
+            if (co + 1 < a.co_true) atomicAdd(d + 1, acc[t][j][2 * h + 1]);
+          }
         }
       }
     }
@@ -751,14 +784,18 @@ cudaError_t launch_dw(rx_cnn *c, const bf16 *in, const bf16 *dz, int64_t K, int 
   a.in = in;
   a.dz = dz;
   a.K = K;
-  const int64_t want = std::max<int64_t>(1, (int64_t)2 * c->sms / (KS / TG));
+  // about one CTA per SM: each partial dW costs 15 x ci x co / TG x ... atomics, so fewer,
+  // longer CTAs (their tile copies double-buffered) beat more, shorter ones
+  const int64_t want = std::max<int64_t>(1, (int64_t)c->sms / (KS / TG));
   a.chunk = ((K + want - 1) / want + TM - 1) / TM * TM;
   a.dw = c->G + c->off_w[l];
   a.db = c->G + c->off_b[l];
   a.ci_true = c->ci[l];
   a.co_true = c->co[l];
   dim3 grid((unsigned)((K + a.chunk - 1) / a.chunk), KS / TG);
-  dw_kernel<CIN, COUT><<<grid, kThreads, 0, c->stream>>>(a);
+  constexpr int smem = dw_smem_bytes<CIN, COUT>();
+  cudaFuncSetAttribute(dw_kernel<CIN, COUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  dw_kernel<CIN, COUT><<<grid, kThreads, smem, c->stream>>>(a);
   return cudaGetLastError();
 }
 
