@@ -15,7 +15,13 @@ transfer function) follow the textbook definitions written out in
 
 Parity status: every function in ``oracle.chain`` is pinned by a
 ``-m "not gpu"`` test in ``tests/test_oracle_pins.py`` (closed forms,
-invariants, brute force, BER theory).  None is marked "parity unpinned".
+invariants, brute force, BER theory); ``oracle.cnn`` by
+``tests/test_cnn_pins.py``; the Kramers-Kronig front end ``oracle.kk`` by
+``tests/test_kk_pins.py`` (exact reconstruction of a minimum-phase field,
+identity overlap-save, decimation, the carrier's dispersion phase, stream
+continuity); the widely-linear DD-LMS ``oracle.wl`` by ``tests/test_wl_pins.py``
+(fixed point, zero-step convolution, closed-form IQ-imbalance inverse, schedule
+locality, AWGN BER).  None is marked "parity unpinned".
 """
 from .chain import (  # noqa: F401
     RxParams, n_cd_taps, default_overlap, default_fft_n, cd_response, rrc_response,
