@@ -287,6 +287,17 @@ __device__ __forceinline__ void run_span(const Hot hot, EqSmem &sm, const Span s
     __syncthreads();  // every warp is done with the previous chunk's window
     load_window(hot.u0, hot.u1, hot.u_fmt, sm, win_lo, count, sp.rot, n_limit);
     __syncthreads();
+    // this lane's 8 window samples u_q[2k+c-i] of a step (zero for inactive symbols or
+    // taps i >= T); the next step's are read while the current step's update runs
+    auto window_samples = [&](int tt, float2 (&xs)[8]) {
+      const int64_t kb = cs + (int64_t)tt * Bu;
+      const bool a_ = kl < (int)min((int64_t)Bu, ce - kb);
+      const float2 *xw = sm.win[ln.q] + (2 * tt * Bu + 2 * c) + 2 * kl - ln.half * 8;
+#pragma unroll
+      for (int ii = 0; ii < 8; ++ii) xs[ii] = (a_ && ln.half * 8 + ii < T) ? xw[-ii] : make_float2(0.f, 0.f);
+    };
+    float2 xn[8];
+    window_samples(0, xn);
     for (int t = 0; t < nsteps; ++t, ++step) {
       const int64_t k0 = cs + (int64_t)t * Bu;
       const int nk = (int)min((int64_t)Bu, ce - k0);
@@ -299,10 +310,8 @@ __device__ __forceinline__ void run_span(const Hot hot, EqSmem &sm, const Span s
       float2 x[8];
       float ax0 = 0.f, ay0 = 0.f, ax1 = 0.f, ay1 = 0.f;
       {
-        const float2 *xw = sm.win[ln.q] + (2 * t * Bu + 2 * c) + 2 * kl - ln.half * 8;
 #pragma unroll
-        for (int ii = 0; ii < 8; ++ii)
-          x[ii] = (act && ln.half * 8 + ii < T) ? xw[-ii] : make_float2(0.f, 0.f);
+        for (int ii = 0; ii < 8; ++ii) x[ii] = xn[ii];
 #pragma unroll
         for (int ii = 0; ii < 8; ii += 2) {
           ax0 = fmaf(h[ii].x, x[ii].x, fmaf(-h[ii].y, x[ii].y, ax0));
@@ -369,7 +378,6 @@ __device__ __forceinline__ void run_span(const Hot hot, EqSmem &sm, const Span s
         const float dsum = (hi1 ? e2[1] : e2[0]) + __shfl_xor_sync(FULL, send, 4);
         sm.bps[ln.warp][ln.part * 8 + ln.j] = dsum;
         __syncthreads();  // (1)
-        fo_pair();
         const float D = (sm.bps[0][ln.lane] + sm.bps[1][ln.lane]) + (sm.bps[2][ln.lane] + sm.bps[3][ln.lane]);
         // order-preserving key of a float (the QPSK cost is negative)
         const unsigned u = __float_as_uint(D);
@@ -387,6 +395,7 @@ __device__ __forceinline__ void run_span(const Hot hot, EqSmem &sm, const Span s
           er = csub(yv, cmul(dd, eth));
         }
       }
+      if (!sp.cma) fo_pair();  // off the argmin chain; the neighbours' outputs are in ybuf since (1)
       // ---- C: gradient e conj(u) of this lane's 8 taps, reduce-scatter over the warp's symbols
       {
         float2 g[8];
@@ -411,7 +420,8 @@ __device__ __forceinline__ void run_span(const Hot hot, EqSmem &sm, const Span s
             make_float2(k2.x + __shfl_xor_sync(FULL, s2.x, 4), k2.y + __shfl_xor_sync(FULL, s2.y, 4));
       }
       __syncthreads();  // (2)
-      if (sp.cma) fo_pair();  // DD blocks did this in the shadow of the argmin
+      if (sp.cma) fo_pair();
+      if (t + 1 < nsteps) window_samples(t + 1, xn);
       // ---- tap update: this lane's own tap, then every FIR lane gathers its 8
       if (ln.tap < T) {
         const float2 g0 = sm.grad[par][0][ln.q][ln.tap], g1 = sm.grad[par][1][ln.q][ln.tap];
