@@ -395,7 +395,6 @@ __device__ __forceinline__ void run_span(const Hot hot, EqSmem &sm, const Span s
           er = csub(yv, cmul(dd, eth));
         }
       }
-      if (!sp.cma) fo_pair();  // off the argmin chain; the neighbours' outputs are in ybuf since (1)
       // ---- C: gradient e conj(u) of this lane's 8 taps, reduce-scatter over the warp's symbols
       {
         float2 g[8];
@@ -420,12 +419,15 @@ __device__ __forceinline__ void run_span(const Hot hot, EqSmem &sm, const Span s
             make_float2(k2.x + __shfl_xor_sync(FULL, s2.x, 4), k2.y + __shfl_xor_sync(FULL, s2.y, 4));
       }
       __syncthreads();  // (2)
-      if (sp.cma) fo_pair();
+      // ---- tap update: this lane's own tap, then every FIR lane gathers its 8.  The
+      // partial-gradient reads go first; the next step's window reads and the frequency
+      // pair (the neighbours' outputs are in ybuf since barrier 1) fill their latency.
+      const int tp = ln.tap < T ? ln.tap : 0;
+      const float2 g0 = sm.grad[par][0][ln.q][tp], g1 = sm.grad[par][1][ln.q][tp];
+      const float2 g2 = sm.grad[par][2][ln.q][tp], g3 = sm.grad[par][3][ln.q][tp];
       if (t + 1 < nsteps) window_samples(t + 1, xn);
-      // ---- tap update: this lane's own tap, then every FIR lane gathers its 8
+      fo_pair();
       if (ln.tap < T) {
-        const float2 g0 = sm.grad[par][0][ln.q][ln.tap], g1 = sm.grad[par][1][ln.q][ln.tap];
-        const float2 g2 = sm.grad[par][2][ln.q][ln.tap], g3 = sm.grad[par][3][ln.q][ln.tap];
         own.x -= mu * ((g0.x + g1.x) + (g2.x + g3.x));
         own.y -= mu * ((g0.y + g1.y) + (g2.y + g3.y));
       }
