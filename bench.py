@@ -145,6 +145,36 @@ def cpu_oracle_run(g, n_samples):
     return out, dt, p
 
 
+def _oracle_replica(args):
+    """One independent replica of the oracle on a bounded sample (all-cores baseline)."""
+    samples, baud, L_km, D, mod, in_scale = args
+    import oracle as O
+    if samples is None:
+        return 0.0
+    p = O.RxParams(baud=baud, L_km=L_km, D=D, mod=mod, in_scale=in_scale)
+    t0 = time.perf_counter()
+    O.run_chain(samples, p)
+    return time.perf_counter() - t0
+
+
+def oracle_all_cores(g, ns):
+    """The oracle on every host core: independent replicas of the first ns sample-times
+    (the chain's waves are sequential, so more cores serve more streams), one process
+    each, started with spawn (the parent holds a CUDA context)."""
+    import multiprocessing as mp
+    cores = len(os.sched_getaffinity(0))
+    lk = g.link
+    job = (g.samples[:ns], lk.baud, lk.L_km, lk.D, lk.mod, g.in_scale)
+    with mp.get_context("spawn").Pool(cores) as pool:
+        pool.map(_oracle_replica, [(None,) + job[1:]] * cores)     # start-up and imports, untimed
+        t0 = time.perf_counter()
+        pool.map(_oracle_replica, [job] * cores)
+        wall = time.perf_counter() - t0
+    return {"value": cores * ns / wall / 1e9, "unit": "GSa/s", "cores": cores, "kind": "oracle",
+            "sample": f"{cores} independent replicas of the first {ns} sample-times, FP64 numpy oracle, "
+                      "one process per core"}
+
+
 def reference_arm(args, rank, world):
     if rank != 0:
         return
@@ -785,6 +815,7 @@ def main():
         orc, dt, p = cpu_oracle_run(g, ns)
         line["cpu_baseline"] = {"value": ns / dt / 1e9, "unit": "GSa/s", "cores": 1, "kind": "oracle",
                                 "sample": f"first {ns} sample-times of the workload, FP64 numpy oracle, one core"}
+        line["cpu_baseline_all_cores"] = oracle_all_cores(g, min(ns, 1 << 20))
         # bit agreement of the CUDA chain with the oracle on that sample (same stream prefix)
         rxs = Receiver(lk.baud, lk.L_km, D=lk.D, stream=stream, MOD=mbits, IN_SCALE=g.in_scale, PRECISION=prec)
         o2 = rxs.run_stream(x[:ns].contiguous())
