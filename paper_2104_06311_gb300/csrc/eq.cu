@@ -43,8 +43,9 @@
 //      CTA barrier; each lane adds the 4 warp partials of its tap, updates it
 //      and the 8 taps of each FIR lane are gathered back by shuffles.
 // Frequency pairs (y_k conj(y_{k-1}))^4, for 16QAM weighted by the ring
-// weights of both symbols, accumulate in compensated (Kahan) FP32 per lane and
-// are summed as double-float per segment.  The input window of a chunk of up
+// weights of both symbols, accumulate in compensated (Kahan) FP32 per lane (each
+// step's pair during the next step's inner BPS, off the update chain) and are
+// summed as double-float per segment.  The input window of a chunk of up
 // to 1152 symbols sits in shared memory (rows padded against bank conflicts),
 // rotated by exp(-j phi_n) from the 64-bit fixed-point phase through a
 // 256-entry phasor table and a short Taylor polynomial.
@@ -279,6 +280,27 @@ __device__ __forceinline__ void run_span(const Hot hot, EqSmem &sm, const Span s
   const int kl = ln.warp * 8 + ln.j;     // this lane's symbol within a block
   const bool hi4 = ln.j & 4, hi2 = ln.j & 2, hi1 = ln.j & 1;
   int step = 0;
+  // the previous step's frequency pair: (on, y_k, in-warp neighbour, previous block's last, parity)
+  bool d_on = false;
+  float2 d_yv = make_float2(0.f, 0.f), d_yup = make_float2(0.f, 0.f), d_ylast = make_float2(0.f, 0.f);
+  int d_par = 0;
+  // branch-free, explicitly rounded products: no FMA contraction, so that every kernel
+  // this body is compiled into forms the same estimate
+  auto fo_deferred = [&]() {
+    const float2 yw = sm.ybuf[d_par][kl > 0 ? kl - 1 : 0];
+    const float2 yp = ln.j > 0 ? d_yup : (ln.warp > 0 ? yw : d_ylast);
+    const float2 v = cmulc_rn(d_yv, yp);
+    const float2 v2 = cmul_rn(v, v);
+    float2 v4 = cmul_rn(v2, v2);
+    if (MB == 4) {  // 16QAM: keep the pi/4-aligned inner and outer rings (soft edge)
+      const float wk = ring_weight(__fadd_rn(__fmul_rn(d_yv.x, d_yv.x), __fmul_rn(d_yv.y, d_yv.y)));
+      const float wp = ring_weight(__fadd_rn(__fmul_rn(yp.x, yp.x), __fmul_rn(yp.y, yp.y)));
+      const float w = __fmul_rn(wk, wp);
+      v4 = make_float2(__fmul_rn(v4.x, w), __fmul_rn(v4.y, w));
+    }
+    kahan_add(fo.sx, fo.cx, d_on ? v4.x : 0.f);   // a select: stale inputs cannot leak
+    kahan_add(fo.sy, fo.cy, d_on ? v4.y : 0.f);
+  };
   for (int64_t cs = sp.kp; cs < sp.ke; cs += chunk) {
     const int64_t ce = min(cs + (int64_t)chunk, sp.ke);
     const int64_t win_lo = 2 * cs - c;
@@ -329,29 +351,13 @@ __device__ __forceinline__ void run_span(const Hot hot, EqSmem &sm, const Span s
         sm.ybuf[par][kl] = act ? yv : make_float2(0.f, 0.f);
         if (out && act) hot.yrow[k0 + kl] = yv;
       }
-      // frequency pairs (k-1, k) inside [fo_lo, fo_hi); the previous symbol is the
-      // in-warp neighbour, else (after a CTA barrier) the previous warp's last one
+      // frequency pair (k-1, k) inside [fo_lo, fo_hi) of this step, evaluated during the
+      // next step's inner BPS (off the update chain): the previous symbol is the in-warp
+      // neighbour, else the previous warp's last one (in ybuf[par], intact until two
+      // steps later), or for the first warp the last symbol of the previous block
       const float yupx = __shfl_up_sync(FULL, yv.x, 4), yupy = __shfl_up_sync(FULL, yv.y, 4);
       const int64_t kk = k0 + kl;
       const bool fo_on = out && act && ln.part == 0 && kk - 1 >= sp.fo_lo && kk < sp.fo_hi;
-      // branch-free so the compiler can interleave it with the argmin chain
-      auto fo_pair = [&]() {
-        const float2 yw = sm.ybuf[par][kl > 0 ? kl - 1 : 0];
-        float2 yp = ln.j > 0 ? make_float2(yupx, yupy) : (ln.warp > 0 ? yw : yprev_last);
-        // explicitly rounded products: no FMA contraction, so that every
-        // kernel this body is compiled into forms the same estimate
-        const float2 v = cmulc_rn(yv, yp);
-        const float2 v2 = cmul_rn(v, v);
-        float2 v4 = cmul_rn(v2, v2);
-        if (MB == 4) {  // 16QAM: keep the pi/4-aligned inner and outer rings (soft edge)
-          const float wk = ring_weight(__fadd_rn(__fmul_rn(yv.x, yv.x), __fmul_rn(yv.y, yv.y)));
-          const float wp = ring_weight(__fadd_rn(__fmul_rn(yp.x, yp.x), __fmul_rn(yp.y, yp.y)));
-          const float w = __fmul_rn(wk, wp);
-          v4 = make_float2(__fmul_rn(v4.x, w), __fmul_rn(v4.y, w));
-        }
-        kahan_add(fo.sx, fo.cx, fo_on ? v4.x : 0.f);   // a select: stale inputs cannot leak
-        kahan_add(fo.sy, fo.cy, fo_on ? v4.y : 0.f);
-      };
       // ---- B: error
       float2 eth = make_float2(1.f, 0.f);  // exp(j theta)
       if (!sp.cma) {
@@ -363,6 +369,7 @@ __device__ __forceinline__ void run_span(const Hot hot, EqSmem &sm, const Span s
           // for every angle, so -(|Re w| + |Im w|) orders the angles alike
           d[a] = act ? (MB == 2 ? -(fabsf(w.x) + fabsf(w.y)) : qam_dist<MB>(w)) : 0.f;
         }
+        fo_deferred();   // the previous step's pair, in the shadow of the reduce-scatter
         float e1[4], e2[2];
 #pragma unroll
         for (int a = 0; a < 4; ++a) {
@@ -386,6 +393,7 @@ __device__ __forceinline__ void run_span(const Hot hot, EqSmem &sm, const Span s
         const int bstar = __ffs(__ballot_sync(FULL, key == mn)) - 1;
         eth = make_float2(__shfl_sync(FULL, ln.rot_b.x, bstar), -__shfl_sync(FULL, ln.rot_b.y, bstar));
       }
+      if (sp.cma) fo_deferred();
       float2 er = make_float2(0.f, 0.f);
       if (act) {
         if (sp.cma) {
@@ -426,14 +434,19 @@ __device__ __forceinline__ void run_span(const Hot hot, EqSmem &sm, const Span s
       const float2 g0 = sm.grad[par][0][ln.q][tp], g1 = sm.grad[par][1][ln.q][tp];
       const float2 g2 = sm.grad[par][2][ln.q][tp], g3 = sm.grad[par][3][ln.q][tp];
       if (t + 1 < nsteps) window_samples(t + 1, xn);
-      fo_pair();
       if (ln.tap < T) {
         own.x -= mu * ((g0.x + g1.x) + (g2.x + g3.x));
         own.y -= mu * ((g0.y + g1.y) + (g2.y + g3.y));
       }
       gather_taps(h, own, ln);
+      d_on = fo_on;
+      d_yv = yv;
+      d_yup = make_float2(yupx, yupy);
+      d_ylast = yprev_last;
+      d_par = par;
     }
   }
+  fo_deferred();   // the span's last pair
 }
 
 // Segment total of the per-lane compensated pair sums as double-float

@@ -144,3 +144,32 @@ def test_submit_from_caller_buffers_matches_the_staged_ring(link):
     for a, b in zip(outs[0][0], outs[1][0]):
         assert np.array_equal(a, b)
     assert np.array_equal(outs[0][1]["errors"], outs[1][1]["errors"])
+
+
+def test_float_input_shallow_ring_and_state_errors():
+    # float32 intensities through a two-slot ring; outputs of overwritten slots and
+    # buffers after the flush are refused
+    from paper_2104_06311_gb300 import RealTime
+    from paper_2104_06311_gb300.rx import RxError
+    n = 1 << 16
+    lk = LK.KKLink(mod="qpsk", n_sym=4 * n // 4, L_km=1000.0, cspr_db=12.0, snr_db=20.0, adc="f32", seed=2104063124)
+    g = LK.generate(lk)
+    rec = g.samples.reshape(4, n)
+    rt = RealTime(lk.baud, lk.carrier_hz, lk.L_km, n, mod_bits=2, depth=2, in_dtype="f32", in_scale=g.in_scale,
+                  in_offset=g.in_offset, ref_bits=g.tx_bits, bin_symbols=n // 4, max_bins=64, acq=1024)
+    for b in range(4):
+        rt.next_input()[:] = rec[b]
+        rt.submit()
+    with pytest.raises(RxError):
+        rt.output(0)                                 # slot reused by buffer 2
+    rt.output(3)
+    rt.flush()
+    with pytest.raises(RxError):
+        rt.next_input()[:] = rec[0]
+        rt.submit()                                  # the stream has ended
+    res = rt.bins()
+    assert int(res["bits"].sum()) == 2 * 4 * n // 4  # every symbol of the four buffers, 2 bits each
+    ber = res["errors"].sum() / res["bits"].sum()
+    print(f"f32 QPSK through a 2-slot ring: BER {ber:.2e}")
+    assert ber < 1e-3
+    rt.close()
