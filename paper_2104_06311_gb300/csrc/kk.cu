@@ -1,7 +1,8 @@
 // Kramers-Kronig receiver front end (declared in rx_kk.h).
 //
-// Stage 1 (kk_hilbert_kernel, one 64-thread CTA per window of 1024 samples,
-// hop 512): intensity I -> a = sqrt(max(I, 1e-30)), ln a; radix-16 Stockham FFT
+// Stage 1 (kk_hilbert_kernel, one 64-thread CTA per two windows of 1024 samples,
+// hop 512, packed as real and imaginary parts of one transform): intensity I ->
+// a = sqrt(max(I, 1e-30)), ln a; radix-16 Stockham FFT
 // in shared memory; multiply by j sign(f) / N and conjugate; the same forward
 // FFT again gives the Hilbert image phi (inverse by conjugation); the kept
 // half of the window becomes E = a exp(j phi) exp(j 2 pi f_c n / fs), the
@@ -57,20 +58,26 @@ __device__ __forceinline__ float kk_intensity(const KkSrc &src, int64_t s) {
   return src.hist[s - (src.pos - KHIST)];
 }
 
-// Window b: the field of stream samples [e0 + 512 b, e0 + 512 b + 512) from the
-// input over [e0 + 512 b - 256, e0 + 512 b + 768), written to E[s - e0].
-__global__ void __launch_bounds__(KN / 16, 10) kk_hilbert_kernel(KkSrc src, int64_t e0, const float2 *__restrict__ tw,
-                                                             unsigned long long inc_q, float2 *__restrict__ E) {
+// Windows 2b and 2b + 1 in one transform pair: window w gives the field of stream
+// samples [e0 + 512 w, e0 + 512 w + 512) from the input over [e0 + 512 w - 256,
+// e0 + 512 w + 768), written to E[s - e0].  The log-amplitudes of the two windows
+// are the real and imaginary parts of one complex sequence: the Hilbert response
+// j sign(f) maps real sequences to real ones, so the inverse transform returns the
+// first window's phase in its real part and the second's in its imaginary part --
+// two windows for the price of one FFT pair.
+__global__ void __launch_bounds__(KN / 16, 10) kk_hilbert_kernel(KkSrc src, int64_t e0, int nwin,
+                                                             const float2 *__restrict__ tw, unsigned long long inc_q,
+                                                             float2 *__restrict__ E) {
   __shared__ float2 buf[KN + KN / 32];
   const int t = threadIdx.x;
-  const int64_t s0 = e0 + (int64_t)blockIdx.x * KH;   // first kept sample
-  const int64_t lo = s0 - KH / 2;
-  for (int m = t; m < KN; m += blockDim.x) {
-    const int64_t s = lo + m;
-    float la = 0.f;                              // outside the stream: zero log-amplitude
-    if (kk_inside(src, s)) la = logf(sqrtf(fmaxf(kk_intensity(src, s), 1e-30f)));
-    buf[pad(m)] = make_float2(la, 0.f);
-  }
+  const int w0 = 2 * blockIdx.x;
+  const bool two = w0 + 1 < nwin;
+  const int64_t lo0 = e0 + (int64_t)w0 * KH - KH / 2, lo1 = lo0 + KH;
+  auto log_amp = [&](int64_t s) -> float {     // outside the stream: zero log-amplitude
+    return kk_inside(src, s) ? logf(sqrtf(fmaxf(kk_intensity(src, s), 1e-30f))) : 0.f;
+  };
+  for (int m = t; m < KN; m += blockDim.x)
+    buf[pad(m)] = make_float2(log_amp(lo0 + m), two ? log_amp(lo1 + m) : 0.f);
   __syncthreads();
   fft_forward<KN, 16>(buf, t, tw);
   const float inv = 1.f / (float)KN;
@@ -86,11 +93,16 @@ __global__ void __launch_bounds__(KN / 16, 10) kk_hilbert_kernel(KkSrc src, int6
   }
   __syncthreads();
   fft_forward<KN, 16>(buf, t, tw);
-  for (int m = KH / 2 + t; m < KH / 2 + KH; m += blockDim.x) {
-    const int64_t s = s0 + (m - KH / 2);
+  // inverse = conj of the forward transform of the conjugate: phase of window w0 in
+  // the real part, of window w0 + 1 in the (negated) imaginary part
+  for (int i = t; i < 2 * KH; i += blockDim.x) {
+    const int w = i / KH, m = KH / 2 + (i % KH);
+    if (w == 1 && !two) break;
+    const int64_t s = e0 + (int64_t)(w0 + w) * KH + (m - KH / 2);
     float2 e = make_float2(0.f, 0.f);            // outside the stream: zero field
     if (kk_inside(src, s)) {
-      const float phi = buf[pad(m)].x;           // real part of the inverse
+      const float2 r = buf[pad(m)];
+      const float phi = w == 0 ? r.x : -r.y;
       const float a = sqrtf(fmaxf(kk_intensity(src, s), 1e-30f));
       float sp, cp;
       sincosf(phi, &sp, &cp);
@@ -301,8 +313,8 @@ rx_status kk_run(rx_kk *k, const KkSrc &src, int64_t no, float *y, float *field)
       if (cudaEventCreate(&e) != cudaSuccess) return kfail(k, RX_ECUDA, "event");
   const int64_t o0 = k->pos - KDELAY, e0 = o0 - KEDGE;
   if (ev[0]) cudaEventRecord(ev[0], k->stream);
-  const unsigned g1 = (unsigned)((no + 2 * KEDGE) / KH);
-  kk_hilbert_kernel<<<g1, KN / 16, 0, k->stream>>>(src, e0, k->tw, k->inc_q, k->E);
+  const int nwin = (int)((no + 2 * KEDGE) / KH);
+  kk_hilbert_kernel<<<(unsigned)((nwin + 1) / 2), KN / 16, 0, k->stream>>>(src, e0, nwin, k->tw, k->inc_q, k->E);
   cudaError_t e = cudaGetLastError();
   if (ev[1]) cudaEventRecord(ev[1], k->stream);
   const int S = KN - k->V;
