@@ -262,6 +262,7 @@ rx_status rx_rt_set_wl_param(rx_rt *r, int key, double v) {
 
 rx_status rx_rt_next_input(rx_rt *r, void **slot) {
   if (!r || !slot) return RX_EINVAL;
+  if (r->ended) return rfail(r, RX_ESTATE, "the stream has ended (rx_rt_flush)");
   const int k = (int)(r->next % r->cfg.depth);
   // the slot's previous buffer must have left the host slot
   if (r->slot_buffer[k] >= 0) {
@@ -287,7 +288,11 @@ rx_status rt_enqueue(rx_rt *r, const void *src, int64_t *index) {
   cudaEvent_t pe[8] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   if (r->profile)
     for (auto &ev : pe)
-      if (cudaEventCreate(&ev) != cudaSuccess) return rfail(r, RX_ECUDA, "event");
+      if (cudaEventCreate(&ev) != cudaSuccess) {
+        for (cudaEvent_t &x : pe)
+          if (x) cudaEventDestroy(x);
+        return rfail(r, RX_ECUDA, "event");
+      }
   auto mark = [&](int i, int stream) {
     if (pe[i]) cudaEventRecord(pe[i], r->st[stream]);
   };
