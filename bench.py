@@ -338,7 +338,6 @@ def bench_batch(args, rank, world, local):
                             "note": "16QAM channels below ~15 dB Es/N0 lose lock under the blind defaults "
                                     "(the oracle shows the same)"},
         "stage_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
-        "stage_rooflines": stage_roofs,
         "gpu_launches": int(launches),
         "roofline": roof,
         "clocks": clk,
