@@ -149,61 +149,109 @@ struct Rot {
   int64_t n0;
 };
 
-// u0/u1: CDC output of pols X/Y, indexed by stream sample n.
-// Sample n of a CDC output row stored in format fmt (RX_FMT_*), as complex float.
-__device__ __forceinline__ float2 ld_u(const unsigned char *__restrict__ row, int64_t n, int fmt) {
-  if (fmt == RX_FMT_F32) return __ldg(reinterpret_cast<const float2 *>(row) + n);
-  const unsigned w = __ldg(reinterpret_cast<const unsigned *>(row) + n);
+// u0/u1: CDC output of pols X/Y, indexed by stream sample n, stored in format
+// fmt (RX_FMT_*).
+__device__ __forceinline__ unsigned smem_u32(const void *p) {
+  return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+
+// Raw samples [win_lo, win_lo + count) of both rows copied into the window
+// asynchronously: element j by thread j mod kEqThreads, the thread that converts
+// it in window_finish, so that its own wait makes the copy visible to it (a
+// 16-bit sample lands in the low half of its float2 slot); samples outside
+// [0, n_limit) are left for window_finish to zero.  Issued early (before a grid barrier), the
+// copies land while the CTA waits.
+__device__ __forceinline__ void window_issue(const unsigned char *__restrict__ u0, const unsigned char *__restrict__ u1,
+                                             int fmt, EqSmem &sm, int64_t win_lo, int count, int64_t n_limit) {
+  const int lo = (int)max((int64_t)0, min((int64_t)count, -win_lo));
+  const int hi = (int)max((int64_t)0, min((int64_t)count, n_limit - win_lo));
+  if (fmt == RX_FMT_F32) {
+    for (int j = threadIdx.x; j < hi; j += kEqThreads) {
+      if (j < lo) continue;
+      const int64_t n = win_lo + j;
+      asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(smem_u32(&sm.win[0][j])), "l"(u0 + n * 8)
+                   : "memory");
+      asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(smem_u32(&sm.win[1][j])), "l"(u1 + n * 8)
+                   : "memory");
+    }
+  } else {
+    for (int j = threadIdx.x; j < hi; j += kEqThreads) {
+      if (j < lo) continue;
+      const int64_t n = win_lo + j;
+      asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(smem_u32(&sm.win[0][j])), "l"(u0 + n * 4)
+                   : "memory");
+      asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(smem_u32(&sm.win[1][j])), "l"(u1 + n * 4)
+                   : "memory");
+    }
+  }
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+
+__device__ __forceinline__ void window_wait() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// Sample from a window slot filled by window_issue, as complex float.
+__device__ __forceinline__ float2 raw_sample(const float2 *slot, int fmt) {
+  if (fmt == RX_FMT_F32) return *slot;
+  const unsigned w = *reinterpret_cast<const unsigned *>(slot);
   if (fmt == RX_FMT_F16) return __half22float2(*reinterpret_cast<const __half2 *>(&w));
   return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&w));
 }
 
-__device__ __forceinline__ void load_window(const unsigned char *__restrict__ u0, const unsigned char *__restrict__ u1,
-                                            int fmt, EqSmem &sm, int64_t win_lo, int count, const Rot &rot,
-                                            int64_t n_limit) {
-  // issue every load of this thread first (HBM latency once, not per sample)
+// Waits for this thread's copies, then converts its samples in place, removing
+// the tracker's phase: window = exp(-j phi_n) u(n), zero outside [0, n_limit).
+__device__ __forceinline__ void window_finish(int fmt, EqSmem &sm, int64_t win_lo, int count, const Rot &rot,
+                                              int64_t n_limit) {
+  window_wait();
+  // groups of kG samples per thread: all raw reads of a group first, then its
+  // independent rotation chains (one warp per scheduler: ILP hides the latency)
   constexpr int kPer = (kWinMax + kEqThreads - 1) / kEqThreads;
-  float2 va[kPer], vb[kPer];
-  // one loop per format (the format is uniform: no per-sample branch)
-#define RX_LOAD_LOOP(FMT_)                                   \
-  _Pragma("unroll") for (int r = 0; r < kPer; ++r) {         \
-    const int j = threadIdx.x + r * kEqThreads;              \
-    const int64_t n = win_lo + j;                            \
-    va[r] = vb[r] = make_float2(0.f, 0.f);                   \
-    if (j < count && n >= 0 && n < n_limit) {                \
-      va[r] = ld_u(u0, n, FMT_);                             \
-      vb[r] = ld_u(u1, n, FMT_);                             \
-    }                                                        \
-  }
-  if (fmt == RX_FMT_F32) {
-    RX_LOAD_LOOP(RX_FMT_F32)
-  } else if (fmt == RX_FMT_F16) {
-    RX_LOAD_LOOP(RX_FMT_F16)
-  } else {
-    RX_LOAD_LOOP(RX_FMT_BF16)
-  }
-#undef RX_LOAD_LOOP
+  constexpr int kG = 5;
+  // turn of the thread's first sample; each further one is kEqThreads samples on
+  // (exact: modular 64-bit arithmetic)
+  const unsigned long long ph0 = rot.Phi_q + (unsigned long long)(win_lo + threadIdx.x - rot.n0) * rot.delta_q;
+  const unsigned long long dph = (unsigned long long)kEqThreads * rot.delta_q;
+#pragma unroll 1
+  for (int r0 = 0; r0 < kPer; r0 += kG) {
+    float2 a[kG], b[kG];
 #pragma unroll
-  for (int r = 0; r < kPer; ++r) {
-    const int j = threadIdx.x + r * kEqThreads;
-    if (j >= count) break;
-    const int64_t n = win_lo + j;
-    float2 a = va[r], b = vb[r];
-    if (rot.on && n >= 0 && n < n_limit) {
-      // exp(-j phi): top 8 bits of the turn from the table, the rest
-      // (theta < 2 pi / 256) by its Taylor series (error < 1e-12)
-      const unsigned ph = (unsigned)((rot.Phi_q + (unsigned long long)(n - rot.n0) * rot.delta_q) >> 32);
-      const float th = (float)(ph & 0xFFFFFFu) * 1.4629180792671596e-09f;  // 2 pi / 2^32
-      const float t2 = th * th;
-      const float cs = fmaf(t2, fmaf(t2, 1.f / 24.f, -0.5f), 1.f);
-      const float sn = th * fmaf(t2, fmaf(t2, 1.f / 120.f, -1.f / 6.f), 1.f);
-      const float2 r2 = cmul(sm.rtab[ph >> 24], make_float2(cs, -sn));
-      a = cmul(a, r2);
-      b = cmul(b, r2);
+    for (int g = 0; g < kG; ++g) {
+      const int j = threadIdx.x + (r0 + g) * kEqThreads;
+      const int64_t n = win_lo + j;
+      a[g] = b[g] = make_float2(0.f, 0.f);
+      if (j < count && n >= 0 && n < n_limit) {
+        a[g] = raw_sample(&sm.win[0][j], fmt);
+        b[g] = raw_sample(&sm.win[1][j], fmt);
+      }
     }
-    sm.win[0][j] = a;
-    sm.win[1][j] = b;
+#pragma unroll
+    for (int g = 0; g < kG; ++g) {
+      const int j = threadIdx.x + (r0 + g) * kEqThreads;
+      if (j < count) {
+        if (rot.on) {
+          // exp(-j phi): top 8 bits of the turn from the table, the rest
+          // (theta < 2 pi / 256) by its Taylor series (error < 1e-12)
+          const unsigned ph = (unsigned)((ph0 + (unsigned long long)(r0 + g) * dph) >> 32);
+          const float th = (float)(ph & 0xFFFFFFu) * 1.4629180792671596e-09f;  // 2 pi / 2^32
+          const float t2 = th * th;
+          const float cs = fmaf(t2, fmaf(t2, 1.f / 24.f, -0.5f), 1.f);
+          const float sn = th * fmaf(t2, fmaf(t2, 1.f / 120.f, -1.f / 6.f), 1.f);
+          const float2 r2 = cmul(sm.rtab[ph >> 24], make_float2(cs, -sn));
+          a[g] = cmul(a[g], r2);
+          b[g] = cmul(b[g], r2);
+        }
+        sm.win[0][j] = a[g];
+        sm.win[1][j] = b[g];
+      }
+    }
   }
+}
+
+// Window of the chunk of a span that starts at symbol cs: samples
+// [2 cs - c, 2 ce + c - 1), ce = min(cs + chunk, ke).
+__device__ __forceinline__ void chunk_window(int64_t cs, int64_t ke, int c, int chunk, int64_t &win_lo, int &count) {
+  const int64_t ce = min(cs + (int64_t)chunk, ke);
+  win_lo = 2 * cs - c;
+  count = (int)(2 * (ce - cs) + 2 * c - 1);
 }
 
 // One run over symbols [kp, ke) with outputs from ks and frequency pairs
@@ -273,7 +321,8 @@ __device__ __forceinline__ float ring_weight(float a) {
 
 template <int MB>
 __device__ __forceinline__ void run_span(const Hot hot, EqSmem &sm, const Span sp, const Lane &ln,
-                                         float2 &own, float2 (&h)[8], Kahan &fo, int64_t n_limit) {
+                                         float2 &own, float2 (&h)[8], Kahan &fo, int64_t n_limit,
+                                         bool pre = false) {
   const int T = hot.T, c = hot.c, Bu = hot.Bu;
   const int chunk = (kChunkSym / Bu) * Bu;
   const float mu = sp.cma ? hot.mu_cma : hot.mu_dd;
@@ -303,11 +352,14 @@ __device__ __forceinline__ void run_span(const Hot hot, EqSmem &sm, const Span s
   };
   for (int64_t cs = sp.kp; cs < sp.ke; cs += chunk) {
     const int64_t ce = min(cs + (int64_t)chunk, sp.ke);
-    const int64_t win_lo = 2 * cs - c;
-    const int count = (int)(2 * (ce - cs) + 2 * c - 1);
+    int64_t win_lo;
+    int count;
+    chunk_window(cs, sp.ke, c, chunk, win_lo, count);
     const int nsteps = (int)((ce - cs + Bu - 1) / Bu);
     __syncthreads();  // every warp is done with the previous chunk's window
-    load_window(hot.u0, hot.u1, hot.u_fmt, sm, win_lo, count, sp.rot, n_limit);
+    // (pre: the first chunk's copies were issued before the caller's grid barrier)
+    if (!(pre && cs == sp.kp)) window_issue(hot.u0, hot.u1, hot.u_fmt, sm, win_lo, count, n_limit);
+    window_finish(hot.u_fmt, sm, win_lo, count, sp.rot, n_limit);
     __syncthreads();
     // this lane's 8 window samples u_q[2k+c-i] of a step (zero for inactive symbols or
     // taps i >= T); the next step's are read while the current step's update runs
@@ -607,6 +659,18 @@ __device__ __forceinline__ void eq_body(const EqLaunch &L, const int cta, EqSmem
     sm.dq = __ldcg(&L.st->delta_q);
   }
   __syncthreads();
+  // segment g: outputs [ks, ke), trained from kp
+  auto seg_span = [&](int64_t g) {
+    Span sp;
+    sp.ks = L.A + g * L.S;
+    sp.ke = L.K >= 0 ? min(sp.ks + (int64_t)L.S, L.K) : sp.ks + L.S;
+    sp.kp = max(sp.ks - (int64_t)L.W, (int64_t)0);
+    sp.fo_lo = sp.ks; sp.fo_hi = sp.ke;
+    sp.cma = 0;
+    return sp;
+  };
+  const int chunk = (kChunkSym / hot.Bu) * hot.Bu;
+  bool pre = false;   // the next segment's first window is in flight
   for (int64_t w = L.wave_first; w < L.wave_last; ++w) {
     const float2 *start = (w == L.wave_first) ? &L.st->taps[0][0][0] : L.tap_slot + ((w - 1) & 1) * 4 * kMaxTaps;
     const int64_t g0 = w * L.P;
@@ -618,21 +682,36 @@ __device__ __forceinline__ void eq_body(const EqLaunch &L, const int cta, EqSmem
     rot.n0 = 2 * (L.A + g0 * L.S);
     for (int64_t g = g0 + slot; g < g_end; g += nslots) {
       load_row(own, h, start, p, ln);
-      Span sp;
-      sp.ks = L.A + g * L.S;
-      sp.ke = L.K >= 0 ? min(sp.ks + (int64_t)L.S, L.K) : sp.ks + L.S;
-      sp.kp = max(sp.ks - (int64_t)L.W, (int64_t)0);
-      sp.fo_lo = sp.ks; sp.fo_hi = sp.ke;
-      sp.cma = 0;
+      Span sp = seg_span(g);
       sp.rot = rot;
       fo = Kahan{0.f, 0.f, 0.f, 0.f};
-      run_span<MB>(hot, sm, sp, ln, own, h, fo, n_limit);
-      const float4 s = reduce_fo(sm, fo, ln);
+      run_span<MB>(hot, sm, sp, ln, own, h, fo, n_limit, pre);
+      pre = false;
+      const float4 s = reduce_fo(sm, fo, ln);   // every warp is done with the window
+      // this CTA's next segment (later in this wave, else in the next): its first
+      // window's raw samples do not depend on the tracker, so their copies are
+      // issued now and land during the grid barrier and the fold
+      int64_t gn = g + nslots;
+      if (gn >= g_end) {
+        gn = (w + 1) * L.P + slot;
+        if (w + 1 >= L.wave_last || gn >= min(gn - slot + (int64_t)L.P, L.n_segments)) gn = -1;
+      }
+      if (gn >= 0) {
+        const Span sn = seg_span(gn);
+        int64_t lo;
+        int cnt;
+        chunk_window(sn.kp, sn.ke, hot.c, chunk, lo, cnt);
+        window_issue(hot.u0, hot.u1, hot.u_fmt, sm, lo, cnt, n_limit);
+        pre = true;
+      }
       if (threadIdx.x == 0) __stcg(L.fo_part + (w & 1) * 2 * L.P + (g - g0) * 2 + p, s);
       // the last segment's end taps start wave w + 1 (trace entry w + 2)
       if (g == g_end - 1) store_row(own, L.tap_slot + (w & 1) * 4 * kMaxTaps, trace_slot(L, w + 2), p, ln);
     }
-    if (!cta_barrier(L.err, L.barrier, (unsigned)L.nblocks, epoch, sm)) return;
+    if (!cta_barrier(L.err, L.barrier, (unsigned)L.nblocks, epoch, sm)) {
+      window_wait();   // no copy left in flight
+      return;
+    }
     // one warp folds the wave's partials (fixed tree, identical in every CTA)
     if (ln.warp == 0) {
       const float4 *src = L.fo_part + (w & 1) * 2 * L.P;
