@@ -770,7 +770,7 @@ int eq_max_blocks() {
 // Batched form: one cooperative launch serves many independent streams.  CTA
 // b works for stream team[b].x as its CTA team[b].y; each stream's team
 // synchronises on its own barrier words (EqLaunch::nblocks = team size).
-__global__ void __launch_bounds__(kEqThreads, 1) eq_batch_kernel(const EqLaunch *__restrict__ Ls,
+__global__ void __launch_bounds__(kEqThreads, 3) eq_batch_kernel(const EqLaunch *__restrict__ Ls,
                                                                  const int2 *__restrict__ team) {
   __shared__ EqSmem sm;
   const int2 t = team[blockIdx.x];
