@@ -14,8 +14,11 @@
 //            segment slot) that runs its acquisition and its segment waves
 //            and synchronises on the channel's own barrier words;
 //   BPS      pass 1 / unwrap scan / demap launches per channel;
-// all enqueued on the bound stream and, from the second call with the same
-// pointers and sizes, replayed from a captured CUDA graph.
+// the per-channel CDC and BPS launches spread over four side streams
+// (longest channel first onto the least loaded; fork and join by events on
+// the bound stream), so that the many short launches of small channels
+// overlap; from the second call with the same pointers and sizes the whole
+// enqueue is replayed from a captured CUDA graph.
 //
 // Autotuner.  The CDC kernel's cost per window depends on the FFT size N
 // only; a channel with overlap V keeps N - V output samples per window.  The
@@ -99,6 +102,11 @@ struct rx_batch {
   std::vector<Chan> ch;
   cudaStream_t stream = nullptr;
   cudaStream_t cap_stream = nullptr;         // graph capture only
+  // side streams: the per-channel CDC and BPS launches, spread over them so
+  // that the small channels' launches overlap (fork / join by events)
+  static constexpr int kSide = 4;
+  cudaStream_t side[kSide] = {};
+  cudaEvent_t ev_fork = nullptr, ev_join[kSide] = {};
   bool use_graph = true;
   int eq_ctas = 0, pad_smem = 0;
   EqLaunch *d_L = nullptr, *h_L = nullptr;   // h_L: pinned host copy source
@@ -164,6 +172,14 @@ void release(rx_batch *b) {
   if (b->h_err) cudaFreeHost(b->h_err);
   if (b->err_ev) cudaEventDestroy(b->err_ev);
   if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+  for (int k = 0; k < rx_batch::kSide; ++k) {
+    if (b->side[k]) cudaStreamDestroy(b->side[k]);
+    if (b->ev_join[k]) cudaEventDestroy(b->ev_join[k]);
+    b->side[k] = nullptr;
+    b->ev_join[k] = nullptr;
+  }
+  if (b->ev_fork) cudaEventDestroy(b->ev_fork);
+  b->ev_fork = nullptr;
   for (cudaEvent_t e : b->ev_pool) cudaEventDestroy(e);
   b->ev_pool.clear();
   b->cap_stream = nullptr;
@@ -280,6 +296,39 @@ struct BStage {
   }
 };
 
+// The side streams start after everything enqueued on s so far.
+cudaError_t side_fork(rx_batch *b, cudaStream_t s) {
+  cudaError_t e = cudaEventRecord(b->ev_fork, s);
+  for (int k = 0; k < rx_batch::kSide && e == cudaSuccess; ++k) e = cudaStreamWaitEvent(b->side[k], b->ev_fork, 0);
+  return e;
+}
+
+// s continues after everything enqueued on the side streams.
+cudaError_t side_join(rx_batch *b, cudaStream_t s) {
+  cudaError_t e = cudaSuccess;
+  for (int k = 0; k < rx_batch::kSide && e == cudaSuccess; ++k) {
+    e = cudaEventRecord(b->ev_join[k], b->side[k]);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, b->ev_join[k], 0);
+  }
+  return e;
+}
+
+// Side stream of each channel: longest channel first onto the least loaded.
+std::vector<int> side_map(const rx_batch *b, const rx_in *ins) {
+  std::vector<int> order(b->n_ch), map(b->n_ch, 0);
+  for (int i = 0; i < b->n_ch; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return ins[x].n > ins[y].n; });
+  int64_t load[rx_batch::kSide] = {};
+  for (int i : order) {
+    int k = 0;
+    for (int q = 1; q < rx_batch::kSide; ++q)
+      if (load[q] < load[k]) k = q;
+    map[i] = k;
+    load[k] += ins[i].n;
+  }
+  return map;
+}
+
 // Everything one call enqueues (eagerly or under capture); launches[] gets
 // the kernel launches per stage.
 rx_status enqueue(rx_batch *b, const rx_in *ins, rx_out *outs, cudaStream_t s, bool timed, int64_t *launches) {
@@ -288,18 +337,21 @@ rx_status enqueue(rx_batch *b, const rx_in *ins, rx_out *outs, cudaStream_t s, b
   batch_init_kernel<<<b->n_ch, 128, 0, s>>>(b->d_L);
   BX_CUDA(cudaGetLastError(), "state init");
   launches[RX_STAGE_MOVE] += 1;
+  const std::vector<int> smap = side_map(b, ins);
   {
     BStage tm(b, RX_STAGE_CDC, s, timed);
+    BX_CUDA(side_fork(b, s), "fork");
     for (int i = 0; i < b->n_ch; ++i) {
       const Chan &c = b->ch[i];
       const int64_t n = ins[i].n;
       if (n == 0) continue;
       const int Sh = c.N - c.V;
       BX_CUDA(launch_cdc(c.N, c.V, nullptr, 0, 0, ins[i].data, 0, n, ins[i].dtype, (float)c.cfg.in_scale, c.H, c.tw,
-                         c.u, 0, c.u_stride, 0, (n + Sh - 1) / Sh, n, s),
+                         c.u, 0, c.u_stride, 0, (n + Sh - 1) / Sh, n, b->side[smap[i]]),
               "cdc");
       launches[RX_STAGE_CDC] += 1;
     }
+    BX_CUDA(side_join(b, s), "join");
   }
   {
     BStage tm(b, RX_STAGE_EQ, s, timed);
@@ -307,8 +359,10 @@ rx_status enqueue(rx_batch *b, const rx_in *ins, rx_out *outs, cudaStream_t s, b
     launches[RX_STAGE_EQ] += 1;
   }
   BStage tm(b, RX_STAGE_BPS, s, timed);
+  BX_CUDA(side_fork(b, s), "fork");
   for (int i = 0; i < b->n_ch; ++i) {
     const Chan &c = b->ch[i];
+    const cudaStream_t cs = b->side[smap[i]];
     const EqLaunch &L = b->h_L[i];
     const int64_t K = L.K;
     if (K == 0) continue;
@@ -342,18 +396,21 @@ rx_status enqueue(rx_batch *b, const rx_in *ins, rx_out *outs, cudaStream_t s, b
     B.sym = reinterpret_cast<float2 *>(outs[i].sym);
     B.sym_stride = outs[i].sym_stride;
     B.out_first = 0;
-    BX_CUDA(launch_bps(B, s), "bps");
+    BX_CUDA(launch_bps(B, cs), "bps");
     launches[RX_STAGE_BPS] += 3;
     if (outs[i].eq) {
-      BX_CUDA(launch_copy_cols(reinterpret_cast<float2 *>(outs[i].eq), outs[i].eq_stride, c.y, c.y_stride, K, s), "eq out");
+      BX_CUDA(launch_copy_cols(reinterpret_cast<float2 *>(outs[i].eq), outs[i].eq_stride, c.y, c.y_stride, K, cs),
+              "eq out");
       launches[RX_STAGE_MOVE] += 1;
     }
     if (outs[i].cdc) {
-      BX_CUDA(launch_copy_cols(reinterpret_cast<float2 *>(outs[i].cdc), outs[i].cdc_stride, c.u, c.u_stride, ins[i].n, s),
+      BX_CUDA(launch_copy_cols(reinterpret_cast<float2 *>(outs[i].cdc), outs[i].cdc_stride, c.u, c.u_stride, ins[i].n,
+                               cs),
               "cdc out");
       launches[RX_STAGE_MOVE] += 1;
     }
   }
+  BX_CUDA(side_join(b, s), "join");
   return RX_OK;
 }
 
@@ -488,6 +545,11 @@ rx_status rx_batch_create(rx_batch **out, int n_ch, const rx_chan_cfg *cfgs) {
   if (e == cudaSuccess) e = cudaMallocHost((void **)&b->h_err, sizeof(int));
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->err_ev, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming);
+  for (int k = 0; k < rx_batch::kSide && e == cudaSuccess; ++k) {
+    e = cudaStreamCreateWithFlags(&b->side[k], cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_join[k], cudaEventDisableTiming);
+  }
   if (e != cudaSuccess) {
     release(b);
     return bcuda(b, e, "pinned launch table");
