@@ -28,8 +28,10 @@
 // output sample.  Team sizes come from a cost model of the equaliser
 // schedule: a channel's time is its acquisition (A / B_u update steps, one
 // CTA pair) plus, per wave, ceil(P / pairs) passes of (S + W) / B_u steps and
-// a fixed wave overhead; pairs go one at a time to the channel whose time is
-// currently largest, within the co-resident CTA budget of the launch.
+// a fixed wave overhead, times the step cost of its format (a 16QAM step costs
+// about 1.3 QPSK steps: its inner-BPS distance is longer); pairs go one at a
+// time to the channel whose time is currently largest, within the co-resident
+// CTA budget of the launch.
 #include <string.h>
 
 #include <algorithm>
@@ -52,6 +54,8 @@ constexpr int64_t kNcma = 8192, kAcqMin = 16384, kBlockSamples = 65536;
 constexpr double kMu = 1e-3, kRolloff = 0.1, kLamNm = 1550.0, kFoSmooth = 16.0;
 constexpr int kMaxChannels = 4096;
 constexpr int kWaveOverheadSteps = 8;   // cost model: grid barrier + FO fold per wave
+constexpr double kStep16qam = 1.3;       // cost model: 16QAM update step / QPSK step (fit to per-team
+                                        // end times of a 64-channel batch)
 
 struct Chan {
   rx_chan_cfg cfg;
@@ -257,7 +261,8 @@ double eq_cost(const Chan &c, int pairs) {
   const int64_t n_seg = c.K_cap > A ? (c.K_cap - A + kS - 1) / kS : 0;
   const int64_t waves = (n_seg + c.P - 1) / c.P;
   const int64_t passes = (c.P + pairs - 1) / pairs;
-  return (double)(A / kBu) + (double)waves * (double)(passes * ((kS + kW) / kBu) + kWaveOverheadSteps);
+  const double step = c.cfg.mod_bits == 4 ? kStep16qam : 1.0;
+  return step * ((double)(A / kBu) + (double)waves * (double)(passes * ((kS + kW) / kBu) + kWaveOverheadSteps));
 }
 
 rx_status check_device_error(rx_batch *b, bool wait) {
