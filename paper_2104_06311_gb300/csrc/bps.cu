@@ -10,11 +10,14 @@
 //   bhat_k  = argmin_b D_{k,b} (smallest b on ties),
 //   r_k = +1 / -1 / 0 when bhat_{k-1} - bhat_k > B/2 / < -B/2 / otherwise,
 //   m_k = m_{k-1} + r_k,  z_k = y_k e^{-j phi_bhat} (-j)^{m_k}.
-// Pass 1: one warp per chunk of symbols, lane = test angle; a sliding window
-//   of d values per lane in shared memory (exact re-sum every 32 symbols);
-//   argmin by a warp min-reduction on the float bits plus a ballot; writes
-//   bhat (int8), the chunk's sum of r and sum of |z - dec z|^2 = d_{k,bhat}.
-// Scan: exclusive prefix of the chunk sums per pol (+ the carried count) and
+// Pass 1: one warp per chunk [a, b) of symbols, lane = test angle; argmin by a
+//   warp min-reduction on the float bits plus a ballot; writes bhat (int8), the
+//   chunk's sum of r_k over a < k < b and of |z - dec z|^2 = d_{k,bhat}.  With
+//   the default half window (Nb = 16, a 33-symbol window) the window sums come
+//   from two 32-symbol blocks of distances in registers (pass1_blocks); other
+//   half windows slide a ring of distances in shared memory.
+// Scan: adds each chunk's boundary step r_a (from bhat of a - 1 and a), then
+//   the exclusive prefix of the chunk sums per pol (+ the carried count) and
 //   the per-region noise variance sigma^2 = mean |z - dec z|^2.
 // Demap: lane = symbol; warp scan of r, derotation, hard bits packed with
 //   warp OR-reductions, optional max-log LLRs and symbols.
@@ -43,7 +46,7 @@ __host__ __device__ inline size_t pass1_warp_bytes(int chunk, int Nb) {
 }
 
 template <int MB, bool NEED_S2>
-__global__ void __launch_bounds__(kBpsWarps * 32) bps_pass1(BpsLaunch L) {
+__global__ void __launch_bounds__(kBpsWarps * 32) bps_pass1_slide(BpsLaunch L) {
   extern __shared__ float4 smem_raw[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t j = (int64_t)blockIdx.x * kBpsWarps + warp;
@@ -55,7 +58,7 @@ __global__ void __launch_bounds__(kBpsWarps * 32) bps_pass1(BpsLaunch L) {
   float2 *ys = reinterpret_cast<float2 *>(base + (size_t)M * 32 * sizeof(float));
   int8_t *bq = reinterpret_cast<int8_t *>(ys + pass1_ys_cap(L.chunk, Nb));
   const int64_t a = chunk_lo(L, j), b = min(a + (int64_t)L.chunk, L.k_hi);
-  const int64_t start = a > 0 ? a - 1 : a;
+  const int64_t start = a;
   const int64_t lo = start - Nb;                 // ys[i] holds symbol lo + i
   const int n_ys = (int)(b - 1 + Nb - lo + 1);
   float sb, cb;
@@ -119,7 +122,7 @@ __global__ void __launch_bounds__(kBpsWarps * 32) bps_pass1(BpsLaunch L) {
         const int bs = bsv[u];
         const int64_t k = start + t;
         if (k >= a) {
-          if (k > 0) R += unwrap_step(prev, bs);
+          if (k > a) R += unwrap_step(prev, bs);   // r_a: added by the scan
           if (NEED_S2) s2 += __shfl_sync(0xffffffffu, dist(t + Nb), bs);   // d of symbol k at angle bs
           if (lane == 0) bq[k - a] = (int8_t)bs;
         }
@@ -136,6 +139,115 @@ __global__ void __launch_bounds__(kBpsWarps * 32) bps_pass1(BpsLaunch L) {
   }
 }
 
+// Pass 1 at the default half window Nb = 16: the 33-symbol window of output
+// symbol 32 q + i spans staged positions 32 q + i .. 32 q + i + 32, i.e. the
+// suffix of block q from i plus the prefix of block q + 1 up to i:
+//   D_{32q+i} = sum_{j=i..31} d_{32q+j} + sum_{j=0..i} d_{32q+32+j}
+// (position m holds symbol a - 16 + m).  Each lane keeps its angle's distances
+// of the two blocks in registers: three adds per symbol and angle, no ring in
+// shared memory.  Distances are taken on the grid scaled by sqrt10 for 16QAM,
+// (||x'| - 2| - 1)^2 per dimension = 10 (x - dec x)^2 (the same argmin); the s2
+// sum is scaled back.
+constexpr int kBlkNb = 16;
+
+__host__ __device__ inline size_t pass1_blk_warp_bytes(int chunk) {
+  return (size_t)(chunk + 2 * kBlkNb) * sizeof(float2) + (size_t)((chunk + 15) / 16) * 16;
+}
+
+template <int MB, bool NEED_S2, bool EDGE>
+__device__ __forceinline__ void pass1_blocks(const float2 *ys, int n_ys, int v_lo, int v_hi, float2 rot, int nt,
+                                             int lane, int8_t *bq, int &R, float &s2) {
+  constexpr unsigned FULL = 0xffffffffu;
+  // distance of staged position m at this lane's angle (zero outside the stream;
+  // positions past the staged ones are read clamped: only unused sums see them)
+  auto dd = [&](int m) -> float {
+    const float2 w = cmul(ys[m < n_ys ? m : n_ys - 1], rot);
+    float ex, ey;
+    if (MB == 2) {
+      ex = fabsf(w.x) - 0.70710678118654752f;
+      ey = fabsf(w.y) - 0.70710678118654752f;
+    } else {
+      ex = fabsf(fabsf(w.x) - 2.f) - 1.f;
+      ey = fabsf(fabsf(w.y) - 2.f) - 1.f;
+    }
+    const float d = ex * ex + ey * ey;
+    return (EDGE && (m < v_lo || m >= v_hi)) ? 0.f : d;
+  };
+  float d0[32], d1[32];
+#pragma unroll
+  for (int j = 0; j < 32; ++j) d0[j] = dd(j);
+  int prev = 0;
+  for (int base = 0; base < nt; base += 32) {
+#pragma unroll
+    for (int j = 0; j < 32; ++j) d1[j] = dd(base + 32 + j);
+#pragma unroll
+    for (int j = 30; j >= 0; --j) d0[j] += d0[j + 1];   // suffix sums of block q
+    float pre = 0.f;
+#pragma unroll
+    for (int i = 0; i < 32; ++i) {
+      pre += d1[i];
+      if (base + i < nt) {
+        const unsigned key = __float_as_uint(d0[i] + pre);   // D >= 0: float order = bit order
+        const unsigned mn = __reduce_min_sync(FULL, key);
+        const int bs = __ffs(__ballot_sync(FULL, key == mn)) - 1;
+        if (base + i > 0) R += unwrap_step(prev, bs);       // r_a: added by the scan
+        prev = bs;
+        if (NEED_S2) {   // d of the symbol itself (position 32 q + i + 16) at angle bs
+          const float own = i < 16 ? d0[i + 16] - (i + 16 < 31 ? d0[i + 17] : 0.f) : d1[i - 16];
+          s2 += __shfl_sync(FULL, own, bs);
+        }
+        if (lane == 0) bq[base + i] = (int8_t)bs;
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < 32; ++j) d0[j] = d1[j];
+  }
+  if (MB == 4) s2 *= 0.1f;
+}
+
+template <int MB, bool NEED_S2>
+__global__ void __launch_bounds__(kBpsWarps * 32) bps_pass1_blk(BpsLaunch L) {
+  extern __shared__ float4 smem_raw[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t j = (int64_t)blockIdx.x * kBpsWarps + warp;
+  const int p = blockIdx.y;
+  if (j >= L.n_chunks) return;
+  char *base = reinterpret_cast<char *>(smem_raw) + (size_t)warp * pass1_blk_warp_bytes(L.chunk);
+  float2 *ys = reinterpret_cast<float2 *>(base);
+  int8_t *bq = reinterpret_cast<int8_t *>(ys + L.chunk + 2 * kBlkNb);
+  const int64_t a = chunk_lo(L, j), b = min(a + (int64_t)L.chunk, L.k_hi);
+  const int64_t lo = a - kBlkNb;                 // ys[m] holds symbol lo + m
+  const int nt = (int)(b - a);
+  const int n_ys = nt + 2 * kBlkNb;
+  float sb, cb;
+  sincospif(((float)lane / 32.f - 0.5f) * 0.5f, &sb, &cb);
+  // this lane's test angle exp(-j phi_b), scaled by sqrt10 for 16QAM
+  const float g = MB == 4 ? 3.16227766016837933f : 1.f;
+  const float2 rot = make_float2(cb * g, -sb * g);
+  const float2 *y = L.y + (int64_t)p * L.y_stride - L.y_base;
+  for (int i = lane; i < n_ys; i += 32) {       // coalesced staging
+    const int64_t k = lo + i;
+    ys[i] = (k >= 0 && k < L.K_end) ? y[k] : make_float2(0.f, 0.f);
+  }
+  __syncwarp();
+  const int64_t v_lo = -lo, v_hi = L.K_end - lo;  // valid staged positions [v_lo, v_hi)
+  int R = 0;
+  float s2 = 0.f;
+  if (v_lo > 0 || v_hi < n_ys) {                  // the window touches a stream end
+    pass1_blocks<MB, NEED_S2, true>(ys, n_ys, (int)max(v_lo, (int64_t)0), (int)min(v_hi, (int64_t)n_ys), rot, nt,
+                                    lane, bq, R, s2);
+  } else {
+    pass1_blocks<MB, NEED_S2, false>(ys, n_ys, 0, n_ys, rot, nt, lane, bq, R, s2);
+  }
+  __syncwarp();
+  int8_t *bh = L.bhat + (int64_t)p * L.bh_stride - L.bh_base;
+  for (int i = lane; i < nt; i += 32) bh[a + i] = bq[i];
+  if (lane == 0) {
+    L.chunk_r[(int64_t)p * L.n_chunks + j] = R;
+    L.chunk_s2[(int64_t)p * L.n_chunks + j] = s2;
+  }
+}
+
 // One CTA per pol: exclusive prefix of chunk unwrap sums (+carry) and region sigma^2.
 __global__ void __launch_bounds__(1024) bps_scan(BpsLaunch L) {
   __shared__ int64_t part[1024];
@@ -143,8 +255,16 @@ __global__ void __launch_bounds__(1024) bps_scan(BpsLaunch L) {
   const int64_t n = L.n_chunks;
   const int64_t per = (n + 1023) / 1024;
   const int64_t c0 = min((int64_t)t * per, n), c1 = min(c0 + per, n);
+  const int8_t *bh = L.bhat + (int64_t)p * L.bh_stride - L.bh_base;
   int64_t s = 0;
-  for (int64_t c = c0; c < c1; ++c) s += L.chunk_r[(int64_t)p * n + c];
+  for (int64_t c = c0; c < c1; ++c) {
+    // the chunk's boundary step r_a (pass 1 sums r_k over a < k < b)
+    const int64_t a = chunk_lo(L, c);
+    int r = L.chunk_r[(int64_t)p * n + c];
+    if (a > 0) r += unwrap_step((int)bh[a - 1], (int)bh[a]);
+    L.chunk_r[(int64_t)p * n + c] = r;
+    s += r;
+  }
   part[t] = s;
   __syncthreads();
   // Hillis-Steele inclusive scan over 1024 partials
@@ -269,16 +389,25 @@ __global__ void __launch_bounds__(kBpsWarps * 32) bps_demap(BpsLaunch L) {
 cudaError_t launch_bps(const BpsLaunch &L, cudaStream_t s) {
   if (L.n_chunks <= 0) return cudaSuccess;
   dim3 grid((unsigned)((L.n_chunks + kBpsWarps - 1) / kBpsWarps), 2);
-  const size_t sm = (size_t)kBpsWarps * pass1_warp_bytes(L.chunk, L.Nb);
+  const bool blk = L.Nb == kBlkNb;
+  const size_t sm = (size_t)kBpsWarps * (blk ? pass1_blk_warp_bytes(L.chunk) : pass1_warp_bytes(L.chunk, L.Nb));
   cudaError_t e;
-#define RX_PASS1(MB, NS)                                                                      \
-  e = cudaFuncSetAttribute(bps_pass1<MB, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm); \
-  if (e != cudaSuccess) return e;                                                             \
-  bps_pass1<MB, NS><<<grid, kBpsWarps * 32, sm, s>>>(L);
-  if (L.mod_bits == 4) {
-    if (L.need_s2) { RX_PASS1(4, true) } else { RX_PASS1(4, false) }
+#define RX_PASS1(KERNEL, MB, NS)                                                                       \
+  e = cudaFuncSetAttribute(KERNEL<MB, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);        \
+  if (e != cudaSuccess) return e;                                                                      \
+  KERNEL<MB, NS><<<grid, kBpsWarps * 32, sm, s>>>(L);
+  if (blk) {
+    if (L.mod_bits == 4) {
+      if (L.need_s2) { RX_PASS1(bps_pass1_blk, 4, true) } else { RX_PASS1(bps_pass1_blk, 4, false) }
+    } else {
+      if (L.need_s2) { RX_PASS1(bps_pass1_blk, 2, true) } else { RX_PASS1(bps_pass1_blk, 2, false) }
+    }
   } else {
-    if (L.need_s2) { RX_PASS1(2, true) } else { RX_PASS1(2, false) }
+    if (L.mod_bits == 4) {
+      if (L.need_s2) { RX_PASS1(bps_pass1_slide, 4, true) } else { RX_PASS1(bps_pass1_slide, 4, false) }
+    } else {
+      if (L.need_s2) { RX_PASS1(bps_pass1_slide, 2, true) } else { RX_PASS1(bps_pass1_slide, 2, false) }
+    }
   }
 #undef RX_PASS1
   e = cudaGetLastError();

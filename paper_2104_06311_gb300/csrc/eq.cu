@@ -419,7 +419,16 @@ __device__ __forceinline__ void run_span(const Hot hot, EqSmem &sm, const Span s
           const float2 w = cmul(yv, ln.rot[a]);
           // QPSK: |w - dec w|^2 = |y|^2 + 1 - sqrt2 (|Re w| + |Im w|), and |y|^2 is the same
           // for every angle, so -(|Re w| + |Im w|) orders the angles alike
-          d[a] = act ? (MB == 2 ? -(fabsf(w.x) + fabsf(w.y)) : qam_dist<MB>(w)) : 0.f;
+          // 16QAM on the grid scaled by sqrt10: (||x| - 2| - 1)^2 per dimension is
+          // 10 (x - dec x)^2 (levels +-1, +-3), the same order of the angles
+          float dq;
+          if (MB == 2) {
+            dq = -(fabsf(w.x) + fabsf(w.y));
+          } else {
+            const float ex = fabsf(fabsf(w.x) - 2.f) - 1.f, ey = fabsf(fabsf(w.y) - 2.f) - 1.f;
+            dq = ex * ex + ey * ey;
+          }
+          d[a] = act ? dq : 0.f;
         }
         fo_deferred();   // the previous step's pair, in the shadow of the reduce-scatter
         float e1[4], e2[2];
@@ -562,7 +571,9 @@ __device__ __forceinline__ void eq_body(const EqLaunch &L, const int cta, EqSmem
     // phi_b = (b/32 - 1/2) pi/2 for b = 8 part + a
     float sb, cb;
     sincospif(((float)(ln.part * 8 + a) / 32.f - 0.5f) * 0.5f, &sb, &cb);
-    ln.rot[a] = make_float2(cb, -sb);
+    // 16QAM: scaled by sqrt10, so that the distance below needs no level table
+    const float g = MB == 4 ? 3.16227766016837933f : 1.f;
+    ln.rot[a] = make_float2(cb * g, -sb * g);
   }
   {
     float sb, cb;
