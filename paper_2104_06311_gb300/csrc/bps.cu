@@ -150,18 +150,21 @@ __global__ void __launch_bounds__(kBpsWarps * 32) bps_pass1_slide(BpsLaunch L) {
 // sum is scaled back.
 constexpr int kBlkNb = 16;
 
+// Staged positions per warp: the chunk, its two 16-symbol halos and the 32
+// positions past them that the last block reads (zero), so that every read of
+// a block is at a constant offset.
+__host__ __device__ inline int pass1_blk_ys_cap(int chunk) { return chunk + 2 * kBlkNb + 32; }
 __host__ __device__ inline size_t pass1_blk_warp_bytes(int chunk) {
-  return (size_t)(chunk + 2 * kBlkNb) * sizeof(float2) + (size_t)((chunk + 15) / 16) * 16;
+  return (size_t)pass1_blk_ys_cap(chunk) * sizeof(float2) + (size_t)((chunk + 15) / 16) * 16;
 }
 
 template <int MB, bool NEED_S2, bool EDGE>
-__device__ __forceinline__ void pass1_blocks(const float2 *ys, int n_ys, int v_lo, int v_hi, float2 rot, int nt,
-                                             int lane, int8_t *bq, int &R, float &s2) {
+__device__ __forceinline__ void pass1_blocks(const float2 *ys, int v_lo, int v_hi, float2 rot, int nt, int lane,
+                                             int8_t *bq, int &R, float &s2) {
   constexpr unsigned FULL = 0xffffffffu;
-  // distance of staged position m at this lane's angle (zero outside the stream;
-  // positions past the staged ones are read clamped: only unused sums see them)
-  auto dd = [&](int m) -> float {
-    const float2 w = cmul(ys[m < n_ys ? m : n_ys - 1], rot);
+  // distance of staged position m at this lane's angle (zero outside the stream)
+  auto dd = [&](const float2 *yb, int off, int m) -> float {
+    const float2 w = cmul(yb[off], rot);
     float ex, ey;
     if (MB == 2) {
       ex = fabsf(w.x) - 0.70710678118654752f;
@@ -175,30 +178,37 @@ __device__ __forceinline__ void pass1_blocks(const float2 *ys, int n_ys, int v_l
   };
   float d0[32], d1[32];
 #pragma unroll
-  for (int j = 0; j < 32; ++j) d0[j] = dd(j);
+  for (int j = 0; j < 32; ++j) d0[j] = dd(ys, j, j);
   int prev = 0;
   for (int base = 0; base < nt; base += 32) {
+    const float2 *yb = ys + base;
+    const int cnt = min(32, nt - base);          // symbols of this block
 #pragma unroll
-    for (int j = 0; j < 32; ++j) d1[j] = dd(base + 32 + j);
+    for (int j = 0; j < 32; ++j) d1[j] = dd(yb, 32 + j, base + 32 + j);
 #pragma unroll
     for (int j = 30; j >= 0; --j) d0[j] += d0[j + 1];   // suffix sums of block q
     float pre = 0.f;
+    int mybs = 0;                                 // lane i: bhat of symbol base + i
 #pragma unroll
     for (int i = 0; i < 32; ++i) {
       pre += d1[i];
-      if (base + i < nt) {
-        const unsigned key = __float_as_uint(d0[i] + pre);   // D >= 0: float order = bit order
-        const unsigned mn = __reduce_min_sync(FULL, key);
-        const int bs = __ffs(__ballot_sync(FULL, key == mn)) - 1;
-        if (base + i > 0) R += unwrap_step(prev, bs);       // r_a: added by the scan
-        prev = bs;
-        if (NEED_S2) {   // d of the symbol itself (position 32 q + i + 16) at angle bs
-          const float own = i < 16 ? d0[i + 16] - (i + 16 < 31 ? d0[i + 17] : 0.f) : d1[i - 16];
-          s2 += __shfl_sync(FULL, own, bs);
-        }
-        if (lane == 0) bq[base + i] = (int8_t)bs;
+      const unsigned key = __float_as_uint(d0[i] + pre);   // D >= 0: float order = bit order
+      const unsigned mn = __reduce_min_sync(FULL, key);
+      const int bs = __ffs(__ballot_sync(FULL, key == mn)) - 1;
+      mybs = lane == i ? bs : mybs;
+      if (NEED_S2) {   // d of the symbol itself (position 32 q + i + 16) at angle bs
+        const float own = i < 16 ? d0[i + 16] - (i + 16 < 31 ? d0[i + 17] : 0.f) : d1[i - 16];
+        const float add = __shfl_sync(FULL, own, bs);
+        s2 += i < cnt ? add : 0.f;
       }
     }
+    // unwrap steps of the block's symbols at once (r of the chunk's first symbol: the scan)
+    const int up = __shfl_up_sync(FULL, mybs, 1);
+    const int pl = lane == 0 ? prev : up;
+    const int r = (lane < cnt && base + lane > 0) ? unwrap_step(pl, mybs) : 0;
+    R += __reduce_add_sync(FULL, r);
+    prev = __shfl_sync(FULL, mybs, cnt - 1);
+    if (lane < cnt) bq[base + lane] = (int8_t)mybs;
 #pragma unroll
     for (int j = 0; j < 32; ++j) d0[j] = d1[j];
   }
@@ -214,7 +224,7 @@ __global__ void __launch_bounds__(kBpsWarps * 32) bps_pass1_blk(BpsLaunch L) {
   if (j >= L.n_chunks) return;
   char *base = reinterpret_cast<char *>(smem_raw) + (size_t)warp * pass1_blk_warp_bytes(L.chunk);
   float2 *ys = reinterpret_cast<float2 *>(base);
-  int8_t *bq = reinterpret_cast<int8_t *>(ys + L.chunk + 2 * kBlkNb);
+  int8_t *bq = reinterpret_cast<int8_t *>(ys + pass1_blk_ys_cap(L.chunk));
   const int64_t a = chunk_lo(L, j), b = min(a + (int64_t)L.chunk, L.k_hi);
   const int64_t lo = a - kBlkNb;                 // ys[m] holds symbol lo + m
   const int nt = (int)(b - a);
@@ -225,19 +235,20 @@ __global__ void __launch_bounds__(kBpsWarps * 32) bps_pass1_blk(BpsLaunch L) {
   const float g = MB == 4 ? 3.16227766016837933f : 1.f;
   const float2 rot = make_float2(cb * g, -sb * g);
   const float2 *y = L.y + (int64_t)p * L.y_stride - L.y_base;
-  for (int i = lane; i < n_ys; i += 32) {       // coalesced staging
+  const int cap = pass1_blk_ys_cap(L.chunk);
+  for (int i = lane; i < cap; i += 32) {        // coalesced staging; zero past the window
     const int64_t k = lo + i;
-    ys[i] = (k >= 0 && k < L.K_end) ? y[k] : make_float2(0.f, 0.f);
+    ys[i] = (i < n_ys && k >= 0 && k < L.K_end) ? y[k] : make_float2(0.f, 0.f);
   }
   __syncwarp();
   const int64_t v_lo = -lo, v_hi = L.K_end - lo;  // valid staged positions [v_lo, v_hi)
   int R = 0;
   float s2 = 0.f;
   if (v_lo > 0 || v_hi < n_ys) {                  // the window touches a stream end
-    pass1_blocks<MB, NEED_S2, true>(ys, n_ys, (int)max(v_lo, (int64_t)0), (int)min(v_hi, (int64_t)n_ys), rot, nt,
-                                    lane, bq, R, s2);
+    pass1_blocks<MB, NEED_S2, true>(ys, (int)max(v_lo, (int64_t)0), (int)min(v_hi, (int64_t)n_ys), rot, nt, lane,
+                                    bq, R, s2);
   } else {
-    pass1_blocks<MB, NEED_S2, false>(ys, n_ys, 0, n_ys, rot, nt, lane, bq, R, s2);
+    pass1_blocks<MB, NEED_S2, false>(ys, 0, n_ys, rot, nt, lane, bq, R, s2);
   }
   __syncwarp();
   int8_t *bh = L.bhat + (int64_t)p * L.bh_stride - L.bh_base;
