@@ -29,7 +29,7 @@
 // schedule: a channel's time is its acquisition (A / B_u update steps, one
 // CTA pair) plus, per wave, ceil(P / pairs) passes of (S + W) / B_u steps and
 // a fixed wave overhead, times the step cost of its format (a 16QAM step costs
-// about 1.3 QPSK steps: its inner-BPS distance is longer); pairs go one at a
+// about 1.08 QPSK steps: its inner-BPS distance is longer); pairs go one at a
 // time to the channel whose time is currently largest, within the co-resident
 // CTA budget of the launch.
 #include <string.h>
@@ -54,7 +54,7 @@ constexpr int64_t kNcma = 8192, kAcqMin = 16384, kBlockSamples = 65536;
 constexpr double kMu = 1e-3, kRolloff = 0.1, kLamNm = 1550.0, kFoSmooth = 16.0;
 constexpr int kMaxChannels = 4096;
 constexpr int kWaveOverheadSteps = 8;   // cost model: grid barrier + FO fold per wave
-constexpr double kStep16qam = 1.3;       // cost model: 16QAM update step / QPSK step (fit to per-team
+constexpr double kStep16qam = 1.075;     // cost model: 16QAM update step / QPSK step (fit to per-team
                                         // end times of a 64-channel batch)
 
 struct Chan {
