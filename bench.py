@@ -57,6 +57,11 @@ def parse():
     return ap.parse_args()
 
 
+# ncu dram__bytes_read.sum + dram__bytes_write.sum of one step's eq_kernel launches per
+# symbol on the 10,000 km QPSK workload (the equaliser as of its window-copy version)
+EQ_DRAM_BYTES_PER_SYMBOL = 135.7e6 / 4194304
+
+
 def max_over_ranks(ms, dist=None, device="cpu"):
     """The slowest rank's time (every rank gets it); ms itself on one rank."""
     if dist is None:
@@ -762,8 +767,13 @@ def main():
         sm_mhz = pk.get("sm_max_mhz", 2070.0)
         peak = N_SM * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
         achieved = flop / (prof[stage][0] / args.steps / 1e3) / 1e12
+        # DRAM bytes of one step's equaliser launches: 32.4 B read per symbol in an ncu
+        # capture of the 2^22-symbol case (profiles/eq_kernel_c2_dram_traffic.md), scaled
+        # to K; recorded for the FP32 10,000 km workload only
+        traffic = (EQ_DRAM_BYTES_PER_SYMBOL * K
+                   if args.workload == "c2" and args.precision == "fp32" else None)
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None, "kernel": "eq_kernel",
+                "frac": achieved / peak, "traffic": traffic, "kernel": "eq_kernel",
                 "peak_note": f"FP32 SIMT: {N_SM} SM x {FP32_LANES_PER_SM} lanes x 2 flop x {sm_mhz:.0f} MHz"}
     else:
         per = {"cdc": 4 + 16, "bps": 16 + 16 + 1 + 0.25 * 2}[stage]   # bytes per sample-time
