@@ -76,27 +76,54 @@ __global__ void __launch_bounds__((SPLIT ? 1 : 2) * N / VPT) cdc_kernel(
   const int64_t lo = i * S_hop - V / 2;
   const int psplit = SPLIT ? (int)blockIdx.y : 0;
   S *b0 = smem, *b1 = smem + PADN;
-  // ingest: one 4-scalar sample-time gives both pols
-  for (int m = threadIdx.x; m < N; m += blockDim.x) {
-    const int64_t n = lo + m;
-    float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (n >= 0 && (n_total < 0 || n < n_total)) {
-      const uint8_t *src;
-      int64_t off;
-      if (n < call_first) { src = tail; off = n - tail_first; }
-      else { src = call; off = n - call_first; }
-      if (dtype == RX_I8x4) {
-        char4 c = reinterpret_cast<const char4 *>(src)[off];
-        x = make_float4((float)c.x, (float)c.y, (float)c.z, (float)c.w);
-      } else {
-        x = reinterpret_cast<const float4 *>(src)[off];
+  // ingest: one 4-scalar sample-time gives both pols.  A thread's loads are issued
+  // in groups of G before any is used (one memory latency per group, not one per
+  // sample): the block size is a compile-time constant and the loops unroll.
+  constexpr int BS = (SPLIT ? 1 : 2) * N / VPT;
+  constexpr int PER = N / BS;
+  constexpr int G = PER < 8 ? PER : 8;
+  auto src_of = [&](int64_t n, int64_t &off) -> const uint8_t * {
+    if (n < call_first) { off = n - tail_first; return tail; }
+    off = n - call_first;
+    return call;
+  };
+#pragma unroll 1
+  for (int r0 = 0; r0 < PER; r0 += G) {
+    float4 x[G];
+    if (dtype == RX_I8x4) {
+#pragma unroll
+      for (int r = 0; r < G; ++r) {
+        const int64_t n = lo + threadIdx.x + (r0 + r) * BS;
+        x[r] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (n >= 0 && (n_total < 0 || n < n_total)) {
+          int64_t off;
+          const uint8_t *src = src_of(n, off);
+          const char4 c = reinterpret_cast<const char4 *>(src)[off];
+          x[r] = make_float4((float)c.x, (float)c.y, (float)c.z, (float)c.w);
+        }
+      }
+    } else {
+#pragma unroll
+      for (int r = 0; r < G; ++r) {
+        const int64_t n = lo + threadIdx.x + (r0 + r) * BS;
+        x[r] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (n >= 0 && (n_total < 0 || n < n_total)) {
+          int64_t off;
+          const uint8_t *src = src_of(n, off);
+          x[r] = reinterpret_cast<const float4 *>(src)[off];
+        }
       }
     }
-    if (SPLIT) {
-      b0[pad(m)] = st2<S>(psplit ? make_float2(x.z * scale, x.w * scale) : make_float2(x.x * scale, x.y * scale));
-    } else {
-      b0[pad(m)] = st2<S>(make_float2(x.x * scale, x.y * scale));
-      b1[pad(m)] = st2<S>(make_float2(x.z * scale, x.w * scale));
+#pragma unroll
+    for (int r = 0; r < G; ++r) {
+      const int m = threadIdx.x + (r0 + r) * BS;
+      if (SPLIT) {
+        b0[pad(m)] = st2<S>(psplit ? make_float2(x[r].z * scale, x[r].w * scale)
+                                   : make_float2(x[r].x * scale, x[r].y * scale));
+      } else {
+        b0[pad(m)] = st2<S>(make_float2(x[r].x * scale, x[r].y * scale));
+        b1[pad(m)] = st2<S>(make_float2(x[r].z * scale, x[r].w * scale));
+      }
     }
   }
   __syncthreads();
