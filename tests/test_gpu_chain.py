@@ -210,6 +210,22 @@ def test_streaming_calls_equal_one_call():
         assert np.array_equal(many["llr"], one["llr"]), chunk
 
 
+@pytest.mark.parametrize("Nb", [0, 7, 24])
+def test_bps_other_half_windows(Nb):
+    """Half windows other than 16 take the sliding-ring BPS pass (16 takes the register
+    blocks); with phase noise the unwrap count moves, so the scan's boundary step of
+    every chunk is exercised, in one call and across calls."""
+    lk = L.Link(n_sym=(1 << 15) + 321, L_km=500.0, snr_db=13.0, linewidth_hz=1e6, seed=2300 + Nb)
+    g = L.generate(lk)
+    p = rx_params(lk, g.in_scale, bps_halfwin=Nb)
+    one = run_gpu(p, g.samples)
+    rep, _ = check_chain(p, g, one, {})
+    print("BPS half window", Nb, rep)
+    many = run_gpu(p, g.samples, chunk=3 * 4096 + 2, reserve=1 << 16)
+    assert np.array_equal(many["words"], one["words"])
+    assert np.array_equal(many["llr"], one["llr"])
+
+
 def test_state_save_restore_resumes_bit_exactly():
     import torch
     from chain_helpers import make_receiver
