@@ -292,15 +292,19 @@ __global__ void __launch_bounds__(1024) bps_scan(BpsLaunch L) {
   }
   __syncthreads();
   if (t == 1023) L.m_carry[p] += part[1023];
-  // regions: [0, A), then [A + r span, ...), clipped to [k_lo, k_hi)
+  if (!L.need_s2) return;   // sigma^2 feeds the LLRs only
+  // regions: [0, A), then [A + r span, ...), clipped to [k_lo, k_hi) (calls emit whole
+  // regions, so a region's chunks start at its first symbol)
   const int64_t r_lo = L.k_lo < L.A ? 0 : 1 + (L.k_lo - L.A) / L.span;
   const int64_t r_hi = L.k_hi <= L.A ? 1 : 1 + (L.k_hi - 1 - L.A) / L.span + 1;
   for (int64_t r = r_lo + t; r < r_hi; r += 1024) {
     const int64_t s_r = r == 0 ? 0 : L.A + (r - 1) * L.span;
     const int64_t e_r = min(r == 0 ? L.A : s_r + L.span, L.k_hi);
+    const int64_t c0 = (s_r - L.k_lo) / L.chunk;
+    const int64_t c1 = min(n, (e_r - L.k_lo + L.chunk - 1) / L.chunk);   // chunks starting before e_r
     double acc = 0.0;
-    for (int64_t c = (s_r - L.k_lo) / L.chunk; c < n && chunk_lo(L, c) < e_r; ++c)
-      acc += (double)L.chunk_s2[(int64_t)p * n + c];
+#pragma unroll 8
+    for (int64_t c = c0; c < c1; ++c) acc += (double)L.chunk_s2[(int64_t)p * n + c];
     L.region_s2[(int64_t)p * (r_hi - r_lo) + (r - r_lo)] = acc / (double)(e_r - s_r);
   }
 }
