@@ -82,7 +82,7 @@ enum {
   RX_P_ACQ_MIN = 15,       /* minimum acquisition length (default 16384)             */
   RX_P_FO_SMOOTH = 16,     /* frequency tracking divisor (default 16)                */
   RX_P_FO_TRACK = 17,      /* 1 = estimate and remove the frequency offset (default) */
-  RX_P_LLR_OUT = 18,       /* 1 = write LLRs to rx_out.llr                          */
+  RX_P_LLR_OUT = 18,       /* 1 = FP32 LLRs to rx_out.llr, 2 = FP16 (same layout)   */
   RX_P_SYM_OUT = 19,       /* 1 = write phase-recovered symbols to rx_out.sym        */
   RX_P_EQ_OUT = 20,        /* 1 = write equaliser outputs to rx_out.eq               */
   RX_P_CDC_OUT = 21,       /* 1 = write CDC outputs to rx_out.cdc (tests)            */
@@ -121,7 +121,8 @@ typedef struct {
  * (LSB first; QPSK bits I,Q; 16QAM bits I-sign, I-outer, Q-sign, Q-outer). */
 typedef struct {
   uint32_t *bits;  int64_t bits_stride;   /* words per pol (required)              */
-  float *llr;      int64_t llr_stride;    /* floats per pol, j*m + t (LLR_OUT)      */
+  float *llr;      int64_t llr_stride;    /* values per pol, j*m + t (LLR_OUT; with
+                                             LLR_OUT = 2 the buffer holds binary16) */
   float *sym;      int64_t sym_stride;    /* complex (2 floats) per pol (SYM_OUT)   */
   float *eq;       int64_t eq_stride;     /* complex per pol, equaliser out (EQ_OUT)*/
   float *cdc;      int64_t cdc_stride;    /* complex per pol, per SAMPLE (CDC_OUT);

@@ -21,6 +21,8 @@
 //   the per-region noise variance sigma^2 = mean |z - dec z|^2.
 // Demap: lane = symbol; warp scan of r, derotation, hard bits packed with
 //   warp OR-reductions, optional max-log LLRs and symbols.
+#include <cuda_fp16.h>
+
 #include "common.cuh"
 #include "rx_internal.h"
 
@@ -383,8 +385,15 @@ __global__ void __launch_bounds__(kBpsWarps * 32) bps_demap(BpsLaunch L) {
       if (L.llr) {
         float o[MB];
         llr_bits<MB>(z, s2inv, o);
+        const int64_t at = (int64_t)p * L.llr_stride + jo * MB;
+        if (L.llr_fp16) {
+          __half *h = reinterpret_cast<__half *>(L.llr);
 #pragma unroll
-        for (int t = 0; t < MB; ++t) L.llr[(int64_t)p * L.llr_stride + jo * MB + t] = o[t];
+          for (int t = 0; t < MB; ++t) h[at + t] = __float2half_rn(o[t]);
+        } else {
+#pragma unroll
+          for (int t = 0; t < MB; ++t) L.llr[at + t] = o[t];
+        }
       }
     }
     // pack: 32 / MB symbols per word

@@ -363,8 +363,8 @@ rx_status rx_set_param(rx_stream *rx, int key, double v) {
       if (v != 2 && v != 4) return fail(rx, RX_EUNSUPPORTED, "modulation must be 2 (QPSK) or 4 (16QAM) bits");
       rx->mod_bits = (int)v;
       return RX_OK;
-    case RX_P_FFT_N: s = as_int(0, 1 << 20, &t); rx->fft_n_req = (int)t; break;
-    case RX_P_OVERLAP: s = as_int(0, 1 << 20, &t); rx->overlap_req = (int)t; break;
+    case RX_P_FFT_N: s = as_int(0, 1 << 20, &t); if (s == RX_OK) rx->fft_n_req = (int)t; break;
+    case RX_P_OVERLAP: s = as_int(0, 1 << 20, &t); if (s == RX_OK) rx->overlap_req = (int)t; break;
     case RX_P_ROLLOFF:
       if (!(v > 0 && v <= 1)) return fail(rx, RX_EINVAL, "roll-off must be in (0, 1]");
       rx->rolloff = v;
@@ -376,10 +376,10 @@ rx_status rx_set_param(rx_stream *rx, int key, double v) {
     case RX_P_MU_CMA: rx->mu_cma = v; return RX_OK;
     case RX_P_MU_DD: rx->mu_dd = v; return RX_OK;
     case RX_P_N_CMA: s = as_int(0, (int64_t)1 << 40, &rx->n_cma); break;
-    case RX_P_UPDATE_BLOCK: s = as_int(1, 32, &t); rx->Bu = (int)t; break;
-    case RX_P_SEG_LEN: s = as_int(32, 1 << 20, &t); rx->S = (int)t; break;
-    case RX_P_SEG_PRETRAIN: s = as_int(0, 1 << 20, &t); rx->W = (int)t; break;
-    case RX_P_BPS_HALFWIN: s = as_int(0, 64, &t); rx->Nb = (int)t; break;
+    case RX_P_UPDATE_BLOCK: s = as_int(1, 32, &t); if (s == RX_OK) rx->Bu = (int)t; break;
+    case RX_P_SEG_LEN: s = as_int(32, 1 << 20, &t); if (s == RX_OK) rx->S = (int)t; break;
+    case RX_P_SEG_PRETRAIN: s = as_int(0, 1 << 20, &t); if (s == RX_OK) rx->W = (int)t; break;
+    case RX_P_BPS_HALFWIN: s = as_int(0, 64, &t); if (s == RX_OK) rx->Nb = (int)t; break;
     case RX_P_BLOCK_SAMPLES: s = as_int(64, (int64_t)1 << 40, &rx->block_samples); break;
     case RX_P_IN_SCALE: rx->in_scale = v; return RX_OK;
     case RX_P_ACQ_MIN: s = as_int(0, (int64_t)1 << 40, &rx->acq_min); break;
@@ -388,13 +388,13 @@ rx_status rx_set_param(rx_stream *rx, int key, double v) {
       rx->fo_smooth = v;
       return RX_OK;
     case RX_P_FO_TRACK: rx->fo_track = v != 0; return RX_OK;
-    case RX_P_LLR_OUT: rx->llr_out = v != 0; return RX_OK;
+    case RX_P_LLR_OUT: s = as_int(0, 2, &t); if (s == RX_OK) rx->llr_out = (int)t; return s;
     case RX_P_SYM_OUT: rx->sym_out = v != 0; return RX_OK;
     case RX_P_EQ_OUT: rx->eq_out = v != 0; return RX_OK;
     case RX_P_CDC_OUT: rx->cdc_out = v != 0; return RX_OK;
     case RX_P_PROFILE: rx->profile = v != 0; return RX_OK;
-    case RX_P_PIPELINE: s = as_int(1, kMaxPieces, &t); rx->pieces = (int)t; return s;
-    case RX_P_PRECISION: s = as_int(0, 2, &t); rx->fmt = (int)t; break;
+    case RX_P_PIPELINE: s = as_int(1, kMaxPieces, &t); if (s == RX_OK) rx->pieces = (int)t; return s;
+    case RX_P_PRECISION: s = as_int(0, 2, &t); if (s == RX_OK) rx->fmt = (int)t; break;
     default: return fail(rx, RX_EINVAL, "unknown parameter key");
   }
   if (s != RX_OK) return s;
@@ -767,6 +767,7 @@ rx_status rx_process(rx_stream *rx, const rx_in *in, rx_out *out) {
       B.bits = out->bits;
       B.bits_stride = out->bits_stride;
       B.llr = rx->llr_out ? out->llr : nullptr;
+      B.llr_fp16 = rx->llr_out == 2;
       B.llr_stride = out->llr_stride;
       B.sym = rx->sym_out ? (float2 *)out->sym : nullptr;
       B.sym_stride = out->sym_stride;

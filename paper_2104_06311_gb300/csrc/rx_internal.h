@@ -94,6 +94,7 @@ struct BpsLaunch {
   // outputs
   uint32_t *bits; int64_t bits_stride;
   float *llr; int64_t llr_stride;
+  int llr_fp16;             // 1: llr holds IEEE binary16 values (round to nearest)
   float2 *sym; int64_t sym_stride;
   int64_t out_first;        // stream index of output symbol 0
 };

@@ -260,7 +260,9 @@ class Receiver:
         words = (capacity * m + 31) // 32
         o = {"bits": t.zeros((2, words), dtype=t.int32, device="cuda"), "capacity": capacity}
         if llr:
-            o["llr"] = t.zeros((2, capacity * m), dtype=t.float32, device="cuda")
+            # LLR_OUT = 2 writes binary16 LLRs
+            dt = t.float16 if int(self.get_param("LLR_OUT")) == 2 else t.float32
+            o["llr"] = t.zeros((2, capacity * m), dtype=dt, device="cuda")
         if sym:
             o["sym"] = t.zeros((2, capacity), dtype=t.complex64, device="cuda")
         if eq:
@@ -292,7 +294,7 @@ class Receiver:
         o.bits = bits.data_ptr() + (sym_offset * m // 32) * 4
         o.bits_stride = bits.shape[1]
         if "llr" in out:
-            o.llr = out["llr"].data_ptr() + sym_offset * m * 4
+            o.llr = out["llr"].data_ptr() + sym_offset * m * out["llr"].element_size()
             o.llr_stride = out["llr"].shape[1]
         if "sym" in out:
             o.sym = out["sym"].data_ptr() + sym_offset * 8

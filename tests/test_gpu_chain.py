@@ -226,6 +226,30 @@ def test_bps_other_half_windows(Nb):
     assert np.array_equal(many["llr"], one["llr"])
 
 
+def test_fp16_llr_output():
+    """LLR_OUT = 2 writes the FP32 path's LLRs rounded to binary16 (nearest even)."""
+    import torch
+    from chain_helpers import make_receiver
+    lk = L.Link(n_sym=20000, L_km=300.0, snr_db=12.0, seed=4242)
+    g = L.generate(lk)
+    p = rx_params(lk, g.in_scale)
+    x = torch.from_numpy(g.samples).cuda()
+    got = []
+    for mode in (1, 2):
+        rx = make_receiver(p, LLR_OUT=mode)
+        out = rx.alloc_out(lk.n_sym + 64, llr=True)
+        _, n1, _, _ = rx.process(x, out, 0)
+        _, n2, _, _ = rx.process(None, out, n1)
+        torch.cuda.synchronize()
+        assert n1 + n2 == lk.n_sym
+        assert out["llr"].dtype == (torch.float32 if mode == 1 else torch.float16)
+        got.append((out["llr"][:, :lk.n_sym * p.bits].cpu().numpy(), out["bits"].cpu().numpy()))
+        rx.close()
+    (l32, b32), (l16, b16) = got
+    assert np.array_equal(b32, b16)
+    assert np.array_equal(l16, l32.astype(np.float16))
+
+
 def test_state_save_restore_resumes_bit_exactly():
     import torch
     from chain_helpers import make_receiver
