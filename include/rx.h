@@ -90,10 +90,14 @@ enum {
   RX_P_PIPELINE = 23,      /* pieces per call overlapped on three internal streams
                               (CDC ahead of, BPS behind the equaliser); 1..64,
                               default 12; 1 = the stages run back to back          */
-  RX_P_PRECISION = 24      /* precision form: storage of the CDC transform and of
+  RX_P_PRECISION = 24,     /* precision form: storage of the CDC transform and of
                               its output: 0 = FP32 (default), 1 = FP16, 2 = BF16;
                               butterflies and the equaliser compute in FP32, the
                               phase trackers stay 64-bit                           */
+  RX_P_INNER_TRACE = 25    /* > 0: record the equaliser's inner BPS angle of every
+                              DD update block, for that many entries per butterfly
+                              row (read with rx_trace_inner); 0 = off (default).
+                              Verification support, not from the paper          */
 };
 
 /* Stages reported by rx_profile. */
@@ -182,6 +186,20 @@ rx_status rx_ber(rx_stream *rx, const uint32_t *rx_bits, int64_t rx_stride,
  * started from, h[p][q][i] as interleaved complex floats (2*2*ntaps*2),
  * the per-symbol frequency offset dw and the phase base Phi.  Synchronises. */
 rx_status rx_trace(rx_stream *rx, int64_t wave, float *taps, double *dw, double *Phi);
+
+/* Inner BPS angles recorded while RX_P_INNER_TRACE > 0: dst[p * count + j] =
+ * entry first + j of butterfly row p (int8 angle index 0..31, -1 = block not
+ * run), for j < count.  Entry layout per row: the acquisition's DD update
+ * blocks first (entry t = the block starting at symbol N_CMA + t B_u),
+ * *n_acq entries; then *per_segment entries for each segment g (entry
+ * *n_acq + g *per_segment + t = the t-th update block of segment g, counted
+ * from its first pre-training symbol).  n_acq and per_segment may be NULL.
+ * The trace lets a checker tell which of two near-equal window sums the
+ * device took (the decision is an argmin over FP32 sums; the paper's DD-LMS
+ * has no phase search).  RX_EINVAL if the range lies outside the recorded
+ * entries.  Synchronises the bound stream. */
+rx_status rx_trace_inner(rx_stream *rx, int64_t first, int64_t count, int8_t *dst, int64_t *n_acq,
+                         int32_t *per_segment);
 
 /* Serialise / restore the streaming state (taps, tracking state, carried
  * samples and symbols, counters) as an opaque host blob.  rx_get_state with

@@ -298,15 +298,56 @@ def _bps_distance(y: np.ndarray, phis: np.ndarray, mod: str) -> np.ndarray:
     return r.real ** 2 + r.imag ** 2
 
 
+FO_GRID_BITS = 16
+
+
+def fo_units(rate: float, sps: int) -> tuple[int, float]:
+    """A rate in rad/symbol as the nearest whole number of 2^-G turns per sample.
+
+    G = FO_GRID_BITS.  Returns (units, edge): `edge` is the distance of the
+    unrounded value from the nearest rounding boundary, in units (0.5 at a grid
+    point, 0 exactly half-way between two).  The paper has no frequency
+    tracker; this grid is a reading of the textbook estimator: every quantity
+    the tracker integrates is a whole multiple of 2^-G turns, so that the phase
+    it accumulates over a stream is exact (no rounding to compound from wave
+    to wave) and any implementation that rounds the same estimates to the same
+    grid tracks the same phase.  2^-16 turns per sample is 1.9e-4 rad per
+    symbol at 2 samples per symbol (305 kHz at 10 GBd): a residual offset of
+    half of that turns a symbol by < 1e-4 rad, and moves the phase by 3e-3
+    rad over a 33-symbol BPS window, well inside what the phase search
+    tracks, while the per-wave estimates it rounds scatter by ~3e-3 rad per
+    symbol.  Ties round to even.
+    """
+    x = rate / (sps * TWO_PI) * float(1 << FO_GRID_BITS)
+    u = int(np.rint(x))
+    return u, abs(abs(x - math.floor(x)) - 0.5)
+
+
+def units_to_rate(u: int, sps: int) -> float:
+    """Whole 2^-G turns per sample -> rad/symbol."""
+    return u * sps * TWO_PI / float(1 << FO_GRID_BITS)
+
+
+def units_to_phase(phi: int) -> float:
+    """A phase of phi 2^-G turns (taken mod 2^G) -> radians in [-pi, pi)."""
+    M = 1 << FO_GRID_BITS
+    phi %= M
+    if phi >= M // 2:
+        phi -= M
+    return phi * TWO_PI / float(M)
+
+
 class _Window:
     """Rotated FIR input for symbols [k_lo, k_hi): samples 2k_lo-c .. 2(k_hi-1)+c.
 
     Rotation (frequency-offset removal in front of the FIR) by
-    exp(-j(Phi + (n - n0) * delta)); delta=None means no rotation.
+    exp(-j 2 pi t_n / 2^G), t_n = (phi + (n - n0) d) mod 2^G: phase base phi
+    and per-sample increment d are whole 2^-G turns (fo_units), so t_n is an
+    exact integer.  d=None means no rotation.
     """
 
     def __init__(self, u: np.ndarray, k_lo: int, k_hi: int, c: int,
-                 Phi: float = 0.0, n0: int = 0, delta: float | None = None):
+                 phi: int = 0, n0: int = 0, d: int | None = None):
         n = u.shape[-1]
         self.lo = 2 * k_lo - c
         hi = 2 * (k_hi - 1) + c + 1
@@ -314,8 +355,10 @@ class _Window:
         ok = (idx >= 0) & (idx < n)
         seg = np.zeros((2, hi - self.lo), np.complex128)
         seg[:, ok] = u[:, idx[ok]]
-        if delta is not None:
-            seg = seg * np.exp(-1j * (Phi + (idx - n0) * delta))[None, :]
+        if d is not None:
+            M = 1 << FO_GRID_BITS
+            t = np.mod(phi + (idx.astype(np.int64) - n0) * d, M)
+            seg = seg * np.exp(-1j * (TWO_PI / M) * t.astype(np.float64))[None, :]
         self.seg = seg
 
     def taps_input(self, k0: int, k1: int, T: int, c: int) -> np.ndarray:
@@ -326,16 +369,34 @@ class _Window:
         return np.transpose(self.seg[:, idx], (1, 0, 2))
 
 
-def lms_step(h: np.ndarray, X: np.ndarray, mode: str, p: RxParams, phis: np.ndarray):
+# Decisions where two candidates are equally correct to within rounding: the
+# inner BPS argmin when the runner-up's block sum is within INNER_TIE_REL of the
+# minimum (an FP32 sum of 32 order-one terms is exact to ~1e-6 of such a sum),
+# and a tracker rounding when the unrounded value lies within TRACK_TIE_UNITS of
+# the half-way point between two grid values.  At such a decision another
+# implementation's choice is as valid as this one's; `equalize` can take it
+# (passed in `ties`) and logs every decision it took that way.
+INNER_TIE_REL = 1e-4
+TRACK_TIE_UNITS = 2e-3
+
+
+def lms_step(h: np.ndarray, X: np.ndarray, mode: str, p: RxParams, phis: np.ndarray,
+             choice=None, log: list | None = None, where=None):
     """One block update of the butterfly; returns (y (2,nk), new h).
 
     y_p[k] = sum_{q,i} h_pq[i] u_q[2k+c-i].
     CMA error e = y(|y|^2 - R2) (Godard's constant-modulus criterion).
     DD error e = y - d e^{j theta}, d = dec(y e^{-j theta}), theta = the test
-    angle minimising the summed BPS distance over this block (the inner phase).
+    angle minimising the summed BPS distance over this block (the inner phase;
+    smallest index on exact ties).
     Update h_pq[i] -= mu * sum_k e_p[k] conj(u_q[2k+c-i]) (a block sum).
     The paper's equaliser is a decision-directed LMS adapted in time domain
     (processing-chain paragraph); CMA and the butterfly are paper-silent.
+
+    choice: optional per-row angle indices another implementation took for
+    this block (negative = none); row p takes choice[p] instead of its own
+    argmin only where choice[p]'s block sum is within INNER_TIE_REL of the
+    minimum, and appends (where, p, own, taken, relative gap) to `log`.
     """
     y = np.einsum("pqi,kqi->pk", h, X)
     if mode == "cma":
@@ -343,7 +404,17 @@ def lms_step(h: np.ndarray, X: np.ndarray, mode: str, p: RxParams, phis: np.ndar
         mu = p.mu_cma
     else:
         d = _bps_distance(y, phis, p.mod)                 # (2, nk, B)
-        b = np.argmin(np.sum(d, axis=1), axis=-1)         # first minimum per pol
+        D = np.sum(d, axis=1)                             # (2, B)
+        b = np.argmin(D, axis=-1)                         # first minimum per pol
+        if choice is not None:
+            for pp in range(2):
+                c = int(choice[pp])
+                if 0 <= c < len(phis) and c != b[pp]:
+                    gap = (D[pp, c] - D[pp, b[pp]]) / max(D[pp, b[pp]], 1e-300)
+                    if gap < INNER_TIE_REL:
+                        if log is not None:
+                            log.append(("inner", where, pp, int(b[pp]), c, float(gap)))
+                        b[pp] = c
         th = phis[b][:, None]
         rot = np.exp(1j * th)
         e = y - decide(y * np.conj(rot), p.mod) * rot
@@ -352,8 +423,17 @@ def lms_step(h: np.ndarray, X: np.ndarray, mode: str, p: RxParams, phis: np.ndar
     return y, h - mu * g
 
 
-def equalize(u: np.ndarray, p: RxParams, trace: dict | None = None,
-             follow: dict | None = None) -> np.ndarray:
+def _track_tie(own: int, edge: float, other, kind: str, where, log: list) -> int:
+    """The tracker rounding to use: `other` (another implementation's rounding
+    of the same quantity) where this one's value lies within TRACK_TIE_UNITS of
+    the half-way point and `other` is the neighbouring grid value, else own."""
+    if other is not None and other != own and abs(other - own) == 1 and edge < TRACK_TIE_UNITS:
+        log.append((kind, where, own, int(other), float(edge)))
+        return int(other)
+    return own
+
+
+def equalize(u: np.ndarray, p: RxParams, trace: dict | None = None, ties: dict | None = None) -> np.ndarray:
     """Butterfly equaliser over the whole stream with the segment schedule.
 
     u: (2, n) CDC output at 2 samples/symbol; returns y (2, K), K = n // 2.
@@ -363,25 +443,34 @@ def equalize(u: np.ndarray, p: RxParams, trace: dict | None = None,
       * Acquisition: symbols [0, A), A = min(max(N_CMA, 2^14), K), one chain
         of update blocks of B_u symbols.  CMA (no rotation) on [0, N_CMA');
         the frequency offset is then estimated from the CMA outputs in
-        [N_CMA'/2, N_CMA') and DD-LMS runs on [N_CMA', A) with the input
-        rotated by exp(-j (n - 2 N_CMA') dw/sps).
+        [N_CMA'/2, N_CMA') and rounded to the tracker grid, d_0 = fo_units(dw),
+        and DD-LMS runs on [N_CMA', A) with sample n rotated by
+        exp(-j 2 pi (n - 2 N_CMA') d_0 / 2^G).
       * Waves: symbols [A, K) in segments of S; wave w holds P segments.
         Every segment of wave w starts from the taps at the end of the last
         segment of wave w-1 (the acquisition for w = 0), pre-trains on the W
         symbols before it (DD, outputs discarded), then equalises its own
-        symbols.  Its input is rotated by exp(-j (Phi_w + (n - n_w) dw_w/sps)),
-        n_w = 2 (A + w P S).
-      * Frequency tracking per wave: dw_{w+1} = dw_w + r_w/16 with r_w a
-        quarter of the argument of fo_estimate_sum over adjacent pairs
-        inside each segment; Phi_{w+1} = remainder(Phi_w + 2PS dw_w/sps, 2pi).
+        symbols.  Its input is rotated by exp(-j 2 pi (phi_w + (n - n_w) d_w)
+        / 2^G), n_w = 2 (A + w P S).
+      * Frequency tracking per wave (one-wave lag): r_w is a quarter of the
+        argument of fo_estimate_sum over adjacent pairs inside each segment;
+        d_{w+1} = d_w + fo_units(r_w / fo_smooth); phi_0 = (2A - 2 N_CMA') d_0,
+        phi_{w+1} = phi_w + 2PS d_w, all mod 2^G.
 
-    The tracked phase integrates the frequency estimate over 2PS samples per
-    wave, so a rounding-level difference in an estimate (FP32 vs FP64) grows
-    into a phase offset that no later step removes.  With `follow` (keys
-    acq_dw, wave_dw, wave_Phi: another implementation's tracker state) the
-    schedule runs on that state instead of its own estimates; its own
-    estimates are still computed and recorded in `trace` (acq_dw_own,
-    wave_r), so each estimate can be compared on identical data.
+    The tracker's state (phi, d) is integer (fo_units): the phase it
+    integrates over the stream is exact, so implementations that round the
+    same estimates to the same grid follow the same phase for the whole
+    stream.  `trace` records the state at every wave start (taps, dw in
+    rad/symbol, Phi in rad, and the integers), the estimates, each rounding's
+    distance from its rounding boundary (fo_edge) and the tie log.
+
+    ties: optional choices of another implementation at the chain's discrete
+    decisions -- 'acq_units' (d_0), 'wave_units' ((phi_w, d_w) per wave),
+    'inner' ([2][n] inner BPS angle per DD update block: the acquisition's
+    'inner_acq' blocks, then 'inner_spb' per segment counted from its first
+    pre-training block).  Each is taken only at a near-tie (INNER_TIE_REL,
+    TRACK_TIE_UNITS); every decision taken that way is logged in
+    trace['ties'].  Without `ties` the schedule runs on its own decisions only.
     """
     p = p.resolved()
     n = u.shape[-1]
@@ -389,35 +478,51 @@ def equalize(u: np.ndarray, p: RxParams, trace: dict | None = None,
     T = p.ntaps
     c = (T - 1) // 2
     Bu = p.upd_block
+    M = 1 << FO_GRID_BITS
     phis = bps_outer_angles(p.bps_angles)
     y = np.zeros((2, K), np.complex128)
     h = np.zeros((2, 2, T), np.complex128)
     h[0, 0, c] = 1.0
     h[1, 1, c] = 1.0
     A = p.acq_len(K)
+    tie_log: list = []
+    if trace is not None:
+        trace["ties"] = tie_log
     if K == 0:
         return y
+    ties = ties or {}
+    inner = ties.get("inner")
+    n_acq_blk = int(ties.get("inner_acq", 0))
+    spb = int(ties.get("inner_spb", 0))
+
+    def inner_choice(j):
+        if inner is None or j < 0 or j >= inner.shape[1]:
+            return None
+        return inner[:, j]
+
     n_cma = min(p.n_cma, A)
+    rot = None if not p.fo_track else 0    # None: no rotation
     # -- acquisition, CMA part
     win = _Window(u, 0, n_cma, c)
     for k0 in range(0, n_cma, Bu):
         k1 = min(k0 + Bu, n_cma)
         y[:, k0:k1], h = lms_step(h, win.taps_input(k0, k1, T, c), "cma", p, phis)
-    dw = 0.25 * np.angle(fo_estimate_sum(y[:, n_cma // 2:n_cma], p.mod)) if p.fo_track else 0.0
-    dw_own = dw
-    if follow is not None:
-        dw = follow["acq_dw"]
-    delta = dw / p.sps
+    dw_est = 0.25 * np.angle(fo_estimate_sum(y[:, n_cma // 2:n_cma], p.mod)) if p.fo_track else 0.0
+    d, edge = fo_units(dw_est, p.sps)
+    edges = [edge] if p.fo_track else []
+    d = _track_tie(d, edge, ties.get("acq_units"), "acq", 0, tie_log)
     # -- acquisition, DD part
     if A > n_cma:
-        win = _Window(u, n_cma, A, c, 0.0, 2 * n_cma, delta)
-        for k0 in range(n_cma, A, Bu):
+        win = _Window(u, n_cma, A, c, 0, 2 * n_cma, d if rot is not None else None)
+        for t, k0 in enumerate(range(n_cma, A, Bu)):
             k1 = min(k0 + Bu, A)
-            y[:, k0:k1], h = lms_step(h, win.taps_input(k0, k1, T, c), "dd", p, phis)
-    Phi = math.remainder((2 * A - 2 * n_cma) * delta, TWO_PI)
+            y[:, k0:k1], h = lms_step(h, win.taps_input(k0, k1, T, c), "dd", p, phis,
+                                      inner_choice(t) if t < n_acq_blk else None, tie_log, ("acq", t))
+    phi = ((2 * A - 2 * n_cma) * d) % M
     if trace is not None:
-        trace.update(acq_dw=dw, acq_dw_own=dw_own, acq_taps=h.copy(), wave_taps=[], wave_dw=[],
-                     wave_Phi=[], wave_r=[])
+        trace.update(acq_dw=units_to_rate(d, p.sps), acq_dw_est=dw_est, acq_units=d, acq_taps=h.copy(),
+                     wave_taps=[], wave_dw=[], wave_Phi=[], wave_units=[], wave_r=[], fo_edge=edges)
+    dev_waves = ties.get("wave_units")
     # -- waves
     S, W, P = p.seg_len, p.seg_pretrain, p.wave_segments()
     G = (K - A + S - 1) // S
@@ -425,32 +530,42 @@ def equalize(u: np.ndarray, p: RxParams, trace: dict | None = None,
     for w0 in range(0, G, P):
         gs = range(w0, min(w0 + P, G))
         n_w = 2 * (A + w0 * S)
-        if follow is not None and w0 // P < len(follow["wave_dw"]):
-            dw, Phi = follow["wave_dw"][w0 // P], follow["wave_Phi"][w0 // P]
-        delta = dw / p.sps
         if trace is not None:
             trace["wave_taps"].append(h_start.copy())
-            trace["wave_dw"].append(dw)
-            trace["wave_Phi"].append(Phi)
+            trace["wave_dw"].append(units_to_rate(d, p.sps))
+            trace["wave_Phi"].append(units_to_phase(phi))
+            trace["wave_units"].append((phi, d))
         acc = 0j
         h_last = h_start
         for g in gs:
             ks, ke = A + g * S, min(A + (g + 1) * S, K)
             kp = max(ks - W, 0)
-            win = _Window(u, kp, ke, c, Phi, n_w, delta)
+            win = _Window(u, kp, ke, c, phi, n_w, d if rot is not None else None)
             hh = h_start
+            base = n_acq_blk + g * spb
+            t = 0
             for k0 in range(kp, ks, Bu):
-                _, hh = lms_step(hh, win.taps_input(k0, min(k0 + Bu, ks), T, c), "dd", p, phis)
+                _, hh = lms_step(hh, win.taps_input(k0, min(k0 + Bu, ks), T, c), "dd", p, phis,
+                                 inner_choice(base + t) if t < spb else None, tie_log, ("seg", g, t))
+                t += 1
             for k0 in range(ks, ke, Bu):
                 k1 = min(k0 + Bu, ke)
-                y[:, k0:k1], hh = lms_step(hh, win.taps_input(k0, k1, T, c), "dd", p, phis)
+                y[:, k0:k1], hh = lms_step(hh, win.taps_input(k0, k1, T, c), "dd", p, phis,
+                                           inner_choice(base + t) if t < spb else None, tie_log, ("seg", g, t))
+                t += 1
             acc += fo_estimate_sum(y[:, ks:ke], p.mod)
             h_last = hh
         r = 0.25 * np.angle(acc) if p.fo_track else 0.0
+        inc, edge = fo_units(r / p.fo_smooth, p.sps)
+        if p.fo_track:
+            edges.append(edge)
+            wi = w0 // P
+            if dev_waves is not None and wi + 1 < len(dev_waves):
+                inc = _track_tie(inc, edge, dev_waves[wi + 1][1] - dev_waves[wi][1], "wave", wi, tie_log)
         if trace is not None:
             trace["wave_r"].append(r)
-        Phi = math.remainder(Phi + (2 * P * S) * delta, TWO_PI)
-        dw = dw + r / p.fo_smooth
+        phi = (phi + (2 * P * S) * d) % M
+        d = d + inc
         h_start = h_last
     return y
 
@@ -526,8 +641,7 @@ def demap(z: np.ndarray, p: RxParams):
     return bits, llr, sig
 
 
-def run_chain(samples: np.ndarray, p: RxParams, trace: dict | None = None,
-              follow: dict | None = None) -> dict:
+def run_chain(samples: np.ndarray, p: RxParams, trace: dict | None = None, ties: dict | None = None) -> dict:
     """Whole stream: ingest -> CDC -> equaliser -> BPS -> demap.
 
     samples: (n, 4) real [Xi, Xq, Yi, Yq] (int8 codes or floats); the ingest
@@ -539,7 +653,7 @@ def run_chain(samples: np.ndarray, p: RxParams, trace: dict | None = None,
     n = a.shape[0] - (a.shape[0] % 2)
     x = np.stack([a[:n, 0] + 1j * a[:n, 1], a[:n, 2] + 1j * a[:n, 3]])
     u = cdc_overlap_save(x, cdc_filter(p), p.overlap)
-    y = equalize(u, p, trace, follow)
+    y = equalize(u, p, trace, ties)
     bhat, m, z = bps_outer(y, p)
     bits, llr, sig = demap(z, p)
     return dict(u=u, y=y, bhat=bhat, m=m, z=z, bits=bits, llr=llr, sigma2=sig)

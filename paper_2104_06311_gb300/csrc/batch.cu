@@ -703,7 +703,7 @@ rx_status rx_batch_process(rx_batch *b, const rx_in *ins, rx_out *outs) {
       L.mu_dd = (float)kMu;
       L.cma_r2 = c.cfg.mod_bits == 4 ? 1.32f : 1.0f;
       L.fo_smooth = kFoSmooth;
-      L.inc_scale = (float)(18446744073709551616.0 / (4.0 * 3.14159265358979323846 * kFoSmooth));
+      L.inc_scale = (double)(1ll << kFoGridBits) / (4.0 * 3.14159265358979323846 * kFoSmooth);
       L.fo_track = 1;
       L.nblocks = c.team;
     }

@@ -22,9 +22,10 @@
 //     the taps at the end of the last segment of wave w-1, pre-trains on the W
 //     symbols before it, then equalises its own symbols.  A bounded grid
 //     barrier closes each wave; one warp per CTA then folds the 4th-power sums
-//     (fixed order, double-float) into the tracker: dw += r/16,
-//     Phi = Phi + 2PS dw/2, both held as 64-bit fixed-point turns so that
-//     the modular phase sum is exact.
+//     (fixed order, double-float) into the tracker: Phi = Phi + 2PS dw/2,
+//     dw += r/16 rounded to whole 2^-kFoGridBits turns per sample (the
+//     acquisition estimate likewise), both held as 64-bit fixed-point turns:
+//     the phase the tracker integrates is an exact sum of grid values.
 //
 // One update block of B_u <= 32 symbols; warp w owns symbols 8w..8w+7 and
 // lane 4j + part works on symbol j of its warp with part = (input pol q, tap
@@ -105,13 +106,9 @@ __device__ __forceinline__ double q64_to_rad(unsigned long long q) {
   return (double)(long long)q * 3.4061215800865545e-19;  // 2 pi / 2^64
 }
 
-__device__ __forceinline__ unsigned long long to_q64_turns(double rad) {
-  // radians -> fraction of a turn in [-1/2, 1/2) as a two's-complement Q0.64
-  const double inv2pi = 0.15915494309189533577;
-  double t = rad * inv2pi;
-  t -= rint(t);
-  if (t >= 0.5) t -= 1.0;
-  return (unsigned long long)__double2ll_rn(t * 18446744073709551616.0);
+// Whole 2^-kFoGridBits turns per sample -> Q0.64 turns per sample.
+__device__ __forceinline__ long long grid_to_q64(long long units) {
+  return (long long)((unsigned long long)units << (64 - kFoGridBits));
 }
 
 // Bounded barrier over `count` CTAs on counter *ctr: returns false (and sets
@@ -261,6 +258,8 @@ struct Span {
   int64_t fo_lo, fo_hi;
   int cma;
   Rot rot;
+  int8_t *itr;   // inner BPS angle of update step t goes to itr[t] for t < itr_n (nullptr: off)
+  int itr_n;
 };
 
 // Per-thread constant roles.
@@ -452,6 +451,7 @@ __device__ __forceinline__ void run_span(const Hot hot, EqSmem &sm, const Span s
         const unsigned key = (u & 0x80000000u) ? ~u : (u | 0x80000000u);
         const unsigned mn = __reduce_min_sync(FULL, key);
         const int bstar = __ffs(__ballot_sync(FULL, key == mn)) - 1;
+        if (sp.itr != nullptr && threadIdx.x == 0 && step < sp.itr_n) sp.itr[step] = (int8_t)bstar;
         eth = make_float2(__shfl_sync(FULL, ln.rot_b.x, bstar), -__shfl_sync(FULL, ln.rot_b.y, bstar));
       }
       if (sp.cma) fo_deferred();
@@ -620,6 +620,7 @@ __device__ __forceinline__ void eq_body(const EqLaunch &L, const int cta, EqSmem
       sp.fo_lo = L.n_cma / 2; sp.fo_hi = L.n_cma;
       sp.cma = 1;
       sp.rot.on = 0; sp.rot.Phi_q = 0; sp.rot.delta_q = 0; sp.rot.n0 = 0;
+      sp.itr = nullptr; sp.itr_n = 0;
       fo = Kahan{0.f, 0.f, 0.f, 0.f};
       run_span<MB>(hot, sm, sp, ln, own, h, fo, n_limit);
       const float4 s = reduce_fo(sm, fo, ln);
@@ -627,15 +628,19 @@ __device__ __forceinline__ void eq_body(const EqLaunch &L, const int cta, EqSmem
       if (!cta_barrier(L.err, L.barrier + 1, 2u, epoch2, sm)) return;
       const float4 s01 = df4_add(__ldcg(&L.fo_part[0]), __ldcg(&L.fo_part[1]));
       const double ax = (double)s01.x + (double)s01.y, ay = (double)s01.z + (double)s01.w;
-      const double dw = L.fo_track ? 0.25 * atan2(ay, ax) : 0.0;   // once per stream
-      const double delta = dw / 2.0;
+      const double dw_est = L.fo_track ? 0.25 * atan2(ay, ax) : 0.0;   // once per stream
+      // rounded to the tracker grid: dw / (4 pi) turns per sample at 2 samples per symbol
+      const long long du = __double2ll_rn(dw_est * (double)(1ll << kFoGridBits) * 0.079577471545947667884);
+      const long long dq = grid_to_q64(du);
       if (L.A > L.n_cma) {
         Span sd;
         sd.kp = L.n_cma; sd.ks = L.n_cma; sd.ke = L.A;
         sd.fo_lo = sd.fo_hi = 0;
         sd.cma = 0;
         sd.rot.on = L.fo_track;
-        sd.rot.Phi_q = 0; sd.rot.delta_q = to_q64_turns(delta); sd.rot.n0 = 2 * L.n_cma;
+        sd.rot.Phi_q = 0; sd.rot.delta_q = (unsigned long long)dq; sd.rot.n0 = 2 * L.n_cma;
+        sd.itr = L.inner ? L.inner + p * L.inner_cap : nullptr;
+        sd.itr_n = (int)min(L.inner_acq, L.inner_cap);
         run_span<MB>(hot, sm, sd, ln, own, h, fo, n_limit);
       }
       // end of acquisition = trace entries 0 (acquisition) and 1 (start of wave 0)
@@ -648,9 +653,9 @@ __device__ __forceinline__ void eq_body(const EqLaunch &L, const int cta, EqSmem
       }
       if (cta == 0 && threadIdx.x == 0) {
         // tracker as a 64-bit fixed-point NCO: exact modular phase arithmetic
-        const long long dq = (long long)to_q64_turns(delta);
         const unsigned long long phq = (unsigned long long)(2 * L.A - 2 * L.n_cma) * (unsigned long long)dq;
         const double Phi = q64_to_rad(phq);
+        const double dw = (double)dq * 6.8122431601731090e-19;   // 4 pi / 2^64 rad per symbol
         L.st->dw = dw;
         L.st->Phi = Phi;
         L.st->delta_q = dq;
@@ -678,6 +683,16 @@ __device__ __forceinline__ void eq_body(const EqLaunch &L, const int cta, EqSmem
     sp.kp = max(sp.ks - (int64_t)L.W, (int64_t)0);
     sp.fo_lo = sp.ks; sp.fo_hi = sp.ke;
     sp.cma = 0;
+    sp.itr = nullptr;
+    sp.itr_n = 0;
+    if (L.inner != nullptr) {
+      const int64_t at = L.inner_acq + g * L.inner_spb;
+      const int64_t n = min((int64_t)L.inner_spb, L.inner_cap - at);
+      if (n > 0) {
+        sp.itr = L.inner + p * L.inner_cap + at;
+        sp.itr_n = (int)n;
+      }
+    }
     return sp;
   };
   const int chunk = (kChunkSym / hot.Bu) * hot.Bu;
@@ -731,11 +746,11 @@ __device__ __forceinline__ void eq_body(const EqLaunch &L, const int cta, EqSmem
       for (int jj = ln.lane; jj < n; jj += 32) v = df4_add(v, __ldcg(&src[jj]));
       for (int o = 16; o >= 1; o >>= 1) v = df4_add(v, shfl_xor_f4(v, o));
       if (ln.lane == 0) {
-        // r = 1/4 arg(sum); Phi += 2PS (dw/2); dw += r/16 -- in Q0.64 turns
+        // r = 1/4 arg(sum); Phi += 2PS (dw/2); dw += r/16 rounded to the grid -- in Q0.64 turns
         const float r = L.fo_track ? 0.25f * atan2f(v.z + v.w, v.x + v.y) : 0.f;
         const long long dq = sm.dq;
         sm.phq += (unsigned long long)(2 * (long long)L.P * L.S) * (unsigned long long)dq;
-        sm.dq = dq + __float2ll_rn(r * L.inc_scale);
+        sm.dq = dq + grid_to_q64(__double2ll_rn((double)r * L.inc_scale));
         if (cta == 0) trace_fo(L, w + 2, (double)sm.dq * 6.8122431601731090e-19, q64_to_rad(sm.phq));
       }
     }

@@ -48,6 +48,7 @@ struct rx_stream {
   int64_t acq_min = 16384;
   double fo_smooth = 16.0;
   int fo_track = 1, llr_out = 0, sym_out = 0, eq_out = 0, cdc_out = 0, profile = 0;
+  int64_t inner_cap = 0;            // RX_P_INNER_TRACE: entries per butterfly row (0 = off)
   // ---- resolved
   int N = 0, V = 0, Sh = 0, P = 0, C = 256;
   int64_t A_full = 0, span = 0;
@@ -70,6 +71,7 @@ struct rx_stream {
   float *trace = nullptr;
   double *trace_fo = nullptr;
   int64_t trace_cap = 4096;
+  int8_t *inner = nullptr;          // [2][inner_cap] inner BPS angles (RX_P_INNER_TRACE)
   unsigned *barrier = nullptr;
   int *err = nullptr;
   int *chunk_r = nullptr;
@@ -178,7 +180,7 @@ rx_status dalloc(rx_stream *rx, Tp **p, size_t count) {
 void release(rx_stream *rx) {
   void *ptrs[] = {rx->H, rx->tw, rx->tail[0], rx->tail[1], rx->u[0], rx->u[1], rx->y[0], rx->y[1],
                   rx->bh[0], rx->bh[1], rx->st, rx->fo_part, rx->tap_slot, rx->trace, rx->trace_fo,
-                  rx->barrier, rx->err, rx->chunk_r, rx->chunk_s2, rx->chunk_m, rx->m_carry,
+                  rx->inner, rx->barrier, rx->err, rx->chunk_r, rx->chunk_s2, rx->chunk_m, rx->m_carry,
                   rx->region_s2, rx->ber_counts, rx->ber_acc, rx->ber_sync};
   for (void *p : ptrs)
     if (p) cudaFree(p);
@@ -203,6 +205,7 @@ void release(rx_stream *rx) {
   rx->tap_slot = nullptr;
   rx->trace = nullptr;
   rx->trace_fo = nullptr;
+  rx->inner = nullptr;
   rx->barrier = nullptr;
   rx->err = nullptr;
   rx->chunk_r = nullptr;
@@ -227,6 +230,8 @@ rx_status init_device_state(rx_stream *rx) {
   RX_CUDA(cudaMemsetAsync(rx->m_carry, 0, 2 * sizeof(int64_t), rx->stream), "state init");
   RX_CUDA(cudaMemsetAsync(rx->err, 0, sizeof(int), rx->stream), "state init");
   RX_CUDA(cudaMemsetAsync(rx->trace_fo, 0, (size_t)rx->trace_cap * 2 * sizeof(double), rx->stream), "state init");
+  if (rx->inner)
+    RX_CUDA(cudaMemsetAsync(rx->inner, 0xff, (size_t)2 * rx->inner_cap, rx->stream), "state init");
   // pageable source: the copy completes before cudaMemcpyAsync returns
   return RX_OK;
 }
@@ -395,6 +400,7 @@ rx_status rx_set_param(rx_stream *rx, int key, double v) {
     case RX_P_PROFILE: rx->profile = v != 0; return RX_OK;
     case RX_P_PIPELINE: s = as_int(1, kMaxPieces, &t); if (s == RX_OK) rx->pieces = (int)t; return s;
     case RX_P_PRECISION: s = as_int(0, 2, &t); if (s == RX_OK) rx->fmt = (int)t; break;
+    case RX_P_INNER_TRACE: s = as_int(0, (int64_t)1 << 32, &rx->inner_cap); break;
     default: return fail(rx, RX_EINVAL, "unknown parameter key");
   }
   if (s != RX_OK) return s;
@@ -434,6 +440,7 @@ rx_status rx_get_param(rx_stream *rx, int key, double *v) {
     case RX_P_PROFILE: *v = rx->profile; break;
     case RX_P_PRECISION: *v = rx->fmt; break;
     case RX_P_PIPELINE: *v = rx->pieces; break;
+    case RX_P_INNER_TRACE: *v = (double)rx->inner_cap; break;
     default: return fail(rx, RX_EINVAL, "unknown parameter key");
   }
   return RX_OK;
@@ -477,6 +484,7 @@ rx_status rx_reserve(rx_stream *rx, int64_t max_call) {
   RX_ALLOC(rx->tap_slot, (size_t)2 * 4 * kMaxTaps);
   RX_ALLOC(rx->trace, (size_t)rx->trace_cap * 4 * kMaxTaps * 2);
   RX_ALLOC(rx->trace_fo, (size_t)rx->trace_cap * 2);
+  if (rx->inner_cap > 0) RX_ALLOC(rx->inner, (size_t)2 * rx->inner_cap);
   RX_ALLOC(rx->barrier, 2);
   RX_ALLOC(rx->err, 1);
   RX_ALLOC(rx->chunk_r, (size_t)2 * rx->chunk_cap);
@@ -722,7 +730,11 @@ rx_status rx_process(rx_stream *rx, const rx_in *in, rx_out *out) {
       L.mu_dd = (float)rx->mu_dd;
       L.cma_r2 = rx->mod_bits == 4 ? 1.32f : 1.0f;
       L.fo_smooth = rx->fo_smooth;
-      L.inc_scale = (float)(18446744073709551616.0 / (4.0 * 3.14159265358979323846 * rx->fo_smooth));
+      L.inc_scale = (double)(1ll << kFoGridBits) / (4.0 * 3.14159265358979323846 * rx->fo_smooth);
+      L.inner = rx->inner;
+      L.inner_cap = rx->inner_cap;
+      L.inner_acq = (std::max(rx->n_cma, rx->acq_min) - rx->n_cma + rx->Bu - 1) / rx->Bu;
+      L.inner_spb = (rx->W + rx->S + rx->Bu - 1) / rx->Bu;
       L.fo_track = rx->fo_track;
       L.nblocks = rx->eq_blocks;
       L.u_fmt = rx->fmt;
@@ -862,6 +874,21 @@ rx_status rx_trace(rx_stream *rx, int64_t wave, float *taps, double *dw, double 
       }
   *dw = fo[0];
   *Phi = fo[1];
+  return RX_OK;
+}
+
+rx_status rx_trace_inner(rx_stream *rx, int64_t first, int64_t count, int8_t *dst, int64_t *n_acq,
+                         int32_t *per_segment) {
+  if (!rx || (count > 0 && !dst) || first < 0 || count < 0) return RX_EINVAL;
+  if (n_acq) *n_acq = (std::max(rx->n_cma, rx->acq_min) - rx->n_cma + rx->Bu - 1) / rx->Bu;
+  if (per_segment) *per_segment = (rx->W + rx->S + rx->Bu - 1) / rx->Bu;
+  if (count == 0) return RX_OK;
+  if (!rx->reserved || !rx->inner) return fail(rx, RX_ESTATE, "inner trace not recorded (RX_P_INNER_TRACE)");
+  if (first + count > rx->inner_cap) return fail(rx, RX_EINVAL, "range outside the inner trace");
+  RX_CUDA(cudaStreamSynchronize(rx->stream), "trace wait");
+  for (int p = 0; p < 2; ++p)
+    RX_CUDA(cudaMemcpy(dst + p * count, rx->inner + p * rx->inner_cap + first, (size_t)count, cudaMemcpyDeviceToHost),
+            "inner trace");
   return RX_OK;
 }
 

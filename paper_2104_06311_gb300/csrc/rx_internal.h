@@ -14,6 +14,10 @@ constexpr int kAngles = 32;       // BPS test angles (one per lane)
 constexpr int kEqThreads = 128;   // equaliser CTA: 4 warps, one butterfly row
 constexpr int kChunkSym = 1152;   // equaliser span chunk (symbols) held in smem
 constexpr int kBpsChunk = 256;    // BPS pass-1 symbols per warp
+// Frequency tracker grid: the estimate and every tracking step are rounded to
+// whole multiples of 2^-kFoGridBits turns per sample, so that the tracked phase
+// is an exact sum (Q0.64 turns whose low 64 - kFoGridBits bits stay zero).
+constexpr int kFoGridBits = 16;
 
 // Storage formats of the CDC output (precision form).
 enum { RX_FMT_F32 = 0, RX_FMT_F16 = 1, RX_FMT_BF16 = 2 };
@@ -69,7 +73,11 @@ struct EqLaunch {
   int mod_bits;             // 2 or 4
   float mu_cma, mu_dd, cma_r2;
   double fo_smooth;
-  float inc_scale;          // 2^64 / (4 pi fo_smooth): tracker step r -> Q0.64 per sample
+  double inc_scale;         // 2^kFoGridBits / (4 pi fo_smooth): tracker step r -> grid units per sample
+  int8_t *inner;            // optional trace of the inner BPS angle per DD update block, [2][inner_cap]
+                            // (row p): acquisition blocks, then inner_spb entries per segment
+  int64_t inner_cap, inner_acq;
+  int inner_spb;
   int fo_track;
   int nblocks;              // CTAs in the grid (even: 2 rows per segment slot)
   int u_fmt;                // storage format of u (RX_FMT_*)

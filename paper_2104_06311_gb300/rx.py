@@ -21,12 +21,12 @@ PARAMS = {
     "N_CMA": 8, "UPDATE_BLOCK": 9, "SEG_LEN": 10, "SEG_PRETRAIN": 11, "BPS_HALFWIN": 12,
     "BLOCK_SAMPLES": 13, "IN_SCALE": 14, "ACQ_MIN": 15, "FO_SMOOTH": 16, "FO_TRACK": 17,
     "LLR_OUT": 18, "SYM_OUT": 19, "EQ_OUT": 20, "CDC_OUT": 21, "PROFILE": 22, "PIPELINE": 23,
-    "PRECISION": 24,
+    "PRECISION": 24, "INNER_TRACE": 25,
 }
 STAGES = ["cdc", "eq", "bps", "move", "ber"]
 
 EXPORTS = ["rx_create", "rx_set_param", "rx_get_param", "rx_set_cuda_stream", "rx_reserve",
-           "rx_process", "rx_ber", "rx_trace", "rx_get_state", "rx_set_state", "rx_reset",
+           "rx_process", "rx_ber", "rx_trace", "rx_trace_inner", "rx_get_state", "rx_set_state", "rx_reset",
            "rx_sync", "rx_destroy", "rx_status_str", "rx_last_error", "rx_profile",
            "rx_bps_demap_noalloc",
            "rx_batch_create", "rx_batch_set_param", "rx_batch_get_param", "rx_batch_set_cuda_stream",
@@ -101,6 +101,7 @@ def load(path: str = LIB_PATH) -> ct.CDLL:
     lib.rx_ber.argtypes = [P, P, ct.c_int64, P, ct.c_int64, ct.c_int64, ct.POINTER(ct.c_uint64),
                            ct.POINTER(ct.c_uint64), ct.POINTER(ct.c_int32)]
     lib.rx_trace.argtypes = [P, ct.c_int64, ct.POINTER(ct.c_float), ct.POINTER(ct.c_double), ct.POINTER(ct.c_double)]
+    lib.rx_trace_inner.argtypes = [P, ct.c_int64, ct.c_int64, P, ct.POINTER(ct.c_int64), ct.POINTER(ct.c_int32)]
     lib.rx_get_state.argtypes = [P, P, ct.POINTER(ct.c_size_t)]
     lib.rx_set_state.argtypes = [P, P, ct.c_size_t]
     lib.rx_profile.argtypes = [P, ct.POINTER(ct.c_double), ct.POINTER(ct.c_int64), ct.c_int]
@@ -330,6 +331,20 @@ class Receiver:
         return (a[0::2] + 1j * a[1::2]).reshape(2, 2, self.ntaps), dw.value, Phi.value
 
     trace = rx_trace
+
+    def rx_trace_inner(self, first=0, count=None):
+        """Inner BPS angles per DD update block: (int8 array [2][count], n_acq, per_segment)."""
+        import numpy as np
+        if count is None:
+            count = int(self.get_param("INNER_TRACE")) - first
+        buf = np.full((2, max(count, 0)), -1, np.int8)
+        na, ps = ct.c_int64(), ct.c_int32()
+        _check(self.lib, self.h, self.lib.rx_trace_inner(self.h, int(first), int(count),
+                                                         buf.ctypes.data if count > 0 else None,
+                                                         ct.byref(na), ct.byref(ps)))
+        return buf, na.value, ps.value
+
+    trace_inner = rx_trace_inner
 
     def rx_get_state(self) -> bytes:
         n = ct.c_size_t()

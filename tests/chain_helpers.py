@@ -54,9 +54,44 @@ def make_receiver(p: O.RxParams, **flags):
     return rx
 
 
+def inner_capacity(p: O.RxParams, K: int) -> int:
+    """Entries per butterfly row of the device's inner-angle trace for a K-symbol stream."""
+    n_acq = -(-(max(p.n_cma, p.acq_min) - p.n_cma) // p.upd_block)
+    spb = -(-(p.seg_pretrain + p.seg_len) // p.upd_block)
+    n_seg = -(-max(K - p.acq_len(K), 0) // p.seg_len) + 1
+    return n_acq + n_seg * spb
+
+
+def tracker_units(dw: float, Phi: float, p: O.RxParams) -> tuple[int, int]:
+    """A reported (dw rad/symbol, Phi rad) pair as the tracker's integers (phi, d)."""
+    M = 1 << O.chain.FO_GRID_BITS
+    d = int(round(dw / (p.sps * 2 * math.pi) * M))
+    phi = int(round(Phi / (2 * math.pi) * M)) % M
+    return phi, d
+
+
+def device_ties(rx, p: O.RxParams, K: int) -> dict:
+    """The device's choices at the equaliser's discrete decisions: the tracker's
+    integer state per wave (from rx_trace) and, when recorded, the inner BPS
+    angle of every DD update block (rx_trace_inner).  The oracle takes one of
+    them only where its own decision is a near-tie (both candidates correct)."""
+    A = p.acq_len(K)
+    S, P = p.seg_len, p.wave_segments()
+    n_waves = -(-(-(-max(K - A, 0) // S)) // P)
+    _, dw_acq, _ = rx.trace(-1)
+    waves = [rx.trace(w) for w in range(n_waves)]
+    out = dict(acq_units=tracker_units(dw_acq, 0.0, p)[1],
+               wave_units=[tracker_units(w[1], w[2], p) for w in waves])
+    if hasattr(rx, "trace_inner") and rx.get_param("INNER_TRACE") > 0:
+        inner, n_acq, spb = rx.trace_inner()
+        out.update(inner=inner, inner_acq=n_acq, inner_spb=spb)
+    return out
+
+
 def run_gpu(p: O.RxParams, samples: np.ndarray, chunk=None, reserve=None):
     import torch
-    rx = make_receiver(p, LLR_OUT=1, SYM_OUT=1, EQ_OUT=1, CDC_OUT=1)
+    rx = make_receiver(p, LLR_OUT=1, SYM_OUT=1, EQ_OUT=1, CDC_OUT=1,
+                       INNER_TRACE=inner_capacity(p, samples.shape[0] // 2))
     x = torch.from_numpy(np.ascontiguousarray(samples)).cuda()
     if reserve:
         rx.reserve(reserve)
@@ -90,18 +125,23 @@ def boundary_mask(z: np.ndarray, mod: str, eps: float = BOUNDARY_EPS) -> np.ndar
     return m.reshape(z.shape[:-1] + (-1,))
 
 
-def bps_near_tie(y: np.ndarray, p: O.RxParams, rel: float = BOUNDARY_EPS) -> np.ndarray:
+def bps_near_tie(y: np.ndarray, p: O.RxParams, rel: float = BOUNDARY_EPS, chunk: int = 1 << 16) -> np.ndarray:
     """(2, K) True where the oracle's best and second-best BPS window sums differ by < rel."""
     B, Nb = p.bps_angles, p.bps_halfwin
     phis = O.bps_outer_angles(B)
     K = y.shape[-1]
-    w = y[..., None] * np.exp(-1j * phis)
-    r = w - O.decide(w, p.mod)
-    d = r.real ** 2 + r.imag ** 2
-    c = np.concatenate([np.zeros((2, 1, B)), np.cumsum(d, axis=1)], axis=1)
-    k = np.arange(K)
-    hi = np.minimum(k + Nb + 1, K)
-    lo = np.maximum(k - Nb, 0)
-    D = c[:, hi] - c[:, lo]
-    Ds = np.sort(D, axis=-1)
-    return (Ds[..., 1] - Ds[..., 0]) < rel * np.maximum(Ds[..., 0], 1e-30)
+    out = np.zeros((2, K), bool)
+    for k0 in range(0, K, chunk):
+        k1 = min(k0 + chunk, K)
+        a, b = max(k0 - Nb, 0), min(k1 + Nb, K)
+        w = y[:, a:b, None] * np.exp(-1j * phis)
+        r = w - O.decide(w, p.mod)
+        d = r.real ** 2 + r.imag ** 2
+        c = np.concatenate([np.zeros((2, 1, B)), np.cumsum(d, axis=1)], axis=1)
+        k = np.arange(k0, k1)
+        hi = np.minimum(k + Nb + 1, K) - a
+        lo = np.maximum(k - Nb, 0) - a
+        D = c[:, hi] - c[:, lo]
+        Ds = np.sort(D, axis=-1)
+        out[:, k0:k1] = (Ds[..., 1] - Ds[..., 0]) < rel * np.maximum(Ds[..., 0], 1e-30)
+    return out

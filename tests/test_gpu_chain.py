@@ -16,7 +16,7 @@ import pytest
 
 import linksim as L
 import oracle as O
-from chain_helpers import (REL_RMS_TOL, boundary_mask, bps_near_tie, ensure_built, rel_rms,
+from chain_helpers import (REL_RMS_TOL, boundary_mask, bps_near_tie, device_ties, ensure_built, rel_rms,
                            rx_params, run_gpu)
 
 pytestmark = pytest.mark.gpu
@@ -46,29 +46,28 @@ def gpu_tracker(rx, p, K):
 def check_chain(p, g, gpu, trace=None, check_taps=True):
     """Compare every stage of one run; returns a dict of the measured errors.
 
-    The oracle runs on the device's frequency-tracker state (follow mode):
-    the tracked phase integrates each estimate over a whole wave, so FP32
-    rounding in an estimate would otherwise grow into a phase offset.  Each
-    estimate and each phase update is then checked on its own.
+    The oracle runs on its own decisions.  Where one of them is a near-tie
+    (inner BPS window sums within INNER_TIE_REL, a tracker rounding within
+    TRACK_TIE_UNITS of half-way) both candidates are correct; the oracle then
+    follows the one the device took, and reports how often it did.  The
+    frequency tracker's integer state must then equal the device's at every
+    wave exactly.
     """
     K = g.samples.shape[0] // 2
     dev = gpu_tracker(gpu["rx"], p, K)
+    ties = device_ties(gpu["rx"], p, K)
     trace = {} if trace is None else trace
-    orc = O.run_chain(g.samples, p, trace, follow=dev)
+    orc = O.run_chain(g.samples, p, trace, ties)
     assert gpu["n"] == K
     rep = {}
-    # frequency estimates on identical data, and the device's phase bookkeeping
-    rep["acq_dw"] = abs(dev["acq_dw"] - trace["acq_dw_own"])
-    assert rep["acq_dw"] < 1e-7 + 1e-5 * abs(trace["acq_dw_own"]), rep
-    worst_r = 0.0
-    for w in range(len(dev["wave_dw"]) - 1):
-        r_dev = (dev["wave_dw"][w + 1] - dev["wave_dw"][w]) * p.fo_smooth
-        worst_r = max(worst_r, abs(r_dev - trace["wave_r"][w]))
-        assert abs(r_dev - trace["wave_r"][w]) < 1e-6 + 1e-4 * abs(trace["wave_r"][w]), (w, r_dev, trace["wave_r"][w])
-        nxt = math.remainder(dev["wave_Phi"][w] + (2 * p.wave_segments() * p.seg_len) * (dev["wave_dw"][w] / 2),
-                             2 * math.pi)
-        assert abs(nxt - dev["wave_Phi"][w + 1]) < 1e-9, (w, nxt, dev["wave_Phi"][w + 1])
-    rep["wave_r"] = worst_r
+    rep["ties"] = len(trace["ties"])
+    rep["tie_kinds"] = sorted({t[0] for t in trace["ties"]})
+    rep["tie_gap_max"] = max((t[-1] for t in trace["ties"]), default=None)
+    rep["fo_edge_min"] = min(trace["fo_edge"]) if trace["fo_edge"] else None
+    # the frequency tracker (integers on the 2^-G turns grid): identical at every wave
+    assert ties["acq_units"] == trace["acq_units"], (ties["acq_units"], trace["acq_units"])
+    assert ties["wave_units"] == trace["wave_units"], [
+        (w, a, b) for w, (a, b) in enumerate(zip(ties["wave_units"], trace["wave_units"])) if a != b][:5]
     # CDC
     rep["cdc"] = rel_rms(gpu["u"][:, :2 * K], orc["u"])
     assert gpu["cdc_n"] == 2 * K
@@ -95,9 +94,11 @@ def check_chain(p, g, gpu, trace=None, check_taps=True):
     assert rep["z"] < REL_RMS_TOL, rep
     # hard bits
     m = p.bits
-    okb = np.repeat(ok, m, axis=1) & ~boundary_mask(orc["z"], p.mod)
+    bmask = boundary_mask(orc["z"], p.mod)
+    okb = np.repeat(ok, m, axis=1) & ~bmask
     mism = (gpu["bits"] != orc["bits"]) & okb
     rep["bit_mismatch"] = int(mism.sum())
+    rep["exempt_bits"] = int(((gpu["bits"] != orc["bits"]) & ~okb).sum())
     assert rep["bit_mismatch"] == 0, rep
     # LLRs
     rep["llr"] = rel_rms(gpu["llr"][okb], orc["llr"][okb])
@@ -289,64 +290,28 @@ def test_flush_of_empty_stream_emits_nothing():
     assert rx.process(None, out)[1] == 0
 
 
-def test_full_size_c2_sampled():
-    """Full 10,000 km workload size (2^24 symbols/pol, int8, one call + flush): sampled checks.
-
-    The oracle recomputes sampled CDC windows exactly and runs sampled waves of
-    the equaliser from the GPU's own state at the wave start (taps, dw, Phi);
-    the BER matches the oracle chain's BER on the first 2^18 symbols'
-    statistics within the binomial spread.
-    """
+def test_full_size_c2_whole_stream():
+    """Full 10,000 km workload (2^24 symbols/pol, int8, one call + flush) against
+    the FP64 oracle run over the whole stream: the frequency tracker identical
+    at all 512 waves, taps at every wave start, equaliser and BPS outputs and
+    LLRs within 1e-4 relative RMS, bits identical outside the exempt bands, and
+    the device's BER count equal to the oracle's on the same bits."""
     import torch
-    from chain_helpers import make_receiver
     lk = L.workload("c2")
     g = L.generate(lk)
     p = rx_params(lk, g.in_scale)
-    rx = make_receiver(p, EQ_OUT=1)
-    x = torch.from_numpy(g.samples).cuda()
-    rx.reserve(x.shape[0])
-    out = rx.run_stream(x, eq=True)
-    torch.cuda.synchronize()
+    gpu = run_gpu(p, g.samples)
     K = lk.n_sym
-    assert out["n"] == K
+    assert gpu["n"] == K
+    tr = {}
+    rep, orc = check_chain(p, g, gpu, tr)
+    assert len(tr["wave_units"]) == 512
+    print("c2 full-size parity", rep)
     ref = torch.from_numpy(L.pack_bits(g.tx_bits).view(np.int32)).cuda()
-    e, n, sync = rx.ber(out["bits"], ref, K)
+    e, n, sync = gpu["rx"].ber(gpu["bits_t"], ref, K)
+    eo, no, so = O.ber_sync_count(orc["bits"], g.tx_bits, p.mod, p.acq_len(K))
     ber = e / n
+    print("BER device", ber, "oracle", eo / no)
     # 10,000 km with PN/PMD/ADC at 9.8 dB: within 0.5 dB of QPSK theory
     assert O.ber_theory("qpsk", 9.8) * 0.9 < ber < O.ber_theory("qpsk", 9.3), ber
-    # sampled equaliser waves re-run by the oracle from the GPU's state
-    x_cdc = None
-    y_gpu = out["eq"]
-    for w in (3, 200, 511):
-        h, dw, Phi = rx.trace(w)
-        A = p.acq_len(K)
-        P, S, W = p.wave_segments(), p.seg_len, p.seg_pretrain
-        g0 = w * P
-        ks, ke = A + g0 * S, A + (g0 + 1) * S
-        lo = 2 * (ks - W) - 8 - p.overlap
-        hi = 2 * ke + 8 + p.overlap
-        # oracle CDC on a slice wide enough for exact outputs in [2(ks-W)-7, 2ke+7]
-        a0 = max(lo - p.fft_n, 0)
-        seg = g.samples[a0:hi + p.fft_n].astype(np.float64) * p.in_scale
-        xs = np.stack([seg[:, 0] + 1j * seg[:, 1], seg[:, 2] + 1j * seg[:, 3]])
-        # overlap-save windows must align with the stream's window grid: pad to a window start
-        Sh = p.fft_n - p.overlap
-        i0 = a0 // Sh
-        pad = a0 - i0 * Sh
-        xs = np.concatenate([np.zeros((2, pad)), xs], axis=1)
-        u = O.cdc_overlap_save(xs, O.cdc_filter(p), p.overlap)
-        ustart = i0 * Sh
-        # first window (i0) has zeros for samples before a0 -> trust outputs from a0 + N
-        full_u = np.zeros((2, 2 * K), np.complex128)
-        full_u[:, ustart:ustart + u.shape[1]] = u
-        win = O.chain._Window(full_u, ks - W, ke, 7, Phi, 2 * (A + g0 * S), dw / 2)
-        hh = h.copy()
-        for k0 in range(ks - W, ks, p.upd_block):
-            _, hh = O.lms_step(hh, win.taps_input(k0, k0 + p.upd_block, 15, 7), "dd", p, O.bps_outer_angles(32))
-        ys = []
-        for k0 in range(ks, ke, p.upd_block):
-            yy, hh = O.lms_step(hh, win.taps_input(k0, k0 + p.upd_block, 15, 7), "dd", p, O.bps_outer_angles(32))
-            ys.append(yy)
-        yo = np.concatenate(ys, axis=1)
-        yg = y_gpu[:, ks:ke].cpu().numpy().astype(np.complex128)
-        assert rel_rms(yg, yo) < 1e-3, (w, rel_rms(yg, yo))
+    assert abs(e - eo) <= rep["exempt_bits"], (e, eo, rep["exempt_bits"])
