@@ -376,35 +376,71 @@ def test_ber_sync_recovers_planted_rotation_swap_delay():
     assert e == expect
 
 
-@pytest.mark.parametrize("mod,snr", [("qpsk", 9.8), ("16qam", 15.0)])
-def test_chain_ber_matches_awgn_theory(mod, snr):
-    # AWGN-only link (no CD, identity Jones, no phase noise or FO; frequency tracking off).
-    # (1) The equaliser output, after the best constant complex gain (data-aided, test
-    #     only), lands in the 99% binomial interval of Gray-coded theory, allowing 0.15 dB
-    #     of LMS misadjustment on the high side.
-    # (2) The whole chain (with blind phase search) stays within 0.4 dB of theory: BPS
-    #     over a 33-symbol window with pi/64 angle steps costs ~0.2-0.3 dB at these BERs.
+def _ci(pb, n):
+    """99 % binomial interval of an error count with probability pb over n bits."""
+    return pb * n - 2.576 * math.sqrt(n * pb), pb * n + 2.576 * math.sqrt(n * pb)
+
+
+@pytest.mark.parametrize("mod,snr,chain_db", [("qpsk", 9.8, 0.2), ("16qam", 15.0, 0.3)])
+def test_chain_ber_matches_awgn_theory(mod, snr, chain_db):
+    # AWGN-only link (no CD, identity Jones, no phase noise or FO; frequency tracking off),
+    # taken apart stage by stage:
+    # (1) the equaliser output, with a data-aided phase and gain over a sliding 33-symbol
+    #     window (test only), lands in the 99 % binomial interval of Gray-coded theory,
+    #     allowing 0.05 dB: the equaliser itself costs nothing measurable;
+    # (2) its gain is the Wiener (MMSE) gain SNR / (1 + SNR) of a unit-energy signal in
+    #     white noise, to 1 %: the LMS converges to the MMSE solution, whose amplitude
+    #     bias moves the 16QAM ring thresholds (closed form: +6 % BER at 15 dB);
+    # (3) the whole chain, blind phase search included, stays within chain_db of theory
+    #     (measured 0.13 dB QPSK, 0.25 dB 16QAM: BPS tracking the equaliser's slow phase
+    #     wander, plus the 16QAM amplitude bias of (2)).
     K = 1 << 17
     lk = L.Link(mod=mod, n_sym=K, L_km=0.0, jones=None, snr_db=snr, seed=31 + int(snr))
     g = L.generate(lk)
     p = O.RxParams(mod=mod, baud=lk.baud, L_km=0.0, fo_track=False)
     out = O.run_chain(g.samples, p)
     A = p.acq_len(K)
-
-    def ci(pb, n):
-        return pb * n - 2.576 * math.sqrt(n * pb), pb * n + 2.576 * math.sqrt(n * pb)
-
     y, s = out["y"][:, A:], g.tx_symbols[:, A:]
+    snr_lin = 10 ** (snr / 10)
     err = n = 0
     for pp in range(2):
         a = np.vdot(s[pp], y[pp]) / np.vdot(s[pp], s[pp])
-        err += int(np.sum(O.hard_bits(y[pp] / a, mod) != O.hard_bits(s[pp], mod)))
+        assert abs(abs(a) / (snr_lin / (1 + snr_lin)) - 1) < 0.01, (pp, abs(a))
+        r = np.convolve(y[pp] * np.conj(s[pp]), np.ones(33), "same")
+        z = y[pp] * np.exp(-1j * np.angle(r)) / abs(a)
+        err += int(np.sum(O.hard_bits(z, mod) != O.hard_bits(s[pp], mod)))
         n += s.shape[1] * p.bits
     assert err >= 200
-    lo, _ = ci(O.ber_theory(mod, snr), n)
-    _, hi = ci(O.ber_theory(mod, snr - 0.15), n)
+    lo, _ = _ci(O.ber_theory(mod, snr), n)
+    _, hi = _ci(O.ber_theory(mod, snr - 0.05), n)
     assert lo <= err <= hi, (err, n, O.ber_theory(mod, snr) * n)
     e, nb, _ = O.ber_sync_count(out["bits"], g.tx_bits, mod, A)
-    lo, _ = ci(O.ber_theory(mod, snr), nb)
-    _, hi = ci(O.ber_theory(mod, snr - 0.4), nb)
+    lo, _ = _ci(O.ber_theory(mod, snr), nb)
+    _, hi = _ci(O.ber_theory(mod, snr - chain_db), nb)
     assert lo <= e <= hi, (e, nb, O.ber_theory(mod, snr) * nb)
+
+
+@pytest.mark.parametrize("mod,snr,bps_db", [("qpsk", 9.8, 0.05), ("16qam", 15.0, 0.15)])
+def test_bps_alone_ber_near_theory(mod, snr, bps_db):
+    # blind phase search alone on AWGN symbols turned by a constant 0.3 rad (off the
+    # test-angle grid): its 33-symbol window estimates the phase close to the
+    # Cramer-Rao bound (var 1/(2 L SNR) plus the pi/64 grid's step^2/12), and the BER lands
+    # within bps_db of theory (measured +3 % QPSK, +12 % 16QAM)
+    K = 1 << 17
+    m = L.bits_per_symbol(mod)
+    bits = L.random_bits(5, 2 * m * K).reshape(2, -1)
+    s = L.map_symbols(bits, mod)
+    rng = np.random.default_rng(7)
+    snr_lin = 10 ** (snr / 10)
+    yv = s + math.sqrt(1 / snr_lin / 2) * (rng.standard_normal(s.shape) + 1j * rng.standard_normal(s.shape))
+    p = O.RxParams(mod=mod)
+    bh, mm, z = O.bps_outer(yv * np.exp(0.3j), p)
+    th = O.bps_outer_angles(p.bps_angles)[bh] + mm * math.pi / 2
+    ph = np.angle(np.exp(4j * (th - 0.3))) / 4
+    if mod == "qpsk":
+        crb = 1 / (2 * (2 * p.bps_halfwin + 1) * snr_lin) + (math.pi / 2 / p.bps_angles) ** 2 / 12
+        assert crb <= np.var(ph) < 1.2 * crb, (np.var(ph), crb)
+    e = int(np.sum(O.hard_bits(z, mod) != bits))
+    lo, _ = _ci(O.ber_theory(mod, snr), bits.size)
+    _, hi = _ci(O.ber_theory(mod, snr - bps_db), bits.size)
+    assert lo <= e <= hi, (e, bits.size, O.ber_theory(mod, snr) * bits.size)
