@@ -58,8 +58,24 @@ def parse():
 
 
 # ncu dram__bytes_read.sum + dram__bytes_write.sum of one step's eq_kernel launches per
-# symbol on the 10,000 km QPSK workload (the equaliser as of its window-copy version)
-EQ_DRAM_BYTES_PER_SYMBOL = 135.7e6 / 4194304
+# symbol on the 10,000 km QPSK workload; None: no capture of the current kernel yet
+EQ_DRAM_BYTES_PER_SYMBOL = None
+# algorithmic equaliser work per dual-pol sample-time: FIR 2x2x15 complex MACs per
+# symbol (240 flop per sample-time) and the same for the LMS gradient
+EQ_FLOP_PER_SAMPLE_TIME = 480.0
+_ALU_PEAK = {}
+
+
+def alu_peak_tflops(stream=None):
+    """FP32 FMA peak measured on this GPU in this run (rx_measure_alu_peak), cached."""
+    if "fp32" not in _ALU_PEAK:
+        from paper_2104_06311_gb300.rx import measure_alu_peak
+        sid = stream.cuda_stream if stream is not None else None
+        best = max(measure_alu_peak("fp32", 32768, sid)[0] for _ in range(3))
+        _ALU_PEAK["fp32"] = best
+        _ALU_PEAK["fp64"] = max(measure_alu_peak("fp64", 512, sid)[0] for _ in range(2))
+    return _ALU_PEAK["fp32"], (f"FP32 FMA chains measured in this run (best of 3): {_ALU_PEAK['fp32']:.1f} TFLOP/s; "
+                               f"FP64 {_ALU_PEAK['fp64']:.2f} TFLOP/s")
 
 
 def max_over_ranks(ms, dist=None, device="cpu"):
@@ -311,19 +327,17 @@ def bench_batch(args, rank, world, local):
     T, W, S = 15, 128, 1024
     stage = max(("cdc", "eq", "bps"), key=lambda s: prof[s][0])
     if stage == "eq":
-        flop = (2 * 2 * T * 8 * 2 + 2 * 32 * 11) * K_total * (1 + W / S)
-        sm_mhz = pk.get("sm_max_mhz", 2070.0)
-        peak = N_SM * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+        flop = EQ_FLOP_PER_SAMPLE_TIME * n_total
+        peak, peak_note = alu_peak_tflops(stream)
         achieved = flop / (prof[stage][0] / args.steps / 1e3) / 1e12
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": None, "kernel": "eq_batch_kernel",
-                "peak_note": f"FP32 SIMT: {N_SM} SM x {FP32_LANES_PER_SM} lanes x 2 flop x {sm_mhz:.0f} MHz"}
+                "traffic": None, "kernel": "eq_batch_kernel", "peak_note": peak_note}
     else:
         per = {"cdc": 4 + 16, "bps": 16 + 16 + 1 + 0.25 * 2}[stage]
         achieved = per * n_total / (prof[stage][0] / args.steps / 1e3) / 1e9
         roof = {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
                 "frac": achieved / pk["hbm_gbs"], "traffic": None, "kernel": stage}
-    roof["peak_source"] = pk_kind
+    roof["peak_source"] = "measured (FMA chains, this run)" if roof["bound"] == "alu" else pk_kind
     Ns = sorted({int(b.get_param(ch, "FFT_N")) for ch in range(len(xs))})
     line = {
         "metric": METRIC, "value": value, "unit": "GSa/s", "n_gpus": world, "steps": args.steps,
@@ -761,31 +775,29 @@ def main():
     stage = max(("cdc", "eq", "bps"), key=lambda s: prof[s][0])
     T, W, S = 15, 128, 1024
     if stage == "eq":
-        # per symbol (both pols): FIR 2*2*T CMAC + gradient 2*2*T CMAC (8 flop each)
-        # + inner BPS 2*32*11 flop; symbols processed include the W pre-training per segment
-        flop = (2 * 2 * T * 8 * 2 + 2 * 32 * 11) * K * (1 + W / S)
-        sm_mhz = pk.get("sm_max_mhz", 2070.0)
-        peak = N_SM * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+        # algorithmic work: FIR 240 + LMS gradient 240 flop per sample-time (the
+        # W pre-training and the inner phase search are executed but not counted)
+        flop = EQ_FLOP_PER_SAMPLE_TIME * n
+        peak, peak_note = alu_peak_tflops(stream)
         achieved = flop / (prof[stage][0] / args.steps / 1e3) / 1e12
-        # DRAM bytes of one step's equaliser launches: 32.4 B read per symbol in an ncu
-        # capture of the 2^22-symbol case (profiles/eq_kernel_c2_dram_traffic.md), scaled
-        # to K; recorded for the FP32 10,000 km workload only
+        # DRAM bytes of one step's equaliser launches, scaled from an ncu capture of a
+        # 2^22-symbol stream (each launch reads in proportion to its symbols); None until
+        # a capture of the current kernel exists
         traffic = (EQ_DRAM_BYTES_PER_SYMBOL * K
-                   if args.workload == "c2" and args.precision == "fp32" else None)
+                   if EQ_DRAM_BYTES_PER_SYMBOL and args.workload == "c2" and args.precision == "fp32" else None)
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": traffic, "kernel": "eq_kernel",
-                "peak_note": f"FP32 SIMT: {N_SM} SM x {FP32_LANES_PER_SM} lanes x 2 flop x {sm_mhz:.0f} MHz"}
+                "frac": achieved / peak, "traffic": traffic, "kernel": "eq_kernel", "peak_note": peak_note}
     else:
         per = {"cdc": 4 + 16, "bps": 16 + 16 + 1 + 0.25 * 2}[stage]   # bytes per sample-time
         bytes_ = per * n
         achieved = bytes_ / (prof[stage][0] / args.steps / 1e3) / 1e9
         roof = {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
                 "frac": achieved / pk["hbm_gbs"], "traffic": None, "kernel": stage}
-    roof["peak_source"] = pk_kind
+    roof["peak_source"] = "measured (FMA chains, this run)" if roof["bound"] == "alu" else pk_kind
     # every stage against both ceilings (algorithmic bytes and flops per sample-time)
-    alu_peak = N_SM * FP32_LANES_PER_SM * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6
+    alu_peak = alu_peak_tflops(stream)[0] * 1e12
     work = {"cdc": (4 + 16, 290.0),                                   # int8 in, 2 pols complex64 out
-            "eq": (16 + 8, (2 * 2 * T * 8 * 2 + 2 * 32 * 11) * 0.5 * (1 + W / S)),
+            "eq": (16 + 8, EQ_FLOP_PER_SAMPLE_TIME),
             "bps": (8 + 1 + 0.25, 32 * 11.0 + 8)}                        # per symbol-pol = per sample-time
     stage_roofs = {}
     for st_, (bpu, fpu) in work.items():
@@ -812,6 +824,8 @@ def main():
         "ber": ber, "ber_sync": sync,
         "stage_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
         "stage_rooflines": stage_roofs,
+        "alu_peaks_measured": {"fp32_tflops": _ALU_PEAK.get("fp32"), "fp64_tflops": _ALU_PEAK.get("fp64"),
+                               "fp32_nominal_at_max_clock": N_SM * FP32_LANES_PER_SM * 2 * 2.07e9 / 1e12},
         "gpu_launches": int(launches),
         "roofline": roof,
         "clocks": clk,

@@ -94,10 +94,18 @@ enum {
                               its output: 0 = FP32 (default), 1 = FP16, 2 = BF16;
                               butterflies and the equaliser compute in FP32, the
                               phase trackers stay 64-bit                           */
-  RX_P_INNER_TRACE = 25    /* > 0: record the equaliser's inner BPS angle of every
+  RX_P_INNER_TRACE = 25,   /* > 0: record the equaliser's inner BPS angle of every
                               DD update block, for that many entries per butterfly
                               row (read with rx_trace_inner); 0 = off (default).
                               Verification support, not from the paper          */
+  RX_P_WAIT_LIMIT_US = 26, /* limit of every bounded device wait (the equaliser's
+                              grid and row-pair barriers), microseconds of device
+                              time, 1..1e8 (default 2e6); a wait that runs out sets
+                              the error word (RX_ETIMEOUT)                          */
+  RX_P_TEST_NO_ARRIVE = 27 /* failure-detection test: the equaliser CTA with this
+                              index leaves out its arrival at the wave barriers, so
+                              that the other CTAs' waits run out after
+                              RX_P_WAIT_LIMIT_US (-1 = off, the default)             */
 };
 
 /* Stages reported by rx_profile. */
@@ -224,12 +232,21 @@ const char *rx_last_error(rx_stream *rx);
  * Synchronises the bound stream.  Not from the paper: measurement support. */
 rx_status rx_profile(rx_stream *rx, double *ms, int64_t *launches, int reset);
 
+/* Measured arithmetic peak of the plain ALUs: kind 0 = FP32 fused multiply-add,
+ * 1 = FP64.  Runs a grid of independent FMA chains (iters FMAs per chain, a
+ * multiple of 8; 8 CTAs of 256 threads x 16 chains per SM) once to warm up and
+ * once timed with CUDA events on cuda_stream (NULL = legacy default stream);
+ * *tflops = 2 x FMAs / time, *ms (optional) = the timed launch.  The roofline
+ * denominator of the stages bound by SIMT arithmetic.  Synchronous.  Not from
+ * the paper: measurement support. */
+rx_status rx_measure_alu_peak(int kind, int iters, void *cuda_stream, double *tflops, double *ms);
+
 /* Blind phase search, unwrap and hard Gray bits of one equalised block,
  * without allocating any device memory.  The paper has no counterpart: this
  * exists for callers that cannot call cudaMalloc when they need carrier
- * recovery (code being recorded into a CUDA graph, real-time loops that must
- * not hit the allocator's implicit device synchronisation, hosts with a
- * fixed device-memory budget).  It runs the same kernels as rx_process's BPS
+ * recovery (real-time loops that must not hit the allocator's implicit device
+ * synchronisation, hosts that give the library a fixed device-memory budget
+ * and own every allocation).  It runs the same kernels as rx_process's BPS
  * stage (32 test angles, +-bps_halfwin window, unwrap count starting at 0)
  * and treats y[0, n_symbols) of each polarisation as a whole stream.
  *   y: device, [pol][y_stride] complex floats (re, im), 8-byte aligned;
@@ -240,8 +257,10 @@ rx_status rx_profile(rx_stream *rx, double *ms, int64_t *launches, int reset);
  * symbols per polarisation (~2.1 MiB, held by every GPU that loads the
  * library until the process exits); larger n_symbols returns RX_EINVAL.
  * All calls share that array: calls that overlap on the GPU race.  The first
- * call on a device looks up the array's device address and caches it; make
- * it before any stream capture.  Asynchronous on cuda_stream. */
+ * call on a device looks up the array's device address and caches it with the
+ * device's current context; make it before any stream capture.  After a device
+ * reset (a new context) the next call looks the address up again.
+ * Asynchronous on cuda_stream. */
 rx_status rx_bps_demap_noalloc(const float *y, int64_t y_stride, int64_t n_symbols,
                                int bits_per_symbol, int bps_halfwin, uint32_t *bits,
                                int64_t bits_stride, void *cuda_stream);

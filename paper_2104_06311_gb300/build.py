@@ -18,7 +18,7 @@ OUT = os.path.join(HERE, "librx.so")
 BUILD_DIR = os.path.join(HERE, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["cdc.cu", "eq.cu", "bps.cu", "ber.cu", "rx_api.cu", "noalloc.cu", "batch.cu", "cnn.cu", "kk.cu", "wl.cu",
-           "rt.cu"]
+           "rt.cu", "peak.cu"]
 
 
 def nvcc() -> str:

@@ -302,6 +302,14 @@ struct BStage {
 };
 
 // The side streams start after everything enqueued on s so far.
+// SMs a channel's CDC launch may fill: the side streams share the device.
+int side_sm_budget() {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return std::max(1, sms / rx_batch::kSide);
+}
+
 cudaError_t side_fork(rx_batch *b, cudaStream_t s) {
   cudaError_t e = cudaEventRecord(b->ev_fork, s);
   for (int k = 0; k < rx_batch::kSide && e == cudaSuccess; ++k) e = cudaStreamWaitEvent(b->side[k], b->ev_fork, 0);
@@ -352,7 +360,7 @@ rx_status enqueue(rx_batch *b, const rx_in *ins, rx_out *outs, cudaStream_t s, b
       if (n == 0) continue;
       const int Sh = c.N - c.V;
       BX_CUDA(launch_cdc(c.N, c.V, nullptr, 0, 0, ins[i].data, 0, n, ins[i].dtype, (float)c.cfg.in_scale, c.H, c.tw,
-                         c.u, 0, c.u_stride, 0, (n + Sh - 1) / Sh, n, b->side[smap[i]]),
+                         c.u, 0, c.u_stride, 0, (n + Sh - 1) / Sh, n, b->side[smap[i]], RX_FMT_F32, side_sm_budget()),
               "cdc");
       launches[RX_STAGE_CDC] += 1;
     }
@@ -706,6 +714,8 @@ rx_status rx_batch_process(rx_batch *b, const rx_in *ins, rx_out *outs) {
       L.inc_scale = (double)(1ll << kFoGridBits) / (4.0 * 3.14159265358979323846 * kFoSmooth);
       L.fo_track = 1;
       L.nblocks = c.team;
+      L.spin_ns = kSpinLimitNs;
+      L.no_arrive_cta = -1;
     }
   }
   if (replay) {

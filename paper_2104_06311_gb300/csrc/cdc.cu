@@ -15,6 +15,8 @@
 #include <cuda_fp16.h>
 #include <math.h>
 
+#include <algorithm>
+
 #include "common.cuh"
 #include "fft.cuh"
 #include "rx_internal.h"
@@ -54,100 +56,239 @@ cudaError_t launch_tables(float2 *H, float2 *tw, int N, double baud, double L_km
   return cudaGetLastError();
 }
 
-// One CTA per window (both polarisations, SPLIT = false) or per (window, pol)
-// (SPLIT = true, blockIdx.y = pol) for the large transforms.  FMT selects the
-// storage of the shared-memory transform and of u (RX_FMT_*); reduced formats
-// scale the window by 1/sqrt(N) on ingest and H by sqrt(N) (kept in `hscale`)
-// so that every intermediate stays near unit magnitude (FP16 range).
-template <int N, int VPT, bool SPLIT, int FMT>
-__global__ void __launch_bounds__((SPLIT ? 1 : 2) * N / VPT) cdc_kernel(
+// Radix plan of an N-point transform: passes of radix 16, the last one smaller
+// where N is not a power of 16.  The inverse runs the same radices in reverse
+// order, which makes the forward transform's last pass and the inverse
+// transform's first pass read the same element set {j + r N / R} in butterfly j:
+// the two passes, the filter multiply and the conjugation between them run in
+// registers (no shared-memory round trip), and the inverse's last pass writes
+// natural order, straight to HBM.
+template <int N> struct Plan {
+  static constexpr int m = N <= 256 ? 2 : (N <= 4096 ? 3 : 4);
+  static constexpr int last = N == 256 ? 16 : (N == 512 ? 2 : (N == 1024 ? 4 : (N == 2048 ? 8 : (N == 4096 ? 16 : (N == 8192 ? 2 : 4)))));
+  // radix of forward pass p (p = 0 .. m-1)
+  static constexpr int radix(int p) { return p == m - 1 ? last : 16; }
+};
+
+// Load the R-point butterflies of a Stockham pass (radix R, stride group Ns) of
+// this thread, twiddled, and run the R-point DFTs in registers.
+template <int N, int VPT, int R, int Ns, class S>
+__device__ __forceinline__ void pass_load(const S *buf, int t, const float2 *__restrict__ tw,
+                                          float2 (&v)[VPT / R][R]) {
+  constexpr int NB = N / R, PER = VPT / R, TW = N / (Ns * R), TPP = N / VPT;
+#pragma unroll
+  for (int q = 0; q < PER; ++q) {
+    const int j = t + q * TPP;
+    const int jm = j & (Ns - 1);
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      float2 x = ld2(buf[pad(j + r * NB)]);
+      if (Ns > 1 && r > 0) x = cmul(x, __ldg(&tw[r * jm * TW]));
+      v[q][r] = x;
+    }
+    dft<R>(v[q]);
+  }
+}
+
+// Store a pass's butterfly outputs in Stockham order.
+template <int N, int VPT, int R, int Ns, class S>
+__device__ __forceinline__ void pass_store(S *buf, int t, const float2 (&v)[VPT / R][R]) {
+  constexpr int PER = VPT / R, TPP = N / VPT;
+#pragma unroll
+  for (int q = 0; q < PER; ++q) {
+    const int j = t + q * TPP;
+    const int jm = j & (Ns - 1);
+    const int d = (j / Ns) * Ns * R + jm;
+#pragma unroll
+    for (int r = 0; r < R; ++r) buf[pad(d + r * Ns)] = st2<S>(v[q][r]);
+  }
+}
+
+// Forward passes 1 .. m-2 (after the input pass, before the fused middle).
+template <int N, int VPT, int P, int Ns, class S>
+__device__ __forceinline__ void forward_middle(S *buf, int t, const float2 *tw) {
+  if constexpr (P < Plan<N>::m - 1) {
+    constexpr int R = Plan<N>::radix(P);
+    float2 v[VPT / R][R];
+    pass_load<N, VPT, R, Ns>(buf, t, tw, v);
+    __syncthreads();
+    pass_store<N, VPT, R, Ns>(buf, t, v);
+    __syncthreads();
+    forward_middle<N, VPT, P + 1, Ns * R>(buf, t, tw);
+  }
+}
+
+// Inverse passes 1 .. m-2 (radices in reverse order; Ns from the inverse's own start).
+template <int N, int VPT, int P, int Ns, class S>
+__device__ __forceinline__ void inverse_middle(S *buf, int t, const float2 *tw) {
+  if constexpr (P < Plan<N>::m - 1) {
+    constexpr int R = Plan<N>::radix(Plan<N>::m - 1 - P);
+    float2 v[VPT / R][R];
+    pass_load<N, VPT, R, Ns>(buf, t, tw, v);
+    __syncthreads();
+    pass_store<N, VPT, R, Ns>(buf, t, v);
+    __syncthreads();
+    inverse_middle<N, VPT, P + 1, Ns * R>(buf, t, tw);
+  }
+}
+
+template <int N> constexpr int fwd_ns_last() {   // Ns of the forward transform's last pass
+  return N / Plan<N>::last;
+}
+
+__device__ __forceinline__ unsigned smem_u32_of(const void *p) {
+  return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+
+// Raw input bytes per sample-time: int8 [Xi Xq Yi Yq] or float [Xi Xq Yi Yq].
+__device__ __forceinline__ int raw_bytes(int dtype) { return dtype == RX_I8x4 ? 4 : 16; }
+
+// One persistent CTA works through windows win_first + i, i = blockIdx.x +
+// k gridDim.x (both polarisations, SPLIT = false; or the polarisation
+// blockIdx.y, SPLIT = true).  With PREFETCH the raw input of a CTA's next window
+// is copied into shared memory (cp.async) while the current window's transform
+// runs; without it (large float windows) the input pass reads HBM directly.
+// FMT selects the storage of the shared-memory transform and of u (RX_FMT_*);
+// reduced formats scale the window by 1/sqrt(N) on ingest and H by sqrt(N)
+// (`hscale`) so that every intermediate stays near unit magnitude (FP16 range).
+template <int N, int VPT, bool SPLIT, int FMT, bool PREFETCH>
+__global__ void __launch_bounds__((SPLIT ? 1 : 2) * N / VPT, ((SPLIT ? 1 : 2) * N / VPT >= 512 ? 1 : 512 / ((SPLIT ? 1 : 2) * N / VPT))) cdc_kernel(
     int V, const uint8_t *__restrict__ tail, int64_t tail_first, int64_t tail_n,
     const uint8_t *__restrict__ call, int64_t call_first, int64_t call_n, int dtype, float scale,
     float hscale, const float2 *__restrict__ H, const float2 *__restrict__ tw, void *__restrict__ u_out,
-    int64_t u_base, int64_t u_stride, int64_t win_first, int64_t n_total) {
+    int64_t u_base, int64_t u_stride, int64_t win_first, int64_t win_count, int64_t n_total) {
   typedef typename Fmt<FMT>::T S;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  S *smem = reinterpret_cast<S *>(smem_raw);
-  S *u = reinterpret_cast<S *>(u_out);
   constexpr int PADN = N + N / 32;
-  constexpr int TPP = N / VPT;  // threads per transform
+  constexpr int TPP = N / VPT;                      // threads per transform
+  constexpr int BS = (SPLIT ? 1 : 2) * N / VPT;      // threads per CTA
+  constexpr int m = Plan<N>::m;
+  constexpr int RL = Plan<N>::last;
+  S *smem = reinterpret_cast<S *>(smem_raw);
+  unsigned char *stage = smem_raw + (size_t)(SPLIT ? 1 : 2) * PADN * sizeof(S);   // 16-byte aligned (PADN % 4 == 0)
+  S *u = reinterpret_cast<S *>(u_out);
   const int S_hop = N - V;
-  const int64_t i = win_first + blockIdx.x;
-  const int64_t lo = i * S_hop - V / 2;
   const int psplit = SPLIT ? (int)blockIdx.y : 0;
-  S *b0 = smem, *b1 = smem + PADN;
-  // ingest: one 4-scalar sample-time gives both pols.  A thread's loads are issued
-  // in groups of G before any is used (one memory latency per group, not one per
-  // sample): the block size is a compile-time constant and the loops unroll.
-  constexpr int BS = (SPLIT ? 1 : 2) * N / VPT;
-  constexpr int PER = N / BS;
-  constexpr int G = PER < 8 ? PER : 8;
+  const int pol = SPLIT ? psplit : (int)threadIdx.x / TPP;
+  const int t = threadIdx.x % TPP;
+  S *buf = smem + ((!SPLIT && pol) ? PADN : 0);
+  const int esz = raw_bytes(dtype);
   auto src_of = [&](int64_t n, int64_t &off) -> const uint8_t * {
     if (n < call_first) { off = n - tail_first; return tail; }
     off = n - call_first;
     return call;
   };
-#pragma unroll 1
-  for (int r0 = 0; r0 < PER; r0 += G) {
-    float4 x[G];
-    if (dtype == RX_I8x4) {
-#pragma unroll
-      for (int r = 0; r < G; ++r) {
-        const int64_t n = lo + threadIdx.x + (r0 + r) * BS;
-        x[r] = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (n >= 0 && (n_total < 0 || n < n_total)) {
-          int64_t off;
-          const uint8_t *src = src_of(n, off);
-          const char4 c = reinterpret_cast<const char4 *>(src)[off];
-          x[r] = make_float4((float)c.x, (float)c.y, (float)c.z, (float)c.w);
-        }
-      }
-    } else {
-#pragma unroll
-      for (int r = 0; r < G; ++r) {
-        const int64_t n = lo + threadIdx.x + (r0 + r) * BS;
-        x[r] = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (n >= 0 && (n_total < 0 || n < n_total)) {
-          int64_t off;
-          const uint8_t *src = src_of(n, off);
-          x[r] = reinterpret_cast<const float4 *>(src)[off];
-        }
-      }
-    }
-#pragma unroll
-    for (int r = 0; r < G; ++r) {
-      const int m = threadIdx.x + (r0 + r) * BS;
-      if (SPLIT) {
-        b0[pad(m)] = st2<S>(psplit ? make_float2(x[r].z * scale, x[r].w * scale)
-                                   : make_float2(x[r].x * scale, x[r].y * scale));
+  auto in_range = [&](int64_t n) { return n >= 0 && (n_total < 0 || n < n_total); };
+  // raw samples of window i into `stage` (zero outside the stream)
+  auto issue = [&](int64_t i) {
+    const int64_t lo = (win_first + i) * S_hop - V / 2;
+    for (int mm = threadIdx.x; mm < N; mm += BS) {
+      const int64_t n = lo + mm;
+      unsigned char *d = stage + (size_t)mm * esz;
+      if (in_range(n)) {
+        int64_t off;
+        const uint8_t *src = src_of(n, off) + off * esz;
+        if (esz == 4)
+          asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(smem_u32_of(d)), "l"(src) : "memory");
+        else
+          asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_u32_of(d)), "l"(src) : "memory");
+      } else if (esz == 4) {
+        *reinterpret_cast<unsigned *>(d) = 0u;
       } else {
-        b0[pad(m)] = st2<S>(make_float2(x[r].x * scale, x[r].y * scale));
-        b1[pad(m)] = st2<S>(make_float2(x[r].z * scale, x[r].w * scale));
+        *reinterpret_cast<float4 *>(d) = make_float4(0.f, 0.f, 0.f, 0.f);
       }
     }
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+  };
+  // sample-time lo + mm of this thread's polarisation, scaled, as complex float
+  auto sample = [&](int64_t lo, int mm) -> float2 {
+    if (PREFETCH) {
+      if (esz == 4) {
+        const char4 c = *reinterpret_cast<const char4 *>(stage + (size_t)mm * 4);
+        return pol ? make_float2((float)c.z * scale, (float)c.w * scale) : make_float2((float)c.x * scale, (float)c.y * scale);
+      }
+      const float4 f = *reinterpret_cast<const float4 *>(stage + (size_t)mm * 16);
+      return pol ? make_float2(f.z * scale, f.w * scale) : make_float2(f.x * scale, f.y * scale);
+    }
+    const int64_t n = lo + mm;
+    if (!in_range(n)) return make_float2(0.f, 0.f);
+    int64_t off;
+    const uint8_t *src = src_of(n, off);
+    if (esz == 4) {
+      const char4 c = reinterpret_cast<const char4 *>(src)[off];
+      return pol ? make_float2((float)c.z * scale, (float)c.w * scale) : make_float2((float)c.x * scale, (float)c.y * scale);
+    }
+    const float4 f = reinterpret_cast<const float4 *>(src)[off];
+    return pol ? make_float2(f.z * scale, f.w * scale) : make_float2(f.x * scale, f.y * scale);
+  };
+  const int64_t stride = gridDim.x;
+  int64_t i = blockIdx.x;
+  if (PREFETCH && i < win_count) issue(i);
+  for (; i < win_count; i += stride) {
+    const int64_t lo = (win_first + i) * S_hop - V / 2;
+    if (PREFETCH) {
+      asm volatile("cp.async.wait_all;\n" ::: "memory");
+      __syncthreads();
+    }
+    // ---- input pass = forward pass 0 (radix 16, Ns 1): samples j + r N/16 -> j 16 + r
+    {
+      constexpr int PER = VPT / 16;
+      float2 v[PER][16];
+#pragma unroll
+      for (int q = 0; q < PER; ++q) {
+        const int j = t + q * TPP;
+#pragma unroll
+        for (int r = 0; r < 16; ++r) v[q][r] = sample(lo, j + r * (N / 16));
+        dft<16>(v[q]);
+      }
+      pass_store<N, VPT, 16, 1>(buf, t, v);
+    }
+    __syncthreads();
+    if (PREFETCH && i + stride < win_count) issue(i + stride);   // stage is free again
+    forward_middle<N, VPT, 1, 16>(buf, t, tw);
+    // ---- fused middle: forward pass m-1 (Ns N/RL), x H/N, conj, inverse pass 0 (Ns 1)
+    {
+      constexpr int PER = VPT / RL;
+      float2 v[PER][RL];
+      pass_load<N, VPT, RL, fwd_ns_last<N>()>(buf, t, tw, v);
+#pragma unroll
+      for (int q = 0; q < PER; ++q) {
+        const int j = t + q * TPP;
+#pragma unroll
+        for (int r = 0; r < RL; ++r) {
+          float2 hk = __ldg(&H[j + r * (N / RL)]);
+          if (FMT != RX_FMT_F32) hk = make_float2(hk.x * hscale, hk.y * hscale);
+          v[q][r] = cconj(cmul(v[q][r], hk));
+        }
+        dft<RL>(v[q]);
+      }
+      __syncthreads();
+      pass_store<N, VPT, RL, 1>(buf, t, v);
+      __syncthreads();
+    }
+    inverse_middle<N, VPT, 1, RL>(buf, t, tw);
+    // ---- output pass = inverse pass m-1 (radix 16, Ns N/16): natural order -> HBM
+    {
+      constexpr int PER = VPT / 16;
+      float2 v[PER][16];
+      pass_load<N, VPT, 16, N / 16>(buf, t, tw, v);
+      S *out = u + (int64_t)pol * u_stride;
+      const int64_t n0 = (win_first + i) * S_hop - V / 2;   // stream index of element 0
+#pragma unroll
+      for (int q = 0; q < PER; ++q) {
+        const int j = t + q * TPP;
+#pragma unroll
+        for (int r = 0; r < 16; ++r) {
+          const int k = j + r * (N / 16);
+          const int64_t n = n0 + k;
+          if (k >= V / 2 && k < V / 2 + S_hop && (n_total < 0 || n < n_total))
+            out[n - u_base] = st2<S>(cconj(v[q][r]));
+        }
+      }
+    }
+    __syncthreads();   // every read of buf is done before the next window's input pass
   }
-  __syncthreads();
-  const int pol = SPLIT ? psplit : threadIdx.x / TPP;
-  const int t = threadIdx.x % TPP;
-  S *buf = (!SPLIT && pol) ? b1 : b0;
-  fft_forward<N, VPT>(buf, t, tw);
-  // multiply by H/N and conjugate (inverse via the forward transform)
-  // (a full unroll at VPT = 32 makes the register allocator spill heavily)
-#pragma unroll(VPT > 16 ? 2 : VPT)
-  for (int q = 0; q < VPT; ++q) {
-    const int k = t + q * TPP;
-    float2 hk = __ldg(&H[k]);
-    if (FMT != RX_FMT_F32) hk = make_float2(hk.x * hscale, hk.y * hscale);
-    buf[pad(k)] = st2<S>(cconj(cmul(ld2(buf[pad(k)]), hk)));
-  }
-  __syncthreads();
-  fft_forward<N, VPT>(buf, t, tw);
-  S *out = u + (int64_t)pol * u_stride;
-  for (int tt = V / 2 + t; tt < V / 2 + S_hop; tt += TPP) {
-    const int64_t n = i * S_hop + (tt - V / 2);
-    if (n_total >= 0 && n >= n_total) break;
-    out[n - u_base] = st2<S>(cconj(ld2(buf[pad(tt)])));
-  }
+  if (PREFETCH) asm volatile("cp.async.wait_all;\n" ::: "memory");
 }
 
 template <int N, int VPT, bool SPLIT, int FMT>
@@ -155,17 +296,36 @@ static cudaError_t launch_cdc_n(int V, const void *tail, int64_t tail_first, int
                                 const void *call, int64_t call_first, int64_t call_n, int dtype,
                                 float scale, const float2 *H, const float2 *tw, void *u,
                                 int64_t u_base, int64_t u_stride, int64_t win_first,
-                                int64_t win_count, int64_t n_total, cudaStream_t s) {
+                                int64_t win_count, int64_t n_total, int sm_budget, cudaStream_t s) {
   typedef typename Fmt<FMT>::T S;
-  const size_t sm = (SPLIT ? 1 : 2) * (N + N / 32) * sizeof(S);
-  cudaError_t e = cudaFuncSetAttribute(cdc_kernel<N, VPT, SPLIT, FMT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  constexpr int BS = (SPLIT ? 1 : 2) * N / VPT;
+  const size_t sm_fft = (size_t)(SPLIT ? 1 : 2) * (N + N / 32) * sizeof(S);
+  const size_t sm_stage = (size_t)N * (dtype == RX_I8x4 ? 4 : 16);
+  const bool prefetch = sm_fft + sm_stage <= 200 * 1024;
+  const size_t sm = sm_fft + (prefetch ? sm_stage : 0);
+  const void *fn = prefetch ? (const void *)cdc_kernel<N, VPT, SPLIT, FMT, true>
+                            : (const void *)cdc_kernel<N, VPT, SPLIT, FMT, false>;
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
-  dim3 grid((unsigned)win_count, SPLIT ? 2 : 1);
+  int dev = 0, sms = 0, per = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, BS, sm);
+  if (e != cudaSuccess) return e;
+  const int64_t budget = (sm_budget > 0 && sm_budget < sms ? sm_budget : sms) * (int64_t)std::max(per, 1);
+  const int64_t ctas = std::max<int64_t>(1, std::min<int64_t>(win_count, SPLIT ? std::max<int64_t>(1, budget / 2) : budget));
+  dim3 grid((unsigned)ctas, SPLIT ? 2 : 1);
   const float rs = sqrtf((float)N);
   const float in_scale = FMT == RX_FMT_F32 ? scale : scale / rs;
-  cdc_kernel<N, VPT, SPLIT, FMT><<<grid, (SPLIT ? 1 : 2) * N / VPT, sm, s>>>(
-      V, (const uint8_t *)tail, tail_first, tail_n, (const uint8_t *)call, call_first, call_n,
-      dtype, in_scale, rs, H, tw, u, u_base, u_stride, win_first, n_total);
+  const uint8_t *tl = (const uint8_t *)tail, *cl = (const uint8_t *)call;
+  if (prefetch)
+    cdc_kernel<N, VPT, SPLIT, FMT, true><<<grid, BS, sm, s>>>(V, tl, tail_first, tail_n, cl, call_first, call_n, dtype,
+                                                              in_scale, rs, H, tw, u, u_base, u_stride, win_first,
+                                                              win_count, n_total);
+  else
+    cdc_kernel<N, VPT, SPLIT, FMT, false><<<grid, BS, sm, s>>>(V, tl, tail_first, tail_n, cl, call_first, call_n, dtype,
+                                                               in_scale, rs, H, tw, u, u_base, u_stride, win_first,
+                                                               win_count, n_total);
   return cudaGetLastError();
 }
 
@@ -174,12 +334,12 @@ static cudaError_t launch_cdc_fmt(int N, int V, const void *tail, int64_t tail_f
                                   const void *call, int64_t call_first, int64_t call_n, int dtype,
                                   float scale, const float2 *H, const float2 *tw, void *u,
                                   int64_t u_base, int64_t u_stride, int64_t win_first, int64_t win_count,
-                                  int64_t n_total, cudaStream_t s) {
+                                  int64_t n_total, int sm_budget, cudaStream_t s) {
 #define RX_CDC_CASE(NN, VPT, SPLIT)                                                                \
   case NN:                                                                                         \
     return launch_cdc_n<NN, VPT, SPLIT, FMT>(V, tail, tail_first, tail_n, call, call_first, call_n, \
                                              dtype, scale, H, tw, u, u_base, u_stride, win_first,  \
-                                             win_count, n_total, s);
+                                             win_count, n_total, sm_budget, s);
   switch (N) {
     RX_CDC_CASE(256, 16, false)
     RX_CDC_CASE(512, 16, false)
@@ -197,18 +357,18 @@ cudaError_t launch_cdc(int N, int V, const void *tail, int64_t tail_first, int64
                        const void *call, int64_t call_first, int64_t call_n, int dtype,
                        float scale, const float2 *H, const float2 *tw, void *u,
                        int64_t u_base, int64_t u_stride, int64_t win_first, int64_t win_count,
-                       int64_t n_total, cudaStream_t s, int fmt) {
+                       int64_t n_total, cudaStream_t s, int fmt, int sm_budget) {
   if (win_count <= 0) return cudaSuccess;
   switch (fmt) {
     case RX_FMT_F32:
       return launch_cdc_fmt<RX_FMT_F32>(N, V, tail, tail_first, tail_n, call, call_first, call_n, dtype, scale, H, tw,
-                                        u, u_base, u_stride, win_first, win_count, n_total, s);
+                                        u, u_base, u_stride, win_first, win_count, n_total, sm_budget, s);
     case RX_FMT_F16:
       return launch_cdc_fmt<RX_FMT_F16>(N, V, tail, tail_first, tail_n, call, call_first, call_n, dtype, scale, H, tw,
-                                        u, u_base, u_stride, win_first, win_count, n_total, s);
+                                        u, u_base, u_stride, win_first, win_count, n_total, sm_budget, s);
     case RX_FMT_BF16:
       return launch_cdc_fmt<RX_FMT_BF16>(N, V, tail, tail_first, tail_n, call, call_first, call_n, dtype, scale, H,
-                                         tw, u, u_base, u_stride, win_first, win_count, n_total, s);
+                                         tw, u, u_base, u_stride, win_first, win_count, n_total, sm_budget, s);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -78,7 +78,4 @@ __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p) {
 // Error codes stored in the sticky device error word.
 enum : int { DEV_ERR_TIMEOUT = 1 };
 
-// Bounded wait for a spin: 2 s of device time.
-constexpr unsigned long long kSpinLimitNs = 2000000000ull;
-
 }  // namespace rx

@@ -1,10 +1,11 @@
 // Allocation-free blind phase search + demap.
 //
 // Some callers of this library cannot allocate device memory at the point
-// where they need carrier recovery: code recording a CUDA graph (cudaMalloc
-// is not capturable), real-time loops that must never hit the allocator's
-// implicit device synchronisation, and plugin hosts that hand out fixed
-// device memory budgets up front.  rx_bps_demap_noalloc serves them: it runs
+// where they need carrier recovery: real-time loops that must never hit the
+// allocator's implicit device synchronisation (a cudaMalloc can wait for work
+// already queued on the device, which breaks their timing), and plugin hosts
+// that hand out fixed device memory budgets up front and own every
+// allocation.  rx_bps_demap_noalloc serves them: it runs
 // the same BPS / unwrap / hard-decision kernels as rx_process on an
 // equalised block the caller provides, with all of its scratch in one
 // file-scope device array, and never calls cudaMalloc or cudaFree.
@@ -14,8 +15,11 @@
 // that loads the library keeps it until the process exits.  All calls share
 // it, so calls whose work overlaps on the GPU race; run them on one stream or
 // order them.  The first call on a device looks up the array's device address
-// (cudaGetSymbolAddress, with that device current) and caches it; make that
-// first call before any stream capture.
+// (cudaGetSymbolAddress, with that device current) and caches it together with
+// the device's current context; make that first call before any stream
+// capture.  A call that finds a different context (the device was reset and its
+// primary context re-created) looks the address up again.
+#include <cudaTypedefs.h>
 #include <string.h>
 
 #include <mutex>
@@ -39,8 +43,31 @@ constexpr size_t kOffRegion = kOffCarry + 256;                              // d
 constexpr size_t kScratchBytes = kOffRegion + 256;
 
 constexpr int kMaxDevices = 64;
-unsigned char *g_scratch_addr[kMaxDevices] = {};  // device address per device, from the symbol lookup
+struct ScratchRef {
+  void *ctx;            // the context the address belongs to
+  unsigned char *addr;  // device address of the array, from the symbol lookup
+};
+ScratchRef g_scratch[kMaxDevices] = {};
 std::mutex g_scratch_mu;
+
+// The calling thread's current context (driver entry point fetched through the
+// runtime, so the library needs no link against the driver library); nullptr
+// if it cannot be had.
+void *current_context() {
+  static PFN_cuCtxGetCurrent_v4000 fn = nullptr;
+  static bool looked = false;
+  if (!looked) {
+    looked = true;
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 4000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuCtxGetCurrent_v4000>(p);
+  }
+  CUcontext c = nullptr;
+  if (!fn || fn(&c) != CUDA_SUCCESS) return nullptr;
+  return c;
+}
 
 }  // namespace
 
@@ -64,12 +91,14 @@ extern "C" rx_status rx_bps_demap_noalloc(const float *y, int64_t y_stride, int6
   unsigned char *base;
   {
     std::lock_guard<std::mutex> lock(g_scratch_mu);
-    if (!g_scratch_addr[dev]) {
+    ScratchRef &ref = g_scratch[dev];
+    if (!ref.addr || (ref.ctx != nullptr && current_context() != ref.ctx)) {
       void *p = nullptr;
       if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return RX_ECUDA;
-      g_scratch_addr[dev] = static_cast<unsigned char *>(p);
+      ref.addr = static_cast<unsigned char *>(p);
+      ref.ctx = current_context();   // the lookup made the device's context current
     }
-    base = g_scratch_addr[dev];
+    base = ref.addr;
   }
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
   // the unwrap count starts at zero for every call

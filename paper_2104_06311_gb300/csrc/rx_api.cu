@@ -49,6 +49,8 @@ struct rx_stream {
   double fo_smooth = 16.0;
   int fo_track = 1, llr_out = 0, sym_out = 0, eq_out = 0, cdc_out = 0, profile = 0;
   int64_t inner_cap = 0;            // RX_P_INNER_TRACE: entries per butterfly row (0 = off)
+  double wait_limit_us = 2e6;       // RX_P_WAIT_LIMIT_US: limit of every bounded device wait
+  int64_t no_arrive = -1;           // RX_P_TEST_NO_ARRIVE: CTA left out of the wave barriers (-1: none)
   // ---- resolved
   int N = 0, V = 0, Sh = 0, P = 0, C = 256;
   int64_t A_full = 0, span = 0;
@@ -86,6 +88,7 @@ struct rx_stream {
   int *h_err = nullptr;  // pinned mirror of the device error word
   cudaEvent_t err_ev = nullptr;
   int eq_blocks = 0;
+  int sms = 0;                      // multiprocessors of the device
   int pieces = 12;                  // pipeline pieces per call (RX_P_PIPELINE)
   cudaStream_t sub[3] = {nullptr, nullptr, nullptr};   // CDC, equaliser, BPS streams
   cudaEvent_t ev_fork = nullptr;
@@ -401,6 +404,11 @@ rx_status rx_set_param(rx_stream *rx, int key, double v) {
     case RX_P_PIPELINE: s = as_int(1, kMaxPieces, &t); if (s == RX_OK) rx->pieces = (int)t; return s;
     case RX_P_PRECISION: s = as_int(0, 2, &t); if (s == RX_OK) rx->fmt = (int)t; break;
     case RX_P_INNER_TRACE: s = as_int(0, (int64_t)1 << 32, &rx->inner_cap); break;
+    case RX_P_WAIT_LIMIT_US:
+      if (!(v >= 1.0 && v <= 1e8)) return fail(rx, RX_EINVAL, "wait limit must lie in [1, 1e8] us");
+      rx->wait_limit_us = v;
+      return RX_OK;
+    case RX_P_TEST_NO_ARRIVE: return as_int(-1, 1 << 20, &rx->no_arrive);
     default: return fail(rx, RX_EINVAL, "unknown parameter key");
   }
   if (s != RX_OK) return s;
@@ -441,6 +449,8 @@ rx_status rx_get_param(rx_stream *rx, int key, double *v) {
     case RX_P_PRECISION: *v = rx->fmt; break;
     case RX_P_PIPELINE: *v = rx->pieces; break;
     case RX_P_INNER_TRACE: *v = (double)rx->inner_cap; break;
+    case RX_P_WAIT_LIMIT_US: *v = rx->wait_limit_us; break;
+    case RX_P_TEST_NO_ARRIVE: *v = (double)rx->no_arrive; break;
     default: return fail(rx, RX_EINVAL, "unknown parameter key");
   }
   return RX_OK;
@@ -511,6 +521,11 @@ rx_status rx_reserve(rx_stream *rx, int64_t max_call) {
   e = launch_tables(rx->H, rx->tw, rx->N, rx->baud, rx->L_km, rx->D, rx->lam_nm, rx->rolloff, rx->stream);
   if (e != cudaSuccess) { release(rx); return cuda_fail(rx, e, "filter tables"); }
   rx->eq_blocks = 2 * std::min(rx->P, eq_max_blocks() / 2);
+  {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&rx->sms, cudaDevAttrMultiProcessorCount, dev);
+  }
   if (rx->eq_blocks < 2) { release(rx); return fail(rx, RX_ECUDA, "equaliser kernel cannot be resident"); }
   rx->reserved = true;
   reset_host_state(rx);
@@ -689,7 +704,8 @@ rx_status rx_process(rx_stream *rx, const rx_in *in, rx_out *out) {
       rx->stage_launches[RX_STAGE_CDC] += 1;
       RX_CUDA(launch_cdc(rx->N, rx->V, rx->tail[rx->cur_tail], rx->tail_first, rx->tail_n, in->data, call_first,
                          call_n, rx->dtype, (float)rx->in_scale, rx->H, rx->tw, rx->u[rx->cur_u], rx->u_base,
-                         rx->u_cap, w_done, w_need - w_done, rx->n_total, rx->sub[0], rx->fmt),
+                         rx->u_cap, w_done, w_need - w_done, rx->n_total, rx->sub[0], rx->fmt,
+                         rx->pieces > 1 ? std::max(16, rx->sms - rx->eq_blocks) : 0),
               "cdc");
       w_done = w_need;
     }
@@ -731,6 +747,8 @@ rx_status rx_process(rx_stream *rx, const rx_in *in, rx_out *out) {
       L.cma_r2 = rx->mod_bits == 4 ? 1.32f : 1.0f;
       L.fo_smooth = rx->fo_smooth;
       L.inc_scale = (double)(1ll << kFoGridBits) / (4.0 * 3.14159265358979323846 * rx->fo_smooth);
+      L.spin_ns = (unsigned long long)(rx->wait_limit_us * 1e3);
+      L.no_arrive_cta = (int)rx->no_arrive;
       L.inner = rx->inner;
       L.inner_cap = rx->inner_cap;
       L.inner_acq = (std::max(rx->n_cma, rx->acq_min) - rx->n_cma + rx->Bu - 1) / rx->Bu;

@@ -18,6 +18,8 @@ constexpr int kBpsChunk = 256;    // BPS pass-1 symbols per warp
 // whole multiples of 2^-kFoGridBits turns per sample, so that the tracked phase
 // is an exact sum (Q0.64 turns whose low 64 - kFoGridBits bits stay zero).
 constexpr int kFoGridBits = 16;
+// Default limit of a bounded device spin: 2 s of device time.
+constexpr unsigned long long kSpinLimitNs = 2000000000ull;
 
 // Storage formats of the CDC output (precision form).
 enum { RX_FMT_F32 = 0, RX_FMT_F16 = 1, RX_FMT_BF16 = 2 };
@@ -74,6 +76,8 @@ struct EqLaunch {
   float mu_cma, mu_dd, cma_r2;
   double fo_smooth;
   double inc_scale;         // 2^kFoGridBits / (4 pi fo_smooth): tracker step r -> grid units per sample
+  unsigned long long spin_ns;  // limit of every bounded device wait (ns of device time)
+  int no_arrive_cta;        // CTA that leaves out its arrival at the wave barriers (-1: none; timeout test)
   int8_t *inner;            // optional trace of the inner BPS angle per DD update block, [2][inner_cap]
                             // (row p): acquisition blocks, then inner_spb entries per segment
   int64_t inner_cap, inner_acq;
@@ -114,7 +118,7 @@ cudaError_t launch_cdc(int N, int V, const void *tail, int64_t tail_first, int64
                        const void *call, int64_t call_first, int64_t call_n, int dtype,
                        float scale, const float2 *H, const float2 *tw, void *u,
                        int64_t u_base, int64_t u_stride, int64_t win_first, int64_t win_count,
-                       int64_t n_total, cudaStream_t s, int fmt = RX_FMT_F32);
+                       int64_t n_total, cudaStream_t s, int fmt = RX_FMT_F32, int sm_budget = 0);
 cudaError_t launch_eq(const EqLaunch &L, cudaStream_t s);
 // Batched equaliser: one cooperative launch of nblocks CTAs; d_team[b] =
 // (stream, CTA within that stream's team).  pad_smem: unused dynamic shared

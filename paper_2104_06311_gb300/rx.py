@@ -21,14 +21,14 @@ PARAMS = {
     "N_CMA": 8, "UPDATE_BLOCK": 9, "SEG_LEN": 10, "SEG_PRETRAIN": 11, "BPS_HALFWIN": 12,
     "BLOCK_SAMPLES": 13, "IN_SCALE": 14, "ACQ_MIN": 15, "FO_SMOOTH": 16, "FO_TRACK": 17,
     "LLR_OUT": 18, "SYM_OUT": 19, "EQ_OUT": 20, "CDC_OUT": 21, "PROFILE": 22, "PIPELINE": 23,
-    "PRECISION": 24, "INNER_TRACE": 25,
+    "PRECISION": 24, "INNER_TRACE": 25, "WAIT_LIMIT_US": 26, "TEST_NO_ARRIVE": 27,
 }
 STAGES = ["cdc", "eq", "bps", "move", "ber"]
 
 EXPORTS = ["rx_create", "rx_set_param", "rx_get_param", "rx_set_cuda_stream", "rx_reserve",
            "rx_process", "rx_ber", "rx_trace", "rx_trace_inner", "rx_get_state", "rx_set_state", "rx_reset",
            "rx_sync", "rx_destroy", "rx_status_str", "rx_last_error", "rx_profile",
-           "rx_bps_demap_noalloc",
+           "rx_bps_demap_noalloc", "rx_measure_alu_peak",
            "rx_batch_create", "rx_batch_set_param", "rx_batch_get_param", "rx_batch_set_cuda_stream",
            "rx_batch_process", "rx_batch_ber", "rx_batch_trace", "rx_batch_sync", "rx_batch_destroy",
            "rx_batch_last_error", "rx_batch_profile",
@@ -106,6 +106,7 @@ def load(path: str = LIB_PATH) -> ct.CDLL:
     lib.rx_set_state.argtypes = [P, P, ct.c_size_t]
     lib.rx_profile.argtypes = [P, ct.POINTER(ct.c_double), ct.POINTER(ct.c_int64), ct.c_int]
     lib.rx_bps_demap_noalloc.argtypes = [P, ct.c_int64, ct.c_int64, ct.c_int, ct.c_int, P, ct.c_int64, P]
+    lib.rx_measure_alu_peak.argtypes = [ct.c_int, ct.c_int, P, ct.POINTER(ct.c_double), ct.POINTER(ct.c_double)]
     lib.rx_reset.argtypes = [P]
     lib.rx_sync.argtypes = [P]
     lib.rx_destroy.argtypes = [P]
@@ -195,6 +196,18 @@ def load(path: str = LIB_PATH) -> ct.CDLL:
             getattr(lib, name).restype = ct.c_int
     _lib = lib
     return lib
+
+
+def measure_alu_peak(kind="fp32", iters=None, stream=None):
+    """Measured FP32 / FP64 FMA throughput (TFLOP/s, ms) of this GPU (rx_measure_alu_peak)."""
+    lib = load()
+    k = {"fp32": 0, "fp64": 1}[kind]
+    iters = iters or (8192 if k == 0 else 256)
+    tf, ms = ct.c_double(), ct.c_double()
+    st = lib.rx_measure_alu_peak(k, int(iters), ct.c_void_p(stream), ct.byref(tf), ct.byref(ms))
+    if st != RX_OK:
+        raise RxError(st, "rx_measure_alu_peak failed")
+    return tf.value, ms.value
 
 
 def _check(lib, h, status):

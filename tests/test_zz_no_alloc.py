@@ -1,8 +1,9 @@
 """The allocation-free BPS + demap entry point, checked against rx_process.
 
 rx_bps_demap_noalloc is for callers that cannot allocate device memory when
-they need carrier recovery (graph capture, real-time loops, fixed device
-budgets); its scratch is a static device array.  Fed the equaliser output of
+they need carrier recovery (real-time loops that must not wait on the
+allocator, hosts with a fixed device-memory budget); its scratch is a static
+device array.  Fed the equaliser output of
 an rx_process run, it must reproduce that run's hard bits exactly (the same
 kernels, chunk grid and window truncation), on two calls in a row (the
 shared scratch keeps the previous call's contents).  This file sorts last so
