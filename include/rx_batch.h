@@ -39,9 +39,15 @@ extern "C" {
 
 typedef struct rx_batch rx_batch;
 
+/* Channel flags. */
+enum {
+  RX_CH_NO_FO_TRACK = 1   /* no frequency-offset estimation or removal (a channel
+                             whose carrier is known to sit at the LO frequency)   */
+};
+
 /* One channel.  Samples per symbol 2 and 32 BPS test angles are fixed; the
  * other parameters take the rx.h defaults (N_CMA 8192, B_u 32, S 1024,
- * W 128, N_b 16, mu 1e-3, 65536-sample blocks, frequency tracking on). */
+ * W 128, mu 1e-3, 65536-sample blocks) unless set below. */
 typedef struct {
   double baud;          /* symbol rate [Bd] (> 0)                                */
   double L_km;          /* dispersion length to compensate [km] (>= 0)           */
@@ -52,6 +58,11 @@ typedef struct {
   int32_t ntaps;        /* butterfly taps T (odd, 3..15)                          */
   int32_t fft_n;        /* 0 = autotuned, else a power of two 256..16384          */
   int32_t overlap;      /* 0 = N_CD - 1 rounded up to a multiple of 32            */
+  int32_t flags;        /* RX_CH_* bits (0: frequency tracking on)                */
+  int32_t bps_halfwin;  /* BPS half window N_b, 1..64 (0 = the default 16).  The
+                           window trades tracking of laser phase noise against
+                           averaging of additive noise: a channel with a stable
+                           carrier (no phase noise) takes a longer one          */
 } rx_chan_cfg;
 
 /* Keys for rx_batch_set_param / rx_batch_get_param.  Per-channel keys of rx.h

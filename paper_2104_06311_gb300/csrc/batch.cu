@@ -199,6 +199,8 @@ rx_status check_cfg(rx_batch *b, int i, const rx_chan_cfg &c) {
   if (c.max_samples <= 0 || c.max_samples % 2) return bfail(b, RX_EINVAL, who + "max_samples must be even and positive");
   if (c.mod_bits != 2 && c.mod_bits != 4) return bfail(b, RX_EUNSUPPORTED, who + "mod_bits must be 2 or 4");
   if (c.ntaps < 3 || c.ntaps > 15 || c.ntaps % 2 == 0) return bfail(b, RX_EUNSUPPORTED, who + "ntaps must be odd, 3..15");
+  if (c.flags & ~RX_CH_NO_FO_TRACK) return bfail(b, RX_EINVAL, who + "unknown flags");
+  if (c.bps_halfwin < 0 || c.bps_halfwin > 64) return bfail(b, RX_EUNSUPPORTED, who + "bps_halfwin must lie in 0..64");
   if (c.fft_n != 0 && (!is_pow2(c.fft_n) || c.fft_n < 256 || c.fft_n > 16384))
     return bfail(b, RX_EUNSUPPORTED, who + "FFT size must be a power of two in [256, 16384]");
   if (c.overlap < 0 || c.overlap % 32) return bfail(b, RX_EINVAL, who + "overlap must be a multiple of 32");
@@ -399,7 +401,7 @@ rx_status enqueue(rx_batch *b, const rx_in *ins, rx_out *outs, cudaStream_t s, b
     B.K_end = K;
     B.A = L.A;
     B.span = c.span;
-    B.Nb = kNb;
+    B.Nb = c.cfg.bps_halfwin > 0 ? c.cfg.bps_halfwin : kNb;
     B.mod_bits = c.cfg.mod_bits;
     B.need_s2 = outs[i].llr != nullptr;
     B.bits = outs[i].bits;
@@ -612,12 +614,12 @@ rx_status rx_batch_get_param(rx_batch *b, int ch, int key, double *v) {
     case RX_P_UPDATE_BLOCK: *v = kBu; break;
     case RX_P_SEG_LEN: *v = kS; break;
     case RX_P_SEG_PRETRAIN: *v = kW; break;
-    case RX_P_BPS_HALFWIN: *v = kNb; break;
+    case RX_P_BPS_HALFWIN: *v = c.cfg.bps_halfwin > 0 ? c.cfg.bps_halfwin : kNb; break;
     case RX_P_BLOCK_SAMPLES: *v = (double)kBlockSamples; break;
     case RX_P_IN_SCALE: *v = c.cfg.in_scale; break;
     case RX_P_ACQ_MIN: *v = (double)kAcqMin; break;
     case RX_P_FO_SMOOTH: *v = kFoSmooth; break;
-    case RX_P_FO_TRACK: *v = 1; break;
+    case RX_P_FO_TRACK: *v = (c.cfg.flags & RX_CH_NO_FO_TRACK) ? 0 : 1; break;
     case RX_BP_EQ_TEAM: *v = c.team; break;
     case RX_BP_CDC_NS_PER_SAMPLE: *v = c.ns_per_sample; break;
     default: return bfail(b, RX_EINVAL, "unknown channel parameter");
@@ -712,7 +714,7 @@ rx_status rx_batch_process(rx_batch *b, const rx_in *ins, rx_out *outs) {
       L.cma_r2 = c.cfg.mod_bits == 4 ? 1.32f : 1.0f;
       L.fo_smooth = kFoSmooth;
       L.inc_scale = (double)(1ll << kFoGridBits) / (4.0 * 3.14159265358979323846 * kFoSmooth);
-      L.fo_track = 1;
+      L.fo_track = (c.cfg.flags & RX_CH_NO_FO_TRACK) ? 0 : 1;
       L.nblocks = c.team;
       L.spin_ns = kSpinLimitNs;
       L.no_arrive_cta = -1;

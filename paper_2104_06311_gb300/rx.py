@@ -71,7 +71,8 @@ class rx_rt_cfg(ct.Structure):
 class rx_chan_cfg(ct.Structure):
     _fields_ = [("baud", ct.c_double), ("L_km", ct.c_double), ("D_ps_nm_km", ct.c_double),
                 ("in_scale", ct.c_double), ("max_samples", ct.c_int64), ("mod_bits", ct.c_int32),
-                ("ntaps", ct.c_int32), ("fft_n", ct.c_int32), ("overlap", ct.c_int32)]
+                ("ntaps", ct.c_int32), ("fft_n", ct.c_int32), ("overlap", ct.c_int32),
+                ("flags", ct.c_int32), ("bps_halfwin", ct.c_int32)]
 
 
 class RxError(RuntimeError):
@@ -437,7 +438,8 @@ class Batch:
         for i, c in enumerate(cfgs):
             arr[i] = rx_chan_cfg(float(c["baud"]), float(c["L_km"]), float(c.get("D", 17.0)),
                                  float(c.get("in_scale", 1.0)), int(c["max_samples"]), int(c.get("mod_bits", 2)),
-                                 int(c.get("ntaps", 15)), int(c.get("fft_n", 0)), int(c.get("overlap", 0)))
+                                 int(c.get("ntaps", 15)), int(c.get("fft_n", 0)), int(c.get("overlap", 0)),
+                                 int(c.get("flags", 0)), int(c.get("bps_halfwin", 0)))
         h = ct.c_void_p()
         st = self.lib.rx_batch_create(ct.byref(h), n, arr)
         if st != RX_OK:

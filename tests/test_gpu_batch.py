@@ -6,6 +6,7 @@ import numpy as np
 import pytest
 
 import linksim as L
+import oracle as O
 from chain_helpers import ensure_built, rx_params, run_gpu
 from test_gpu_chain import check_chain
 
@@ -115,3 +116,35 @@ def test_batch_graph_replay_is_exact():
     for r in runs[1:]:
         for (b0, y0), (b1, y1) in zip(runs[0], r):
             assert np.array_equal(b0, b1) and np.array_equal(y0, y1)
+
+
+def test_batch_channel_options_no_fo_tracking_and_long_bps_window():
+    """Per-channel options: a 16QAM channel at 12.5 dB with a stable carrier (no
+    frequency offset, no phase noise) configured with frequency tracking off and a
+    BPS half window of 64, beside a default QPSK channel; each against the oracle
+    with the same options, and the 16QAM BER within 40 % of AWGN theory (the blind
+    chain with the default 33-symbol window and tracking on loses lock here)."""
+    from paper_2104_06311_gb300 import Batch
+    import torch
+    links = [L.Link(mod="16qam", baud=20e9, n_sym=1 << 16, L_km=3000.0, jones=(0.7, 1.3), snr_db=12.5,
+                    adc="int8", seed=71),
+             L.Link(mod="qpsk", baud=12e9, n_sym=40_000, L_km=1500.0, snr_db=11.0, adc="int8", seed=72)]
+    opts = [dict(flags=1, bps_halfwin=64), {}]
+    gens = [L.generate(lk) for lk in links]
+    xs = _samples(gens)
+    b = Batch([dict(_cfg(lk, g), **o) for lk, g, o in zip(links, gens, opts)])
+    assert b.get_param(0, "FO_TRACK") == 0 and b.get_param(0, "BPS_HALFWIN") == 64
+    assert b.get_param(1, "FO_TRACK") == 1 and b.get_param(1, "BPS_HALFWIN") == 16
+    outs = b.alloc_outs(xs, llr=True, sym=True, eq=True, cdc=True)
+    b.process(xs, outs)
+    b.sync()
+    for ch, (lk, g, o) in enumerate(zip(links, gens, opts)):
+        N, V = int(b.get_param(ch, "FFT_N")), int(b.get_param(ch, "OVERLAP"))
+        p = rx_params(lk, g.in_scale, fft_n=N, overlap=V, fo_track=not o.get("flags", 0),
+                      bps_halfwin=o.get("bps_halfwin", 16))
+        rep, _ = check_chain(p, g, _gpu_dict(b, ch, outs[ch], p), {})
+        ref = torch.from_numpy(L.pack_bits(g.tx_bits).view(np.int32)).cuda()
+        e, n, _ = b.ber(ch, outs[ch]["bits"], ref, lk.n_sym)
+        print("batch options ch", ch, o, "BER", e / n, "theory", O.ber_theory(lk.mod, lk.snr_db), rep)
+        if ch == 0:
+            assert e / n < 1.4 * O.ber_theory(lk.mod, lk.snr_db)

@@ -72,7 +72,10 @@ def test_precision_forms_against_oracle_and_fp32():
     evm32 = rows[0][3]
     for fmt, e_u, e_y, evm, evm_o, ber in rows:
         name = {0: "FP32", 1: "FP16", 2: "BF16"}[fmt]
-        print(f"{name}: CDC rel RMS {e_u:.2e}, equaliser rel RMS {e_y:.2e}, EVM {evm:.3f} dB "
+        # the reduced formats' trackers integrate their own (FP16/BF16-input) estimates, so
+        # their equaliser outputs are compared through EVM, not element by element
+        eq_txt = f"equaliser rel RMS {e_y:.2e}, " if fmt == 0 else ""
+        print(f"{name}: CDC rel RMS {e_u:.2e}, {eq_txt}EVM {evm:.3f} dB "
               f"(oracle {evm_o:.3f} dB), penalty vs FP32 {evm - evm32:+.4f} dB, BER {ber:.3e}")
         assert evm - evm32 < 0.1
     # BER of every form within 3 sigma (Poisson) of the FP32 count
@@ -95,3 +98,27 @@ def test_precision_streaming_and_state_roundtrip():
         torch.cuda.synchronize()
         outs.append((o["bits"].cpu().numpy(), o["eq"][:, :o["n"]].cpu().numpy()))
     assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
+
+
+@pytest.mark.parametrize("N", [256, 1024, 4096, 16384])
+@pytest.mark.parametrize("fmt", [1, 2])
+def test_precision_cdc_every_transform_size(N, fmt):
+    """The reduced-format CDC (tensor-core radix-16 passes from N = 512 on, per-window
+    max-abs scaling) against the FP64 overlap-save oracle at every kind of plan:
+    N = 256 (register passes), 1024 (radix-4 middle), 4096 (tensor-core fused middle),
+    16384 (two butterfly groups per thread); float input of large amplitude checks
+    that the per-window scaling keeps FP16 in range."""
+    import torch
+    lk = L.Link(n_sym=20000 + 77, L_km=300.0, snr_db=15.0, adc="f32", seed=880 + N)
+    g = L.generate(lk)
+    samples = np.ascontiguousarray(g.samples * 3000.0)       # far beyond FP16's comfort without scaling
+    p = rx_params(lk, g.in_scale, fft_n=N, overlap=64)
+    rx = make_receiver(p, CDC_OUT=1, PRECISION=fmt)
+    out = rx.run_stream(torch.from_numpy(samples).cuda(), cdc=True)
+    torch.cuda.synchronize()
+    u = out["cdc"][:, :out["cdc_n"]].cpu().numpy().astype(np.complex128)
+    ref = O.cdc_overlap_save(L.deinterleave(samples), O.cdc_filter(p), p.overlap)
+    err = rel_rms(u[:, :ref.shape[1]], ref)
+    print(f"N {N} fmt {fmt}: CDC rel RMS {err:.2e}")
+    assert np.all(np.isfinite(u))
+    assert err < U_TOL[fmt], err
