@@ -53,6 +53,8 @@ def parse():
                     help="c2: the 10,000 km single stream (default); c4: the 64-channel batched form; "
                          "c5: the chain plus the learned post-equaliser on a Kerr-nonlinear link")
     ap.add_argument("--channels", type=int, default=64, help="c4: number of channels")
+    ap.add_argument("--dft-tc", type=int, default=0,
+                    help="precision form: 1 = CDC radix-16 passes on tensor cores, 0 = register butterflies")
     ap.add_argument("--train-symbols", type=int, default=1 << 14, help="c5: symbols per training sequence")
     return ap.parse_args()
 
@@ -301,16 +303,32 @@ def bench_batch(args, rank, world, local):
     prof = b.profile(reset=True)
     b.set_param("PROFILE", 0)
     # BER per channel (after the timed region)
+    # each channel's last V/2 symbols are not counted: the generator applies the fibre's
+    # dispersion circularly over the finite stream, so the tail carries the head's
+    # dispersed energy, which no linear receiver undoes (the head is skipped anyway)
     errs = []
     for ch in range(len(xs)):
-        e, nb, _ = b.ber(ch, outs[ch]["bits"], refs[ch], xs[ch].shape[0] // 2)
+        edge = int(b.get_param(ch, "OVERLAP")) // 2
+        e, nb, _ = b.ber(ch, outs[ch]["bits"], refs[ch], xs[ch].shape[0] // 2 - edge)
         errs.append((e, nb))
     errs_all = merge_counts(errs, len(links_all), mine, dist, "cuda")
     ber = [e / nb if nb else None for e, nb in errs_all]
     import oracle as O_
     theory = [O_.ber_theory(lk.mod, lk.snr_db) for lk in links_all]
-    ratio = [b_ / t_ if b_ is not None else None for b_, t_ in zip(ber, theory)]
-    hi_snr = [r for r, lk in zip(ratio, links_all) if r is not None and lk.snr_db >= 12.0]
+
+    def snr_penalty_db(lk, b_):
+        """Es/N0 at which AWGN theory gives this BER, below the channel's own (None: error-free)."""
+        if b_ is None or b_ <= 0.0:
+            return None
+        if b_ >= O_.ber_theory(lk.mod, -10.0):
+            return float("inf")
+        from scipy.optimize import brentq
+        eff = brentq(lambda x: O_.ber_theory(lk.mod, x) - b_, -10.0, 40.0)
+        return lk.snr_db - eff
+
+    pen = [snr_penalty_db(lk, b_) for lk, b_ in zip(links_all, ber)]
+    hi_snr = [q for q, lk in zip(pen, links_all) if q is not None and lk.snr_db >= 12.0]
+    hi_free = sum(1 for q, lk in zip(pen, links_all) if q is None and lk.snr_db >= 12.0)
     lo_snr = [(ch, lk.mod, round(lk.snr_db, 1), ber[ch]) for ch, lk in enumerate(links_all) if lk.snr_db < 12.0]
     correct_bits = sum(2 * lk.n_sym * (4 if lk.mod == "16qam" else 2) * (1.0 - (b_ or 0.0))
                        for lk, b_ in zip(links_all, ber))
@@ -375,11 +393,18 @@ def bench_batch(args, rank, world, local):
                             "median": statistics.median(x for x in ber if x is not None),
                             "max": max(x for x in ber if x is not None),
                             "channels_above_0.1": sum(1 for x in ber if x is not None and x > 0.1),
-                            "ber_over_theory_at_or_above_12dB": {"channels": len(hi_snr), "max": max(hi_snr),
-                                                                 "median": statistics.median(hi_snr)},
+                            "snr_penalty_db_at_or_above_12dB": {
+                                "channels_with_errors": len(hi_snr), "error_free": hi_free,
+                                "max": max(hi_snr) if hi_snr else None,
+                                "median": statistics.median(hi_snr) if hi_snr else None,
+                                "worst": sorted(((round(q, 2), ch) for ch, q in enumerate(pen)
+                                                 if q is not None and links_all[ch].snr_db >= 12.0),
+                                                reverse=True)[:5]},
                             "below_12dB": lo_snr,
                             "config": "per channel: frequency tracking off (the channels carry no offset), "
-                                      "BPS half window 64 for 16QAM, 16 for QPSK (no laser phase noise)"},
+                                      "BPS half window 64 for 16QAM, 16 for QPSK (no laser phase noise)",
+                            "counted": "symbols [A + 8192, K - V/2) of each channel (the synthetic stream's "
+                                       "dispersion is circular: its last V/2 symbols hold wrapped energy)"},
         "stage_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
         "gpu_launches": int(launches),
         "roofline": roof,
@@ -723,7 +748,8 @@ def main():
     stream = torch.cuda.current_stream()
     mbits = L.bits_per_symbol(lk.mod)
     prec = {"fp32": 0, "fp16": 1, "bf16": 2}[args.precision]
-    rx = Receiver(lk.baud, lk.L_km, D=lk.D, stream=stream, MOD=mbits, IN_SCALE=g.in_scale, PRECISION=prec)
+    rx = Receiver(lk.baud, lk.L_km, D=lk.D, stream=stream, MOD=mbits, IN_SCALE=g.in_scale, PRECISION=prec,
+                  DFT_TC=args.dft_tc)
     rx.reserve(n)
     out = rx.alloc_out(K + 64)
 
@@ -839,6 +865,8 @@ def main():
         "scaling": "weak", "vs_baseline": None, "dtype": "f32" if prec == 0 else f"f32 ({args.precision} CDC storage)",
         "data": f"synthetic (seeded linksim {lk.L_km:.0f} km link), resident in HBM",
         "config": {"workload": WORKLOADS[args.workload], "precision": args.precision,
+                   "cdc_dft": ("tensor-core DFT-16 (FP32 accumulate)" if args.dft_tc and prec else
+                               "register butterflies"),
                    "sample_times": n, "fft_n": int(rx.get_param("FFT_N")), "overlap": int(rx.get_param("OVERLAP")),
                    "taps": T, "bps_angles": 32, "segments_per_wave": 32,
                    "l2": f"inputs ({n * 4 >> 20} MiB) and CDC intermediates ({n * 16 >> 20} MiB) exceed L2; no flush",

@@ -102,10 +102,15 @@ enum {
                               grid and row-pair barriers), microseconds of device
                               time, 1..1e8 (default 2e6); a wait that runs out sets
                               the error word (RX_ETIMEOUT)                          */
-  RX_P_TEST_NO_ARRIVE = 27 /* failure-detection test: the equaliser CTA with this
+  RX_P_TEST_NO_ARRIVE = 27, /* failure-detection test: the equaliser CTA with this
                               index leaves out its arrival at the wave barriers, so
                               that the other CTAs' waits run out after
                               RX_P_WAIT_LIMIT_US (-1 = off, the default)             */
+  RX_P_DFT_TC = 28         /* precision form (RX_P_PRECISION 1 or 2): 1 = the CDC's
+                              radix-16 DFT passes as FP16/BF16 tensor-core products
+                              with FP32 accumulation, 0 = FP32 register butterflies
+                              on FP16/BF16 storage (default: measured faster, the
+                              transform being bound by shared-memory traffic)      */
 };
 
 /* Stages reported by rx_profile. */

@@ -32,6 +32,8 @@
 // about 1.08 QPSK steps: its inner-BPS distance is longer); pairs go one at a
 // time to the channel whose time is currently largest, within the co-resident
 // CTA budget of the launch.
+#include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
@@ -77,6 +79,67 @@ struct Chan {
 
 std::mutex g_tune_mu;
 std::map<std::pair<int, int>, double> g_tune;   // (device, N) -> ns per window
+std::map<int, bool> g_tune_loaded;              // device -> persisted entries read
+
+// The tuning table can persist across processes in the text file named by the
+// environment variable RX_TUNE_CACHE: one line per entry, "<GPU name>|<SMs>|<N>|<ns
+// per window>".  Entries belong to the GPU model (name and SM count) they were
+// measured on; lines of other GPUs are kept when the file is rewritten.
+std::string gpu_key(int dev) {
+  cudaDeviceProp prop;
+  if (cudaGetDeviceProperties(&prop, dev) != cudaSuccess) return std::string();
+  for (char *c = prop.name; *c; ++c)
+    if (*c == '|' || *c == '\n') *c = ' ';
+  return std::string(prop.name) + "|" + std::to_string(prop.multiProcessorCount);
+}
+
+std::vector<std::string> cache_lines(const char *path) {
+  std::vector<std::string> lines;
+  FILE *f = fopen(path, "r");
+  if (!f) return lines;
+  char buf[512];
+  while (fgets(buf, sizeof(buf), f)) {
+    std::string l(buf);
+    while (!l.empty() && (l.back() == '\n' || l.back() == '\r')) l.pop_back();
+    if (!l.empty()) lines.push_back(l);
+  }
+  fclose(f);
+  return lines;
+}
+
+// Entries of this GPU from the persisted file into g_tune (caller holds g_tune_mu).
+void load_tune_cache(int dev) {
+  if (g_tune_loaded[dev]) return;
+  g_tune_loaded[dev] = true;
+  const char *path = getenv("RX_TUNE_CACHE");
+  if (!path || !*path) return;
+  const std::string key = gpu_key(dev);
+  for (const std::string &l : cache_lines(path)) {
+    if (l.compare(0, key.size() + 1, key + "|") != 0) continue;
+    int N = 0;
+    double ns = 0.0;
+    if (sscanf(l.c_str() + key.size() + 1, "%d|%lf", &N, &ns) == 2 && N >= 256 && N <= 16384 && ns > 0.0)
+      g_tune[{dev, N}] = ns;
+  }
+}
+
+// Rewrite the persisted file with this GPU's entries (caller holds g_tune_mu).
+void save_tune_cache(int dev) {
+  const char *path = getenv("RX_TUNE_CACHE");
+  if (!path || !*path) return;
+  const std::string key = gpu_key(dev);
+  std::vector<std::string> keep;
+  for (const std::string &l : cache_lines(path))
+    if (l.compare(0, key.size() + 1, key + "|") != 0) keep.push_back(l);
+  const std::string tmp = std::string(path) + ".tmp";
+  FILE *f = fopen(tmp.c_str(), "w");
+  if (!f) return;
+  for (const std::string &l : keep) fprintf(f, "%s\n", l.c_str());
+  for (const auto &kv : g_tune)
+    if (kv.first.first == dev) fprintf(f, "%s|%d|%.6g\n", key.c_str(), kv.first.second, kv.second);
+  fclose(f);
+  rename(tmp.c_str(), path);
+}
 
 __global__ void batch_init_kernel(const EqLaunch *__restrict__ Ls) {
   const EqLaunch &L = Ls[blockIdx.x];
@@ -213,6 +276,8 @@ rx_status tune_table(rx_batch *b, std::map<int, double> &out) {
   BX_CUDA(cudaGetDevice(&dev), "device");
   BX_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "device");
   std::lock_guard<std::mutex> lock(g_tune_mu);
+  load_tune_cache(dev);
+  bool measured = false;
   for (int N = 256; N <= 16384; N *= 2) {
     auto it = g_tune.find({dev, N});
     if (it != g_tune.end()) {
@@ -254,7 +319,9 @@ rx_status tune_table(rx_batch *b, std::map<int, double> &out) {
     const double ns = (double)best * 1e6 / (double)nw;
     g_tune[{dev, N}] = ns;
     out[N] = ns;
+    measured = true;
   }
+  if (measured) save_tune_cache(dev);
   return RX_OK;
 }
 

@@ -141,26 +141,29 @@ __global__ void __launch_bounds__(kBpsWarps * 32) bps_pass1_slide(BpsLaunch L) {
   }
 }
 
-// Pass 1 at the default half window Nb = 16: the 33-symbol window of output
-// symbol 32 q + i spans staged positions 32 q + i .. 32 q + i + 32, i.e. the
-// suffix of block q from i plus the prefix of block q + 1 up to i:
-//   D_{32q+i} = sum_{j=i..31} d_{32q+j} + sum_{j=0..i} d_{32q+32+j}
-// (position m holds symbol a - 16 + m).  Each lane keeps its angle's distances
-// of the two blocks in registers: three adds per symbol and angle, no ring in
-// shared memory.  Distances are taken on the grid scaled by sqrt10 for 16QAM,
-// (||x'| - 2| - 1)^2 per dimension = 10 (x - dec x)^2 (the same argmin); the s2
-// sum is scaled back.
+// Pass 1 at half windows Nb = 16 M (M = 1..4): the (32 M + 1)-symbol window of
+// output symbol 32 q + i spans staged positions 32 q + i .. 32 q + i + 32 M, i.e.
+// the suffix of block q from i, the whole blocks q + 1 .. q + M - 1 and the
+// prefix of block q + M up to i:
+//   D_{32q+i} = sum_{j=i..31} d_{32q+j} + sum_{r=1..M-1} T_{q+r} + sum_{j=0..i} d_{32(q+M)+j}
+// (position m holds symbol a - Nb + m; T = a whole block's sum).  Each lane keeps
+// its angle's distances of the two edge blocks in registers and the totals of the
+// blocks between them: a few adds per symbol and angle, no ring in shared memory
+// (for M > 1 block q's distances are computed a second time, when it becomes the
+// suffix block).  Distances are taken on the grid scaled by sqrt10 for 16QAM,
+// (||x'| - 2| - 1)^2 per dimension = 10 (x - dec x)^2 (the same argmin); the s2 sum
+// is scaled back.
 constexpr int kBlkNb = 16;
 
-// Staged positions per warp: the chunk, its two 16-symbol halos and the 32
+// Staged positions per warp: the chunk, its two Nb-symbol halos and the 32
 // positions past them that the last block reads (zero), so that every read of
 // a block is at a constant offset.
-__host__ __device__ inline int pass1_blk_ys_cap(int chunk) { return chunk + 2 * kBlkNb + 32; }
-__host__ __device__ inline size_t pass1_blk_warp_bytes(int chunk) {
-  return (size_t)pass1_blk_ys_cap(chunk) * sizeof(float2) + (size_t)((chunk + 15) / 16) * 16;
+__host__ __device__ inline int pass1_blk_ys_cap(int chunk, int Nb) { return chunk + 2 * Nb + 32; }
+__host__ __device__ inline size_t pass1_blk_warp_bytes(int chunk, int Nb) {
+  return (size_t)pass1_blk_ys_cap(chunk, Nb) * sizeof(float2) + (size_t)((chunk + 15) / 16) * 16;
 }
 
-template <int MB, bool NEED_S2, bool EDGE>
+template <int MB, bool NEED_S2, bool EDGE, int M>
 __device__ __forceinline__ void pass1_blocks(const float2 *ys, int v_lo, int v_hi, float2 rot, int nt, int lane,
                                              int8_t *bq, int &R, float &s2) {
   constexpr unsigned FULL = 0xffffffffu;
@@ -179,27 +182,50 @@ __device__ __forceinline__ void pass1_blocks(const float2 *ys, int v_lo, int v_h
     return (EDGE && (m < v_lo || m >= v_hi)) ? 0.f : d;
   };
   float d0[32], d1[32];
+  float T[M > 1 ? M - 1 : 1];           // totals of blocks q + 1 .. q + M - 1
 #pragma unroll
   for (int j = 0; j < 32; ++j) d0[j] = dd(ys, j, j);
+  if constexpr (M > 1) {
+#pragma unroll
+    for (int r = 1; r < M; ++r) {
+      float t = 0.f;
+#pragma unroll
+      for (int j = 0; j < 32; ++j) t += dd(ys, 32 * r + j, 32 * r + j);
+      T[r - 1] = t;
+    }
+  }
   int prev = 0;
   for (int base = 0; base < nt; base += 32) {
     const float2 *yb = ys + base;
     const int cnt = min(32, nt - base);          // symbols of this block
+    if constexpr (M > 1) {
+      if (base > 0) {
 #pragma unroll
-    for (int j = 0; j < 32; ++j) d1[j] = dd(yb, 32 + j, base + 32 + j);
+        for (int j = 0; j < 32; ++j) d0[j] = dd(yb, j, base + j);
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < 32; ++j) d1[j] = dd(yb, 32 * M + j, base + 32 * M + j);
 #pragma unroll
     for (int j = 30; j >= 0; --j) d0[j] += d0[j + 1];   // suffix sums of block q
+    float mid = 0.f;
+    if constexpr (M > 1) {
+#pragma unroll
+      for (int r = 0; r < M - 1; ++r) mid += T[r];
+    }
     float pre = 0.f;
     int mybs = 0;                                 // lane i: bhat of symbol base + i
 #pragma unroll
     for (int i = 0; i < 32; ++i) {
       pre += d1[i];
-      const unsigned key = __float_as_uint(d0[i] + pre);   // D >= 0: float order = bit order
+      const unsigned key = __float_as_uint((d0[i] + mid) + pre);   // D >= 0: float order = bit order
       const unsigned mn = __reduce_min_sync(FULL, key);
       const int bs = __ffs(__ballot_sync(FULL, key == mn)) - 1;
       mybs = lane == i ? bs : mybs;
-      if (NEED_S2) {   // d of the symbol itself (position 32 q + i + 16) at angle bs
-        const float own = i < 16 ? d0[i + 16] - (i + 16 < 31 ? d0[i + 17] : 0.f) : d1[i - 16];
+      if (NEED_S2) {   // d of the symbol itself (position 32 q + i + 16 M) at angle bs
+        float own;
+        if (M == 1) own = i < 16 ? d0[i + 16] - (i + 16 < 31 ? d0[i + 17] : 0.f) : d1[i - 16];
+        else own = dd(yb, i + 16 * M, base + i + 16 * M);
         const float add = __shfl_sync(FULL, own, bs);
         s2 += i < cnt ? add : 0.f;
       }
@@ -211,33 +237,44 @@ __device__ __forceinline__ void pass1_blocks(const float2 *ys, int v_lo, int v_h
     R += __reduce_add_sync(FULL, r);
     prev = __shfl_sync(FULL, mybs, cnt - 1);
     if (lane < cnt) bq[base + lane] = (int8_t)mybs;
+    if constexpr (M == 1) {
 #pragma unroll
-    for (int j = 0; j < 32; ++j) d0[j] = d1[j];
+      for (int j = 0; j < 32; ++j) d0[j] = d1[j];
+    } else {
+      // the next window drops block q + 1 from the middle and takes block q + M
+      float t = 0.f;
+#pragma unroll
+      for (int j = 0; j < 32; ++j) t += d1[j];
+#pragma unroll
+      for (int r = 0; r < M - 2; ++r) T[r] = T[r + 1];
+      T[M - 2] = t;
+    }
   }
   if (MB == 4) s2 *= 0.1f;
 }
 
-template <int MB, bool NEED_S2>
+template <int MB, bool NEED_S2, int M>
 __global__ void __launch_bounds__(kBpsWarps * 32) bps_pass1_blk(BpsLaunch L) {
   extern __shared__ float4 smem_raw[];
+  constexpr int Nb = kBlkNb * M;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t j = (int64_t)blockIdx.x * kBpsWarps + warp;
   const int p = blockIdx.y;
   if (j >= L.n_chunks) return;
-  char *base = reinterpret_cast<char *>(smem_raw) + (size_t)warp * pass1_blk_warp_bytes(L.chunk);
+  char *base = reinterpret_cast<char *>(smem_raw) + (size_t)warp * pass1_blk_warp_bytes(L.chunk, Nb);
   float2 *ys = reinterpret_cast<float2 *>(base);
-  int8_t *bq = reinterpret_cast<int8_t *>(ys + pass1_blk_ys_cap(L.chunk));
+  int8_t *bq = reinterpret_cast<int8_t *>(ys + pass1_blk_ys_cap(L.chunk, Nb));
   const int64_t a = chunk_lo(L, j), b = min(a + (int64_t)L.chunk, L.k_hi);
-  const int64_t lo = a - kBlkNb;                 // ys[m] holds symbol lo + m
+  const int64_t lo = a - Nb;                     // ys[m] holds symbol lo + m
   const int nt = (int)(b - a);
-  const int n_ys = nt + 2 * kBlkNb;
+  const int n_ys = nt + 2 * Nb;
   float sb, cb;
   sincospif(((float)lane / 32.f - 0.5f) * 0.5f, &sb, &cb);
   // this lane's test angle exp(-j phi_b), scaled by sqrt10 for 16QAM
   const float g = MB == 4 ? 3.16227766016837933f : 1.f;
   const float2 rot = make_float2(cb * g, -sb * g);
   const float2 *y = L.y + (int64_t)p * L.y_stride - L.y_base;
-  const int cap = pass1_blk_ys_cap(L.chunk);
+  const int cap = pass1_blk_ys_cap(L.chunk, Nb);
   for (int i = lane; i < cap; i += 32) {        // coalesced staging; zero past the window
     const int64_t k = lo + i;
     ys[i] = (i < n_ys && k >= 0 && k < L.K_end) ? y[k] : make_float2(0.f, 0.f);
@@ -247,10 +284,10 @@ __global__ void __launch_bounds__(kBpsWarps * 32) bps_pass1_blk(BpsLaunch L) {
   int R = 0;
   float s2 = 0.f;
   if (v_lo > 0 || v_hi < n_ys) {                  // the window touches a stream end
-    pass1_blocks<MB, NEED_S2, true>(ys, (int)max(v_lo, (int64_t)0), (int)min(v_hi, (int64_t)n_ys), rot, nt, lane,
-                                    bq, R, s2);
+    pass1_blocks<MB, NEED_S2, true, M>(ys, (int)max(v_lo, (int64_t)0), (int)min(v_hi, (int64_t)n_ys), rot, nt, lane,
+                                       bq, R, s2);
   } else {
-    pass1_blocks<MB, NEED_S2, false>(ys, 0, n_ys, rot, nt, lane, bq, R, s2);
+    pass1_blocks<MB, NEED_S2, false, M>(ys, 0, n_ys, rot, nt, lane, bq, R, s2);
   }
   __syncwarp();
   int8_t *bh = L.bhat + (int64_t)p * L.bh_stride - L.bh_base;
@@ -261,7 +298,6 @@ __global__ void __launch_bounds__(kBpsWarps * 32) bps_pass1_blk(BpsLaunch L) {
   }
 }
 
-// One CTA per pol: exclusive prefix of chunk unwrap sums (+carry) and region sigma^2.
 __global__ void __launch_bounds__(1024) bps_scan(BpsLaunch L) {
   __shared__ int64_t part[1024];
   const int p = blockIdx.x, t = threadIdx.x;
@@ -413,18 +449,30 @@ __global__ void __launch_bounds__(kBpsWarps * 32) bps_demap(BpsLaunch L) {
 cudaError_t launch_bps(const BpsLaunch &L, cudaStream_t s) {
   if (L.n_chunks <= 0) return cudaSuccess;
   dim3 grid((unsigned)((L.n_chunks + kBpsWarps - 1) / kBpsWarps), 2);
-  const bool blk = L.Nb == kBlkNb;
-  const size_t sm = (size_t)kBpsWarps * (blk ? pass1_blk_warp_bytes(L.chunk) : pass1_warp_bytes(L.chunk, L.Nb));
+  // half windows of whole 16-symbol multiples up to 64 take the register-block pass
+  const int M = (L.Nb >= kBlkNb && L.Nb <= 4 * kBlkNb && L.Nb % kBlkNb == 0) ? L.Nb / kBlkNb : 0;
+  const size_t sm = (size_t)kBpsWarps * (M ? pass1_blk_warp_bytes(L.chunk, L.Nb) : pass1_warp_bytes(L.chunk, L.Nb));
   cudaError_t e;
 #define RX_PASS1(KERNEL, MB, NS)                                                                       \
   e = cudaFuncSetAttribute(KERNEL<MB, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);        \
   if (e != cudaSuccess) return e;                                                                      \
   KERNEL<MB, NS><<<grid, kBpsWarps * 32, sm, s>>>(L);
-  if (blk) {
+#define RX_BLK(MB, NS, MM)                                                                             \
+  e = cudaFuncSetAttribute(bps_pass1_blk<MB, NS, MM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm); \
+  if (e != cudaSuccess) return e;                                                                      \
+  bps_pass1_blk<MB, NS, MM><<<grid, kBpsWarps * 32, sm, s>>>(L);
+#define RX_BLK_M(MB, NS)                                                                               \
+  switch (M) {                                                                                         \
+    case 1: RX_BLK(MB, NS, 1) break;                                                                   \
+    case 2: RX_BLK(MB, NS, 2) break;                                                                   \
+    case 3: RX_BLK(MB, NS, 3) break;                                                                   \
+    default: RX_BLK(MB, NS, 4) break;                                                                  \
+  }
+  if (M) {
     if (L.mod_bits == 4) {
-      if (L.need_s2) { RX_PASS1(bps_pass1_blk, 4, true) } else { RX_PASS1(bps_pass1_blk, 4, false) }
+      if (L.need_s2) { RX_BLK_M(4, true) } else { RX_BLK_M(4, false) }
     } else {
-      if (L.need_s2) { RX_PASS1(bps_pass1_blk, 2, true) } else { RX_PASS1(bps_pass1_blk, 2, false) }
+      if (L.need_s2) { RX_BLK_M(2, true) } else { RX_BLK_M(2, false) }
     }
   } else {
     if (L.mod_bits == 4) {
@@ -434,6 +482,8 @@ cudaError_t launch_bps(const BpsLaunch &L, cudaStream_t s) {
     }
   }
 #undef RX_PASS1
+#undef RX_BLK
+#undef RX_BLK_M
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   bps_scan<<<2, 1024, 0, s>>>(L);

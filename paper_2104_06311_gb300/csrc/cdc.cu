@@ -325,7 +325,7 @@ __device__ __forceinline__ int raw_bytes(int dtype) { return dtype == RX_I8x4 ? 
 // FMT selects the storage of the shared-memory transform and of u (RX_FMT_*);
 // reduced formats scale the window by 1/sqrt(N) on ingest and H by sqrt(N)
 // (`hscale`) so that every intermediate stays near unit magnitude (FP16 range).
-template <int N, int VPT, bool SPLIT, int FMT, bool PREFETCH>
+template <int N, int VPT, bool SPLIT, int FMT, bool PREFETCH, bool TCREQ>
 __global__ void __launch_bounds__((SPLIT ? 1 : 2) * N / VPT, ((SPLIT ? 1 : 2) * N / VPT >= 512 ? 1 : 512 / ((SPLIT ? 1 : 2) * N / VPT))) cdc_kernel(
     int V, const uint8_t *__restrict__ tail, int64_t tail_first, int64_t tail_n,
     const uint8_t *__restrict__ call, int64_t call_first, int64_t call_n, int dtype, float scale,
@@ -396,7 +396,7 @@ __global__ void __launch_bounds__((SPLIT ? 1 : 2) * N / VPT, ((SPLIT ? 1 : 2) * 
     return pol ? make_float2(f.z * scale, f.w * scale) : make_float2(f.x * scale, f.y * scale);
   };
   // tensor-core passes in the reduced formats, where a warp owns whole groups of butterflies
-  constexpr bool TC = FMT != RX_FMT_F32 && TPP >= 32;
+  constexpr bool TC = TCREQ && FMT != RX_FMT_F32 && TPP >= 32;
   DftA A;
   if constexpr (TC) dft16_init<S>(A);
   float2 *scr_base = reinterpret_cast<float2 *>(stage + (PREFETCH ? (size_t)N * esz : 0));
@@ -580,8 +580,8 @@ __global__ void __launch_bounds__((SPLIT ? 1 : 2) * N / VPT, ((SPLIT ? 1 : 2) * 
   if (PREFETCH) asm volatile("cp.async.wait_all;\n" ::: "memory");
 }
 
-template <int N, int VPT, bool SPLIT, int FMT>
-static cudaError_t launch_cdc_n(int V, const void *tail, int64_t tail_first, int64_t tail_n,
+template <int N, int VPT, bool SPLIT, int FMT, bool TCREQ>
+static cudaError_t launch_cdc_k(int V, const void *tail, int64_t tail_first, int64_t tail_n,
                                 const void *call, int64_t call_first, int64_t call_n, int dtype,
                                 float scale, const float2 *H, const float2 *tw, void *u,
                                 int64_t u_base, int64_t u_stride, int64_t win_first,
@@ -592,10 +592,10 @@ static cudaError_t launch_cdc_n(int V, const void *tail, int64_t tail_first, int
   const size_t sm_stage = (size_t)N * (dtype == RX_I8x4 ? 4 : 16);
   const bool prefetch = sm_fft + sm_stage <= 200 * 1024;
   // per-warp transpose scratch of the tensor-core fused middle (reduced formats)
-  const size_t sm_scr = (FMT != RX_FMT_F32 && N / VPT >= 32) ? (size_t)(BS / 32) * 8 * 17 * sizeof(float2) : 0;
+  const size_t sm_scr = (TCREQ && FMT != RX_FMT_F32 && N / VPT >= 32) ? (size_t)(BS / 32) * 8 * 17 * sizeof(float2) : 0;
   const size_t sm = sm_fft + (prefetch ? sm_stage : 0) + sm_scr + (FMT != RX_FMT_F32 ? 32 * sizeof(float) : 0);
-  const void *fn = prefetch ? (const void *)cdc_kernel<N, VPT, SPLIT, FMT, true>
-                            : (const void *)cdc_kernel<N, VPT, SPLIT, FMT, false>;
+  const void *fn = prefetch ? (const void *)cdc_kernel<N, VPT, SPLIT, FMT, true, TCREQ>
+                            : (const void *)cdc_kernel<N, VPT, SPLIT, FMT, false, TCREQ>;
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
   int dev = 0, sms = 0, per = 0;
@@ -610,14 +610,27 @@ static cudaError_t launch_cdc_n(int V, const void *tail, int64_t tail_first, int
   const float in_scale = scale;   // reduced formats normalise each window by its own max-abs
   const uint8_t *tl = (const uint8_t *)tail, *cl = (const uint8_t *)call;
   if (prefetch)
-    cdc_kernel<N, VPT, SPLIT, FMT, true><<<grid, BS, sm, s>>>(V, tl, tail_first, tail_n, cl, call_first, call_n, dtype,
-                                                              in_scale, rs, H, tw, u, u_base, u_stride, win_first,
-                                                              win_count, n_total);
+    cdc_kernel<N, VPT, SPLIT, FMT, true, TCREQ><<<grid, BS, sm, s>>>(V, tl, tail_first, tail_n, cl, call_first, call_n,
+                                                                     dtype, in_scale, rs, H, tw, u, u_base, u_stride,
+                                                                     win_first, win_count, n_total);
   else
-    cdc_kernel<N, VPT, SPLIT, FMT, false><<<grid, BS, sm, s>>>(V, tl, tail_first, tail_n, cl, call_first, call_n, dtype,
-                                                               in_scale, rs, H, tw, u, u_base, u_stride, win_first,
-                                                               win_count, n_total);
+    cdc_kernel<N, VPT, SPLIT, FMT, false, TCREQ><<<grid, BS, sm, s>>>(V, tl, tail_first, tail_n, cl, call_first, call_n,
+                                                                      dtype, in_scale, rs, H, tw, u, u_base, u_stride,
+                                                                      win_first, win_count, n_total);
   return cudaGetLastError();
+}
+
+template <int N, int VPT, bool SPLIT, int FMT>
+static cudaError_t launch_cdc_n(int V, const void *tail, int64_t tail_first, int64_t tail_n,
+                                const void *call, int64_t call_first, int64_t call_n, int dtype,
+                                float scale, const float2 *H, const float2 *tw, void *u,
+                                int64_t u_base, int64_t u_stride, int64_t win_first,
+                                int64_t win_count, int64_t n_total, int sm_budget, bool tc, cudaStream_t s) {
+  if (FMT != RX_FMT_F32 && tc)
+    return launch_cdc_k<N, VPT, SPLIT, FMT, true>(V, tail, tail_first, tail_n, call, call_first, call_n, dtype, scale, H,
+                                                  tw, u, u_base, u_stride, win_first, win_count, n_total, sm_budget, s);
+  return launch_cdc_k<N, VPT, SPLIT, FMT, false>(V, tail, tail_first, tail_n, call, call_first, call_n, dtype, scale, H,
+                                                 tw, u, u_base, u_stride, win_first, win_count, n_total, sm_budget, s);
 }
 
 template <int FMT>
@@ -625,12 +638,12 @@ static cudaError_t launch_cdc_fmt(int N, int V, const void *tail, int64_t tail_f
                                   const void *call, int64_t call_first, int64_t call_n, int dtype,
                                   float scale, const float2 *H, const float2 *tw, void *u,
                                   int64_t u_base, int64_t u_stride, int64_t win_first, int64_t win_count,
-                                  int64_t n_total, int sm_budget, cudaStream_t s) {
+                                  int64_t n_total, int sm_budget, bool tc, cudaStream_t s) {
 #define RX_CDC_CASE(NN, VPT, SPLIT)                                                                \
   case NN:                                                                                         \
     return launch_cdc_n<NN, VPT, SPLIT, FMT>(V, tail, tail_first, tail_n, call, call_first, call_n, \
                                              dtype, scale, H, tw, u, u_base, u_stride, win_first,  \
-                                             win_count, n_total, sm_budget, s);
+                                             win_count, n_total, sm_budget, tc, s);
   switch (N) {
     RX_CDC_CASE(256, 16, false)
     RX_CDC_CASE(512, 16, false)
@@ -648,18 +661,19 @@ cudaError_t launch_cdc(int N, int V, const void *tail, int64_t tail_first, int64
                        const void *call, int64_t call_first, int64_t call_n, int dtype,
                        float scale, const float2 *H, const float2 *tw, void *u,
                        int64_t u_base, int64_t u_stride, int64_t win_first, int64_t win_count,
-                       int64_t n_total, cudaStream_t s, int fmt, int sm_budget) {
+                       int64_t n_total, cudaStream_t s, int fmt, int sm_budget, int tc) {
+  // tc: the reduced formats' radix-16 passes on the tensor pipe (else register butterflies)
   if (win_count <= 0) return cudaSuccess;
   switch (fmt) {
     case RX_FMT_F32:
       return launch_cdc_fmt<RX_FMT_F32>(N, V, tail, tail_first, tail_n, call, call_first, call_n, dtype, scale, H, tw,
-                                        u, u_base, u_stride, win_first, win_count, n_total, sm_budget, s);
+                                        u, u_base, u_stride, win_first, win_count, n_total, sm_budget, tc != 0, s);
     case RX_FMT_F16:
       return launch_cdc_fmt<RX_FMT_F16>(N, V, tail, tail_first, tail_n, call, call_first, call_n, dtype, scale, H, tw,
-                                        u, u_base, u_stride, win_first, win_count, n_total, sm_budget, s);
+                                        u, u_base, u_stride, win_first, win_count, n_total, sm_budget, tc != 0, s);
     case RX_FMT_BF16:
       return launch_cdc_fmt<RX_FMT_BF16>(N, V, tail, tail_first, tail_n, call, call_first, call_n, dtype, scale, H,
-                                         tw, u, u_base, u_stride, win_first, win_count, n_total, sm_budget, s);
+                                         tw, u, u_base, u_stride, win_first, win_count, n_total, sm_budget, tc != 0, s);
     default: return cudaErrorInvalidValue;
   }
 }

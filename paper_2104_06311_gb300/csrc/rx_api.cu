@@ -51,6 +51,7 @@ struct rx_stream {
   int64_t inner_cap = 0;            // RX_P_INNER_TRACE: entries per butterfly row (0 = off)
   double wait_limit_us = 2e6;       // RX_P_WAIT_LIMIT_US: limit of every bounded device wait
   int64_t no_arrive = -1;           // RX_P_TEST_NO_ARRIVE: CTA left out of the wave barriers (-1: none)
+  int dft_tc = 0;                   // RX_P_DFT_TC: reduced formats' radix-16 passes on the tensor pipe
   // ---- resolved
   int N = 0, V = 0, Sh = 0, P = 0, C = 256;
   int64_t A_full = 0, span = 0;
@@ -409,6 +410,7 @@ rx_status rx_set_param(rx_stream *rx, int key, double v) {
       rx->wait_limit_us = v;
       return RX_OK;
     case RX_P_TEST_NO_ARRIVE: return as_int(-1, 1 << 20, &rx->no_arrive);
+    case RX_P_DFT_TC: s = as_int(0, 1, &t); if (s == RX_OK) rx->dft_tc = (int)t; return s;
     default: return fail(rx, RX_EINVAL, "unknown parameter key");
   }
   if (s != RX_OK) return s;
@@ -451,6 +453,7 @@ rx_status rx_get_param(rx_stream *rx, int key, double *v) {
     case RX_P_INNER_TRACE: *v = (double)rx->inner_cap; break;
     case RX_P_WAIT_LIMIT_US: *v = rx->wait_limit_us; break;
     case RX_P_TEST_NO_ARRIVE: *v = (double)rx->no_arrive; break;
+    case RX_P_DFT_TC: *v = rx->dft_tc; break;
     default: return fail(rx, RX_EINVAL, "unknown parameter key");
   }
   return RX_OK;
@@ -705,7 +708,7 @@ rx_status rx_process(rx_stream *rx, const rx_in *in, rx_out *out) {
       RX_CUDA(launch_cdc(rx->N, rx->V, rx->tail[rx->cur_tail], rx->tail_first, rx->tail_n, in->data, call_first,
                          call_n, rx->dtype, (float)rx->in_scale, rx->H, rx->tw, rx->u[rx->cur_u], rx->u_base,
                          rx->u_cap, w_done, w_need - w_done, rx->n_total, rx->sub[0], rx->fmt,
-                         rx->pieces > 1 ? std::max(16, rx->sms - rx->eq_blocks) : 0),
+                         rx->pieces > 1 ? std::max(16, rx->sms - rx->eq_blocks) : 0, rx->dft_tc),
               "cdc");
       w_done = w_need;
     }

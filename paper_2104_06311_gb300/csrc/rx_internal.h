@@ -118,7 +118,7 @@ cudaError_t launch_cdc(int N, int V, const void *tail, int64_t tail_first, int64
                        const void *call, int64_t call_first, int64_t call_n, int dtype,
                        float scale, const float2 *H, const float2 *tw, void *u,
                        int64_t u_base, int64_t u_stride, int64_t win_first, int64_t win_count,
-                       int64_t n_total, cudaStream_t s, int fmt = RX_FMT_F32, int sm_budget = 0);
+                       int64_t n_total, cudaStream_t s, int fmt = RX_FMT_F32, int sm_budget = 0, int tc = 0);
 cudaError_t launch_eq(const EqLaunch &L, cudaStream_t s);
 // Batched equaliser: one cooperative launch of nblocks CTAs; d_team[b] =
 // (stream, CTA within that stream's team).  pad_smem: unused dynamic shared

@@ -211,11 +211,12 @@ def test_streaming_calls_equal_one_call():
         assert np.array_equal(many["llr"], one["llr"]), chunk
 
 
-@pytest.mark.parametrize("Nb", [0, 7, 24])
+@pytest.mark.parametrize("Nb", [0, 7, 24, 32, 64])
 def test_bps_other_half_windows(Nb):
-    """Half windows other than 16 take the sliding-ring BPS pass (16 takes the register
-    blocks); with phase noise the unwrap count moves, so the scan's boundary step of
-    every chunk is exercised, in one call and across calls."""
+    """Half windows 0, 7 and 24 take the sliding-ring BPS pass; whole multiples of 16
+    (16, 32, 64) take the register blocks (for 32 and 64 with block totals between
+    the two edge blocks); with phase noise the unwrap count moves, so the scan's
+    boundary step of every chunk is exercised, in one call and across calls."""
     lk = L.Link(n_sym=(1 << 15) + 321, L_km=500.0, snr_db=13.0, linewidth_hz=1e6, seed=2300 + Nb)
     g = L.generate(lk)
     p = rx_params(lk, g.in_scale, bps_halfwin=Nb)

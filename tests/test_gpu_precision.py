@@ -28,9 +28,9 @@ def _built():
     ensure_built()
 
 
-def _run(p, g, fmt):
+def _run(p, g, fmt, tc=0):
     import torch
-    rx = make_receiver(p, LLR_OUT=1, SYM_OUT=1, EQ_OUT=1, CDC_OUT=1, PRECISION=fmt)
+    rx = make_receiver(p, LLR_OUT=1, SYM_OUT=1, EQ_OUT=1, CDC_OUT=1, PRECISION=fmt, DFT_TC=tc)
     assert rx.get_param("PRECISION") == fmt
     x = torch.from_numpy(np.ascontiguousarray(g.samples)).cuda()
     out = rx.run_stream(x, llr=True, sym=True, eq=True, cdc=True)
@@ -51,14 +51,17 @@ def _evm_db(z, mod, k0):
     return 10 * math.log10(np.mean(np.abs(z[:, k0:] - d) ** 2) / np.mean(np.abs(d) ** 2))
 
 
-def test_precision_forms_against_oracle_and_fp32():
+@pytest.mark.parametrize("tc", [0, 1])
+def test_precision_forms_against_oracle_and_fp32(tc):
+    """tc = 0: FP32 register butterflies on FP16/BF16 storage; tc = 1: the radix-16
+    passes as FP16/BF16 tensor-core products with FP32 accumulation."""
     lk = L.workload("c3", n_sym=1 << 16)
     g = L.generate(lk)
     p = rx_params(lk, g.in_scale)
     assert p.fft_n == 16384
     K = lk.n_sym
     k0 = p.acq_len(K) + 8192
-    runs = {fmt: _run(p, g, fmt) for fmt in (0, 1, 2)}
+    runs = {fmt: _run(p, g, fmt, tc) for fmt in (0, 1, 2)}
     orc = O.run_chain(g.samples, p)     # the oracle on its own decisions throughout
     rows = []
     for fmt, r in runs.items():
@@ -75,7 +78,7 @@ def test_precision_forms_against_oracle_and_fp32():
         # the reduced formats' trackers integrate their own (FP16/BF16-input) estimates, so
         # their equaliser outputs are compared through EVM, not element by element
         eq_txt = f"equaliser rel RMS {e_y:.2e}, " if fmt == 0 else ""
-        print(f"{name}: CDC rel RMS {e_u:.2e}, {eq_txt}EVM {evm:.3f} dB "
+        print(f"{name} (tc {tc}): CDC rel RMS {e_u:.2e}, {eq_txt}EVM {evm:.3f} dB "
               f"(oracle {evm_o:.3f} dB), penalty vs FP32 {evm - evm32:+.4f} dB, BER {ber:.3e}")
         assert evm - evm32 < 0.1
     # BER of every form within 3 sigma (Poisson) of the FP32 count
@@ -102,7 +105,8 @@ def test_precision_streaming_and_state_roundtrip():
 
 @pytest.mark.parametrize("N", [256, 1024, 4096, 16384])
 @pytest.mark.parametrize("fmt", [1, 2])
-def test_precision_cdc_every_transform_size(N, fmt):
+@pytest.mark.parametrize("tc", [0, 1])
+def test_precision_cdc_every_transform_size(N, fmt, tc):
     """The reduced-format CDC (tensor-core radix-16 passes from N = 512 on, per-window
     max-abs scaling) against the FP64 overlap-save oracle at every kind of plan:
     N = 256 (register passes), 1024 (radix-4 middle), 4096 (tensor-core fused middle),
@@ -113,12 +117,12 @@ def test_precision_cdc_every_transform_size(N, fmt):
     g = L.generate(lk)
     samples = np.ascontiguousarray(g.samples * 3000.0)       # far beyond FP16's comfort without scaling
     p = rx_params(lk, g.in_scale, fft_n=N, overlap=64)
-    rx = make_receiver(p, CDC_OUT=1, PRECISION=fmt)
+    rx = make_receiver(p, CDC_OUT=1, PRECISION=fmt, DFT_TC=tc)
     out = rx.run_stream(torch.from_numpy(samples).cuda(), cdc=True)
     torch.cuda.synchronize()
     u = out["cdc"][:, :out["cdc_n"]].cpu().numpy().astype(np.complex128)
     ref = O.cdc_overlap_save(L.deinterleave(samples), O.cdc_filter(p), p.overlap)
     err = rel_rms(u[:, :ref.shape[1]], ref)
-    print(f"N {N} fmt {fmt}: CDC rel RMS {err:.2e}")
+    print(f"N {N} fmt {fmt} tc {tc}: CDC rel RMS {err:.2e}")
     assert np.all(np.isfinite(u))
     assert err < U_TOL[fmt], err
