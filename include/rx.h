@@ -106,11 +106,16 @@ enum {
                               index leaves out its arrival at the wave barriers, so
                               that the other CTAs' waits run out after
                               RX_P_WAIT_LIMIT_US (-1 = off, the default)             */
-  RX_P_DFT_TC = 28         /* precision form (RX_P_PRECISION 1 or 2): 1 = the CDC's
+  RX_P_DFT_TC = 28,        /* precision form (RX_P_PRECISION 1 or 2): 1 = the CDC's
                               radix-16 DFT passes as FP16/BF16 tensor-core products
                               with FP32 accumulation, 0 = FP32 register butterflies
                               on FP16/BF16 storage (default: measured faster, the
                               transform being bound by shared-memory traffic)      */
+  RX_P_EQ_WARPS = 29       /* warps per butterfly-row CTA of the equaliser, 4 or 8
+                              (default 4; 8 measured 12 % slower on GB300): the 32
+                              symbols of an update block split over that many warps;
+                              results equal to within FP32 rounding (the sums run in
+                              another order)                                         */
 };
 
 /* Stages reported by rx_profile. */

@@ -452,10 +452,12 @@ def equalize(u: np.ndarray, p: RxParams, trace: dict | None = None, ties: dict |
         symbols before it (DD, outputs discarded), then equalises its own
         symbols.  Its input is rotated by exp(-j 2 pi (phi_w + (n - n_w) d_w)
         / 2^G), n_w = 2 (A + w P S).
-      * Frequency tracking per wave (one-wave lag): r_w is a quarter of the
-        argument of fo_estimate_sum over adjacent pairs inside each segment;
-        d_{w+1} = d_w + fo_units(r_w / fo_smooth); phi_0 = (2A - 2 N_CMA') d_0,
-        phi_{w+1} = phi_w + 2PS d_w, all mod 2^G.
+      * Frequency tracking per wave, applied two waves on: r_w is a quarter
+        of the argument of fo_estimate_sum over adjacent pairs inside each
+        segment of wave w; i_w = fo_units(r_w / fo_smooth); d_1 = d_0 and
+        d_{w+1} = d_w + i_{w-1}; phi_0 = (2A - 2 N_CMA') d_0,
+        phi_{w+1} = phi_w + 2PS d_w, all mod 2^G.  (Wave w+1's rotation is
+        then fixed before wave w ends: only its start taps wait for wave w.)
 
     The tracker's state (phi, d) is integer (fo_units): the phase it
     integrates over the stream is exact, so implementations that round the
@@ -527,6 +529,7 @@ def equalize(u: np.ndarray, p: RxParams, trace: dict | None = None, ties: dict |
     S, W, P = p.seg_len, p.seg_pretrain, p.wave_segments()
     G = (K - A + S - 1) // S
     h_start = h
+    inc_prev = 0          # i_{w-1}: the previous wave's increment, applied after this wave
     for w0 in range(0, G, P):
         gs = range(w0, min(w0 + P, G))
         n_w = 2 * (A + w0 * S)
@@ -560,12 +563,14 @@ def equalize(u: np.ndarray, p: RxParams, trace: dict | None = None, ties: dict |
         if p.fo_track:
             edges.append(edge)
             wi = w0 // P
-            if dev_waves is not None and wi + 1 < len(dev_waves):
-                inc = _track_tie(inc, edge, dev_waves[wi + 1][1] - dev_waves[wi][1], "wave", wi, tie_log)
+            # the other implementation applies i_w from wave w+2 on
+            if dev_waves is not None and wi + 2 < len(dev_waves):
+                inc = _track_tie(inc, edge, dev_waves[wi + 2][1] - dev_waves[wi + 1][1], "wave", wi, tie_log)
         if trace is not None:
             trace["wave_r"].append(r)
         phi = (phi + (2 * P * S) * d) % M
-        d = d + inc
+        d = d + inc_prev
+        inc_prev = inc
         h_start = h_last
     return y
 

@@ -155,10 +155,10 @@ __global__ void batch_init_kernel(const EqLaunch *__restrict__ Ls) {
     L.st->Phi = 0.0;
     L.st->Phi_q = 0ull;
     L.st->delta_q = 0ll;
+    L.st->pend_q = 0ll;
     L.st->next_wave = 0;
     L.st->acq_done = 0;
-    L.barrier[0] = 0u;
-    L.barrier[1] = 0u;
+    for (int k = 0; k < kEqBarrierWords; ++k) L.barrier[k] = 0u;
   }
 }
 
@@ -178,7 +178,7 @@ struct rx_batch {
   int eq_ctas = 0, pad_smem = 0;
   EqLaunch *d_L = nullptr, *h_L = nullptr;   // h_L: pinned host copy source
   int2 *d_team = nullptr;
-  unsigned *barriers = nullptr;              // [n_ch][2]
+  unsigned *barriers = nullptr;              // [n_ch][kEqBarrierWords]
   int64_t *m_carry = nullptr;                // [n_ch][2]
   int *err = nullptr, *h_err = nullptr;
   cudaEvent_t err_ev = nullptr;
@@ -589,7 +589,7 @@ rx_status rx_batch_create(rx_batch **out, int n_ch, const rx_chan_cfg *cfgs) {
   } while (0)
   BX_ALLOC(b->d_L, (size_t)n_ch);
   BX_ALLOC(b->d_team, team.size());
-  BX_ALLOC(b->barriers, (size_t)2 * n_ch);
+  BX_ALLOC(b->barriers, (size_t)kEqBarrierWords * n_ch);
   BX_ALLOC(b->m_carry, (size_t)2 * n_ch);
   BX_ALLOC(b->err, 1);
   BX_ALLOC(b->ber_counts, 2 * 2 * 4 * 129);
@@ -615,8 +615,8 @@ rx_status rx_batch_create(rx_batch **out, int n_ch, const rx_chan_cfg *cfgs) {
     BX_ALLOC(c.chunk_m, (size_t)2 * c.chunk_cap);
     BX_ALLOC(c.region_s2, (size_t)2 * c.region_cap);
     BX_ALLOC(c.st, 1);
-    BX_ALLOC(c.fo_part, (size_t)4 * c.P);
-    BX_ALLOC(c.tap_slot, (size_t)2 * 4 * kMaxTaps);
+    BX_ALLOC(c.fo_part, (size_t)kWaveSlots * 2 * c.P);
+    BX_ALLOC(c.tap_slot, (size_t)kWaveSlots * 4 * kMaxTaps);
     BX_ALLOC(c.trace, (size_t)c.trace_cap * 4 * kMaxTaps * 2);
     BX_ALLOC(c.trace_fo, (size_t)c.trace_cap * 2);
     BX_CUDA(launch_tables(c.H, c.tw, c.N, c.cfg.baud, c.cfg.L_km, c.cfg.D_ps_nm_km, kLamNm, kRolloff, b->stream),
@@ -761,7 +761,7 @@ rx_status rx_batch_process(rx_batch *b, const rx_in *ins, rx_out *outs) {
       L.trace = c.trace;
       L.trace_fo = c.trace_fo;
       L.trace_cap = c.trace_cap;
-      L.barrier = b->barriers + 2 * i;
+      L.barrier = b->barriers + kEqBarrierWords * i;
       L.err = b->err;
       L.K = K;
       L.run_acq = A > 0;

@@ -61,20 +61,36 @@ namespace rx {
 
 namespace {
 
-constexpr int kWarps = kEqThreads / 32;  // 4
 constexpr int kWinMax = 2 * kChunkSym + 2 * 8;
 constexpr int kWinRow = kWinMax + 1;     // odd row length: pol rows land 8 bytes apart in the banks
 constexpr unsigned FULL = 0xffffffffu;
 
+// Work split of one butterfly row over NW warps (NW = 4 or 8): warp w owns the
+// SPW symbols SPW w .. SPW w + SPW - 1 of an update block; the PPS lanes of a
+// symbol each hold TPL taps of one input pol (part = (q, sub): taps
+// TPL sub .. TPL sub + TPL - 1 of h_q) and ANG of the 32 inner-BPS angles.
+template <int NW> struct Geo {
+  static constexpr int NT = NW * 32;       // threads per CTA
+  static constexpr int SPW = 32 / NW;      // symbols per warp
+  static constexpr int PPS = NW;           // lanes per symbol
+  static constexpr int SUB = PPS / 2;      // tap groups per input pol
+  static constexpr int TPL = kMaxTaps / SUB;   // taps per lane (= SPW)
+  static constexpr int ANG = 32 / PPS;     // inner-BPS angles per lane (= SPW)
+  static constexpr int LPPS = NW == 4 ? 2 : 3;   // log2 PPS
+  static_assert(TPL == SPW && ANG == SPW, "square reduce-scatter");
+};
+
+template <int NW>
 struct EqSmem {
   float2 win[2][kWinRow];
   float2 ybuf[2][32];                    // double-buffered by step parity
-  float bps[kWarps][32];
-  float2 grad[2][kWarps][2][kMaxTaps];   // double-buffered by step parity
-  float4 fo_warp[kWarps];                // per-warp double-float pair sums
+  float bps[NW][32];
+  float2 grad[2][NW][2][kMaxTaps];       // double-buffered by step parity
+  float4 fo_warp[NW];                    // per-warp double-float pair sums
   float2 rtab[256];                      // exp(-j 2 pi m / 256)
   unsigned long long phq;                // tracker: phase base, Q0.64 turns
   long long dq;                          // tracker: per-sample increment, Q0.64 turns
+  long long pend;                        // increment of the wave before the launch's first
   int fail;
 };
 
@@ -115,7 +131,8 @@ __device__ __forceinline__ long long grid_to_q64(long long units) {
 // the error word) once limit_ns of device time pass without every CTA arriving,
 // or when another CTA already failed.  arrive = false leaves this CTA's arrival
 // out (a host-requested test of the timeout path: the others' waits run out).
-__device__ bool cta_barrier(int *err, unsigned *ctr, unsigned count, unsigned &epoch, EqSmem &sm,
+template <class SM>
+__device__ bool cta_barrier(int *err, unsigned *ctr, unsigned count, unsigned &epoch, SM &sm,
                             unsigned long long limit_ns, bool arrive = true) {
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -144,6 +161,31 @@ __device__ bool cta_barrier(int *err, unsigned *ctr, unsigned count, unsigned &e
   return sm.fail == 0;
 }
 
+// Bounded wait until *ctr >= target: false (and the error word set) once
+// limit_ns of device time pass, or when another CTA already failed.  Every
+// thread of the CTA returns the same verdict; thread 0's acquire and fence make
+// what the arrivals published visible to the whole CTA after the barrier.
+template <class SM>
+__device__ bool cta_wait(int *err, const unsigned *ctr, unsigned target, SM &sm, unsigned long long limit_ns) {
+  if (threadIdx.x == 0) {
+    sm.fail = 0;
+    const unsigned long long t0 = globaltimer_ns();
+    unsigned polls = 0;
+    while (ld_acquire_u32(ctr) < target) {
+      if (*(volatile int *)err != 0) { sm.fail = 1; break; }
+      if (globaltimer_ns() - t0 > limit_ns) {
+        atomicOr(err, DEV_ERR_TIMEOUT);
+        sm.fail = 1;
+        break;
+      }
+      if (++polls > 4096) __nanosleep(256);
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return sm.fail == 0;
+}
+
 // Rotation parameters for a span: phase(n) = Phi_q + (n - n0) * delta_q (Q0.64 turns).
 struct Rot {
   int on;
@@ -158,17 +200,18 @@ __device__ __forceinline__ unsigned smem_u32(const void *p) {
 }
 
 // Raw samples [win_lo, win_lo + count) of both rows copied into the window
-// asynchronously: element j by thread j mod kEqThreads, the thread that converts
+// asynchronously: element j by thread j mod NT (the CTA's threads), the thread that converts
 // it in window_finish, so that its own wait makes the copy visible to it (a
 // 16-bit sample lands in the low half of its float2 slot); samples outside
 // [0, n_limit) are left for window_finish to zero.  Issued early (before a grid barrier), the
 // copies land while the CTA waits.
+template <int NT, class SM>
 __device__ __forceinline__ void window_issue(const unsigned char *__restrict__ u0, const unsigned char *__restrict__ u1,
-                                             int fmt, EqSmem &sm, int64_t win_lo, int count, int64_t n_limit) {
+                                             int fmt, SM &sm, int64_t win_lo, int count, int64_t n_limit) {
   const int lo = (int)max((int64_t)0, min((int64_t)count, -win_lo));
   const int hi = (int)max((int64_t)0, min((int64_t)count, n_limit - win_lo));
   if (fmt == RX_FMT_F32) {
-    for (int j = threadIdx.x; j < hi; j += kEqThreads) {
+    for (int j = threadIdx.x; j < hi; j += NT) {
       if (j < lo) continue;
       const int64_t n = win_lo + j;
       asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(smem_u32(&sm.win[0][j])), "l"(u0 + n * 8)
@@ -177,7 +220,7 @@ __device__ __forceinline__ void window_issue(const unsigned char *__restrict__ u
                    : "memory");
     }
   } else {
-    for (int j = threadIdx.x; j < hi; j += kEqThreads) {
+    for (int j = threadIdx.x; j < hi; j += NT) {
       if (j < lo) continue;
       const int64_t n = win_lo + j;
       asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(smem_u32(&sm.win[0][j])), "l"(u0 + n * 4)
@@ -199,25 +242,59 @@ __device__ __forceinline__ float2 raw_sample(const float2 *slot, int fmt) {
   return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&w));
 }
 
+// Complex products with the fused-multiply-add placement fixed (the first product
+// fused, the second rounded), so that every kernel this file's bodies are
+// compiled into rounds them alike whatever the compiler would contract.
+__device__ __forceinline__ float2 cmul_f(float2 a, float2 b) {
+  return make_float2(__fmaf_rn(a.x, b.x, -__fmul_rn(a.y, b.y)), __fmaf_rn(a.x, b.y, __fmul_rn(a.y, b.x)));
+}
+__device__ __forceinline__ float2 cmulc_f(float2 a, float2 b) {  // a conj(b)
+  return make_float2(__fmaf_rn(a.x, b.x, __fmul_rn(a.y, b.y)), __fmaf_rn(a.y, b.x, -__fmul_rn(a.x, b.y)));
+}
+
+// Complex products rounded term by term (never contracted into FMAs).
+__device__ __forceinline__ float2 cmul_rn(float2 a, float2 b) {
+  return make_float2(__fsub_rn(__fmul_rn(a.x, b.x), __fmul_rn(a.y, b.y)),
+                     __fadd_rn(__fmul_rn(a.x, b.y), __fmul_rn(a.y, b.x)));
+}
+__device__ __forceinline__ float2 cmulc_rn(float2 a, float2 b) {  // a conj(b)
+  return make_float2(__fadd_rn(__fmul_rn(a.x, b.x), __fmul_rn(a.y, b.y)),
+                     __fsub_rn(__fmul_rn(a.y, b.x), __fmul_rn(a.x, b.y)));
+}
+
+// exp(-j 2 pi t) of a Q0.64 turn t: the top 8 bits from the table, the rest
+// (theta < 2 pi / 256) by its Taylor series.
+template <class SM>
+__device__ __forceinline__ float2 q64_phasor(const SM &sm, unsigned long long t) {
+  const unsigned ph = (unsigned)(t >> 32);
+  const float th = (float)(ph & 0xFFFFFFu) * 1.4629180792671596e-09f;  // 2 pi / 2^32
+  const float t2 = th * th;
+  const float cs = fmaf(t2, fmaf(t2, 1.f / 24.f, -0.5f), 1.f);
+  const float sn = th * fmaf(t2, fmaf(t2, 1.f / 120.f, -1.f / 6.f), 1.f);
+  return cmul_f(sm.rtab[ph >> 24], make_float2(cs, -sn));
+}
+
 // Waits for this thread's copies, then converts its samples in place, removing
 // the tracker's phase: window = exp(-j phi_n) u(n), zero outside [0, n_limit).
-__device__ __forceinline__ void window_finish(int fmt, EqSmem &sm, int64_t win_lo, int count, const Rot &rot,
+template <int NT, class SM>
+__device__ __forceinline__ void window_finish(int fmt, SM &sm, int64_t win_lo, int count, const Rot &rot,
                                               int64_t n_limit) {
   window_wait();
   // groups of kG samples per thread: all raw reads of a group first, then its
   // independent rotation chains (one warp per scheduler: ILP hides the latency)
-  constexpr int kPer = (kWinMax + kEqThreads - 1) / kEqThreads;
+  constexpr int kPer = (kWinMax + NT - 1) / NT;
   constexpr int kG = 5;
-  // turn of the thread's first sample; each further one is kEqThreads samples on
+  // turn of the thread's first sample; each further one is NT samples on
   // (exact: modular 64-bit arithmetic)
   const unsigned long long ph0 = rot.Phi_q + (unsigned long long)(win_lo + threadIdx.x - rot.n0) * rot.delta_q;
-  const unsigned long long dph = (unsigned long long)kEqThreads * rot.delta_q;
+  const unsigned long long dph = (unsigned long long)NT * rot.delta_q;
+  const float2 wstep = q64_phasor(sm, dph);
 #pragma unroll 1
   for (int r0 = 0; r0 < kPer; r0 += kG) {
     float2 a[kG], b[kG];
 #pragma unroll
     for (int g = 0; g < kG; ++g) {
-      const int j = threadIdx.x + (r0 + g) * kEqThreads;
+      const int j = threadIdx.x + (r0 + g) * NT;
       const int64_t n = win_lo + j;
       a[g] = b[g] = make_float2(0.f, 0.f);
       if (j < count && n >= 0 && n < n_limit) {
@@ -225,22 +302,20 @@ __device__ __forceinline__ void window_finish(int fmt, EqSmem &sm, int64_t win_l
         b[g] = raw_sample(&sm.win[1][j], fmt);
       }
     }
+    float2 r2 = make_float2(1.f, 0.f);
 #pragma unroll
     for (int g = 0; g < kG; ++g) {
-      const int j = threadIdx.x + (r0 + g) * kEqThreads;
+      const int j = threadIdx.x + (r0 + g) * NT;
       if (j < count) {
         if (rot.on) {
-          // exp(-j phi): top 8 bits of the turn from the table, the rest
-          // (theta < 2 pi / 256) by its Taylor series (error < 1e-12); faster
-          // here than a second table read
-          const unsigned ph = (unsigned)((ph0 + (unsigned long long)(r0 + g) * dph) >> 32);
-          const float th = (float)(ph & 0xFFFFFFu) * 1.4629180792671596e-09f;  // 2 pi / 2^32
-          const float t2 = th * th;
-          const float cs = fmaf(t2, fmaf(t2, 1.f / 24.f, -0.5f), 1.f);
-          const float sn = th * fmaf(t2, fmaf(t2, 1.f / 120.f, -1.f / 6.f), 1.f);
-          const float2 r2 = cmul(sm.rtab[ph >> 24], make_float2(cs, -sn));
-          a[g] = cmul(a[g], r2);
-          b[g] = cmul(b[g], r2);
+          // exp(-j phi) of the group's first sample: top 8 bits of the turn from the
+          // table, the rest (theta < 2 pi / 256) by its Taylor series (error < 1e-12);
+          // each further sample of the group (NT samples on) by one product with the
+          // step phasor (error a few ulps after four products)
+          if (g == 0) r2 = q64_phasor(sm, ph0 + (unsigned long long)r0 * dph);
+          else r2 = cmul_rn(r2, wstep);   // rounded term by term: the same in every kernel
+          a[g] = cmul_f(a[g], r2);
+          b[g] = cmul_f(b[g], r2);
         }
         sm.win[0][j] = a[g];
         sm.win[1][j] = b[g];
@@ -271,9 +346,9 @@ struct Span {
 // Per-thread constant roles.
 struct Lane {
   int warp, lane;
-  int j, part, q, half;   // symbol j of the warp; (q, half) = (part >> 1, part & 1)
-  int tap;                // tap this lane owns in the update: 8 half + j
-  float2 rot[8];          // exp(-j phi_b) for b = 8 part + a, a = 0..7
+  int j, part, q, sub;    // symbol j of the warp; (q, sub) = (part / SUB, part % SUB)
+  int tap;                // tap this lane owns in the update: TPL sub + j
+  float2 rot[8];          // exp(-j phi_b) for b = ANG part + a, a < ANG
   float2 rot_b;           // exp(-j phi_b) for b = lane (argmin source)
 };
 
@@ -298,23 +373,16 @@ __device__ __forceinline__ void kahan_add(float &s, float &c, float v) {
   s = t;
 }
 
-// The 8 taps a FIR lane needs, gathered from the lanes owning them.
+// The TPL taps a FIR lane needs, gathered from the lanes owning them (tap
+// TPL sub + ii of pol q is owned by lane PPS ii + part).
+template <int NW>
 __device__ __forceinline__ void gather_taps(float2 (&h)[8], float2 own, const Lane &ln) {
+  typedef Geo<NW> G;
 #pragma unroll
-  for (int ii = 0; ii < 8; ++ii) {
-    h[ii].x = __shfl_sync(FULL, own.x, 4 * ii + ln.part);
-    h[ii].y = __shfl_sync(FULL, own.y, 4 * ii + ln.part);
+  for (int ii = 0; ii < G::TPL; ++ii) {
+    h[ii].x = __shfl_sync(FULL, own.x, G::PPS * ii + ln.part);
+    h[ii].y = __shfl_sync(FULL, own.y, G::PPS * ii + ln.part);
   }
-}
-
-// Complex products rounded term by term (never contracted into FMAs).
-__device__ __forceinline__ float2 cmul_rn(float2 a, float2 b) {
-  return make_float2(__fsub_rn(__fmul_rn(a.x, b.x), __fmul_rn(a.y, b.y)),
-                     __fadd_rn(__fmul_rn(a.x, b.y), __fmul_rn(a.y, b.x)));
-}
-__device__ __forceinline__ float2 cmulc_rn(float2 a, float2 b) {  // a conj(b)
-  return make_float2(__fadd_rn(__fmul_rn(a.x, b.x), __fmul_rn(a.y, b.y)),
-                     __fsub_rn(__fmul_rn(a.y, b.x), __fmul_rn(a.x, b.y)));
 }
 
 // Weight of a 16QAM symbol of power a = |y|^2 in the frequency estimate: 0 on the
@@ -324,20 +392,43 @@ __device__ __forceinline__ float ring_weight(float a) {
   return fminf(fmaxf(__fmul_rn(__fsub_rn(fabsf(__fsub_rn(a, 1.f)), 0.2f), 5.f), 0.f), 1.f);
 }
 
-template <int MB>
-__device__ __forceinline__ void run_span(const Hot hot, EqSmem &sm, const Span sp, const Lane &ln,
+// Reduce-scatter of SPW values over the warp's SPW symbols (lanes PPS apart): on
+// return v[0] holds the sum over the warp's symbols of value index j (this lane's
+// symbol index).  Recursive halving, highest symbol bit first.
+template <int NW, class V, class ADD>
+__device__ __forceinline__ V reduce_scatter(V (&v)[8], int j, ADD add) {
+  typedef Geo<NW> G;
+#pragma unroll
+  for (int half = G::SPW / 2; half >= 1; half >>= 1) {
+    const bool hi = j & half;
+#pragma unroll
+    for (int a = 0; a < half; ++a) {
+      const V send = hi ? v[a] : v[a + half];
+      const V keep = hi ? v[a + half] : v[a];
+      v[a] = add(keep, send, G::PPS * half);
+    }
+  }
+  return v[0];
+}
+
+template <int MB, int NW>
+__device__ __forceinline__ void run_span(const Hot hot, EqSmem<NW> &sm, const Span sp, const Lane &ln,
                                          float2 &own, float2 (&h)[8], Kahan &fo, int64_t n_limit,
                                          bool pre = false) {
+  typedef Geo<NW> G;
   const int T = hot.T, c = hot.c, Bu = hot.Bu;
   const int chunk = (kChunkSym / Bu) * Bu;
   const float mu = sp.cma ? hot.mu_cma : hot.mu_dd;
-  const int kl = ln.warp * 8 + ln.j;     // this lane's symbol within a block
-  const bool hi4 = ln.j & 4, hi2 = ln.j & 2, hi1 = ln.j & 1;
+  const int kl = ln.warp * G::SPW + ln.j;   // this lane's symbol within a block
   int step = 0;
   // the previous step's frequency pair: (on, y_k, in-warp neighbour, previous block's last, parity)
   bool d_on = false;
   float2 d_yv = make_float2(0.f, 0.f), d_yup = make_float2(0.f, 0.f), d_ylast = make_float2(0.f, 0.f);
   int d_par = 0;
+  auto addf = [](float keep, float send, int o) { return keep + __shfl_xor_sync(FULL, send, o); };
+  auto addf2 = [](float2 keep, float2 send, int o) {
+    return make_float2(keep.x + __shfl_xor_sync(FULL, send.x, o), keep.y + __shfl_xor_sync(FULL, send.y, o));
+  };
   // branch-free, explicitly rounded products: no FMA contraction, so that every kernel
   // this body is compiled into forms the same estimate
   auto fo_deferred = [&]() {
@@ -363,17 +454,18 @@ __device__ __forceinline__ void run_span(const Hot hot, EqSmem &sm, const Span s
     const int nsteps = (int)((ce - cs + Bu - 1) / Bu);
     __syncthreads();  // every warp is done with the previous chunk's window
     // (pre: the first chunk's copies were issued before the caller's grid barrier)
-    if (!(pre && cs == sp.kp)) window_issue(hot.u0, hot.u1, hot.u_fmt, sm, win_lo, count, n_limit);
-    window_finish(hot.u_fmt, sm, win_lo, count, sp.rot, n_limit);
+    if (!(pre && cs == sp.kp)) window_issue<G::NT>(hot.u0, hot.u1, hot.u_fmt, sm, win_lo, count, n_limit);
+    window_finish<G::NT>(hot.u_fmt, sm, win_lo, count, sp.rot, n_limit);
     __syncthreads();
-    // this lane's 8 window samples u_q[2k+c-i] of a step (zero for inactive symbols or
+    // this lane's TPL window samples u_q[2k+c-i] of a step (zero for inactive symbols or
     // taps i >= T); the next step's are read while the current step's update runs
     auto window_samples = [&](int tt, float2 (&xs)[8]) {
       const int64_t kb = cs + (int64_t)tt * Bu;
       const bool a_ = kl < (int)min((int64_t)Bu, ce - kb);
-      const float2 *xw = sm.win[ln.q] + (2 * tt * Bu + 2 * c) + 2 * kl - ln.half * 8;
+      const float2 *xw = sm.win[ln.q] + (2 * tt * Bu + 2 * c) + 2 * kl - ln.sub * G::TPL;
 #pragma unroll
-      for (int ii = 0; ii < 8; ++ii) xs[ii] = (a_ && ln.half * 8 + ii < T) ? xw[-ii] : make_float2(0.f, 0.f);
+      for (int ii = 0; ii < G::TPL; ++ii)
+        xs[ii] = (a_ && ln.sub * G::TPL + ii < T) ? xw[-ii] : make_float2(0.f, 0.f);
     };
     float2 xn[8];
     window_samples(0, xn);
@@ -390,9 +482,9 @@ __device__ __forceinline__ void run_span(const Hot hot, EqSmem &sm, const Span s
       float ax0 = 0.f, ay0 = 0.f, ax1 = 0.f, ay1 = 0.f;
       {
 #pragma unroll
-        for (int ii = 0; ii < 8; ++ii) x[ii] = xn[ii];
+        for (int ii = 0; ii < G::TPL; ++ii) x[ii] = xn[ii];
 #pragma unroll
-        for (int ii = 0; ii < 8; ii += 2) {
+        for (int ii = 0; ii < G::TPL; ii += 2) {
           ax0 = fmaf(h[ii].x, x[ii].x, fmaf(-h[ii].y, x[ii].y, ax0));
           ay0 = fmaf(h[ii].x, x[ii].y, fmaf(h[ii].y, x[ii].x, ay0));
           ax1 = fmaf(h[ii + 1].x, x[ii + 1].x, fmaf(-h[ii + 1].y, x[ii + 1].y, ax1));
@@ -400,10 +492,11 @@ __device__ __forceinline__ void run_span(const Hot hot, EqSmem &sm, const Span s
         }
       }
       float2 yv = make_float2(ax0 + ax1, ay0 + ay1);
-      yv.x += __shfl_xor_sync(FULL, yv.x, 1);
-      yv.y += __shfl_xor_sync(FULL, yv.y, 1);
-      yv.x += __shfl_xor_sync(FULL, yv.x, 2);
-      yv.y += __shfl_xor_sync(FULL, yv.y, 2);
+#pragma unroll
+      for (int o = 1; o < G::PPS; o <<= 1) {
+        yv.x += __shfl_xor_sync(FULL, yv.x, o);
+        yv.y += __shfl_xor_sync(FULL, yv.y, o);
+      }
       if (ln.part == 0) {
         sm.ybuf[par][kl] = act ? yv : make_float2(0.f, 0.f);
         if (out && act) hot.yrow[k0 + kl] = yv;
@@ -412,7 +505,7 @@ __device__ __forceinline__ void run_span(const Hot hot, EqSmem &sm, const Span s
       // next step's inner BPS (off the update chain): the previous symbol is the in-warp
       // neighbour, else the previous warp's last one (in ybuf[par], intact until two
       // steps later), or for the first warp the last symbol of the previous block
-      const float yupx = __shfl_up_sync(FULL, yv.x, 4), yupy = __shfl_up_sync(FULL, yv.y, 4);
+      const float yupx = __shfl_up_sync(FULL, yv.x, G::PPS), yupy = __shfl_up_sync(FULL, yv.y, G::PPS);
       const int64_t kk = k0 + kl;
       const bool fo_on = out && act && ln.part == 0 && kk - 1 >= sp.fo_lo && kk < sp.fo_hi;
       // ---- B: error
@@ -420,8 +513,8 @@ __device__ __forceinline__ void run_span(const Hot hot, EqSmem &sm, const Span s
       if (!sp.cma) {
         float d[8];
 #pragma unroll
-        for (int a = 0; a < 8; ++a) {
-          const float2 w = cmul(yv, ln.rot[a]);
+        for (int a = 0; a < G::ANG; ++a) {
+          const float2 w = cmul_f(yv, ln.rot[a]);
           // QPSK: |w - dec w|^2 = |y|^2 + 1 - sqrt2 (|Re w| + |Im w|), and |y|^2 is the same
           // for every angle, so -(|Re w| + |Im w|) orders the angles alike
           // 16QAM on the grid scaled by sqrt10: (||x| - 2| - 1)^2 per dimension is
@@ -431,27 +524,21 @@ __device__ __forceinline__ void run_span(const Hot hot, EqSmem &sm, const Span s
             dq = -(fabsf(w.x) + fabsf(w.y));
           } else {
             const float ex = fabsf(fabsf(w.x) - 2.f) - 1.f, ey = fabsf(fabsf(w.y) - 2.f) - 1.f;
-            dq = ex * ex + ey * ey;
+            dq = __fmaf_rn(ex, ex, __fmul_rn(ey, ey));
           }
           d[a] = act ? dq : 0.f;
         }
         fo_deferred();   // the previous step's pair, in the shadow of the reduce-scatter
-        float e1[4], e2[2];
-#pragma unroll
-        for (int a = 0; a < 4; ++a) {
-          const float send = hi4 ? d[a] : d[a + 4];
-          e1[a] = (hi4 ? d[a + 4] : d[a]) + __shfl_xor_sync(FULL, send, 16);
-        }
-#pragma unroll
-        for (int a = 0; a < 2; ++a) {
-          const float send = hi2 ? e1[a] : e1[a + 2];
-          e2[a] = (hi2 ? e1[a + 2] : e1[a]) + __shfl_xor_sync(FULL, send, 8);
-        }
-        const float send = hi1 ? e2[0] : e2[1];
-        const float dsum = (hi1 ? e2[1] : e2[0]) + __shfl_xor_sync(FULL, send, 4);
-        sm.bps[ln.warp][ln.part * 8 + ln.j] = dsum;
+        const float dsum = reduce_scatter<NW>(d, ln.j, addf);
+        sm.bps[ln.warp][ln.part * G::ANG + ln.j] = dsum;
         __syncthreads();  // (1)
-        const float D = (sm.bps[0][ln.lane] + sm.bps[1][ln.lane]) + (sm.bps[2][ln.lane] + sm.bps[3][ln.lane]);
+        float D;
+        if (NW == 4) {
+          D = (sm.bps[0][ln.lane] + sm.bps[1][ln.lane]) + (sm.bps[2][ln.lane] + sm.bps[3][ln.lane]);
+        } else {
+          D = ((sm.bps[0][ln.lane] + sm.bps[1][ln.lane]) + (sm.bps[2][ln.lane] + sm.bps[3][ln.lane])) +
+              ((sm.bps[4 % NW][ln.lane] + sm.bps[5 % NW][ln.lane]) + (sm.bps[6 % NW][ln.lane] + sm.bps[7 % NW][ln.lane]));
+        }
         // order-preserving key of a float (the QPSK cost is negative)
         const unsigned u = __float_as_uint(D);
         const unsigned key = (u & 0x80000000u) ? ~u : (u | 0x80000000u);
@@ -464,48 +551,40 @@ __device__ __forceinline__ void run_span(const Hot hot, EqSmem &sm, const Span s
       float2 er = make_float2(0.f, 0.f);
       if (act) {
         if (sp.cma) {
-          er = cscale(yv, yv.x * yv.x + yv.y * yv.y - hot.cma_r2);
+          er = cscale(yv, __fmaf_rn(yv.x, yv.x, __fmaf_rn(yv.y, yv.y, -hot.cma_r2)));
         } else {
-          const float2 dd = qam_decide<MB>(cmulc(yv, eth));
-          er = csub(yv, cmul(dd, eth));
+          const float2 dd = qam_decide<MB>(cmulc_f(yv, eth));
+          er = csub(yv, cmul_f(dd, eth));
         }
       }
-      // ---- C: gradient e conj(u) of this lane's 8 taps, reduce-scatter over the warp's symbols
+      // ---- C: gradient e conj(u) of this lane's TPL taps, reduce-scatter over the warp's symbols
       {
         float2 g[8];
 #pragma unroll
-        for (int ii = 0; ii < 8; ++ii) g[ii] = cmulc(er, x[ii]);
-        float2 g1[4], g2[2];
-#pragma unroll
-        for (int a = 0; a < 4; ++a) {
-          const float2 s2 = hi4 ? g[a] : g[a + 4];
-          const float2 k2 = hi4 ? g[a + 4] : g[a];
-          g1[a] = make_float2(k2.x + __shfl_xor_sync(FULL, s2.x, 16), k2.y + __shfl_xor_sync(FULL, s2.y, 16));
-        }
-#pragma unroll
-        for (int a = 0; a < 2; ++a) {
-          const float2 s2 = hi2 ? g1[a] : g1[a + 2];
-          const float2 k2 = hi2 ? g1[a + 2] : g1[a];
-          g2[a] = make_float2(k2.x + __shfl_xor_sync(FULL, s2.x, 8), k2.y + __shfl_xor_sync(FULL, s2.y, 8));
-        }
-        const float2 s2 = hi1 ? g2[0] : g2[1];
-        const float2 k2 = hi1 ? g2[1] : g2[0];
-        sm.grad[par][ln.warp][ln.q][ln.tap] =
-            make_float2(k2.x + __shfl_xor_sync(FULL, s2.x, 4), k2.y + __shfl_xor_sync(FULL, s2.y, 4));
+        for (int ii = 0; ii < G::TPL; ++ii) g[ii] = cmulc_f(er, x[ii]);
+        sm.grad[par][ln.warp][ln.q][ln.tap] = reduce_scatter<NW>(g, ln.j, addf2);
       }
       __syncthreads();  // (2)
-      // ---- tap update: this lane's own tap, then every FIR lane gathers its 8.  The
+      // ---- tap update: this lane's own tap, then every FIR lane gathers its TPL.  The
       // partial-gradient reads go first; the next step's window reads and the frequency
       // pair (the neighbours' outputs are in ybuf since barrier 1) fill their latency.
       const int tp = ln.tap < T ? ln.tap : 0;
-      const float2 g0 = sm.grad[par][0][ln.q][tp], g1 = sm.grad[par][1][ln.q][tp];
-      const float2 g2 = sm.grad[par][2][ln.q][tp], g3 = sm.grad[par][3][ln.q][tp];
+      float2 gs[NW];
+#pragma unroll
+      for (int w = 0; w < NW; ++w) gs[w] = sm.grad[par][w][ln.q][tp];
       if (t + 1 < nsteps) window_samples(t + 1, xn);
       if (ln.tap < T) {
-        own.x -= mu * ((g0.x + g1.x) + (g2.x + g3.x));
-        own.y -= mu * ((g0.y + g1.y) + (g2.y + g3.y));
+        float2 tot;
+        if (NW == 4) {
+          tot = make_float2((gs[0].x + gs[1].x) + (gs[2].x + gs[3].x), (gs[0].y + gs[1].y) + (gs[2].y + gs[3].y));
+        } else {
+          tot = make_float2(((gs[0].x + gs[1].x) + (gs[2].x + gs[3].x)) + ((gs[4 % NW].x + gs[5 % NW].x) + (gs[6 % NW].x + gs[7 % NW].x)),
+                            ((gs[0].y + gs[1].y) + (gs[2].y + gs[3].y)) + ((gs[4 % NW].y + gs[5 % NW].y) + (gs[6 % NW].y + gs[7 % NW].y)));
+        }
+        own.x = __fmaf_rn(-mu, tot.x, own.x);
+        own.y = __fmaf_rn(-mu, tot.y, own.y);
       }
-      gather_taps(h, own, ln);
+      gather_taps<NW>(h, own, ln);
       d_on = fo_on;
       d_yv = yv;
       d_yup = make_float2(yupx, yupy);
@@ -518,21 +597,26 @@ __device__ __forceinline__ void run_span(const Hot hot, EqSmem &sm, const Span s
 
 // Segment total of the per-lane compensated pair sums as double-float
 // (x_hi, x_lo, y_hi, y_lo), in a fixed order.
-__device__ __forceinline__ float4 reduce_fo(EqSmem &sm, const Kahan &fo, const Lane &ln) {
+template <int NW>
+__device__ __forceinline__ float4 reduce_fo(EqSmem<NW> &sm, const Kahan &fo, const Lane &ln) {
   // Kahan (s, c) holds s - c; renormalise into (hi, lo)
   const float hx = fo.sx - fo.cx, hy = fo.sy - fo.cy;
   float4 acc = make_float4(hx, (fo.sx - hx) - fo.cx, hy, (fo.sy - hy) - fo.cy);
-  for (int o = 16; o >= 4; o >>= 1) acc = df4_add(acc, shfl_xor_f4(acc, o));
+  for (int o = 16; o >= Geo<NW>::PPS; o >>= 1) acc = df4_add(acc, shfl_xor_f4(acc, o));
   __syncthreads();
   if (ln.lane == 0) sm.fo_warp[ln.warp] = acc;
   __syncthreads();
-  return df4_add(df4_add(sm.fo_warp[0], sm.fo_warp[1]), df4_add(sm.fo_warp[2], sm.fo_warp[3]));
+  const float4 a = df4_add(df4_add(sm.fo_warp[0], sm.fo_warp[1]), df4_add(sm.fo_warp[2], sm.fo_warp[3]));
+  if (NW == 4) return a;
+  return df4_add(a, df4_add(df4_add(sm.fo_warp[4 % NW], sm.fo_warp[5 % NW]),
+                            df4_add(sm.fo_warp[6 % NW], sm.fo_warp[7 % NW])));
 }
 
 // This lane's own tap of row p from a [2][2][kMaxTaps] array, then the FIR gather.
+template <int NW>
 __device__ __forceinline__ void load_row(float2 &own, float2 (&h)[8], const float2 *src, int p, const Lane &ln) {
   own = __ldcg(&src[(p * 2 + ln.q) * kMaxTaps + ln.tap]);
-  gather_taps(h, own, ln);
+  gather_taps<NW>(h, own, ln);
 }
 
 // Row p's taps (warp 0's 32 lanes own all of them) to dst and, optionally, a trace entry.
@@ -562,21 +646,22 @@ __device__ __forceinline__ void trace_fo(const EqLaunch &L, int64_t idx, double 
 
 // One CTA's part of an equaliser launch: CTA `cta` of the L.nblocks CTAs that
 // serve this stream (a whole grid, or a team inside a batched grid).
-template <int MB>
-__device__ __forceinline__ void eq_body(const EqLaunch &L, const int cta, EqSmem &sm) {
+template <int MB, int NW>
+__device__ __forceinline__ void eq_body(const EqLaunch &L, const int cta, EqSmem<NW> &sm) {
+  typedef Geo<NW> G;
   Lane ln;
   ln.warp = threadIdx.x >> 5;
   ln.lane = threadIdx.x & 31;
-  ln.j = ln.lane >> 2;
-  ln.part = ln.lane & 3;
-  ln.q = ln.part >> 1;
-  ln.half = ln.part & 1;
-  ln.tap = ln.half * 8 + ln.j;
+  ln.j = ln.lane >> G::LPPS;
+  ln.part = ln.lane & (G::PPS - 1);
+  ln.q = ln.part / G::SUB;
+  ln.sub = ln.part % G::SUB;
+  ln.tap = ln.sub * G::TPL + ln.j;
 #pragma unroll
-  for (int a = 0; a < 8; ++a) {
-    // phi_b = (b/32 - 1/2) pi/2 for b = 8 part + a
+  for (int a = 0; a < G::ANG; ++a) {
+    // phi_b = (b/32 - 1/2) pi/2 for b = ANG part + a
     float sb, cb;
-    sincospif(((float)(ln.part * 8 + a) / 32.f - 0.5f) * 0.5f, &sb, &cb);
+    sincospif(((float)(ln.part * G::ANG + a) / 32.f - 0.5f) * 0.5f, &sb, &cb);
     // 16QAM: scaled by sqrt10, so that the distance below needs no level table
     const float g = MB == 4 ? 3.16227766016837933f : 1.f;
     ln.rot[a] = make_float2(cb * g, -sb * g);
@@ -611,7 +696,7 @@ __device__ __forceinline__ void eq_body(const EqLaunch &L, const int cta, EqSmem
   if (threadIdx.x == 0) {
     sm.ybuf[0][31] = sm.ybuf[1][31] = make_float2(0.f, 0.f);
   }
-  for (int m = threadIdx.x; m < 256; m += kEqThreads) {
+  for (int m = threadIdx.x; m < 256; m += G::NT) {
     float s, c;
     sincospif((float)m / 128.f, &s, &c);
     sm.rtab[m] = make_float2(c, -s);
@@ -620,7 +705,7 @@ __device__ __forceinline__ void eq_body(const EqLaunch &L, const int cta, EqSmem
 
   if (L.run_acq) {
     if (cta < 2) {
-      load_row(own, h, &L.st->taps[0][0][0], p, ln);
+      load_row<NW>(own, h, &L.st->taps[0][0][0], p, ln);
       Span sp;
       sp.kp = 0; sp.ks = 0; sp.ke = L.n_cma;
       sp.fo_lo = L.n_cma / 2; sp.fo_hi = L.n_cma;
@@ -628,7 +713,7 @@ __device__ __forceinline__ void eq_body(const EqLaunch &L, const int cta, EqSmem
       sp.rot.on = 0; sp.rot.Phi_q = 0; sp.rot.delta_q = 0; sp.rot.n0 = 0;
       sp.itr = nullptr; sp.itr_n = 0;
       fo = Kahan{0.f, 0.f, 0.f, 0.f};
-      run_span<MB>(hot, sm, sp, ln, own, h, fo, n_limit);
+      run_span<MB, NW>(hot, sm, sp, ln, own, h, fo, n_limit);
       const float4 s = reduce_fo(sm, fo, ln);
       if (threadIdx.x == 0) __stcg(&L.fo_part[p], s);
       if (!cta_barrier(L.err, L.barrier + 1, 2u, epoch2, sm, L.spin_ns)) return;
@@ -647,7 +732,7 @@ __device__ __forceinline__ void eq_body(const EqLaunch &L, const int cta, EqSmem
         sd.rot.Phi_q = 0; sd.rot.delta_q = (unsigned long long)dq; sd.rot.n0 = 2 * L.n_cma;
         sd.itr = L.inner ? L.inner + p * L.inner_cap : nullptr;
         sd.itr_n = (int)min(L.inner_acq, L.inner_cap);
-        run_span<MB>(hot, sm, sd, ln, own, h, fo, n_limit);
+        run_span<MB, NW>(hot, sm, sd, ln, own, h, fo, n_limit);
       }
       // end of acquisition = trace entries 0 (acquisition) and 1 (start of wave 0)
       store_row(own, &L.st->taps[0][0][0], trace_slot(L, 0), p, ln);
@@ -666,6 +751,7 @@ __device__ __forceinline__ void eq_body(const EqLaunch &L, const int cta, EqSmem
         L.st->Phi = Phi;
         L.st->delta_q = dq;
         L.st->Phi_q = phq;
+        L.st->pend_q = 0;
         L.st->acq_done = 1;
         L.st->next_wave = 0;
         trace_fo(L, 0, dw, Phi);
@@ -679,6 +765,7 @@ __device__ __forceinline__ void eq_body(const EqLaunch &L, const int cta, EqSmem
   if (threadIdx.x == 0) {
     sm.phq = __ldcg(&L.st->Phi_q);
     sm.dq = __ldcg(&L.st->delta_q);
+    sm.pend = __ldcg(&L.st->pend_q);
   }
   __syncthreads();
   // segment g: outputs [ks, ke), trained from kp
@@ -701,10 +788,35 @@ __device__ __forceinline__ void eq_body(const EqLaunch &L, const int cta, EqSmem
     }
     return sp;
   };
+  // Increment i_v of wave v from the FO partials of its segments (warp 0, a fixed
+  // tree: identical in every CTA): r = 1/4 arg(sum), r / fo_smooth rounded to the
+  // tracker grid, in Q0.64 turns per sample.
+  auto wave_increment = [&](int64_t v) -> long long {
+    const float4 *src = L.fo_part + ((v - L.wave_first) & (kWaveSlots - 1)) * 2 * L.P;
+    const int64_t vg0 = v * L.P;
+    const int n = (int)(2 * (min(vg0 + (int64_t)L.P, L.n_segments) - vg0));
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int jj = ln.lane; jj < n; jj += 32) acc = df4_add(acc, __ldcg(&src[jj]));
+    for (int o = 16; o >= 1; o >>= 1) acc = df4_add(acc, shfl_xor_f4(acc, o));
+    const float r = L.fo_track ? 0.25f * atan2f(acc.z + acc.w, acc.x + acc.y) : 0.f;
+    return grid_to_q64(__double2ll_rn((double)r * L.inc_scale));
+  };
+  // Arrival counters, exact per wave: a CTA arrives on ctr_part[k mod kWaveSlots] once its
+  // FO partials of the launch's wave k are written (so the counter of a slot reaches
+  // nblocks (k / kWaveSlots + 1) exactly when every CTA has published wave k: none can
+  // publish wave k + kWaveSlots before that), and the CTA that ran the last segment of
+  // wave k arrives on ctr_taps[p] once row p's end taps are written (one producer per
+  // row and wave, in wave order).
+  unsigned *const ctr_part = L.barrier + 2;
+  unsigned *const ctr_taps = L.barrier + 2 + kWaveSlots;
+  auto part_target = [&](unsigned k) { return ((k / kWaveSlots) + 1u) * (unsigned)L.nblocks; };
   const int chunk = (kChunkSym / hot.Bu) * hot.Bu;
-  bool pre = false;   // the next segment's first window is in flight
+  bool pre = false;        // the next segment's first window is in flight
+  bool have_taps = false;  // own / h hold row p's end taps of the previous wave
   for (int64_t w = L.wave_first; w < L.wave_last; ++w) {
-    const float2 *start = (w == L.wave_first) ? &L.st->taps[0][0][0] : L.tap_slot + ((w - 1) & 1) * 4 * kMaxTaps;
+    const unsigned i = (unsigned)(w - L.wave_first);   // wave index within the launch
+    const float2 *start = (w == L.wave_first) ? &L.st->taps[0][0][0]
+                                              : L.tap_slot + ((i - 1u) & (kWaveSlots - 1)) * 4 * kMaxTaps;
     const int64_t g0 = w * L.P;
     const int64_t g_end = min(g0 + (int64_t)L.P, L.n_segments);
     Rot rot;
@@ -712,17 +824,33 @@ __device__ __forceinline__ void eq_body(const EqLaunch &L, const int cta, EqSmem
     rot.Phi_q = sm.phq;
     rot.delta_q = (unsigned long long)sm.dq;
     rot.n0 = 2 * (L.A + g0 * L.S);
+    // the start taps of this wave are in registers (this CTA ran the previous wave's
+    // last segment: its own row), or at the launch's start in the state, or wait for
+    // the previous wave's last-segment rows
+    bool ready = (w == L.wave_first) || have_taps;
+    bool producer = false;
     for (int64_t g = g0 + slot; g < g_end; g += nslots) {
-      load_row(own, h, start, p, ln);
+      if (have_taps) {
+        have_taps = false;
+      } else {
+        if (!ready) {
+          if (!cta_wait(L.err, ctr_taps + p, i, sm, L.spin_ns)) {
+            window_wait();   // no copy left in flight
+            return;
+          }
+          ready = true;
+        }
+        load_row<NW>(own, h, start, p, ln);
+      }
       Span sp = seg_span(g);
       sp.rot = rot;
       fo = Kahan{0.f, 0.f, 0.f, 0.f};
-      run_span<MB>(hot, sm, sp, ln, own, h, fo, n_limit, pre);
+      run_span<MB, NW>(hot, sm, sp, ln, own, h, fo, n_limit, pre);
       pre = false;
       const float4 s = reduce_fo(sm, fo, ln);   // every warp is done with the window
       // this CTA's next segment (later in this wave, else in the next): its first
       // window's raw samples do not depend on the tracker, so their copies are
-      // issued now and land during the grid barrier and the fold
+      // issued now and land during the waits and the fold
       int64_t gn = g + nslots;
       if (gn >= g_end) {
         gn = (w + 1) * L.P + slot;
@@ -733,53 +861,69 @@ __device__ __forceinline__ void eq_body(const EqLaunch &L, const int cta, EqSmem
         int64_t lo;
         int cnt;
         chunk_window(sn.kp, sn.ke, hot.c, chunk, lo, cnt);
-        window_issue(hot.u0, hot.u1, hot.u_fmt, sm, lo, cnt, n_limit);
+        window_issue<G::NT>(hot.u0, hot.u1, hot.u_fmt, sm, lo, cnt, n_limit);
         pre = true;
       }
-      if (threadIdx.x == 0) __stcg(L.fo_part + (w & 1) * 2 * L.P + (g - g0) * 2 + p, s);
+      if (threadIdx.x == 0) __stcg(L.fo_part + (i & (kWaveSlots - 1)) * 2 * L.P + (g - g0) * 2 + p, s);
       // the last segment's end taps start wave w + 1 (trace entry w + 2)
-      if (g == g_end - 1) store_row(own, L.tap_slot + (w & 1) * 4 * kMaxTaps, trace_slot(L, w + 2), p, ln);
+      if (g == g_end - 1) {
+        store_row(own, L.tap_slot + (i & (kWaveSlots - 1)) * 4 * kMaxTaps, trace_slot(L, w + 2), p, ln);
+        producer = true;
+      }
     }
-    if (!cta_barrier(L.err, L.barrier, (unsigned)L.nblocks, epoch, sm, L.spin_ns, cta != L.no_arrive_cta)) {
-      window_wait();   // no copy left in flight
+    // publish this CTA's part of wave w (its partials; its row's end taps)
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      __threadfence();
+      if (producer) atomicAdd(ctr_taps + p, 1u);
+      if (cta != L.no_arrive_cta) atomicAdd(ctr_part + (i & (kWaveSlots - 1)), 1u);
+    }
+    have_taps = producer;
+    // tracker of wave w + 1: the phase base advances by wave w's rate, the rate by
+    // i_{w-1} (the estimate of the wave before: fixed once every CTA has finished it,
+    // so this wait is normally over before it starts)
+    if (w > L.wave_first &&
+        !cta_wait(L.err, ctr_part + ((i - 1u) & (kWaveSlots - 1)), part_target(i - 1u), sm, L.spin_ns)) {
+      window_wait();
       return;
     }
-    // one warp folds the wave's partials (fixed tree, identical in every CTA)
     if (ln.warp == 0) {
-      const float4 *src = L.fo_part + (w & 1) * 2 * L.P;
-      const int n = (int)(2 * (g_end - g0));
-      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-      for (int jj = ln.lane; jj < n; jj += 32) v = df4_add(v, __ldcg(&src[jj]));
-      for (int o = 16; o >= 1; o >>= 1) v = df4_add(v, shfl_xor_f4(v, o));
+      const long long inc = w > L.wave_first ? wave_increment(w - 1) : sm.pend;
       if (ln.lane == 0) {
-        // r = 1/4 arg(sum); Phi += 2PS (dw/2); dw += r/16 rounded to the grid -- in Q0.64 turns
-        const float r = L.fo_track ? 0.25f * atan2f(v.z + v.w, v.x + v.y) : 0.f;
         const long long dq = sm.dq;
         sm.phq += (unsigned long long)(2 * (long long)L.P * L.S) * (unsigned long long)dq;
-        sm.dq = dq + grid_to_q64(__double2ll_rn((double)r * L.inc_scale));
+        sm.dq = dq + inc;
         if (cta == 0) trace_fo(L, w + 2, (double)sm.dq * 6.8122431601731090e-19, q64_to_rad(sm.phq));
       }
     }
     __syncthreads();
   }
+  window_wait();
   if (cta == 0) {
-    const float2 *last = L.tap_slot + ((L.wave_last - 1) & 1) * 4 * kMaxTaps;
+    // every CTA has published the launch's last wave: the state for the next launch
+    const unsigned kl = (unsigned)(L.wave_last - 1 - L.wave_first);
+    if (!cta_wait(L.err, ctr_part + (kl & (kWaveSlots - 1)), part_target(kl), sm, L.spin_ns)) return;
+    const float2 *last = L.tap_slot + (kl & (kWaveSlots - 1)) * 4 * kMaxTaps;
     for (int jj = threadIdx.x; jj < 4 * kMaxTaps; jj += blockDim.x)
       __stcg(&(&L.st->taps[0][0][0])[jj], __ldcg(&last[jj]));
-    if (threadIdx.x == 0) {
-      L.st->Phi_q = sm.phq;
-      L.st->delta_q = sm.dq;
-      L.st->dw = (double)sm.dq * 6.8122431601731090e-19;   // 4 pi / 2^64 rad per symbol
-      L.st->Phi = q64_to_rad(sm.phq);
-      L.st->next_wave = L.wave_last;
+    if (ln.warp == 0) {
+      const long long inc = wave_increment(L.wave_last - 1);
+      if (ln.lane == 0) {
+        L.st->pend_q = inc;
+        L.st->Phi_q = sm.phq;
+        L.st->delta_q = sm.dq;
+        L.st->dw = (double)sm.dq * 6.8122431601731090e-19;   // 4 pi / 2^64 rad per symbol
+        L.st->Phi = q64_to_rad(sm.phq);
+        L.st->next_wave = L.wave_last;
+      }
     }
   }
 }
 
-template <int MB>
-__global__ void __launch_bounds__(kEqThreads, 1) eq_kernel(EqLaunch L) {
-  __shared__ EqSmem sm;
-  eq_body<MB>(L, (int)blockIdx.x, sm);
+template <int MB, int NW>
+__global__ void __launch_bounds__(NW * 32, 1) eq_kernel(EqLaunch L) {
+  __shared__ EqSmem<NW> sm;
+  eq_body<MB, NW>(L, (int)blockIdx.x, sm);
 }
 
 // Unused dynamic shared memory that keeps the equaliser's SMs to itself: the
@@ -789,14 +933,19 @@ __global__ void __launch_bounds__(kEqThreads, 1) eq_kernel(EqLaunch L) {
 constexpr int kEqPadSmem = 180 * 1024;
 
 int eq_max_blocks() {
-  int dev = 0, sms = 0, per = 0, per4 = 0;
+  int dev = 0, sms = 0, best = 1 << 30;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaFuncSetAttribute(eq_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kEqPadSmem);
-  cudaFuncSetAttribute(eq_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, kEqPadSmem);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, eq_kernel<2>, kEqThreads, kEqPadSmem);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per4, eq_kernel<4>, kEqThreads, kEqPadSmem);
-  return sms * min(per, per4);
+  const void *fns[4] = {(const void *)eq_kernel<2, 4>, (const void *)eq_kernel<4, 4>, (const void *)eq_kernel<2, 8>,
+                        (const void *)eq_kernel<4, 8>};
+  const int threads[4] = {128, 128, 256, 256};
+  for (int k = 0; k < 4; ++k) {
+    int per = 0;
+    cudaFuncSetAttribute(fns[k], cudaFuncAttributeMaxDynamicSharedMemorySize, kEqPadSmem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fns[k], threads[k], kEqPadSmem);
+    best = min(best, per);
+  }
+  return sms * best;
 }
 
 // Batched form: one cooperative launch serves many independent streams.  CTA
@@ -804,11 +953,11 @@ int eq_max_blocks() {
 // synchronises on its own barrier words (EqLaunch::nblocks = team size).
 __global__ void __launch_bounds__(kEqThreads, 3) eq_batch_kernel(const EqLaunch *__restrict__ Ls,
                                                                  const int2 *__restrict__ team) {
-  __shared__ EqSmem sm;
+  __shared__ EqSmem<4> sm;
   const int2 t = team[blockIdx.x];
   const EqLaunch &L = Ls[t.x];
-  if (L.mod_bits == 4) eq_body<4>(L, t.y, sm);
-  else eq_body<2>(L, t.y, sm);
+  if (L.mod_bits == 4) eq_body<4, 4>(L, t.y, sm);
+  else eq_body<2, 4>(L, t.y, sm);
 }
 
 int eq_batch_max_blocks(int pad_smem) {
@@ -833,8 +982,10 @@ cudaError_t launch_eq_batch(const EqLaunch *d_L, const int2 *d_team, int nblocks
 cudaError_t launch_eq(const EqLaunch &L, cudaStream_t s) {
   EqLaunch a = L;
   void *args[] = {&a};
-  const void *fn = L.mod_bits == 4 ? (const void *)eq_kernel<4> : (const void *)eq_kernel<2>;
-  return cudaLaunchCooperativeKernel(fn, dim3(L.nblocks), dim3(kEqThreads), args, kEqPadSmem, s);
+  const bool w8 = L.nw == 8;
+  const void *fn = L.mod_bits == 4 ? (w8 ? (const void *)eq_kernel<4, 8> : (const void *)eq_kernel<4, 4>)
+                                   : (w8 ? (const void *)eq_kernel<2, 8> : (const void *)eq_kernel<2, 4>);
+  return cudaLaunchCooperativeKernel(fn, dim3(L.nblocks), dim3(w8 ? 256 : 128), args, kEqPadSmem, s);
 }
 
 }  // namespace rx

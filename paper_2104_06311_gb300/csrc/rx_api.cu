@@ -52,6 +52,7 @@ struct rx_stream {
   double wait_limit_us = 2e6;       // RX_P_WAIT_LIMIT_US: limit of every bounded device wait
   int64_t no_arrive = -1;           // RX_P_TEST_NO_ARRIVE: CTA left out of the wave barriers (-1: none)
   int dft_tc = 0;                   // RX_P_DFT_TC: reduced formats' radix-16 passes on the tensor pipe
+  int eq_warps = 4;                 // RX_P_EQ_WARPS: warps per butterfly-row CTA of the equaliser
   // ---- resolved
   int N = 0, V = 0, Sh = 0, P = 0, C = 256;
   int64_t A_full = 0, span = 0;
@@ -411,6 +412,10 @@ rx_status rx_set_param(rx_stream *rx, int key, double v) {
       return RX_OK;
     case RX_P_TEST_NO_ARRIVE: return as_int(-1, 1 << 20, &rx->no_arrive);
     case RX_P_DFT_TC: s = as_int(0, 1, &t); if (s == RX_OK) rx->dft_tc = (int)t; return s;
+    case RX_P_EQ_WARPS:
+      if (v != 4.0 && v != 8.0) return fail(rx, RX_EINVAL, "equaliser warps per row must be 4 or 8");
+      rx->eq_warps = (int)v;
+      return RX_OK;
     default: return fail(rx, RX_EINVAL, "unknown parameter key");
   }
   if (s != RX_OK) return s;
@@ -454,6 +459,7 @@ rx_status rx_get_param(rx_stream *rx, int key, double *v) {
     case RX_P_WAIT_LIMIT_US: *v = rx->wait_limit_us; break;
     case RX_P_TEST_NO_ARRIVE: *v = (double)rx->no_arrive; break;
     case RX_P_DFT_TC: *v = rx->dft_tc; break;
+    case RX_P_EQ_WARPS: *v = rx->eq_warps; break;
     default: return fail(rx, RX_EINVAL, "unknown parameter key");
   }
   return RX_OK;
@@ -493,12 +499,12 @@ rx_status rx_reserve(rx_stream *rx, int64_t max_call) {
     RX_ALLOC(rx->bh[i], (size_t)2 * rx->y_cap);
   }
   RX_ALLOC(rx->st, 1);
-  RX_ALLOC(rx->fo_part, (size_t)4 * rx->P);
-  RX_ALLOC(rx->tap_slot, (size_t)2 * 4 * kMaxTaps);
+  RX_ALLOC(rx->fo_part, (size_t)kWaveSlots * 2 * rx->P);
+  RX_ALLOC(rx->tap_slot, (size_t)kWaveSlots * 4 * kMaxTaps);
   RX_ALLOC(rx->trace, (size_t)rx->trace_cap * 4 * kMaxTaps * 2);
   RX_ALLOC(rx->trace_fo, (size_t)rx->trace_cap * 2);
   if (rx->inner_cap > 0) RX_ALLOC(rx->inner, (size_t)2 * rx->inner_cap);
-  RX_ALLOC(rx->barrier, 2);
+  RX_ALLOC(rx->barrier, kEqBarrierWords);
   RX_ALLOC(rx->err, 1);
   RX_ALLOC(rx->chunk_r, (size_t)2 * rx->chunk_cap);
   RX_ALLOC(rx->chunk_s2, (size_t)2 * rx->chunk_cap);
@@ -750,6 +756,7 @@ rx_status rx_process(rx_stream *rx, const rx_in *in, rx_out *out) {
       L.cma_r2 = rx->mod_bits == 4 ? 1.32f : 1.0f;
       L.fo_smooth = rx->fo_smooth;
       L.inc_scale = (double)(1ll << kFoGridBits) / (4.0 * 3.14159265358979323846 * rx->fo_smooth);
+      L.nw = rx->eq_warps;
       L.spin_ns = (unsigned long long)(rx->wait_limit_us * 1e3);
       L.no_arrive_cta = (int)rx->no_arrive;
       L.inner = rx->inner;
@@ -759,7 +766,7 @@ rx_status rx_process(rx_stream *rx, const rx_in *in, rx_out *out) {
       L.fo_track = rx->fo_track;
       L.nblocks = rx->eq_blocks;
       L.u_fmt = rx->fmt;
-      RX_CUDA(cudaMemsetAsync(rx->barrier, 0, 2 * sizeof(unsigned), rx->sub[1]), "barrier reset");
+      RX_CUDA(cudaMemsetAsync(rx->barrier, 0, kEqBarrierWords * sizeof(unsigned), rx->sub[1]), "barrier reset");
       StageTimer tm(rx, RX_STAGE_EQ, rx->sub[1]);
       rx->stage_launches[RX_STAGE_EQ] += 1;
       RX_CUDA(launch_eq(L, rx->sub[1]), "equaliser");

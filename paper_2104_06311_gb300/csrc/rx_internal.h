@@ -11,13 +11,18 @@ namespace rx {
 
 constexpr int kMaxTaps = 16;      // butterfly taps T <= 15 (odd), padded to 16
 constexpr int kAngles = 32;       // BPS test angles (one per lane)
-constexpr int kEqThreads = 128;   // equaliser CTA: 4 warps, one butterfly row
+constexpr int kEqThreads = 128;   // batched equaliser CTA: 4 warps, one butterfly row
 constexpr int kChunkSym = 1152;   // equaliser span chunk (symbols) held in smem
 constexpr int kBpsChunk = 256;    // BPS pass-1 symbols per warp
 // Frequency tracker grid: the estimate and every tracking step are rounded to
 // whole multiples of 2^-kFoGridBits turns per sample, so that the tracked phase
 // is an exact sum (Q0.64 turns whose low 64 - kFoGridBits bits stay zero).
 constexpr int kFoGridBits = 16;
+// Equaliser wave bookkeeping: FO partials and end taps per wave are kept in
+// kWaveSlots rotating slots (a slot is rewritten four waves later, after every
+// CTA has provably read it), synchronised through kEqBarrierWords counters.
+constexpr int kWaveSlots = 4;
+constexpr int kEqBarrierWords = 2 + kWaveSlots + 2;
 // Default limit of a bounded device spin: 2 s of device time.
 constexpr unsigned long long kSpinLimitNs = 2000000000ull;
 
@@ -45,6 +50,8 @@ struct EqState {
   double Phi;                      // phase base of the next wave (rad), reported
   unsigned long long Phi_q;        // phase base as Q0.64 turns (the tracked value)
   long long delta_q;               // per-sample phase increment dw/2 as Q0.64 turns
+  long long pend_q;                // increment estimated in the last wave run, applied one
+                                   // wave later (Q0.64 turns per sample)
   int64_t next_wave;               // next wave to run
   int32_t acq_done;
   int32_t pad;
@@ -57,13 +64,16 @@ struct EqLaunch {
   float2 *y;                // equaliser out [2][y_stride], symbol k at y[k - y_base]
   int64_t y_base, y_stride;
   EqState *st;
-  float4 *fo_part;          // [2][2 * P] FO partial sums per (segment, row) as double-float
-                            // (x_hi, x_lo, y_hi, y_lo), double buffered
-  float2 *tap_slot;         // [2][2*2*kMaxTaps] last-segment taps (double buffered)
+  float4 *fo_part;          // [kWaveSlots][2 * P] FO partial sums per (segment, row) as
+                            // double-float (x_hi, x_lo, y_hi, y_lo), slot = wave mod kWaveSlots
+  float2 *tap_slot;         // [kWaveSlots][2*2*kMaxTaps] last-segment end taps per wave
   float *trace;             // [trace_cap][2*2*kMaxTaps*2] wave start taps
   double *trace_fo;         // [trace_cap][2] (dw, Phi)
   int64_t trace_cap;
-  unsigned *barrier;        // [0] grid barrier, [1] acquisition row pair (zeroed before launch)
+  unsigned *barrier;        // [kEqBarrierWords] (zeroed before launch): [0] grid barrier after
+                            // the acquisition, [1] acquisition row pair, [2 + s] CTA arrivals
+                            // of the waves in slot s (FO partials written), [2 + kWaveSlots
+                            // + p] row-p arrivals (a wave's end taps written)
   int *err;                 // sticky error word
   int64_t K;                // symbols of the whole stream if known (flushed), else -1
   int run_acq;              // 1: run the acquisition in this launch
@@ -77,13 +87,14 @@ struct EqLaunch {
   double fo_smooth;
   double inc_scale;         // 2^kFoGridBits / (4 pi fo_smooth): tracker step r -> grid units per sample
   unsigned long long spin_ns;  // limit of every bounded device wait (ns of device time)
-  int no_arrive_cta;        // CTA that leaves out its arrival at the wave barriers (-1: none; timeout test)
+  int no_arrive_cta;        // CTA that leaves out its wave arrivals (-1: none; timeout test)
   int8_t *inner;            // optional trace of the inner BPS angle per DD update block, [2][inner_cap]
                             // (row p): acquisition blocks, then inner_spb entries per segment
   int64_t inner_cap, inner_acq;
   int inner_spb;
   int fo_track;
   int nblocks;              // CTAs in the grid (even: 2 rows per segment slot)
+  int nw;                   // warps per butterfly-row CTA: 4 or 8 (0 = 4; the batched form uses 4)
   int u_fmt;                // storage format of u (RX_FMT_*)
 };
 

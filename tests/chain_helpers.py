@@ -88,10 +88,10 @@ def device_ties(rx, p: O.RxParams, K: int) -> dict:
     return out
 
 
-def run_gpu(p: O.RxParams, samples: np.ndarray, chunk=None, reserve=None):
+def run_gpu(p: O.RxParams, samples: np.ndarray, chunk=None, reserve=None, **flags):
     import torch
     rx = make_receiver(p, LLR_OUT=1, SYM_OUT=1, EQ_OUT=1, CDC_OUT=1,
-                       INNER_TRACE=inner_capacity(p, samples.shape[0] // 2))
+                       INNER_TRACE=inner_capacity(p, samples.shape[0] // 2), **flags)
     x = torch.from_numpy(np.ascontiguousarray(samples)).cuda()
     if reserve:
         rx.reserve(reserve)

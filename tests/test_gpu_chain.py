@@ -164,6 +164,23 @@ def test_c3_16qam_6000km_parity():
     print("c3 parity", rep)
 
 
+@pytest.mark.parametrize("mod", ["qpsk", "16qam"])
+def test_eq_eight_warps_per_row_parity(mod):
+    """The equaliser's butterfly row split over 8 warps (4 taps and 4 inner angles per
+    lane) follows the oracle as the default 4-warp split does: QPSK on the 10,000 km
+    shape (FO, phase noise, PMD), 16QAM on a 2000 km link."""
+    if mod == "qpsk":
+        lk = L.workload("c2", n_sym=1 << 16)
+    else:
+        lk = dataclasses.replace(L.workload("c3", n_sym=1 << 16), L_km=2000.0)
+    g = L.generate(lk)
+    p = rx_params(lk, g.in_scale)
+    gpu = run_gpu(p, g.samples, EQ_WARPS=8)
+    assert gpu["rx"].get_param("EQ_WARPS") == 8
+    rep, _ = check_chain(p, g, gpu, {})
+    print("8 warps", mod, rep)
+
+
 @pytest.mark.parametrize("N", [256, 512, 2048, 4096, 8192, 16384])
 def test_cdc_fft_sizes(N):
     lk = L.Link(n_sym=20000 + 123, L_km=300.0, snr_db=15.0, seed=77 + N)

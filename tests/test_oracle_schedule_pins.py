@@ -165,6 +165,36 @@ def test_tracker_removes_a_grid_exact_offset_exactly():
         assert phi == ((2 * A - 2 * p.n_cma) * d + w * 2 * PS * d) % M
 
 
+def test_tracker_applies_each_wave_estimate_two_waves_on():
+    # noise-free QPSK with a grid-exact offset d (as above) up to the start of wave 1,
+    # then d + J: wave 0 sees no residual (its step is 0), wave 1 sees J.  Wave 1's
+    # estimate moves the rate first at wave 3: d_0 = d_1 = d_2 = d, d_3 > d, and the
+    # phase bases integrate the rates wave by wave
+    p = O.RxParams(**SCHED).resolved()
+    P, S = p.wave_segments(), p.seg_len
+    K = 1024 + 5 * P * S
+    d, J = 32 * 37, 32
+    M = 1 << C.FO_GRID_BITS
+    A = p.acq_len(K)
+    n1 = 2 * (A + P * S)                       # first sample of wave 1
+    s = L.map_symbols(L.random_bits(46, 2 * 2 * K).reshape(2, -1), "qpsk")
+    n = np.arange(2 * K)
+    ph = np.where(n < n1, n * d, n1 * d + (n - n1) * (d + J)) % M
+    u = np.zeros((2, 2 * K), np.complex128)
+    u[:, ::2] = s
+    u = u * np.exp(1j * 2 * math.pi * ph / M)
+    tr = {}
+    O.equalize(u, p, tr)
+    units = tr["wave_units"]
+    assert len(units) == 5 and tr["acq_units"] == d
+    assert [dw for _, dw in units[:3]] == [d, d, d]
+    assert tr["wave_r"][0] == 0.0 or abs(tr["wave_r"][0]) < 1e-12
+    inc1, _ = C.fo_units(tr["wave_r"][1] / p.fo_smooth, p.sps)
+    assert inc1 > 0 and units[3][1] == d + inc1
+    for w in range(4):
+        assert units[w + 1][0] == (units[w][0] + 2 * P * S * units[w][1]) % M
+
+
 def test_window_rotation_is_the_exact_integer_phase():
     # _Window turns sample n by exp(-j 2 pi ((phi + (n - n0) d) mod 2^G) / 2^G)
     M = 1 << C.FO_GRID_BITS
