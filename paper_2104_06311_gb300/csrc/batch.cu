@@ -150,6 +150,7 @@ __global__ void batch_init_kernel(const EqLaunch *__restrict__ Ls) {
     taps[i] = make_float2((tap == c && (pq == 0 || pq == 3)) ? 1.f : 0.f, 0.f);
   }
   for (int64_t i = threadIdx.x; i < 2 * L.trace_cap; i += blockDim.x) L.trace_fo[i] = 0.0;
+  for (int k = threadIdx.x; k < kEqBarrierWords; k += blockDim.x) L.barrier[k] = 0u;
   if (threadIdx.x == 0) {
     L.st->dw = 0.0;
     L.st->Phi = 0.0;
@@ -158,7 +159,6 @@ __global__ void batch_init_kernel(const EqLaunch *__restrict__ Ls) {
     L.st->pend_q = 0ll;
     L.st->next_wave = 0;
     L.st->acq_done = 0;
-    for (int k = 0; k < kEqBarrierWords; ++k) L.barrier[k] = 0u;
   }
 }
 
@@ -600,7 +600,7 @@ rx_status rx_batch_create(rx_batch **out, int n_ch, const rx_chan_cfg *cfgs) {
     const int64_t A = std::min(c.A_full, c.K_cap);
     const int64_t n_seg = c.K_cap > A ? (c.K_cap - A + kS - 1) / kS : 0;
     const int64_t waves = (n_seg + c.P - 1) / c.P;
-    c.u_stride = c.n_cap + 64;
+    c.u_stride = (c.n_cap + 64) | 1;   // odd: pol rows at opposite 16-byte phases (equaliser window banks)
     c.y_stride = c.K_cap + 64;
     c.chunk_cap = (c.K_cap + c.C - 1) / c.C + 16;
     c.region_cap = (c.K_cap > A ? (c.K_cap - A + c.span - 1) / c.span : 0) + 1 + 16;

@@ -62,7 +62,9 @@ namespace rx {
 namespace {
 
 constexpr int kWinMax = 2 * kChunkSym + 2 * 8;
-constexpr int kWinRow = kWinMax + 1;     // odd row length: pol rows land 8 bytes apart in the banks
+// odd row length (pol rows apart in the banks) with two spare slots: element 0 sits at slot
+// 1 or 2, so that a bulk copy's 16-byte-aligned source lands on a 16-byte-aligned slot
+constexpr int kWinRow = kWinMax + 3;
 constexpr unsigned FULL = 0xffffffffu;
 
 // Work split of one butterfly row over NW warps (NW = 4 or 8): warp w owns the
@@ -91,8 +93,15 @@ struct EqSmem {
   unsigned long long phq;                // tracker: phase base, Q0.64 turns
   long long dq;                          // tracker: per-sample increment, Q0.64 turns
   long long pend;                        // increment of the wave before the launch's first
+  unsigned long long wbar;               // mbarrier of the window's bulk copies
+  int wo[2];                             // slot of window element 0 per row (1 or 2)
+  int w_uses, w_par, w_out;              // bulk copies issued, parity of the last, its mode
   int fail;
 };
+
+// Row q of the window: element j (sample win_lo + j) at slot wo[q] + j.
+template <class SM>
+__device__ __forceinline__ float2 *wrow(SM &sm, int q) { return sm.win[q] + sm.wo[q]; }
 
 // Double-float (hi + lo) arithmetic for the frequency sums: Knuth's two-sum
 // keeps ~44 bits in FP32 operations (FP64 issues slowly on this part).
@@ -126,6 +135,8 @@ __device__ __forceinline__ double q64_to_rad(unsigned long long q) {
 __device__ __forceinline__ long long grid_to_q64(long long units) {
   return (long long)((unsigned long long)units << (64 - kFoGridBits));
 }
+
+__device__ __forceinline__ void fence_acq_rel_gpu() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
 
 // Bounded barrier over `count` CTAs on counter *ctr: returns false (and sets
 // the error word) once limit_ns of device time pass without every CTA arriving,
@@ -161,27 +172,33 @@ __device__ bool cta_barrier(int *err, unsigned *ctr, unsigned count, unsigned &e
   return sm.fail == 0;
 }
 
-// Bounded wait until *ctr >= target: false (and the error word set) once
-// limit_ns of device time pass, or when another CTA already failed.  Every
-// thread of the CTA returns the same verdict; thread 0's acquire and fence make
-// what the arrivals published visible to the whole CTA after the barrier.
-template <class SM>
-__device__ bool cta_wait(int *err, const unsigned *ctr, unsigned target, SM &sm, unsigned long long limit_ns) {
-  if (threadIdx.x == 0) {
-    sm.fail = 0;
-    const unsigned long long t0 = globaltimer_ns();
-    unsigned polls = 0;
-    while (ld_acquire_u32(ctr) < target) {
-      if (*(volatile int *)err != 0) { sm.fail = 1; break; }
-      if (globaltimer_ns() - t0 > limit_ns) {
-        atomicOr(err, DEV_ERR_TIMEOUT);
-        sm.fail = 1;
-        break;
-      }
-      if (++polls > 4096) __nanosleep(256);
+// One thread's bounded poll until *ctr >= target: false (and the error word set)
+// once limit_ns of device time pass, or when another CTA already failed.  The
+// acquire loads order what the arrivals released before this thread's later
+// accesses, and a CTA barrier after it before the other threads' (the pattern
+// needs no further fence, so the wait does not drain this thread's own pending
+// arrivals).  After `eager` back-to-back polls it sleeps backoff_ns between polls.
+__device__ __forceinline__ bool poll_ge(int *err, const unsigned *ctr, unsigned target,
+                                        unsigned long long limit_ns, unsigned eager, unsigned backoff_ns) {
+  const unsigned long long t0 = globaltimer_ns();
+  unsigned polls = 0;
+  while (ld_acquire_u32(ctr) < target) {
+    if (*(volatile int *)err != 0) return false;
+    if (globaltimer_ns() - t0 > limit_ns) {
+      atomicOr(err, DEV_ERR_TIMEOUT);
+      return false;
     }
-    __threadfence();
+    if (++polls > eager) __nanosleep(backoff_ns);
   }
+  return true;
+}
+
+// CTA-wide bounded wait until *ctr >= target (thread 0 polls); every thread
+// returns the same verdict.
+template <class SM>
+__device__ bool cta_wait(int *err, const unsigned *ctr, unsigned target, SM &sm, unsigned long long limit_ns,
+                         unsigned eager = 4096, unsigned backoff_ns = 256) {
+  if (threadIdx.x == 0) sm.fail = poll_ge(err, ctr, target, limit_ns, eager, backoff_ns) ? 0 : 1;
   __syncthreads();
   return sm.fail == 0;
 }
@@ -200,39 +217,112 @@ __device__ __forceinline__ unsigned smem_u32(const void *p) {
 }
 
 // Raw samples [win_lo, win_lo + count) of both rows copied into the window
-// asynchronously: element j by thread j mod NT (the CTA's threads), the thread that converts
-// it in window_finish, so that its own wait makes the copy visible to it (a
-// 16-bit sample lands in the low half of its float2 slot); samples outside
-// [0, n_limit) are left for window_finish to zero.  Issued early (before a grid barrier), the
-// copies land while the CTA waits.
+// asynchronously; samples outside [0, n_limit) are left for window_finish to zero.
+// FP32 rows: thread 0 issues one bulk copy per row (cp.async.bulk, completion on the
+// window's mbarrier), widened to 16-byte boundaries in global memory and placed at
+// the same 16-byte phase in the row's slots (wo); the widened range must stay inside
+// the buffer's samples [u_lo, u_hi), else (and for 16-bit formats) every thread copies
+// the elements it later converts (cp.async, a 16-bit sample in the low half of its
+// float2 slot).  Issued early (before the waves' waits), the copies land meanwhile.
+// Called by the whole CTA once every warp is done with the window.
 template <int NT, class SM>
 __device__ __forceinline__ void window_issue(const unsigned char *__restrict__ u0, const unsigned char *__restrict__ u1,
-                                             int fmt, SM &sm, int64_t win_lo, int count, int64_t n_limit) {
+                                             int fmt, SM &sm, int64_t win_lo, int count, int64_t n_limit,
+                                             int64_t u_lo, int64_t u_hi) {
   const int lo = (int)max((int64_t)0, min((int64_t)count, -win_lo));
   const int hi = (int)max((int64_t)0, min((int64_t)count, n_limit - win_lo));
+  if (threadIdx.x == 0) {
+    int mode = 0;            // 0: nothing to copy, 1: bulk copies in flight, -1: element copies
+    int wo[2] = {1, 1};
+    if (hi > lo) {
+      mode = -1;
+      if (fmt == RX_FMT_F32) {
+        const unsigned char *src[2] = {u0, u1};
+        int ja[2], jb[2];
+        bool ok = true;
+        for (int q = 0; q < 2; ++q) {
+          const size_t a_lo = __cvta_generic_to_global(src[q] + (win_lo + lo) * 8);
+          const size_t a_hi = __cvta_generic_to_global(src[q] + (win_lo + hi) * 8);
+          ja[q] = lo - (int)((a_lo >> 3) & 1);
+          jb[q] = hi + (int)((a_hi >> 3) & 1);
+          ok = ok && win_lo + ja[q] >= u_lo && win_lo + jb[q] <= u_hi;
+          // (slot address of element ja) % 16 == 0
+          wo[q] = 1 + (int)(((smem_u32(&sm.win[q][0]) >> 3) + (unsigned)ja[q] + 1u) & 1u);
+        }
+        if (ok) {
+          // the window's earlier generic accesses before the async proxy's writes
+          asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+          const unsigned bar = smem_u32(&sm.wbar);
+          const unsigned bytes = (unsigned)((jb[0] - ja[0]) + (jb[1] - ja[1])) * 8u;
+          asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(bytes) : "memory");
+          for (int q = 0; q < 2; ++q) {
+            asm volatile(
+                "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+                    smem_u32(&sm.win[q][wo[q] + ja[q]])),
+                "l"(__cvta_generic_to_global(src[q] + (win_lo + ja[q]) * 8)), "r"((unsigned)(jb[q] - ja[q]) * 8u),
+                "r"(bar)
+                : "memory");
+          }
+          sm.w_par = sm.w_uses & 1;
+          sm.w_uses += 1;
+          mode = 1;
+        } else {
+          wo[0] = wo[1] = 1;
+        }
+      }
+    }
+    sm.wo[0] = wo[0];
+    sm.wo[1] = wo[1];
+    sm.w_out = mode;
+  }
+  __syncthreads();
+  if (sm.w_out != -1) return;
+  float2 *w0 = wrow(sm, 0), *w1 = wrow(sm, 1);
   if (fmt == RX_FMT_F32) {
     for (int j = threadIdx.x; j < hi; j += NT) {
       if (j < lo) continue;
       const int64_t n = win_lo + j;
-      asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(smem_u32(&sm.win[0][j])), "l"(u0 + n * 8)
+      asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(smem_u32(&w0[j])), "l"(u0 + n * 8)
                    : "memory");
-      asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(smem_u32(&sm.win[1][j])), "l"(u1 + n * 8)
+      asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(smem_u32(&w1[j])), "l"(u1 + n * 8)
                    : "memory");
     }
   } else {
     for (int j = threadIdx.x; j < hi; j += NT) {
       if (j < lo) continue;
       const int64_t n = win_lo + j;
-      asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(smem_u32(&sm.win[0][j])), "l"(u0 + n * 4)
+      asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(smem_u32(&w0[j])), "l"(u0 + n * 4)
                    : "memory");
-      asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(smem_u32(&sm.win[1][j])), "l"(u1 + n * 4)
+      asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(smem_u32(&w1[j])), "l"(u1 + n * 4)
                    : "memory");
     }
   }
   asm volatile("cp.async.commit_group;\n" ::: "memory");
 }
 
-__device__ __forceinline__ void window_wait() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+// Waits for the window's copies: this thread's element copies, and the bulk copies
+// of the last issue (bounded: past limit_ns the error word is set and the wait ends).
+template <class SM>
+__device__ __forceinline__ void window_wait(SM &sm, int *err, unsigned long long limit_ns) {
+  asm volatile("cp.async.wait_all;\n" ::: "memory");
+  if (sm.w_out == 1) {
+    const unsigned bar = smem_u32(&sm.wbar), par = (unsigned)sm.w_par;
+    const unsigned long long t0 = globaltimer_ns();
+    while (true) {
+      unsigned done;
+      asm volatile(
+          "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+          : "=r"(done)
+          : "r"(bar), "r"(par)
+          : "memory");
+      if (done) break;
+      if (globaltimer_ns() - t0 > limit_ns) {
+        atomicOr(err, DEV_ERR_TIMEOUT);
+        break;
+      }
+    }
+  }
+}
 
 // Sample from a window slot filled by window_issue, as complex float.
 __device__ __forceinline__ float2 raw_sample(const float2 *slot, int fmt) {
@@ -274,12 +364,13 @@ __device__ __forceinline__ float2 q64_phasor(const SM &sm, unsigned long long t)
   return cmul_f(sm.rtab[ph >> 24], make_float2(cs, -sn));
 }
 
-// Waits for this thread's copies, then converts its samples in place, removing
-// the tracker's phase: window = exp(-j phi_n) u(n), zero outside [0, n_limit).
+// Waits for the window's copies, then converts this thread's samples in place,
+// removing the tracker's phase: window = exp(-j phi_n) u(n), zero outside [0, n_limit).
 template <int NT, class SM>
 __device__ __forceinline__ void window_finish(int fmt, SM &sm, int64_t win_lo, int count, const Rot &rot,
-                                              int64_t n_limit) {
-  window_wait();
+                                              int64_t n_limit, int *err, unsigned long long limit_ns) {
+  window_wait(sm, err, limit_ns);
+  float2 *w0 = wrow(sm, 0), *w1 = wrow(sm, 1);
   // groups of kG samples per thread: all raw reads of a group first, then its
   // independent rotation chains (one warp per scheduler: ILP hides the latency)
   constexpr int kPer = (kWinMax + NT - 1) / NT;
@@ -298,8 +389,8 @@ __device__ __forceinline__ void window_finish(int fmt, SM &sm, int64_t win_lo, i
       const int64_t n = win_lo + j;
       a[g] = b[g] = make_float2(0.f, 0.f);
       if (j < count && n >= 0 && n < n_limit) {
-        a[g] = raw_sample(&sm.win[0][j], fmt);
-        b[g] = raw_sample(&sm.win[1][j], fmt);
+        a[g] = raw_sample(&w0[j], fmt);
+        b[g] = raw_sample(&w1[j], fmt);
       }
     }
     float2 r2 = make_float2(1.f, 0.f);
@@ -317,8 +408,8 @@ __device__ __forceinline__ void window_finish(int fmt, SM &sm, int64_t win_lo, i
           a[g] = cmul_f(a[g], r2);
           b[g] = cmul_f(b[g], r2);
         }
-        sm.win[0][j] = a[g];
-        sm.win[1][j] = b[g];
+        w0[j] = a[g];
+        w1[j] = b[g];
       }
     }
   }
@@ -356,6 +447,9 @@ struct Lane {
 struct Hot {
   float2 *yrow;                    // equaliser output of this row, indexed by stream symbol
   const unsigned char *u0, *u1;    // CDC output of pols X / Y (format u_fmt), indexed by stream sample
+  int64_t u_lo, u_hi;              // samples the CDC buffer holds: [u_lo, u_hi)
+  int *err;                        // sticky error word
+  unsigned long long spin_ns;      // limit of a bounded wait
   int u_fmt;
   int T, c, Bu;
   float mu_cma, mu_dd, cma_r2;
@@ -454,15 +548,17 @@ __device__ __forceinline__ void run_span(const Hot hot, EqSmem<NW> &sm, const Sp
     const int nsteps = (int)((ce - cs + Bu - 1) / Bu);
     __syncthreads();  // every warp is done with the previous chunk's window
     // (pre: the first chunk's copies were issued before the caller's grid barrier)
-    if (!(pre && cs == sp.kp)) window_issue<G::NT>(hot.u0, hot.u1, hot.u_fmt, sm, win_lo, count, n_limit);
-    window_finish<G::NT>(hot.u_fmt, sm, win_lo, count, sp.rot, n_limit);
+    if (!(pre && cs == sp.kp))
+      window_issue<G::NT>(hot.u0, hot.u1, hot.u_fmt, sm, win_lo, count, n_limit, hot.u_lo, hot.u_hi);
+    window_finish<G::NT>(hot.u_fmt, sm, win_lo, count, sp.rot, n_limit, hot.err, hot.spin_ns);
     __syncthreads();
+    const float2 *wq = wrow(sm, ln.q);
     // this lane's TPL window samples u_q[2k+c-i] of a step (zero for inactive symbols or
     // taps i >= T); the next step's are read while the current step's update runs
     auto window_samples = [&](int tt, float2 (&xs)[8]) {
       const int64_t kb = cs + (int64_t)tt * Bu;
       const bool a_ = kl < (int)min((int64_t)Bu, ce - kb);
-      const float2 *xw = sm.win[ln.q] + (2 * tt * Bu + 2 * c) + 2 * kl - ln.sub * G::TPL;
+      const float2 *xw = wq + (2 * tt * Bu + 2 * c) + 2 * kl - ln.sub * G::TPL;
 #pragma unroll
       for (int ii = 0; ii < G::TPL; ++ii)
         xs[ii] = (a_ && ln.sub * G::TPL + ii < T) ? xw[-ii] : make_float2(0.f, 0.f);
@@ -684,6 +780,10 @@ __device__ __forceinline__ void eq_body(const EqLaunch &L, const int cta, EqSmem
     hot.u1 = ub + (L.u_stride - L.u_base) * esz;
     hot.u_fmt = L.u_fmt;
   }
+  hot.u_lo = L.u_base;
+  hot.u_hi = L.u_base + L.u_stride;
+  hot.err = L.err;
+  hot.spin_ns = L.spin_ns;
   hot.T = L.T;
   hot.c = (L.T - 1) / 2;
   hot.Bu = L.Bu;
@@ -701,6 +801,14 @@ __device__ __forceinline__ void eq_body(const EqLaunch &L, const int cta, EqSmem
     sincospif((float)m / 128.f, &s, &c);
     sm.rtab[m] = make_float2(c, -s);
   }
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&sm.wbar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    sm.w_uses = 0;
+    sm.w_par = 0;
+    sm.w_out = 0;
+    sm.wo[0] = sm.wo[1] = 1;
+  }
   __syncthreads();
 
   if (L.run_acq) {
@@ -716,7 +824,7 @@ __device__ __forceinline__ void eq_body(const EqLaunch &L, const int cta, EqSmem
       run_span<MB, NW>(hot, sm, sp, ln, own, h, fo, n_limit);
       const float4 s = reduce_fo(sm, fo, ln);
       if (threadIdx.x == 0) __stcg(&L.fo_part[p], s);
-      if (!cta_barrier(L.err, L.barrier + 1, 2u, epoch2, sm, L.spin_ns)) return;
+      if (!cta_barrier(L.err, L.barrier + kCtrStride, 2u, epoch2, sm, L.spin_ns)) return;
       const float4 s01 = df4_add(__ldcg(&L.fo_part[0]), __ldcg(&L.fo_part[1]));
       const double ax = (double)s01.x + (double)s01.y, ay = (double)s01.z + (double)s01.w;
       const double dw_est = L.fo_track ? 0.25 * atan2(ay, ax) : 0.0;   // once per stream
@@ -807,8 +915,8 @@ __device__ __forceinline__ void eq_body(const EqLaunch &L, const int cta, EqSmem
   // publish wave k + kWaveSlots before that), and the CTA that ran the last segment of
   // wave k arrives on ctr_taps[p] once row p's end taps are written (one producer per
   // row and wave, in wave order).
-  unsigned *const ctr_part = L.barrier + 2;
-  unsigned *const ctr_taps = L.barrier + 2 + kWaveSlots;
+  auto ctr_part = [&](unsigned k) { return L.barrier + (2 + (k & (kWaveSlots - 1))) * kCtrStride; };
+  auto ctr_taps = [&](int row) { return L.barrier + (2 + kWaveSlots + row) * kCtrStride; };
   auto part_target = [&](unsigned k) { return ((k / kWaveSlots) + 1u) * (unsigned)L.nblocks; };
   const int chunk = (kChunkSym / hot.Bu) * hot.Bu;
   bool pre = false;        // the next segment's first window is in flight
@@ -834,8 +942,11 @@ __device__ __forceinline__ void eq_body(const EqLaunch &L, const int cta, EqSmem
         have_taps = false;
       } else {
         if (!ready) {
-          if (!cta_wait(L.err, ctr_taps + p, i, sm, L.spin_ns)) {
-            window_wait();   // no copy left in flight
+          // gentle polling: this wait is off the critical path (the producer runs ahead),
+          // and back-to-back acquire loads on the counter line would slow the producer's
+          // own memory operations there
+          if (!cta_wait(L.err, ctr_taps(p), i, sm, L.spin_ns, 8u, 64u)) {
+            window_wait(sm, L.err, L.spin_ns);   // no copy left in flight
             return;
           }
           ready = true;
@@ -861,7 +972,7 @@ __device__ __forceinline__ void eq_body(const EqLaunch &L, const int cta, EqSmem
         int64_t lo;
         int cnt;
         chunk_window(sn.kp, sn.ke, hot.c, chunk, lo, cnt);
-        window_issue<G::NT>(hot.u0, hot.u1, hot.u_fmt, sm, lo, cnt, n_limit);
+        window_issue<G::NT>(hot.u0, hot.u1, hot.u_fmt, sm, lo, cnt, n_limit, hot.u_lo, hot.u_hi);
         pre = true;
       }
       if (threadIdx.x == 0) __stcg(L.fo_part + (i & (kWaveSlots - 1)) * 2 * L.P + (g - g0) * 2 + p, s);
@@ -871,20 +982,23 @@ __device__ __forceinline__ void eq_body(const EqLaunch &L, const int cta, EqSmem
         producer = true;
       }
     }
-    // publish this CTA's part of wave w (its partials; its row's end taps)
+    // publish this CTA's part of wave w (its partials; its row's end taps): the last
+    // warp's lane 0 releases the CTA's writes (ordered by the barrier) and arrives,
+    // while thread 0 waits until every CTA has published wave w - 1.  That wave fixes
+    // the tracker of wave w + 1 (the phase base advances by wave w's rate, the rate by
+    // i_{w-1}); it ended a wave ago, so the wait is normally over at the first poll.
     __syncthreads();
-    if (threadIdx.x == 0) {
-      __threadfence();
-      if (producer) atomicAdd(ctr_taps + p, 1u);
-      if (cta != L.no_arrive_cta) atomicAdd(ctr_part + (i & (kWaveSlots - 1)), 1u);
+    if (threadIdx.x == (NW - 1) * 32) {
+      fence_acq_rel_gpu();
+      if (producer) atomicAdd(ctr_taps(p), 1u);
+      if (cta != L.no_arrive_cta) atomicAdd(ctr_part(i), 1u);
     }
+    if (threadIdx.x == 0)
+      sm.fail = (w > L.wave_first && !poll_ge(L.err, ctr_part(i - 1u), part_target(i - 1u), L.spin_ns, 4096u, 256u));
+    __syncthreads();
     have_taps = producer;
-    // tracker of wave w + 1: the phase base advances by wave w's rate, the rate by
-    // i_{w-1} (the estimate of the wave before: fixed once every CTA has finished it,
-    // so this wait is normally over before it starts)
-    if (w > L.wave_first &&
-        !cta_wait(L.err, ctr_part + ((i - 1u) & (kWaveSlots - 1)), part_target(i - 1u), sm, L.spin_ns)) {
-      window_wait();
+    if (sm.fail) {
+      window_wait(sm, L.err, L.spin_ns);
       return;
     }
     if (ln.warp == 0) {
@@ -898,11 +1012,11 @@ __device__ __forceinline__ void eq_body(const EqLaunch &L, const int cta, EqSmem
     }
     __syncthreads();
   }
-  window_wait();
+  window_wait(sm, L.err, L.spin_ns);
   if (cta == 0) {
     // every CTA has published the launch's last wave: the state for the next launch
     const unsigned kl = (unsigned)(L.wave_last - 1 - L.wave_first);
-    if (!cta_wait(L.err, ctr_part + (kl & (kWaveSlots - 1)), part_target(kl), sm, L.spin_ns)) return;
+    if (!cta_wait(L.err, ctr_part(kl), part_target(kl), sm, L.spin_ns)) return;
     const float2 *last = L.tap_slot + (kl & (kWaveSlots - 1)) * 4 * kMaxTaps;
     for (int jj = threadIdx.x; jj < 4 * kMaxTaps; jj += blockDim.x)
       __stcg(&(&L.st->taps[0][0][0])[jj], __ldcg(&last[jj]));

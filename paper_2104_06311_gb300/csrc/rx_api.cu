@@ -482,6 +482,9 @@ rx_status rx_reserve(rx_stream *rx, int64_t max_call) {
   const int64_t region = std::max(rx->A_full, rx->span);
   rx->tail_cap = rx->N + max_call + 2 * rx->Sh + 64;
   rx->u_cap = max_call + 2 * (region + rx->W) + 2 * rx->N + 4096;
+  // odd row stride: the two pol rows' samples sit at opposite 16-byte phases, so the
+  // equaliser's bulk-copied window rows land 8 bytes apart in the shared-memory banks
+  rx->u_cap |= 1;
   rx->y_cap = max_call / 2 + 4 * region + 4 * rx->Nb + 4096;
   rx->chunk_cap = rx->y_cap / rx->C + 16;
   rx->region_cap = rx->y_cap / std::min(rx->A_full > 0 ? rx->A_full : rx->span, rx->span) + 16;

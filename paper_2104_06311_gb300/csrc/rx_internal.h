@@ -22,7 +22,9 @@ constexpr int kFoGridBits = 16;
 // kWaveSlots rotating slots (a slot is rewritten four waves later, after every
 // CTA has provably read it), synchronised through kEqBarrierWords counters.
 constexpr int kWaveSlots = 4;
-constexpr int kEqBarrierWords = 2 + kWaveSlots + 2;
+constexpr int kCtrStride = 32;                      // words between counters: one per 128-byte line
+constexpr int kEqCounters = 2 + kWaveSlots + 2;
+constexpr int kEqBarrierWords = kEqCounters * kCtrStride;
 // Default limit of a bounded device spin: 2 s of device time.
 constexpr unsigned long long kSpinLimitNs = 2000000000ull;
 
@@ -70,10 +72,11 @@ struct EqLaunch {
   float *trace;             // [trace_cap][2*2*kMaxTaps*2] wave start taps
   double *trace_fo;         // [trace_cap][2] (dw, Phi)
   int64_t trace_cap;
-  unsigned *barrier;        // [kEqBarrierWords] (zeroed before launch): [0] grid barrier after
-                            // the acquisition, [1] acquisition row pair, [2 + s] CTA arrivals
-                            // of the waves in slot s (FO partials written), [2 + kWaveSlots
-                            // + p] row-p arrivals (a wave's end taps written)
+  unsigned *barrier;        // [kEqCounters][kCtrStride] counters, one per 128-byte line (zeroed
+                            // before launch): [0] grid barrier after the acquisition, [1]
+                            // acquisition row pair, [2 + s] CTA arrivals of the waves in slot s
+                            // (FO partials written), [2 + kWaveSlots + p] row-p arrivals (a
+                            // wave's end taps written)
   int *err;                 // sticky error word
   int64_t K;                // symbols of the whole stream if known (flushed), else -1
   int run_acq;              // 1: run the acquisition in this launch
