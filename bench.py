@@ -40,7 +40,8 @@ N_SM = 152
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=150)
+    ap.add_argument("--steps", type=int, default=None,
+                    help="timed steps (default: 150; 40 for --impl reference, ~1 s of CPU each)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--n-sym", type=int, default=1 << 24, help="symbols per pol (default: the full workload)")
@@ -56,7 +57,10 @@ def parse():
     ap.add_argument("--dft-tc", type=int, default=0,
                     help="precision form: 1 = CDC radix-16 passes on tensor cores, 0 = register butterflies")
     ap.add_argument("--train-symbols", type=int, default=1 << 14, help="c5: symbols per training sequence")
-    return ap.parse_args()
+    args = ap.parse_args()
+    if args.steps is None:
+        args.steps = 40 if args.impl == "reference" else 150
+    return args
 
 
 # ncu dram__bytes_read.sum + dram__bytes_write.sum of one step's eq_kernel launches per
@@ -203,7 +207,7 @@ def reference_arm(args, rank, world):
     if rank != 0:
         return
     # each step a bounded sample (2^19 sample-times, ~2 s of FP64 numpy) so that a
-    # default --steps 40 --warmup 3 run ends within a few minutes
+    # default --steps 40 --warmup 3 run ends within a few minutes (each step ~1 s)
     lk, g = make_input(min(args.cpu_sample, 1 << 19) // 2)
     n = g.samples.shape[0]
     times = []
