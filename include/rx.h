@@ -111,11 +111,22 @@ enum {
                               with FP32 accumulation, 0 = FP32 register butterflies
                               on FP16/BF16 storage (default: measured faster, the
                               transform being bound by shared-memory traffic)      */
-  RX_P_EQ_WARPS = 29       /* warps per butterfly-row CTA of the equaliser, 4 or 8
+  RX_P_EQ_WARPS = 29,      /* warps per butterfly-row CTA of the equaliser, 4 or 8
                               (default 4; 8 measured 12 % slower on GB300): the 32
                               symbols of an update block split over that many warps;
                               results equal to within FP32 rounding (the sums run in
                               another order)                                         */
+  RX_P_EQ_ALT = 30,        /* 1 (default): the equaliser's segments run on two banks of
+                              CTA pairs that take the waves by turns (4 P CTAs when
+                              they fit co-resident), so that each CTA rotates its next
+                              input window and folds the frequency tracker in the wave
+                              it sits out; 0: one bank runs every wave (2 P CTAs).
+                              Results are identical                                   */
+  RX_P_CDC_4STEP = 31      /* 1 (default): FP32 overlap-save windows of N = 4096 as a
+                              four-step transform (64-point DFTs in registers, two
+                              transposes through shared memory); 0: the radix-16
+                              Stockham plan every N uses.  Equal to within FP32
+                              rounding (the sums run in another order)              */
 };
 
 /* Stages reported by rx_profile. */

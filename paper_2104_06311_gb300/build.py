@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "librx.so")
 BUILD_DIR = os.path.join(HERE, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["cdc.cu", "eq.cu", "bps.cu", "ber.cu", "rx_api.cu", "noalloc.cu", "batch.cu", "cnn.cu", "kk.cu", "wl.cu",
+SOURCES = ["cdc.cu", "cdc64.cu", "eq.cu", "bps.cu", "ber.cu", "rx_api.cu", "noalloc.cu", "batch.cu", "cnn.cu", "kk.cu", "wl.cu",
            "rt.cu", "peak.cu"]
 
 

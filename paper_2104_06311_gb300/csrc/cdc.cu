@@ -661,9 +661,13 @@ cudaError_t launch_cdc(int N, int V, const void *tail, int64_t tail_first, int64
                        const void *call, int64_t call_first, int64_t call_n, int dtype,
                        float scale, const float2 *H, const float2 *tw, void *u,
                        int64_t u_base, int64_t u_stride, int64_t win_first, int64_t win_count,
-                       int64_t n_total, cudaStream_t s, int fmt, int sm_budget, int tc) {
-  // tc: the reduced formats' radix-16 passes on the tensor pipe (else register butterflies)
+                       int64_t n_total, cudaStream_t s, int fmt, int sm_budget, int tc, int four_step) {
+  // tc: the reduced formats' radix-16 passes on the tensor pipe (else register butterflies);
+  // four_step: N = 4096 in FP32 as 64 x 64 register DFTs (cdc64.cu), else radix-16 Stockham
   if (win_count <= 0) return cudaSuccess;
+  if (four_step && N == 4096 && fmt == RX_FMT_F32)
+    return launch_cdc4(V, tail, tail_first, tail_n, call, call_first, call_n, dtype, scale, H, tw,
+                       static_cast<float2 *>(u), u_base, u_stride, win_first, win_count, n_total, sm_budget, s);
   switch (fmt) {
     case RX_FMT_F32:
       return launch_cdc_fmt<RX_FMT_F32>(N, V, tail, tail_first, tail_n, call, call_first, call_n, dtype, scale, H, tw,

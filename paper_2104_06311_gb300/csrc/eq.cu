@@ -508,7 +508,9 @@ __device__ __forceinline__ V reduce_scatter(V (&v)[8], int j, ADD add) {
 template <int MB, int NW>
 __device__ __forceinline__ void run_span(const Hot hot, EqSmem<NW> &sm, const Span sp, const Lane &ln,
                                          float2 &own, float2 (&h)[8], Kahan &fo, int64_t n_limit,
-                                         bool pre = false) {
+                                         bool pre = false, bool ready = false) {
+  // pre: the first chunk's copies were issued earlier; ready: the caller has already
+  // converted the first chunk's window
   typedef Geo<NW> G;
   const int T = hot.T, c = hot.c, Bu = hot.Bu;
   const int chunk = (kChunkSym / Bu) * Bu;
@@ -547,10 +549,11 @@ __device__ __forceinline__ void run_span(const Hot hot, EqSmem<NW> &sm, const Sp
     chunk_window(cs, sp.ke, c, chunk, win_lo, count);
     const int nsteps = (int)((ce - cs + Bu - 1) / Bu);
     __syncthreads();  // every warp is done with the previous chunk's window
-    // (pre: the first chunk's copies were issued before the caller's grid barrier)
-    if (!(pre && cs == sp.kp))
-      window_issue<G::NT>(hot.u0, hot.u1, hot.u_fmt, sm, win_lo, count, n_limit, hot.u_lo, hot.u_hi);
-    window_finish<G::NT>(hot.u_fmt, sm, win_lo, count, sp.rot, n_limit, hot.err, hot.spin_ns);
+    if (!(ready && cs == sp.kp)) {
+      if (!(pre && cs == sp.kp))
+        window_issue<G::NT>(hot.u0, hot.u1, hot.u_fmt, sm, win_lo, count, n_limit, hot.u_lo, hot.u_hi);
+      window_finish<G::NT>(hot.u_fmt, sm, win_lo, count, sp.rot, n_limit, hot.err, hot.spin_ns);
+    }
     __syncthreads();
     const float2 *wq = wrow(sm, ln.q);
     // this lane's TPL window samples u_q[2k+c-i] of a step (zero for inactive symbols or
@@ -919,6 +922,20 @@ __device__ __forceinline__ void eq_body(const EqLaunch &L, const int cta, EqSmem
   auto ctr_taps = [&](int row) { return L.barrier + (2 + kWaveSlots + row) * kCtrStride; };
   auto part_target = [&](unsigned k) { return ((k / kWaveSlots) + 1u) * (unsigned)L.nblocks; };
   const int chunk = (kChunkSym / hot.Bu) * hot.Bu;
+  // Two-bank mode (L.alt, 4P CTAs): CTA pair s + P b (s < P, bank b = 0, 1) runs segment
+  // s of the waves v with (v - wave_first) mod 2 = b.  Every CTA then sits out every other
+  // wave, in which it folds the tracker and rotates its next window, so that a CTA's
+  // per-wave work (rotation, fold, publication) is off the chain of update steps: the
+  // waves follow each other at the pace of the last segment's steps and the hand-over
+  // of its end taps, not at that of one CTA's whole per-wave work.
+  const bool alt = L.alt != 0;
+  auto alt_seg = [&](int64_t v) -> int64_t {   // segment of wave v for this CTA pair, or -1
+    const int64_t v0 = v * L.P;
+    const int64_t nseg = min(v0 + (int64_t)L.P, L.n_segments) - v0;
+    const int bank = slot / L.P, s = slot % L.P;
+    if (nseg <= 0 || ((v - L.wave_first) & 1) != bank) return -1;
+    return s < nseg ? v0 + s : -1;
+  };
   bool pre = false;        // the next segment's first window is in flight
   bool have_taps = false;  // own / h hold row p's end taps of the previous wave
   for (int64_t w = L.wave_first; w < L.wave_last; ++w) {
@@ -937,15 +954,33 @@ __device__ __forceinline__ void eq_body(const EqLaunch &L, const int cta, EqSmem
     // the previous wave's last-segment rows
     bool ready = (w == L.wave_first) || have_taps;
     bool producer = false;
-    for (int64_t g = g0 + slot; g < g_end; g += nslots) {
+    bool taps_out = false;   // row p's end taps of this wave already published
+    const int64_t g_first = alt ? alt_seg(w) : g0 + slot;
+    const int64_t g_step = alt ? (int64_t)L.P : (int64_t)nslots;   // two banks: one at most
+    for (int64_t g = g_first; g >= 0 && g < g_end; g += g_step) {
+      Span sp = seg_span(g);
+      sp.rot = rot;
+      {
+        // the segment's first window before its start taps: the rotation is known, so
+        // the conversion is not on the path from the previous wave's end taps
+        int64_t lo;
+        int cnt;
+        chunk_window(sp.kp, sp.ke, hot.c, chunk, lo, cnt);
+        __syncthreads();   // every warp is done with the previous window
+        if (!pre) window_issue<G::NT>(hot.u0, hot.u1, hot.u_fmt, sm, lo, cnt, n_limit, hot.u_lo, hot.u_hi);
+        window_finish<G::NT>(hot.u_fmt, sm, lo, cnt, sp.rot, n_limit, hot.err, hot.spin_ns);
+        pre = false;
+      }
       if (have_taps) {
         have_taps = false;
       } else {
         if (!ready) {
-          // gentle polling: this wait is off the critical path (the producer runs ahead),
-          // and back-to-back acquire loads on the counter line would slow the producer's
-          // own memory operations there
-          if (!cta_wait(L.err, ctr_taps(p), i, sm, L.spin_ns, 8u, 64u)) {
+          // one-bank mode: gentle polling, the wait is off the critical path (the producer
+          // runs ahead) and back-to-back acquire loads on the counter line would slow the
+          // producer's own memory operations there; two-bank mode: the wait of the wave's
+          // last segment is the critical path, poll back to back
+          const bool crit = alt && g == g_end - 1;
+          if (!cta_wait(L.err, ctr_taps(p), i, sm, L.spin_ns, crit ? (1u << 20) : 8u, crit ? 32u : 64u)) {
             window_wait(sm, L.err, L.spin_ns);   // no copy left in flight
             return;
           }
@@ -953,19 +988,34 @@ __device__ __forceinline__ void eq_body(const EqLaunch &L, const int cta, EqSmem
         }
         load_row<NW>(own, h, start, p, ln);
       }
-      Span sp = seg_span(g);
-      sp.rot = rot;
       fo = Kahan{0.f, 0.f, 0.f, 0.f};
-      run_span<MB, NW>(hot, sm, sp, ln, own, h, fo, n_limit, pre);
-      pre = false;
+      run_span<MB, NW>(hot, sm, sp, ln, own, h, fo, n_limit, false, true);
+      if (alt && g == g_end - 1) {
+        // publish row p's end taps at once (warp 0 owns them): the next wave starts from
+        // them on the other bank
+        store_row(own, L.tap_slot + (i & (kWaveSlots - 1)) * 4 * kMaxTaps, trace_slot(L, w + 2), p, ln);
+        if (ln.warp == 0) {
+          __syncwarp();
+          if (ln.lane == 0) {
+            fence_acq_rel_gpu();
+            atomicAdd(ctr_taps(p), 1u);
+          }
+        }
+        taps_out = true;
+      }
       const float4 s = reduce_fo(sm, fo, ln);   // every warp is done with the window
       // this CTA's next segment (later in this wave, else in the next): its first
       // window's raw samples do not depend on the tracker, so their copies are
       // issued now and land during the waits and the fold
-      int64_t gn = g + nslots;
-      if (gn >= g_end) {
-        gn = (w + 1) * L.P + slot;
-        if (w + 1 >= L.wave_last || gn >= min(gn - slot + (int64_t)L.P, L.n_segments)) gn = -1;
+      int64_t gn = -1;
+      if (alt) {
+        for (int64_t v = w + 1; gn < 0 && v < L.wave_last && v <= w + 2; ++v) gn = alt_seg(v);
+      } else {
+        gn = g + nslots;
+        if (gn >= g_end) {
+          gn = (w + 1) * L.P + slot;
+          if (w + 1 >= L.wave_last || gn >= min(gn - slot + (int64_t)L.P, L.n_segments)) gn = -1;
+        }
       }
       if (gn >= 0) {
         const Span sn = seg_span(gn);
@@ -978,7 +1028,7 @@ __device__ __forceinline__ void eq_body(const EqLaunch &L, const int cta, EqSmem
       if (threadIdx.x == 0) __stcg(L.fo_part + (i & (kWaveSlots - 1)) * 2 * L.P + (g - g0) * 2 + p, s);
       // the last segment's end taps start wave w + 1 (trace entry w + 2)
       if (g == g_end - 1) {
-        store_row(own, L.tap_slot + (i & (kWaveSlots - 1)) * 4 * kMaxTaps, trace_slot(L, w + 2), p, ln);
+        if (!taps_out) store_row(own, L.tap_slot + (i & (kWaveSlots - 1)) * 4 * kMaxTaps, trace_slot(L, w + 2), p, ln);
         producer = true;
       }
     }
@@ -990,13 +1040,13 @@ __device__ __forceinline__ void eq_body(const EqLaunch &L, const int cta, EqSmem
     __syncthreads();
     if (threadIdx.x == (NW - 1) * 32) {
       fence_acq_rel_gpu();
-      if (producer) atomicAdd(ctr_taps(p), 1u);
+      if (producer && !taps_out) atomicAdd(ctr_taps(p), 1u);
       if (cta != L.no_arrive_cta) atomicAdd(ctr_part(i), 1u);
     }
     if (threadIdx.x == 0)
       sm.fail = (w > L.wave_first && !poll_ge(L.err, ctr_part(i - 1u), part_target(i - 1u), L.spin_ns, 4096u, 256u));
     __syncthreads();
-    have_taps = producer;
+    have_taps = producer && !alt;   // two banks: the other bank runs the next wave
     if (sm.fail) {
       window_wait(sm, L.err, L.spin_ns);
       return;

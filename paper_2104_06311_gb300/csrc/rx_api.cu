@@ -53,6 +53,8 @@ struct rx_stream {
   int64_t no_arrive = -1;           // RX_P_TEST_NO_ARRIVE: CTA left out of the wave barriers (-1: none)
   int dft_tc = 0;                   // RX_P_DFT_TC: reduced formats' radix-16 passes on the tensor pipe
   int eq_warps = 4;                 // RX_P_EQ_WARPS: warps per butterfly-row CTA of the equaliser
+  int eq_alt = 1;                   // RX_P_EQ_ALT: two banks of CTA pairs take the waves by turns
+  int cdc_4step = 1;                // RX_P_CDC_4STEP: N = 4096 FP32 windows as 64 x 64 register DFTs
   // ---- resolved
   int N = 0, V = 0, Sh = 0, P = 0, C = 256;
   int64_t A_full = 0, span = 0;
@@ -89,7 +91,8 @@ struct rx_stream {
   int *ber_sync = nullptr;
   int *h_err = nullptr;  // pinned mirror of the device error word
   cudaEvent_t err_ev = nullptr;
-  int eq_blocks = 0;
+  int eq_blocks = 0;                // equaliser CTAs of one bank (launch time: eq_grid)
+  int eq_alt_ok = 0;                // 4 P CTAs fit co-resident
   int sms = 0;                      // multiprocessors of the device
   int pieces = 12;                  // pipeline pieces per call (RX_P_PIPELINE)
   cudaStream_t sub[3] = {nullptr, nullptr, nullptr};   // CDC, equaliser, BPS streams
@@ -223,6 +226,12 @@ void release(rx_stream *rx) {
   rx->h_err = nullptr;
   rx->err_ev = nullptr;
   rx->reserved = false;
+}
+
+// Equaliser grid of a launch: 4 P CTAs in two-bank mode (two banks of P CTA pairs take
+// the waves by turns) when requested and co-resident, else eq_blocks.
+int eq_grid(const rx_stream *rx) {
+  return (rx->eq_alt && rx->eq_alt_ok && rx->eq_blocks == 2 * rx->P) ? 4 * rx->P : rx->eq_blocks;
 }
 
 rx_status init_device_state(rx_stream *rx) {
@@ -416,6 +425,8 @@ rx_status rx_set_param(rx_stream *rx, int key, double v) {
       if (v != 4.0 && v != 8.0) return fail(rx, RX_EINVAL, "equaliser warps per row must be 4 or 8");
       rx->eq_warps = (int)v;
       return RX_OK;
+    case RX_P_EQ_ALT: s = as_int(0, 1, &t); if (s == RX_OK) rx->eq_alt = (int)t; return s;
+    case RX_P_CDC_4STEP: s = as_int(0, 1, &t); if (s == RX_OK) rx->cdc_4step = (int)t; return s;
     default: return fail(rx, RX_EINVAL, "unknown parameter key");
   }
   if (s != RX_OK) return s;
@@ -460,6 +471,8 @@ rx_status rx_get_param(rx_stream *rx, int key, double *v) {
     case RX_P_TEST_NO_ARRIVE: *v = (double)rx->no_arrive; break;
     case RX_P_DFT_TC: *v = rx->dft_tc; break;
     case RX_P_EQ_WARPS: *v = rx->eq_warps; break;
+    case RX_P_EQ_ALT: *v = rx->eq_alt; break;
+    case RX_P_CDC_4STEP: *v = rx->cdc_4step; break;
     default: return fail(rx, RX_EINVAL, "unknown parameter key");
   }
   return RX_OK;
@@ -532,7 +545,11 @@ rx_status rx_reserve(rx_stream *rx, int64_t max_call) {
   if (e != cudaSuccess) { release(rx); return cuda_fail(rx, e, "pipeline streams"); }
   e = launch_tables(rx->H, rx->tw, rx->N, rx->baud, rx->L_km, rx->D, rx->lam_nm, rx->rolloff, rx->stream);
   if (e != cudaSuccess) { release(rx); return cuda_fail(rx, e, "filter tables"); }
-  rx->eq_blocks = 2 * std::min(rx->P, eq_max_blocks() / 2);
+  {
+    const int maxb = eq_max_blocks();
+    rx->eq_blocks = 2 * std::min(rx->P, maxb / 2);
+    rx->eq_alt_ok = 4 * rx->P <= maxb;
+  }
   {
     int dev = 0;
     cudaGetDevice(&dev);
@@ -717,7 +734,7 @@ rx_status rx_process(rx_stream *rx, const rx_in *in, rx_out *out) {
       RX_CUDA(launch_cdc(rx->N, rx->V, rx->tail[rx->cur_tail], rx->tail_first, rx->tail_n, in->data, call_first,
                          call_n, rx->dtype, (float)rx->in_scale, rx->H, rx->tw, rx->u[rx->cur_u], rx->u_base,
                          rx->u_cap, w_done, w_need - w_done, rx->n_total, rx->sub[0], rx->fmt,
-                         rx->pieces > 1 ? std::max(16, rx->sms - rx->eq_blocks) : 0, rx->dft_tc),
+                         rx->pieces > 1 ? std::max(16, rx->sms - eq_grid(rx)) : 0, rx->dft_tc, rx->cdc_4step),
               "cdc");
       w_done = w_need;
     }
@@ -767,7 +784,8 @@ rx_status rx_process(rx_stream *rx, const rx_in *in, rx_out *out) {
       L.inner_acq = (std::max(rx->n_cma, rx->acq_min) - rx->n_cma + rx->Bu - 1) / rx->Bu;
       L.inner_spb = (rx->W + rx->S + rx->Bu - 1) / rx->Bu;
       L.fo_track = rx->fo_track;
-      L.nblocks = rx->eq_blocks;
+      L.nblocks = eq_grid(rx);
+      L.alt = L.nblocks > rx->eq_blocks;
       L.u_fmt = rx->fmt;
       RX_CUDA(cudaMemsetAsync(rx->barrier, 0, kEqBarrierWords * sizeof(unsigned), rx->sub[1]), "barrier reset");
       StageTimer tm(rx, RX_STAGE_EQ, rx->sub[1]);

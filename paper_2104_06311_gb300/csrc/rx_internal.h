@@ -97,6 +97,9 @@ struct EqLaunch {
   int inner_spb;
   int fo_track;
   int nblocks;              // CTAs in the grid (even: 2 rows per segment slot)
+  int alt;                  // 1: nblocks = 4 P, two banks of P CTA pairs taking the waves by
+                            // turns (single stream); 0: pair s runs segments s, s + nblocks / 2,
+                            // ... of every wave
   int nw;                   // warps per butterfly-row CTA: 4 or 8 (0 = 4; the batched form uses 4)
   int u_fmt;                // storage format of u (RX_FMT_*)
 };
@@ -132,7 +135,13 @@ cudaError_t launch_cdc(int N, int V, const void *tail, int64_t tail_first, int64
                        const void *call, int64_t call_first, int64_t call_n, int dtype,
                        float scale, const float2 *H, const float2 *tw, void *u,
                        int64_t u_base, int64_t u_stride, int64_t win_first, int64_t win_count,
-                       int64_t n_total, cudaStream_t s, int fmt = RX_FMT_F32, int sm_budget = 0, int tc = 0);
+                       int64_t n_total, cudaStream_t s, int fmt = RX_FMT_F32, int sm_budget = 0, int tc = 0,
+                       int four_step = 1);
+// N = 4096, FP32 storage: the four-step (64 x 64) form of the same transform (cdc64.cu).
+cudaError_t launch_cdc4(int V, const void *tail, int64_t tail_first, int64_t tail_n, const void *call,
+                        int64_t call_first, int64_t call_n, int dtype, float scale, const float2 *H,
+                        const float2 *tw, float2 *u, int64_t u_base, int64_t u_stride, int64_t win_first,
+                        int64_t win_count, int64_t n_total, int sm_budget, cudaStream_t s);
 cudaError_t launch_eq(const EqLaunch &L, cudaStream_t s);
 // Batched equaliser: one cooperative launch of nblocks CTAs; d_team[b] =
 // (stream, CTA within that stream's team).  pad_smem: unused dynamic shared

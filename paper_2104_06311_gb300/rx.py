@@ -21,7 +21,7 @@ PARAMS = {
     "N_CMA": 8, "UPDATE_BLOCK": 9, "SEG_LEN": 10, "SEG_PRETRAIN": 11, "BPS_HALFWIN": 12,
     "BLOCK_SAMPLES": 13, "IN_SCALE": 14, "ACQ_MIN": 15, "FO_SMOOTH": 16, "FO_TRACK": 17,
     "LLR_OUT": 18, "SYM_OUT": 19, "EQ_OUT": 20, "CDC_OUT": 21, "PROFILE": 22, "PIPELINE": 23,
-    "PRECISION": 24, "INNER_TRACE": 25, "WAIT_LIMIT_US": 26, "TEST_NO_ARRIVE": 27, "DFT_TC": 28, "EQ_WARPS": 29,
+    "PRECISION": 24, "INNER_TRACE": 25, "WAIT_LIMIT_US": 26, "TEST_NO_ARRIVE": 27, "DFT_TC": 28, "EQ_WARPS": 29, "EQ_ALT": 30, "CDC_4STEP": 31,
 }
 STAGES = ["cdc", "eq", "bps", "move", "ber"]
 

@@ -181,6 +181,49 @@ def test_eq_eight_warps_per_row_parity(mod):
     print("8 warps", mod, rep)
 
 
+@pytest.mark.parametrize("chunk", [None, 40_000 * 2 + 64])
+def test_eq_two_banks_are_identical(chunk):
+    """Segments on two banks of CTA pairs taking the waves by turns (RX_P_EQ_ALT = 1, the
+    default: 4 P CTAs) against one bank for every wave (2 P CTAs): the same update chain in
+    the same order, so the equaliser output, the taps at every wave and the bits are
+    identical, in one call and streamed (each call its own launches), with a ragged
+    last wave."""
+    lk = L.workload("c2", n_sym=(1 << 17) + 3 * 1024 + 77)
+    g = L.generate(lk)
+    p = rx_params(lk, g.in_scale)
+    runs = {a: run_gpu(p, g.samples, chunk=chunk, EQ_ALT=a) for a in (0, 1)}
+    assert runs[1]["rx"].get_param("EQ_ALT") == 1 and runs[0]["rx"].get_param("EQ_ALT") == 0
+    assert runs[0]["n"] == runs[1]["n"]
+    assert np.array_equal(runs[0]["y"], runs[1]["y"])
+    assert np.array_equal(runs[0]["words"], runs[1]["words"])
+    assert np.array_equal(runs[0]["llr"], runs[1]["llr"])
+    n_waves = -(-(runs[0]["n"] - p.acq_len(runs[0]["n"])) // (p.wave_segments() * p.seg_len))
+    for w in range(-1, n_waves):
+        t0, t1 = runs[0]["rx"].trace(w), runs[1]["rx"].trace(w)
+        assert all(np.array_equal(np.asarray(a), np.asarray(b)) for a, b in zip(t0, t1)), w
+
+
+@pytest.mark.parametrize("adc,chunk", [("int8", None), ("int8", 30_000 * 2 + 64), ("f32", None)])
+def test_cdc_four_step_4096(adc, chunk):
+    """N = 4096 as 64 x 64 register DFTs (RX_P_CDC_4STEP = 1, the default) and as the
+    radix-16 Stockham plan (0): both against the FP64 oracle's overlap-save output,
+    int8 and FP32 input, one call and streamed (windows across the carried tail)."""
+    lk = L.Link(n_sym=70_000 + 321, L_km=4000.0, snr_db=14.0, adc=adc, seed=4096)
+    g = L.generate(lk)
+    p = rx_params(lk, g.in_scale, fft_n=4096)
+    assert p.fft_n == 4096
+    orc_u = O.cdc_overlap_save(L.deinterleave(g.samples) * g.in_scale, O.cdc_filter(p), p.overlap)
+    us = {}
+    for fs in (0, 1):
+        gpu = run_gpu(p, g.samples, chunk=chunk, CDC_4STEP=fs)
+        assert gpu["rx"].get_param("CDC_4STEP") == fs
+        us[fs] = gpu["u"][:, :orc_u.shape[1]]
+        err = rel_rms(us[fs], orc_u)
+        print(f"CDC_4STEP={fs} {adc} chunk={chunk}: rel RMS vs FP64 {err:.2e}")
+        assert err < 1e-6, (fs, err)
+    assert rel_rms(us[1], us[0]) < 1e-6
+
+
 @pytest.mark.parametrize("N", [256, 512, 2048, 4096, 8192, 16384])
 def test_cdc_fft_sizes(N):
     lk = L.Link(n_sym=20000 + 123, L_km=300.0, snr_db=15.0, seed=77 + N)
