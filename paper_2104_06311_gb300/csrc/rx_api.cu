@@ -734,7 +734,9 @@ rx_status rx_process(rx_stream *rx, const rx_in *in, rx_out *out) {
       RX_CUDA(launch_cdc(rx->N, rx->V, rx->tail[rx->cur_tail], rx->tail_first, rx->tail_n, in->data, call_first,
                          call_n, rx->dtype, (float)rx->in_scale, rx->H, rx->tw, rx->u[rx->cur_u], rx->u_base,
                          rx->u_cap, w_done, w_need - w_done, rx->n_total, rx->sub[0], rx->fmt,
-                         rx->pieces > 1 ? std::max(16, rx->sms - eq_grid(rx)) : 0, rx->dft_tc, rx->cdc_4step),
+                         // piece 0 runs before any equaliser launch: the whole GPU
+                         (rx->pieces > 1 && j > 0) ? std::max(16, rx->sms - eq_grid(rx)) : 0, rx->dft_tc,
+                         rx->cdc_4step),
               "cdc");
       w_done = w_need;
     }
