@@ -66,7 +66,7 @@ def parse():
 # ncu dram__bytes_read.sum + dram__bytes_write.sum of one step's eq_kernel launches per
 # symbol on the 10,000 km QPSK workload (13 launches of a 2^22-symbol step); None when
 # the kernel has changed since the counters were taken
-EQ_DRAM_BYTES_PER_SYMBOL = None
+EQ_DRAM_BYTES_PER_SYMBOL = 32.4
 # algorithmic equaliser work per dual-pol sample-time: FIR 2x2x15 complex MACs per
 # symbol (240 flop per sample-time) and the same for the LMS gradient
 EQ_FLOP_PER_SAMPLE_TIME = 480.0

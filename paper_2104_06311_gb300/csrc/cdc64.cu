@@ -169,28 +169,29 @@ __global__ void __launch_bounds__(kCdc4Threads, 2) cdc4_kernel(
         v[n1] = pol ? make_float2(f.z * scale, f.w * scale) : make_float2(f.x * scale, f.y * scale);
       }
     }
-    dft64(v);
-    twiddle_tm(v, t, tw);
+    // Four DFT-64 stages through one call site (the unrolled stages would not fit the
+    // instruction cache): 0 = pass A, 1 = pass B's first half, 2 = its second half,
+    // 3 = pass C.
+#pragma unroll 1
+    for (int st = 0; st < 4; ++st) {
+      dft64(v);
+      if (st == 1) {
+        // X[t + 64 k2] -> conj(X H): the inverse transform as the DFT of the conjugate
 #pragma unroll
-    for (int k1 = 0; k1 < 64; ++k1) buf[k1 * kPitch + t] = v[k1];
-    __syncthreads();
-    if (i + stride < win_count) issue(i + stride);   // the stage is free again
-    // ---- pass B: row k1 = t, DFT over n2 -> X[t + 64 k2], conj(X H), DFT over k2, W^{t n2}
+        for (int k2 = 0; k2 < 64; ++k2) v[k2] = cconj(cmul(v[k2], __ldg(&H[t + 64 * k2])));
+        continue;
+      }
+      if (st == 3) break;
+      // st 0: W^{t k1}, column t -> [k1][t], row t back; st 2: W^{t n2}, [n2][t], row t
+      twiddle_tm(v, t, tw);
+      __syncthreads();   // every read of the buffer (and of the stage) is done
 #pragma unroll
-    for (int n2 = 0; n2 < 64; ++n2) v[n2] = buf[t * kPitch + n2];
-    dft64(v);
+      for (int m = 0; m < 64; ++m) buf[m * kPitch + t] = v[m];
+      __syncthreads();
+      if (st == 0 && i + stride < win_count) issue(i + stride);   // the stage is free again
 #pragma unroll
-    for (int k2 = 0; k2 < 64; ++k2) v[k2] = cconj(cmul(v[k2], __ldg(&H[t + 64 * k2])));
-    dft64(v);
-    twiddle_tm(v, t, tw);
-    __syncthreads();   // every row of the buffer has been read
-#pragma unroll
-    for (int n2 = 0; n2 < 64; ++n2) buf[n2 * kPitch + t] = v[n2];
-    __syncthreads();
-    // ---- pass C: row n2 = t, DFT over k1, conjugate: samples t + 64 n1 of the window
-#pragma unroll
-    for (int k1 = 0; k1 < 64; ++k1) v[k1] = buf[t * kPitch + k1];
-    dft64(v);
+      for (int m = 0; m < 64; ++m) v[m] = buf[t * kPitch + m];
+    }
     {
       float2 *out = u + (int64_t)pol * u_stride;
       const int64_t n0 = (win_first + i) * S_hop - V / 2;   // stream index of element 0
