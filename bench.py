@@ -381,6 +381,11 @@ def bench_batch(args, rank, world, local):
                 "frac": achieved / pk["hbm_gbs"], "traffic": None, "kernel": stage}
     roof["peak_source"] = "measured (FMA chains, this run)" if roof["bound"] == "alu" else pk_kind
     Ns = sorted({int(b.get_param(ch, "FFT_N")) for ch in range(len(xs))})
+    # channels per (FFT size, CDC engine) the autotuner picked (engine 1: four-step)
+    picks = {}
+    for ch in range(len(xs)):
+        k = f"{int(b.get_param(ch, 'FFT_N'))}/{'four-step' if b.get_param(ch, 'CDC_ENGINE') else 'radix-16'}"
+        picks[k] = picks.get(k, 0) + 1
     line = {
         "metric": METRIC, "value": value, "unit": "GSa/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
@@ -388,7 +393,8 @@ def bench_batch(args, rank, world, local):
         "data": "synthetic (seeded linksim WDM channels), resident in HBM",
         "config": {"workload": f"{len(links_all)} WDM channels, 2^18-2^22 symbols/pol, 2000-10000 km, 10-32 GBd, "
                                "QPSK/16QAM, Es/N0 10-18 dB, int8 ADC; one enqueue per step (CUDA graph replay)",
-                   "sample_times": n_all, "fft_n_autotuned": Ns, "eq_ctas": int(b.get_param(-1, "EQ_CTAS")),
+                   "sample_times": n_all, "fft_n_autotuned": Ns, "cdc_autotuned": picks,
+                   "eq_ctas": int(b.get_param(-1, "EQ_CTAS")),
                    "l2": f"inputs ({n_all * 4 >> 20} MiB) and CDC intermediates exceed L2; no flush",
                    "parallelism": (f"channels sharded over {world} ranks (cost-balanced, no data-path collective)"
                                    if world > 1 else "one batch")},

@@ -74,13 +74,16 @@ enum {
   RX_BP_EQ_TEAM = 102,      /* read-only, per channel: CTAs of its equaliser team  */
   RX_BP_CDC_NS_PER_SAMPLE = 103, /* read-only, per channel: autotuned CDC kernel
                                     time per output sample-time [ns]               */
-  RX_BP_PROFILE = 104       /* 1 = time the stages of each call with CUDA events
+  RX_BP_PROFILE = 104,      /* 1 = time the stages of each call with CUDA events
                                (such calls run eagerly, not from the graph)        */
+  RX_BP_CDC_ENGINE = 105    /* read-only, per channel: the CDC kernel the autotuner
+                               picked, 0 = radix-16 Stockham, 1 = four-step 64 x 64
+                               (N = 4096)                                          */
 };
 
 /* Create a batch of n_ch channels (1..4096) and allocate all device state,
- * then run the autotuner (the first batch on a device times the CDC kernel
- * for each candidate FFT size; later batches reuse the table).  Synchronous.
+ * then run the autotuner (the first batch on a device times the CDC kernels
+ * for each candidate FFT size and engine; later batches reuse the table).  Synchronous.
  * Returns RX_EINVAL / RX_EUNSUPPORTED for a bad channel (its index is in
  * the message of rx_batch_last_error(*out) when *out is not NULL). */
 rx_status rx_batch_create(rx_batch **out, int n_ch, const rx_chan_cfg *cfgs);

@@ -62,6 +62,7 @@ constexpr double kStep16qam = 1.075;     // cost model: 16QAM update step / QPSK
 struct Chan {
   rx_chan_cfg cfg;
   int N = 0, V = 0, P = 0, C = 256, team = 2;
+  int engine = 0;             // CDC kernel: 0 radix-16 Stockham, 1 four-step (N = 4096)
   int64_t A_full = 0, span = 0, n_cap = 0, K_cap = 0;
   int64_t u_stride = 0, y_stride = 0, chunk_cap = 0, region_cap = 0, trace_cap = 0;
   double ns_per_sample = 0;
@@ -78,13 +79,14 @@ struct Chan {
 };
 
 std::mutex g_tune_mu;
-std::map<std::pair<int, int>, double> g_tune;   // (device, N) -> ns per window
+std::map<std::pair<int, int>, double> g_tune;   // (device, 2 N + engine) -> ns per window
 std::map<int, bool> g_tune_loaded;              // device -> persisted entries read
 
 // The tuning table can persist across processes in the text file named by the
-// environment variable RX_TUNE_CACHE: one line per entry, "<GPU name>|<SMs>|<N>|<ns
-// per window>".  Entries belong to the GPU model (name and SM count) they were
-// measured on; lines of other GPUs are kept when the file is rewritten.
+// environment variable RX_TUNE_CACHE: one line per entry, "<GPU name>|<SMs>|<N>|<engine>|
+// <ns per window>" (a line without the engine field is engine 0).  Entries belong to
+// the GPU model (name and SM count) they were measured on; lines of other GPUs are
+// kept when the file is rewritten.
 std::string gpu_key(int dev) {
   cudaDeviceProp prop;
   if (cudaGetDeviceProperties(&prop, dev) != cudaSuccess) return std::string();
@@ -116,10 +118,13 @@ void load_tune_cache(int dev) {
   const std::string key = gpu_key(dev);
   for (const std::string &l : cache_lines(path)) {
     if (l.compare(0, key.size() + 1, key + "|") != 0) continue;
-    int N = 0;
+    const char *rest = l.c_str() + key.size() + 1;
+    int N = 0, eng = 0;
     double ns = 0.0;
-    if (sscanf(l.c_str() + key.size() + 1, "%d|%lf", &N, &ns) == 2 && N >= 256 && N <= 16384 && ns > 0.0)
-      g_tune[{dev, N}] = ns;
+    const bool three = std::count(l.begin() + key.size() + 1, l.end(), '|') == 2;
+    const bool ok = three ? sscanf(rest, "%d|%d|%lf", &N, &eng, &ns) == 3 : sscanf(rest, "%d|%lf", &N, &ns) == 2;
+    if (ok && N >= 256 && N <= 16384 && (eng == 0 || (eng == 1 && N == 4096)) && ns > 0.0)
+      g_tune[{dev, 2 * N + eng}] = ns;
   }
 }
 
@@ -136,7 +141,8 @@ void save_tune_cache(int dev) {
   if (!f) return;
   for (const std::string &l : keep) fprintf(f, "%s\n", l.c_str());
   for (const auto &kv : g_tune)
-    if (kv.first.first == dev) fprintf(f, "%s|%d|%.6g\n", key.c_str(), kv.first.second, kv.second);
+    if (kv.first.first == dev)
+      fprintf(f, "%s|%d|%d|%.6g\n", key.c_str(), kv.first.second / 2, kv.first.second % 2, kv.second);
   fclose(f);
   rename(tmp.c_str(), path);
 }
@@ -270,7 +276,8 @@ rx_status check_cfg(rx_batch *b, int i, const rx_chan_cfg &c) {
   return RX_OK;
 }
 
-// ns per CDC window for every FFT size, measured once per device.
+// ns per CDC window for every FFT size and CDC engine (0: radix-16 Stockham, 1: the
+// four-step kernel, N = 4096 only), measured once per device; out is keyed 2 N + engine.
 rx_status tune_table(rx_batch *b, std::map<int, double> &out) {
   int dev = 0, sms = 0;
   BX_CUDA(cudaGetDevice(&dev), "device");
@@ -278,10 +285,12 @@ rx_status tune_table(rx_batch *b, std::map<int, double> &out) {
   std::lock_guard<std::mutex> lock(g_tune_mu);
   load_tune_cache(dev);
   bool measured = false;
-  for (int N = 256; N <= 16384; N *= 2) {
-    auto it = g_tune.find({dev, N});
+  for (int ke = 2 * 256; ke <= 2 * 16384 + 1; ++ke) {
+    const int N = ke / 2, eng = ke % 2;
+    if ((N & (N - 1)) != 0 || (eng == 1 && N != 4096)) continue;
+    auto it = g_tune.find({dev, ke});
     if (it != g_tune.end()) {
-      out[N] = it->second;
+      out[ke] = it->second;
       continue;
     }
     const int V = 32;
@@ -302,7 +311,7 @@ rx_status tune_table(rx_batch *b, std::map<int, double> &out) {
       e = cudaEventRecord(e0, b->stream);
       if (e == cudaSuccess)
         e = launch_cdc(N, V, nullptr, 0, 0, in, 0, n, RX_I8x4, 1.f, (const float2 *)H, (const float2 *)tw,
-                       (float2 *)uu, 0, n, 0, nw, n, b->stream);
+                       (float2 *)uu, 0, n, 0, nw, n, b->stream, RX_FMT_F32, 0, 0, eng);
       if (e == cudaSuccess) e = cudaEventRecord(e1, b->stream);
       if (e == cudaSuccess) e = cudaEventSynchronize(e1);
       float ms = 0.f;
@@ -317,8 +326,8 @@ rx_status tune_table(rx_batch *b, std::map<int, double> &out) {
     cudaFree(tw);
     if (e != cudaSuccess) return bcuda(b, e, "autotuner");
     const double ns = (double)best * 1e6 / (double)nw;
-    g_tune[{dev, N}] = ns;
-    out[N] = ns;
+    g_tune[{dev, ke}] = ns;
+    out[ke] = ns;
     measured = true;
   }
   if (measured) save_tune_cache(dev);
@@ -429,7 +438,8 @@ rx_status enqueue(rx_batch *b, const rx_in *ins, rx_out *outs, cudaStream_t s, b
       if (n == 0) continue;
       const int Sh = c.N - c.V;
       BX_CUDA(launch_cdc(c.N, c.V, nullptr, 0, 0, ins[i].data, 0, n, ins[i].dtype, (float)c.cfg.in_scale, c.H, c.tw,
-                         c.u, 0, c.u_stride, 0, (n + Sh - 1) / Sh, n, b->side[smap[i]], RX_FMT_F32, side_sm_budget()),
+                         c.u, 0, c.u_stride, 0, (n + Sh - 1) / Sh, n, b->side[smap[i]], RX_FMT_F32, side_sm_budget(),
+                         0, c.engine),
               "cdc");
       launches[RX_STAGE_CDC] += 1;
     }
@@ -536,20 +546,21 @@ rx_status rx_batch_create(rx_batch **out, int n_ch, const rx_chan_cfg *cfgs) {
   if (s != RX_OK) return s;
   for (int i = 0; i < n_ch; ++i) {
     Chan &c = b->ch[i];
-    if (c.cfg.fft_n) {
-      c.N = c.cfg.fft_n;
-    } else {
-      double best = 1e300;
-      for (const auto &kv : tab) {
-        if (c.V >= kv.first / 2) continue;
-        const double per = kv.second / (double)(kv.first - c.V);
-        if (per < best) {
-          best = per;
-          c.N = kv.first;
-        }
+    // the admissible (N, engine) with the least time per output sample (N fixed when the
+    // channel asks for one)
+    double best = 1e300;
+    for (const auto &kv : tab) {
+      const int N = kv.first / 2;
+      if (c.cfg.fft_n ? N != c.cfg.fft_n : c.V >= N / 2) continue;
+      const double per = kv.second / (double)(N - c.V);
+      if (per < best) {
+        best = per;
+        c.N = N;
+        c.engine = kv.first % 2;
       }
     }
-    c.ns_per_sample = tab[c.N] / (double)(c.N - c.V);
+    if (c.cfg.fft_n && best > 1e299) c.N = c.cfg.fft_n, c.engine = 0;
+    c.ns_per_sample = tab[2 * c.N + c.engine] / (double)(c.N - c.V);
   }
   // equaliser launch: co-resident CTA budget and teams
   b->pad_smem = 0;
@@ -689,6 +700,7 @@ rx_status rx_batch_get_param(rx_batch *b, int ch, int key, double *v) {
     case RX_P_FO_TRACK: *v = (c.cfg.flags & RX_CH_NO_FO_TRACK) ? 0 : 1; break;
     case RX_BP_EQ_TEAM: *v = c.team; break;
     case RX_BP_CDC_NS_PER_SAMPLE: *v = c.ns_per_sample; break;
+    case RX_BP_CDC_ENGINE: *v = c.engine; break;
     default: return bfail(b, RX_EINVAL, "unknown channel parameter");
   }
   return RX_OK;

@@ -960,9 +960,9 @@ __device__ __forceinline__ void eq_body(const EqLaunch &L, const int cta, EqSmem
     for (int64_t g = g_first; g >= 0 && g < g_end; g += g_step) {
       Span sp = seg_span(g);
       sp.rot = rot;
-      {
-        // the segment's first window before its start taps: the rotation is known, so
-        // the conversion is not on the path from the previous wave's end taps
+      if (alt) {
+        // two banks: the segment's first window before its start taps (the rotation is
+        // known), so the conversion is not on the path from the previous wave's end taps
         int64_t lo;
         int cnt;
         chunk_window(sp.kp, sp.ke, hot.c, chunk, lo, cnt);
@@ -989,7 +989,10 @@ __device__ __forceinline__ void eq_body(const EqLaunch &L, const int cta, EqSmem
         load_row<NW>(own, h, start, p, ln);
       }
       fo = Kahan{0.f, 0.f, 0.f, 0.f};
-      run_span<MB, NW>(hot, sm, sp, ln, own, h, fo, n_limit, false, true);
+      // one bank (and the batched form): the window after the taps, inside run_span,
+      // its copies landing meanwhile
+      run_span<MB, NW>(hot, sm, sp, ln, own, h, fo, n_limit, pre, alt);
+      pre = false;
       if (alt && g == g_end - 1) {
         // publish row p's end taps at once (warp 0 owns them): the next wave starts from
         // them on the other bank

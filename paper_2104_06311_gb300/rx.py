@@ -43,7 +43,8 @@ EXPORTS = ["rx_create", "rx_set_param", "rx_get_param", "rx_set_cuda_stream", "r
            "rx_rt_bins", "rx_rt_profile", "rx_rt_destroy", "rx_rt_last_error", "rx_q_db"]
 WL_PARAMS = {"MU": 1, "SEG_LEN": 2, "PRETRAIN": 3, "ACQ": 4, "LINEAR": 5}
 CNN_KINDS = ["fwd_hidden", "fwd_edge", "dx", "dw", "update"]
-BATCH_PARAMS = {"GRAPH": 100, "EQ_CTAS": 101, "EQ_TEAM": 102, "CDC_NS_PER_SAMPLE": 103, "PROFILE": 104}
+BATCH_PARAMS = {"GRAPH": 100, "EQ_CTAS": 101, "EQ_TEAM": 102, "CDC_NS_PER_SAMPLE": 103, "PROFILE": 104,
+                "CDC_ENGINE": 105}
 
 
 class rx_in(ct.Structure):
