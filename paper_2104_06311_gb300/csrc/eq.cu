@@ -745,7 +745,7 @@ __device__ __forceinline__ void trace_fo(const EqLaunch &L, int64_t idx, double 
 
 // One CTA's part of an equaliser launch: CTA `cta` of the L.nblocks CTAs that
 // serve this stream (a whole grid, or a team inside a batched grid).
-template <int MB, int NW>
+template <int MB, int NW, bool BANKS>
 __device__ __forceinline__ void eq_body(const EqLaunch &L, const int cta, EqSmem<NW> &sm) {
   typedef Geo<NW> G;
   Lane ln;
@@ -928,7 +928,9 @@ __device__ __forceinline__ void eq_body(const EqLaunch &L, const int cta, EqSmem
   // per-wave work (rotation, fold, publication) is off the chain of update steps: the
   // waves follow each other at the pace of the last segment's steps and the hand-over
   // of its end taps, not at that of one CTA's whole per-wave work.
-  const bool alt = L.alt != 0;
+  // BANKS = false compiles the one-bank schedule alone (the batched form); the single
+  // stream reads the mode at run time
+  const bool alt = BANKS && L.alt != 0;
   auto alt_seg = [&](int64_t v) -> int64_t {   // segment of wave v for this CTA pair, or -1
     const int64_t v0 = v * L.P;
     const int64_t nseg = min(v0 + (int64_t)L.P, L.n_segments) - v0;
@@ -957,7 +959,7 @@ __device__ __forceinline__ void eq_body(const EqLaunch &L, const int cta, EqSmem
     bool taps_out = false;   // row p's end taps of this wave already published
     const int64_t g_first = alt ? alt_seg(w) : g0 + slot;
     const int64_t g_step = alt ? (int64_t)L.P : (int64_t)nslots;   // two banks: one at most
-    for (int64_t g = g_first; g >= 0 && g < g_end; g += g_step) {
+    for (int64_t g = g_first; (!alt || g >= 0) && g < g_end; g += g_step) {
       Span sp = seg_span(g);
       sp.rot = rot;
       if (alt) {
@@ -1090,7 +1092,7 @@ __device__ __forceinline__ void eq_body(const EqLaunch &L, const int cta, EqSmem
 template <int MB, int NW>
 __global__ void __launch_bounds__(NW * 32, 1) eq_kernel(EqLaunch L) {
   __shared__ EqSmem<NW> sm;
-  eq_body<MB, NW>(L, (int)blockIdx.x, sm);
+  eq_body<MB, NW, true>(L, (int)blockIdx.x, sm);
 }
 
 // Unused dynamic shared memory that keeps the equaliser's SMs to itself: the
@@ -1123,8 +1125,8 @@ __global__ void __launch_bounds__(kEqThreads, 3) eq_batch_kernel(const EqLaunch 
   __shared__ EqSmem<4> sm;
   const int2 t = team[blockIdx.x];
   const EqLaunch &L = Ls[t.x];
-  if (L.mod_bits == 4) eq_body<4, 4>(L, t.y, sm);
-  else eq_body<2, 4>(L, t.y, sm);
+  if (L.mod_bits == 4) eq_body<4, 4, false>(L, t.y, sm);
+  else eq_body<2, 4, false>(L, t.y, sm);
 }
 
 int eq_batch_max_blocks(int pad_smem) {
