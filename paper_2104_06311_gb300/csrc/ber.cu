@@ -64,21 +64,46 @@ __global__ void ber_sync_kernel(const uint32_t *rx, int64_t rxs, const uint32_t 
   }
 }
 
-// acc[0] = errors, acc[1] = bits counted; sync = (q, r, d) per rx pol
+// Gray rotation by j of every m-bit symbol field of a 32-bit word of packed bits (the
+// per-symbol map above, applied to all fields at once): QPSK fields (b0, b1) ->
+// (!b1, b0); 16QAM fields (b0, b1, b2, b3) -> (!b2, b3, b0, b1).
+__device__ __forceinline__ uint32_t rotate_word(uint32_t w, int r, int m) {
+  for (int i = 0; i < r; ++i)
+    w = m == 2 ? (((~w) >> 1) & 0x55555555u) | ((w << 1) & 0xAAAAAAAAu)
+               : ((((w >> 2) & 0x33333333u) ^ 0x11111111u) | ((w << 2) & 0xCCCCCCCCu));
+  return w;
+}
+
+// acc[0] = errors, acc[1] = bits counted; sync = (q, r, d) per rx pol.  One thread per
+// 32-bit word of received bits (32 / m symbols): the reference word of the same
+// symbols, delayed by d, is the funnel shift of two neighbouring reference words,
+// rotated field-wise; symbols outside [k0, K) and with k + d outside [0, K) are masked.
 __global__ void ber_count_kernel(const uint32_t *rx, int64_t rxs, const uint32_t *ref, int64_t refs,
                                  int64_t K, int m, int64_t k0, const int *sync,
                                  unsigned long long *acc) {
   const int p = blockIdx.y;
   const int q = sync[3 * p], r = sync[3 * p + 1], d = sync[3 * p + 2];
+  const int W = 32 / m;                                // symbols per word
+  const int64_t n_words = (K * m + 31) / 32;           // words of K symbols
+  const uint32_t *rrow = rx + p * rxs, *frow = ref + q * refs;
+  const int64_t lo_all = max(k0, (int64_t)-d), hi_all = min(K, K - (int64_t)d);
   unsigned long long e = 0, n = 0;
-  for (int64_t k = k0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < K;
-       k += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t kk = k + d;
-    if (kk < 0 || kk >= K) continue;
-    const unsigned a = sym_bits(rx + p * rxs, k, m);
-    const unsigned b = rotate_bits(sym_bits(ref + q * refs, kk, m), r, m);
-    e += __popc(a ^ b);
-    n += m;
+  for (int64_t w = (k0 / W) + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < n_words;
+       w += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t s0 = w * W;
+    const int64_t lo = max(lo_all, s0), hi = min(hi_all, s0 + W);
+    if (hi <= lo) continue;
+    const int b0 = (int)(lo - s0) * m, b1 = (int)(hi - s0) * m;   // valid bits [b0, b1)
+    const uint32_t mask = (b1 >= 32 ? 0xFFFFFFFFu : ((1u << b1) - 1u)) & ~((1u << b0) - 1u);
+    // reference bits of symbols s0 + d .. : bit offset 32 w + d m (d m may be negative)
+    const int64_t bit = 32 * w + (int64_t)d * m;
+    const int64_t fw = bit >= 0 ? bit / 32 : -((-bit + 31) / 32);
+    const int sh = (int)(bit - 32 * fw);
+    const uint32_t lo_w = (fw >= 0 && fw < n_words) ? frow[fw] : 0u;
+    const uint32_t hi_w = (fw + 1 >= 0 && fw + 1 < n_words) ? frow[fw + 1] : 0u;
+    const uint32_t refw = rotate_word(__funnelshift_r(lo_w, hi_w, sh), r, m);
+    e += __popc((rrow[w] ^ refw) & mask);
+    n += __popc(mask);
   }
   for (int o = 16; o > 0; o >>= 1) {
     e += __shfl_down_sync(0xffffffffu, e, o);
@@ -102,7 +127,8 @@ cudaError_t launch_ber_count(const uint32_t *rx, int64_t rxs, const uint32_t *re
                              unsigned long long *acc, cudaStream_t s) {
   const int64_t n = K - k0;
   if (n <= 0) return cudaSuccess;
-  unsigned blocks = (unsigned)min((int64_t)1216, (n + 255) / 256);
+  const int64_t words = (n * m + 31) / 32 + 1;
+  unsigned blocks = (unsigned)min((int64_t)1216, (words + 255) / 256);
   ber_count_kernel<<<dim3(blocks, 2), 256, 0, s>>>(rx, rxs, ref, refs, K, m, k0, sync, acc);
   return cudaGetLastError();
 }
