@@ -14,6 +14,11 @@ named directly.
 * The equaliser's window rotation advances the turn of a thread's samples by
   exact modular 64-bit steps: Phi + (n - n0) delta (mod 2^64) is the same for the
   direct product and for the start value plus r times the step.
+* The BER count over 32-bit words: the reference word of a received word's
+  symbols, delayed by d, is the funnel shift of two neighbouring reference words by
+  d m bits; the Gray rotation by j applies to every m-bit field at once with masks
+  and shifts; masking the symbols outside the counted range gives the oracle's
+  per-symbol count (oracle.chain.ber_sync_count's counting rule).
 """
 import numpy as np
 
@@ -93,3 +98,65 @@ def test_rotation_turns_by_modular_steps():
             n = win_lo + tid + 128 * r
             direct = (phi + ((n - n0) % M) * delta) % M
             assert (ph0 + r * step) % M == direct
+
+
+M32 = 0xFFFFFFFF
+
+
+def _rotate_word(w, r, m):
+    """The field-wise Gray rotation of the BER count kernel."""
+    for _ in range(r):
+        if m == 2:
+            w = (((~w & M32) >> 1) & 0x55555555) | ((w << 1) & 0xAAAAAAAA)
+        else:
+            w = (((w >> 2) & 0x33333333) ^ 0x11111111) | ((w << 2) & 0xCCCCCCCC)
+        w &= M32
+    return w
+
+
+def _count_words(rx, ref, K, m, k0, q, r, d, p):
+    """The word-wide count the BER kernel makes: one 32-bit word of received bits at a
+    time, the delayed reference word by a funnel shift, the valid symbols masked."""
+    W, nw = 32 // m, (K * m + 31) // 32
+    lo_all, hi_all = max(k0, -d), min(K, K - d)
+    e = n = 0
+    for w in range(k0 // W, nw):
+        s0 = w * W
+        lo, hi = max(lo_all, s0), min(hi_all, s0 + W)
+        if hi <= lo:
+            continue
+        b0, b1 = (lo - s0) * m, (hi - s0) * m
+        mask = (M32 if b1 >= 32 else (1 << b1) - 1) & ~((1 << b0) - 1) & M32
+        bit = 32 * w + d * m
+        fw = bit // 32
+        sh = bit - 32 * fw
+        low = int(ref[q][fw]) if 0 <= fw < nw else 0
+        high = int(ref[q][fw + 1]) if 0 <= fw + 1 < nw else 0
+        refw = _rotate_word(((high << 32 | low) >> sh) & M32, r, m)
+        e += bin((int(rx[p][w]) ^ refw) & mask).count("1")
+        n += bin(mask).count("1")
+    return e, n
+
+
+def test_word_wide_ber_count_equals_the_per_symbol_count():
+    import oracle.chain as OC
+    mods = {2: "qpsk", 4: "16qam"}
+    for m in (2, 4):
+        for K in (777, 1000, 1003):
+            nw = (K * m + 31) // 32
+            rx = RNG.integers(0, 2 ** 32, size=(2, nw), dtype=np.uint64)
+            ref = RNG.integers(0, 2 ** 32, size=(2, nw), dtype=np.uint64)
+            # unpacked bits (the oracle's layout: bit t of symbol k at k m + t, LSB first)
+            unpack = lambda a: ((a[:, :, None] >> np.arange(32, dtype=np.uint64)) & 1).reshape(2, -1)[:, :K * m]
+            rxb, refb = unpack(rx).astype(np.uint8), unpack(ref).astype(np.uint8)
+            for _ in range(12):
+                k0 = int(RNG.integers(0, 300))
+                q, r, p, d = int(RNG.integers(0, 2)), int(RNG.integers(0, 4)), int(RNG.integers(0, 2)), \
+                    int(RNG.integers(-64, 65))
+                # the per-symbol definition: the oracle's rotation of the reference, delayed
+                rot = OC._rotate_bits(refb, r, mods[m]).reshape(2, K, m)
+                a = rxb.reshape(2, K, m)
+                k = np.arange(k0, K)
+                ok = (k + d >= 0) & (k + d < K)
+                e = int(np.sum(a[p, k[ok]] != rot[q, (k + d)[ok]]))
+                assert _count_words(rx, ref, K, m, k0, q, r, d, p) == (e, int(ok.sum()) * m)
